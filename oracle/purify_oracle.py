@@ -1,0 +1,387 @@
+"""Plain FP64 CPU oracle for recursive polynomial purification with the
+non-monotonic scale-and-fold schemes of E. H. Rubensson, "Non-monotonic
+recursive polynomial expansions for linear scaling calculation of the density
+matrix" (arXiv:1101.0265).
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import, call or
+execute this module: only the tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` use it.  It shares no code with
+the CUDA library and imports nothing from the product package.
+
+Everything is float64 numpy.  Matrix products use ``@`` (a library primitive);
+there is no blocking, fusion or reordering beyond the steps the paper states.
+Each function names the passage it follows.
+
+Two kinds of result (the paper's target function and its recursion):
+
+* the plain definition D = theta(mu I - F) (the introduction's statement of
+  the problem), by eigendecomposition or, for generated inputs, in closed
+  form from the known eigenvectors;
+* the recursion itself (Eq. 1 with the polynomials of Algorithm 1 and
+  Algorithm 2), step by step, with the scalar schedule (alpha, beta, beta-bar)
+  that accompanies it; needed for iteration counts, multiplication counts and
+  parity at a fixed number of steps.
+
+Readings where the paper is silent (each also listed in the design notes):
+
+* Loop bound.  The algorithms loop "for i = 1, 2, ..., n" with no stop rule.
+  In exact arithmetic the unoccupied eigenvalues of X_i lie in [0, beta_i] and
+  the occupied ones in [beta-bar_i, 1] (Algorithm 1: beta-bar = 1 - beta by
+  the symmetry P11(1 - x) = 1 - P11(x)), so ||X_i - D||_2 <= max(beta_i,
+  1 - beta-bar_i), which is the accuracy measure of Fig. 3.  The loop stops
+  once that bound is <= tol, or after max_iter iterations.
+* Tie in Algorithm 2's branch test: the test is strict, (beta + beta-bar) > 1,
+  evaluated in float64 in that order; a tie takes the P01 branch.
+* Asymmetric gap in Algorithm 1 (the paper assumes the gap symmetric around
+  mu): beta_0 = 1/2 - min(mu - homo, lumo - mu) / gamma, the nearer edge.
+* Niklasson's trace rule (the alpha = 0 relative of Algorithm 2): take the
+  P10 branch when trace(X_{i-1}) > nocc, otherwise P01.
+* Multiplication count: Algorithm 1 uses two matrix products per iteration
+  (X_s^2 and X_s^2 X_s), Algorithm 2 one (the square).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SCHEMES = ("FIXED_MU_SF", "FIXED_MU_MONO", "TC_SF", "TC_MONO")
+
+
+# ---------------------------------------------------------------------------
+# The P_{i,j} polynomials used by the schemes (paper: notation P_{i,j} of
+# degree 1 + i + j with fixed points 0 and 1; P_{1,0} = x^2, P_{0,1} = 2x - x^2;
+# Algorithm 1 uses P_{1,1} = 3x^2 - 2x^3).
+# ---------------------------------------------------------------------------
+
+def P10(x):
+    return x * x
+
+
+def P01(x):
+    return 2.0 * x - x * x
+
+
+def P11(x):
+    return 3.0 * x * x - 2.0 * x * x * x
+
+
+# ---------------------------------------------------------------------------
+# Result record
+# ---------------------------------------------------------------------------
+
+@dataclass
+class Result:
+    scheme: str
+    iterations: int = 0
+    multiplications: int = 0
+    converged: bool = False
+    alphas: list = field(default_factory=list)
+    branches: list = field(default_factory=list)   # Algorithm 2: "P10" / "P01"
+    betas: list = field(default_factory=list)      # beta after each iteration
+    betabars: list = field(default_factory=list)   # beta-bar after each iteration
+    traces: list = field(default_factory=list)     # trace(X_i) after each iteration
+    idem: list = field(default_factory=list)       # ||X_{i-1} - X_{i-1}^2||_F (Algorithm 2)
+    beta0: float = float("nan")
+    betabar0: float = float("nan")
+    f0: tuple = ()                                 # (c0, c1): X_0 = c0 I + c1 F
+
+    @property
+    def err_bound(self) -> float:
+        if not self.betas:
+            return float("nan")
+        return max(self.betas[-1], 1.0 - self.betabars[-1])
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1: McWeeny-based fixed-mu purification with scaling
+# ---------------------------------------------------------------------------
+
+def fixed_mu_gamma(lmin: float, lmax: float, mu: float) -> float:
+    """Algorithm 1, first step: gamma = 2 max(lambda_max - mu, mu - lambda_min)."""
+    return 2.0 * max(lmax - mu, mu - lmin)
+
+
+def fixed_mu_beta0(gamma: float, mu: float, homo: float, lumo: float) -> float:
+    """Algorithm 1, beta = 0.5 (1 - xi / gamma) for a gap xi centred on mu.
+    For an off-centre gap the nearer edge is used (see module docstring)."""
+    half = min(mu - homo, lumo - mu)
+    return 0.5 - half / gamma
+
+
+def fixed_mu_alpha(beta: float) -> float:
+    """Algorithm 1: alpha = 3 / sqrt(12 beta^2 - 18 beta + 9), the alpha >= 1
+    that solves Eq. 3 for P_{1,1}."""
+    return 3.0 / math.sqrt(12.0 * beta * beta - 18.0 * beta + 9.0)
+
+
+def fixed_mu_schedule(beta: float, tol: float, max_iter: int, scaled: bool = True):
+    """Scalar part of Algorithm 1: the alpha of each iteration and the beta
+    after it.  Stops once beta <= tol (module docstring) or at max_iter."""
+    alphas, betas = [], []
+    while beta > tol and len(alphas) < max_iter:
+        alpha = fixed_mu_alpha(beta) if scaled else 1.0
+        beta_s = alpha * (beta - 0.5) + 0.5
+        beta = 3.0 * beta_s * beta_s - 2.0 * beta_s * beta_s * beta_s
+        alphas.append(alpha)
+        betas.append(beta)
+    return alphas, betas
+
+
+def purify_fixed_mu(F, lmin, lmax, mu, homo, lumo, tol=1e-12, max_iter=200, scaled=True):
+    """Algorithm 1 on a dense symmetric F; scaled=False gives the regular
+    grand-canonical McWeeny purification (alpha = 1), which the paper uses as
+    its reference for this scheme."""
+    F = np.asarray(F, dtype=np.float64)
+    n = F.shape[0]
+    I = np.eye(n)
+    gamma = fixed_mu_gamma(lmin, lmax, mu)
+    X = (mu * I - F) / gamma + 0.5 * I
+    beta = fixed_mu_beta0(gamma, mu, homo, lumo)
+    res = Result(scheme="FIXED_MU_SF" if scaled else "FIXED_MU_MONO", beta0=beta,
+                 betabar0=1.0 - beta, f0=(mu / gamma + 0.5, -1.0 / gamma))
+    alphas, betas = fixed_mu_schedule(beta, tol, max_iter, scaled)
+    for alpha, beta_i in zip(alphas, betas):
+        Xs = alpha * (X - 0.5 * I) + 0.5 * I
+        Xs2 = Xs @ Xs
+        X = 3.0 * Xs2 - 2.0 * (Xs2 @ Xs)
+        res.alphas.append(alpha)
+        res.betas.append(beta_i)
+        res.betabars.append(1.0 - beta_i)
+        res.traces.append(float(np.trace(X)))
+        res.iterations += 1
+        res.multiplications += 2
+    res.converged = bool(betas) and betas[-1] <= tol or (not betas and beta <= tol)
+    return X, res
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 2: P_{0,1} & P_{1,0} based varying-mu purification with scaling
+# ---------------------------------------------------------------------------
+
+def tc_f0(lmin: float, lmax: float):
+    """Algorithm 2: X_0 = (lambda_max I - F) / (lambda_max - lambda_min),
+    returned as (c0, c1) with X_0 = c0 I + c1 F."""
+    w = lmax - lmin
+    return lmax / w, -1.0 / w
+
+
+def tc_beta0(lmin, lmax, homo, lumo):
+    """Algorithm 2: beta = f_0(lambda_lumo), beta-bar = f_0(lambda_homo)."""
+    w = lmax - lmin
+    return (lmax - lumo) / w, (lmax - homo) / w
+
+
+def tc_branch_by_beta(beta: float, betabar: float) -> str:
+    """Algorithm 2's test: P10 when beta + beta-bar > 1 (strict), else P01."""
+    return "P10" if (beta + betabar) > 1.0 else "P01"
+
+
+def tc_alpha(branch: str, beta: float, betabar: float) -> float:
+    """Algorithm 2: alpha = beta / (2 - beta) before x^2, alpha =
+    (1 - beta-bar) / (1 + beta-bar) before 2x - x^2."""
+    if branch == "P10":
+        return beta / (2.0 - beta)
+    return (1.0 - betabar) / (1.0 + betabar)
+
+
+def tc_map(branch: str, alpha: float, x: float) -> float:
+    """The scalar form of Eq. 4 (P10 branch) and Eq. 5 (P01 branch), used on
+    beta and beta-bar."""
+    if branch == "P10":
+        y = (1.0 + alpha) * x - alpha
+        return y * y
+    return 2.0 * (1.0 + alpha) * x - (1.0 + alpha) ** 2 * x * x
+
+
+def tc_schedule(beta: float, betabar: float, tol: float, max_iter: int, scaled: bool = True):
+    """Scalar part of Algorithm 2 with the beta rule: per iteration the
+    branch, alpha, and (beta, beta-bar) after it."""
+    out = []
+    while max(beta, 1.0 - betabar) > tol and len(out) < max_iter:
+        branch = tc_branch_by_beta(beta, betabar)
+        alpha = tc_alpha(branch, beta, betabar) if scaled else 0.0
+        beta, betabar = tc_map(branch, alpha, beta), tc_map(branch, alpha, betabar)
+        out.append((branch, alpha, beta, betabar))
+    return out
+
+
+def purify_tc(F, lmin, lmax, homo=None, lumo=None, tol=1e-12, max_iter=200, scaled=True,
+              branch_rule="beta", nocc=None):
+    """Algorithm 2 on a dense symmetric F.
+
+    scaled=False is the alpha = 0 scheme the paper identifies with
+    Niklasson's second-order trace-correcting purification (up to the branch
+    rule).  branch_rule="trace" takes the branch from trace(X_{i-1}) versus
+    nocc instead of from beta + beta-bar.  Without homo/lumo the loop stops
+    when ||X_{i-1} - X_{i-1}^2||_F <= tol (trace rule only)."""
+    F = np.asarray(F, dtype=np.float64)
+    n = F.shape[0]
+    I = np.eye(n)
+    c0, c1 = tc_f0(lmin, lmax)
+    X = (lmax * I - F) / (lmax - lmin)
+    have_bounds = homo is not None and lumo is not None
+    if not have_bounds and branch_rule != "trace":
+        raise ValueError("the beta rule needs homo and lumo")
+    if branch_rule == "trace" and nocc is None:
+        raise ValueError("the trace rule needs nocc")
+    beta, betabar = tc_beta0(lmin, lmax, homo, lumo) if have_bounds else (float("nan"),) * 2
+    res = Result(scheme="TC_SF" if scaled else "TC_MONO", beta0=beta, betabar0=betabar,
+                 f0=(c0, c1))
+    while res.iterations < max_iter:
+        if have_bounds and max(beta, 1.0 - betabar) <= tol:
+            res.converged = True
+            break
+        if branch_rule == "trace":
+            branch = "P10" if float(np.trace(X)) > nocc else "P01"
+        else:
+            branch = tc_branch_by_beta(beta, betabar)
+        if scaled:
+            alpha = tc_alpha(branch, beta, betabar)
+        else:
+            alpha = 0.0
+        X2 = X @ X
+        res.idem.append(float(np.linalg.norm(X - X2)))
+        if branch == "P10":
+            # ((1 + alpha) X - alpha I)^2 expanded over the square X^2
+            X = (1.0 + alpha) ** 2 * X2 - 2.0 * alpha * (1.0 + alpha) * X + alpha * alpha * I
+        else:
+            X = 2.0 * (1.0 + alpha) * X - (1.0 + alpha) ** 2 * X2
+        if have_bounds:
+            beta, betabar = tc_map(branch, alpha, beta), tc_map(branch, alpha, betabar)
+        res.alphas.append(alpha)
+        res.branches.append(branch)
+        res.betas.append(beta)
+        res.betabars.append(betabar)
+        res.traces.append(float(np.trace(X)))
+        res.iterations += 1
+        res.multiplications += 1
+        if not have_bounds and res.idem[-1] <= tol:
+            res.converged = True
+            break
+    else:
+        if have_bounds and max(beta, 1.0 - betabar) <= tol:
+            res.converged = True
+    return X, res
+
+
+def purify(F, scheme, lmin, lmax, mu=None, homo=None, lumo=None, nocc=None, tol=1e-12,
+           max_iter=200, branch_rule="beta"):
+    """Dispatch on the four scheme names used by the library."""
+    if scheme == "FIXED_MU_SF" or scheme == "FIXED_MU_MONO":
+        if mu is None:
+            mu = 0.5 * (homo + lumo)
+        return purify_fixed_mu(F, lmin, lmax, mu, homo, lumo, tol, max_iter,
+                               scaled=scheme == "FIXED_MU_SF")
+    if scheme == "TC_SF" or scheme == "TC_MONO":
+        return purify_tc(F, lmin, lmax, homo, lumo, tol, max_iter, scaled=scheme == "TC_SF",
+                         branch_rule=branch_rule, nocc=nocc)
+    raise ValueError(scheme)
+
+
+# ---------------------------------------------------------------------------
+# The plain definition D = theta(mu I - F)
+# ---------------------------------------------------------------------------
+
+def density_by_eigh(F, mu: float):
+    """D = theta(mu I - F): the sum of v v^T over eigenpairs with lambda < mu."""
+    lam, V = np.linalg.eigh(np.asarray(F, dtype=np.float64))
+    occ = V[:, lam < mu]
+    return occ @ occ.T
+
+
+def density_closed_form(Q, lam, mu: float):
+    """D = Q_occ Q_occ^T for F = Q diag(lam) Q^T."""
+    occ = np.asarray(Q)[:, np.asarray(lam) < mu]
+    return occ @ occ.T
+
+
+# ---------------------------------------------------------------------------
+# Spectral bounds lambda_min, lambda_max ("extremal eigenvalues of F or
+# bounds thereof", the inputs of Algorithms 1 and 2)
+# ---------------------------------------------------------------------------
+
+def gershgorin(F):
+    """Gershgorin's circle theorem: every eigenvalue lies in
+    [min_i (F_ii - R_i), max_i (F_ii + R_i)], R_i = sum_{j != i} |F_ij|."""
+    F = np.asarray(F, dtype=np.float64)
+    d = np.diag(F)
+    R = np.abs(F).sum(axis=1) - np.abs(d)
+    return float(np.min(d - R)), float(np.max(d + R))
+
+
+_GOLDEN = 0x9E3779B97F4A7C15
+_MASK = (1 << 64) - 1
+LANCZOS_KEY = 0x11010265
+
+
+def _splitmix64(x: int) -> int:
+    # SplitMix64 (Steele, Lea, Flood 2014): one step from state x.
+    z = (x + _GOLDEN) & _MASK
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+    return z ^ (z >> 31)
+
+
+def lanczos_start(n: int, key: int = LANCZOS_KEY):
+    """Counter-based start vector: q_i = 2 u_i - 1 with u_i the top 53 bits of
+    SplitMix64 at state key + i * golden, as a fraction of 2^53."""
+    q = np.empty(n)
+    for i in range(n):
+        z = _splitmix64((key + i * _GOLDEN) & _MASK)
+        q[i] = 2.0 * ((z >> 11) * (1.0 / 9007199254740992.0)) - 1.0
+    return q
+
+
+def lanczos(F, k: int, q):
+    """k steps of the symmetric Lanczos three-term recurrence from q (no
+    reorthogonalisation).  Returns the diagonal a[0..m) and off-diagonal
+    b[0..m) of the tridiagonal T_m (m <= k; b[m-1] is the residual norm)."""
+    F = np.asarray(F, dtype=np.float64)
+    v = np.asarray(q, dtype=np.float64) / np.linalg.norm(q)
+    v_prev = np.zeros_like(v)
+    b_prev = 0.0
+    a, b = [], []
+    for _ in range(k):
+        w = F @ v - b_prev * v_prev
+        aj = float(w @ v)
+        w = w - aj * v
+        bj = float(np.linalg.norm(w))
+        a.append(aj)
+        b.append(bj)
+        if bj == 0.0:
+            break
+        v_prev, v, b_prev = v, w / bj, bj
+    return np.array(a), np.array(b)
+
+
+def lanczos_bounds(F, k: int, q=None):
+    """Extremal Ritz values of T_k widened by their residual norms
+    |b_k y_k|, intersected with the Gershgorin interval."""
+    F = np.asarray(F, dtype=np.float64)
+    if q is None:
+        q = lanczos_start(F.shape[0])
+    a, b = lanczos(F, k, q)
+    m = a.size
+    T = np.diag(a) + np.diag(b[:m - 1], 1) + np.diag(b[:m - 1], -1)
+    theta, Y = np.linalg.eigh(T)
+    r_lo = abs(b[m - 1] * Y[m - 1, 0])
+    r_hi = abs(b[m - 1] * Y[m - 1, -1])
+    g_lo, g_hi = gershgorin(F)
+    return max(g_lo, theta[0] - r_lo), min(g_hi, theta[-1] + r_hi)
+
+
+# ---------------------------------------------------------------------------
+# Invariants
+# ---------------------------------------------------------------------------
+
+def idempotency_error(X):
+    X = np.asarray(X)
+    return float(np.linalg.norm(X - X @ X))
+
+
+def commutator_norm(X, F):
+    X = np.asarray(X)
+    F = np.asarray(F)
+    return float(np.linalg.norm(X @ F - F @ X))

@@ -1,0 +1,297 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+None of these compares the oracle with a retyped copy of its own formulas:
+each pin comes from a definition (fixed points and vanishing derivatives of
+P_{i,j}, Eq. 3's fold condition, D = theta(mu I - F)), from a library routine
+(eigh, a scalar root finder), from functional calculus on the eigenbasis, or
+from a claim the paper states (half the multiplications, speedup growing as
+the gap closes, independent of mu).
+"""
+import math
+
+import numpy as np
+import pytest
+import sympy
+from scipy.optimize import brentq
+
+from oracle import purify_oracle as O
+from paper_1101_0265_gb300 import inputs as I
+
+SCHEMES = O.SCHEMES
+
+
+# --- P_{i,j}: degree 1+i+j, fixed points 0 and 1, i vanishing derivatives at
+# 0 and j at 1 (the paper's definition of the notation) ---------------------
+
+@pytest.mark.parametrize("fn,i,j", [(O.P10, 1, 0), (O.P01, 0, 1), (O.P11, 1, 1)])
+def test_polynomial_family_definition(fn, i, j):
+    x = sympy.Symbol("x")
+    p = sympy.nsimplify(sympy.expand(fn(x)), rational=True)
+    assert sympy.degree(p, x) == 1 + i + j
+    assert p.subs(x, 0) == 0 and p.subs(x, 1) == 1
+    for d in range(1, i + 1):
+        assert sympy.diff(p, x, d).subs(x, 0) == 0
+    for d in range(1, j + 1):
+        assert sympy.diff(p, x, d).subs(x, 1) == 0
+    # and the next derivative does not vanish (exactly i and j)
+    assert sympy.diff(p, x, i + 1).subs(x, 0) != 0
+    assert sympy.diff(p, x, j + 1).subs(x, 1) != 0
+
+
+# --- Algorithm 1's alpha solves Eq. 3 (independently, by root finding) ---------
+
+@pytest.mark.parametrize("beta", [1e-9, 1e-4, 0.01, 0.1, 0.25, 0.4, 0.49, 0.4999])
+def test_fixed_mu_alpha_solves_eq3(beta):
+    def g(a):
+        return O.P11(a * (beta - 0.5) + 0.5) - O.P11(0.5 * (1.0 - a))
+    a_root = brentq(g, 1.0 + 1e-12, math.sqrt(3.0) + 1e-9, xtol=1e-15, rtol=1e-15)
+    a = O.fixed_mu_alpha(beta)
+    assert a >= 1.0
+    assert abs(a - a_root) <= 1e-12 * a
+    # the fold is complete: the stretched interval [0.5(1-a), a(b-0.5)+0.5]
+    # straddles 0, so the unoccupied part folds over itself
+    assert 0.5 * (1 - a) <= 0.0 <= a * (beta - 0.5) + 0.5
+
+
+def test_fixed_mu_alpha_limits():
+    # alpha -> 1 (plain McWeeny) as beta -> 0; alpha = sqrt(3) at beta = 1/2
+    assert abs(O.fixed_mu_alpha(0.0) - 1.0) < 1e-15
+    assert abs(O.fixed_mu_alpha(0.5) - math.sqrt(3.0)) < 1e-15
+
+
+# --- Algorithm 2's alpha makes the folded ends meet --------------------------
+
+@pytest.mark.parametrize("beta,betabar", [(0.45, 0.6), (0.3, 0.9), (0.1, 0.95), (0.49, 0.51),
+                                          (0.2, 0.55), (0.02, 0.3)])
+def test_tc_alpha_fold_condition(beta, betabar):
+    # P10 branch: the images of 0 and beta under x -> (1+a)x - a have equal
+    # squares, i.e. the stretched unoccupied interval is folded onto itself.
+    a10 = O.tc_alpha("P10", beta, betabar)
+    root10 = brentq(lambda a: O.P10(-a) - O.P10((1 + a) * beta - a), 1e-14, 1.0, xtol=1e-16)
+    assert abs(a10 - root10) < 1e-12
+    # P01 branch: the images of 1 and beta-bar under x -> (1+a)x meet under 2y - y^2.
+    a01 = O.tc_alpha("P01", beta, betabar)
+    root01 = brentq(lambda a: O.P01(1 + a) - O.P01((1 + a) * betabar), 1e-14, 1.0, xtol=1e-16)
+    assert abs(a01 - root01) < 1e-12
+    assert a10 >= 0 and a01 >= 0
+
+
+# --- the scalar bound tracks the gap edges exactly (diagonal test matrices,
+# the paper's own test setting) ---------------------------------------------
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("mu,gap", [(0.5, 0.1), (0.25, 0.01), (0.8, 0.02)])
+def test_scalar_bound_tracks_edges_on_diagonal(scheme, mu, gap):
+    lam = I.unit_interval_spectrum(40, mu, gap)
+    h = I.diagonal_hamiltonian(lam, mu)
+    X, r = O.purify(h.F, scheme, 0.0, 1.0, mu=mu, homo=h.homo, lumo=h.lumo, tol=1e-12)
+    assert r.converged
+    # rerun step by step, checking every iterate's spectrum against the bound
+    x_unocc = np.diag(X)[h.nocc:]
+    x_occ = np.diag(X)[:h.nocc]
+    b, bb = r.betas[-1], r.betabars[-1]
+    assert x_unocc.max() <= b + 1e-15 and x_unocc.min() >= -1e-15
+    assert x_occ.min() >= bb - 1e-15 and x_occ.max() <= 1 + 1e-15
+    for k in range(1, r.iterations + 1):
+        Xk, rk = O.purify(h.F, scheme, 0.0, 1.0, mu=mu, homo=h.homo, lumo=h.lumo, tol=0.0,
+                          max_iter=k)
+        d = np.diag(Xk)
+        # the lumo / homo images are the bound itself (the edge is attained)
+        assert abs(d[h.nocc] - rk.betas[-1]) <= 1e-13
+        assert abs(d[h.nocc - 1] - rk.betabars[-1]) <= 1e-13
+        assert d[h.nocc:].max() <= rk.betas[-1] + 1e-13
+        assert d[:h.nocc].min() >= rk.betabars[-1] - 1e-13
+
+
+# --- functional calculus: on F = Q diag(lam) Q^T the matrix recursion equals
+# Q diag(f(lam)) Q^T with f the composed scalar maps ------------------------
+
+def _scalar_compose(scheme, r, x):
+    x = np.array(x, dtype=np.float64)
+    if scheme.startswith("FIXED_MU"):
+        for a in r.alphas:
+            xs = a * (x - 0.5) + 0.5
+            x = O.P11(xs)
+    else:
+        for br, a in zip(r.branches, r.alphas):
+            x = O.P10((1 + a) * x - a) if br == "P10" else O.P01((1 + a) * x)
+    return x
+
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+def test_matrix_recursion_is_functional_calculus(scheme):
+    h = I.dense_hamiltonian(48, 20, 0.2, config=90)
+    for k in (1, 2, 5):
+        X, r = O.purify(h.F, scheme, h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo,
+                        tol=0.0, max_iter=k)
+        c0, c1 = r.f0
+        x0 = c0 + c1 * h.lam
+        fx = _scalar_compose(scheme, r, x0)
+        ref = (h.Q * fx[None, :]) @ h.Q.T
+        assert np.max(np.abs(X - ref)) < 1e-12
+        # f0 maps the spectrum into [0, 1] with occupied states above
+        assert x0.min() >= -1e-15 and x0.max() <= 1 + 1e-15
+        assert x0[: h.nocc].min() > x0[h.nocc:].max()
+
+
+# --- brute force: D = theta(mu I - F) by eigendecomposition ------------------
+
+@pytest.mark.parametrize("scheme", SCHEMES)
+@pytest.mark.parametrize("n,nocc,gap", [(64, 32, 0.1), (96, 30, 0.01), (33, 17, 0.3)])
+def test_density_matches_eigendecomposition(scheme, n, nocc, gap):
+    h = I.dense_hamiltonian(n, nocc, gap, config=91)
+    tol = 1e-12
+    D, r = O.purify(h.F, scheme, h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=tol)
+    assert r.converged and r.err_bound <= tol
+    D_ref = O.density_by_eigh(h.F, 0.0)
+    assert np.max(np.abs(D - D_ref)) <= tol + 1e-11
+    D_cf = O.density_closed_form(h.Q, h.lam, 0.0)
+    assert np.max(np.abs(D - D_cf)) <= tol + 1e-11
+    # invariants: trace = nocc, idempotent, commutes with F
+    assert abs(np.trace(D) - nocc) < 1e-10
+    assert O.idempotency_error(D) < 1e-10
+    assert O.commutator_norm(D, h.F) < 1e-10
+
+
+def test_density_on_diagonal_is_step_function():
+    lam = I.unit_interval_spectrum(50, 0.3, 0.05)
+    h = I.diagonal_hamiltonian(lam, 0.3)
+    for scheme in SCHEMES:
+        D, r = O.purify(h.F, scheme, 0.0, 1.0, mu=0.3, homo=h.homo, lumo=h.lumo, tol=1e-13)
+        expect = np.diag((lam < 0.3).astype(float))
+        assert np.max(np.abs(D - expect)) <= 1e-13
+
+
+def test_trace_rule_niklasson():
+    # alpha = 0 with the trace rule: Niklasson's TC2.  It needs only nocc;
+    # without gap bounds it stops on idempotency.
+    h = I.dense_hamiltonian(64, 21, 0.1, config=92)
+    D, r = O.purify_tc(h.F, h.lmin, h.lmax, tol=1e-10, scaled=False, branch_rule="trace",
+                       nocc=h.nocc, max_iter=100)
+    assert r.converged
+    D_ref = O.density_by_eigh(h.F, 0.0)
+    assert np.max(np.abs(D - D_ref)) < 1e-9
+    # with bounds given, the trace rule and the beta rule reach the same D
+    D2, r2 = O.purify_tc(h.F, h.lmin, h.lmax, h.homo, h.lumo, tol=1e-12, scaled=False,
+                         branch_rule="trace", nocc=h.nocc)
+    assert np.max(np.abs(D2 - D_ref)) < 1e-11
+
+
+def test_tie_takes_p01_branch():
+    # symmetric gap: beta + beta-bar == 1 exactly -> the strict test is false
+    b, bb = O.tc_beta0(-1.0, 1.0, -0.05, 0.05)
+    assert b + bb == 1.0
+    assert O.tc_branch_by_beta(b, bb) == "P01"
+
+
+# --- the paper's claims about multiplication counts (Fig. 3 protocol:
+# spectral width 1, accuracy 1e-9) -------------------------------------------
+
+def _counts(mu, xi, tol=1e-9):
+    g = O.fixed_mu_gamma(0.0, 1.0, mu)
+    b = O.fixed_mu_beta0(g, mu, mu - xi / 2, mu + xi / 2)
+    mcw_sf = 2 * len(O.fixed_mu_schedule(b, tol, 10_000, True)[0])
+    mcw_mono = 2 * len(O.fixed_mu_schedule(b, tol, 10_000, False)[0])
+    tb, tbb = O.tc_beta0(0.0, 1.0, mu - xi / 2, mu + xi / 2)
+    tc_sf = len(O.tc_schedule(tb, tbb, tol, 10_000, True))
+    tc_mono = len(O.tc_schedule(tb, tbb, tol, 10_000, False))
+    return mcw_mono, mcw_sf, tc_mono, tc_sf
+
+
+def test_half_the_multiplications():
+    # Abstract and Fig. 3b: about half the multiplications, "around twice as fast"
+    for xi in (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
+        mm, ms, tm, ts = _counts(0.5, xi)
+        assert 0.4 <= ms / mm <= 0.65, (xi, mm, ms)
+        assert 0.4 <= ts / tm <= 0.65, (xi, tm, ts)
+
+
+def test_speedup_grows_as_gap_closes_and_cost_is_logarithmic():
+    xis = [10.0 ** -k for k in range(1, 9)]
+    c = np.array([_counts(0.5, xi) for xi in xis], dtype=float)
+    saved_mcw = c[:, 0] - c[:, 1]
+    saved_tc = c[:, 2] - c[:, 3]
+    assert np.all(np.diff(saved_mcw) >= 0) and saved_mcw[-1] > saved_mcw[0]
+    assert np.all(np.diff(saved_tc) >= 0) and saved_tc[-1] > saved_tc[0]
+    # counts grow linearly in ln(1/xi) (cost O(ln(width/gap)))
+    x = np.log(1.0 / np.array(xis))
+    for col in range(4):
+        slope, icept = np.polyfit(x, c[:, col], 1)
+        resid = c[:, col] - (slope * x + icept)
+        assert slope > 0 and np.max(np.abs(resid)) <= 2.5
+
+
+def test_speedup_independent_of_mu():
+    # Fig. 3a: xi = 0.01, mu varied; the ratio stays near one half everywhere
+    ratios = []
+    for mu in (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.7, 0.8, 0.9):
+        mm, ms, tm, ts = _counts(mu, 0.01)
+        ratios += [ms / mm, ts / tm]
+    assert min(ratios) >= 0.45 and max(ratios) <= 0.65
+
+
+def test_mirror_symmetry_in_mu():
+    # theta(mu I - F) for mu -> 1 - mu is the complement problem: equal counts
+    for mu in (0.1, 0.25, 0.4):
+        assert _counts(mu, 0.01) == _counts(1.0 - mu, 0.01)
+
+
+def test_gap_zero_alpha1_fixed_point():
+    # beta = 1/2 (no gap) is a fixed point of Algorithm 1's scalar map: the
+    # method cannot converge, which is why a zero gap is rejected
+    a = O.fixed_mu_alpha(0.5)
+    bs = a * (0.5 - 0.5) + 0.5
+    assert O.P11(bs) == 0.5
+
+
+# --- spectral bounds ---------------------------------------------------------
+
+def test_gershgorin_contains_spectrum():
+    h = I.dense_hamiltonian(80, 40, 0.1, config=93)
+    lo, hi = O.gershgorin(h.F)
+    assert lo <= h.lam[0] and hi >= h.lam[-1]
+    d = np.array([3.0, -2.0, 0.5])
+    assert O.gershgorin(np.diag(d)) == (-2.0, 3.0)
+    # 2x2 with known discs
+    F = np.array([[1.0, -2.0], [-2.0, 4.0]])
+    assert O.gershgorin(F) == (-1.0, 6.0)
+
+
+def test_splitmix64_published_vector():
+    # SplitMix64 seeded with 1234567: first outputs of the reference generator
+    seq = [O._splitmix64((1234567 + i * O._GOLDEN) & O._MASK) for i in range(5)]
+    assert seq == [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                   4593380528125082431, 16408922859458223821]
+
+
+def test_lanczos_full_recovers_spectrum():
+    h = I.dense_hamiltonian(24, 12, 0.3, config=94)
+    q = O.lanczos_start(24)
+    a, b = O.lanczos(h.F, 24, q)
+    T = np.diag(a) + np.diag(b[:-1], 1) + np.diag(b[:-1], -1)
+    assert np.max(np.abs(np.linalg.eigvalsh(T) - h.lam)) < 1e-8
+    # tridiagonal of the Lanczos basis: V^T F V = T for a few steps
+    k = 6
+    a, b = O.lanczos(h.F, k, q)
+    V = [q / np.linalg.norm(q)]
+    vp = np.zeros(24)
+    for j in range(k - 1):
+        w = h.F @ V[-1] - (b[j - 1] * vp if j else 0.0) - a[j] * V[-1]
+        vp = V[-1]
+        V.append(w / b[j])
+    V = np.array(V).T
+    Tk = np.diag(a) + np.diag(b[:k - 1], 1) + np.diag(b[:k - 1], -1)
+    assert np.max(np.abs(V.T @ h.F @ V - Tk)) < 1e-12
+    assert np.max(np.abs(V.T @ V - np.eye(k))) < 1e-12
+
+
+def test_lanczos_bounds_bracket_extremes():
+    h = I.dense_hamiltonian(300, 150, 0.1, config=95)
+    lo, hi = O.lanczos_bounds(h.F, 30)
+    g_lo, g_hi = O.gershgorin(h.F)
+    assert g_lo <= lo and hi <= g_hi
+    # the estimates bracket the extreme eigenvalues -1, 1 and are far tighter
+    # than Gershgorin on a dense matrix
+    assert lo <= -1.0 + 1e-12 and hi >= 1.0 - 1e-12
+    assert lo > -1.05 and hi < 1.05
+    assert g_hi - g_lo > 4.0
