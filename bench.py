@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Throughput of recursive density-matrix purification on one GB300.
+
+One step purifies the dense n = 4096 sweep (F = Q diag(lambda) Q^T, spectrum
+[-1, 1], nocc in {n/2, n/4} x gap in {1e-1, 1e-2, 1e-3, 1e-4}: eight
+matrices) with both scale-and-fold schemes (Algorithm 2, then Algorithm 1),
+i.e. 16 purifications per step, inputs resident in HBM.  Prints one JSON line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+    python bench.py --impl reference     # the CPU oracle on the same metric
+
+With N > 1 (torchrun) every rank purifies its own eight matrices (weak
+scaling, no collective on the data path); the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("purified n=4096 matrices/sec + tensor-pipe % at max-err<=1e-6 vs plain FP64; "
+          "serve p50/p99")
+GAPS = (1e-1, 1e-2, 1e-3, 1e-4)
+SCHEMES = ("TC_SF", "FIXED_MU_SF")
+FP64_PER_BF16 = 1.25 / 2250.0   # nominal dense fp64 : bf16 ratio of GB300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
+    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_specs(n):
+    return [(nocc, gap) for nocc in (n // 2, n // 4) for gap in GAPS]
+
+
+def make_inputs(n, rank, count=None):
+    from paper_1101_0265_gb300 import inputs as I
+    specs = workload_specs(n)[:count]
+    return [I.dense_hamiltonian(n, nocc, gap, config=2, instance=1000 * rank + i)
+            for i, (nocc, gap) in enumerate(specs)]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (started before, stopped after)."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        smax = max(num(r[2]) for r in rows)
+        loaded = [r for r in rows if num(r[3]) > 300.0] or rows
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in loaded for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(num(r[1]) for r in loaded), "sm_max_mhz": smax,
+                "samples": len(rows), "samples_loaded": len(loaded),
+                "power_w_max": max(num(r[3]) for r in rows), "reasons": reasons,
+                "sm_mhz_min": min(sm)}
+
+
+def cpu_baseline(hs, tol):
+    """The oracle as it stands, on a bounded sample: one purification."""
+    from oracle import purify_oracle as O
+    h = hs[0]
+    t0 = time.perf_counter()
+    O.purify(h.F, "TC_SF", h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=tol)
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "matrices/s", "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"1 purification (TC_SF, n={h.n}, nocc={h.nocc}, gap={h.meta['gap']:g}, "
+                      f"tol={tol:g}) of the step's 16, numpy float64, {dt:.2f} s"}
+
+
+def _blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+        n = [i.get("num_threads") for i in threadpool_info() if i.get("user_api") == "blas"]
+        if n:
+            return int(n[0])
+    except Exception:
+        pass
+    env = os.environ.get("OPENBLAS_NUM_THREADS") or os.environ.get("OMP_NUM_THREADS")
+    return int(env) if env else os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle (no GPU work), rank 0 only."""
+    if rank != 0:
+        return
+    n = args.n
+    count = min(args.steps + args.warmup, len(workload_specs(n)))
+    hs = make_inputs(n, 0, count)
+    from oracle import purify_oracle as O
+
+    def one(i):
+        h = hs[i % count]
+        O.purify(h.F, "TC_SF", h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=args.tol)
+    for i in range(args.warmup):
+        one(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        one(args.warmup + i)
+    dt = time.perf_counter() - t0
+    value = args.steps / dt
+    cores = _blas_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"dense F n={n} sweep, one TC_SF purification per step (CPU oracle)",
+                   "n": n, "tol": args.tol},
+        "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": cores, "kind": "oracle",
+                         "sample": f"one purification per step, cycling the first {count} "
+                                   "matrices of the sweep"},
+        "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import numpy as np
+    import torch
+    import paper_1101_0265_gb300 as P
+    from paper_1101_0265_gb300 import build
+
+    if rank == 0:
+        build.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.barrier()
+        if rank != 0:
+            build.build()
+    else:
+        torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    hs = make_inputs(n, rank)
+    Fd = [torch.from_numpy(h.F).to(dev) for h in hs]
+    Fh = [torch.from_numpy(h.F).pin_memory() for h in hs]
+    Dh = torch.empty((n, n), dtype=torch.float64).pin_memory()
+    stream = torch.cuda.current_stream(dev)
+    pur = P.Purifier(device=local, stream=stream.cuda_stream, precision=args.precision,
+                     time_products=True)
+
+    acc = {"launches": 0, "prod_s": 0.0, "prod_n": 0, "tensor_flops": 0.0, "useful": 0.0,
+           "mults": 0, "digit_max": 0}
+
+    def one(h, F, scheme, D=None, record=False):
+        pur.set_hamiltonian(F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo,
+                            lumo=h.lumo)
+        s0 = pur.stats()
+        code = pur.run(scheme, args.tol, 200)
+        if code != P.OK:
+            raise RuntimeError(f"{scheme} did not converge: {P.strerror(code)}")
+        if D is not None:
+            pur.density(D)
+        if record:
+            s = pur.stats()
+            acc["launches"] += s0["kernel_launches"] + s["kernel_launches"]
+            acc["prod_s"] += s["product_seconds"]
+            acc["prod_n"] += s["product_launches"]
+            acc["tensor_flops"] += s["tensor_flops"]
+            acc["useful"] += s["useful_flops"]
+            acc["mults"] += s["multiplications"]
+            acc["digit_max"] = max(acc["digit_max"], s["digit_max"])
+
+    def step(host=False, record=False):
+        for i, h in enumerate(hs):
+            for scheme in SCHEMES:
+                if host:
+                    one(h, Fh[i], scheme, D=Dh, record=record)
+                else:
+                    one(h, Fd[i], scheme, record=record)
+
+    def timed(k, host=False, record=False, clocks=False):
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            step(host=host, record=record)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ck = sampler.stop() if sampler else None
+        if dist:
+            dist.barrier()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, ck
+
+    for _ in range(args.warmup):
+        step()
+    ms, clocks = timed(args.steps, record=True, clocks=True)
+    per_step = len(hs) * len(SCHEMES)
+    value = world * per_step * args.steps / (ms * 1e-3)
+    # end to end: host F in, host D out, copies inside the timed region
+    step(host=True)
+    ms_e2e, _ = timed(max(1, args.steps // 2), host=True)
+    k_e2e = max(1, args.steps // 2)
+    value_e2e = world * per_step * k_e2e / (ms_e2e * 1e-3)
+
+    pk, pk_kind = peaks()
+    steps_launched = args.steps
+    if args.precision == "mixed":
+        achieved = acc["tensor_flops"] / acc["prod_s"] / 1e12
+        peak = pk["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "digit-plane tcgen05 product", "peak_kind": f"{pk_kind} bf16 sustained"}
+    else:
+        achieved = acc["useful"] / acc["prod_s"] / 1e12
+        peak = pk["bf16_tflops_sustained"] * FP64_PER_BF16
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "step_f64_kernel",
+                "peak_kind": f"{pk_kind} bf16 sustained x nominal fp64:bf16 (1.25/2250)"}
+    line = {
+        "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": f"dense F=Q diag(lambda) Q^T n={n}, nocc in {{n/2,n/4}} x gap in "
+                               f"{{1e-1,1e-2,1e-3,1e-4}} (8 matrices) x schemes TC_SF, "
+                               f"FIXED_MU_SF; tol {args.tol:g}",
+                   "n": n, "matrices_per_step": per_step, "precision": args.precision,
+                   "tol": args.tol, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (each F is 134 MB, 8 distinct per step)"},
+        "clocks": clocks,
+        "e2e": {"value": value_e2e, "unit": "matrices/s",
+                "h2d_bytes_per_step": per_step * n * n * 8,
+                "d2h_bytes_per_step": per_step * n * n * 8},
+        "gpu_launches": acc["launches"],
+        "roofline": roof,
+        "multiplications_per_step": acc["mults"] / steps_launched,
+        "useful_tflops": acc["useful"] / (ms * 1e-3) / 1e12,
+    }
+    if args.precision == "mixed":
+        line["tensor_pipe_frac_of_step"] = acc["tensor_flops"] / (ms * 1e-3) / 1e12 / pk["bf16_tflops"]
+        line["digit_max"] = acc["digit_max"]
+    # max error against the plain float64 GPU recursion, and its throughput
+    if not args.no_fp64_check and args.precision == "mixed":
+        ref = P.Purifier(device=local, stream=stream.cuda_stream, precision="fp64")
+        D1 = torch.empty((n, n), dtype=torch.float64, device=dev)
+        D2 = torch.empty((n, n), dtype=torch.float64, device=dev)
+        worst = 0.0
+        t64 = 0.0
+        for i, h in enumerate(hs):
+            for scheme in SCHEMES:
+                one(h, Fd[i], scheme, D=D1)
+                ref.set_hamiltonian(Fd[i], nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax,
+                                    homo=h.homo, lumo=h.lumo)
+                ref.run(scheme, args.tol, 200)
+                t64 += ref.stats()["seconds"]
+                ref.density(D2)
+                worst = max(worst, float((D1 - D2).abs().max()))
+        ref.close()
+        line["max_err_vs_fp64"] = worst
+        line["fp64_path"] = {"value": per_step / t64, "unit": "matrices/s",
+                             "note": "same schedules through the float64 SIMT path, same GPU"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(hs, args.tol)
+    pur.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,222 @@
+/*
+ * libpurify: recursive polynomial purification of the one-particle density
+ * matrix D = theta(mu I - F) on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: E. H. Rubensson, "Non-monotonic recursive polynomial expansions for
+ * linear scaling calculation of the density matrix", arXiv:1101.0265.
+ *   - the problem: D = theta(mu I - F), introduction;
+ *   - the recursion X_0 = f_0(F), X_i = f_i(X_{i-1}): Eq. 1;
+ *   - fixed-mu scale-and-fold McWeeny (P_{1,1}): Eq. 2, Eq. 3, Algorithm 1;
+ *   - varying-mu scale-and-fold P_{1,0} / P_{0,1}: Eq. 4, Eq. 5, Algorithm 2;
+ *   - the alpha = 1 / alpha = 0 reference schemes the paper compares with
+ *     (regular grand-canonical McWeeny; second-order trace-correcting).
+ *
+ * Conventions for every entry point:
+ *   - Return value: PURIFY_OK (0) or a negative PURIFY_ERR_* code.  No C++
+ *     exception crosses this boundary.  purify_strerror() names a code.
+ *   - Matrices are dense, row-major, float64, with a leading dimension
+ *     (elements between consecutive rows) >= n.  Only symmetric matrices are
+ *     accepted; F's upper triangle (j >= i) is read and mirrored.
+ *   - Pointers passed to purify_set_hamiltonian / purify_get_density may be
+ *     host memory (pageable or pinned) or device memory of the handle's
+ *     device; the library tells them apart with cudaPointerGetAttributes.
+ *     The caller keeps ownership; the library copies F and never retains a
+ *     caller pointer after the call returns.
+ *   - A handle owns all device memory it uses and is NOT thread-safe; separate
+ *     handles are independent.  Work is issued on the handle's stream; the
+ *     calls that return host-visible results synchronise that stream.
+ *   - The purify_k_* entry points run one kernel family on caller-owned
+ *     DEVICE pointers, asynchronously on the given stream (NULL = the legacy
+ *     default stream), and allocate nothing unless stated.
+ */
+#ifndef LIBPURIFY_PURIFY_H
+#define LIBPURIFY_PURIFY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PURIFY_OK                   0
+#define PURIFY_ERR_INVALID_ARG     -1  /* bad pointer, size, scheme or option      */
+#define PURIFY_ERR_BOUNDS          -2  /* inconsistent spectral bounds, zero gap,
+                                          or a trace that shows occupied and
+                                          unoccupied states mixed up              */
+#define PURIFY_ERR_NOT_CONVERGED   -3  /* max_iter reached; stats still filled     */
+#define PURIFY_ERR_OOM             -4  /* device allocation failed                 */
+#define PURIFY_ERR_CUDA            -5  /* a CUDA runtime/driver call failed        */
+#define PURIFY_ERR_DEVICE_TIMEOUT  -6  /* a bounded device-side wait ran out       */
+#define PURIFY_ERR_STATE           -7  /* call order (e.g. run before set)         */
+#define PURIFY_ERR_UNSUPPORTED     -8  /* no sm_103a device / feature not built    */
+
+/* ---- schemes (Algorithm 1, Algorithm 2 and their reference forms) ------- */
+#define PURIFY_FIXED_MU_SF    0  /* Algorithm 1: P_{1,1}(alpha(X - I/2) + I/2)      */
+#define PURIFY_FIXED_MU_MONO  1  /* Algorithm 1 with alpha = 1 (regular McWeeny)     */
+#define PURIFY_TC_SF          2  /* Algorithm 2: Eq. 4 / Eq. 5 with scaling alpha    */
+#define PURIFY_TC_MONO        3  /* Algorithm 2 with alpha = 0 (trace-correcting)    */
+
+/* ---- arithmetic of the matrix products -------------------------------- */
+#define PURIFY_FP64    0  /* float64 FMA on the SIMT pipes                          */
+#define PURIFY_MIXED   1  /* float64 values held as integer digit planes in bf16,
+                             multiplied exactly on the tcgen05 tensor cores with
+                             fp32 accumulation in tensor memory, recombined in
+                             float64; number of digits set per step               */
+
+/* ---- branch rule of the varying-mu schemes ---------------------------- */
+#define PURIFY_BRANCH_BETA   0  /* Algorithm 2's test: beta + beta_bar > 1 -> P_{1,0} */
+#define PURIFY_BRANCH_TRACE  1  /* trace(X_{i-1}) > nocc -> P_{1,0} (Niklasson)       */
+
+typedef struct purify_ctx* purify_t;
+
+/* Spectral landmarks of F: extremal eigenvalues (or bounds of them) and the
+ * eigenvalues just below (homo) and above (lumo) the gap (Algorithm 1 and
+ * Algorithm 2, "Require" lines).  lmin / lmax may be NaN: they are then
+ * estimated on the device (Gershgorin discs tightened by Lanczos).  homo /
+ * lumo may be NaN only for PURIFY_TC_MONO with PURIFY_BRANCH_TRACE, which then
+ * stops on idempotency.  Loose inner estimates (homo_est >= homo, lumo_est <=
+ * lumo) are safe and only slow convergence; homo >= lumo is rejected. */
+typedef struct purify_bounds {
+    double lmin, lmax, homo, lumo;
+} purify_bounds;
+
+typedef struct purify_options {
+    int precision;       /* PURIFY_FP64 (default) or PURIFY_MIXED                        */
+    int branch_rule;     /* PURIFY_BRANCH_BETA (default) or PURIFY_BRANCH_TRACE          */
+    int lanczos_steps;   /* Lanczos steps when lmin/lmax are NaN (default 32, 0 = none)  */
+    int refine_squares;  /* MIXED: extra unscaled McWeeny steps at the finest digit
+                            count after the schedule ends (default 0)                  */
+    int digits;          /* MIXED: 0 = per-step digit count from the mapped gap
+                            (default); 2..7 = fixed count                             */
+    int time_products;   /* 1 = bracket every matrix-product launch with CUDA events
+                            on the handle's stream and report their total time      */
+    int reserved[10];
+} purify_options;
+
+typedef struct purify_stats_t {
+    int status;                 /* return code of the last purify_run                    */
+    int iterations;             /* iterations of the scheme (f_1 .. f_n)                 */
+    int multiplications;        /* matrix products: 2 per Algorithm 1 iteration, 1 per
+                                   Algorithm 2 iteration, plus refinement products       */
+    int refine_multiplications; /* of which refinement                                   */
+    double err_bound;           /* max(beta, 1 - beta_bar) after the last iteration: a
+                                   bound on ||X_n - D||_2 in exact arithmetic             */
+    double trace;               /* trace(X_n)                                            */
+    double trace_err;           /* |trace(X_n) - nocc| (NaN when nocc is unknown)        */
+    double idem_err_fro;        /* ||X - X^2||_F of the last iterate that was squared
+                                   (Algorithm 2 only; NaN otherwise)                     */
+    double seconds;             /* device time of the iteration loop                     */
+    double lmin, lmax, homo, lumo, mu;  /* landmarks used                              */
+    double useful_flops;        /* n^2 (n + 1) per symmetric product                     */
+    double tensor_flops;        /* MMA flops issued on the tensor cores (MIXED)          */
+    int digit_max;              /* MIXED: largest digit count used                       */
+    int kernel_launches;        /* kernels launched by the last set/run call             */
+    int product_launches;       /* matrix-product kernels among them (last run)          */
+    int reserved[5];
+    double product_seconds;     /* summed event time of the product launches
+                                   (time_products = 1; else NaN)                         */
+} purify_stats_t;
+
+/* Fill *opt with the defaults above. */
+void purify_options_default(purify_options* opt);
+
+/* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * owned by the caller, or NULL to let the handle create its own non-blocking
+ * stream.  `opt` may be NULL (defaults).  Fails with PURIFY_ERR_UNSUPPORTED
+ * if the device is not compute capability 10.3. */
+int purify_create(purify_t* h, int device, void* cuda_stream, const purify_options* opt);
+
+/* Release the handle and all device memory it owns.  NULL is accepted. */
+int purify_destroy(purify_t h);
+
+/* Replace the handle's options (takes effect at the next set/run). */
+int purify_set_options(purify_t h, const purify_options* opt);
+
+/* Load F (n x n, leading dimension ld, host or device) and its landmarks.
+ * nocc < 0 means unknown; mu NaN means mu = (homo + lumo) / 2 (fixed-mu
+ * schemes).  When b->lmin or b->lmax is NaN, the bounds are estimated here
+ * (Gershgorin discs, then `lanczos_steps` Lanczos steps from a SplitMix64
+ * start vector, Ritz values widened by their residuals and clipped to the
+ * discs).  The estimate runs on the device; its result is in purify_stats. */
+int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld,
+                           int64_t nocc, double mu, const purify_bounds* b);
+
+/* Run `scheme` until the bound of the scheme's scalar recursion (beta for
+ * Algorithm 1, max(beta, 1 - beta_bar) for Algorithm 2) is <= tol, or, for
+ * PURIFY_BRANCH_TRACE without gap bounds, until ||X - X^2||_F <= tol; at most
+ * max_iter iterations.  Returns PURIFY_ERR_NOT_CONVERGED (stats filled,
+ * density available) when max_iter is reached, and PURIFY_ERR_BOUNDS when
+ * nocc >= 0 and the final trace differs from nocc by more than 0.5. */
+int purify_run(purify_t h, int scheme, double tol, int max_iter);
+
+/* Copy the current density matrix (the last X_i, symmetric, n x n) into D
+ * (host or device, leading dimension ld >= n). */
+int purify_get_density(purify_t h, double* D, int64_t ld);
+
+/* Copy the statistics of the last set/run into *out. */
+int purify_stats(purify_t h, purify_stats_t* out);
+
+/* Device pointer of the handle's current density (n x n, leading dimension
+ * n, float64), valid until the next set/run/destroy; NULL before a run. */
+const double* purify_density_device_ptr(purify_t h);
+
+/* Human-readable name of a status code (static string). */
+const char* purify_strerror(int code);
+
+/* ---- host-only: the scalar schedule ------------------------------------ */
+
+/* The scalar recursion of a scheme with the beta rule, computed on the host
+ * (Algorithm 1: alpha, beta; Algorithm 2: branch, alpha, beta, beta_bar),
+ * exactly as purify_run uses it.  Arrays have room for max_iter entries; any
+ * of them may be NULL.  branch[i] = 1 for P_{1,0}, 0 for P_{0,1} (0 for
+ * Algorithm 1).  *iterations receives the count; returns
+ * PURIFY_ERR_NOT_CONVERGED if max_iter is reached first.  Needs no GPU. */
+int purify_schedule(int scheme, double lmin, double lmax, double mu, double homo, double lumo,
+                    double tol, int max_iter, double* alpha, int* branch, double* beta,
+                    double* beta_bar, int* iterations);
+
+/* Eigenvalues of the symmetric tridiagonal matrix with diagonal a[0..m) and
+ * off-diagonal b[0..m-1) by cyclic Jacobi rotations; w receives them
+ * ascending and, if last_row is not NULL, last_row[j] the last component of
+ * the j-th normalised eigenvector (for Ritz residuals).  Needs no GPU. */
+int purify_tridiag_eig(const double* a, const double* b, int m, double* w, double* last_row);
+
+/* ---- kernel-level entry points (device pointers, asynchronous) ---------- */
+
+/* C = A B for symmetric A, B whose product is symmetric (in the schemes:
+ * polynomials of the same matrix), n x n, leading dimension n, float64.
+ * Only tiles on or above the diagonal are computed; each is written twice
+ * (itself and its transpose).  The matrix product of every step of Eq. 1. */
+int purify_k_symm_product_f64(const double* A, const double* B, double* C, int64_t n,
+                              void* stream);
+
+/* One fused scheme step in float64 (the matrix form of Eq. 4, Eq. 5 or the
+ * two products of Algorithm 1's P_{1,1}), n x n, leading dimension n:
+ *   P = A B (upper tiles),  Y = cP P + cE E + cI I,  C = dY Y + dI I,
+ * C written with its mirror; E may equal A and may be NULL when cE == 0.
+ * red (device, 3 doubles, accumulated with atomics, NOT cleared here):
+ *   red[0] += trace(Y), red[1] += ||E - P||_F^2, red[2] += ||Y||_F^2.
+ * C must not alias A, B or E. */
+int purify_k_step_f64(const double* A, const double* B, const double* E, double* C, int64_t n,
+                      double cP, double cE, double cI, double dY, double dI, double* red,
+                      void* stream);
+
+/* Gershgorin interval of symmetric F (n x n, leading dimension ld):
+ * lohi[0] = min_i (F_ii - R_i), lohi[1] = max_i (F_ii + R_i),
+ * R_i = sum_{j != i} |F_ij|.  lohi is device memory.  Allocates (and frees)
+ * a device scratch array of 2 * ceil(n / 8) doubles per call. */
+int purify_k_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi, void* stream);
+
+/* k Lanczos steps on symmetric F (n x n, leading dimension n) from the
+ * SplitMix64 start vector q_i = 2 u_i - 1, u_i = (splitmix64(key + i *
+ * 0x9E3779B97F4A7C15) >> 11) / 2^53 with key 0x11010265.  Writes the
+ * tridiagonal diagonal a[0..k) and off-diagonal b[0..k) (b[k-1] = residual
+ * norm) to HOST arrays; synchronises the stream.  Allocates 4 n + 2 k + 2
+ * doubles of device scratch per call. */
+int purify_k_lanczos_f64(const double* F, int64_t n, int k, double* a, double* b, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBPURIFY_PURIFY_H */

@@ -192,7 +192,7 @@ def tc_map(branch: str, alpha: float, x: float) -> float:
     if branch == "P10":
         y = (1.0 + alpha) * x - alpha
         return y * y
-    return 2.0 * (1.0 + alpha) * x - (1.0 + alpha) ** 2 * x * x
+    return 2.0 * (1.0 + alpha) * x - (1.0 + alpha) * (1.0 + alpha) * x * x
 
 
 def tc_schedule(beta: float, betabar: float, tol: float, max_iter: int, scaled: bool = True):
@@ -245,9 +245,9 @@ def purify_tc(F, lmin, lmax, homo=None, lumo=None, tol=1e-12, max_iter=200, scal
         res.idem.append(float(np.linalg.norm(X - X2)))
         if branch == "P10":
             # ((1 + alpha) X - alpha I)^2 expanded over the square X^2
-            X = (1.0 + alpha) ** 2 * X2 - 2.0 * alpha * (1.0 + alpha) * X + alpha * alpha * I
+            X = (1.0 + alpha) * (1.0 + alpha) * X2 - 2.0 * alpha * (1.0 + alpha) * X + alpha * alpha * I
         else:
-            X = 2.0 * (1.0 + alpha) * X - (1.0 + alpha) ** 2 * X2
+            X = 2.0 * (1.0 + alpha) * X - (1.0 + alpha) * (1.0 + alpha) * X2
         if have_bounds:
             beta, betabar = tc_map(branch, alpha, beta), tc_map(branch, alpha, betabar)
         res.alphas.append(alpha)

@@ -1,0 +1,306 @@
+"""ctypes binding of libpurify's C ABI (include/purify.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Loading fails loudly if ``libpurify.so`` has not been built; there
+is no fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libpurify.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_BOUNDS = -2
+ERR_NOT_CONVERGED = -3
+ERR_OOM = -4
+ERR_CUDA = -5
+ERR_DEVICE_TIMEOUT = -6
+ERR_STATE = -7
+ERR_UNSUPPORTED = -8
+
+SCHEMES = {"FIXED_MU_SF": 0, "FIXED_MU_MONO": 1, "TC_SF": 2, "TC_MONO": 3}
+PRECISIONS = {"fp64": 0, "mixed": 1}
+BRANCH_RULES = {"beta": 0, "trace": 1}
+
+EXPORTED = (
+    "purify_options_default", "purify_create", "purify_destroy", "purify_set_options",
+    "purify_set_hamiltonian", "purify_run", "purify_get_density", "purify_stats",
+    "purify_density_device_ptr", "purify_strerror", "purify_schedule", "purify_tridiag_eig",
+    "purify_k_symm_product_f64", "purify_k_step_f64", "purify_k_gershgorin_f64",
+    "purify_k_lanczos_f64",
+)
+
+
+class Bounds(C.Structure):
+    _fields_ = [("lmin", C.c_double), ("lmax", C.c_double), ("homo", C.c_double),
+                ("lumo", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("branch_rule", C.c_int), ("lanczos_steps", C.c_int),
+                ("refine_squares", C.c_int), ("digits", C.c_int), ("time_products", C.c_int),
+                ("reserved", C.c_int * 10)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("status", C.c_int), ("iterations", C.c_int), ("multiplications", C.c_int),
+                ("refine_multiplications", C.c_int), ("err_bound", C.c_double),
+                ("trace", C.c_double), ("trace_err", C.c_double), ("idem_err_fro", C.c_double),
+                ("seconds", C.c_double), ("lmin", C.c_double), ("lmax", C.c_double),
+                ("homo", C.c_double), ("lumo", C.c_double), ("mu", C.c_double),
+                ("useful_flops", C.c_double), ("tensor_flops", C.c_double),
+                ("digit_max", C.c_int), ("kernel_launches", C.c_int),
+                ("product_launches", C.c_int), ("reserved", C.c_int * 5),
+                ("product_seconds", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class PurifyError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libpurify.so (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1101_0265_gb300.build.build()")
+    lib = C.CDLL(path)
+    vp, i64, dbl, ip = C.c_void_p, C.c_int64, C.c_double, C.c_int
+    dp = C.POINTER(C.c_double)
+    sig = {
+        "purify_options_default": (None, [C.POINTER(Options)]),
+        "purify_create": (ip, [C.POINTER(vp), ip, vp, C.POINTER(Options)]),
+        "purify_destroy": (ip, [vp]),
+        "purify_set_options": (ip, [vp, C.POINTER(Options)]),
+        "purify_set_hamiltonian": (ip, [vp, vp, i64, i64, i64, dbl, C.POINTER(Bounds)]),
+        "purify_run": (ip, [vp, ip, dbl, ip]),
+        "purify_get_density": (ip, [vp, vp, i64]),
+        "purify_stats": (ip, [vp, C.POINTER(Stats)]),
+        "purify_density_device_ptr": (vp, [vp]),
+        "purify_strerror": (C.c_char_p, [ip]),
+        "purify_schedule": (ip, [ip, dbl, dbl, dbl, dbl, dbl, dbl, ip, dp, C.POINTER(C.c_int), dp,
+                                 dp, C.POINTER(C.c_int)]),
+        "purify_tridiag_eig": (ip, [dp, dp, ip, dp, dp]),
+        "purify_k_symm_product_f64": (ip, [vp, vp, vp, i64, vp]),
+        "purify_k_step_f64": (ip, [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, dbl, vp, vp]),
+        "purify_k_gershgorin_f64": (ip, [vp, i64, i64, vp, vp]),
+        "purify_k_lanczos_f64": (ip, [vp, i64, ip, dp, dp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().purify_strerror(code).decode()
+
+
+def _check(code: int, what: str, allow=()):
+    if code != OK and code not in allow:
+        raise PurifyError(code, what)
+    return code
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _ptr(x) -> int:
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x.data_ptr())
+
+
+def _stream_of(x=None) -> int | None:
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _nan(v):
+    return float("nan") if v is None else float(v)
+
+
+# ---------------------------------------------------------------------------
+# Handle
+# ---------------------------------------------------------------------------
+
+class Purifier:
+    """One libpurify handle on one device."""
+
+    def __init__(self, device: int = 0, stream: int | None = None, precision: str = "fp64",
+                 branch_rule: str = "beta", lanczos_steps: int = 32, refine_squares: int = 0,
+                 digits: int = 0, time_products: bool = False):
+        lib = load()
+        self._lib = lib
+        self.options = Options()
+        lib.purify_options_default(C.byref(self.options))
+        self.options.precision = PRECISIONS[precision]
+        self.options.branch_rule = BRANCH_RULES[branch_rule]
+        self.options.lanczos_steps = lanczos_steps
+        self.options.refine_squares = refine_squares
+        self.options.digits = digits
+        self.options.time_products = int(time_products)
+        h = C.c_void_p()
+        _check(lib.purify_create(C.byref(h), device, stream, C.byref(self.options)), "purify_create")
+        self._h = h
+        self.n = 0
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.purify_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            if k == "precision":
+                v = PRECISIONS[v]
+            elif k == "branch_rule":
+                v = BRANCH_RULES[v]
+            setattr(self.options, k, v)
+        _check(self._lib.purify_set_options(self._h, C.byref(self.options)), "purify_set_options")
+
+    def set_hamiltonian(self, F, nocc: int = -1, mu=None, lmin=None, lmax=None, homo=None,
+                        lumo=None, ld: int | None = None):
+        """F: (n, n) float64 numpy array or torch tensor (host or device)."""
+        n = int(F.shape[0])
+        if ld is None:
+            ld = int(F.strides[0] // 8) if isinstance(F, np.ndarray) else int(F.stride(0))
+        b = Bounds(_nan(lmin), _nan(lmax), _nan(homo), _nan(lumo))
+        code = self._lib.purify_set_hamiltonian(self._h, _ptr(F), n, ld, int(nocc), _nan(mu),
+                                                C.byref(b))
+        _check(code, "purify_set_hamiltonian")
+        self.n = n
+        return code
+
+    def run(self, scheme: str, tol: float = 1e-12, max_iter: int = 200, check: bool = True) -> int:
+        code = self._lib.purify_run(self._h, SCHEMES[scheme], float(tol), int(max_iter))
+        if check:
+            _check(code, "purify_run", allow=(ERR_NOT_CONVERGED,))
+        return code
+
+    def density(self, out=None):
+        """The density as a new host float64 array, or into `out` (numpy or
+        torch, host or device, row-major with unit column stride)."""
+        if out is None:
+            out = np.empty((self.n, self.n), dtype=np.float64)
+        ld = int(out.strides[0] // 8) if isinstance(out, np.ndarray) else int(out.stride(0))
+        _check(self._lib.purify_get_density(self._h, _ptr(out), ld), "purify_get_density")
+        return out
+
+    def density_device_ptr(self) -> int:
+        return self._lib.purify_density_device_ptr(self._h) or 0
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(self._lib.purify_stats(self._h, C.byref(s)), "purify_stats")
+        return s.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# Host-only entry points
+# ---------------------------------------------------------------------------
+
+def schedule(scheme: str, lmin, lmax, mu, homo, lumo, tol, max_iter=500):
+    lib = load()
+    alpha = np.zeros(max_iter)
+    beta = np.zeros(max_iter)
+    betabar = np.zeros(max_iter)
+    branch = (C.c_int * max(max_iter, 1))()
+    it = C.c_int(0)
+    code = lib.purify_schedule(SCHEMES[scheme], float(lmin), float(lmax), _nan(mu), float(homo),
+                               float(lumo), float(tol), int(max_iter), _dptr(alpha), branch,
+                               _dptr(beta), _dptr(betabar), C.byref(it))
+    _check(code, "purify_schedule", allow=(ERR_NOT_CONVERGED,))
+    m = it.value
+    return {"alpha": alpha[:m].copy(), "branch": np.array(branch[:m], dtype=int),
+            "beta": beta[:m].copy(), "betabar": betabar[:m].copy(), "iterations": m,
+            "converged": code == OK}
+
+
+def tridiag_eig(a, b):
+    lib = load()
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    m = a.size
+    b = np.ascontiguousarray(b if m > 1 else np.zeros(1), dtype=np.float64)
+    w = np.zeros(m)
+    last = np.zeros(m)
+    _check(lib.purify_tridiag_eig(_dptr(a), _dptr(b), m, _dptr(w), _dptr(last)), "tridiag_eig")
+    return w, last
+
+
+# ---------------------------------------------------------------------------
+# Kernel-level entry points (torch CUDA tensors, current stream)
+# ---------------------------------------------------------------------------
+
+def _dev_f64(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+
+
+def k_symm_product_f64(A, B, out):
+    _dev_f64(A, "A"), _dev_f64(B, "B"), _dev_f64(out, "out")
+    _check(load().purify_k_symm_product_f64(_ptr(A), _ptr(B), _ptr(out), int(A.shape[0]),
+                                            _stream_of()), "k_symm_product_f64")
+    return out
+
+
+def k_step_f64(A, B, E, out, cP, cE, cI, dY=1.0, dI=0.0, red=None):
+    for t, nm in ((A, "A"), (B, "B"), (out, "out")):
+        _dev_f64(t, nm)
+    if E is not None:
+        _dev_f64(E, "E")
+    _check(load().purify_k_step_f64(_ptr(A), _ptr(B), _ptr(E) if E is not None else None,
+                                    _ptr(out), int(A.shape[0]), cP, cE, cI, dY, dI,
+                                    _ptr(red) if red is not None else None, _stream_of()),
+           "k_step_f64")
+    return out
+
+
+def k_gershgorin_f64(F, lohi):
+    _dev_f64(lohi, "lohi")
+    _check(load().purify_k_gershgorin_f64(_ptr(F), int(F.shape[0]), int(F.stride(0)), _ptr(lohi),
+                                          _stream_of()), "k_gershgorin_f64")
+    return lohi
+
+
+def k_lanczos_f64(F, k: int):
+    _dev_f64(F, "F")
+    a = np.zeros(k)
+    b = np.zeros(k)
+    _check(load().purify_k_lanczos_f64(_ptr(F), int(F.shape[0]), int(k), _dptr(a), _dptr(b),
+                                       _stream_of()), "k_lanczos_f64")
+    return a, b

@@ -1,0 +1,113 @@
+// Internal declarations shared by the libpurify translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <vector>
+
+#include "../../include/purify.h"
+
+namespace purify {
+
+// Record the failing call for purify_strerror-style diagnostics and map a
+// CUDA error to PURIFY_ERR_CUDA / PURIFY_ERR_OOM.
+int cuda_status(cudaError_t e, const char* what);
+
+#define PURIFY_CUDA_TRY(call)                                                  \
+    do {                                                                       \
+        cudaError_t e_ = (call);                                               \
+        if (e_ != cudaSuccess) return ::purify::cuda_status(e_, #call);        \
+    } while (0)
+
+#define PURIFY_TRY(call)                                                       \
+    do {                                                                       \
+        int r_ = (call);                                                       \
+        if (r_ != PURIFY_OK) return r_;                                        \
+    } while (0)
+
+// Number of upper-triangle tiles (ti <= tj) for a T x T tile grid.
+inline int64_t upper_tiles(int64_t T) { return T * (T + 1) / 2; }
+
+// ---- float64 SIMT kernels (kernels_fp64.cu) -------------------------------
+// Fused scheme step, see purify_k_step_f64 in purify.h.
+int launch_step_f64(const double* A, const double* B, const double* E, double* C, int64_t n,
+                    double cP, double cE, double cI, double dY, double dI, double* red,
+                    cudaStream_t s);
+// out = a F + b I on an n x n matrix (ld_out = n, ld_f = ldf).
+int launch_affine_f64(const double* F, int64_t ldf, double* out, int64_t n, double a, double b,
+                      cudaStream_t s);
+// Copy the upper triangle onto the lower one in place (n x n, ld n).
+int launch_mirror_upper_f64(double* X, int64_t n, cudaStream_t s);
+// red[0] += trace(X)
+int launch_trace_f64(const double* X, int64_t n, double* red, cudaStream_t s);
+
+// ---- bounds (kernels_bounds.cu) ------------------------------------------
+int launch_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi,
+                          double* scratch, cudaStream_t s);
+int64_t gershgorin_scratch_doubles(int64_t n);
+// k Lanczos steps; scratch holds lanczos_scratch_doubles(n, k) doubles.
+// Writes a[0..k), bsq[0..k) (squared off-diagonals) into scratch tail; the
+// host copies them out (see purify_k_lanczos_f64).
+int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaStream_t s);
+int64_t lanczos_scratch_doubles(int64_t n, int k);
+// Offsets of the a / bsq arrays inside the Lanczos scratch.
+inline int64_t lanczos_a_offset(int64_t n) { return 3 * n + 1; }
+inline int64_t lanczos_bsq_offset(int64_t n, int k) { return 3 * n + 1 + k; }
+
+// Host-side helpers (purify_api.cu)
+int host_bounds_from_lanczos(const double* a, const double* bsq, int k, double g_lo, double g_hi,
+                             double* lo, double* hi);
+
+// Count kernels launched by the library (for the statistics).
+void count_launches(int k);
+long long launches_so_far();
+
+// Scalar schedule of one run (Algorithm 1: alpha, beta; Algorithm 2:
+// branch, alpha, beta, beta_bar), computed on the host.
+struct Schedule {
+    std::vector<double> alpha, beta, betabar;
+    std::vector<int> branch;
+    double beta0 = NAN, betabar0 = NAN;
+    bool converged = false;
+};
+
+struct MixedState;
+
+}  // namespace purify
+
+// The handle behind purify_t.
+struct purify_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    purify_options opt{};
+    int64_t n = 0, cap = 0;
+    double* F = nullptr;
+    double* X[2] = {nullptr, nullptr};
+    double* S = nullptr;
+    double* red = nullptr;
+    int64_t red_cap = 0;  // doubles
+    double* scratch = nullptr;
+    int64_t scratch_cap = 0;  // doubles
+    int cur = -1;
+    bool have_F = false;
+    int64_t nocc = -1;
+    double mu = NAN;
+    purify_bounds b{NAN, NAN, NAN, NAN};
+    purify_stats_t st{};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<cudaEvent_t> pev;  // product timing events (pairs)
+    int pev_used = 0;
+    purify::MixedState* mixed = nullptr;
+};
+
+namespace purify {
+// Product timing: bracket one product launch with events when requested.
+int product_begin(purify_ctx* h);
+int product_end(purify_ctx* h);
+// Sum of the bracketed product times of the last run (seconds), NaN if off.
+double product_seconds(purify_ctx* h);
+int ensure_red(purify_ctx* h, int64_t doubles);
+}  // namespace purify

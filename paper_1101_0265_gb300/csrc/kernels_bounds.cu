@@ -1,0 +1,223 @@
+// Spectral bounds lambda_min, lambda_max of F, the inputs that Algorithm 1
+// and Algorithm 2 require ("the extremal eigenvalues of F or bounds
+// thereof"): Gershgorin discs, tightened by a few float64 Lanczos steps.
+//
+// Both kernels stream F once per pass and are bound by HBM bandwidth: one
+// warp per row reads the row with coalesced 8-byte loads.
+#include "internal.h"
+
+#include <cmath>
+
+namespace purify {
+
+namespace {
+
+constexpr int ROWS_PER_CTA = 8;  // one warp per row
+constexpr unsigned long long GOLDEN = 0x9E3779B97F4A7C15ull;
+constexpr unsigned long long LANCZOS_KEY = 0x11010265ull;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Per-CTA partial (min lo, max hi) of the Gershgorin interval.
+__global__ void __launch_bounds__(256)
+gershgorin_rows_kernel(const double* __restrict__ F, int64_t n, int64_t ld, double* __restrict__ part) {
+    __shared__ double slo[ROWS_PER_CTA], shi[ROWS_PER_CTA];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * ROWS_PER_CTA + warp;
+    double lo = INFINITY, hi = -INFINITY;
+    if (i < n) {
+        const double* row = F + i * ld;
+        double r = 0.0;
+        for (int64_t j = lane; j < n; j += 32) r += (j == i) ? 0.0 : fabs(row[j]);
+        r = warp_sum(r);
+        const double d = row[i];
+        lo = d - r;
+        hi = d + r;
+    }
+    if (lane == 0) {
+        slo[warp] = lo;
+        shi[warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < ROWS_PER_CTA; ++w) {
+            lo = fmin(lo, slo[w]);
+            hi = fmax(hi, shi[w]);
+        }
+        part[2 * blockIdx.x] = lo;
+        part[2 * blockIdx.x + 1] = hi;
+    }
+}
+
+__global__ void minmax_reduce_kernel(const double* __restrict__ part, int64_t m, double* lohi) {
+    __shared__ double slo[32], shi[32];
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t q = threadIdx.x; q < m; q += blockDim.x) {
+        lo = fmin(lo, part[2 * q]);
+        hi = fmax(hi, part[2 * q + 1]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        slo[warp] = lo;
+        shi[warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        for (int w = 1; w < nw; ++w) {
+            lo = fmin(lo, slo[w]);
+            hi = fmax(hi, shi[w]);
+        }
+        lohi[0] = fmin(slo[0], lo);
+        lohi[1] = fmax(shi[0], hi);
+    }
+}
+
+// ---- Lanczos ---------------------------------------------------------------
+// Scratch layout (doubles): v_prev[n] | v[n] | w[n] | qnorm2 | a[k] | bsq[k]
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
+    unsigned long long z = x + GOLDEN;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void lanczos_start_kernel(double* v, double* vprev, int64_t n, double* qnorm2) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long z = splitmix64(LANCZOS_KEY + (unsigned long long)i * GOLDEN);
+        const double q = 2.0 * ((double)(z >> 11) * (1.0 / 9007199254740992.0)) - 1.0;
+        v[i] = q;
+        vprev[i] = 0.0;
+        s += q * q;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) atomicAdd(qnorm2, s);
+}
+
+// v <- v / sqrt(*norm2)
+__global__ void scale_by_norm_kernel(double* v, int64_t n, const double* norm2) {
+    const double inv = 1.0 / sqrt(*norm2);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        v[i] *= inv;
+}
+
+// w = F v - b_{j-1} v_prev; a_j += w . v   (one warp per row)
+__global__ void __launch_bounds__(256)
+lanczos_matvec_kernel(const double* __restrict__ F, int64_t n, const double* __restrict__ v,
+                      const double* __restrict__ vprev, double* __restrict__ w,
+                      const double* bsq_prev, double* a_j) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * ROWS_PER_CTA + warp;
+    __shared__ double sdot[ROWS_PER_CTA];
+    double dot = 0.0;
+    if (i < n) {
+        const double* row = F + i * n;
+        double s = 0.0;
+        for (int64_t j = lane; j < n; j += 32) s = fma(row[j], v[j], s);
+        s = warp_sum(s);
+        const double bprev = bsq_prev ? sqrt(*bsq_prev) : 0.0;
+        const double wi = s - bprev * vprev[i];
+        if (lane == 0) w[i] = wi;
+        dot = wi * v[i];
+    }
+    if (lane == 0) sdot[warp] = dot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < ROWS_PER_CTA; ++q) t += sdot[q];
+        atomicAdd(a_j, t);
+    }
+}
+
+// w -= a_j v; bsq_j += w . w
+__global__ void lanczos_orth_kernel(double* __restrict__ w, const double* __restrict__ v, int64_t n,
+                                    const double* a_j, double* bsq_j) {
+    const double a = *a_j;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double wi = w[i] - a * v[i];
+        w[i] = wi;
+        s += wi * wi;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) atomicAdd(bsq_j, s);
+}
+
+// v_prev <- v; v <- w / b_j  (v <- 0 on breakdown b_j == 0)
+__global__ void lanczos_shift_kernel(double* __restrict__ vprev, double* __restrict__ v,
+                                     const double* __restrict__ w, int64_t n, const double* bsq_j) {
+    const double b = sqrt(*bsq_j);
+    const double inv = b > 0.0 ? 1.0 / b : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        vprev[i] = v[i];
+        v[i] = w[i] * inv;
+    }
+}
+
+unsigned vec_blocks(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    if (b > 152 * 4) b = 152 * 4;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+int64_t gershgorin_scratch_doubles(int64_t n) {
+    return 2 * ((n + ROWS_PER_CTA - 1) / ROWS_PER_CTA);
+}
+
+int launch_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi, double* scratch,
+                          cudaStream_t s) {
+    if (n <= 0 || ld < n) return PURIFY_ERR_INVALID_ARG;
+    const int64_t ctas = (n + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
+    gershgorin_rows_kernel<<<(unsigned)ctas, 32 * ROWS_PER_CTA, 0, s>>>(F, n, ld, scratch);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    minmax_reduce_kernel<<<1, 1024, 0, s>>>(scratch, ctas, lohi);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(2);
+    return PURIFY_OK;
+}
+
+int64_t lanczos_scratch_doubles(int64_t n, int k) { return 3 * n + 1 + 2 * (int64_t)k; }
+
+int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaStream_t s) {
+    if (n <= 0 || k <= 0) return PURIFY_ERR_INVALID_ARG;
+    double* vprev = scratch;
+    double* v = scratch + n;
+    double* w = scratch + 2 * n;
+    double* qn = scratch + 3 * n;
+    double* a = scratch + lanczos_a_offset(n);
+    double* bsq = scratch + lanczos_bsq_offset(n, k);
+    PURIFY_CUDA_TRY(cudaMemsetAsync(qn, 0, sizeof(double) * (1 + 2 * (size_t)k), s));
+    const unsigned vb = vec_blocks(n);
+    lanczos_start_kernel<<<vb, 256, 0, s>>>(v, vprev, n, qn);
+    scale_by_norm_kernel<<<vb, 256, 0, s>>>(v, n, qn);
+    const unsigned rows = (unsigned)((n + ROWS_PER_CTA - 1) / ROWS_PER_CTA);
+    for (int j = 0; j < k; ++j) {
+        lanczos_matvec_kernel<<<rows, 32 * ROWS_PER_CTA, 0, s>>>(F, n, v, vprev, w,
+                                                                   j ? bsq + j - 1 : nullptr, a + j);
+        lanczos_orth_kernel<<<vb, 256, 0, s>>>(w, v, n, a + j, bsq + j);
+        lanczos_shift_kernel<<<vb, 256, 0, s>>>(vprev, v, w, n, bsq + j);
+    }
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(2 + 3 * k);
+    return PURIFY_OK;
+}
+
+}  // namespace purify

@@ -1,0 +1,772 @@
+// C ABI of libpurify: handle management, the host-side scalar schedule of
+// the two scale-and-fold schemes (Algorithm 1, Algorithm 2), and the
+// iteration driver that issues one fused device step per matrix product.
+//
+// Host arithmetic here is compiled without FMA contraction so that the
+// scalar schedule (alpha, beta, beta-bar, the branch test) is evaluated in
+// the plain float64 order the algorithms state.
+#include "internal.h"
+#include "mixed.h"
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace purify {
+
+static thread_local char g_last_error[256] = "";
+
+static std::atomic<long long> g_launches{0};
+void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+int cuda_status(cudaError_t e, const char* what) {
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PURIFY_ERR_OOM : PURIFY_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// Scalar schedule (host, float64)
+// ---------------------------------------------------------------------------
+
+// Algorithm 1: alpha = 3 / sqrt(12 beta^2 - 18 beta + 9) (solves Eq. 3).
+static double fixed_mu_alpha(double beta) {
+    return 3.0 / std::sqrt(12.0 * beta * beta - 18.0 * beta + 9.0);
+}
+
+// Algorithm 1: gamma = 2 max(lmax - mu, mu - lmin).
+static double fixed_mu_gamma(double lmin, double lmax, double mu) {
+    return 2.0 * std::max(lmax - mu, mu - lmin);
+}
+
+// Algorithm 1: beta = (1 - xi / gamma) / 2 for a gap centred on mu; for an
+// off-centre gap the nearer edge is used.
+static double fixed_mu_beta0(double gamma, double mu, double homo, double lumo) {
+    const double half = std::min(mu - homo, lumo - mu);
+    return 0.5 - half / gamma;
+}
+
+// Algorithm 2: beta = f_0(lumo), beta_bar = f_0(homo).
+static void tc_beta0(double lmin, double lmax, double homo, double lumo, double* b, double* bb) {
+    const double w = lmax - lmin;
+    *b = (lmax - lumo) / w;
+    *bb = (lmax - homo) / w;
+}
+
+// Algorithm 2's test (strict): P_{1,0} when beta + beta_bar > 1.
+static int tc_branch(double b, double bb) { return (b + bb) > 1.0 ? 1 : 0; }
+
+// Algorithm 2: alpha of the chosen branch.
+static double tc_alpha(int branch, double b, double bb) {
+    return branch ? b / (2.0 - b) : (1.0 - bb) / (1.0 + bb);
+}
+
+// Eq. 4 (branch 1) / Eq. 5 (branch 0) on a scalar.
+static double tc_map(int branch, double a, double x) {
+    if (branch) {
+        const double y = (1.0 + a) * x - a;
+        return y * y;
+    }
+    return 2.0 * (1.0 + a) * x - (1.0 + a) * (1.0 + a) * x * x;
+}
+
+static bool is_fixed_mu(int scheme) {
+    return scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_FIXED_MU_MONO;
+}
+static bool is_scaled(int scheme) { return scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_TC_SF; }
+
+static int build_schedule(int scheme, double lmin, double lmax, double mu, double homo, double lumo,
+                          double tol, int max_iter, Schedule& S) {
+    if (is_fixed_mu(scheme)) {
+        const double gamma = fixed_mu_gamma(lmin, lmax, mu);
+        double beta = fixed_mu_beta0(gamma, mu, homo, lumo);
+        S.beta0 = beta;
+        S.betabar0 = 1.0 - beta;
+        const bool scaled = is_scaled(scheme);
+        while (beta > tol && (int)S.alpha.size() < max_iter) {
+            const double alpha = scaled ? fixed_mu_alpha(beta) : 1.0;
+            const double bs = alpha * (beta - 0.5) + 0.5;
+            beta = 3.0 * bs * bs - 2.0 * bs * bs * bs;
+            S.alpha.push_back(alpha);
+            S.beta.push_back(beta);
+            S.betabar.push_back(1.0 - beta);
+            S.branch.push_back(0);
+        }
+        S.converged = beta <= tol;
+        return PURIFY_OK;
+    }
+    double b, bb;
+    tc_beta0(lmin, lmax, homo, lumo, &b, &bb);
+    S.beta0 = b;
+    S.betabar0 = bb;
+    const bool scaled = is_scaled(scheme);
+    while (std::max(b, 1.0 - bb) > tol && (int)S.alpha.size() < max_iter) {
+        const int br = tc_branch(b, bb);
+        const double a = scaled ? tc_alpha(br, b, bb) : 0.0;
+        const double nb = tc_map(br, a, b), nbb = tc_map(br, a, bb);
+        b = nb;
+        bb = nbb;
+        S.alpha.push_back(a);
+        S.branch.push_back(br);
+        S.beta.push_back(b);
+        S.betabar.push_back(bb);
+    }
+    S.converged = std::max(b, 1.0 - bb) <= tol;
+    return PURIFY_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Cyclic Jacobi on a small symmetric matrix (Lanczos tridiagonal)
+// ---------------------------------------------------------------------------
+
+static void jacobi_eig(std::vector<double>& A, int m, std::vector<double>& V) {
+    V.assign((size_t)m * m, 0.0);
+    for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < m; ++p)
+            for (int q = p + 1; q < m; ++q) off += A[(size_t)p * m + q] * A[(size_t)p * m + q];
+        if (off == 0.0) break;
+        for (int p = 0; p < m; ++p) {
+            for (int q = p + 1; q < m; ++q) {
+                const double apq = A[(size_t)p * m + q];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)p * m + p], aqq = A[(size_t)q * m + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) /
+                                 (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < m; ++k) {  // A <- J^T A J
+                    const double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
+                    A[(size_t)k * m + p] = c * akp - s * akq;
+                    A[(size_t)k * m + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < m; ++k) {
+                    const double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
+                    A[(size_t)p * m + k] = c * apk - s * aqk;
+                    A[(size_t)q * m + k] = s * apk + c * aqk;
+                }
+                for (int k = 0; k < m; ++k) {
+                    const double vkp = V[(size_t)k * m + p], vkq = V[(size_t)k * m + q];
+                    V[(size_t)k * m + p] = c * vkp - s * vkq;
+                    V[(size_t)k * m + q] = s * vkp + c * vkq;
+                }
+            }
+        }
+    }
+}
+
+int host_bounds_from_lanczos(const double* a, const double* bsq, int k, double g_lo, double g_hi,
+                             double* lo, double* hi) {
+    // Truncate at an exact breakdown (b_j == 0: invariant subspace found).
+    int m = 0;
+    std::vector<double> b(k);
+    for (int j = 0; j < k; ++j) {
+        b[j] = std::sqrt(std::max(bsq[j], 0.0));
+        ++m;
+        if (b[j] == 0.0) break;
+    }
+    std::vector<double> w(m), last(m);
+    int r = purify_tridiag_eig(a, b.data(), m, w.data(), last.data());
+    if (r != PURIFY_OK) return r;
+    const double r_lo = std::fabs(b[m - 1] * last[0]);
+    const double r_hi = std::fabs(b[m - 1] * last[m - 1]);
+    *lo = std::max(g_lo, w[0] - r_lo);
+    *hi = std::min(g_hi, w[m - 1] + r_hi);
+    return PURIFY_OK;
+}
+
+}  // namespace purify
+
+using namespace purify;
+
+// ---------------------------------------------------------------------------
+// Handle
+// ---------------------------------------------------------------------------
+
+static void free_buffers(purify_ctx* h) {
+    cudaFree(h->F);
+    cudaFree(h->X[0]);
+    cudaFree(h->X[1]);
+    cudaFree(h->S);
+    h->F = h->X[0] = h->X[1] = h->S = nullptr;
+    h->cap = 0;
+}
+
+static int ensure_capacity(purify_ctx* h, int64_t n) {
+    if (n <= h->cap) return PURIFY_OK;
+    free_buffers(h);
+    const size_t bytes = sizeof(double) * (size_t)n * (size_t)n;
+    PURIFY_CUDA_TRY(cudaMalloc(&h->F, bytes));
+    PURIFY_CUDA_TRY(cudaMalloc(&h->X[0], bytes));
+    PURIFY_CUDA_TRY(cudaMalloc(&h->X[1], bytes));
+    PURIFY_CUDA_TRY(cudaMalloc(&h->S, bytes));
+    h->cap = n;
+    return PURIFY_OK;
+}
+
+static int ensure_scratch(purify_ctx* h, int64_t doubles) {
+    if (doubles <= h->scratch_cap) return PURIFY_OK;
+    cudaFree(h->scratch);
+    h->scratch = nullptr;
+    h->scratch_cap = 0;
+    PURIFY_CUDA_TRY(cudaMalloc(&h->scratch, sizeof(double) * (size_t)doubles));
+    h->scratch_cap = doubles;
+    return PURIFY_OK;
+}
+
+int purify::ensure_red(purify_ctx* h, int64_t doubles) {
+    if (doubles <= h->red_cap) return PURIFY_OK;
+    cudaFree(h->red);
+    h->red = nullptr;
+    h->red_cap = 0;
+    PURIFY_CUDA_TRY(cudaMalloc(&h->red, sizeof(double) * (size_t)doubles));
+    h->red_cap = doubles;
+    return PURIFY_OK;
+}
+
+int purify::product_begin(purify_ctx* h) {
+    if (!h->opt.time_products) return PURIFY_OK;
+    const size_t need = 2 * (size_t)h->pev_used + 2;
+    while (h->pev.size() < need) {
+        cudaEvent_t e;
+        PURIFY_CUDA_TRY(cudaEventCreate(&e));
+        h->pev.push_back(e);
+    }
+    PURIFY_CUDA_TRY(cudaEventRecord(h->pev[2 * (size_t)h->pev_used], h->stream));
+    return PURIFY_OK;
+}
+
+int purify::product_end(purify_ctx* h) {
+    if (!h->opt.time_products) return PURIFY_OK;
+    PURIFY_CUDA_TRY(cudaEventRecord(h->pev[2 * (size_t)h->pev_used + 1], h->stream));
+    ++h->pev_used;
+    return PURIFY_OK;
+}
+
+double purify::product_seconds(purify_ctx* h) {
+    if (!h->opt.time_products) return NAN;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return NAN;
+    double s = 0.0;
+    for (int i = 0; i < h->pev_used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->pev[2 * (size_t)i], h->pev[2 * (size_t)i + 1]) != cudaSuccess)
+            return NAN;
+        s += 1e-3 * ms;
+    }
+    return s;
+}
+
+static int set_device(purify_ctx* h) {
+    PURIFY_CUDA_TRY(cudaSetDevice(h->device));
+    return PURIFY_OK;
+}
+
+extern "C" {
+
+void purify_options_default(purify_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = PURIFY_FP64;
+    opt->branch_rule = PURIFY_BRANCH_BETA;
+    opt->lanczos_steps = 32;
+    opt->refine_squares = 0;
+    opt->digits = 0;
+}
+
+static int check_options(const purify_options* o) {
+    if (o->precision != PURIFY_FP64 && o->precision != PURIFY_MIXED) return PURIFY_ERR_INVALID_ARG;
+    if (o->branch_rule != PURIFY_BRANCH_BETA && o->branch_rule != PURIFY_BRANCH_TRACE)
+        return PURIFY_ERR_INVALID_ARG;
+    if (o->lanczos_steps < 0 || o->lanczos_steps > 512) return PURIFY_ERR_INVALID_ARG;
+    if (o->refine_squares < 0 || o->refine_squares > 8) return PURIFY_ERR_INVALID_ARG;
+    if (o->digits != 0 && (o->digits < 2 || o->digits > kMaxDigits)) return PURIFY_ERR_INVALID_ARG;
+    return PURIFY_OK;
+}
+
+int purify_create(purify_t* out, int device, void* cuda_stream, const purify_options* opt) {
+    if (!out) return PURIFY_ERR_INVALID_ARG;
+    *out = nullptr;
+    purify_options o;
+    purify_options_default(&o);
+    if (opt) o = *opt;
+    PURIFY_TRY(check_options(&o));
+    int ndev = 0;
+    PURIFY_CUDA_TRY(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return PURIFY_ERR_INVALID_ARG;
+    cudaDeviceProp prop;
+    PURIFY_CUDA_TRY(cudaGetDeviceProperties(&prop, device));
+    if (!(prop.major == 10 && prop.minor == 3)) return PURIFY_ERR_UNSUPPORTED;
+    purify_ctx* h = new (std::nothrow) purify_ctx();
+    if (!h) return PURIFY_ERR_OOM;
+    h->device = device;
+    h->opt = o;
+    int r = set_device(h);
+    if (r == PURIFY_OK) {
+        if (cuda_stream) {
+            h->stream = (cudaStream_t)cuda_stream;
+        } else {
+            cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) r = cuda_status(e, "cudaStreamCreateWithFlags");
+            h->own_stream = (e == cudaSuccess);
+        }
+    }
+    if (r == PURIFY_OK) {
+        cudaError_t e = cudaEventCreate(&h->e0);
+        if (e == cudaSuccess) e = cudaEventCreate(&h->e1);
+        if (e != cudaSuccess) r = cuda_status(e, "cudaEventCreate");
+    }
+    if (r != PURIFY_OK) {
+        purify_destroy(h);
+        return r;
+    }
+    h->st.status = PURIFY_ERR_STATE;
+    *out = h;
+    return PURIFY_OK;
+}
+
+int purify_destroy(purify_t h) {
+    if (!h) return PURIFY_OK;
+    cudaSetDevice(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    free_buffers(h);
+    cudaFree(h->red);
+    cudaFree(h->scratch);
+    mixed_free(h->mixed);
+    for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
+    if (h->e0) cudaEventDestroy(h->e0);
+    if (h->e1) cudaEventDestroy(h->e1);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return PURIFY_OK;
+}
+
+int purify_set_options(purify_t h, const purify_options* opt) {
+    if (!h || !opt) return PURIFY_ERR_INVALID_ARG;
+    PURIFY_TRY(check_options(opt));
+    h->opt = *opt;
+    return PURIFY_OK;
+}
+
+const double* purify_density_device_ptr(purify_t h) {
+    if (!h || h->cur < 0) return nullptr;
+    return h->X[h->cur];
+}
+
+int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld, int64_t nocc,
+                           double mu, const purify_bounds* b) {
+    if (!h || !F || !b || n <= 0 || ld < n) return PURIFY_ERR_INVALID_ARG;
+    if (nocc > n) return PURIFY_ERR_INVALID_ARG;
+    if (n > (int64_t)1 << 17) return PURIFY_ERR_INVALID_ARG;
+    PURIFY_TRY(set_device(h));
+    const long long set_launches0 = launches_so_far();
+    h->have_F = false;
+    h->cur = -1;
+    PURIFY_TRY(ensure_capacity(h, n));
+    h->n = n;
+    PURIFY_CUDA_TRY(cudaMemcpy2DAsync(h->F, sizeof(double) * n, F, sizeof(double) * ld,
+                                      sizeof(double) * n, n, cudaMemcpyDefault, h->stream));
+    PURIFY_TRY(launch_mirror_upper_f64(h->F, n, h->stream));
+
+    purify_bounds bb = *b;
+    if (std::isnan(bb.lmin) || std::isnan(bb.lmax)) {
+        const int k = (int)std::min<int64_t>(h->opt.lanczos_steps, n);
+        const int64_t need = 2 + gershgorin_scratch_doubles(n) + (k > 0 ? lanczos_scratch_doubles(n, k) : 0);
+        PURIFY_TRY(ensure_scratch(h, need));
+        double* lohi = h->scratch;
+        double* gs = h->scratch + 2;
+        PURIFY_TRY(launch_gershgorin_f64(h->F, n, n, lohi, gs, h->stream));
+        double g[2];
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(g, lohi, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
+        double lo = g[0], hi = g[1];
+        if (k > 0) {
+            double* ls = h->scratch + 2;  // Gershgorin partials are consumed already
+            PURIFY_TRY(launch_lanczos_f64(h->F, n, k, ls, h->stream));
+            std::vector<double> a(k), bsq(k);
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(a.data(), ls + lanczos_a_offset(n), sizeof(double) * k,
+                                            cudaMemcpyDeviceToHost, h->stream));
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(bsq.data(), ls + lanczos_bsq_offset(n, k),
+                                            sizeof(double) * k, cudaMemcpyDeviceToHost, h->stream));
+            PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+            PURIFY_TRY(host_bounds_from_lanczos(a.data(), bsq.data(), k, g[0], g[1], &lo, &hi));
+        } else {
+            PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        }
+        if (std::isnan(bb.lmin)) bb.lmin = lo;
+        if (std::isnan(bb.lmax)) bb.lmax = hi;
+        // Estimated extremes never cut into the given gap edges.
+        if (!std::isnan(bb.homo)) bb.lmin = std::min(bb.lmin, bb.homo);
+        if (!std::isnan(bb.lumo)) bb.lmax = std::max(bb.lmax, bb.lumo);
+    }
+    if (!(bb.lmax > bb.lmin)) return PURIFY_ERR_BOUNDS;
+    if (!std::isnan(bb.homo) && !std::isnan(bb.lumo)) {
+        if (!(bb.homo < bb.lumo)) return PURIFY_ERR_BOUNDS;
+        if (bb.homo < bb.lmin || bb.lumo > bb.lmax) return PURIFY_ERR_BOUNDS;
+    }
+    const int set_launches = (int)(launches_so_far() - set_launches0);
+    h->b = bb;
+    h->nocc = nocc;
+    h->mu = mu;
+    std::memset(&h->st, 0, sizeof(h->st));
+    h->st.status = PURIFY_ERR_STATE;
+    h->st.lmin = bb.lmin;
+    h->st.lmax = bb.lmax;
+    h->st.homo = bb.homo;
+    h->st.lumo = bb.lumo;
+    h->st.mu = mu;
+    h->st.kernel_launches = set_launches;
+    h->st.product_seconds = NAN;
+    h->have_F = true;
+    return PURIFY_OK;
+}
+
+// One float64 step with reductions into slot `slot` (4 doubles).
+static int step64(purify_ctx* h, const double* A, const double* B, const double* E, double* C,
+                  double cP, double cE, double cI, double dY, double dI, int64_t slot) {
+    PURIFY_TRY(product_begin(h));
+    PURIFY_TRY(launch_step_f64(A, B, E, C, h->n, cP, cE, cI, dY, dI, h->red + 4 * slot, h->stream));
+    ++h->st.product_launches;
+    return product_end(h);
+}
+
+// Coefficients of the Algorithm 2 step on X: Y = cP X^2 + cE X + cI I.
+static void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
+    if (branch) {  // ((1 + a) X - a I)^2
+        *cP = (1.0 + a) * (1.0 + a);
+        *cE = -2.0 * a * (1.0 + a);
+        *cI = a * a;
+    } else {  // 2 (1 + a) X - (1 + a)^2 X^2
+        *cP = -(1.0 + a) * (1.0 + a);
+        *cE = 2.0 * (1.0 + a);
+        *cI = 0.0;
+    }
+}
+
+static int run_fp64(purify_ctx* h, int scheme, double tol, int max_iter, double mu, Schedule& S,
+                    bool trace_rule, int* iters_out, std::vector<double>& red_host) {
+    const int64_t n = h->n;
+    const double lmin = h->b.lmin, lmax = h->b.lmax;
+    int m = (int)S.alpha.size();
+    if (is_fixed_mu(scheme)) {
+        // X_s of the first iteration straight from F: X_0 = c0 I + c1 F.
+        const double gamma = fixed_mu_gamma(lmin, lmax, mu);
+        const double c0 = mu / gamma + 0.5, c1 = -1.0 / gamma;
+        PURIFY_TRY(ensure_red(h, 4 * (int64_t)(2 * m + 2)));
+        PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * (2 * m + 2), h->stream));
+        PURIFY_CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+        if (m == 0) {
+            PURIFY_TRY(launch_affine_f64(h->F, n, h->X[0], n, c1, c0, h->stream));
+            h->cur = 0;
+        } else {
+            const double a1 = S.alpha[0];
+            PURIFY_TRY(launch_affine_f64(h->F, n, h->X[0], n, a1 * c1, a1 * (c0 - 0.5) + 0.5, h->stream));
+            int xs = 0;
+            for (int i = 0; i < m; ++i) {
+                // S = X_s^2
+                PURIFY_TRY(step64(h, h->X[xs], h->X[xs], nullptr, h->S, 1.0, 0.0, 0.0, 1.0, 0.0, 2 * i));
+                // X_i = 3 S - 2 S X_s, emitted as the next X_s (or as D after the last)
+                const double an = (i + 1 < m) ? S.alpha[i + 1] : 1.0;
+                const double dY = an, dI = 0.5 * (1.0 - an);
+                PURIFY_TRY(step64(h, h->S, h->X[xs], h->S, h->X[xs ^ 1], -2.0, 3.0, 0.0, dY, dI, 2 * i + 1));
+                xs ^= 1;
+            }
+            h->cur = xs;
+        }
+        PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+        red_host.assign(4 * (size_t)(2 * m + 2), 0.0);
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(red_host.data(), h->red, sizeof(double) * red_host.size(),
+                                        cudaMemcpyDeviceToHost, h->stream));
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        *iters_out = m;
+        return PURIFY_OK;
+    }
+    // Algorithm 2
+    const double w = lmax - lmin;
+    const double c0 = lmax / w, c1 = -1.0 / w;
+    const int slots = (trace_rule ? max_iter : m) + 2;
+    PURIFY_TRY(ensure_red(h, 4 * (int64_t)slots));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * slots, h->stream));
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+    PURIFY_TRY(launch_affine_f64(h->F, n, h->X[0], n, c1, c0, h->stream));
+    int x = 0;
+    if (!trace_rule) {
+        for (int i = 0; i < m; ++i) {
+            double cP, cE, cI;
+            tc_coeffs(S.branch[i], S.alpha[i], &cP, &cE, &cI);
+            PURIFY_TRY(step64(h, h->X[x], h->X[x], h->X[x], h->X[x ^ 1], cP, cE, cI, 1.0, 0.0, i));
+            x ^= 1;
+        }
+        h->cur = x;
+        PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+        red_host.assign(4 * (size_t)slots, 0.0);
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(red_host.data(), h->red, sizeof(double) * red_host.size(),
+                                        cudaMemcpyDeviceToHost, h->stream));
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        *iters_out = m;
+        return PURIFY_OK;
+    }
+    // Trace rule: the branch of step i needs trace(X_{i-1}); one host round
+    // trip per step.  Slot max_iter + 1 holds trace(X_0).
+    const bool have_gap = !std::isnan(h->b.homo) && !std::isnan(h->b.lumo);
+    const bool scaled = is_scaled(scheme);
+    double b = S.beta0, bb = S.betabar0;
+    S.alpha.clear();
+    S.branch.clear();
+    S.beta.clear();
+    S.betabar.clear();
+    double* tr0 = h->red + 4 * (int64_t)(max_iter + 1);
+    PURIFY_TRY(launch_trace_f64(h->X[0], n, tr0, h->stream));
+    double tr_prev;
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(&tr_prev, tr0, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    int it = 0;
+    bool done = have_gap && std::max(b, 1.0 - bb) <= tol;
+    while (!done && it < max_iter) {
+        const int br = tr_prev > (double)h->nocc ? 1 : 0;
+        const double a = scaled ? tc_alpha(br, b, bb) : 0.0;
+        double cP, cE, cI;
+        tc_coeffs(br, a, &cP, &cE, &cI);
+        PURIFY_TRY(step64(h, h->X[x], h->X[x], h->X[x], h->X[x ^ 1], cP, cE, cI, 1.0, 0.0, it));
+        x ^= 1;
+        double r[4];
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(r, h->red + 4 * it, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        tr_prev = r[0];
+        if (have_gap) {
+            const double nb = tc_map(br, a, b), nbb = tc_map(br, a, bb);
+            b = nb;
+            bb = nbb;
+        }
+        S.alpha.push_back(a);
+        S.branch.push_back(br);
+        S.beta.push_back(b);
+        S.betabar.push_back(bb);
+        ++it;
+        if (have_gap) done = std::max(b, 1.0 - bb) <= tol;
+        else done = std::sqrt(std::max(r[1], 0.0)) <= tol;
+    }
+    S.converged = done;
+    h->cur = x;
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+    red_host.assign(4 * (size_t)slots, 0.0);
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(red_host.data(), h->red, sizeof(double) * red_host.size(),
+                                    cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    *iters_out = it;
+    return PURIFY_OK;
+}
+
+int purify_run(purify_t h, int scheme, double tol, int max_iter) {
+    if (!h) return PURIFY_ERR_INVALID_ARG;
+    if (!h->have_F) return PURIFY_ERR_STATE;
+    if (scheme < PURIFY_FIXED_MU_SF || scheme > PURIFY_TC_MONO) return PURIFY_ERR_INVALID_ARG;
+    if (!(tol >= 0.0) || max_iter < 0 || max_iter > 10000) return PURIFY_ERR_INVALID_ARG;
+    PURIFY_TRY(set_device(h));
+    const purify_bounds& bb = h->b;
+    const bool have_gap = !std::isnan(bb.homo) && !std::isnan(bb.lumo);
+    const bool trace_rule = !is_fixed_mu(scheme) && h->opt.branch_rule == PURIFY_BRANCH_TRACE;
+    double mu = h->mu;
+    if (is_fixed_mu(scheme)) {
+        if (!have_gap) return PURIFY_ERR_BOUNDS;
+        if (std::isnan(mu)) mu = 0.5 * (bb.homo + bb.lumo);
+        if (!(std::min(mu - bb.homo, bb.lumo - mu) > 0.0)) return PURIFY_ERR_BOUNDS;
+        if (mu <= bb.lmin || mu >= bb.lmax) return PURIFY_ERR_BOUNDS;
+    } else {
+        if (trace_rule) {
+            if (h->nocc < 0) return PURIFY_ERR_INVALID_ARG;
+            if (scheme == PURIFY_TC_SF && !have_gap) return PURIFY_ERR_BOUNDS;
+        } else if (!have_gap) {
+            return PURIFY_ERR_BOUNDS;
+        }
+    }
+    Schedule S;
+    if (have_gap)
+        PURIFY_TRY(build_schedule(scheme, bb.lmin, bb.lmax, mu, bb.homo, bb.lumo, tol, max_iter, S));
+    h->cur = -1;
+    const long long launches0 = launches_so_far();
+    h->pev_used = 0;
+    h->st.product_launches = 0;
+    h->st.refine_multiplications = 0;
+    h->st.tensor_flops = 0.0;
+    h->st.digit_max = 0;
+    std::vector<double> red;
+    int iters = 0;
+    int r;
+    if (h->opt.precision == PURIFY_MIXED) {
+        if (trace_rule) return PURIFY_ERR_UNSUPPORTED;
+        r = run_mixed(h, scheme, mu, S, &h->cur, red);
+        iters = (int)S.alpha.size();
+    } else {
+        r = run_fp64(h, scheme, tol, max_iter, mu, S, trace_rule, &iters, red);
+    }
+    if (r != PURIFY_OK) {
+        h->st.status = r;
+        return r;
+    }
+    float ms = 0.f;
+    PURIFY_CUDA_TRY(cudaEventElapsedTime(&ms, h->e0, h->e1));
+    purify_stats_t& st = h->st;
+    const int mult_per_it = is_fixed_mu(scheme) ? 2 : 1;
+    st.iterations = iters;
+    st.multiplications = mult_per_it * iters + st.refine_multiplications;
+    st.seconds = 1e-3 * ms;
+    st.mu = mu;
+    st.err_bound = iters > 0 ? std::max(S.beta[iters - 1], 1.0 - S.betabar[iters - 1])
+                             : std::max(S.beta0, 1.0 - S.betabar0);
+    const double nn = (double)h->n;
+    st.useful_flops = (double)st.multiplications * nn * nn * (nn + 1.0);
+    // trace(X_n) and idempotency of the last squared iterate
+    double trace = NAN, idem = NAN;
+    if (h->opt.precision == PURIFY_MIXED) {
+        trace = st.trace;
+        idem = st.idem_err_fro;
+    } else if (iters > 0) {
+        if (is_fixed_mu(scheme)) {
+            trace = red[4 * (size_t)(2 * (iters - 1) + 1) + 0];
+        } else {
+            trace = red[4 * (size_t)(iters - 1) + 0];
+            idem = std::sqrt(std::max(red[4 * (size_t)(iters - 1) + 1], 0.0));
+        }
+    }
+    st.trace = trace;
+    st.idem_err_fro = idem;
+    st.kernel_launches = (int)(launches_so_far() - launches0);
+    st.product_seconds = product_seconds(h);
+    st.trace_err = h->nocc >= 0 ? std::fabs(trace - (double)h->nocc) : NAN;
+    int status = S.converged ? PURIFY_OK : PURIFY_ERR_NOT_CONVERGED;
+    if (status == PURIFY_OK && h->nocc >= 0 && iters > 0 && !(st.trace_err <= 0.5))
+        status = PURIFY_ERR_BOUNDS;
+    st.status = status;
+    return status;
+}
+
+int purify_get_density(purify_t h, double* D, int64_t ld) {
+    if (!h || !D || ld < h->n) return PURIFY_ERR_INVALID_ARG;
+    if (h->cur < 0) return PURIFY_ERR_STATE;
+    PURIFY_TRY(set_device(h));
+    PURIFY_CUDA_TRY(cudaMemcpy2DAsync(D, sizeof(double) * ld, h->X[h->cur], sizeof(double) * h->n,
+                                      sizeof(double) * h->n, h->n, cudaMemcpyDefault, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return PURIFY_OK;
+}
+
+int purify_stats(purify_t h, purify_stats_t* out) {
+    if (!h || !out) return PURIFY_ERR_INVALID_ARG;
+    *out = h->st;
+    return PURIFY_OK;
+}
+
+const char* purify_strerror(int code) {
+    switch (code) {
+        case PURIFY_OK: return "ok";
+        case PURIFY_ERR_INVALID_ARG: return "invalid argument";
+        case PURIFY_ERR_BOUNDS: return "inconsistent spectral bounds, zero gap, or occupied/unoccupied mix-up";
+        case PURIFY_ERR_NOT_CONVERGED: return "not converged within max_iter";
+        case PURIFY_ERR_OOM: return "device out of memory";
+        case PURIFY_ERR_CUDA: return g_last_error[0] ? g_last_error : "CUDA error";
+        case PURIFY_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
+        case PURIFY_ERR_STATE: return "wrong call order";
+        case PURIFY_ERR_UNSUPPORTED: return "unsupported device or feature";
+        default: return "unknown status";
+    }
+}
+
+int purify_schedule(int scheme, double lmin, double lmax, double mu, double homo, double lumo,
+                    double tol, int max_iter, double* alpha, int* branch, double* beta,
+                    double* beta_bar, int* iterations) {
+    if (scheme < PURIFY_FIXED_MU_SF || scheme > PURIFY_TC_MONO) return PURIFY_ERR_INVALID_ARG;
+    if (max_iter < 0 || !(tol >= 0.0)) return PURIFY_ERR_INVALID_ARG;
+    if (!(lmax > lmin) || !(homo < lumo)) return PURIFY_ERR_BOUNDS;
+    if (is_fixed_mu(scheme)) {
+        if (std::isnan(mu)) mu = 0.5 * (homo + lumo);
+        if (!(std::min(mu - homo, lumo - mu) > 0.0)) return PURIFY_ERR_BOUNDS;
+    }
+    Schedule S;
+    PURIFY_TRY(build_schedule(scheme, lmin, lmax, mu, homo, lumo, tol, max_iter, S));
+    const int m = (int)S.alpha.size();
+    for (int i = 0; i < m; ++i) {
+        if (alpha) alpha[i] = S.alpha[i];
+        if (branch) branch[i] = S.branch[i];
+        if (beta) beta[i] = S.beta[i];
+        if (beta_bar) beta_bar[i] = S.betabar[i];
+    }
+    if (iterations) *iterations = m;
+    return S.converged ? PURIFY_OK : PURIFY_ERR_NOT_CONVERGED;
+}
+
+int purify_tridiag_eig(const double* a, const double* b, int m, double* w, double* last_row) {
+    if (!a || !w || m <= 0 || (m > 1 && !b) || m > 4096) return PURIFY_ERR_INVALID_ARG;
+    std::vector<double> A((size_t)m * m, 0.0), V;
+    for (int i = 0; i < m; ++i) {
+        A[(size_t)i * m + i] = a[i];
+        if (i + 1 < m) A[(size_t)i * m + i + 1] = A[(size_t)(i + 1) * m + i] = b[i];
+    }
+    jacobi_eig(A, m, V);
+    std::vector<int> order(m);
+    for (int i = 0; i < m; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        return A[(size_t)x * m + x] < A[(size_t)y * m + y];
+    });
+    for (int j = 0; j < m; ++j) {
+        const int c = order[j];
+        w[j] = A[(size_t)c * m + c];
+        if (last_row) last_row[j] = V[(size_t)(m - 1) * m + c];
+    }
+    return PURIFY_OK;
+}
+
+// ---- kernel-level entry points --------------------------------------------
+
+int purify_k_symm_product_f64(const double* A, const double* B, double* C, int64_t n, void* stream) {
+    if (!A || !B || !C || n <= 0) return PURIFY_ERR_INVALID_ARG;
+    return launch_step_f64(A, B, nullptr, C, n, 1.0, 0.0, 0.0, 1.0, 0.0, nullptr, (cudaStream_t)stream);
+}
+
+int purify_k_step_f64(const double* A, const double* B, const double* E, double* C, int64_t n,
+                      double cP, double cE, double cI, double dY, double dI, double* red,
+                      void* stream) {
+    if (!A || !B || !C || n <= 0) return PURIFY_ERR_INVALID_ARG;
+    if (!E && cE != 0.0) return PURIFY_ERR_INVALID_ARG;
+    if (C == A || C == B || (E && C == E)) return PURIFY_ERR_INVALID_ARG;
+    return launch_step_f64(A, B, E, C, n, cP, cE, cI, dY, dI, red, (cudaStream_t)stream);
+}
+
+int purify_k_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi, void* stream) {
+    if (!F || !lohi || n <= 0 || ld < n) return PURIFY_ERR_INVALID_ARG;
+    double* scratch = nullptr;
+    PURIFY_CUDA_TRY(cudaMalloc(&scratch, sizeof(double) * (size_t)gershgorin_scratch_doubles(n)));
+    int r = launch_gershgorin_f64(F, n, ld, lohi, scratch, (cudaStream_t)stream);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaFree(scratch);
+    if (r != PURIFY_OK) return r;
+    PURIFY_CUDA_TRY(e);
+    return PURIFY_OK;
+}
+
+int purify_k_lanczos_f64(const double* F, int64_t n, int k, double* a, double* b, void* stream) {
+    if (!F || !a || !b || n <= 0 || k <= 0 || k > 4096) return PURIFY_ERR_INVALID_ARG;
+    double* scratch = nullptr;
+    PURIFY_CUDA_TRY(cudaMalloc(&scratch, sizeof(double) * (size_t)lanczos_scratch_doubles(n, k)));
+    cudaStream_t s = (cudaStream_t)stream;
+    int r = launch_lanczos_f64(F, n, k, scratch, s);
+    std::vector<double> bsq(k);
+    if (r == PURIFY_OK) {
+        cudaError_t e = cudaMemcpyAsync(a, scratch + lanczos_a_offset(n), sizeof(double) * k,
+                                        cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bsq.data(), scratch + lanczos_bsq_offset(n, k), sizeof(double) * k,
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) r = cuda_status(e, "lanczos copy-out");
+    }
+    cudaFree(scratch);
+    if (r != PURIFY_OK) return r;
+    for (int j = 0; j < k; ++j) b[j] = std::sqrt(std::max(bsq[j], 0.0));
+    return PURIFY_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+"""CPU-side checks of the library: it loads, exports what include/purify.h
+declares, and its host logic (the scalar schedule and the tridiagonal
+eigensolver used for Lanczos bounds) agrees with the oracle and the paper."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1101_0265_gb300 as P
+from oracle import purify_oracle as O
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _ensure_built():
+    from paper_1101_0265_gb300 import build
+    build.build()
+
+
+def header_symbols():
+    out = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            out += re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?)\b(purify_\w+)\s*\(", src, re.M)
+    return sorted(set(out))
+
+
+def test_library_exports_every_header_symbol():
+    _ensure_built()
+    lib = P.load()
+    syms = header_symbols()
+    assert len(syms) >= 16
+    for s in syms:
+        assert hasattr(lib, s), s
+    # and the binding knows all of them
+    assert set(P.EXPORTED) == set(syms)
+
+
+def test_strerror_names_codes():
+    _ensure_built()
+    for code in (P.OK, P.ERR_INVALID_ARG, P.ERR_BOUNDS, P.ERR_NOT_CONVERGED, P.ERR_OOM,
+                 P.ERR_DEVICE_TIMEOUT, P.ERR_STATE, P.ERR_UNSUPPORTED):
+        assert P.strerror(code) and P.strerror(code) != "unknown status"
+
+
+def _oracle_schedule(scheme, lmin, lmax, mu, homo, lumo, tol, max_iter):
+    if scheme.startswith("FIXED_MU"):
+        g = O.fixed_mu_gamma(lmin, lmax, mu)
+        b = O.fixed_mu_beta0(g, mu, homo, lumo)
+        al, be = O.fixed_mu_schedule(b, tol, max_iter, scheme == "FIXED_MU_SF")
+        return np.array(al), np.zeros(len(al), int), np.array(be)
+    b, bb = O.tc_beta0(lmin, lmax, homo, lumo)
+    s = O.tc_schedule(b, bb, tol, max_iter, scheme == "TC_SF")
+    return (np.array([x[1] for x in s]), np.array([1 if x[0] == "P10" else 0 for x in s]),
+            np.array([x[2] for x in s]))
+
+
+CASES = [(-1.0, 1.0, 0.0, -g / 2, g / 2) for g in (1e-1, 1e-2, 1e-3, 1e-4)] + [
+    (0.0, 1.0, mu, mu - 0.005, mu + 0.005) for mu in (0.1, 0.25, 0.5, 0.75, 0.9)] + [
+    (-3.0, 2.0, -0.4, -0.45, -0.2), (-1.0, 1.0, 0.3, 0.25, 0.31)]
+
+
+@pytest.mark.parametrize("scheme", O.SCHEMES)
+@pytest.mark.parametrize("case", CASES)
+@pytest.mark.parametrize("tol", [1e-12, 1e-9, 1e-6])
+def test_schedule_bitwise_equal_to_oracle(scheme, case, tol):
+    _ensure_built()
+    lmin, lmax, mu, homo, lumo = case
+    s = P.schedule(scheme, lmin, lmax, mu, homo, lumo, tol, 500)
+    al, br, be = _oracle_schedule(scheme, lmin, lmax, mu, homo, lumo, tol, 500)
+    assert s["iterations"] == len(al)
+    assert s["converged"]
+    assert np.array_equal(s["alpha"], al)
+    assert np.array_equal(s["branch"], br)
+    assert np.array_equal(s["beta"], be)
+
+
+def test_schedule_not_converged_and_bad_bounds():
+    _ensure_built()
+    s = P.schedule("TC_SF", -1, 1, 0, -0.05, 0.05, 1e-12, max_iter=3)
+    assert s["iterations"] == 3 and not s["converged"]
+    with pytest.raises(P.PurifyError) as e:
+        P.schedule("TC_SF", -1, 1, 0, 0.05, -0.05, 1e-12)
+    assert e.value.code == P.ERR_BOUNDS
+    with pytest.raises(P.PurifyError) as e:   # gap does not contain mu
+        P.schedule("FIXED_MU_SF", -1, 1, 0.2, -0.05, 0.05, 1e-12)
+    assert e.value.code == P.ERR_BOUNDS
+
+
+@pytest.mark.parametrize("m", [1, 2, 5, 17, 40])
+def test_tridiag_eig_against_lapack(m):
+    _ensure_built()
+    rng = np.random.default_rng(m)
+    a = rng.normal(size=m)
+    b = rng.uniform(0.1, 1.0, size=max(m - 1, 1))
+    T = np.diag(a)
+    if m > 1:
+        T += np.diag(b[:m - 1], 1) + np.diag(b[:m - 1], -1)
+    lam, V = np.linalg.eigh(T)
+    w, last = P.tridiag_eig(a, b[:max(m - 1, 1)])
+    assert np.max(np.abs(w - lam)) < 1e-12 * max(1.0, np.max(np.abs(lam)))
+    assert np.max(np.abs(np.abs(last) - np.abs(V[-1, :]))) < 1e-10
