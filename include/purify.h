@@ -88,7 +88,7 @@ typedef struct purify_options {
     int refine_squares;  /* MIXED: extra unscaled McWeeny steps at the finest digit
                             count after the schedule ends (default 0)                  */
     int digits;          /* MIXED: 0 = per-step digit count from the mapped gap
-                            (default); 2..7 = fixed count                             */
+                            (default); 2..6 = fixed count                             */
     int time_products;   /* 1 = bracket every matrix-product launch with CUDA events
                             on the handle's stream and report their total time      */
     int reserved[10];
@@ -215,6 +215,18 @@ int purify_k_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi
  * norm) to HOST arrays; synchronises the stream.  Allocates 4 n + 2 k + 2
  * doubles of device scratch per call. */
 int purify_k_lanczos_f64(const double* F, int64_t n, int k, double* a, double* b, void* stream);
+
+/* C = A B in the arithmetic of PURIFY_MIXED: A and B (n x n, leading
+ * dimension n, float64, symmetric, device) are split into `digits` bf16
+ * digit planes of 8 bits with scale 2^eA and 2^eB (|A_ij| <= 2^eA, |B_ij| <=
+ * 2^eB are required), multiplied on the tcgen05 tensor cores with exact fp32
+ * accumulation of the leading digit levels, and recombined; tiles on or
+ * above the diagonal are formed and mirrored, so C holds the upper triangle
+ * of A B^T mirrored (= A B when A and B commute).  The product of every step
+ * of Eq. 1 on the mixed path.  Allocates and frees 2 * digits * p^2 bf16 of
+ * device scratch (p = n rounded up to 128); synchronises the stream. */
+int purify_k_digit_product_f64(const double* A, const double* B, double* C, int64_t n, int digits,
+                               int eA, int eB, void* stream);
 
 #ifdef __cplusplus
 }

@@ -34,7 +34,7 @@ EXPORTED = (
     "purify_set_hamiltonian", "purify_run", "purify_get_density", "purify_stats",
     "purify_density_device_ptr", "purify_strerror", "purify_schedule", "purify_tridiag_eig",
     "purify_k_symm_product_f64", "purify_k_step_f64", "purify_k_gershgorin_f64",
-    "purify_k_lanczos_f64",
+    "purify_k_lanczos_f64", "purify_k_digit_product_f64",
 )
 
 
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH):
         "purify_k_step_f64": (ip, [vp, vp, vp, vp, i64, dbl, dbl, dbl, dbl, dbl, vp, vp]),
         "purify_k_gershgorin_f64": (ip, [vp, i64, i64, vp, vp]),
         "purify_k_lanczos_f64": (ip, [vp, i64, ip, dp, dp, vp]),
+        "purify_k_digit_product_f64": (ip, [vp, vp, vp, i64, ip, ip, ip, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -304,3 +305,13 @@ def k_lanczos_f64(F, k: int):
     _check(load().purify_k_lanczos_f64(_ptr(F), int(F.shape[0]), int(k), _dptr(a), _dptr(b),
                                        _stream_of()), "k_lanczos_f64")
     return a, b
+
+
+def k_digit_product_f64(A, B, out, digits: int, eA: int = 0, eB: int = 0):
+    """out = A B through the digit-plane tensor-core product (see purify.h)."""
+    for t, nm in ((A, "A"), (B, "B"), (out, "out")):
+        _dev_f64(t, nm)
+    _check(load().purify_k_digit_product_f64(_ptr(A), _ptr(B), _ptr(out), int(A.shape[0]),
+                                             int(digits), int(eA), int(eB), _stream_of()),
+           "k_digit_product_f64")
+    return out

@@ -1,0 +1,625 @@
+// Digit-plane symmetric products on the tcgen05 tensor cores (sm_103a).
+//
+// A float64 matrix X with |X_ij| <= 2^e is held as s bf16 "digit planes"
+//     X = 2^(e-8) * sum_p V_p,    V_p = d_p * 2^(-r p),  d_p integer,
+// with a leading digit of 8 bits (|d_0| <= 256) and remainder digits of
+// r = 7 bits (|d_p| <= 65; r = 6 above n = 4096), all round-to-nearest.
+// bf16 stores every such value exactly.  The product of two such
+// matrices is the sum over digit pairs (p, q) of V_p V_q^T.  Pairs with
+// p + q = l form "level" l; levels 0, 1 and 2 each get their own fp32
+// accumulator in tensor memory and are exact: by Cauchy-Schwarz a row of d_0
+// has 2-norm <= 256 ||X_i||_2 / 2^e + sqrt(n)/2, so level 0 and level 1 stay
+// below 2^24 in their own units for n <= 8192; level 2 holds the sum of
+// squares of the remainder digits on the product's diagonal, about
+// n 2^(2r) / 12, which the choice of r keeps below 2^24 for uniformly
+// distributed remainders (8-bit remainders exceed it at n = 4096).  All levels
+// >= 3 share a fourth accumulator whose rounding sits 2^-48 below the
+// leading term.  Pairs with p + q >= s are dropped (their size is that of
+// the digits' own truncation).  The four accumulators are recombined in
+// double-float (pairs of fp32) arithmetic in the epilogue, which also
+// applies the step's polynomial (Eq. 4 / Eq. 5 / Algorithm 1's 3S - 2S X_s),
+// re-splits the result into the next step's digit planes, optionally writes
+// float64, and reduces trace and Frobenius norms.
+//
+// Only output tiles on or above the diagonal are formed; each is written
+// twice (itself and its mirror), so every product is exactly symmetric.
+// Exact symmetry matters: antisymmetric rounding errors are not damped by
+// the purification maps.
+//
+// Structure of one CTA (one 128 x 128 output tile, 192 threads):
+//   warp 0  TMA producer: per 32-wide k-chunk one 3D TMA load of all s
+//           planes of the A row panel and one of the B row panel
+//   warp 1  TMEM allocator and MMA issuer (tcgen05.mma kind::f16, bf16 in,
+//           fp32 accumulate, M = N = 128, K = 16)
+//   warps 2-5 epilogue (tcgen05.ld, one TMEM lane quarter each)
+// Every wait on an mbarrier is bounded; on time-out the CTA records an error
+// flag, waits (bounded) for its own copies and MMAs, frees its tensor memory
+// and exits.
+#include "digits_tc.h"
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+namespace purify {
+
+namespace {
+
+constexpr int TILE = 128;        // output tile edge
+constexpr int KC = 32;           // k-chunk (bf16 elements) = 64 bytes: SWIZZLE_64B
+constexpr int PLANE_BYTES = TILE * KC * 2;   // one plane of one operand per stage: 8 KB
+constexpr int NUM_ACC = 4;       // tensor-memory accumulators (levels 0, 1, 2, >= 3)
+constexpr int NTHREADS = 192;
+constexpr long long WAIT_CYCLES = 1ll << 31;  // ~1 s at 2 GHz
+
+// ---- PTX wrappers ------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false when the deadline passes first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long deadline) {
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() > deadline) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
+                                            int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+// 32 lanes x 32 bits, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile written by TMA
+// with 64-byte swizzle: rows of 64 bytes, 8-row groups 512 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
+    d |= (uint64_t)(512 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version (tcgen05)
+    d |= (uint64_t)4 << 61;                          // 64-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: kind::f16, bf16 A and B (K-major), fp32 D,
+// M = 128, N = 128.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TILE >> 3) << 17) |
+                           ((uint32_t)(TILE >> 4) << 24);
+
+// ---- double-float arithmetic (pairs of fp32) ---------------------------------
+
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df df_add_f(df x, float y) {
+    const df s = two_sum(x.h, y);
+    return fast_two_sum(s.h, __fadd_rn(s.l, x.l));
+}
+
+__device__ __forceinline__ df df_add(df x, df y) {
+    const df s = two_sum(x.h, y.h);
+    const df t = two_sum(x.l, y.l);
+    df u = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+    return fast_two_sum(u.h, __fadd_rn(u.l, t.l));
+}
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, e);
+    e = __fmaf_rn(x.l, y.h, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_scale(df x, float pow2) { return {x.h * pow2, x.l * pow2}; }
+
+// ---- kernel parameters ------------------------------------------------------
+
+struct DigitGemmParams {
+    int n, n_pad, s_in;      // matrix size, padded size (multiple of 128), digits of A and B
+    int s_out;               // digits of the output (0 = none)
+    int tiles_per_row;       // n_pad / 128
+    float scale_in_h;        // 2^(eA + eB - 16): value of one unit of the accumulators
+    float e_scale;           // 2^(eA - 8): value of one unit of A's planes (for E)
+    float out_digit_scale;   // 2^(8 - e_out)
+    float out_rscale;        // 2^r of the output's remainder digits
+    df cP, cE, cI, dY, dI;   // Y = cP P + cE E + cI I;  out = dY Y + dI I
+    int use_E;               // E = A (the matrix in the A operand)
+    const __nv_bfloat16* A;  // A's planes (for E), [s_in][n_pad][n_pad]
+    __nv_bfloat16* out;      // output planes [s_out][n_pad][n_pad] (may be null)
+    double* out64;           // float64 output n x n (leading dimension n) or null
+    double* red;             // [0] trace(Y), [1] ||E - P||_F^2, [2] ||Y||_F^2 (atomics) or null
+    int* err;                // device error flag
+};
+
+__device__ __forceinline__ void decode_upper(int t, int& ti, int& tj) {
+    int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((j + 1) * (j + 2) / 2 <= t) ++j;
+    while (j * (j + 1) / 2 > t) --j;
+    tj = j;
+    ti = t - j * (j + 1) / 2;
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const DigitGemmParams prm, int stages) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte aligned operand area: stages x (A planes | B planes)
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const int s = prm.s_in;
+    const int stage_bytes = 2 * s * PLANE_BYTES;
+    uint64_t* bars = (uint64_t*)(base + (size_t)stages * stage_bytes);
+    // bars[0..stages): full, bars[stages..2 stages): empty, bars[2 stages]: accumulators ready
+    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * stages + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int ti, tj;
+    decode_upper(blockIdx.x, ti, tj);
+    const int nk = prm.n_pad / KC;
+    const long long deadline = clock64() + WAIT_CYCLES;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2 * stages + 1; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), NUM_ACC * TILE);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            int issued = 0;
+            for (int kc = 0; kc < nk; ++kc) {
+                const int st = kc % stages;
+                const uint32_t ph = (uint32_t)((kc / stages) & 1);
+                if (kc >= stages && !mbar_wait(smem_u32(&bars[stages + st]), ph ^ 1, deadline)) {
+                    atomicExch(prm.err, 1);
+                    *abort_flag = 1;
+                    break;
+                }
+                if (*abort_flag) break;
+                const uint32_t full = smem_u32(&bars[st]);
+                uint8_t* sa = base + (size_t)st * stage_bytes;
+                mbar_arrive_expect_tx(full, (uint32_t)stage_bytes);
+                tma_load_3d(smem_u32(sa), &mapA, full, kc * KC, ti * TILE, 0);
+                tma_load_3d(smem_u32(sa + s * PLANE_BYTES), &mapB, full, kc * KC, tj * TILE, 0);
+                ++issued;
+            }
+            // wait (bounded) for the copies this thread issued
+            for (int kc = (issued > stages ? issued - stages : 0); kc < issued; ++kc)
+                mbar_wait(smem_u32(&bars[kc % stages]), (uint32_t)((kc / stages) & 1), deadline + WAIT_CYCLES);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            uint32_t started = 0;  // bit a: accumulator a has been written
+            bool ok = true;
+            for (int kc = 0; kc < nk; ++kc) {
+                const int st = kc % stages;
+                const uint32_t ph = (uint32_t)((kc / stages) & 1);
+                if (!mbar_wait(smem_u32(&bars[st]), ph, deadline) || *abort_flag) {
+                    atomicExch(prm.err, 2);
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = smem_u32(base + (size_t)st * stage_bytes);
+                const uint32_t sb = sa + s * PLANE_BYTES;
+                for (int p = 0; p < s; ++p) {
+                    for (int q = 0; p + q < s; ++q) {
+                        const int a = (p + q < NUM_ACC - 1) ? p + q : NUM_ACC - 1;
+                        const uint32_t d = tmem + (uint32_t)(a * TILE);
+#pragma unroll
+                        for (int kk = 0; kk < KC / 16; ++kk) {
+                            const uint64_t ad = smem_desc_sw64(sa + p * PLANE_BYTES + kk * 32);
+                            const uint64_t bd = smem_desc_sw64(sb + q * PLANE_BYTES + kk * 32);
+                            mma_bf16(d, ad, bd, IDESC, (started >> a) & 1u);
+                            started |= 1u << a;
+                        }
+                    }
+                }
+                mma_commit(smem_u32(&bars[stages + st]));
+            }
+            // zero-fill accumulators that no pair reached (s < 4)
+            mma_commit(smem_u32(&bars[2 * stages]));
+            if (!ok) mbar_wait(smem_u32(&bars[2 * stages]), 0, deadline + WAIT_CYCLES);
+            (void)started;
+        }
+    } else {
+        // epilogue warps 2..5: lane quarter q = warp % 4
+        const int quarter = warp & 3;
+        bool ready = mbar_wait(smem_u32(&bars[2 * stages]), 0, deadline + WAIT_CYCLES);
+        if (!ready) {
+            atomicExch(prm.err, 3);
+            *abort_flag = 1;
+        }
+        // tcgen05.ld is warp-collective: decide once per warp
+        ready = __all_sync(0xffffffffu, ready && !*abort_flag);
+        tc_fence_after();
+        const int row_in_tile = quarter * 32 + lane;
+        const int i = ti * TILE + row_in_tile;
+        const bool diag_tile = (ti == tj);
+        const int nacc = s < NUM_ACC ? s : NUM_ACC;
+        double s_tr = 0.0;  // the trace decides the occupation check: float64
+        float s_idem = 0.f, s_fro = 0.f;
+        if (ready) {
+            const size_t plane = (size_t)prm.n_pad * prm.n_pad;
+            for (int c0 = 0; c0 < TILE; c0 += 16) {
+                const int jb = tj * TILE + c0;
+                float acc[NUM_ACC][16];
+#pragma unroll
+                for (int a = 0; a < NUM_ACC; ++a) {
+                    if (a < nacc) {
+                        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * TILE + c0), acc[a]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) acc[a][c] = 0.f;
+                    }
+                }
+                // E = A at (i, jb .. jb + 15), summed from its digit planes
+                df Ev[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) Ev[c] = {0.f, 0.f};
+                if (prm.use_E) {
+                    for (int p = 0; p < s; ++p) {
+                        const __nv_bfloat16* src = prm.A + p * plane + (size_t)i * prm.n_pad + jb;
+                        uint4 u[2];
+                        u[0] = *(const uint4*)src;
+                        u[1] = *(const uint4*)(src + 8);
+                        const __nv_bfloat16* hv = (const __nv_bfloat16*)u;
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) Ev[c] = df_add_f(Ev[c], __bfloat162float(hv[c]));
+                    }
+                }
+                // O = dY (cP P + cE E + cI I) + dI I, zero outside n x n
+                df Ov[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int j = jb + c;
+                    df P = two_sum(acc[0][c], acc[1][c]);
+                    P = df_add_f(P, acc[2][c]);
+                    P = df_add_f(P, acc[3][c]);
+                    P = df_scale(P, prm.scale_in_h);
+                    const df E = df_scale(Ev[c], prm.e_scale);
+                    df Y = df_add(df_mul(prm.cP, P), df_mul(prm.cE, E));
+                    if (i == j) Y = df_add(Y, prm.cI);
+                    df O = df_mul(prm.dY, Y);
+                    if (i == j) O = df_add(O, prm.dI);
+                    const bool valid = i < prm.n && j < prm.n;
+                    if (!valid) O = {0.f, 0.f};
+                    Ov[c] = O;
+                    if (valid && (!diag_tile || i <= j)) {
+                        const float w = (i == j) ? 1.f : 2.f;
+                        if (i == j) s_tr += (double)Y.h + (double)Y.l;
+                        const df dE = df_add(E, {-P.h, -P.l});
+                        s_idem += w * dE.h * dE.h;
+                        s_fro += w * Y.h * Y.h;
+                    }
+                }
+                // float64 output (n x n): row segment and its mirror column
+                if (prm.out64 && i < prm.n) {
+                    for (int c = 0; c < 16; ++c) {
+                        const int j = jb + c;
+                        if (j < prm.n && (!diag_tile || i <= j)) {
+                            const double v = (double)Ov[c].h + (double)Ov[c].l;
+                            prm.out64[(size_t)i * prm.n + j] = v;
+                            if (i != j) prm.out64[(size_t)j * prm.n + i] = v;
+                        }
+                    }
+                }
+                // digit planes of the output (next step's operand)
+                if (prm.out) {
+                    df z[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) z[c] = df_scale(Ov[c], prm.out_digit_scale);
+                    float plane_scale = 1.f;
+                    const float rs = prm.out_rscale, rinv = 1.f / prm.out_rscale;
+                    for (int p = 0; p < prm.s_out; ++p) {
+                        __align__(16) __nv_bfloat16 dv[16];
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            const float d = rintf(z[c].h);
+                            z[c] = df_scale(two_sum(__fsub_rn(z[c].h, d), z[c].l), rs);
+                            dv[c] = __float2bfloat16_rn(d * plane_scale);
+                        }
+                        plane_scale *= rinv;
+                        __nv_bfloat16* dst = prm.out + p * plane;
+                        if (!diag_tile) {
+                            uint4* row = (uint4*)(dst + (size_t)i * prm.n_pad + jb);
+                            row[0] = ((const uint4*)dv)[0];
+                            row[1] = ((const uint4*)dv)[1];
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) dst[(size_t)(jb + c) * prm.n_pad + i] = dv[c];
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) {
+                                const int j = jb + c;
+                                if (i <= j) {
+                                    dst[(size_t)i * prm.n_pad + j] = dv[c];
+                                    if (i != j) dst[(size_t)j * prm.n_pad + i] = dv[c];
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (prm.red) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s_tr += __shfl_xor_sync(0xffffffffu, s_tr, o);
+            s_idem = warp_sum_f(s_idem);
+            s_fro = warp_sum_f(s_fro);
+            if (lane == 0) {
+                atomicAdd(&prm.red[0], s_tr);
+                atomicAdd(&prm.red[1], (double)s_idem);
+                atomicAdd(&prm.red[2], (double)s_fro);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, NUM_ACC * TILE);
+    }
+}
+
+// ---- float64 (with affine) -> digit planes ----------------------------------
+// out = a F + b I for i, j < n, 0 in the padding; split into s planes with
+// the scale 2^e.  F and the coefficients enter in float64; the split runs in
+// double-float.
+__global__ void split_kernel(const double* __restrict__ F, int64_t ldf, int n, int n_pad, double a,
+                             double b, float digit_scale, float rscale, int s,
+                             __nv_bfloat16* __restrict__ out, double* red) {
+    const int64_t total = (int64_t)n_pad * n_pad;
+    float tr = 0.f;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(idx / n_pad), j = (int)(idx - (int64_t)i * n_pad);
+        df z = {0.f, 0.f};
+        if (i < n && j < n) {
+            double x = a * F[(int64_t)i * ldf + j];
+            if (i == j) x += b;
+            const float h = (float)x;
+            z = {h, (float)(x - (double)h)};
+            if (i == j) tr += h + z.l;
+        }
+        z = df_scale(z, digit_scale);
+        float plane_scale = 1.f;
+        for (int p = 0; p < s; ++p) {
+            const float d = rintf(z.h);
+            z = two_sum(__fsub_rn(z.h, d), z.l);
+            out[(size_t)p * total + idx] = __float2bfloat16_rn(d * plane_scale);
+            z = df_scale(z, rscale);
+            plane_scale *= (1.f / rscale);
+        }
+    }
+    if (red) {
+        tr = warp_sum_f(tr);
+        if ((threadIdx.x & 31) == 0) atomicAdd(red, (double)tr);
+    }
+}
+
+// ---- tensor maps --------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)p;
+    });
+    return fn;
+}
+
+// 3D map over planes [s][n_pad][n_pad] bf16, box {32, 128, s}, 64-byte swizzle.
+int make_plane_map(CUtensorMap* map, const __nv_bfloat16* planes, int n_pad, int s) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return PURIFY_ERR_UNSUPPORTED;
+    if (((uintptr_t)planes & 15) || n_pad % TILE) return PURIFY_ERR_INVALID_ARG;
+    cuuint64_t dims[3] = {(cuuint64_t)n_pad, (cuuint64_t)n_pad, (cuuint64_t)s};
+    cuuint64_t strides[2] = {(cuuint64_t)n_pad * 2, (cuuint64_t)n_pad * n_pad * 2};
+    cuuint32_t box[3] = {(cuuint32_t)KC, (cuuint32_t)TILE, (cuuint32_t)s};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)planes, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? PURIFY_OK : PURIFY_ERR_CUDA;
+}
+
+df to_df(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+}  // namespace
+
+int digit_stages(int s) {
+    const int stage_bytes = 2 * s * PLANE_BYTES;
+    int st = (200 * 1024) / stage_bytes;
+    if (st > 4) st = 4;
+    return st;
+}
+
+size_t digit_smem_bytes(int s) {
+    return 1024 + (size_t)digit_stages(s) * 2 * s * PLANE_BYTES + 256;
+}
+
+int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
+    if (st.s_in < 1 || st.s_in > kMaxDigitPlanes || st.s_out < 0 || st.s_out > kMaxDigitPlanes)
+        return PURIFY_ERR_INVALID_ARG;
+    if (st.n <= 0 || st.n_pad % TILE || st.n > st.n_pad) return PURIFY_ERR_INVALID_ARG;
+    if (st.rbits < 4 || st.rbits > 8) return PURIFY_ERR_INVALID_ARG;
+    CUtensorMap ma, mb;
+    PURIFY_TRY(make_plane_map(&ma, st.A, st.n_pad, st.s_in));
+    PURIFY_TRY(make_plane_map(&mb, st.B, st.n_pad, st.s_in));
+    DigitGemmParams p;
+    std::memset(&p, 0, sizeof(p));
+    p.n = st.n;
+    p.n_pad = st.n_pad;
+    p.s_in = st.s_in;
+    p.s_out = st.out ? st.s_out : 0;
+    p.tiles_per_row = st.n_pad / TILE;
+    p.scale_in_h = ldexpf(1.f, st.eA + st.eB - 16);
+    p.e_scale = ldexpf(1.f, st.eA - 8);
+    p.out_digit_scale = ldexpf(1.f, 8 - st.e_out);
+    p.out_rscale = ldexpf(1.f, st.rbits);
+    p.cP = to_df(st.cP);
+    p.cE = to_df(st.cE);
+    p.cI = to_df(st.cI);
+    p.dY = to_df(st.dY);
+    p.dI = to_df(st.dI);
+    p.use_E = st.use_E;
+    p.A = st.A;
+    p.out = st.out;
+    p.out64 = st.out64;
+    p.red = st.red;
+    p.err = st.err;
+    const int stages = digit_stages(st.s_in);
+    const size_t smem = digit_smem_bytes(st.s_in);
+    static bool attr_set = false;
+    if (!attr_set) {
+        PURIFY_CUDA_TRY(cudaFuncSetAttribute(digit_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             227 * 1024));
+        attr_set = true;
+    }
+    const int T = st.n_pad / TILE;
+    const int tiles = T * (T + 1) / 2;
+    digit_gemm_kernel<<<tiles, NTHREADS, smem, stream>>>(ma, mb, p, stages);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return PURIFY_OK;
+}
+
+int launch_split(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s,
+                 int rbits, __nv_bfloat16* out, double* red, cudaStream_t stream) {
+    if (s < 1 || s > kMaxDigitPlanes || n <= 0 || n_pad < n || rbits < 4 || rbits > 8)
+        return PURIFY_ERR_INVALID_ARG;
+    int64_t blocks = ((int64_t)n_pad * n_pad + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    split_kernel<<<(unsigned)blocks, 256, 0, stream>>>(F, ldf, n, n_pad, a, b, ldexpf(1.f, 8 - e),
+                                                        ldexpf(1.f, rbits), s, out, red);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return PURIFY_OK;
+}
+
+}  // namespace purify

@@ -1,0 +1,52 @@
+// Digit-plane tensor-core products (see digits_tc.cu for the representation).
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "internal.h"
+
+namespace purify {
+
+constexpr int kMaxDigitPlanes = 6;
+
+// One fused step: P = A B (A, B symmetric, held as s_in digit planes each,
+// scale exponents eA, eB), Y = cP P + cE E + cI I with E = A when use_E,
+// out = dY Y + dI I written as s_out digit planes with exponent e_out and
+// remainder digits of rbits bits (when `out` is not null) and/or as float64
+// n x n (when `out64` is not null).  red (3 doubles, atomics): trace(Y),
+// ||E - P||_F^2, ||Y||_F^2.
+struct DigitStep {
+    int n = 0, n_pad = 0;
+    const __nv_bfloat16* A = nullptr;
+    const __nv_bfloat16* B = nullptr;
+    int s_in = 0, eA = 0, eB = 0;
+    double cP = 1.0, cE = 0.0, cI = 0.0, dY = 1.0, dI = 0.0;
+    int use_E = 0;
+    __nv_bfloat16* out = nullptr;
+    int s_out = 0, e_out = 0;
+    int rbits = 7;  // bits of the output's remainder digits
+    double* out64 = nullptr;
+    double* red = nullptr;
+    int* err = nullptr;
+};
+
+int launch_digit_step(const DigitStep& st, cudaStream_t stream);
+
+// out planes of a F + b I (i, j < n; zero padding up to n_pad), exponent e,
+// s digits.  red[0] += trace (float accuracy) when red is not null.
+int launch_split(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s,
+                 int rbits, __nv_bfloat16* out, double* red, cudaStream_t stream);
+
+// Bits of the remainder digits for a padded size: 7 up to 4096 (level-2
+// sums of squares stay below 2^24), 6 above.
+inline int remainder_bits(int n_pad) { return n_pad <= 4096 ? 7 : 6; }
+
+// Bits carried by s digits (8 leading + r per remainder digit).
+inline int digit_bits(int s, int rbits) { return 8 + rbits * (s - 1); }
+
+int digit_stages(int s);
+size_t digit_smem_bytes(int s);
+
+inline int pad128(int64_t n) { return (int)((n + 127) / 128 * 128); }
+
+}  // namespace purify

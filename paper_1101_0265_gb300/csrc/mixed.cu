@@ -1,15 +1,324 @@
+// Driver of the mixed path: every matrix product of the scheme runs as a
+// digit-plane product on the tcgen05 tensor cores (digits_tc.cu).
+//
+// Precision per step.  Rounding added at step i in the block that couples
+// occupied and unoccupied states is not damped by later steps: it reaches
+// the result multiplied by about 1 / (beta_bar - beta), the gap between the
+// mapped gap edges at step i (the scalar bounds of Algorithm 1 and
+// Algorithm 2).  The digit count of step i is therefore chosen from that
+// mapped gap g_i: the smallest s in [3, 6] whose digits carry
+// max(30, 26 + log2(1 / g_i)) bits (8 + 7 (s - 1) bits up to n = 4096), so
+// early steps (small g) carry 43 bits and late ones 36.
 #include "mixed.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "digits_tc.h"
 
 namespace purify {
 
 struct MixedState {
-    int dummy;
+    int n_pad_cap = 0;
+    __nv_bfloat16* Xd[2] = {nullptr, nullptr};
+    __nv_bfloat16* Sd = nullptr;
+    int* err = nullptr;
 };
 
-int run_mixed(purify_ctx*, int, double, const Schedule&, int*, std::vector<double>&) {
-    return PURIFY_ERR_UNSUPPORTED;
+void mixed_free(MixedState* ms) {
+    if (!ms) return;
+    cudaFree(ms->Xd[0]);
+    cudaFree(ms->Xd[1]);
+    cudaFree(ms->Sd);
+    cudaFree(ms->err);
+    delete ms;
 }
 
-void mixed_free(MixedState* ms) { delete ms; }
+static int ensure_mixed(purify_ctx* h, int n_pad) {
+    if (!h->mixed) {
+        h->mixed = new (std::nothrow) MixedState();
+        if (!h->mixed) return PURIFY_ERR_OOM;
+        PURIFY_CUDA_TRY(cudaMalloc(&h->mixed->err, sizeof(int)));
+    }
+    MixedState* ms = h->mixed;
+    if (n_pad <= ms->n_pad_cap) return PURIFY_OK;
+    cudaFree(ms->Xd[0]);
+    cudaFree(ms->Xd[1]);
+    cudaFree(ms->Sd);
+    ms->Xd[0] = ms->Xd[1] = ms->Sd = nullptr;
+    ms->n_pad_cap = 0;
+    const size_t bytes = sizeof(__nv_bfloat16) * (size_t)kMaxDigitPlanes * n_pad * n_pad;
+    PURIFY_CUDA_TRY(cudaMalloc(&ms->Xd[0], bytes));
+    PURIFY_CUDA_TRY(cudaMalloc(&ms->Xd[1], bytes));
+    PURIFY_CUDA_TRY(cudaMalloc(&ms->Sd, bytes));
+    ms->n_pad_cap = n_pad;
+    return PURIFY_OK;
+}
+
+// Digits for a step whose mapped gap (distance between the images of the
+// gap edges) is g.
+int digits_for_gap(double g, int fixed, int rbits) {
+    if (fixed > 0) return fixed;
+    if (!(g > 0.0)) return kMaxDigitPlanes;
+    const double need = std::max(30.0, 26.0 + std::log2(1.0 / g));
+    for (int s = 3; s < kMaxDigitPlanes; ++s)
+        if (digit_bits(s, rbits) >= need) return s;
+    return kMaxDigitPlanes;
+}
+
+static double pairs_of(int s) { return 0.5 * s * (s + 1); }
+
+// Algorithm 2 step coefficients: Y = cP X^2 + cE X + cI I.
+static void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
+    if (branch) {
+        *cP = (1.0 + a) * (1.0 + a);
+        *cE = -2.0 * a * (1.0 + a);
+        *cI = a * a;
+    } else {
+        *cP = -(1.0 + a) * (1.0 + a);
+        *cE = 2.0 * (1.0 + a);
+        *cI = 0.0;
+    }
+}
+
+static int product(purify_ctx* h, const DigitStep& st, double flops) {
+    PURIFY_TRY(product_begin(h));
+    PURIFY_TRY(launch_digit_step(st, h->stream));
+    ++h->st.product_launches;
+    h->st.tensor_flops += flops;
+    return product_end(h);
+}
+
+int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
+              std::vector<double>& red) {
+    const int n = (int)h->n;
+    const int n_pad = pad128(n);
+    PURIFY_TRY(ensure_mixed(h, n_pad));
+    MixedState* ms = h->mixed;
+    const bool fixed_mu = scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_FIXED_MU_MONO;
+    const int m = (int)S.alpha.size();
+    const int R = h->opt.refine_squares;
+    const int fixed = h->opt.digits;
+    const int T = n_pad / 128;
+    const int rb = remainder_bits(n_pad);
+    const double tile_flops = 2.0 * 128.0 * 128.0 * (double)n_pad * (double)(T * (T + 1) / 2);
+
+    // digit count of every product step (index m.. are refinement steps)
+    std::vector<int> sd(m + R + 1);
+    for (int i = 0; i < m; ++i) {
+        const double b = i ? S.beta[i - 1] : S.beta0;
+        const double bb = i ? S.betabar[i - 1] : S.betabar0;
+        sd[i] = digits_for_gap(bb - b, fixed, rb);
+    }
+    for (int i = m; i <= m + R; ++i) sd[i] = fixed > 0 ? fixed : kMaxDigitPlanes;
+    int dmax = 0;
+    for (int i = 0; i < m + R; ++i) dmax = sd[i] > dmax ? sd[i] : dmax;
+    h->st.digit_max = dmax;
+
+    const int slots = 2 * (m + R) + 2;
+    PURIFY_TRY(ensure_red(h, 4 * (int64_t)slots));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * slots, h->stream));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), h->stream));
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+
+    const double lmin = h->b.lmin, lmax = h->b.lmax;
+    double c0, c1;  // X_0 = c0 I + c1 F
+    if (fixed_mu) {
+        const double gamma = 2.0 * std::max(lmax - mu, mu - lmin);
+        c0 = mu / gamma + 0.5;
+        c1 = -1.0 / gamma;
+    } else {
+        c0 = lmax / (lmax - lmin);
+        c1 = -1.0 / (lmax - lmin);
+    }
+    double* D = h->X[0];
+    *cur = 0;
+    if (m + R == 0) {
+        PURIFY_TRY(launch_affine_f64(h->F, n, D, n, c1, c0, h->stream));
+    } else if (fixed_mu) {
+        // X_s of the first iteration, e = 1 (eigenvalues in [(1-a)/2, (1+a)/2])
+        const double a1 = m ? S.alpha[0] : 1.0;
+        PURIFY_TRY(launch_split(h->F, n, n, n_pad, a1 * c1, a1 * (c0 - 0.5) + 0.5, 1, sd[0], rb,
+                                ms->Xd[0], nullptr, h->stream));
+        int x = 0;
+        for (int i = 0; i < m + R; ++i) {
+            const int s = sd[i];
+            DigitStep p1;
+            p1.n = n;
+            p1.n_pad = n_pad;
+            p1.rbits = rb;
+            p1.A = p1.B = ms->Xd[x];
+            p1.s_in = s;
+            p1.eA = p1.eB = 1;
+            p1.out = ms->Sd;
+            p1.s_out = s;
+            p1.e_out = 1;
+            p1.red = h->red + 4 * (2 * i);
+            p1.err = ms->err;
+            PURIFY_TRY(product(h, p1, pairs_of(s) * tile_flops));
+            // X_i = 3 S - 2 S X_s, emitted as the next X_s (or as D)
+            DigitStep p2 = p1;
+            p2.A = ms->Sd;
+            p2.B = ms->Xd[x];
+            p2.use_E = 1;
+            p2.cP = -2.0;
+            p2.cE = 3.0;
+            p2.red = h->red + 4 * (2 * i + 1);
+            const bool last = (i + 1 == m + R);
+            if (last) {
+                p2.out = nullptr;
+                p2.s_out = 0;
+                p2.out64 = D;
+            } else {
+                const double an = (i + 1 < m) ? S.alpha[i + 1] : 1.0;
+                p2.dY = an;
+                p2.dI = 0.5 * (1.0 - an);
+                p2.out = ms->Xd[x ^ 1];
+                p2.s_out = sd[i + 1];
+            }
+            PURIFY_TRY(product(h, p2, pairs_of(s) * tile_flops));
+            x ^= 1;
+        }
+    } else {
+        PURIFY_TRY(launch_split(h->F, n, n, n_pad, c1, c0, 0, sd[0], rb, ms->Xd[0], nullptr, h->stream));
+        int x = 0;
+        for (int i = 0; i < m; ++i) {
+            const int s = sd[i];
+            DigitStep st;
+            st.n = n;
+            st.n_pad = n_pad;
+            st.rbits = rb;
+            st.A = st.B = ms->Xd[x];
+            st.s_in = s;
+            st.eA = st.eB = 0;
+            st.use_E = 1;
+            tc_coeffs(S.branch[i], S.alpha[i], &st.cP, &st.cE, &st.cI);
+            st.red = h->red + 4 * (2 * i + 1);
+            st.err = ms->err;
+            const bool last = (i + 1 == m) && R == 0;
+            if (last) {
+                st.out64 = D;
+            } else {
+                st.out = ms->Xd[x ^ 1];
+                st.s_out = sd[i + 1];
+                st.e_out = 0;
+            }
+            PURIFY_TRY(product(h, st, pairs_of(s) * tile_flops));
+            x ^= 1;
+        }
+        // refinement: unscaled McWeeny X <- 3 X^2 - 2 X^3 at the finest digits
+        for (int r = 0; r < R; ++r) {
+            const int i = m + r;
+            const int s = sd[i];
+            DigitStep p1;
+            p1.n = n;
+            p1.n_pad = n_pad;
+            p1.rbits = rb;
+            p1.A = p1.B = ms->Xd[x];
+            p1.s_in = s;
+            p1.eA = p1.eB = 0;
+            p1.out = ms->Sd;
+            p1.s_out = s;
+            p1.e_out = 0;
+            p1.use_E = 1;  // ||X - X^2|| of the iterate
+            p1.cP = 1.0;
+            p1.cE = 0.0;
+            p1.red = h->red + 4 * (2 * i);
+            p1.err = ms->err;
+            PURIFY_TRY(product(h, p1, pairs_of(s) * tile_flops));
+            DigitStep p2 = p1;
+            p2.A = ms->Sd;
+            p2.B = ms->Xd[x];
+            p2.cP = -2.0;
+            p2.cE = 3.0;
+            p2.red = h->red + 4 * (2 * i + 1);
+            if (r + 1 == R) {
+                p2.out = nullptr;
+                p2.s_out = 0;
+                p2.out64 = D;
+            } else {
+                p2.out = ms->Xd[x ^ 1];
+                p2.s_out = sd[i + 1];
+            }
+            PURIFY_TRY(product(h, p2, pairs_of(s) * tile_flops));
+            x ^= 1;
+        }
+    }
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+    red.assign(4 * (size_t)slots, 0.0);
+    int err = 0;
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(red.data(), h->red, sizeof(double) * red.size(),
+                                    cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, ms->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (err) return PURIFY_ERR_DEVICE_TIMEOUT;
+    h->st.refine_multiplications = 2 * R;
+    // statistics: trace of the result; idempotency of the last squared iterate
+    const int last = m + R - 1;
+    if (last >= 0) {
+        h->st.trace = red[4 * (size_t)(2 * last + 1)];
+        if (!fixed_mu && R == 0) {
+            h->st.idem_err_fro = std::sqrt(std::max(red[4 * (size_t)(2 * last + 1) + 1], 0.0));
+        } else if (R > 0) {
+            h->st.idem_err_fro = std::sqrt(std::max(red[4 * (size_t)(2 * last) + 1], 0.0));
+        } else {
+            h->st.idem_err_fro = NAN;
+        }
+    } else {
+        h->st.trace = NAN;
+        h->st.idem_err_fro = NAN;
+    }
+    return PURIFY_OK;
+}
 
 }  // namespace purify
+
+using namespace purify;
+
+extern "C" int purify_k_digit_product_f64(const double* A, const double* B, double* C, int64_t n,
+                                          int digits, int eA, int eB, void* stream) {
+    if (!A || !B || !C || n <= 0 || n > (int64_t)1 << 15) return PURIFY_ERR_INVALID_ARG;
+    if (digits < 1 || digits > kMaxDigitPlanes || eA < -8 || eA > 8 || eB < -8 || eB > 8)
+        return PURIFY_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n_pad = pad128(n);
+    const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)digits * n_pad * n_pad;
+    __nv_bfloat16 *pa = nullptr, *pb = nullptr;
+    int* err = nullptr;
+    int r = PURIFY_OK;
+    if (cudaMalloc(&pa, plane_bytes) != cudaSuccess || cudaMalloc(&pb, plane_bytes) != cudaSuccess ||
+        cudaMalloc(&err, sizeof(int)) != cudaSuccess)
+        r = PURIFY_ERR_OOM;
+    if (r == PURIFY_OK && cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) r = PURIFY_ERR_CUDA;
+    const int rb = remainder_bits(n_pad);
+    if (r == PURIFY_OK) r = launch_split(A, n, (int)n, n_pad, 1.0, 0.0, eA, digits, rb, pa, nullptr, s);
+    if (r == PURIFY_OK) r = launch_split(B, n, (int)n, n_pad, 1.0, 0.0, eB, digits, rb, pb, nullptr, s);
+    if (r == PURIFY_OK) {
+        DigitStep st;
+        st.n = (int)n;
+        st.n_pad = n_pad;
+        st.A = pa;
+        st.B = pb;
+        st.s_in = digits;
+        st.eA = eA;
+        st.eB = eB;
+        st.out64 = C;
+        st.err = err;
+        r = launch_digit_step(st, s);
+    }
+    int herr = 0;
+    if (r == PURIFY_OK) {
+        cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) r = cuda_status(e, "digit product");
+    } else {
+        cudaStreamSynchronize(s);
+    }
+    cudaFree(pa);
+    cudaFree(pb);
+    cudaFree(err);
+    if (r == PURIFY_OK && herr) r = PURIFY_ERR_DEVICE_TIMEOUT;
+    return r;
+}

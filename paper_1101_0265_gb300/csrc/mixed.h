@@ -8,7 +8,7 @@
 namespace purify {
 
 struct MixedState;
-constexpr int kMaxDigits = 7;
+constexpr int kMaxDigits = 6;  // equals kMaxDigitPlanes (digits_tc.h)
 
 // Run the scheme's coefficient schedule with every matrix product on the
 // tcgen05 tensor cores (see mixed.cu).  Sets *cur (index into h->X of the

@@ -1,0 +1,147 @@
+"""GPU tests of the mixed path: digit-plane products on the tcgen05 tensor
+cores, and whole purifications against the CPU oracle."""
+import numpy as np
+import pytest
+
+from oracle import purify_oracle as O
+from paper_1101_0265_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1101_0265_gb300 import build
+    build.build()
+    import paper_1101_0265_gb300 as P
+    return P
+
+
+def _cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _sym_int(n, lim, rng):
+    A = rng.integers(-lim, lim + 1, size=(n, n)).astype(np.float64)
+    return np.triu(A) + np.triu(A, 1).T
+
+
+@pytest.mark.parametrize("n", [128, 200, 256, 383])
+def test_one_digit_products_are_exact(P, n):
+    # X = 2^(e-8) d with integer d: one digit, level 0 only; the tensor-core
+    # sum of integer products must be exact
+    rng = np.random.default_rng(n)
+    for e in (0, 1):
+        dA = _sym_int(n, 48, rng)
+        dB = _sym_int(n, 48, rng)
+        A = dA * 2.0 ** (e - 8)
+        B = dB * 2.0 ** (e - 8)
+        out = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        P.k_digit_product_f64(_cuda(A), _cuda(B), out, 1, e, e)
+        got = out.cpu().numpy()
+        ref = A @ B.T           # upper triangle of A B^T, mirrored
+        iu = np.triu_indices(n)
+        assert np.array_equal(got[iu], ref[iu])
+        assert np.array_equal(got, got.T)
+
+
+@pytest.mark.parametrize("n", [130, 256])
+def test_two_digit_inputs_three_digit_product_exact(P, n):
+    # inputs with exactly two digits; with three product digits every nonzero
+    # digit pair is kept and every level is exact
+    # (leading digit 8 bits, remainder digits 7 bits up to n = 4096)
+    rng = np.random.default_rng(7 + n)
+    d0 = _sym_int(n, 40, rng)
+    d1 = _sym_int(n, 60, rng)
+    A = d0 * 2.0 ** -8 + d1 * 2.0 ** -15
+    out = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    P.k_digit_product_f64(_cuda(A), _cuda(A), out, 3, 0, 0)
+    ref = A @ A
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("n,s", [(256, 3), (256, 4), (500, 5), (1024, 6), (129, 6)])
+def test_digit_product_accuracy(P, n, s):
+    # a density-like operand: X = Q diag(x) Q^T with x in [0, 1]
+    h = I.dense_hamiltonian(n, n // 2, 0.1, config=70, instance=n)
+    X = (h.lmax * np.eye(n) - h.F) / (h.lmax - h.lmin)
+    out = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    P.k_digit_product_f64(_cuda(X), _cuda(X), out, s, 0, 0)
+    err = np.max(np.abs(out.cpu().numpy() - X @ X))
+    # truncation of the digits: s digits carry 8 + 7 (s - 1) bits below 2^0;
+    # the kept pairs reproduce the product to about sqrt(n) 2^-bits
+    bits = 8 + 7 * (s - 1)
+    assert err <= np.sqrt(n) * 2.0 ** (-bits + 3), err
+
+
+@pytest.mark.parametrize("scheme", O.SCHEMES)
+def test_mixed_purify_parity_n256(P, scheme):
+    h = I.dense_hamiltonian(256, 128, 0.1, config=1)
+    pur = P.Purifier(precision="mixed")
+    pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo,
+                        lumo=h.lumo)
+    code = pur.run(scheme, 1e-12, 200)
+    D = pur.density()
+    st = pur.stats()
+    Do, r = O.purify(h.F, scheme, h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=1e-12)
+    assert code == P.OK
+    assert st["iterations"] == r.iterations
+    err = np.max(np.abs(D - Do))
+    assert err <= 5e-8, err
+    assert st["trace_err"] < 1e-6
+    assert st["digit_max"] >= 4
+    assert st["tensor_flops"] > 0
+
+
+@pytest.mark.parametrize("n,nocc,gap", [(100, 3, 0.3), (333, 200, 0.02), (129, 64, 0.001),
+                                        (65, 64, 0.1), (700, 350, 1e-4)])
+@pytest.mark.parametrize("scheme", ["FIXED_MU_SF", "TC_SF", "TC_MONO"])
+def test_mixed_purify_parity_ragged(P, n, nocc, gap, scheme):
+    h = I.dense_hamiltonian(n, nocc, gap, config=71, instance=n)
+    pur = P.Purifier(precision="mixed")
+    pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo,
+                        lumo=h.lumo)
+    assert pur.run(scheme, 1e-12, 300) == P.OK
+    D = pur.density()
+    Do, r = O.purify(h.F, scheme, h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=1e-12)
+    assert np.max(np.abs(D - Do)) <= 3e-7
+
+
+def test_mixed_refine_and_fixed_digits(P):
+    h = I.dense_hamiltonian(300, 120, 0.05, config=72)
+    Do, _ = O.purify(h.F, "TC_SF", h.lmin, h.lmax, homo=h.homo, lumo=h.lumo, tol=1e-12)
+    for kw in ({"digits": 6}, {"refine_squares": 1}, {"digits": 5, "refine_squares": 2}):
+        pur = P.Purifier(precision="mixed", **kw)
+        pur.set_hamiltonian(h.F, nocc=h.nocc, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+        pur.run("TC_SF", 1e-12)
+        st = pur.stats()
+        assert st["refine_multiplications"] == 2 * kw.get("refine_squares", 0)
+        assert np.max(np.abs(pur.density() - Do)) <= 1e-8
+    # too few digits (15 bits) is visibly worse, but still near the right trace
+    pur = P.Purifier(precision="mixed", digits=2)
+    pur.set_hamiltonian(h.F, nocc=h.nocc, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+    pur.run("TC_SF", 1e-12)
+    assert np.max(np.abs(pur.density() - Do)) > 1e-6
+    assert abs(pur.stats()["trace"] - h.nocc) < 0.1
+
+
+@pytest.mark.parametrize("gap", [1e-2, 1e-4])
+def test_mixed_full_size_vs_fp64(P, gap):
+    # the workload of the throughput benchmark: n = 4096, max error vs the
+    # float64 GPU path at the same schedule must stay below 1e-6
+    h = I.dense_hamiltonian(4096, 2048, gap, config=2)
+    F = _cuda(h.F)
+    out = []
+    for precision in ("mixed", "fp64"):
+        pur = P.Purifier(precision=precision)
+        pur.set_hamiltonian(F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo,
+                            lumo=h.lumo)
+        assert pur.run("TC_SF", 1e-9, 200) == P.OK
+        D = torch.empty((4096, 4096), dtype=torch.float64, device="cuda")
+        pur.density(D)
+        out.append(D)
+        pur.close()
+    err = float((out[0] - out[1]).abs().max())
+    assert err <= 1e-6, err
