@@ -26,12 +26,16 @@
 // Exact symmetry matters: antisymmetric rounding errors are not damped by
 // the purification maps.
 //
-// Structure of one CTA (one 128 x 128 output tile, 192 threads):
-//   warp 0  TMA producer: per 32-wide k-chunk one 3D TMA load of all s
-//           planes of the A row panel and one of the B row panel
+// Structure of one CTA (one 128 x 128 output tile, 320 threads):
+//   warp 0  TMA producer: per k-chunk (16, 32 or 64 wide, with a swizzle of
+//           the chunk's row width) one 3D TMA load of all s planes of the A
+//           row panel and one of the B row panel
 //   warp 1  TMEM allocator and MMA issuer (tcgen05.mma kind::f16, bf16 in,
 //           fp32 accumulate, M = N = 128, K = 16)
-//   warps 2-5 epilogue (tcgen05.ld, one TMEM lane quarter each)
+//   warps 2-9 epilogue (tcgen05.ld; warp w reads TMEM lane quarter w % 4 and
+//           one half of the tile's columns)
+// Tiles are numbered in bands of 12 tile columns so that the CTAs resident
+// at one time share row panels in L2.
 // Every wait on an mbarrier is bounded; on time-out the CTA records an error
 // flag, waits (bounded) for its own copies and MMAs, frees its tensor memory
 // and exits.
@@ -42,19 +46,22 @@
 #include <cuda_bf16.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <vector>
 
 namespace purify {
 
 namespace {
 
 constexpr int TILE = 128;        // output tile edge
-constexpr int KC = 32;           // k-chunk (bf16 elements) = 64 bytes: SWIZZLE_64B
-constexpr int PLANE_BYTES = TILE * KC * 2;   // one plane of one operand per stage: 8 KB
+constexpr int BAND = 12;         // tile columns per rasterisation band
+constexpr int MAX_STAGES = 8;
 constexpr int NUM_ACC = 4;       // tensor-memory accumulators (levels 0, 1, 2, >= 3)
-constexpr int NTHREADS = 192;
-constexpr long long WAIT_CYCLES = 1ll << 31;  // ~1 s at 2 GHz
+constexpr int NTHREADS = 320;
+constexpr int EPI_WARPS = 8;
+constexpr long long WAIT_CYCLES = 1ll << 31;  // one wait gives up after ~1 s at 2 GHz
 
 // ---- PTX wrappers ------------------------------------------------------------
 
@@ -84,14 +91,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0;
-}
-
-// Bounded wait: false when the deadline passes first.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long deadline) {
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() > deadline) return false;
-    }
-    return true;
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
@@ -154,14 +153,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // Shared-memory matrix descriptor for a K-major operand tile written by TMA
-// with 64-byte swizzle: rows of 64 bytes, 8-row groups 512 bytes apart.
-__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
+// with a swizzle as wide as its rows (KC bf16 = 2 KC bytes: 32, 64 or 128):
+// 8-row groups 16 KC bytes apart; one K = 16 step advances 32 bytes.
+template <int KC>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    constexpr uint64_t layout = KC == 16 ? 6 : (KC == 32 ? 4 : 2);  // 32B / 64B / 128B swizzle
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
     d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
-    d |= (uint64_t)(512 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)((16 * KC) >> 4) << 32;           // stride byte offset
     d |= (uint64_t)1 << 46;                          // descriptor version (tcgen05)
-    d |= (uint64_t)4 << 61;                          // 64-byte swizzle
+    d |= layout << 61;
     return d;
 }
 
@@ -222,6 +224,8 @@ struct DigitGemmParams {
     float out_rscale;        // 2^r of the output's remainder digits
     df cP, cE, cI, dY, dI;   // Y = cP P + cE E + cI I;  out = dY Y + dI I
     int use_E;               // E = A (the matrix in the A operand)
+    int affine_out;          // (dY, dI) != (1, 0)
+    float2* scratch;         // per CTA 128 x 128 double-float tile
     const __nv_bfloat16* A;  // A's planes (for E), [s_in][n_pad][n_pad]
     __nv_bfloat16* out;      // output planes [s_out][n_pad][n_pad] (may be null)
     double* out64;           // float64 output n x n (leading dimension n) or null
@@ -229,12 +233,28 @@ struct DigitGemmParams {
     int* err;                // device error flag
 };
 
-__device__ __forceinline__ void decode_upper(int t, int& ti, int& tj) {
-    int j = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
-    while ((j + 1) * (j + 2) / 2 <= t) ++j;
-    while (j * (j + 1) / 2 > t) --j;
-    tj = j;
-    ti = t - j * (j + 1) / 2;
+// Tile t of the upper triangle (ti <= tj) of a T x T tile grid, in bands of
+// BAND tile columns; inside a band row by row.
+__device__ __forceinline__ void decode_banded(int t, int T, int& ti, int& tj) {
+    int b0 = 0;
+    for (;;) {
+        const int b1 = min(T, b0 + BAND);
+        const int cnt = (b1 * (b1 + 1) - b0 * (b0 + 1)) / 2;
+        if (t < cnt || b1 == T) {
+            for (int r = 0;; ++r) {
+                const int first = max(b0, r);
+                const int c = b1 - first;
+                if (t < c) {
+                    ti = r;
+                    tj = first + t;
+                    return;
+                }
+                t -= c;
+            }
+        }
+        t -= cnt;
+        b0 = b1;
+    }
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -243,27 +263,49 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
+// Bounded wait measured from its own start: false when it gives up.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
+    return true;
+}
+
+// Persistent CTA: tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The four
+// accumulators of a tile are drained into a double-float tile in the CTA's
+// scratch (global, 128 x 128 x 8 bytes) so that tensor memory is released
+// before the polynomial, the re-split and the stores; those overlap the
+// next tile's MMAs.
+template <int KC, int S>
 __global__ void __launch_bounds__(NTHREADS, 1)
 digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                  const DigitGemmParams prm, int stages) {
+                  const DigitGemmParams prm, int stages, int num_tiles) {
+    constexpr int PLANE_BYTES = TILE * KC * 2;  // one plane of one operand per stage
+    constexpr int s = S;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned operand area: stages x (A planes | B planes)
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const int s = prm.s_in;
-    const int stage_bytes = 2 * s * PLANE_BYTES;
+    constexpr int stage_bytes = 2 * S * PLANE_BYTES;
     uint64_t* bars = (uint64_t*)(base + (size_t)stages * stage_bytes);
-    // bars[0..stages): full, bars[stages..2 stages): empty, bars[2 stages]: accumulators ready
-    uint32_t* tmem_slot = (uint32_t*)(bars + 2 * stages + 1);
+    // bars: full[stages] | empty[stages] | tmem_full | tmem_empty | drain
+    uint64_t* full_bar = bars;
+    uint64_t* empty_bar = bars + stages;
+    uint64_t* tmem_full = bars + 2 * stages;
+    uint64_t* tmem_empty = tmem_full + 1;
+    uint64_t* drain = tmem_full + 2;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    int ti, tj;
-    decode_upper(blockIdx.x, ti, tj);
     const int nk = prm.n_pad / KC;
-    const long long deadline = clock64() + WAIT_CYCLES;
+    const int T = prm.tiles_per_row;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2 * stages + 1; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        for (int i = 0; i < 2 * stages; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        mbar_init(smem_u32(tmem_full), 1);
+        mbar_init(smem_u32(tmem_empty), EPI_WARPS);
+        mbar_init(smem_u32(drain), 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -275,86 +317,107 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
 
     if (warp == 0) {
         if (lane == 0) {
-            // producer
-            int issued = 0;
-            for (int kc = 0; kc < nk; ++kc) {
-                const int st = kc % stages;
-                const uint32_t ph = (uint32_t)((kc / stages) & 1);
-                if (kc >= stages && !mbar_wait(smem_u32(&bars[stages + st]), ph ^ 1, deadline)) {
-                    atomicExch(prm.err, 1);
-                    *abort_flag = 1;
-                    break;
+            // producer: one continuous ring of k-chunks over all tiles
+            int it = 0;
+            for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x) {
+                int ti, tj;
+                decode_banded(t, T, ti, tj);
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int st = it % stages;
+                    if (it >= stages && !mbar_wait_for(smem_u32(&empty_bar[st]), (uint32_t)(((it / stages) & 1) ^ 1))) {
+                        atomicExch(prm.err, 1);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    const uint32_t fb = smem_u32(&full_bar[st]);
+                    uint8_t* sa = base + (size_t)st * stage_bytes;
+                    mbar_arrive_expect_tx(fb, (uint32_t)stage_bytes);
+                    tma_load_3d(smem_u32(sa), &mapA, fb, kc * KC, ti * TILE, 0);
+                    tma_load_3d(smem_u32(sa + s * PLANE_BYTES), &mapB, fb, kc * KC, tj * TILE, 0);
                 }
-                if (*abort_flag) break;
-                const uint32_t full = smem_u32(&bars[st]);
-                uint8_t* sa = base + (size_t)st * stage_bytes;
-                mbar_arrive_expect_tx(full, (uint32_t)stage_bytes);
-                tma_load_3d(smem_u32(sa), &mapA, full, kc * KC, ti * TILE, 0);
-                tma_load_3d(smem_u32(sa + s * PLANE_BYTES), &mapB, full, kc * KC, tj * TILE, 0);
-                ++issued;
             }
-            // wait (bounded) for the copies this thread issued
-            for (int kc = (issued > stages ? issued - stages : 0); kc < issued; ++kc)
-                mbar_wait(smem_u32(&bars[kc % stages]), (uint32_t)((kc / stages) & 1), deadline + WAIT_CYCLES);
+            // wait (bounded) for the copies still in flight
+            for (int k = (it > stages ? it - stages : 0); k < it; ++k)
+                mbar_wait_for(smem_u32(&full_bar[k % stages]), (uint32_t)((k / stages) & 1));
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            // MMA issuer
-            uint32_t started = 0;  // bit a: accumulator a has been written
+            // MMA issuer.  Descriptors are one base plus compile-time offsets
+            // (the start address sits in the low 14 bits and never carries).
+            const uint64_t desc_base = smem_desc<KC>(smem_u32(base));
+            int it = 0, lt = 0;
             bool ok = true;
-            for (int kc = 0; kc < nk; ++kc) {
-                const int st = kc % stages;
-                const uint32_t ph = (uint32_t)((kc / stages) & 1);
-                if (!mbar_wait(smem_u32(&bars[st]), ph, deadline) || *abort_flag) {
-                    atomicExch(prm.err, 2);
-                    *abort_flag = 1;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++lt) {
+                if (lt > 0 && !mbar_wait_for(smem_u32(tmem_empty), (uint32_t)((lt - 1) & 1))) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t sa = smem_u32(base + (size_t)st * stage_bytes);
-                const uint32_t sb = sa + s * PLANE_BYTES;
-                for (int p = 0; p < s; ++p) {
-                    for (int q = 0; p + q < s; ++q) {
-                        const int a = (p + q < NUM_ACC - 1) ? p + q : NUM_ACC - 1;
-                        const uint32_t d = tmem + (uint32_t)(a * TILE);
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int st = it % stages;
+                    if (!mbar_wait_for(smem_u32(&full_bar[st]), (uint32_t)((it / stages) & 1)) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t da = desc_base + (uint64_t)((st * stage_bytes) >> 4);
+                    const uint64_t db = da + (uint64_t)((S * PLANE_BYTES) >> 4);
+                    const uint32_t later = kc > 0 ? 1u : 0u;
 #pragma unroll
-                        for (int kk = 0; kk < KC / 16; ++kk) {
-                            const uint64_t ad = smem_desc_sw64(sa + p * PLANE_BYTES + kk * 32);
-                            const uint64_t bd = smem_desc_sw64(sb + q * PLANE_BYTES + kk * 32);
-                            mma_bf16(d, ad, bd, IDESC, (started >> a) & 1u);
-                            started |= 1u << a;
+                    for (int p = 0; p < S; ++p) {
+#pragma unroll
+                        for (int q = 0; q < S - p; ++q) {
+                            const int a = (p + q < NUM_ACC - 1) ? p + q : NUM_ACC - 1;
+#pragma unroll
+                            for (int kk = 0; kk < KC / 16; ++kk) {
+                                // the first write of accumulator a in a tile is pair
+                                // (0, a) at k = 0; all later ones accumulate
+                                const uint32_t acc_in = (kk > 0 || p > 0 || q > NUM_ACC - 1) ? 1u : later;
+                                mma_bf16(tmem + (uint32_t)(a * TILE),
+                                         da + (uint64_t)((p * PLANE_BYTES + kk * 32) >> 4),
+                                         db + (uint64_t)((q * PLANE_BYTES + kk * 32) >> 4), IDESC, acc_in);
+                            }
                         }
                     }
+                    mma_commit(smem_u32(&empty_bar[st]));
                 }
-                mma_commit(smem_u32(&bars[stages + st]));
+                if (!ok) break;
+                mma_commit(smem_u32(tmem_full));
             }
-            // zero-fill accumulators that no pair reached (s < 4)
-            mma_commit(smem_u32(&bars[2 * stages]));
-            if (!ok) mbar_wait(smem_u32(&bars[2 * stages]), 0, deadline + WAIT_CYCLES);
-            (void)started;
+            if (!ok) {
+                atomicExch(prm.err, 2);
+                *abort_flag = 1;
+            }
+            // every MMA this thread issued has completed before teardown
+            mma_commit(smem_u32(drain));
+            mbar_wait_for(smem_u32(drain), 0);
         }
     } else {
-        // epilogue warps 2..5: lane quarter q = warp % 4
+        // epilogue warps 2..9: lane quarter warp % 4, column half (warp - 2) / 4
         const int quarter = warp & 3;
-        bool ready = mbar_wait(smem_u32(&bars[2 * stages]), 0, deadline + WAIT_CYCLES);
-        if (!ready) {
-            atomicExch(prm.err, 3);
-            *abort_flag = 1;
-        }
-        // tcgen05.ld is warp-collective: decide once per warp
-        ready = __all_sync(0xffffffffu, ready && !*abort_flag);
-        tc_fence_after();
+        const int col0 = ((warp - 2) >> 2) * (TILE / 2);
         const int row_in_tile = quarter * 32 + lane;
-        const int i = ti * TILE + row_in_tile;
-        const bool diag_tile = (ti == tj);
-        const int nacc = s < NUM_ACC ? s : NUM_ACC;
+        const size_t plane = (size_t)prm.n_pad * prm.n_pad;
+        float2* scr = prm.scratch + ((size_t)blockIdx.x * TILE + row_in_tile) * TILE;
         double s_tr = 0.0;  // the trace decides the occupation check: float64
         float s_idem = 0.f, s_fro = 0.f;
-        if (ready) {
-            const size_t plane = (size_t)prm.n_pad * prm.n_pad;
-            for (int c0 = 0; c0 < TILE; c0 += 16) {
-                const int jb = tj * TILE + c0;
+        int lt = 0;
+        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++lt) {
+            int ti, tj;
+            decode_banded(t, T, ti, tj);
+            bool ready = mbar_wait_for(smem_u32(tmem_full), (uint32_t)(lt & 1));
+            if (!ready) {
+                atomicExch(prm.err, 3);
+                *abort_flag = 1;
+            }
+            // tcgen05.ld is warp-collective: decide once per warp
+            ready = __all_sync(0xffffffffu, ready && !*abort_flag);
+            if (!ready) break;
+            tc_fence_after();
+            // phase 1: accumulators -> double-float P in scratch; release TMEM
+            const int nacc = s < NUM_ACC ? s : NUM_ACC;
+            for (int c0 = col0; c0 < col0 + TILE / 2; c0 += 16) {
                 float acc[NUM_ACC][16];
 #pragma unroll
                 for (int a = 0; a < NUM_ACC; ++a) {
@@ -365,44 +428,77 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                         for (int c = 0; c < 16; ++c) acc[a][c] = 0.f;
                     }
                 }
-                // E = A at (i, jb .. jb + 15), summed from its digit planes
-                df Ev[16];
+                float4* dst = (float4*)(scr + c0);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) Ev[c] = {0.f, 0.f};
-                if (prm.use_E) {
-                    for (int p = 0; p < s; ++p) {
-                        const __nv_bfloat16* src = prm.A + p * plane + (size_t)i * prm.n_pad + jb;
-                        uint4 u[2];
-                        u[0] = *(const uint4*)src;
-                        u[1] = *(const uint4*)(src + 8);
-                        const __nv_bfloat16* hv = (const __nv_bfloat16*)u;
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) Ev[c] = df_add_f(Ev[c], __bfloat162float(hv[c]));
-                    }
+                for (int c = 0; c < 16; c += 2) {
+                    df P0 = two_sum(acc[0][c], acc[1][c]);
+                    P0 = df_add_f(P0, acc[2][c]);
+                    P0 = df_add_f(P0, acc[3][c]);
+                    df P1 = two_sum(acc[0][c + 1], acc[1][c + 1]);
+                    P1 = df_add_f(P1, acc[2][c + 1]);
+                    P1 = df_add_f(P1, acc[3][c + 1]);
+                    dst[c / 2] = make_float4(P0.h, P0.l, P1.h, P1.l);
                 }
-                // O = dY (cP P + cE E + cI I) + dI I, zero outside n x n
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_empty)) : "memory");
+
+            // phase 2: polynomial, outputs, reductions
+            const int i = ti * TILE + row_in_tile;
+            const bool diag_tile = (ti == tj);
+            for (int c0 = col0; c0 < col0 + TILE / 2; c0 += 16) {
+                const int jb = tj * TILE + c0;
                 df Ov[16];
+                {
+                    float4 pv[8];
+                    const float4* src = (const float4*)(scr + c0);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const int j = jb + c;
-                    df P = two_sum(acc[0][c], acc[1][c]);
-                    P = df_add_f(P, acc[2][c]);
-                    P = df_add_f(P, acc[3][c]);
-                    P = df_scale(P, prm.scale_in_h);
-                    const df E = df_scale(Ev[c], prm.e_scale);
-                    df Y = df_add(df_mul(prm.cP, P), df_mul(prm.cE, E));
-                    if (i == j) Y = df_add(Y, prm.cI);
-                    df O = df_mul(prm.dY, Y);
-                    if (i == j) O = df_add(O, prm.dI);
-                    const bool valid = i < prm.n && j < prm.n;
-                    if (!valid) O = {0.f, 0.f};
-                    Ov[c] = O;
-                    if (valid && (!diag_tile || i <= j)) {
-                        const float w = (i == j) ? 1.f : 2.f;
-                        if (i == j) s_tr += (double)Y.h + (double)Y.l;
-                        const df dE = df_add(E, {-P.h, -P.l});
-                        s_idem += w * dE.h * dE.h;
-                        s_fro += w * Y.h * Y.h;
+                    for (int c = 0; c < 8; ++c) pv[c] = src[c];
+                    // E = A at (i, jb .. jb + 15): exact two-float sum of its digits
+                    float eh[16], el[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) eh[c] = el[c] = 0.f;
+                    if (prm.use_E) {
+                        for (int p = 0; p < s; ++p) {
+                            const __nv_bfloat16* srcd = prm.A + p * plane + (size_t)i * prm.n_pad + jb;
+                            uint4 u[2];
+                            u[0] = *(const uint4*)srcd;
+                            u[1] = *(const uint4*)(srcd + 8);
+                            const __nv_bfloat16* hv = (const __nv_bfloat16*)u;
+                            if (p < 3) {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) eh[c] += __bfloat162float(hv[c]);
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) el[c] += __bfloat162float(hv[c]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const int j = jb + c;
+                        const float4 q4 = pv[c >> 1];
+                        const df P = df_scale((c & 1) ? df{q4.z, q4.w} : df{q4.x, q4.y}, prm.scale_in_h);
+                        const df E = df_scale(fast_two_sum(eh[c], el[c]), prm.e_scale);
+                        df Y = df_mul(prm.cP, P);
+                        if (prm.use_E) Y = df_add(Y, df_mul(prm.cE, E));
+                        if (i == j) Y = df_add(Y, prm.cI);
+                        df O = Y;
+                        if (prm.affine_out) {
+                            O = df_mul(prm.dY, Y);
+                            if (i == j) O = df_add(O, prm.dI);
+                        }
+                        const bool valid = i < prm.n && j < prm.n;
+                        if (!valid) O = {0.f, 0.f};
+                        Ov[c] = O;
+                        if (prm.red && valid && (!diag_tile || i <= j)) {
+                            const float w = (i == j) ? 1.f : 2.f;
+                            if (i == j) s_tr += (double)Y.h + (double)Y.l;
+                            const df dE = df_add(E, {-P.h, -P.l});
+                            s_idem += w * dE.h * dE.h;
+                            s_fro += w * Y.h * Y.h;
+                        }
                     }
                 }
                 // float64 output (n x n): row segment and its mirror column
@@ -427,8 +523,10 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                         __align__(16) __nv_bfloat16 dv[16];
 #pragma unroll
                         for (int c = 0; c < 16; ++c) {
+                            // z.h - d is exact; |z.l| <= ulp(z.h) / 2, so the
+                            // fast two-sum renormalises exactly
                             const float d = rintf(z[c].h);
-                            z[c] = df_scale(two_sum(__fsub_rn(z[c].h, d), z[c].l), rs);
+                            z[c] = df_scale(fast_two_sum(__fsub_rn(z[c].h, d), z[c].l), rs);
                             dv[c] = __float2bfloat16_rn(d * plane_scale);
                         }
                         plane_scale *= rinv;
@@ -530,17 +628,20 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 3D map over planes [s][n_pad][n_pad] bf16, box {32, 128, s}, 64-byte swizzle.
-int make_plane_map(CUtensorMap* map, const __nv_bfloat16* planes, int n_pad, int s) {
+// 3D map over planes [s][n_pad][n_pad] bf16, box {kc, 128, s}, with a
+// swizzle of 2 kc bytes.
+int make_plane_map(CUtensorMap* map, const __nv_bfloat16* planes, int n_pad, int s, int kc) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return PURIFY_ERR_UNSUPPORTED;
     if (((uintptr_t)planes & 15) || n_pad % TILE) return PURIFY_ERR_INVALID_ARG;
     cuuint64_t dims[3] = {(cuuint64_t)n_pad, (cuuint64_t)n_pad, (cuuint64_t)s};
     cuuint64_t strides[2] = {(cuuint64_t)n_pad * 2, (cuuint64_t)n_pad * n_pad * 2};
-    cuuint32_t box[3] = {(cuuint32_t)KC, (cuuint32_t)TILE, (cuuint32_t)s};
+    cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)TILE, (cuuint32_t)s};
+    const CUtensorMapSwizzle sw = kc == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                 : (kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)planes, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? PURIFY_OK : PURIFY_ERR_CUDA;
 }
@@ -552,15 +653,59 @@ df to_df(double x) {
 
 }  // namespace
 
-int digit_stages(int s) {
-    const int stage_bytes = 2 * s * PLANE_BYTES;
+// k-chunk width for a digit count: the widest chunk that still leaves at
+// least two pipeline stages, unless overridden (tuning).
+int digit_kc(int s) {
+    static int forced = -1;
+    if (forced < 0) {
+        const char* e = getenv("PURIFY_DIGIT_KC");
+        forced = e ? atoi(e) : 0;
+        if (forced != 32 && forced != 64) forced = 0;
+    }
+    if (forced) return forced;
+    return s <= 3 ? 64 : 32;
+}
+
+int digit_stages(int s, int kc) {
+    const int stage_bytes = 2 * s * TILE * kc * 2;
     int st = (200 * 1024) / stage_bytes;
-    if (st > 4) st = 4;
+    if (st > MAX_STAGES) st = MAX_STAGES;
     return st;
 }
 
-size_t digit_smem_bytes(int s) {
-    return 1024 + (size_t)digit_stages(s) * 2 * s * PLANE_BYTES + 256;
+size_t digit_smem_bytes(int s, int kc) {
+    return 1024 + (size_t)digit_stages(s, kc) * 2 * s * TILE * kc * 2 + 512;
+}
+
+typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const DigitGemmParams, int, int);
+
+template <int KC>
+KernelFn kernel_for_s(int s) {
+    switch (s) {
+        case 1: return digit_gemm_kernel<KC, 1>;
+        case 2: return digit_gemm_kernel<KC, 2>;
+        case 3: return digit_gemm_kernel<KC, 3>;
+        case 4: return digit_gemm_kernel<KC, 4>;
+        case 5: return digit_gemm_kernel<KC, 5>;
+        case 6: return digit_gemm_kernel<KC, 6>;
+        default: return nullptr;
+    }
+}
+
+KernelFn kernel_for(int kc, int s) {
+    return kc == 64 ? kernel_for_s<64>(s) : (kc == 32 ? kernel_for_s<32>(s) : nullptr);
+}
+
+// Opt every instantiation into the full 227 KB of shared memory (once).
+int prepare_kernel(KernelFn fn) {
+    static std::mutex mu;
+    static std::vector<KernelFn> done;
+    std::lock_guard<std::mutex> g(mu);
+    for (KernelFn f : done)
+        if (f == fn) return PURIFY_OK;
+    PURIFY_CUDA_TRY(cudaFuncSetAttribute((const void*)fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    done.push_back(fn);
+    return PURIFY_OK;
 }
 
 int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
@@ -568,9 +713,11 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
         return PURIFY_ERR_INVALID_ARG;
     if (st.n <= 0 || st.n_pad % TILE || st.n > st.n_pad) return PURIFY_ERR_INVALID_ARG;
     if (st.rbits < 4 || st.rbits > 8) return PURIFY_ERR_INVALID_ARG;
+    const int kc = digit_kc(st.s_in);
+    if (digit_stages(st.s_in, kc) < 1) return PURIFY_ERR_INVALID_ARG;
     CUtensorMap ma, mb;
-    PURIFY_TRY(make_plane_map(&ma, st.A, st.n_pad, st.s_in));
-    PURIFY_TRY(make_plane_map(&mb, st.B, st.n_pad, st.s_in));
+    PURIFY_TRY(make_plane_map(&ma, st.A, st.n_pad, st.s_in, kc));
+    PURIFY_TRY(make_plane_map(&mb, st.B, st.n_pad, st.s_in, kc));
     DigitGemmParams p;
     std::memset(&p, 0, sizeof(p));
     p.n = st.n;
@@ -588,22 +735,23 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
     p.dY = to_df(st.dY);
     p.dI = to_df(st.dI);
     p.use_E = st.use_E;
+    p.affine_out = !(st.dY == 1.0 && st.dI == 0.0);
+    p.scratch = st.scratch;
     p.A = st.A;
     p.out = st.out;
     p.out64 = st.out64;
     p.red = st.red;
     p.err = st.err;
-    const int stages = digit_stages(st.s_in);
-    const size_t smem = digit_smem_bytes(st.s_in);
-    static bool attr_set = false;
-    if (!attr_set) {
-        PURIFY_CUDA_TRY(cudaFuncSetAttribute(digit_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024));
-        attr_set = true;
-    }
+    const int stages = digit_stages(st.s_in, kc);
+    const size_t smem = digit_smem_bytes(st.s_in, kc);
     const int T = st.n_pad / TILE;
     const int tiles = T * (T + 1) / 2;
-    digit_gemm_kernel<<<tiles, NTHREADS, smem, stream>>>(ma, mb, p, stages);
+    const int grid = tiles < st.max_ctas ? tiles : st.max_ctas;
+    if (!st.scratch || grid < 1) return PURIFY_ERR_INVALID_ARG;
+    KernelFn fn = kernel_for(kc, st.s_in);
+    if (!fn) return PURIFY_ERR_INVALID_ARG;
+    PURIFY_TRY(prepare_kernel(fn));
+    fn<<<grid, NTHREADS, smem, stream>>>(ma, mb, p, stages, tiles);
     PURIFY_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return PURIFY_OK;

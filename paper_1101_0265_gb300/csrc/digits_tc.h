@@ -28,7 +28,12 @@ struct DigitStep {
     double* out64 = nullptr;
     double* red = nullptr;
     int* err = nullptr;
+    float2* scratch = nullptr;  // max_ctas x 128 x 128 float2 (digit_scratch_bytes)
+    int max_ctas = 0;           // persistent grid size (the SM count)
 };
+
+// Device scratch of the persistent product kernel for a grid of `ctas`.
+inline size_t digit_scratch_bytes(int ctas) { return (size_t)ctas * 128 * 128 * sizeof(float2); }
 
 int launch_digit_step(const DigitStep& st, cudaStream_t stream);
 
@@ -44,8 +49,9 @@ inline int remainder_bits(int n_pad) { return n_pad <= 4096 ? 7 : 6; }
 // Bits carried by s digits (8 leading + r per remainder digit).
 inline int digit_bits(int s, int rbits) { return 8 + rbits * (s - 1); }
 
-int digit_stages(int s);
-size_t digit_smem_bytes(int s);
+int digit_kc(int s);
+int digit_stages(int s, int kc);
+size_t digit_smem_bytes(int s, int kc);
 
 inline int pad128(int64_t n) { return (int)((n + 127) / 128 * 128); }
 

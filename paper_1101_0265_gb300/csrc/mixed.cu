@@ -25,6 +25,8 @@ struct MixedState {
     __nv_bfloat16* Xd[2] = {nullptr, nullptr};
     __nv_bfloat16* Sd = nullptr;
     int* err = nullptr;
+    float2* scratch = nullptr;  // persistent product kernel, one tile per CTA
+    int ctas = 0;
 };
 
 void mixed_free(MixedState* ms) {
@@ -33,6 +35,7 @@ void mixed_free(MixedState* ms) {
     cudaFree(ms->Xd[1]);
     cudaFree(ms->Sd);
     cudaFree(ms->err);
+    cudaFree(ms->scratch);
     delete ms;
 }
 
@@ -41,6 +44,10 @@ static int ensure_mixed(purify_ctx* h, int n_pad) {
         h->mixed = new (std::nothrow) MixedState();
         if (!h->mixed) return PURIFY_ERR_OOM;
         PURIFY_CUDA_TRY(cudaMalloc(&h->mixed->err, sizeof(int)));
+        int sms = 0;
+        PURIFY_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
+        h->mixed->ctas = sms;
+        PURIFY_CUDA_TRY(cudaMalloc(&h->mixed->scratch, digit_scratch_bytes(sms)));
     }
     MixedState* ms = h->mixed;
     if (n_pad <= ms->n_pad_cap) return PURIFY_OK;
@@ -155,8 +162,10 @@ int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
             p1.out = ms->Sd;
             p1.s_out = s;
             p1.e_out = 1;
-            p1.red = h->red + 4 * (2 * i);
+            p1.red = nullptr;
             p1.err = ms->err;
+            p1.scratch = ms->scratch;
+            p1.max_ctas = ms->ctas;
             PURIFY_TRY(product(h, p1, pairs_of(s) * tile_flops));
             // X_i = 3 S - 2 S X_s, emitted as the next X_s (or as D)
             DigitStep p2 = p1;
@@ -165,8 +174,8 @@ int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
             p2.use_E = 1;
             p2.cP = -2.0;
             p2.cE = 3.0;
-            p2.red = h->red + 4 * (2 * i + 1);
             const bool last = (i + 1 == m + R);
+            p2.red = last ? h->red + 4 * (2 * i + 1) : nullptr;
             if (last) {
                 p2.out = nullptr;
                 p2.s_out = 0;
@@ -195,8 +204,10 @@ int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
             st.eA = st.eB = 0;
             st.use_E = 1;
             tc_coeffs(S.branch[i], S.alpha[i], &st.cP, &st.cE, &st.cI);
-            st.red = h->red + 4 * (2 * i + 1);
+            st.red = (i + 1 == m && R == 0) ? h->red + 4 * (2 * i + 1) : nullptr;
             st.err = ms->err;
+            st.scratch = ms->scratch;
+            st.max_ctas = ms->ctas;
             const bool last = (i + 1 == m) && R == 0;
             if (last) {
                 st.out64 = D;
@@ -225,15 +236,17 @@ int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
             p1.use_E = 1;  // ||X - X^2|| of the iterate
             p1.cP = 1.0;
             p1.cE = 0.0;
-            p1.red = h->red + 4 * (2 * i);
+            p1.red = (r + 1 == R) ? h->red + 4 * (2 * i) : nullptr;
             p1.err = ms->err;
+            p1.scratch = ms->scratch;
+            p1.max_ctas = ms->ctas;
             PURIFY_TRY(product(h, p1, pairs_of(s) * tile_flops));
             DigitStep p2 = p1;
             p2.A = ms->Sd;
             p2.B = ms->Xd[x];
             p2.cP = -2.0;
             p2.cE = 3.0;
-            p2.red = h->red + 4 * (2 * i + 1);
+            p2.red = (r + 1 == R) ? h->red + 4 * (2 * i + 1) : nullptr;
             if (r + 1 == R) {
                 p2.out = nullptr;
                 p2.s_out = 0;
@@ -287,9 +300,15 @@ extern "C" int purify_k_digit_product_f64(const double* A, const double* B, doub
     const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)digits * n_pad * n_pad;
     __nv_bfloat16 *pa = nullptr, *pb = nullptr;
     int* err = nullptr;
+    float2* scratch = nullptr;
     int r = PURIFY_OK;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return PURIFY_ERR_CUDA;
     if (cudaMalloc(&pa, plane_bytes) != cudaSuccess || cudaMalloc(&pb, plane_bytes) != cudaSuccess ||
-        cudaMalloc(&err, sizeof(int)) != cudaSuccess)
+        cudaMalloc(&err, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&scratch, digit_scratch_bytes(sms)) != cudaSuccess)
         r = PURIFY_ERR_OOM;
     if (r == PURIFY_OK && cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) r = PURIFY_ERR_CUDA;
     const int rb = remainder_bits(n_pad);
@@ -306,6 +325,8 @@ extern "C" int purify_k_digit_product_f64(const double* A, const double* B, doub
         st.eB = eB;
         st.out64 = C;
         st.err = err;
+        st.scratch = scratch;
+        st.max_ctas = sms;
         r = launch_digit_step(st, s);
     }
     int herr = 0;
@@ -319,6 +340,7 @@ extern "C" int purify_k_digit_product_f64(const double* A, const double* B, doub
     cudaFree(pa);
     cudaFree(pb);
     cudaFree(err);
+    cudaFree(scratch);
     if (r == PURIFY_OK && herr) r = PURIFY_ERR_DEVICE_TIMEOUT;
     return r;
 }
