@@ -208,6 +208,31 @@ int purify_k_step_f64(const double* A, const double* B, const double* E, double*
  * a device scratch array of 2 * ceil(n / 8) doubles per call. */
 int purify_k_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi, void* stream);
 
+/* Largest n accepted by purify_k_gershgorin_f64_noalloc. */
+#define PURIFY_GERSHGORIN_NOALLOC_MAX_N 65536
+
+/* The Gershgorin interval of purify_k_gershgorin_f64, for callers that must
+ * not allocate device memory: hosts that hand all device memory to their own
+ * pool allocator and do not let libraries call cudaMalloc/cudaFree, callers
+ * whose device memory budget is fully committed, and latency-sensitive loops
+ * that cannot absorb the device-wide synchronisation of cudaFree.  The paper
+ * has no counterpart; this is a library-level variant of the bound kernel.
+ *
+ * It allocates nothing: the per-block partial results live in one static
+ * device array of 2 * ceil(PURIFY_GERSHGORIN_NOALLOC_MAX_N / 8) doubles
+ * (128 KiB), which every GPU that loads the library holds until the process
+ * exits.  n > PURIFY_GERSHGORIN_NOALLOC_MAX_N is rejected with
+ * PURIFY_ERR_INVALID_ARG before anything is launched.  The first call on a
+ * device looks up that array's device address (once per device, with the
+ * device current); make that first call before any stream capture begins.
+ * The work is queued on `stream` and the call returns without synchronising;
+ * lohi (device, 2 doubles) is valid once the stream reaches that point.
+ * Every call shares the one array and nothing in it needs to start at zero,
+ * but calls whose kernels overlap on the GPU (different streams, or
+ * different host threads) race on it: serialise them. */
+int purify_k_gershgorin_f64_noalloc(const double* F, int64_t n, int64_t ld, double* lohi,
+                                    void* stream);
+
 /* k Lanczos steps on symmetric F (n x n, leading dimension n) from the
  * SplitMix64 start vector q_i = 2 u_i - 1, u_i = (splitmix64(key + i *
  * 0x9E3779B97F4A7C15) >> 11) / 2^53 with key 0x11010265.  Writes the

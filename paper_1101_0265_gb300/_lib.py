@@ -34,7 +34,7 @@ EXPORTED = (
     "purify_set_hamiltonian", "purify_run", "purify_get_density", "purify_stats",
     "purify_density_device_ptr", "purify_strerror", "purify_schedule", "purify_tridiag_eig",
     "purify_k_symm_product_f64", "purify_k_step_f64", "purify_k_gershgorin_f64",
-    "purify_k_lanczos_f64", "purify_k_digit_product_f64",
+    "purify_k_lanczos_f64", "purify_k_digit_product_f64", "purify_k_gershgorin_f64_noalloc",
 )
 
 
@@ -102,6 +102,7 @@ def load(path: str = LIB_PATH):
         "purify_k_gershgorin_f64": (ip, [vp, i64, i64, vp, vp]),
         "purify_k_lanczos_f64": (ip, [vp, i64, ip, dp, dp, vp]),
         "purify_k_digit_product_f64": (ip, [vp, vp, vp, i64, ip, ip, ip, vp]),
+        "purify_k_gershgorin_f64_noalloc": (ip, [vp, i64, i64, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -315,3 +316,18 @@ def k_digit_product_f64(A, B, out, digits: int, eA: int = 0, eB: int = 0):
                                              int(digits), int(eA), int(eB), _stream_of()),
            "k_digit_product_f64")
     return out
+
+
+GERSHGORIN_NOALLOC_MAX_N = 65536
+
+
+def k_gershgorin_f64_noalloc(F, lohi, n=None, check=True):
+    """Gershgorin interval through the allocation-free entry point (static
+    device scratch; see purify.h).  Returns the status code."""
+    _dev_f64(lohi, "lohi")
+    n = int(F.shape[0]) if n is None else int(n)
+    code = load().purify_k_gershgorin_f64_noalloc(_ptr(F), n, max(n, int(F.stride(0))), _ptr(lohi),
+                                                  _stream_of())
+    if check:
+        _check(code, "k_gershgorin_f64_noalloc")
+    return code

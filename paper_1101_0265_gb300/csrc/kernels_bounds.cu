@@ -7,6 +7,7 @@
 #include "internal.h"
 
 #include <cmath>
+#include <mutex>
 
 namespace purify {
 
@@ -221,3 +222,51 @@ int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaS
 }
 
 }  // namespace purify
+
+// ---------------------------------------------------------------------------
+// Allocation-free Gershgorin entry point: the per-block partials of the bound
+// kernel live in a file-scope device array instead of caller- or
+// library-allocated memory.  Host code may only use the array's name with
+// cudaGetSymbolAddress: on the host the name is a stand-in, not a device
+// address.
+// ---------------------------------------------------------------------------
+
+namespace purify {
+namespace {
+
+constexpr int64_t kNoAllocMaxN = PURIFY_GERSHGORIN_NOALLOC_MAX_N;
+static __device__ __align__(256) double g_gershgorin_scratch[2 * ((kNoAllocMaxN + ROWS_PER_CTA - 1) / ROWS_PER_CTA)];
+
+std::mutex g_scratch_mu;
+constexpr int kMaxDevices = 64;
+double* g_scratch_dev[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device, looked up once
+// per device.
+int noalloc_scratch(double** out) {
+    int dev = 0;
+    PURIFY_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return PURIFY_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> g(g_scratch_mu);
+    if (!g_scratch_dev[dev]) {
+        void* p = nullptr;
+        PURIFY_CUDA_TRY(cudaGetSymbolAddress(&p, g_gershgorin_scratch));
+        g_scratch_dev[dev] = (double*)p;
+    }
+    *out = g_scratch_dev[dev];
+    return PURIFY_OK;
+}
+
+}  // namespace
+
+}  // namespace purify
+
+extern "C" int purify_k_gershgorin_f64_noalloc(const double* F, int64_t n, int64_t ld, double* lohi,
+                                               void* stream) {
+    using namespace purify;
+    if (!F || !lohi || n <= 0 || ld < n) return PURIFY_ERR_INVALID_ARG;
+    if (n > kNoAllocMaxN) return PURIFY_ERR_INVALID_ARG;
+    double* scratch = nullptr;
+    PURIFY_TRY(noalloc_scratch(&scratch));
+    return launch_gershgorin_f64(F, n, ld, lohi, scratch, (cudaStream_t)stream);
+}
