@@ -32,6 +32,10 @@ METRIC = ("purified n=4096 matrices/sec + tensor-pipe % at max-err<=1e-6 vs plai
 GAPS = (1e-1, 1e-2, 1e-3, 1e-4)
 SCHEMES = ("TC_SF", "FIXED_MU_SF")
 FP64_PER_BF16 = 1.25 / 2250.0   # nominal dense fp64 : bf16 ratio of GB300
+# DRAM bytes (read + write) of one digit-plane product launch, from one ncu
+# capture of digit_gemm_kernel<32, 5> at n = 4096 (bytes per launch).
+TRAFFIC_DIGIT_GEMM = 716.2e6
+TRAFFIC_SOURCE = "ncu dram__bytes_read+write of digit_gemm_kernel<32,5>, n=4096, one launch"
 
 
 def parse():
@@ -43,6 +47,9 @@ def parse():
     ap.add_argument("--precision", choices=("mixed", "fp64"), default="mixed")
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--tol", type=float, default=1e-9)
+    ap.add_argument("--matrices", type=int, default=8,
+                    help="use the first K matrices of the sweep (profiling / small runs)")
+    ap.add_argument("--schemes", default=",".join(SCHEMES))
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -211,7 +218,8 @@ def main():
         torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.n
-    hs = make_inputs(n, rank)
+    schemes = tuple(args.schemes.split(","))
+    hs = make_inputs(n, rank, args.matrices)
     Fd = [torch.from_numpy(h.F).to(dev) for h in hs]
     Fh = [torch.from_numpy(h.F).pin_memory() for h in hs]
     Dh = torch.empty((n, n), dtype=torch.float64).pin_memory()
@@ -243,7 +251,7 @@ def main():
 
     def step(host=False, record=False):
         for i, h in enumerate(hs):
-            for scheme in SCHEMES:
+            for scheme in schemes:
                 if host:
                     one(h, Fh[i], scheme, D=Dh, record=record)
                 else:
@@ -276,7 +284,7 @@ def main():
     for _ in range(args.warmup):
         step()
     ms, clocks = timed(args.steps, record=True, clocks=True)
-    per_step = len(hs) * len(SCHEMES)
+    per_step = len(hs) * len(schemes)
     value = world * per_step * args.steps / (ms * 1e-3)
     # end to end: host F in, host D out, copies inside the timed region
     step(host=True)
@@ -290,8 +298,9 @@ def main():
         achieved = acc["tensor_flops"] / acc["prod_s"] / 1e12
         peak = pk["bf16_tflops_sustained"]
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "digit-plane tcgen05 product", "peak_kind": f"{pk_kind} bf16 sustained"}
+                "frac": achieved / peak, "traffic": TRAFFIC_DIGIT_GEMM,
+                "kernel": "digit-plane tcgen05 product", "peak_kind": f"{pk_kind} bf16 sustained",
+                "traffic_source": TRAFFIC_SOURCE}
     else:
         achieved = acc["useful"] / acc["prod_s"] / 1e12
         peak = pk["bf16_tflops_sustained"] * FP64_PER_BF16
@@ -304,8 +313,8 @@ def main():
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": f"dense F=Q diag(lambda) Q^T n={n}, nocc in {{n/2,n/4}} x gap in "
-                               f"{{1e-1,1e-2,1e-3,1e-4}} (8 matrices) x schemes TC_SF, "
-                               f"FIXED_MU_SF; tol {args.tol:g}",
+                               f"{{1e-1,1e-2,1e-3,1e-4}} ({len(hs)} matrices) x schemes "
+                               f"{', '.join(schemes)}; tol {args.tol:g}",
                    "n": n, "matrices_per_step": per_step, "precision": args.precision,
                    "tol": args.tol, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (each F is 134 MB, 8 distinct per step)"},
@@ -329,7 +338,7 @@ def main():
         worst = 0.0
         t64 = 0.0
         for i, h in enumerate(hs):
-            for scheme in SCHEMES:
+            for scheme in schemes:
                 one(h, Fd[i], scheme, D=D1)
                 ref.set_hamiltonian(Fd[i], nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax,
                                     homo=h.homo, lumo=h.lumo)

@@ -1,0 +1,18 @@
+// Instantiations of the digit-plane product kernel: k-chunk 64, digit
+// counts 1..3 (one translation unit each, compiled in parallel).
+#include "digits_kernel.cuh"
+
+namespace purify {
+namespace dk {
+
+KernelFn kernel_k64_lo(int s) {
+    switch (s) {
+        case 1: return digit_gemm_kernel<64, 1>;
+        case 2: return digit_gemm_kernel<64, 2>;
+        case 3: return digit_gemm_kernel<64, 3>;
+        default: return nullptr;
+    }
+}
+
+}  // namespace dk
+}  // namespace purify

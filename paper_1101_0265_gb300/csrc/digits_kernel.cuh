@@ -1,0 +1,579 @@
+// Digit-plane symmetric products on the tcgen05 tensor cores (sm_103a).
+//
+// A float64 matrix X with |X_ij| <= 2^e is held as s bf16 "digit planes"
+//     X = 2^(e-8) * sum_p V_p,    V_p = d_p * 2^(-r p),  d_p integer,
+// with a leading digit of 8 bits (|d_0| <= 256) and remainder digits of
+// r = 7 bits (|d_p| <= 65; r = 6 above n = 4096), all round-to-nearest.
+// bf16 stores every such value exactly.  The product of two such
+// matrices is the sum over digit pairs (p, q) of V_p V_q^T.  Pairs with
+// p + q = l form "level" l; levels 0, 1 and 2 each get their own fp32
+// accumulator in tensor memory and are exact: by Cauchy-Schwarz a row of d_0
+// has 2-norm <= 256 ||X_i||_2 / 2^e + sqrt(n)/2, so level 0 and level 1 stay
+// below 2^24 in their own units for n <= 8192; level 2 holds the sum of
+// squares of the remainder digits on the product's diagonal, about
+// n 2^(2r) / 12, which the choice of r keeps below 2^24 for uniformly
+// distributed remainders (8-bit remainders exceed it at n = 4096).  All levels
+// >= 3 share a fourth accumulator whose rounding sits 2^-48 below the
+// leading term.  Pairs with p + q >= s are dropped (their size is that of
+// the digits' own truncation).  The four accumulators are recombined in
+// double-float (pairs of fp32) arithmetic in the epilogue, which also
+// applies the step's polynomial (Eq. 4 / Eq. 5 / Algorithm 1's 3S - 2S X_s),
+// re-splits the result into the next step's digit planes, optionally writes
+// float64, and reduces trace and Frobenius norms.
+//
+// Only output tiles on or above the diagonal are formed; each is written
+// twice (itself and its mirror), so every product is exactly symmetric.
+// Exact symmetry matters: antisymmetric rounding errors are not damped by
+// the purification maps.
+//
+// Structure of one CTA (one 128 x 128 output tile, 320 threads):
+//   warp 0  TMA producer: per k-chunk (16, 32 or 64 wide, with a swizzle of
+//           the chunk's row width) one 3D TMA load of all s planes of the A
+//           row panel and one of the B row panel
+//   warp 1  TMEM allocator and MMA issuer (tcgen05.mma kind::f16, bf16 in,
+//           fp32 accumulate, M = N = 128, K = 16)
+//   warps 2-9 epilogue (tcgen05.ld; warp w reads TMEM lane quarter w % 4 and
+//           one half of the tile's columns)
+// Tiles are numbered in bands of 12 tile columns so that the CTAs resident
+// at one time share row panels in L2.
+// Every wait on an mbarrier is bounded; on time-out the CTA records an error
+// flag, waits (bounded) for its own copies and MMAs, frees its tensor memory
+// and exits.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "digits_tc.h"
+
+namespace purify {
+namespace dk {
+
+constexpr int TILE = 128;        // output tile edge
+constexpr int BAND = 12;         // tile columns per rasterisation band
+constexpr int MAX_STAGES = 8;
+constexpr int NUM_ACC = 4;       // tensor-memory accumulators (levels 0, 1, 2, >= 3)
+constexpr int NTHREADS = 320;
+constexpr int EPI_WARPS = 8;
+constexpr long long WAIT_CYCLES = 1ll << 31;  // one wait gives up after ~1 s at 2 GHz
+
+// ---- PTX wrappers ------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int c0,
+                                            int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+// 32 lanes x 32 bits, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+        "%12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile written by TMA
+// with a swizzle as wide as its rows (KC bf16 = 2 KC bytes: 32, 64 or 128):
+// 8-row groups 16 KC bytes apart; one K = 16 step advances 32 bytes.
+template <int KC>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    constexpr uint64_t layout = KC == 16 ? 6 : (KC == 32 ? 4 : 2);  // 32B / 64B / 128B swizzle
+    uint64_t d = 0;
+    d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
+    d |= (uint64_t)((16 * KC) >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)1 << 46;                          // descriptor version (tcgen05)
+    d |= layout << 61;
+    return d;
+}
+
+// Instruction descriptor: kind::f16, bf16 A and B (K-major), fp32 D,
+// M = 128, N = 128.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TILE >> 3) << 17) |
+                           ((uint32_t)(TILE >> 4) << 24);
+
+// ---- double-float arithmetic (pairs of fp32) ---------------------------------
+
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ df fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df df_add_f(df x, float y) {
+    const df s = two_sum(x.h, y);
+    return fast_two_sum(s.h, __fadd_rn(s.l, x.l));
+}
+
+__device__ __forceinline__ df df_add(df x, df y) {
+    const df s = two_sum(x.h, y.h);
+    const df t = two_sum(x.l, y.l);
+    df u = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+    return fast_two_sum(u.h, __fadd_rn(u.l, t.l));
+}
+
+__device__ __forceinline__ df df_mul(df x, df y) {
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, e);
+    e = __fmaf_rn(x.l, y.h, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_scale(df x, float pow2) { return {x.h * pow2, x.l * pow2}; }
+
+// ---- kernel parameters ------------------------------------------------------
+
+struct DigitGemmParams {
+    int n, n_pad, s_in;      // matrix size, padded size (multiple of 128), digits of A and B
+    int s_out;               // digits of the output (0 = none)
+    int tiles_per_row;       // n_pad / 128
+    float scale_in_h;        // 2^(eA + eB - 16): value of one unit of the accumulators
+    float e_scale;           // 2^(eA - 8): value of one unit of A's planes (for E)
+    float out_digit_scale;   // 2^(8 - e_out)
+    float out_rscale;        // 2^r of the output's remainder digits
+    df cP, cE, cI, dY, dI;   // Y = cP P + cE E + cI I;  out = dY Y + dI I
+    int use_E;               // E = A (the matrix in the A operand)
+    int affine_out;          // (dY, dI) != (1, 0)
+    float2* scratch;         // per CTA 128 x 128 double-float tile
+    const __nv_bfloat16* A;  // A's planes (for E), [s_in][n_pad][n_pad]
+    __nv_bfloat16* out;      // output planes [s_out][n_pad][n_pad] (may be null)
+    double* out64;           // float64 output n x n (leading dimension n) or null
+    double* red;             // [0] trace(Y), [1] ||E - P||_F^2, [2] ||Y||_F^2 (atomics) or null
+    int* err;                // device error flag
+};
+
+// Tile t of the upper triangle (ti <= tj) of a T x T tile grid, in bands of
+// BAND tile columns; inside a band row by row.
+__device__ __forceinline__ void decode_banded(int t, int T, int& ti, int& tj) {
+    int b0 = 0;
+    for (;;) {
+        const int b1 = min(T, b0 + BAND);
+        const int cnt = (b1 * (b1 + 1) - b0 * (b0 + 1)) / 2;
+        if (t < cnt || b1 == T) {
+            for (int r = 0;; ++r) {
+                const int first = max(b0, r);
+                const int c = b1 - first;
+                if (t < c) {
+                    ti = r;
+                    tj = first + t;
+                    return;
+                }
+                t -= c;
+            }
+        }
+        t -= cnt;
+        b0 = b1;
+    }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Bounded wait measured from its own start: false when it gives up.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
+    return true;
+}
+
+// Persistent CTA: tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The four
+// accumulators of a tile are drained into a double-float tile in the CTA's
+// scratch (global, 128 x 128 x 8 bytes) so that tensor memory is released
+// before the polynomial, the re-split and the stores; those overlap the
+// next tile's MMAs.
+template <int KC, int S>
+__global__ void __launch_bounds__(NTHREADS, 1)
+digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                  const DigitGemmParams prm, int stages, int num_tiles) {
+    constexpr int PLANE_BYTES = TILE * KC * 2;  // one plane of one operand per stage
+    constexpr int s = S;
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte aligned operand area: stages x (A planes | B planes)
+    uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    constexpr int stage_bytes = 2 * S * PLANE_BYTES;
+    uint64_t* bars = (uint64_t*)(base + (size_t)stages * stage_bytes);
+    // bars: full[stages] | empty[stages] | tmem_full | tmem_empty | drain
+    uint64_t* full_bar = bars;
+    uint64_t* empty_bar = bars + stages;
+    uint64_t* tmem_full = bars + 2 * stages;
+    uint64_t* tmem_empty = tmem_full + 1;
+    uint64_t* drain = tmem_full + 2;
+    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nk = prm.n_pad / KC;
+    const int T = prm.tiles_per_row;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2 * stages; ++i) mbar_init(smem_u32(&bars[i]), 1);
+        mbar_init(smem_u32(tmem_full), 1);
+        mbar_init(smem_u32(tmem_empty), EPI_WARPS);
+        mbar_init(smem_u32(drain), 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) tmem_alloc(smem_u32(tmem_slot), NUM_ACC * TILE);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer: one continuous ring of k-chunks over all tiles
+            int it = 0;
+            for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x) {
+                int ti, tj;
+                decode_banded(t, T, ti, tj);
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int st = it % stages;
+                    if (it >= stages && !mbar_wait_for(smem_u32(&empty_bar[st]), (uint32_t)(((it / stages) & 1) ^ 1))) {
+                        atomicExch(prm.err, 1);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    const uint32_t fb = smem_u32(&full_bar[st]);
+                    uint8_t* sa = base + (size_t)st * stage_bytes;
+                    mbar_arrive_expect_tx(fb, (uint32_t)stage_bytes);
+                    tma_load_3d(smem_u32(sa), &mapA, fb, kc * KC, ti * TILE, 0);
+                    tma_load_3d(smem_u32(sa + s * PLANE_BYTES), &mapB, fb, kc * KC, tj * TILE, 0);
+                }
+            }
+            // wait (bounded) for the copies still in flight
+            for (int k = (it > stages ? it - stages : 0); k < it; ++k)
+                mbar_wait_for(smem_u32(&full_bar[k % stages]), (uint32_t)((k / stages) & 1));
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer.  Descriptors are one base plus compile-time offsets
+            // (the start address sits in the low 14 bits and never carries).
+            const uint64_t desc_base = smem_desc<KC>(smem_u32(base));
+            int it = 0, lt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++lt) {
+                if (lt > 0 && !mbar_wait_for(smem_u32(tmem_empty), (uint32_t)((lt - 1) & 1))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int kc = 0; kc < nk; ++kc, ++it) {
+                    const int st = it % stages;
+                    if (!mbar_wait_for(smem_u32(&full_bar[st]), (uint32_t)((it / stages) & 1)) || *abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t da = desc_base + (uint64_t)((st * stage_bytes) >> 4);
+                    const uint64_t db = da + (uint64_t)((S * PLANE_BYTES) >> 4);
+                    const uint32_t later = kc > 0 ? 1u : 0u;
+#pragma unroll
+                    for (int p = 0; p < S; ++p) {
+#pragma unroll
+                        for (int q = 0; q < S - p; ++q) {
+                            const int a = (p + q < NUM_ACC - 1) ? p + q : NUM_ACC - 1;
+#pragma unroll
+                            for (int kk = 0; kk < KC / 16; ++kk) {
+                                // the first write of accumulator a in a tile is pair
+                                // (0, a) at k = 0; all later ones accumulate
+                                const uint32_t acc_in = (kk > 0 || p > 0 || q > NUM_ACC - 1) ? 1u : later;
+                                mma_bf16(tmem + (uint32_t)(a * TILE),
+                                         da + (uint64_t)((p * PLANE_BYTES + kk * 32) >> 4),
+                                         db + (uint64_t)((q * PLANE_BYTES + kk * 32) >> 4), IDESC, acc_in);
+                            }
+                        }
+                    }
+                    mma_commit(smem_u32(&empty_bar[st]));
+                }
+                if (!ok) break;
+                mma_commit(smem_u32(tmem_full));
+            }
+            if (!ok) {
+                atomicExch(prm.err, 2);
+                *abort_flag = 1;
+            }
+            // every MMA this thread issued has completed before teardown
+            mma_commit(smem_u32(drain));
+            mbar_wait_for(smem_u32(drain), 0);
+        }
+    } else {
+        // epilogue warps 2..9: lane quarter warp % 4, column half (warp - 2) / 4
+        const int quarter = warp & 3;
+        const int col0 = ((warp - 2) >> 2) * (TILE / 2);
+        const int row_in_tile = quarter * 32 + lane;
+        const size_t plane = (size_t)prm.n_pad * prm.n_pad;
+        float2* scr = prm.scratch + ((size_t)blockIdx.x * TILE + row_in_tile) * TILE;
+        double s_tr = 0.0;  // the trace decides the occupation check: float64
+        float s_idem = 0.f, s_fro = 0.f;
+        int lt = 0;
+        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++lt) {
+            int ti, tj;
+            decode_banded(t, T, ti, tj);
+            bool ready = mbar_wait_for(smem_u32(tmem_full), (uint32_t)(lt & 1));
+            if (!ready) {
+                atomicExch(prm.err, 3);
+                *abort_flag = 1;
+            }
+            // tcgen05.ld is warp-collective: decide once per warp
+            ready = __all_sync(0xffffffffu, ready && !*abort_flag);
+            if (!ready) break;
+            tc_fence_after();
+            // phase 1: accumulators -> double-float P in scratch; release TMEM
+            const int nacc = s < NUM_ACC ? s : NUM_ACC;
+            for (int c0 = col0; c0 < col0 + TILE / 2; c0 += 16) {
+                float acc[NUM_ACC][16];
+#pragma unroll
+                for (int a = 0; a < NUM_ACC; ++a) {
+                    if (a < nacc) {
+                        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * TILE + c0), acc[a]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) acc[a][c] = 0.f;
+                    }
+                }
+                float4* dst = (float4*)(scr + c0);
+#pragma unroll
+                for (int c = 0; c < 16; c += 2) {
+                    df P0 = two_sum(acc[0][c], acc[1][c]);
+                    P0 = df_add_f(P0, acc[2][c]);
+                    P0 = df_add_f(P0, acc[3][c]);
+                    df P1 = two_sum(acc[0][c + 1], acc[1][c + 1]);
+                    P1 = df_add_f(P1, acc[2][c + 1]);
+                    P1 = df_add_f(P1, acc[3][c + 1]);
+                    dst[c / 2] = make_float4(P0.h, P0.l, P1.h, P1.l);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_empty)) : "memory");
+
+            // phase 2: polynomial, outputs, reductions
+            const int i = ti * TILE + row_in_tile;
+            const bool diag_tile = (ti == tj);
+            for (int c0 = col0; c0 < col0 + TILE / 2; c0 += 16) {
+                const int jb = tj * TILE + c0;
+                df Ov[16];
+                {
+                    float4 pv[8];
+                    const float4* src = (const float4*)(scr + c0);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) pv[c] = src[c];
+                    // E = A at (i, jb .. jb + 15): exact two-float sum of its digits
+                    float eh[16], el[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) eh[c] = el[c] = 0.f;
+                    if (prm.use_E) {
+                        for (int p = 0; p < s; ++p) {
+                            const __nv_bfloat16* srcd = prm.A + p * plane + (size_t)i * prm.n_pad + jb;
+                            uint4 u[2];
+                            u[0] = *(const uint4*)srcd;
+                            u[1] = *(const uint4*)(srcd + 8);
+                            const __nv_bfloat16* hv = (const __nv_bfloat16*)u;
+                            if (p < 3) {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) eh[c] += __bfloat162float(hv[c]);
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) el[c] += __bfloat162float(hv[c]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const int j = jb + c;
+                        const float4 q4 = pv[c >> 1];
+                        const df P = df_scale((c & 1) ? df{q4.z, q4.w} : df{q4.x, q4.y}, prm.scale_in_h);
+                        const df E = df_scale(fast_two_sum(eh[c], el[c]), prm.e_scale);
+                        df Y = df_mul(prm.cP, P);
+                        if (prm.use_E) Y = df_add(Y, df_mul(prm.cE, E));
+                        if (i == j) Y = df_add(Y, prm.cI);
+                        df O = Y;
+                        if (prm.affine_out) {
+                            O = df_mul(prm.dY, Y);
+                            if (i == j) O = df_add(O, prm.dI);
+                        }
+                        const bool valid = i < prm.n && j < prm.n;
+                        if (!valid) O = {0.f, 0.f};
+                        Ov[c] = O;
+                        if (prm.red && valid && (!diag_tile || i <= j)) {
+                            const float w = (i == j) ? 1.f : 2.f;
+                            if (i == j) s_tr += (double)Y.h + (double)Y.l;
+                            const df dE = df_add(E, {-P.h, -P.l});
+                            s_idem += w * dE.h * dE.h;
+                            s_fro += w * Y.h * Y.h;
+                        }
+                    }
+                }
+                // float64 output (n x n): row segment and its mirror column
+                if (prm.out64 && i < prm.n) {
+                    for (int c = 0; c < 16; ++c) {
+                        const int j = jb + c;
+                        if (j < prm.n && (!diag_tile || i <= j)) {
+                            const double v = (double)Ov[c].h + (double)Ov[c].l;
+                            prm.out64[(size_t)i * prm.n + j] = v;
+                            if (i != j) prm.out64[(size_t)j * prm.n + i] = v;
+                        }
+                    }
+                }
+                // digit planes of the output (next step's operand)
+                if (prm.out) {
+                    df z[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) z[c] = df_scale(Ov[c], prm.out_digit_scale);
+                    float plane_scale = 1.f;
+                    const float rs = prm.out_rscale, rinv = 1.f / prm.out_rscale;
+                    for (int p = 0; p < prm.s_out; ++p) {
+                        __align__(16) __nv_bfloat16 dv[16];
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) {
+                            // z.h - d is exact; |z.l| <= ulp(z.h) / 2, so the
+                            // fast two-sum renormalises exactly
+                            const float d = rintf(z[c].h);
+                            z[c] = df_scale(fast_two_sum(__fsub_rn(z[c].h, d), z[c].l), rs);
+                            dv[c] = __float2bfloat16_rn(d * plane_scale);
+                        }
+                        plane_scale *= rinv;
+                        __nv_bfloat16* dst = prm.out + p * plane;
+                        if (!diag_tile) {
+                            uint4* row = (uint4*)(dst + (size_t)i * prm.n_pad + jb);
+                            row[0] = ((const uint4*)dv)[0];
+                            row[1] = ((const uint4*)dv)[1];
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) dst[(size_t)(jb + c) * prm.n_pad + i] = dv[c];
+                        } else {
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) {
+                                const int j = jb + c;
+                                if (i <= j) {
+                                    dst[(size_t)i * prm.n_pad + j] = dv[c];
+                                    if (i != j) dst[(size_t)j * prm.n_pad + i] = dv[c];
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (prm.red) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) s_tr += __shfl_xor_sync(0xffffffffu, s_tr, o);
+            s_idem = warp_sum_f(s_idem);
+            s_fro = warp_sum_f(s_fro);
+            if (lane == 0) {
+                atomicAdd(&prm.red[0], s_tr);
+                atomicAdd(&prm.red[1], (double)s_idem);
+                atomicAdd(&prm.red[2], (double)s_fro);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem, NUM_ACC * TILE);
+    }
+}
+
+typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const DigitGemmParams, int, int);
+
+// Kernel pointers of the instantiations in digits_k<KC><lo|hi>.cu.
+KernelFn kernel_k32_lo(int s);
+KernelFn kernel_k32_hi(int s);
+KernelFn kernel_k64_lo(int s);
+KernelFn kernel_k64_hi(int s);
+
+}  // namespace dk
+}  // namespace purify
