@@ -208,6 +208,59 @@ int purify_k_step_f64(const double* A, const double* B, const double* E, double*
  * a device scratch array of 2 * ceil(n / 8) doubles per call. */
 int purify_k_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi, void* stream);
 
+/* ---- many Hamiltonians on one device ----------------------------------- */
+/* A batch holds any number of purifications of different sizes, schemes and
+ * tolerances (the recursion of Eq. 1 with Algorithm 1 or 2 for each), always
+ * on the mixed path.  Each instance's product steps are planned when it is
+ * added, from its own scalar schedule; a round advances every active
+ * instance by one matrix product, with the tiles of all instances that share
+ * a digit count in one persistent tensor-core launch.  Instances retire at
+ * their own iteration counts.  Not thread-safe; one stream. */
+typedef struct purify_batch* purify_batch_t;
+
+/* Device bytes an instance of size n holds while it is in a batch (F, D and
+ * three sets of up to 6 digit planes), for admission control. */
+int64_t purify_batch_footprint(int64_t n);
+
+/* Create / destroy a batch on `device` (stream: caller-owned cudaStream_t or
+ * NULL).  opt->digits fixes the digit count (0: from the mapped gap). */
+int purify_batch_create(purify_batch_t* b, int device, void* cuda_stream, const purify_options* opt);
+int purify_batch_destroy(purify_batch_t b);
+
+/* Add one instance: F (n x n, leading dimension ld, host or device; copied;
+ * upper triangle read), nocc (< 0: unknown), mu (fixed-mu schemes; NaN: the
+ * gap centre), all four bounds required, scheme, tol, max_iter.  Allocates
+ * the instance's device memory (purify_batch_footprint) and writes its id. */
+int purify_batch_add(purify_batch_t b, const double* F, int64_t n, int64_t ld, int64_t nocc, double mu,
+                     const purify_bounds* bounds, int scheme, double tol, int max_iter, int* id);
+
+/* One round (continuous batching): queue f_0 for instances added since the
+ * last round, advance every active instance by one product, synchronise.
+ * *active receives the instances still running, *finished those that
+ * completed in this round. */
+int purify_batch_step(purify_batch_t b, int* active, int* finished);
+
+/* Run every instance of the batch from f_0 to completion.  use_graph = 1
+ * captures the splits and all rounds into one CUDA graph, replayed by later
+ * calls while the set of instances is unchanged. */
+int purify_batch_run(purify_batch_t b, int use_graph);
+
+/* 1 when instance `id` has finished, 0 while it is pending or running. */
+int purify_batch_status(purify_batch_t b, int id);
+
+/* Copy a finished instance's density (host or device, leading dimension ld). */
+int purify_batch_get_density(purify_batch_t b, int id, double* D, int64_t ld);
+
+/* Statistics of one instance (trace, idempotency of Algorithm 2, schedule,
+ * work); seconds = device time of the last purify_batch_run. */
+int purify_batch_stats(purify_batch_t b, int id, purify_stats_t* st);
+
+/* Free an instance's device memory (its id stays invalid afterwards). */
+int purify_batch_release(purify_batch_t b, int id);
+
+/* Device bytes held by the batch's instances. */
+int64_t purify_batch_bytes_in_use(purify_batch_t b);
+
 /* Largest n accepted by purify_k_gershgorin_f64_noalloc. */
 #define PURIFY_GERSHGORIN_NOALLOC_MAX_N 65536
 

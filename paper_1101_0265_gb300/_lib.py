@@ -35,6 +35,9 @@ EXPORTED = (
     "purify_density_device_ptr", "purify_strerror", "purify_schedule", "purify_tridiag_eig",
     "purify_k_symm_product_f64", "purify_k_step_f64", "purify_k_gershgorin_f64",
     "purify_k_lanczos_f64", "purify_k_digit_product_f64", "purify_k_gershgorin_f64_noalloc",
+    "purify_batch_footprint", "purify_batch_create", "purify_batch_destroy", "purify_batch_add",
+    "purify_batch_step", "purify_batch_run", "purify_batch_status", "purify_batch_get_density",
+    "purify_batch_stats", "purify_batch_release", "purify_batch_bytes_in_use",
 )
 
 
@@ -103,6 +106,18 @@ def load(path: str = LIB_PATH):
         "purify_k_lanczos_f64": (ip, [vp, i64, ip, dp, dp, vp]),
         "purify_k_digit_product_f64": (ip, [vp, vp, vp, i64, ip, ip, ip, vp]),
         "purify_k_gershgorin_f64_noalloc": (ip, [vp, i64, i64, vp, vp]),
+        "purify_batch_footprint": (i64, [i64]),
+        "purify_batch_create": (ip, [C.POINTER(vp), ip, vp, C.POINTER(Options)]),
+        "purify_batch_destroy": (ip, [vp]),
+        "purify_batch_add": (ip, [vp, vp, i64, i64, i64, dbl, C.POINTER(Bounds), ip, dbl, ip,
+                                  C.POINTER(C.c_int)]),
+        "purify_batch_step": (ip, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "purify_batch_run": (ip, [vp, ip]),
+        "purify_batch_status": (ip, [vp, ip]),
+        "purify_batch_get_density": (ip, [vp, ip, vp, i64]),
+        "purify_batch_stats": (ip, [vp, ip, C.POINTER(Stats)]),
+        "purify_batch_release": (ip, [vp, ip]),
+        "purify_batch_bytes_in_use": (i64, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -331,3 +346,85 @@ def k_gershgorin_f64_noalloc(F, lohi, n=None, check=True):
     if check:
         _check(code, "k_gershgorin_f64_noalloc")
     return code
+
+
+# ---------------------------------------------------------------------------
+# Batch (many Hamiltonians, grouped launches) and continuous batching
+# ---------------------------------------------------------------------------
+
+def batch_footprint(n: int) -> int:
+    return int(load().purify_batch_footprint(int(n)))
+
+
+class Batch:
+    """A libpurify batch: many purifications of uneven size on one device."""
+
+    def __init__(self, device: int = 0, stream: int | None = None, digits: int = 0):
+        lib = load()
+        self._lib = lib
+        o = Options()
+        lib.purify_options_default(C.byref(o))
+        o.digits = digits
+        h = C.c_void_p()
+        _check(lib.purify_batch_create(C.byref(h), device, stream, C.byref(o)), "purify_batch_create")
+        self._h = h
+        self.sizes = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.purify_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add(self, F, nocc, lmin, lmax, homo, lumo, scheme="TC_SF", tol=1e-9, max_iter=200, mu=None,
+            ld=None) -> int:
+        n = int(F.shape[0])
+        if ld is None:
+            ld = int(F.strides[0] // 8) if isinstance(F, np.ndarray) else int(F.stride(0))
+        b = Bounds(float(lmin), float(lmax), float(homo), float(lumo))
+        i = C.c_int(-1)
+        _check(self._lib.purify_batch_add(self._h, _ptr(F), n, ld, int(nocc), _nan(mu), C.byref(b),
+                                          SCHEMES[scheme], float(tol), int(max_iter), C.byref(i)),
+               "purify_batch_add")
+        self.sizes[i.value] = n
+        return i.value
+
+    def step(self):
+        a, f = C.c_int(0), C.c_int(0)
+        _check(self._lib.purify_batch_step(self._h, C.byref(a), C.byref(f)), "purify_batch_step")
+        return a.value, f.value
+
+    def run(self, use_graph: bool = True):
+        _check(self._lib.purify_batch_run(self._h, int(use_graph)), "purify_batch_run")
+
+    def done(self, i: int) -> bool:
+        r = self._lib.purify_batch_status(self._h, int(i))
+        if r < 0:
+            raise PurifyError(r, "purify_batch_status")
+        return r == 1
+
+    def density(self, i: int, out=None):
+        n = self.sizes[i]
+        if out is None:
+            out = np.empty((n, n), dtype=np.float64)
+        ld = int(out.strides[0] // 8) if isinstance(out, np.ndarray) else int(out.stride(0))
+        _check(self._lib.purify_batch_get_density(self._h, int(i), _ptr(out), ld),
+               "purify_batch_get_density")
+        return out
+
+    def stats(self, i: int) -> dict:
+        s = Stats()
+        _check(self._lib.purify_batch_stats(self._h, int(i), C.byref(s)), "purify_batch_stats")
+        return s.as_dict()
+
+    def release(self, i: int):
+        _check(self._lib.purify_batch_release(self._h, int(i)), "purify_batch_release")
+        self.sizes.pop(i, None)
+
+    def bytes_in_use(self) -> int:
+        return int(self._lib.purify_batch_bytes_in_use(self._h))

@@ -220,13 +220,44 @@ struct DigitGemmParams {
     df cP, cE, cI, dY, dI;   // Y = cP P + cE E + cI I;  out = dY Y + dI I
     int use_E;               // E = A (the matrix in the A operand)
     int affine_out;          // (dY, dI) != (1, 0)
-    float2* scratch;         // per CTA 128 x 128 double-float tile
     const __nv_bfloat16* A;  // A's planes (for E), [s_in][n_pad][n_pad]
     __nv_bfloat16* out;      // output planes [s_out][n_pad][n_pad] (may be null)
     double* out64;           // float64 output n x n (leading dimension n) or null
     double* red;             // [0] trace(Y), [1] ||E - P||_F^2, [2] ||Y||_F^2 (atomics) or null
-    int* err;                // device error flag
 };
+
+// One launch: either a single product (maps and parameters by value, tiles
+// in banded order) or a group of products of different sizes (tensor maps,
+// parameters and the list of work items in global memory).
+struct DigitLaunch {
+    CUtensorMap mapA, mapB;          // single product
+    DigitGemmParams one;             // single product
+    const CUtensorMap* maps;         // group: A and B map of product g at [2g], [2g + 1]
+    const DigitGemmParams* prms;     // group: parameters of product g
+    const int4* work;                // group: {g, ti, tj, -} per work item
+    int num_items;                   // tiles (single) or work items (group)
+    int stages;                      // depth of the shared-memory ring
+    float2* scratch;                 // per CTA 128 x 128 double-float tile
+    int* err;                        // device error flag
+};
+
+__device__ __forceinline__ void decode_banded(int t, int T, int& ti, int& tj);
+
+__device__ __forceinline__ void item_of(const DigitLaunch& L, int t, int& g, int& ti, int& tj) {
+    if (L.work) {
+        const int4 w = L.work[t];
+        g = w.x;
+        ti = w.y;
+        tj = w.z;
+    } else {
+        g = 0;
+        decode_banded(t, L.one.tiles_per_row, ti, tj);
+    }
+}
+
+__device__ __forceinline__ const DigitGemmParams& params_of(const DigitLaunch& L, int g) {
+    return L.prms ? L.prms[g] : L.one;
+}
 
 // Tile t of the upper triangle (ti <= tj) of a T x T tile grid, in bands of
 // BAND tile columns; inside a band row by row.
@@ -267,21 +298,20 @@ __device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity) {
     return true;
 }
 
-// Persistent CTA: tiles blockIdx.x, blockIdx.x + gridDim.x, ...  The four
-// accumulators of a tile are drained into a double-float tile in the CTA's
-// scratch (global, 128 x 128 x 8 bytes) so that tensor memory is released
-// before the polynomial, the re-split and the stores; those overlap the
-// next tile's MMAs.
+// Persistent CTA: work items blockIdx.x, blockIdx.x + gridDim.x, ...  The
+// four accumulators of a tile are drained into a double-float tile in the
+// CTA's scratch (global, 128 x 128 x 8 bytes) so that tensor memory is
+// released before the polynomial, the re-split and the stores; those overlap
+// the next tile's MMAs.  All digit counts of a launch are S.
 template <int KC, int S>
-__global__ void __launch_bounds__(NTHREADS, 1)
-digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                  const DigitGemmParams prm, int stages, int num_tiles) {
+__global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_constant__ DigitLaunch L) {
     constexpr int PLANE_BYTES = TILE * KC * 2;  // one plane of one operand per stage
     constexpr int s = S;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned operand area: stages x (A planes | B planes)
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int stage_bytes = 2 * S * PLANE_BYTES;
+    const int stages = L.stages;
     uint64_t* bars = (uint64_t*)(base + (size_t)stages * stage_bytes);
     // bars: full[stages] | empty[stages] | tmem_full | tmem_empty | drain
     uint64_t* full_bar = bars;
@@ -293,8 +323,7 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = prm.n_pad / KC;
-    const int T = prm.tiles_per_row;
+    const int num_items = L.num_items;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2 * stages; ++i) mbar_init(smem_u32(&bars[i]), 1);
@@ -312,15 +341,18 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
 
     if (warp == 0) {
         if (lane == 0) {
-            // producer: one continuous ring of k-chunks over all tiles
+            // producer: one continuous ring of k-chunks over all work items
             int it = 0;
-            for (int t = blockIdx.x; t < num_tiles && !*abort_flag; t += gridDim.x) {
-                int ti, tj;
-                decode_banded(t, T, ti, tj);
+            for (int t = blockIdx.x; t < num_items && !*abort_flag; t += gridDim.x) {
+                int g, ti, tj;
+                item_of(L, t, g, ti, tj);
+                const int nk = params_of(L, g).n_pad / KC;
+                const CUtensorMap* mA = L.maps ? &L.maps[2 * g] : &L.mapA;
+                const CUtensorMap* mB = L.maps ? &L.maps[2 * g + 1] : &L.mapB;
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int st = it % stages;
                     if (it >= stages && !mbar_wait_for(smem_u32(&empty_bar[st]), (uint32_t)(((it / stages) & 1) ^ 1))) {
-                        atomicExch(prm.err, 1);
+                        atomicExch(L.err, 1);
                         *abort_flag = 1;
                         break;
                     }
@@ -328,8 +360,8 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                     const uint32_t fb = smem_u32(&full_bar[st]);
                     uint8_t* sa = base + (size_t)st * stage_bytes;
                     mbar_arrive_expect_tx(fb, (uint32_t)stage_bytes);
-                    tma_load_3d(smem_u32(sa), &mapA, fb, kc * KC, ti * TILE, 0);
-                    tma_load_3d(smem_u32(sa + s * PLANE_BYTES), &mapB, fb, kc * KC, tj * TILE, 0);
+                    tma_load_3d(smem_u32(sa), mA, fb, kc * KC, ti * TILE, 0);
+                    tma_load_3d(smem_u32(sa + s * PLANE_BYTES), mB, fb, kc * KC, tj * TILE, 0);
                 }
             }
             // wait (bounded) for the copies still in flight
@@ -343,7 +375,10 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             const uint64_t desc_base = smem_desc<KC>(smem_u32(base));
             int it = 0, lt = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < num_tiles && ok; t += gridDim.x, ++lt) {
+            for (int t = blockIdx.x; t < num_items && ok; t += gridDim.x, ++lt) {
+                int g, ti, tj;
+                item_of(L, t, g, ti, tj);
+                const int nk = params_of(L, g).n_pad / KC;
                 if (lt > 0 && !mbar_wait_for(smem_u32(tmem_empty), (uint32_t)((lt - 1) & 1))) {
                     ok = false;
                     break;
@@ -381,7 +416,7 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                 mma_commit(smem_u32(tmem_full));
             }
             if (!ok) {
-                atomicExch(prm.err, 2);
+                atomicExch(L.err, 2);
                 *abort_flag = 1;
             }
             // every MMA this thread issued has completed before teardown
@@ -393,17 +428,16 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
         const int quarter = warp & 3;
         const int col0 = ((warp - 2) >> 2) * (TILE / 2);
         const int row_in_tile = quarter * 32 + lane;
-        const size_t plane = (size_t)prm.n_pad * prm.n_pad;
-        float2* scr = prm.scratch + ((size_t)blockIdx.x * TILE + row_in_tile) * TILE;
-        double s_tr = 0.0;  // the trace decides the occupation check: float64
-        float s_idem = 0.f, s_fro = 0.f;
+        float2* scr = L.scratch + ((size_t)blockIdx.x * TILE + row_in_tile) * TILE;
         int lt = 0;
-        for (int t = blockIdx.x; t < num_tiles; t += gridDim.x, ++lt) {
-            int ti, tj;
-            decode_banded(t, T, ti, tj);
+        for (int t = blockIdx.x; t < num_items; t += gridDim.x, ++lt) {
+            int g, ti, tj;
+            item_of(L, t, g, ti, tj);
+            const DigitGemmParams& P = params_of(L, g);
+            const size_t plane = (size_t)P.n_pad * P.n_pad;
             bool ready = mbar_wait_for(smem_u32(tmem_full), (uint32_t)(lt & 1));
             if (!ready) {
-                atomicExch(prm.err, 3);
+                atomicExch(L.err, 3);
                 *abort_flag = 1;
             }
             // tcgen05.ld is warp-collective: decide once per warp
@@ -442,6 +476,9 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
             // phase 2: polynomial, outputs, reductions
             const int i = ti * TILE + row_in_tile;
             const bool diag_tile = (ti == tj);
+            const int n = P.n, n_pad = P.n_pad;
+            double s_tr = 0.0;  // the trace decides the occupation check: float64
+            float s_idem = 0.f, s_fro = 0.f;
             for (int c0 = col0; c0 < col0 + TILE / 2; c0 += 16) {
                 const int jb = tj * TILE + c0;
                 df Ov[16];
@@ -454,9 +491,9 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                     float eh[16], el[16];
 #pragma unroll
                     for (int c = 0; c < 16; ++c) eh[c] = el[c] = 0.f;
-                    if (prm.use_E) {
+                    if (P.use_E) {
                         for (int p = 0; p < s; ++p) {
-                            const __nv_bfloat16* srcd = prm.A + p * plane + (size_t)i * prm.n_pad + jb;
+                            const __nv_bfloat16* srcd = P.A + p * plane + (size_t)i * n_pad + jb;
                             uint4 u[2];
                             u[0] = *(const uint4*)srcd;
                             u[1] = *(const uint4*)(srcd + 8);
@@ -474,47 +511,47 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                     for (int c = 0; c < 16; ++c) {
                         const int j = jb + c;
                         const float4 q4 = pv[c >> 1];
-                        const df P = df_scale((c & 1) ? df{q4.z, q4.w} : df{q4.x, q4.y}, prm.scale_in_h);
-                        const df E = df_scale(fast_two_sum(eh[c], el[c]), prm.e_scale);
-                        df Y = df_mul(prm.cP, P);
-                        if (prm.use_E) Y = df_add(Y, df_mul(prm.cE, E));
-                        if (i == j) Y = df_add(Y, prm.cI);
+                        const df Pv = df_scale((c & 1) ? df{q4.z, q4.w} : df{q4.x, q4.y}, P.scale_in_h);
+                        const df E = df_scale(fast_two_sum(eh[c], el[c]), P.e_scale);
+                        df Y = df_mul(P.cP, Pv);
+                        if (P.use_E) Y = df_add(Y, df_mul(P.cE, E));
+                        if (i == j) Y = df_add(Y, P.cI);
                         df O = Y;
-                        if (prm.affine_out) {
-                            O = df_mul(prm.dY, Y);
-                            if (i == j) O = df_add(O, prm.dI);
+                        if (P.affine_out) {
+                            O = df_mul(P.dY, Y);
+                            if (i == j) O = df_add(O, P.dI);
                         }
-                        const bool valid = i < prm.n && j < prm.n;
+                        const bool valid = i < n && j < n;
                         if (!valid) O = {0.f, 0.f};
                         Ov[c] = O;
-                        if (prm.red && valid && (!diag_tile || i <= j)) {
+                        if (P.red && valid && (!diag_tile || i <= j)) {
                             const float w = (i == j) ? 1.f : 2.f;
                             if (i == j) s_tr += (double)Y.h + (double)Y.l;
-                            const df dE = df_add(E, {-P.h, -P.l});
+                            const df dE = df_add(E, {-Pv.h, -Pv.l});
                             s_idem += w * dE.h * dE.h;
                             s_fro += w * Y.h * Y.h;
                         }
                     }
                 }
                 // float64 output (n x n): row segment and its mirror column
-                if (prm.out64 && i < prm.n) {
+                if (P.out64 && i < n) {
                     for (int c = 0; c < 16; ++c) {
                         const int j = jb + c;
-                        if (j < prm.n && (!diag_tile || i <= j)) {
+                        if (j < n && (!diag_tile || i <= j)) {
                             const double v = (double)Ov[c].h + (double)Ov[c].l;
-                            prm.out64[(size_t)i * prm.n + j] = v;
-                            if (i != j) prm.out64[(size_t)j * prm.n + i] = v;
+                            P.out64[(size_t)i * n + j] = v;
+                            if (i != j) P.out64[(size_t)j * n + i] = v;
                         }
                     }
                 }
                 // digit planes of the output (next step's operand)
-                if (prm.out) {
+                if (P.out) {
                     df z[16];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) z[c] = df_scale(Ov[c], prm.out_digit_scale);
+                    for (int c = 0; c < 16; ++c) z[c] = df_scale(Ov[c], P.out_digit_scale);
                     float plane_scale = 1.f;
-                    const float rs = prm.out_rscale, rinv = 1.f / prm.out_rscale;
-                    for (int p = 0; p < prm.s_out; ++p) {
+                    const float rs = P.out_rscale, rinv = 1.f / P.out_rscale;
+                    for (int p = 0; p < P.s_out; ++p) {
                         __align__(16) __nv_bfloat16 dv[16];
 #pragma unroll
                         for (int c = 0; c < 16; ++c) {
@@ -525,36 +562,36 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
                             dv[c] = __float2bfloat16_rn(d * plane_scale);
                         }
                         plane_scale *= rinv;
-                        __nv_bfloat16* dst = prm.out + p * plane;
+                        __nv_bfloat16* dst = P.out + p * plane;
                         if (!diag_tile) {
-                            uint4* row = (uint4*)(dst + (size_t)i * prm.n_pad + jb);
+                            uint4* row = (uint4*)(dst + (size_t)i * n_pad + jb);
                             row[0] = ((const uint4*)dv)[0];
                             row[1] = ((const uint4*)dv)[1];
 #pragma unroll
-                            for (int c = 0; c < 16; ++c) dst[(size_t)(jb + c) * prm.n_pad + i] = dv[c];
+                            for (int c = 0; c < 16; ++c) dst[(size_t)(jb + c) * n_pad + i] = dv[c];
                         } else {
 #pragma unroll
                             for (int c = 0; c < 16; ++c) {
                                 const int j = jb + c;
                                 if (i <= j) {
-                                    dst[(size_t)i * prm.n_pad + j] = dv[c];
-                                    if (i != j) dst[(size_t)j * prm.n_pad + i] = dv[c];
+                                    dst[(size_t)i * n_pad + j] = dv[c];
+                                    if (i != j) dst[(size_t)j * n_pad + i] = dv[c];
                                 }
                             }
                         }
                     }
                 }
             }
-        }
-        if (prm.red) {
+            if (P.red) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s_tr += __shfl_xor_sync(0xffffffffu, s_tr, o);
-            s_idem = warp_sum_f(s_idem);
-            s_fro = warp_sum_f(s_fro);
-            if (lane == 0) {
-                atomicAdd(&prm.red[0], s_tr);
-                atomicAdd(&prm.red[1], (double)s_idem);
-                atomicAdd(&prm.red[2], (double)s_fro);
+                for (int o = 16; o > 0; o >>= 1) s_tr += __shfl_xor_sync(0xffffffffu, s_tr, o);
+                s_idem = warp_sum_f(s_idem);
+                s_fro = warp_sum_f(s_fro);
+                if (lane == 0) {
+                    atomicAdd(&P.red[0], s_tr);
+                    atomicAdd(&P.red[1], (double)s_idem);
+                    atomicAdd(&P.red[2], (double)s_fro);
+                }
             }
         }
     }
@@ -567,7 +604,7 @@ digit_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constan
     }
 }
 
-typedef void (*KernelFn)(const CUtensorMap, const CUtensorMap, const DigitGemmParams, int, int);
+typedef void (*KernelFn)(const DigitLaunch);
 
 // Kernel pointers of the instantiations in digits_k<KC><lo|hi>.cu.
 KernelFn kernel_k32_lo(int s);

@@ -139,53 +139,87 @@ int prepare_kernel(KernelFn fn) {
     return PURIFY_OK;
 }
 
-int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
+int prepare_digit_kernels() {
+    for (int kc : {32, 64})
+        for (int s = 1; s <= kMaxDigitPlanes; ++s) {
+            KernelFn fn = kernel_for(kc, s);
+            if (fn) PURIFY_TRY(prepare_kernel(fn));
+        }
+    return PURIFY_OK;
+}
+
+int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, CUtensorMap* mb) {
     if (st.s_in < 1 || st.s_in > kMaxDigitPlanes || st.s_out < 0 || st.s_out > kMaxDigitPlanes)
         return PURIFY_ERR_INVALID_ARG;
     if (st.n <= 0 || st.n_pad % TILE || st.n > st.n_pad) return PURIFY_ERR_INVALID_ARG;
     if (st.rbits < 4 || st.rbits > 8) return PURIFY_ERR_INVALID_ARG;
     const int kc = digit_kc(st.s_in);
-    if (digit_stages(st.s_in, kc) < 1) return PURIFY_ERR_INVALID_ARG;
-    CUtensorMap ma, mb;
-    PURIFY_TRY(make_plane_map(&ma, st.A, st.n_pad, st.s_in, kc));
-    PURIFY_TRY(make_plane_map(&mb, st.B, st.n_pad, st.s_in, kc));
-    DigitGemmParams p;
-    std::memset(&p, 0, sizeof(p));
-    p.n = st.n;
-    p.n_pad = st.n_pad;
-    p.s_in = st.s_in;
-    p.s_out = st.out ? st.s_out : 0;
-    p.tiles_per_row = st.n_pad / TILE;
-    p.scale_in_h = ldexpf(1.f, st.eA + st.eB - 16);
-    p.e_scale = ldexpf(1.f, st.eA - 8);
-    p.out_digit_scale = ldexpf(1.f, 8 - st.e_out);
-    p.out_rscale = ldexpf(1.f, st.rbits);
-    p.cP = to_df(st.cP);
-    p.cE = to_df(st.cE);
-    p.cI = to_df(st.cI);
-    p.dY = to_df(st.dY);
-    p.dI = to_df(st.dI);
-    p.use_E = st.use_E;
-    p.affine_out = !(st.dY == 1.0 && st.dI == 0.0);
-    p.scratch = st.scratch;
-    p.A = st.A;
-    p.out = st.out;
-    p.out64 = st.out64;
-    p.red = st.red;
-    p.err = st.err;
-    const int stages = digit_stages(st.s_in, kc);
-    const size_t smem = digit_smem_bytes(st.s_in, kc);
-    const int T = st.n_pad / TILE;
-    const int tiles = T * (T + 1) / 2;
-    const int grid = tiles < st.max_ctas ? tiles : st.max_ctas;
-    if (!st.scratch || grid < 1) return PURIFY_ERR_INVALID_ARG;
-    KernelFn fn = kernel_for(kc, st.s_in);
-    if (!fn) return PURIFY_ERR_INVALID_ARG;
+    PURIFY_TRY(make_plane_map(ma, st.A, st.n_pad, st.s_in, kc));
+    PURIFY_TRY(make_plane_map(mb, st.B, st.n_pad, st.s_in, kc));
+    std::memset(p, 0, sizeof(*p));
+    p->n = st.n;
+    p->n_pad = st.n_pad;
+    p->s_in = st.s_in;
+    p->s_out = st.out ? st.s_out : 0;
+    p->tiles_per_row = st.n_pad / TILE;
+    p->scale_in_h = ldexpf(1.f, st.eA + st.eB - 16);
+    p->e_scale = ldexpf(1.f, st.eA - 8);
+    p->out_digit_scale = ldexpf(1.f, 8 - st.e_out);
+    p->out_rscale = ldexpf(1.f, st.rbits);
+    p->cP = to_df(st.cP);
+    p->cE = to_df(st.cE);
+    p->cI = to_df(st.cI);
+    p->dY = to_df(st.dY);
+    p->dI = to_df(st.dI);
+    p->use_E = st.use_E;
+    p->affine_out = !(st.dY == 1.0 && st.dI == 0.0);
+    p->A = st.A;
+    p->out = st.out;
+    p->out64 = st.out64;
+    p->red = st.red;
+    return PURIFY_OK;
+}
+
+static int launch_kernel(const DigitLaunch& L, int s, int grid, cudaStream_t stream) {
+    const int kc = digit_kc(s);
+    KernelFn fn = kernel_for(kc, s);
+    if (!fn || grid < 1 || L.stages < 1) return PURIFY_ERR_INVALID_ARG;
     PURIFY_TRY(prepare_kernel(fn));
-    fn<<<grid, NTHREADS, smem, stream>>>(ma, mb, p, stages, tiles);
+    fn<<<grid, NTHREADS, digit_smem_bytes(s, kc), stream>>>(L);
     PURIFY_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return PURIFY_OK;
+}
+
+int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
+    DigitLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    PURIFY_TRY(fill_digit_params(st, &L.one, &L.mapA, &L.mapB));
+    const int T = st.n_pad / TILE;
+    L.num_items = T * (T + 1) / 2;
+    L.stages = digit_stages(st.s_in, digit_kc(st.s_in));
+    L.scratch = st.scratch;
+    L.err = st.err;
+    if (!st.scratch || !st.err) return PURIFY_ERR_INVALID_ARG;
+    const int grid = L.num_items < st.max_ctas ? L.num_items : st.max_ctas;
+    return launch_kernel(L, st.s_in, grid, stream);
+}
+
+int launch_digit_group(int s, const CUtensorMap* maps, const DigitGemmParams* prms, const int4* work,
+                       int num_items, float2* scratch, int max_ctas, int* err, cudaStream_t stream) {
+    if (s < 1 || s > kMaxDigitPlanes || !maps || !prms || !work || !scratch || !err) return PURIFY_ERR_INVALID_ARG;
+    if (num_items <= 0) return PURIFY_OK;
+    DigitLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.maps = maps;
+    L.prms = prms;
+    L.work = work;
+    L.num_items = num_items;
+    L.stages = digit_stages(s, digit_kc(s));
+    L.scratch = scratch;
+    L.err = err;
+    const int grid = num_items < max_ctas ? num_items : max_ctas;
+    return launch_kernel(L, s, grid, stream);
 }
 
 int launch_split(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s,

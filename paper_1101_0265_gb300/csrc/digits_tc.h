@@ -1,6 +1,7 @@
 // Digit-plane tensor-core products (see digits_tc.cu for the representation).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 
 #include "internal.h"
@@ -36,6 +37,22 @@ struct DigitStep {
 inline size_t digit_scratch_bytes(int ctas) { return (size_t)ctas * 128 * 128 * sizeof(float2); }
 
 int launch_digit_step(const DigitStep& st, cudaStream_t stream);
+
+// Opt every product-kernel instantiation into the full shared memory (once
+// per process; call before capturing launches into a graph).
+int prepare_digit_kernels();
+
+namespace dk {
+struct DigitGemmParams;
+}
+// The kernel parameters and the A / B tensor maps of one product (for grouped
+// launches, whose parameters live in device memory).
+int fill_digit_params(const DigitStep& st, dk::DigitGemmParams* p, CUtensorMap* ma, CUtensorMap* mb);
+// One launch over `num_items` work items {g, ti, tj, -} of products whose
+// maps (2 per product), parameters and work list are in device memory; all
+// products have s digits.
+int launch_digit_group(int s, const CUtensorMap* maps, const dk::DigitGemmParams* prms, const int4* work,
+                       int num_items, float2* scratch, int max_ctas, int* err, cudaStream_t stream);
 
 // out planes of a F + b I (i, j < n; zero padding up to n_pad), exponent e,
 // s digits.  red[0] += trace (float accuracy) when red is not null.

@@ -119,6 +119,11 @@ static int build_schedule(int scheme, double lmin, double lmax, double mu, doubl
     return PURIFY_OK;
 }
 
+int build_schedule_public(int scheme, double lmin, double lmax, double mu, double homo, double lumo,
+                          double tol, int max_iter, Schedule& S) {
+    return build_schedule(scheme, lmin, lmax, mu, homo, lumo, tol, max_iter, S);
+}
+
 // ---------------------------------------------------------------------------
 // Cyclic Jacobi on a small symmetric matrix (Lanczos tridiagonal)
 // ---------------------------------------------------------------------------

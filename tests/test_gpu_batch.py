@@ -1,0 +1,117 @@
+"""GPU tests of the batch engine: many purifications of uneven size in
+grouped tensor-core launches (CUDA graph), and continuous batching.  Every
+result must equal the same purification run alone, bit for bit, and the
+CPU oracle to the mixed path's tolerance."""
+import numpy as np
+import pytest
+
+from oracle import purify_oracle as O
+from paper_1101_0265_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1101_0265_gb300 import build
+    build.build()
+    import paper_1101_0265_gb300 as P
+    return P
+
+
+SPECS = [  # n, nocc, gap, scheme
+    (64, 20, 0.05, "TC_SF"), (100, 61, 0.002, "FIXED_MU_SF"), (129, 64, 0.01, "TC_SF"),
+    (200, 77, 0.1, "TC_MONO"), (256, 128, 1e-3, "TC_SF"), (300, 150, 0.02, "FIXED_MU_SF"),
+    (383, 200, 0.05, "FIXED_MU_MONO"), (511, 300, 0.004, "TC_SF"), (640, 320, 0.03, "TC_SF"),
+    (77, 30, 0.2, "FIXED_MU_SF"),
+]
+
+
+def _hams():
+    return [I.dense_hamiltonian(n, nocc, gap, config=60, instance=i) for i, (n, nocc, gap, _) in
+            enumerate(SPECS)]
+
+
+def _alone(P, h, scheme, tol):
+    pur = P.Purifier(precision="mixed")
+    pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+    pur.run(scheme, tol, 300)
+    D = pur.density()
+    st = pur.stats()
+    pur.close()
+    return D, st
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_equals_alone_and_oracle(P, use_graph):
+    hs = _hams()
+    tol = 1e-10
+    B = P.Batch()
+    ids = [B.add(h.F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme=sp[3], tol=tol, mu=0.0)
+           for h, sp in zip(hs, SPECS)]
+    for rep in range(2):  # the second run replays the captured graph
+        B.run(use_graph=use_graph)
+        for i, h, sp in zip(ids, hs, SPECS):
+            assert B.done(i)
+            D = B.density(i)
+            Da, sta = _alone(P, h, sp[3], tol)
+            assert np.array_equal(D, Da), (sp, np.max(np.abs(D - Da)))
+            st = B.stats(i)
+            assert st["iterations"] == sta["iterations"]
+            assert st["multiplications"] == sta["multiplications"]
+            assert abs(st["trace"] - h.nocc) < 1e-6
+            if rep == 0:
+                Do, r = O.purify(h.F, sp[3], h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo,
+                                 tol=tol)
+                assert st["iterations"] == r.iterations
+                assert np.max(np.abs(D - Do)) <= 3e-7
+    B.close()
+
+
+def test_continuous_batching_equals_alone(P):
+    # requests arrive while others are running: admit two, step, admit three
+    # more, step ... ; results are those of each request alone
+    hs = _hams()
+    tol = 1e-9
+    B = P.Batch()
+    pending = list(range(len(hs)))
+    live = {}
+    rounds = 0
+    while pending or live:
+        for _ in range(min(2 + rounds % 2, len(pending))):
+            k = pending.pop(0)
+            h = hs[k]
+            live[k] = B.add(h.F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme=SPECS[k][3], tol=tol,
+                            mu=0.0)
+        active, finished = B.step()
+        rounds += 1
+        for k, i in list(live.items()):
+            if B.done(i):
+                D = B.density(i)
+                Da, _ = _alone(P, hs[k], SPECS[k][3], tol)
+                assert np.array_equal(D, Da), SPECS[k]
+                before = B.bytes_in_use()
+                B.release(i)
+                assert B.bytes_in_use() < before
+                del live[k]
+        assert rounds < 500
+    assert B.bytes_in_use() == 0
+    B.close()
+
+
+def test_batch_device_inputs_and_footprint(P):
+    h = I.dense_hamiltonian(300, 100, 0.05, config=61)
+    B = P.Batch()
+    Fd = torch.from_numpy(h.F).cuda()
+    i = B.add(Fd, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme="TC_SF", tol=1e-9)
+    assert 0 < B.bytes_in_use() <= P.batch_footprint(300)
+    B.run()
+    Dd = torch.empty((300, 300), dtype=torch.float64, device="cuda")
+    B.density(i, Dd)
+    Da, _ = _alone(P, h, "TC_SF", 1e-9)
+    assert np.array_equal(Dd.cpu().numpy(), Da)
+    with pytest.raises(P.PurifyError):
+        B.add(h.F, h.nocc, h.lmin, h.lmax, h.lumo, h.homo)       # homo > lumo
+    B.close()
