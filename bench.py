@@ -51,6 +51,10 @@ def parse():
                     help="use the first K matrices of the sweep (profiling / small runs)")
     ap.add_argument("--schemes", default=",".join(SCHEMES))
     ap.add_argument("--no-fp64-check", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-size", type=int, default=256)
+    ap.add_argument("--serve-rates", default="30", help="comma list; empty to skip serving")
+    ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -64,6 +68,99 @@ def make_inputs(n, rank, count=None):
     specs = workload_specs(n)[:count]
     return [I.dense_hamiltonian(n, nocc, gap, config=2, instance=1000 * rank + i)
             for i, (nocc, gap) in enumerate(specs)]
+
+
+def make_device_inputs(n, rank, count, dev):
+    """The same sweep built on the GPU (torch QR); F stays on the device."""
+    from paper_1101_0265_gb300 import inputs as I
+    hs, Fs = [], []
+    for i, (nocc, gap) in enumerate(workload_specs(n)[:count]):
+        spec = I.InstanceSpec(n=n, nocc=nocc, gap=gap, scheme="TC_SF", instance=1000 * rank + i,
+                              config=2)
+        F, h = I.dense_hamiltonian_device(spec, dev)
+        hs.append(h)
+        Fs.append(F)
+    return hs, Fs
+
+
+def run_batch(P, dev, stream, count=256, reps=3, tol=1e-9):
+    """The batch workload: `count` dense Hamiltonians, n log-uniform in
+    [64, 2048], gap log-uniform in [1e-3, 1e-1], nocc = round(U(0.3, 0.7) n),
+    TC_SF, all in one CUDA-graph replay of grouped launches."""
+    import torch
+    from paper_1101_0265_gb300 import inputs as I
+    specs = I.batch_specs(count)
+    B = P.Batch(device=dev.index, stream=stream.cuda_stream)
+    ids, metas = [], []
+    for sp in specs:
+        F, h = I.dense_hamiltonian_device(sp, dev)
+        ids.append(B.add(F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme="TC_SF", tol=tol, mu=0.0))
+        metas.append(h)
+        del F
+    torch.cuda.synchronize(dev)
+    B.run(use_graph=True)        # capture + first replay (warm-up)
+    times = []
+    for _ in range(reps):
+        B.run(use_graph=True)
+        times.append(B.stats(ids[0])["seconds"])
+    t = statistics.median(times)
+    st = [B.stats(i) for i in ids]
+    B.close()
+    tensor = sum(x["tensor_flops"] for x in st)
+    return {"workload": f"{count} dense F, n log-uniform [64, 2048], gap log-uniform [1e-3, 1e-1], "
+                        f"TC_SF tol {tol:g}, one CUDA-graph replay per batch",
+            "value": count / t, "unit": "purifications/s", "ms_per_batch": 1e3 * t,
+            "replays": reps, "tensor_tflops": tensor / t / 1e12,
+            "multiplications": sum(x["multiplications"] for x in st),
+            "max_trace_err": max(x["trace_err"] for x in st)}
+
+
+def run_serve(P, dev, stream, rate, count, budget_gb=64.0, tol=1e-9):
+    """Continuous batching under Poisson arrivals: requests (n log-uniform in
+    [128, 8192], gap log-uniform in [1e-4, 1e-1], half FIXED_MU_SF, half
+    TC_SF) are admitted while the HBM budget allows, every round advances all
+    admitted requests by one product, finished ones are read out and freed.
+    Latency is arrival -> density available."""
+    import torch
+    from collections import deque
+    from paper_1101_0265_gb300 import inputs as I
+    specs = I.serve_specs(rate, count)
+    reqs = [I.dense_hamiltonian_device(sp, dev) for sp in specs]   # untimed
+    torch.cuda.synchronize(dev)
+    B = P.Batch(device=dev.index, stream=stream.cuda_stream)
+    budget = budget_gb * 2 ** 30
+    pending = deque(range(count))
+    live, lat, rounds, peak_live = {}, [], 0, 0
+    t0 = time.perf_counter()
+    while pending or live:
+        now = time.perf_counter() - t0
+        while pending and specs[pending[0]].arrival <= now:
+            k = pending[0]
+            if live and B.bytes_in_use() + P.batch_footprint(specs[k].n) > budget:
+                break
+            F, h = reqs[k]
+            live[B.add(F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme=specs[k].scheme, tol=tol,
+                       mu=0.0)] = k
+            pending.popleft()
+        if not live:
+            time.sleep(max(0.0, specs[pending[0]].arrival - (time.perf_counter() - t0)))
+            continue
+        peak_live = max(peak_live, len(live))
+        B.step()
+        rounds += 1
+        t = time.perf_counter() - t0
+        for i, k in list(live.items()):
+            if B.done(i):
+                lat.append(t - specs[k].arrival)
+                B.release(i)
+                del live[i]
+    total = time.perf_counter() - t0
+    B.close()
+    lat.sort()
+    pct = lambda q: 1e3 * lat[min(len(lat) - 1, int(q * len(lat)))]
+    return {"rate_per_s": rate, "requests": count, "p50_ms": pct(0.50), "p99_ms": pct(0.99),
+            "max_ms": 1e3 * lat[-1], "throughput_per_s": count / total, "rounds": rounds,
+            "peak_concurrent": peak_live, "hbm_budget_gb": budget_gb}
 
 
 def peaks():
@@ -131,12 +228,12 @@ class ClockSampler:
                 "sm_mhz_min": min(sm)}
 
 
-def cpu_baseline(hs, tol):
+def cpu_baseline(hs, F0, tol):
     """The oracle as it stands, on a bounded sample: one purification."""
     from oracle import purify_oracle as O
     h = hs[0]
     t0 = time.perf_counter()
-    O.purify(h.F, "TC_SF", h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=tol)
+    O.purify(F0, "TC_SF", h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=tol)
     dt = time.perf_counter() - t0
     return {"value": 1.0 / dt, "unit": "matrices/s", "cores": _blas_threads(), "kind": "oracle",
             "sample": f"1 purification (TC_SF, n={h.n}, nocc={h.nocc}, gap={h.meta['gap']:g}, "
@@ -219,9 +316,8 @@ def main():
     dev = torch.device("cuda", local)
     n = args.n
     schemes = tuple(args.schemes.split(","))
-    hs = make_inputs(n, rank, args.matrices)
-    Fd = [torch.from_numpy(h.F).to(dev) for h in hs]
-    Fh = [torch.from_numpy(h.F).pin_memory() for h in hs]
+    hs, Fd = make_device_inputs(n, rank, args.matrices, dev)
+    Fh = [F.cpu().pin_memory() for F in Fd]
     Dh = torch.empty((n, n), dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream(dev)
     pur = P.Purifier(device=local, stream=stream.cuda_stream, precision=args.precision,
@@ -350,8 +446,13 @@ def main():
         line["max_err_vs_fp64"] = worst
         line["fp64_path"] = {"value": per_step / t64, "unit": "matrices/s",
                              "note": "same schedules through the float64 SIMT path, same GPU"}
+    if world == 1 and args.precision == "mixed" and not args.no_batch:
+        line["batch"] = run_batch(P, dev, stream, count=args.batch_size)
+    if world == 1 and args.precision == "mixed" and args.serve_rates:
+        line["serve"] = [run_serve(P, dev, stream, float(r), args.serve_requests)
+                         for r in args.serve_rates.split(",")]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(hs, args.tol)
+        line["cpu_baseline"] = cpu_baseline(hs, Fh[0].numpy(), args.tol)
     pur.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -121,10 +121,14 @@ typedef struct purify_stats_t {
 /* Fill *opt with the defaults above. */
 void purify_options_default(purify_options* opt);
 
-/* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t
- * owned by the caller, or NULL to let the handle create its own non-blocking
- * stream.  `opt` may be NULL (defaults).  Fails with PURIFY_ERR_UNSUPPORTED
- * if the device is not compute capability 10.3. */
+/* Create a handle on CUDA device `device`.  `cuda_stream` is the caller's
+ * cudaStream_t (NULL = the legacy default stream).  The handle queues its
+ * work on a private non-blocking stream; every call first orders that stream
+ * after the work the caller has queued on `cuda_stream` (device inputs
+ * produced there are complete when the handle reads them) and, before it
+ * returns, orders `cuda_stream` after the handle's work.  `opt` may be NULL
+ * (defaults).  Fails with PURIFY_ERR_UNSUPPORTED if the device is not compute
+ * capability 10.3. */
 int purify_create(purify_t* h, int device, void* cuda_stream, const purify_options* opt);
 
 /* Release the handle and all device memory it owns.  NULL is accepted. */
@@ -222,8 +226,10 @@ typedef struct purify_batch* purify_batch_t;
  * three sets of up to 6 digit planes), for admission control. */
 int64_t purify_batch_footprint(int64_t n);
 
-/* Create / destroy a batch on `device` (stream: caller-owned cudaStream_t or
- * NULL).  opt->digits fixes the digit count (0: from the mapped gap). */
+/* Create / destroy a batch on `device`.  `cuda_stream` is the caller's stream
+ * (NULL = legacy default), joined as for purify_create; the batch's own
+ * private stream is the one its CUDA graph is captured on.  opt->digits fixes
+ * the digit count (0: from the mapped gap). */
 int purify_batch_create(purify_batch_t* b, int device, void* cuda_stream, const purify_options* opt);
 int purify_batch_destroy(purify_batch_t b);
 

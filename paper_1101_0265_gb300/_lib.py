@@ -149,8 +149,23 @@ def _ptr(x) -> int:
 
 
 def _stream_of(x=None) -> int | None:
+    """torch's current stream on the current device (0 = legacy default)."""
     import torch
     return torch.cuda.current_stream().cuda_stream
+
+
+def _caller_stream(stream):
+    """The stream a handle is joined to: the given one, else torch's current
+    stream when torch has CUDA, else the legacy default stream (None)."""
+    if stream is not None:
+        return int(stream) or None
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream or None
+    except Exception:
+        pass
+    return None
 
 
 def _nan(v):
@@ -178,7 +193,8 @@ class Purifier:
         self.options.digits = digits
         self.options.time_products = int(time_products)
         h = C.c_void_p()
-        _check(lib.purify_create(C.byref(h), device, stream, C.byref(self.options)), "purify_create")
+        _check(lib.purify_create(C.byref(h), device, _caller_stream(stream), C.byref(self.options)),
+               "purify_create")
         self._h = h
         self.n = 0
 
@@ -366,7 +382,8 @@ class Batch:
         lib.purify_options_default(C.byref(o))
         o.digits = digits
         h = C.c_void_p()
-        _check(lib.purify_batch_create(C.byref(h), device, stream, C.byref(o)), "purify_batch_create")
+        _check(lib.purify_batch_create(C.byref(h), device, _caller_stream(stream), C.byref(o)),
+               "purify_batch_create")
         self._h = h
         self.sizes = {}
 

@@ -11,6 +11,7 @@
 // iteration counts and drop out of later rounds.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -68,7 +69,9 @@ void free_instance(Instance& in) {
 
 struct purify_batch {
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // private, non-blocking (capturable)
+    cudaStream_t user_stream = nullptr;  // the caller's stream (null = legacy default)
+    cudaEvent_t join_ev = nullptr;
     bool own_stream = false;
     purify_options opt{};
     int ctas = 0;
@@ -221,64 +224,62 @@ int ensure_dev(purify_batch* B, size_t bytes) {
     return PURIFY_OK;
 }
 
-// One group (common digit count) of one round, laid out at `off` in the
-// staging buffers: maps | params | work.
+// One grouped launch of one round: up to kGroupMax products with a common
+// digit count; their work list is staged at work_off.
 struct GroupPlan {
     int s = 0;
-    size_t off = 0, maps_off = 0, prms_off = 0, work_off = 0;
+    std::vector<DigitStep> steps;
+    size_t work_off = 0;
     int items = 0;
 };
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Stage the grouped launches of one round (the next product of every listed
-// instance) into host_buf starting at `off`; append the group plans.
+// instance): work lists into host_buf from `off`; append the group plans.
 int stage_round(purify_batch* B, const std::vector<Instance*>& act, size_t& off, std::vector<GroupPlan>& groups) {
     for (int s = 1; s <= kMaxDigitPlanes; ++s) {
-        std::vector<Instance*> mem;
+        std::vector<Instance*> all_s;
         for (Instance* in : act)
-            if (in->steps[in->k].s_in == s) mem.push_back(in);
-        if (mem.empty()) continue;
+            if (in->steps[in->k].s_in == s) all_s.push_back(in);
+        if (all_s.empty()) continue;
         // largest products first: long work items are handed out before short ones
-        std::stable_sort(mem.begin(), mem.end(), [](Instance* a, Instance* b) { return a->n_pad > b->n_pad; });
-        GroupPlan g;
-        g.s = s;
-        g.maps_off = align_up(off, 128);
-        g.prms_off = align_up(g.maps_off + 2 * sizeof(CUtensorMap) * mem.size(), 128);
-        size_t items = 0;
-        for (Instance* in : mem) {
-            const int T = in->n_pad / 128;
-            items += (size_t)T * (T + 1) / 2;
+        std::stable_sort(all_s.begin(), all_s.end(), [](Instance* a, Instance* b) { return a->n_pad > b->n_pad; });
+        for (size_t c0 = 0; c0 < all_s.size(); c0 += kGroupMax) {
+            const size_t c1 = std::min(all_s.size(), c0 + (size_t)kGroupMax);
+            GroupPlan g;
+            g.s = s;
+            std::vector<std::vector<int4>> per;
+            size_t items = 0;
+            for (size_t k = c0; k < c1; ++k) {
+                Instance* in = all_s[k];
+                const int gi = (int)(k - c0);
+                g.steps.push_back(in->steps[in->k]);
+                const int T = in->n_pad / 128;
+                per.emplace_back();
+                for (int tj = 0; tj < T; ++tj)
+                    for (int ti = 0; ti <= tj; ++ti) per.back().push_back(make_int4(gi, ti, tj, 0));
+                items += per.back().size();
+            }
+            g.work_off = align_up(off, 128);
+            const size_t end = g.work_off + sizeof(int4) * items;
+            if (B->host_buf.size() < end) B->host_buf.resize(end * 2);
+            int4* work = (int4*)(B->host_buf.data() + g.work_off);
+            // interleaved by tile rank so the persistent CTAs start on large products
+            size_t w = 0;
+            for (size_t r = 0;; ++r) {
+                bool any = false;
+                for (size_t gi = 0; gi < per.size(); ++gi)
+                    if (r < per[gi].size()) {
+                        work[w++] = per[gi][r];
+                        any = true;
+                    }
+                if (!any) break;
+            }
+            g.items = (int)items;
+            off = end;
+            groups.push_back(std::move(g));
         }
-        g.work_off = align_up(g.prms_off + sizeof(dk::DigitGemmParams) * mem.size(), 128);
-        const size_t end = g.work_off + sizeof(int4) * items;
-        if (B->host_buf.size() < end) B->host_buf.resize(end * 2);
-        CUtensorMap* maps = (CUtensorMap*)(B->host_buf.data() + g.maps_off);
-        dk::DigitGemmParams* prms = (dk::DigitGemmParams*)(B->host_buf.data() + g.prms_off);
-        int4* work = (int4*)(B->host_buf.data() + g.work_off);
-        // work items: tiles of all members, interleaved by tile rank so that
-        // the persistent CTAs start on large products
-        std::vector<std::vector<int4>> per(mem.size());
-        for (size_t gi = 0; gi < mem.size(); ++gi) {
-            PURIFY_TRY(fill_digit_params(mem[gi]->steps[mem[gi]->k], &prms[gi], &maps[2 * gi], &maps[2 * gi + 1]));
-            const int T = mem[gi]->n_pad / 128;
-            for (int tj = 0; tj < T; ++tj)
-                for (int ti = 0; ti <= tj; ++ti) per[gi].push_back(make_int4((int)gi, ti, tj, 0));
-        }
-        size_t w = 0;
-        for (size_t r = 0;; ++r) {
-            bool any = false;
-            for (size_t gi = 0; gi < mem.size(); ++gi)
-                if (r < per[gi].size()) {
-                    work[w++] = per[gi][r];
-                    any = true;
-                }
-            if (!any) break;
-        }
-        g.items = (int)items;
-        g.off = g.maps_off;
-        off = end;
-        groups.push_back(g);
     }
     return PURIFY_OK;
 }
@@ -286,10 +287,8 @@ int stage_round(purify_batch* B, const std::vector<Instance*>& act, size_t& off,
 int launch_groups(purify_batch* B, const std::vector<GroupPlan>& groups) {
     const uint8_t* dev = (const uint8_t*)B->dev_buf;
     for (const GroupPlan& g : groups)
-        PURIFY_TRY(launch_digit_group(g.s, (const CUtensorMap*)(dev + g.maps_off),
-                                      (const dk::DigitGemmParams*)(dev + g.prms_off),
-                                      (const int4*)(dev + g.work_off), g.items, B->scratch, B->ctas, B->err,
-                                      B->stream));
+        PURIFY_TRY(launch_digit_group(g.s, g.steps.data(), (int)g.steps.size(), (const int4*)(dev + g.work_off),
+                                      g.items, B->scratch, B->ctas, B->err, B->stream));
     return PURIFY_OK;
 }
 
@@ -336,13 +335,16 @@ int purify_batch_create(purify_batch_t* out, int device, void* cuda_stream, cons
     B->device = device;
     B->opt = o;
     B->ctas = prop.multiProcessorCount;
-    int r = PURIFY_OK;
-    if (cuda_stream) {
-        B->stream = (cudaStream_t)cuda_stream;
-    } else {
-        if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) r = PURIFY_ERR_CUDA;
-        B->own_stream = (r == PURIFY_OK);
+    if (const char* e = getenv("PURIFY_BATCH_MAX_CTAS")) {  // share the device: cap the persistent grid
+        const int cap = atoi(e);
+        if (cap > 0 && cap < B->ctas) B->ctas = cap;
     }
+    int r = PURIFY_OK;
+    B->user_stream = (cudaStream_t)cuda_stream;
+    if (cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking) != cudaSuccess) r = PURIFY_ERR_CUDA;
+    B->own_stream = (r == PURIFY_OK);
+    if (r == PURIFY_OK && cudaEventCreateWithFlags(&B->join_ev, cudaEventDisableTiming) != cudaSuccess)
+        r = PURIFY_ERR_CUDA;
     if (r == PURIFY_OK && (cudaMalloc(&B->scratch, digit_scratch_bytes(B->ctas)) != cudaSuccess ||
                            cudaMalloc(&B->err, sizeof(int)) != cudaSuccess))
         r = PURIFY_ERR_OOM;
@@ -373,6 +375,7 @@ int purify_batch_destroy(purify_batch_t B) {
     cudaFree(B->dev_buf);
     if (B->e0) cudaEventDestroy(B->e0);
     if (B->e1) cudaEventDestroy(B->e1);
+    if (B->join_ev) cudaEventDestroy(B->join_ev);
     if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
     delete B;
     return PURIFY_OK;
@@ -389,6 +392,7 @@ int purify_batch_add(purify_batch_t B, const double* F, int64_t n, int64_t ld, i
         return PURIFY_ERR_BOUNDS;
     if (nocc > n) return PURIFY_ERR_INVALID_ARG;
     PURIFY_CUDA_TRY(cudaSetDevice(B->device));
+    PURIFY_TRY(join_streams(B->stream, B->user_stream, B->join_ev));
     Instance* in = new (std::nothrow) Instance();
     if (!in) return PURIFY_ERR_OOM;
     in->n = (int)n;
@@ -453,7 +457,7 @@ int purify_batch_add(purify_batch_t B, const double* F, int64_t n, int64_t ld, i
     B->inst.push_back(in);
     B->bytes_in_use += in->bytes;
     *id = in->id;
-    return PURIFY_OK;
+    return join_streams(B->user_stream, B->stream, B->join_ev);
 }
 
 // One round: queue the f_0 split of pending instances, then one product of
@@ -461,6 +465,7 @@ int purify_batch_add(purify_batch_t B, const double* F, int64_t n, int64_t ld, i
 int purify_batch_step(purify_batch_t B, int* active_out, int* finished_out) {
     if (!B) return PURIFY_ERR_INVALID_ARG;
     PURIFY_CUDA_TRY(cudaSetDevice(B->device));
+    PURIFY_TRY(join_streams(B->stream, B->user_stream, B->join_ev));
     std::vector<Instance*> act;
     for (Instance* in : B->inst) {
         if (!in || in->state >= 2 || in->state < 0) continue;
@@ -490,7 +495,7 @@ int purify_batch_step(purify_batch_t B, int* active_out, int* finished_out) {
     }
     if (active_out) *active_out = (int)act.size() - finished;
     if (finished_out) *finished_out = finished;
-    return PURIFY_OK;
+    return join_streams(B->user_stream, B->stream, B->join_ev);
 }
 
 // Run every added instance from its start to completion.  With use_graph,
@@ -499,6 +504,7 @@ int purify_batch_step(purify_batch_t B, int* active_out, int* finished_out) {
 int purify_batch_run(purify_batch_t B, int use_graph) {
     if (!B) return PURIFY_ERR_INVALID_ARG;
     PURIFY_CUDA_TRY(cudaSetDevice(B->device));
+    PURIFY_TRY(join_streams(B->stream, B->user_stream, B->join_ev));
     std::vector<Instance*> all;
     std::vector<int> ids;
     for (Instance* in : B->inst)
@@ -566,7 +572,7 @@ int purify_batch_run(purify_batch_t B, int use_graph) {
         in->k = (int)in->steps.size();
         finish_instance(*in);
     }
-    return PURIFY_OK;
+    return join_streams(B->user_stream, B->stream, B->join_ev);
 }
 
 int purify_batch_status(purify_batch_t B, int id) {
@@ -580,10 +586,11 @@ int purify_batch_get_density(purify_batch_t B, int id, double* D, int64_t ld) {
     if (ld < in->n) return PURIFY_ERR_INVALID_ARG;
     if (in->state != 2) return PURIFY_ERR_STATE;
     PURIFY_CUDA_TRY(cudaSetDevice(B->device));
+    PURIFY_TRY(join_streams(B->stream, B->user_stream, B->join_ev));
     PURIFY_CUDA_TRY(cudaMemcpy2DAsync(D, sizeof(double) * ld, in->D, sizeof(double) * in->n,
                                       sizeof(double) * in->n, in->n, cudaMemcpyDefault, B->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(B->stream));
-    return PURIFY_OK;
+    return join_streams(B->user_stream, B->stream, B->join_ev);
 }
 
 int purify_batch_stats(purify_batch_t B, int id, purify_stats_t* st) {

@@ -226,15 +226,21 @@ struct DigitGemmParams {
     double* red;             // [0] trace(Y), [1] ||E - P||_F^2, [2] ||Y||_F^2 (atomics) or null
 };
 
-// One launch: either a single product (maps and parameters by value, tiles
-// in banded order) or a group of products of different sizes (tensor maps,
-// parameters and the list of work items in global memory).
+// Products per launch whose tensor maps and parameters travel as kernel
+// parameters (grid constants).  TMA reads a tensor map written to global
+// memory by the host through a proxy that is not ordered with that write;
+// maps reused at the same address across launches were seen stale, so no
+// launch takes its maps from global memory.
+constexpr int GMAX = 64;
+
+// One launch: products g = 0 .. ngroups-1 (tensor maps and parameters by
+// value) and the list of work items {g, ti, tj, -} in global memory, or, when
+// `work` is null, all upper tiles of product 0 in banded order.
 struct DigitLaunch {
-    CUtensorMap mapA, mapB;          // single product
-    DigitGemmParams one;             // single product
-    const CUtensorMap* maps;         // group: A and B map of product g at [2g], [2g + 1]
-    const DigitGemmParams* prms;     // group: parameters of product g
-    const int4* work;                // group: {g, ti, tj, -} per work item
+    CUtensorMap maps[2 * GMAX];      // A and B map of product g at [2g], [2g + 1]
+    DigitGemmParams prms[GMAX];
+    int ngroups;
+    const int4* work;
     int num_items;                   // tiles (single) or work items (group)
     int stages;                      // depth of the shared-memory ring
     float2* scratch;                 // per CTA 128 x 128 double-float tile
@@ -251,12 +257,12 @@ __device__ __forceinline__ void item_of(const DigitLaunch& L, int t, int& g, int
         tj = w.z;
     } else {
         g = 0;
-        decode_banded(t, L.one.tiles_per_row, ti, tj);
+        decode_banded(t, L.prms[0].tiles_per_row, ti, tj);
     }
 }
 
 __device__ __forceinline__ const DigitGemmParams& params_of(const DigitLaunch& L, int g) {
-    return L.prms ? L.prms[g] : L.one;
+    return L.prms[g];
 }
 
 // Tile t of the upper triangle (ti <= tj) of a T x T tile grid, in bands of
@@ -347,8 +353,8 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                 int g, ti, tj;
                 item_of(L, t, g, ti, tj);
                 const int nk = params_of(L, g).n_pad / KC;
-                const CUtensorMap* mA = L.maps ? &L.maps[2 * g] : &L.mapA;
-                const CUtensorMap* mB = L.maps ? &L.maps[2 * g + 1] : &L.mapB;
+                const CUtensorMap* mA = &L.maps[2 * g];
+                const CUtensorMap* mB = &L.maps[2 * g + 1];
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int st = it % stages;
                     if (it >= stages && !mbar_wait_for(smem_u32(&empty_bar[st]), (uint32_t)(((it / stages) & 1) ^ 1))) {

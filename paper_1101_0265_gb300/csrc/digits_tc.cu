@@ -194,7 +194,8 @@ static int launch_kernel(const DigitLaunch& L, int s, int grid, cudaStream_t str
 int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
     DigitLaunch L;
     std::memset(&L, 0, sizeof(L));
-    PURIFY_TRY(fill_digit_params(st, &L.one, &L.mapA, &L.mapB));
+    PURIFY_TRY(fill_digit_params(st, &L.prms[0], &L.maps[0], &L.maps[1]));
+    L.ngroups = 1;
     const int T = st.n_pad / TILE;
     L.num_items = T * (T + 1) / 2;
     L.stages = digit_stages(st.s_in, digit_kc(st.s_in));
@@ -205,14 +206,18 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
     return launch_kernel(L, st.s_in, grid, stream);
 }
 
-int launch_digit_group(int s, const CUtensorMap* maps, const DigitGemmParams* prms, const int4* work,
-                       int num_items, float2* scratch, int max_ctas, int* err, cudaStream_t stream) {
-    if (s < 1 || s > kMaxDigitPlanes || !maps || !prms || !work || !scratch || !err) return PURIFY_ERR_INVALID_ARG;
+int launch_digit_group(int s, const DigitStep* steps, int count, const int4* work, int num_items,
+                       float2* scratch, int max_ctas, int* err, cudaStream_t stream) {
+    if (s < 1 || s > kMaxDigitPlanes || count < 1 || count > GMAX || !work || !scratch || !err)
+        return PURIFY_ERR_INVALID_ARG;
     if (num_items <= 0) return PURIFY_OK;
     DigitLaunch L;
     std::memset(&L, 0, sizeof(L));
-    L.maps = maps;
-    L.prms = prms;
+    for (int g = 0; g < count; ++g) {
+        if (steps[g].s_in != s) return PURIFY_ERR_INVALID_ARG;
+        PURIFY_TRY(fill_digit_params(steps[g], &L.prms[g], &L.maps[2 * g], &L.maps[2 * g + 1]));
+    }
+    L.ngroups = count;
     L.work = work;
     L.num_items = num_items;
     L.stages = digit_stages(s, digit_kc(s));

@@ -42,17 +42,14 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream);
 // per process; call before capturing launches into a graph).
 int prepare_digit_kernels();
 
-namespace dk {
-struct DigitGemmParams;
-}
-// The kernel parameters and the A / B tensor maps of one product (for grouped
-// launches, whose parameters live in device memory).
-int fill_digit_params(const DigitStep& st, dk::DigitGemmParams* p, CUtensorMap* ma, CUtensorMap* mb);
-// One launch over `num_items` work items {g, ti, tj, -} of products whose
-// maps (2 per product), parameters and work list are in device memory; all
-// products have s digits.
-int launch_digit_group(int s, const CUtensorMap* maps, const dk::DigitGemmParams* prms, const int4* work,
-                       int num_items, float2* scratch, int max_ctas, int* err, cudaStream_t stream);
+// One launch over `num_items` work items {g, ti, tj, -} (device memory) of
+// `count` <= 64 products that all have s digits; their tensor maps and
+// parameters are passed by value.
+int launch_digit_group(int s, const DigitStep* steps, int count, const int4* work, int num_items,
+                       float2* scratch, int max_ctas, int* err, cudaStream_t stream);
+
+// Products per grouped launch.
+constexpr int kGroupMax = 64;
 
 // out planes of a F + b I (i, j < n; zero padding up to n_pad), exponent e,
 // s digits.  red[0] += trace (float accuracy) when red is not null.

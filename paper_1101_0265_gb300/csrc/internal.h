@@ -80,7 +80,9 @@ struct MixedState;
 // The handle behind purify_t.
 struct purify_ctx {
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;       // private, non-blocking: all library work
+    cudaStream_t user_stream = nullptr;  // the caller's stream (null = legacy default)
+    cudaEvent_t join_ev = nullptr;
     bool own_stream = false;
     purify_options opt{};
     int64_t n = 0, cap = 0;
@@ -104,6 +106,9 @@ struct purify_ctx {
 };
 
 namespace purify {
+// Order `work` after what the caller queued on `user` (join_in) and the
+// caller's stream after the library's work (join_out).
+int join_streams(cudaStream_t after, cudaStream_t before, cudaEvent_t ev);
 // Product timing: bracket one product launch with events when requested.
 int product_begin(purify_ctx* h);
 int product_end(purify_ctx* h);

@@ -234,6 +234,15 @@ int purify::ensure_red(purify_ctx* h, int64_t doubles) {
     return PURIFY_OK;
 }
 
+int purify::join_streams(cudaStream_t after, cudaStream_t before, cudaEvent_t ev) {
+    PURIFY_CUDA_TRY(cudaEventRecord(ev, before));
+    PURIFY_CUDA_TRY(cudaStreamWaitEvent(after, ev, 0));
+    return PURIFY_OK;
+}
+
+static int join_in(purify_ctx* h) { return join_streams(h->stream, h->user_stream, h->join_ev); }
+static int join_out(purify_ctx* h) { return join_streams(h->user_stream, h->stream, h->join_ev); }
+
 int purify::product_begin(purify_ctx* h) {
     if (!h->opt.time_products) return PURIFY_OK;
     const size_t need = 2 * (size_t)h->pev_used + 2;
@@ -312,17 +321,15 @@ int purify_create(purify_t* out, int device, void* cuda_stream, const purify_opt
     h->opt = o;
     int r = set_device(h);
     if (r == PURIFY_OK) {
-        if (cuda_stream) {
-            h->stream = (cudaStream_t)cuda_stream;
-        } else {
-            cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-            if (e != cudaSuccess) r = cuda_status(e, "cudaStreamCreateWithFlags");
-            h->own_stream = (e == cudaSuccess);
-        }
+        h->user_stream = (cudaStream_t)cuda_stream;
+        cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) r = cuda_status(e, "cudaStreamCreateWithFlags");
+        h->own_stream = (e == cudaSuccess);
     }
     if (r == PURIFY_OK) {
         cudaError_t e = cudaEventCreate(&h->e0);
         if (e == cudaSuccess) e = cudaEventCreate(&h->e1);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming);
         if (e != cudaSuccess) r = cuda_status(e, "cudaEventCreate");
     }
     if (r != PURIFY_OK) {
@@ -345,6 +352,7 @@ int purify_destroy(purify_t h) {
     for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
     if (h->e0) cudaEventDestroy(h->e0);
     if (h->e1) cudaEventDestroy(h->e1);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
     return PURIFY_OK;
@@ -371,6 +379,7 @@ int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld, i
     const long long set_launches0 = launches_so_far();
     h->have_F = false;
     h->cur = -1;
+    PURIFY_TRY(join_in(h));
     PURIFY_TRY(ensure_capacity(h, n));
     h->n = n;
     PURIFY_CUDA_TRY(cudaMemcpy2DAsync(h->F, sizeof(double) * n, F, sizeof(double) * ld,
@@ -426,7 +435,7 @@ int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld, i
     h->st.kernel_launches = set_launches;
     h->st.product_seconds = NAN;
     h->have_F = true;
-    return PURIFY_OK;
+    return join_out(h);
 }
 
 // One float64 step with reductions into slot `slot` (4 doubles).
@@ -591,6 +600,7 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
     Schedule S;
     if (have_gap)
         PURIFY_TRY(build_schedule(scheme, bb.lmin, bb.lmax, mu, bb.homo, bb.lumo, tol, max_iter, S));
+    PURIFY_TRY(join_in(h));
     h->cur = -1;
     const long long launches0 = launches_so_far();
     h->pev_used = 0;
@@ -646,6 +656,7 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
     if (status == PURIFY_OK && h->nocc >= 0 && iters > 0 && !(st.trace_err <= 0.5))
         status = PURIFY_ERR_BOUNDS;
     st.status = status;
+    PURIFY_TRY(join_out(h));
     return status;
 }
 
@@ -653,10 +664,11 @@ int purify_get_density(purify_t h, double* D, int64_t ld) {
     if (!h || !D || ld < h->n) return PURIFY_ERR_INVALID_ARG;
     if (h->cur < 0) return PURIFY_ERR_STATE;
     PURIFY_TRY(set_device(h));
+    PURIFY_TRY(join_in(h));
     PURIFY_CUDA_TRY(cudaMemcpy2DAsync(D, sizeof(double) * ld, h->X[h->cur], sizeof(double) * h->n,
                                       sizeof(double) * h->n, h->n, cudaMemcpyDefault, h->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    return PURIFY_OK;
+    return join_out(h);
 }
 
 int purify_stats(purify_t h, purify_stats_t* out) {

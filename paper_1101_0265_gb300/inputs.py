@@ -18,7 +18,9 @@ same mu and gap, so a rotated diagonal matrix is an equally valid test case):
 * ``lattice_hamiltonian``: a cubic tight-binding model with a gap around 0,
   sites ordered by 4x4x2 sub-cubes so that 32-site blocks are spatially
   compact.
-* ``batch_specs`` / ``serve_specs``: many instances of uneven size.
+* ``batch_specs`` / ``serve_specs``: many instances of uneven size;
+  ``dense_hamiltonian_device`` builds one on a CUDA device with torch (same
+  recipe, torch's generator) when thousands of large inputs are needed.
 
 Seeds: every instance draws from ``numpy.random.Generator(PCG64(s))`` with
 ``s = splitmix64(BASE_SEED ^ splitmix64(config) ^ splitmix64(instance + 1))``.
@@ -271,3 +273,25 @@ def serve_specs(rate: float, count: int, n_lo: int = 128, n_hi: int = 8192,
 def instance_hamiltonian(spec: InstanceSpec) -> Hamiltonian:
     return dense_hamiltonian(spec.n, spec.nocc, spec.gap, config=spec.config,
                              instance=spec.instance)
+
+
+def dense_hamiltonian_device(spec: InstanceSpec, device="cuda"):
+    """The dense recipe built on a GPU with torch (Haar Q from a seeded torch
+    generator, spectrum from the numpy generator as above).  Returns
+    (F as a float64 CUDA tensor, Hamiltonian metadata without F / Q)."""
+    import torch
+    rng = rng_for(spec.config, spec.instance)
+    lam = gapped_spectrum(spec.n, spec.nocc, spec.gap, rng)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed_for(spec.config, spec.instance) & ((1 << 63) - 1))
+    Z = torch.randn(spec.n, spec.n, generator=g, dtype=torch.float64, device=device)
+    Q, R = torch.linalg.qr(Z)
+    Q = Q * torch.sign(torch.diagonal(R))[None, :]
+    lt = torch.from_numpy(lam).to(device)
+    F = (Q * lt[None, :]) @ Q.T
+    F = 0.5 * (F + F.T)
+    meta = Hamiltonian(F=None, n=spec.n, nocc=spec.nocc, mu=0.0, lmin=float(lam[0]),
+                       lmax=float(lam[-1]), homo=float(lam[spec.nocc - 1]),
+                       lumo=float(lam[spec.nocc]), lam=lam, Q=None,
+                       meta={"kind": "dense-device", "gap": spec.gap, "scheme": spec.scheme})
+    return F.contiguous(), meta

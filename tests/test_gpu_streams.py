@@ -1,0 +1,55 @@
+"""Stream ordering at the C ABI: a handle works on its own stream but is
+joined to the caller's stream, so device inputs still being produced on the
+caller's stream are read only once complete, and the caller's stream waits
+for the results."""
+import numpy as np
+import pytest
+
+from oracle import purify_oracle as O
+from paper_1101_0265_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1101_0265_gb300 import build
+    build.build()
+    import paper_1101_0265_gb300 as P
+    return P
+
+
+def _late_input(F_host):
+    """A device copy of F that only completes after a long device-side delay
+    queued on torch's current stream."""
+    Fd = torch.zeros(F_host.shape, dtype=torch.float64, device="cuda")
+    src = torch.from_numpy(F_host).pin_memory()
+    torch.cuda._sleep(200_000_000)          # ~0.1 s of device time first
+    Fd.copy_(src, non_blocking=True)
+    return Fd
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_handle_waits_for_callers_stream(P, precision):
+    h = I.dense_hamiltonian(300, 120, 0.05, config=62)
+    Do, _ = O.purify(h.F, "TC_SF", h.lmin, h.lmax, homo=h.homo, lumo=h.lumo, tol=1e-12)
+    pur = P.Purifier(precision=precision)                 # joined to torch's current stream
+    pur.set_hamiltonian(_late_input(h.F), nocc=h.nocc, lmin=h.lmin, lmax=h.lmax, homo=h.homo,
+                        lumo=h.lumo)
+    pur.run("TC_SF", 1e-12)
+    Dd = torch.empty((300, 300), dtype=torch.float64, device="cuda")
+    pur.density(Dd)
+    Dd.mul_(1.0)                                          # a torch op after the library's write
+    assert np.max(np.abs(Dd.cpu().numpy() - Do)) <= (1e-10 if precision == "fp64" else 1e-7)
+
+
+def test_batch_waits_for_callers_stream(P):
+    h = I.dense_hamiltonian(257, 100, 0.05, config=63)
+    Do, _ = O.purify(h.F, "TC_SF", h.lmin, h.lmax, homo=h.homo, lumo=h.lumo, tol=1e-10)
+    B = P.Batch()
+    i = B.add(_late_input(h.F), h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme="TC_SF", tol=1e-10)
+    B.run(use_graph=True)
+    assert np.max(np.abs(B.density(i) - Do)) <= 1e-7
+    B.close()
