@@ -91,7 +91,13 @@ typedef struct purify_options {
                             (default); 2..6 = fixed count                             */
     int time_products;   /* 1 = bracket every matrix-product launch with CUDA events
                             on the handle's stream and report their total time      */
-    int reserved[10];
+    int block_sparse;    /* MIXED, Algorithm 2 schemes: keep every iterate as a
+                            pattern of 32 x 32 blocks, form products only over
+                            nonzero blocks and truncate after every step         */
+    int reserved[9];
+    double trunc_tau;    /* block_sparse: per-step truncation budget: blocks of
+                            smallest Frobenius norm are dropped while the dropped
+                            mass (off-diagonal blocks twice) stays <= tau^2       */
 } purify_options;
 
 typedef struct purify_stats_t {
@@ -113,7 +119,8 @@ typedef struct purify_stats_t {
     int digit_max;              /* MIXED: largest digit count used                       */
     int kernel_launches;        /* kernels launched by the last set/run call             */
     int product_launches;       /* matrix-product kernels among them (last run)          */
-    int reserved[5];
+    int nnz_blocks;             /* block_sparse: upper 32 x 32 blocks of the result      */
+    int reserved[4];
     double product_seconds;     /* summed event time of the product launches
                                    (time_products = 1; else NaN)                         */
 } purify_stats_t;
@@ -145,6 +152,19 @@ int purify_set_options(purify_t h, const purify_options* opt);
  * discs).  The estimate runs on the device; its result is in purify_stats. */
 int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld,
                            int64_t nocc, double mu, const purify_bounds* b);
+
+/* Load a sparse symmetric F given as COO triplets (host arrays rows[k],
+ * cols[k], vals[k], 0-based, both triangles present) into the handle's dense
+ * float64 copy; otherwise as purify_set_hamiltonian.  Duplicates are summed in
+ * input order; the summed (i, j) and (j, i) entries must be equal, else
+ * PURIFY_ERR_INVALID_ARG (so is an index outside [0, n)). */
+int purify_set_hamiltonian_coo(purify_t h, int64_t n, int64_t nnz, const int64_t* rows,
+                               const int64_t* cols, const double* vals, int64_t nocc, double mu,
+                               const purify_bounds* b);
+
+/* Block-sparse runs: the number of upper 32 x 32 blocks kept after the
+ * truncation of X_0 and of every step (count <= cap entries written). */
+int purify_block_history(purify_t h, int* nnz_blocks, int cap, int* count);
 
 /* Run `scheme` until the bound of the scheme's scalar recursion (beta for
  * Algorithm 1, max(beta, 1 - beta_bar) for Algorithm 2) is <= tol, or, for

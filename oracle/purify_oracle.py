@@ -38,6 +38,11 @@ Readings where the paper is silent (each also listed in the design notes):
   P10 branch when trace(X_{i-1}) > nocc, otherwise P01.
 * Multiplication count: Algorithm 1 uses two matrix products per iteration
   (X_s^2 and X_s^2 X_s), Algorithm 2 one (the square).
+* Truncation (the paper leaves the scheme to future work and names control
+  of the forward error): after every step, drop the 32 x 32 blocks of
+  smallest Frobenius norm while the dropped mass sum ||B||_F^2 (blocks off
+  the diagonal counted twice, for B and B^T) stays <= tau^2, so each step
+  perturbs X by at most tau in the Frobenius (hence 2-) norm.
 """
 from __future__ import annotations
 
@@ -385,3 +390,78 @@ def commutator_norm(X, F):
     X = np.asarray(X)
     F = np.asarray(F)
     return float(np.linalg.norm(X @ F - F @ X))
+
+
+# ---------------------------------------------------------------------------
+# Block truncation (sparsity discussion: drop small elements, controlling the
+# error each step adds)
+# ---------------------------------------------------------------------------
+
+def block_norms(X, bs: int = 32):
+    """Frobenius norms of the bs x bs blocks of X (n a multiple of bs)."""
+    X = np.asarray(X, dtype=np.float64)
+    nb = X.shape[0] // bs
+    B = X.reshape(nb, bs, nb, bs)
+    return np.sqrt(np.einsum("ikjl,ikjl->ij", B, B))
+
+
+def truncation_mask(X, tau: float, bs: int = 32):
+    """Blocks kept (boolean nb x nb, symmetric): blocks (I <= J) sorted by
+    ascending norm (ties by row, then column) are dropped while the dropped
+    mass, counting off-diagonal blocks twice, stays <= tau^2; a block of norm
+    exactly zero is always dropped."""
+    N = block_norms(X, bs)
+    nb = N.shape[0]
+    I, J = np.triu_indices(nb)
+    w = np.where(I == J, 1.0, 2.0)
+    order = np.lexsort((J, I, N[I, J]))
+    keep = np.ones((nb, nb), dtype=bool)
+    budget = tau * tau
+    acc = 0.0
+    for k in order:
+        m = w[k] * N[I[k], J[k]] ** 2
+        if m > 0.0 and acc + m > budget:
+            break
+        acc += m
+        keep[I[k], J[k]] = keep[J[k], I[k]] = False
+    return keep
+
+
+def truncate_blocks(X, tau: float, bs: int = 32):
+    keep = truncation_mask(X, tau, bs)
+    mask = np.repeat(np.repeat(keep, bs, axis=0), bs, axis=1)
+    return np.where(mask, X, 0.0), keep
+
+
+def purify_tc_truncated(F, lmin, lmax, homo, lumo, tau, tol=1e-9, max_iter=200, scaled=True,
+                        bs: int = 32):
+    """Algorithm 2 with the truncation above applied to every iterate
+    (X_0 included).  Returns X, the Result and the kept-block counts (blocks
+    I <= J) after each truncation."""
+    F = np.asarray(F, dtype=np.float64)
+    n = F.shape[0]
+    I = np.eye(n)
+    X = (lmax * I - F) / (lmax - lmin)
+    X, keep = truncate_blocks(X, tau, bs)
+    nnzb = [int(np.triu(keep).sum())]
+    beta, betabar = tc_beta0(lmin, lmax, homo, lumo)
+    res = Result(scheme="TC_SF" if scaled else "TC_MONO", beta0=beta, betabar0=betabar,
+                 f0=tc_f0(lmin, lmax))
+    for branch, alpha, b, bb in tc_schedule(beta, betabar, tol, max_iter, scaled):
+        X2 = X @ X
+        res.idem.append(float(np.linalg.norm(X - X2)))
+        if branch == "P10":
+            X = (1.0 + alpha) * (1.0 + alpha) * X2 - 2.0 * alpha * (1.0 + alpha) * X + alpha * alpha * I
+        else:
+            X = 2.0 * (1.0 + alpha) * X - (1.0 + alpha) * (1.0 + alpha) * X2
+        X, keep = truncate_blocks(X, tau, bs)
+        nnzb.append(int(np.triu(keep).sum()))
+        res.alphas.append(alpha)
+        res.branches.append(branch)
+        res.betas.append(b)
+        res.betabars.append(bb)
+        res.traces.append(float(np.trace(X)))
+        res.iterations += 1
+        res.multiplications += 1
+    res.converged = bool(res.betas) and max(res.betas[-1], 1.0 - res.betabars[-1]) <= tol
+    return X, res, nnzb

@@ -31,7 +31,8 @@ BRANCH_RULES = {"beta": 0, "trace": 1}
 
 EXPORTED = (
     "purify_options_default", "purify_create", "purify_destroy", "purify_set_options",
-    "purify_set_hamiltonian", "purify_run", "purify_get_density", "purify_stats",
+    "purify_set_hamiltonian", "purify_set_hamiltonian_coo", "purify_block_history",
+    "purify_run", "purify_get_density", "purify_stats",
     "purify_density_device_ptr", "purify_strerror", "purify_schedule", "purify_tridiag_eig",
     "purify_k_symm_product_f64", "purify_k_step_f64", "purify_k_gershgorin_f64",
     "purify_k_lanczos_f64", "purify_k_digit_product_f64", "purify_k_gershgorin_f64_noalloc",
@@ -49,7 +50,7 @@ class Bounds(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("branch_rule", C.c_int), ("lanczos_steps", C.c_int),
                 ("refine_squares", C.c_int), ("digits", C.c_int), ("time_products", C.c_int),
-                ("reserved", C.c_int * 10)]
+                ("block_sparse", C.c_int), ("reserved", C.c_int * 9), ("trunc_tau", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -60,7 +61,7 @@ class Stats(C.Structure):
                 ("homo", C.c_double), ("lumo", C.c_double), ("mu", C.c_double),
                 ("useful_flops", C.c_double), ("tensor_flops", C.c_double),
                 ("digit_max", C.c_int), ("kernel_launches", C.c_int),
-                ("product_launches", C.c_int), ("reserved", C.c_int * 5),
+                ("product_launches", C.c_int), ("nnz_blocks", C.c_int), ("reserved", C.c_int * 4),
                 ("product_seconds", C.c_double)]
 
     def as_dict(self) -> dict:
@@ -93,6 +94,8 @@ def load(path: str = LIB_PATH):
         "purify_set_options": (ip, [vp, C.POINTER(Options)]),
         "purify_set_hamiltonian": (ip, [vp, vp, i64, i64, i64, dbl, C.POINTER(Bounds)]),
         "purify_run": (ip, [vp, ip, dbl, ip]),
+        "purify_set_hamiltonian_coo": (ip, [vp, i64, i64, vp, vp, vp, i64, dbl, C.POINTER(Bounds)]),
+        "purify_block_history": (ip, [vp, C.POINTER(C.c_int), ip, C.POINTER(C.c_int)]),
         "purify_get_density": (ip, [vp, vp, i64]),
         "purify_stats": (ip, [vp, C.POINTER(Stats)]),
         "purify_density_device_ptr": (vp, [vp]),
@@ -181,7 +184,8 @@ class Purifier:
 
     def __init__(self, device: int = 0, stream: int | None = None, precision: str = "fp64",
                  branch_rule: str = "beta", lanczos_steps: int = 32, refine_squares: int = 0,
-                 digits: int = 0, time_products: bool = False):
+                 digits: int = 0, time_products: bool = False, block_sparse: bool = False,
+                 trunc_tau: float = 1e-6):
         lib = load()
         self._lib = lib
         self.options = Options()
@@ -192,6 +196,8 @@ class Purifier:
         self.options.refine_squares = refine_squares
         self.options.digits = digits
         self.options.time_products = int(time_products)
+        self.options.block_sparse = int(block_sparse)
+        self.options.trunc_tau = float(trunc_tau)
         h = C.c_void_p()
         _check(lib.purify_create(C.byref(h), device, _caller_stream(stream), C.byref(self.options)),
                "purify_create")
@@ -236,6 +242,29 @@ class Purifier:
         _check(code, "purify_set_hamiltonian")
         self.n = n
         return code
+
+    def set_hamiltonian_coo(self, n: int, rows, cols, vals, nocc: int = -1, mu=None, lmin=None,
+                            lmax=None, homo=None, lumo=None):
+        """Sparse symmetric F as COO triplets (host int64 / float64 arrays,
+        both triangles, duplicates summed)."""
+        r = np.ascontiguousarray(rows, dtype=np.int64)
+        c = np.ascontiguousarray(cols, dtype=np.int64)
+        v = np.ascontiguousarray(vals, dtype=np.float64)
+        b = Bounds(_nan(lmin), _nan(lmax), _nan(homo), _nan(lumo))
+        code = self._lib.purify_set_hamiltonian_coo(self._h, int(n), int(v.size), r.ctypes.data,
+                                                    c.ctypes.data, v.ctypes.data, int(nocc), _nan(mu),
+                                                    C.byref(b))
+        _check(code, "purify_set_hamiltonian_coo")
+        self.n = int(n)
+        return code
+
+    def block_history(self):
+        cnt = C.c_int(0)
+        _check(self._lib.purify_block_history(self._h, None, 0, C.byref(cnt)), "purify_block_history")
+        buf = (C.c_int * max(cnt.value, 1))()
+        _check(self._lib.purify_block_history(self._h, buf, cnt.value, C.byref(cnt)),
+               "purify_block_history")
+        return list(buf[:cnt.value])
 
     def run(self, scheme: str, tol: float = 1e-12, max_iter: int = 200, check: bool = True) -> int:
         code = self._lib.purify_run(self._h, SCHEMES[scheme], float(tol), int(max_iter))

@@ -224,6 +224,14 @@ struct DigitGemmParams {
     __nv_bfloat16* out;      // output planes [s_out][n_pad][n_pad] (may be null)
     double* out64;           // float64 output n x n (leading dimension n) or null
     double* red;             // [0] trace(Y), [1] ||E - P||_F^2, [2] ||Y||_F^2 (atomics) or null
+    // block sparsity (null: dense): per upper tile t = tj (tj + 1) / 2 + ti,
+    // kc_list[kc_off[t]] = number of 32-wide k-chunks (-1: all of them),
+    // followed by their indices; bnorm2[I * nb + J] receives ||out block
+    // (I, J)||_F^2 for upper 32 x 32 blocks I <= J (k-chunk width must be 32)
+    const int* kc_off;
+    const int* kc_list;
+    float* bnorm2;
+    int nb;
 };
 
 // Products per launch whose tensor maps and parameters travel as kernel
@@ -352,10 +360,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             for (int t = blockIdx.x; t < num_items && !*abort_flag; t += gridDim.x) {
                 int g, ti, tj;
                 item_of(L, t, g, ti, tj);
-                const int nk = params_of(L, g).n_pad / KC;
+                const DigitGemmParams& Pg = params_of(L, g);
+                const int* kl = Pg.kc_list ? Pg.kc_list + Pg.kc_off[tj * (tj + 1) / 2 + ti] : nullptr;
+                if (kl && kl[0] < 0) kl = nullptr;  // every k-chunk
+                const int nk = kl ? kl[0] : Pg.n_pad / KC;
                 const CUtensorMap* mA = &L.maps[2 * g];
                 const CUtensorMap* mB = &L.maps[2 * g + 1];
-                for (int kc = 0; kc < nk; ++kc, ++it) {
+                for (int c = 0; c < nk; ++c, ++it) {
+                    const int kc = kl ? kl[1 + c] : c;
                     const int st = it % stages;
                     if (it >= stages && !mbar_wait_for(smem_u32(&empty_bar[st]), (uint32_t)(((it / stages) & 1) ^ 1))) {
                         atomicExch(L.err, 1);
@@ -384,7 +396,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             for (int t = blockIdx.x; t < num_items && ok; t += gridDim.x, ++lt) {
                 int g, ti, tj;
                 item_of(L, t, g, ti, tj);
-                const int nk = params_of(L, g).n_pad / KC;
+                const DigitGemmParams& Pg = params_of(L, g);
+                const int nl = Pg.kc_list ? Pg.kc_list[Pg.kc_off[tj * (tj + 1) / 2 + ti]] : -1;
+                const int nk = nl >= 0 ? nl : Pg.n_pad / KC;
                 if (lt > 0 && !mbar_wait_for(smem_u32(tmem_empty), (uint32_t)((lt - 1) & 1))) {
                     ok = false;
                     break;
@@ -451,7 +465,9 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             if (!ready) break;
             tc_fence_after();
             // phase 1: accumulators -> double-float P in scratch; release TMEM
-            const int nacc = s < NUM_ACC ? s : NUM_ACC;
+            // (a tile with no k-chunk of either operand has P = 0)
+            const bool empty = P.kc_list && P.kc_list[P.kc_off[tj * (tj + 1) / 2 + ti]] == 0;
+            const int nacc = empty ? 0 : (s < NUM_ACC ? s : NUM_ACC);
             for (int c0 = col0; c0 < col0 + TILE / 2; c0 += 16) {
                 float acc[NUM_ACC][16];
 #pragma unroll
@@ -485,6 +501,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             const int n = P.n, n_pad = P.n_pad;
             double s_tr = 0.0;  // the trace decides the occupation check: float64
             float s_idem = 0.f, s_fro = 0.f;
+            float bn2[2] = {0.f, 0.f};  // this row's share of two 32 x 32 output blocks
             for (int c0 = col0; c0 < col0 + TILE / 2; c0 += 16) {
                 const int jb = tj * TILE + c0;
                 df Ov[16];
@@ -530,6 +547,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                         const bool valid = i < n && j < n;
                         if (!valid) O = {0.f, 0.f};
                         Ov[c] = O;
+                        if (P.bnorm2 && (!diag_tile || i <= j)) {
+                            const float bw = (i == j || ((i >> 5) != (j >> 5))) ? 1.f : 2.f;
+                            bn2[(c0 - col0) >> 5] += bw * O.h * O.h;
+                        }
                         if (P.red && valid && (!diag_tile || i <= j)) {
                             const float w = (i == j) ? 1.f : 2.f;
                             if (i == j) s_tr += (double)Y.h + (double)Y.l;
@@ -586,6 +607,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                             }
                         }
                     }
+                }
+            }
+            if (P.bnorm2) {
+                // lanes are the 32 rows of one block row: reduce each block
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    const float v = warp_sum_f(bn2[b]);
+                    const int I = (ti * TILE + quarter * 32) >> 5;
+                    const int J = (tj * TILE + col0 + 32 * b) >> 5;
+                    if (lane == 0 && I <= J) P.bnorm2[(size_t)I * P.nb + J] = v;
                 }
             }
             if (P.red) {

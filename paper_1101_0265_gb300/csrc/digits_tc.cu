@@ -98,6 +98,8 @@ df to_df(double x) {
 
 // k-chunk width for a digit count: the widest chunk that still leaves at
 // least two pipeline stages, unless overridden (tuning).
+int digit_kc_for(int s, bool sparse) { return sparse ? 32 : digit_kc(s); }
+
 int digit_kc(int s) {
     static int forced = -1;
     if (forced < 0) {
@@ -153,7 +155,7 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
         return PURIFY_ERR_INVALID_ARG;
     if (st.n <= 0 || st.n_pad % TILE || st.n > st.n_pad) return PURIFY_ERR_INVALID_ARG;
     if (st.rbits < 4 || st.rbits > 8) return PURIFY_ERR_INVALID_ARG;
-    const int kc = digit_kc(st.s_in);
+    const int kc = digit_kc_for(st.s_in, st.kc_list || st.bnorm2);
     PURIFY_TRY(make_plane_map(ma, st.A, st.n_pad, st.s_in, kc));
     PURIFY_TRY(make_plane_map(mb, st.B, st.n_pad, st.s_in, kc));
     std::memset(p, 0, sizeof(*p));
@@ -177,11 +179,15 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
     p->out = st.out;
     p->out64 = st.out64;
     p->red = st.red;
+    p->kc_off = st.kc_off;
+    p->kc_list = st.kc_list;
+    p->bnorm2 = st.bnorm2;
+    p->nb = st.n_pad / 32;
+    if ((st.kc_list || st.bnorm2) && kc != 32) return PURIFY_ERR_INVALID_ARG;
     return PURIFY_OK;
 }
 
-static int launch_kernel(const DigitLaunch& L, int s, int grid, cudaStream_t stream) {
-    const int kc = digit_kc(s);
+static int launch_kernel(const DigitLaunch& L, int s, int kc, int grid, cudaStream_t stream) {
     KernelFn fn = kernel_for(kc, s);
     if (!fn || grid < 1 || L.stages < 1) return PURIFY_ERR_INVALID_ARG;
     PURIFY_TRY(prepare_kernel(fn));
@@ -198,12 +204,13 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
     L.ngroups = 1;
     const int T = st.n_pad / TILE;
     L.num_items = T * (T + 1) / 2;
-    L.stages = digit_stages(st.s_in, digit_kc(st.s_in));
+    const int kc = digit_kc_for(st.s_in, st.kc_list || st.bnorm2);
+    L.stages = digit_stages(st.s_in, kc);
     L.scratch = st.scratch;
     L.err = st.err;
     if (!st.scratch || !st.err) return PURIFY_ERR_INVALID_ARG;
     const int grid = L.num_items < st.max_ctas ? L.num_items : st.max_ctas;
-    return launch_kernel(L, st.s_in, grid, stream);
+    return launch_kernel(L, st.s_in, kc, grid, stream);
 }
 
 int launch_digit_group(int s, const DigitStep* steps, int count, const int4* work, int num_items,
@@ -213,18 +220,21 @@ int launch_digit_group(int s, const DigitStep* steps, int count, const int4* wor
     if (num_items <= 0) return PURIFY_OK;
     DigitLaunch L;
     std::memset(&L, 0, sizeof(L));
+    const bool sparse = steps[0].kc_list || steps[0].bnorm2;
     for (int g = 0; g < count; ++g) {
-        if (steps[g].s_in != s) return PURIFY_ERR_INVALID_ARG;
+        if (steps[g].s_in != s || (bool)(steps[g].kc_list || steps[g].bnorm2) != sparse)
+            return PURIFY_ERR_INVALID_ARG;
         PURIFY_TRY(fill_digit_params(steps[g], &L.prms[g], &L.maps[2 * g], &L.maps[2 * g + 1]));
     }
+    const int kc = digit_kc_for(s, sparse);
     L.ngroups = count;
     L.work = work;
     L.num_items = num_items;
-    L.stages = digit_stages(s, digit_kc(s));
+    L.stages = digit_stages(s, kc);
     L.scratch = scratch;
     L.err = err;
     const int grid = num_items < max_ctas ? num_items : max_ctas;
-    return launch_kernel(L, s, grid, stream);
+    return launch_kernel(L, s, kc, grid, stream);
 }
 
 int launch_split(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s,

@@ -84,7 +84,12 @@ __global__ void minmax_reduce_kernel(const double* __restrict__ part, int64_t m,
 }
 
 // ---- Lanczos ---------------------------------------------------------------
-// Scratch layout (doubles): v_prev[n] | v[n] | w[n] | qnorm2 | a[k] | bsq[k]
+// Scratch layout (doubles): v_prev[n] | v[n] | w[n] | qnorm2 | a[k] | bsq[k] |
+// pa[rows] | pb[kVecBlocksMax].  Every reduction goes through per-block
+// partials summed in a fixed order, so the coefficients (and the bounds built
+// from them) are the same on every run.
+
+constexpr int kVecBlocksMax = 152 * 4;
 
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
     unsigned long long z = x + GOLDEN;
@@ -93,7 +98,33 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long x) {
     return z ^ (z >> 31);
 }
 
-__global__ void lanczos_start_kernel(double* v, double* vprev, int64_t n, double* qnorm2) {
+// Sum over a 256-thread block in a fixed order; the result is valid in every
+// thread.
+__device__ double block_sum256(double v) {
+    __shared__ double ws[8];
+    __shared__ double total;
+    v = warp_sum(v);
+    __syncthreads();  // ws and total may still be read from a previous call
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < 8; ++q) t += ws[q];
+        total = t;
+    }
+    __syncthreads();
+    return total;
+}
+
+// Fixed-order sum of count partials (256-thread block).
+__device__ double sum_parts256(const double* __restrict__ p, int64_t count) {
+    double s = 0.0;
+    for (int64_t q = threadIdx.x; q < count; q += 256) s += p[q];
+    return block_sum256(s);
+}
+
+__global__ void __launch_bounds__(256)
+lanczos_start_kernel(double* v, double* vprev, int64_t n, double* pb) {
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -103,23 +134,27 @@ __global__ void lanczos_start_kernel(double* v, double* vprev, int64_t n, double
         vprev[i] = 0.0;
         s += q * q;
     }
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) atomicAdd(qnorm2, s);
+    s = block_sum256(s);
+    if (threadIdx.x == 0) pb[blockIdx.x] = s;
 }
 
-// v <- v / sqrt(*norm2)
-__global__ void scale_by_norm_kernel(double* v, int64_t n, const double* norm2) {
-    const double inv = 1.0 / sqrt(*norm2);
+// v <- v / ||v|| with ||v||^2 the sum of the start kernel's partials
+__global__ void __launch_bounds__(256)
+scale_by_norm_kernel(double* v, int64_t n, const double* pb, int parts, double* qnorm2) {
+    const double q2 = sum_parts256(pb, parts);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *qnorm2 = q2;
+    const double inv = 1.0 / sqrt(q2);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         v[i] *= inv;
 }
 
-// w = F v - b_{j-1} v_prev; a_j += w . v   (one warp per row)
+// w = F v - b_{j-1} v_prev; pa[block] = this block's share of w . v
+// (one warp per row)
 __global__ void __launch_bounds__(256)
 lanczos_matvec_kernel(const double* __restrict__ F, int64_t n, const double* __restrict__ v,
                       const double* __restrict__ vprev, double* __restrict__ w,
-                      const double* bsq_prev, double* a_j) {
+                      const double* bsq_prev, double* pa) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * ROWS_PER_CTA + warp;
     __shared__ double sdot[ROWS_PER_CTA];
@@ -139,14 +174,16 @@ lanczos_matvec_kernel(const double* __restrict__ F, int64_t n, const double* __r
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int q = 0; q < ROWS_PER_CTA; ++q) t += sdot[q];
-        atomicAdd(a_j, t);
+        pa[blockIdx.x] = t;
     }
 }
 
-// w -= a_j v; bsq_j += w . w
-__global__ void lanczos_orth_kernel(double* __restrict__ w, const double* __restrict__ v, int64_t n,
-                                    const double* a_j, double* bsq_j) {
-    const double a = *a_j;
+// a_j = sum of the matvec partials; w -= a_j v; pb[block] = share of w . w
+__global__ void __launch_bounds__(256)
+lanczos_orth_kernel(double* __restrict__ w, const double* __restrict__ v, int64_t n, const double* pa,
+                    int64_t rows, double* a_j, double* pb) {
+    const double a = sum_parts256(pa, rows);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *a_j = a;
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -154,14 +191,18 @@ __global__ void lanczos_orth_kernel(double* __restrict__ w, const double* __rest
         w[i] = wi;
         s += wi * wi;
     }
-    s = warp_sum(s);
-    if ((threadIdx.x & 31) == 0) atomicAdd(bsq_j, s);
+    s = block_sum256(s);
+    if (threadIdx.x == 0) pb[blockIdx.x] = s;
 }
 
-// v_prev <- v; v <- w / b_j  (v <- 0 on breakdown b_j == 0)
-__global__ void lanczos_shift_kernel(double* __restrict__ vprev, double* __restrict__ v,
-                                     const double* __restrict__ w, int64_t n, const double* bsq_j) {
-    const double b = sqrt(*bsq_j);
+// b_j^2 = sum of the orth partials; v_prev <- v; v <- w / b_j
+// (v <- 0 on breakdown b_j == 0)
+__global__ void __launch_bounds__(256)
+lanczos_shift_kernel(double* __restrict__ vprev, double* __restrict__ v, const double* __restrict__ w,
+                     int64_t n, const double* pb, int parts, double* bsq_j) {
+    const double b2 = sum_parts256(pb, parts);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *bsq_j = b2;
+    const double b = sqrt(b2);
     const double inv = b > 0.0 ? 1.0 / b : 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -172,7 +213,7 @@ __global__ void lanczos_shift_kernel(double* __restrict__ vprev, double* __restr
 
 unsigned vec_blocks(int64_t n) {
     int64_t b = (n + 255) / 256;
-    if (b > 152 * 4) b = 152 * 4;
+    if (b > kVecBlocksMax) b = kVecBlocksMax;
     if (b < 1) b = 1;
     return (unsigned)b;
 }
@@ -195,7 +236,9 @@ int launch_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi, 
     return PURIFY_OK;
 }
 
-int64_t lanczos_scratch_doubles(int64_t n, int k) { return 3 * n + 1 + 2 * (int64_t)k; }
+int64_t lanczos_scratch_doubles(int64_t n, int k) {
+    return 3 * n + 1 + 2 * (int64_t)k + (n + ROWS_PER_CTA - 1) / ROWS_PER_CTA + kVecBlocksMax;
+}
 
 int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaStream_t s) {
     if (n <= 0 || k <= 0) return PURIFY_ERR_INVALID_ARG;
@@ -205,16 +248,17 @@ int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaS
     double* qn = scratch + 3 * n;
     double* a = scratch + lanczos_a_offset(n);
     double* bsq = scratch + lanczos_bsq_offset(n, k);
-    PURIFY_CUDA_TRY(cudaMemsetAsync(qn, 0, sizeof(double) * (1 + 2 * (size_t)k), s));
+    const int64_t rows = (n + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
+    double* pa = bsq + k;
+    double* pb = pa + rows;
     const unsigned vb = vec_blocks(n);
-    lanczos_start_kernel<<<vb, 256, 0, s>>>(v, vprev, n, qn);
-    scale_by_norm_kernel<<<vb, 256, 0, s>>>(v, n, qn);
-    const unsigned rows = (unsigned)((n + ROWS_PER_CTA - 1) / ROWS_PER_CTA);
+    lanczos_start_kernel<<<vb, 256, 0, s>>>(v, vprev, n, pb);
+    scale_by_norm_kernel<<<vb, 256, 0, s>>>(v, n, pb, (int)vb, qn);
     for (int j = 0; j < k; ++j) {
-        lanczos_matvec_kernel<<<rows, 32 * ROWS_PER_CTA, 0, s>>>(F, n, v, vprev, w,
-                                                                   j ? bsq + j - 1 : nullptr, a + j);
-        lanczos_orth_kernel<<<vb, 256, 0, s>>>(w, v, n, a + j, bsq + j);
-        lanczos_shift_kernel<<<vb, 256, 0, s>>>(vprev, v, w, n, bsq + j);
+        lanczos_matvec_kernel<<<(unsigned)rows, 32 * ROWS_PER_CTA, 0, s>>>(F, n, v, vprev, w,
+                                                                             j ? bsq + j - 1 : nullptr, pa);
+        lanczos_orth_kernel<<<vb, 256, 0, s>>>(w, v, n, pa, rows, a + j, pb);
+        lanczos_shift_kernel<<<vb, 256, 0, s>>>(vprev, v, w, n, pb, (int)vb, bsq + j);
     }
     PURIFY_CUDA_TRY(cudaGetLastError());
     count_launches(2 + 3 * k);

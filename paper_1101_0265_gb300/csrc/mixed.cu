@@ -20,15 +20,6 @@
 
 namespace purify {
 
-struct MixedState {
-    int n_pad_cap = 0;
-    __nv_bfloat16* Xd[2] = {nullptr, nullptr};
-    __nv_bfloat16* Sd = nullptr;
-    int* err = nullptr;
-    float2* scratch = nullptr;  // persistent product kernel, one tile per CTA
-    int ctas = 0;
-};
-
 void mixed_free(MixedState* ms) {
     if (!ms) return;
     cudaFree(ms->Xd[0]);
@@ -36,10 +27,13 @@ void mixed_free(MixedState* ms) {
     cudaFree(ms->Sd);
     cudaFree(ms->err);
     cudaFree(ms->scratch);
+    cudaFree(ms->kc_list);
+    cudaFree(ms->bnorm2);
+    cudaFree(ms->drops);
     delete ms;
 }
 
-static int ensure_mixed(purify_ctx* h, int n_pad) {
+int ensure_mixed(purify_ctx* h, int n_pad) {
     if (!h->mixed) {
         h->mixed = new (std::nothrow) MixedState();
         if (!h->mixed) return PURIFY_ERR_OOM;

@@ -1,14 +1,41 @@
 // Mixed-precision (digit-plane tensor-core) path of the iteration driver.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <vector>
 
 #include "internal.h"
 
 namespace purify {
 
-struct MixedState;
 constexpr int kMaxDigits = 6;  // equals kMaxDigitPlanes (digits_tc.h)
+
+// Device buffers of the mixed path, owned by a handle.
+struct MixedState {
+    int n_pad_cap = 0;
+    __nv_bfloat16* Xd[2] = {nullptr, nullptr};
+    __nv_bfloat16* Sd = nullptr;
+    int* err = nullptr;
+    float2* scratch = nullptr;  // persistent product kernel, one tile per CTA
+    int ctas = 0;
+    // block-sparse runs (per-tile offsets and k-chunk lists in one array)
+    int* kc_list = nullptr;
+    size_t kc_list_cap = 0;
+    float* bnorm2 = nullptr;
+    size_t bnorm2_cap = 0;
+    int2* drops = nullptr;
+    size_t drops_cap = 0;
+    std::vector<int> nnzb_history;  // upper blocks kept: X_0, then after every step
+};
+
+// Allocate (or grow) the handle's mixed-path buffers for a padded size.
+int ensure_mixed(purify_ctx* h, int n_pad);
+int digits_for_gap(double g, int fixed, int rbits);
+// F[key[k]] = v[k] for distinct keys row * n + col (device arrays).
+int launch_scatter_coo(const int64_t* key, const double* v, int64_t nnz, double* F, cudaStream_t s);
+// Block-sparse Algorithm 2 run (sparse.cu).
+int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std::vector<double>& red);
 
 // Run the scheme's coefficient schedule with every matrix product on the
 // tcgen05 tensor cores (see mixed.cu).  Sets *cur (index into h->X of the

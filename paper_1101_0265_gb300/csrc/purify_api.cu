@@ -290,6 +290,8 @@ void purify_options_default(purify_options* opt) {
     opt->lanczos_steps = 32;
     opt->refine_squares = 0;
     opt->digits = 0;
+    opt->block_sparse = 0;
+    opt->trunc_tau = 1e-6;
 }
 
 static int check_options(const purify_options* o) {
@@ -299,6 +301,8 @@ static int check_options(const purify_options* o) {
     if (o->lanczos_steps < 0 || o->lanczos_steps > 512) return PURIFY_ERR_INVALID_ARG;
     if (o->refine_squares < 0 || o->refine_squares > 8) return PURIFY_ERR_INVALID_ARG;
     if (o->digits != 0 && (o->digits < 2 || o->digits > kMaxDigits)) return PURIFY_ERR_INVALID_ARG;
+    if (o->block_sparse != 0 && o->block_sparse != 1) return PURIFY_ERR_INVALID_ARG;
+    if (!(o->trunc_tau >= 0.0)) return PURIFY_ERR_INVALID_ARG;
     return PURIFY_OK;
 }
 
@@ -370,22 +374,10 @@ const double* purify_density_device_ptr(purify_t h) {
     return h->X[h->cur];
 }
 
-int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld, int64_t nocc,
-                           double mu, const purify_bounds* b) {
-    if (!h || !F || !b || n <= 0 || ld < n) return PURIFY_ERR_INVALID_ARG;
-    if (nocc > n) return PURIFY_ERR_INVALID_ARG;
-    if (n > (int64_t)1 << 17) return PURIFY_ERR_INVALID_ARG;
-    PURIFY_TRY(set_device(h));
-    const long long set_launches0 = launches_so_far();
-    h->have_F = false;
-    h->cur = -1;
-    PURIFY_TRY(join_in(h));
-    PURIFY_TRY(ensure_capacity(h, n));
-    h->n = n;
-    PURIFY_CUDA_TRY(cudaMemcpy2DAsync(h->F, sizeof(double) * n, F, sizeof(double) * ld,
-                                      sizeof(double) * n, n, cudaMemcpyDefault, h->stream));
-    PURIFY_TRY(launch_mirror_upper_f64(h->F, n, h->stream));
-
+// The part of loading a Hamiltonian after h->F (n x n, dense) holds it:
+// bounds (estimated when NaN), validation, statistics.
+static int finish_set(purify_t h, int64_t n, int64_t nocc, double mu, const purify_bounds* b,
+                      long long set_launches0) {
     purify_bounds bb = *b;
     if (std::isnan(bb.lmin) || std::isnan(bb.lmax)) {
         const int k = (int)std::min<int64_t>(h->opt.lanczos_steps, n);
@@ -436,6 +428,90 @@ int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld, i
     h->st.product_seconds = NAN;
     h->have_F = true;
     return join_out(h);
+}
+
+int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld, int64_t nocc,
+                           double mu, const purify_bounds* b) {
+    if (!h || !F || !b || n <= 0 || ld < n) return PURIFY_ERR_INVALID_ARG;
+    if (nocc > n) return PURIFY_ERR_INVALID_ARG;
+    if (n > (int64_t)1 << 17) return PURIFY_ERR_INVALID_ARG;
+    PURIFY_TRY(set_device(h));
+    const long long set_launches0 = launches_so_far();
+    h->have_F = false;
+    h->cur = -1;
+    PURIFY_TRY(join_in(h));
+    PURIFY_TRY(ensure_capacity(h, n));
+    h->n = n;
+    PURIFY_CUDA_TRY(cudaMemcpy2DAsync(h->F, sizeof(double) * n, F, sizeof(double) * ld,
+                                      sizeof(double) * n, n, cudaMemcpyDefault, h->stream));
+    PURIFY_TRY(launch_mirror_upper_f64(h->F, n, h->stream));
+    return finish_set(h, n, nocc, mu, b, set_launches0);
+}
+
+int purify_set_hamiltonian_coo(purify_t h, int64_t n, int64_t nnz, const int64_t* rows,
+                               const int64_t* cols, const double* vals, int64_t nocc, double mu,
+                               const purify_bounds* b) {
+    if (!h || !b || n <= 0 || nnz < 0 || (nnz > 0 && (!rows || !cols || !vals))) return PURIFY_ERR_INVALID_ARG;
+    if (nocc > n || n > (int64_t)1 << 17) return PURIFY_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < nnz; ++k)
+        if (rows[k] < 0 || rows[k] >= n || cols[k] < 0 || cols[k] >= n) return PURIFY_ERR_INVALID_ARG;
+    // merge duplicates (summed in input order, so the result does not depend
+    // on the device's scheduling) and require (i, j) and (j, i) to agree
+    std::vector<int64_t> perm(nnz), key(nnz);
+    for (int64_t k = 0; k < nnz; ++k) {
+        perm[k] = k;
+        key[k] = rows[k] * n + cols[k];
+    }
+    std::stable_sort(perm.begin(), perm.end(), [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+    std::vector<int64_t> ukey;
+    std::vector<double> uval;
+    ukey.reserve(nnz);
+    uval.reserve(nnz);
+    for (int64_t q = 0; q < nnz; ++q) {
+        const int64_t k = perm[q];
+        if (!ukey.empty() && ukey.back() == key[k])
+            uval.back() += vals[k];
+        else {
+            ukey.push_back(key[k]);
+            uval.push_back(vals[k]);
+        }
+    }
+    for (size_t u = 0; u < ukey.size(); ++u) {
+        const int64_t t = (ukey[u] % n) * n + ukey[u] / n;
+        const auto it = std::lower_bound(ukey.begin(), ukey.end(), t);
+        if (it == ukey.end() || *it != t || uval[it - ukey.begin()] != uval[u]) return PURIFY_ERR_INVALID_ARG;
+    }
+    nnz = (int64_t)ukey.size();
+    PURIFY_TRY(set_device(h));
+    const long long set_launches0 = launches_so_far();
+    h->have_F = false;
+    h->cur = -1;
+    PURIFY_TRY(join_in(h));
+    PURIFY_TRY(ensure_capacity(h, n));
+    h->n = n;
+    PURIFY_CUDA_TRY(cudaMemsetAsync(h->F, 0, sizeof(double) * (size_t)n * n, h->stream));
+    if (nnz > 0) {
+        PURIFY_TRY(ensure_scratch(h, 2 * nnz));
+        int64_t* dk = (int64_t*)h->scratch;
+        double* dv = (double*)(dk + nnz);
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(dk, ukey.data(), sizeof(int64_t) * nnz, cudaMemcpyHostToDevice, h->stream));
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(dv, uval.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice, h->stream));
+        PURIFY_TRY(launch_scatter_coo(dk, dv, nnz, h->F, h->stream));
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));  // the scratch is reused below
+    }
+    return finish_set(h, n, nocc, mu, b, set_launches0);
+}
+
+int purify_block_history(purify_t h, int* nnz_blocks, int cap, int* count) {
+    if (!h || !count || cap < 0 || (cap > 0 && !nnz_blocks)) return PURIFY_ERR_INVALID_ARG;
+    if (!h->mixed) {
+        *count = 0;
+        return PURIFY_OK;
+    }
+    const std::vector<int>& hist = h->mixed->nnzb_history;
+    *count = (int)hist.size();
+    for (int i = 0; i < cap && i < (int)hist.size(); ++i) nnz_blocks[i] = hist[i];
+    return PURIFY_OK;
 }
 
 // One float64 step with reductions into slot `slot` (4 doubles).
@@ -611,9 +687,16 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
     std::vector<double> red;
     int iters = 0;
     int r;
+    if (h->opt.block_sparse && h->opt.precision != PURIFY_MIXED) return PURIFY_ERR_UNSUPPORTED;
     if (h->opt.precision == PURIFY_MIXED) {
         if (trace_rule) return PURIFY_ERR_UNSUPPORTED;
-        r = run_mixed(h, scheme, mu, S, &h->cur, red);
+        if (h->opt.block_sparse) {
+            r = run_block_sparse(h, scheme, S, &h->cur, red);
+            if (r == PURIFY_OK && h->mixed && !h->mixed->nnzb_history.empty())
+                h->st.nnz_blocks = h->mixed->nnzb_history.back();
+        } else {
+            r = run_mixed(h, scheme, mu, S, &h->cur, red);
+        }
         iters = (int)S.alpha.size();
     } else {
         r = run_fp64(h, scheme, tol, max_iter, mu, S, trace_rule, &iters, red);

@@ -1,0 +1,410 @@
+// Block-sparse purification with truncation (Algorithm 2, mixed path).
+//
+// The paper expects sparsity to be "critical" in linear-scaling runs and
+// leaves the truncation scheme to future work, naming control of the forward
+// error.  Here every iterate X_i is kept as a pattern of 32 x 32 blocks:
+//   - the product X_{i-1}^2 is formed only over 32-wide k-chunks in which
+//     both row panels of an output tile hold a nonzero block (per-tile chunk
+//     lists fed to the same tensor-core kernel), and tiles with no such
+//     chunk run the epilogue alone;
+//   - the epilogue reports ||B||_F^2 of every 32 x 32 output block;
+//   - truncation drops the blocks of smallest norm while the dropped mass
+//     (off-diagonal blocks twice, for B and B^T) stays <= tau^2, so each step
+//     moves X by at most tau in the Frobenius norm; dropped blocks are zeroed
+//     in the digit planes and leave the pattern.
+// Digit planes stay dense in memory (n_pad^2 per plane); the work follows
+// the pattern.  Patterns are bitsets on the host: the pattern of X^2 is the
+// union over K in row I of the rows K.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "digits_tc.h"
+#include "mixed.h"
+
+namespace purify {
+
+namespace {
+
+// ||block (I, J) of c0 I + c1 F||_F^2 for upper blocks, J-major block number.
+__global__ void x0_block_norms_kernel(const double* __restrict__ F, int n, int nb, double c0, double c1,
+                                      float* __restrict__ bn) {
+    const int t = blockIdx.x;
+    int J = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
+    while ((J + 1) * (J + 2) / 2 <= t) ++J;
+    while (J * (J + 1) / 2 > t) --J;
+    const int I = t - J * (J + 1) / 2;
+    double s = 0.0;
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+        const int i = I * 32 + (e >> 5), j = J * 32 + (e & 31);
+        if (i >= n || j >= n) continue;
+        double w = 1.0;
+        if (I == J) {
+            if (i > j) continue;
+            w = (i == j) ? 1.0 : 2.0;
+        }
+        double x = c1 * F[(size_t)i * n + j];
+        if (i == j) x += c0;
+        s += w * x * x;
+    }
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) bn[(size_t)I * nb + J] = (float)red[0];
+}
+
+// Zero blocks (I, J) and (J, I) in s digit planes.
+__global__ void mask_planes_kernel(__nv_bfloat16* planes, int s, int n_pad, const int2* blocks) {
+    const int2 b = blocks[blockIdx.x];
+    const size_t plane = (size_t)n_pad * n_pad;
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+    for (int p = 0; p < s; ++p)
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+            const int r = e >> 5, c = e & 31;
+            planes[p * plane + (size_t)(b.x * 32 + r) * n_pad + b.y * 32 + c] = z;
+            planes[p * plane + (size_t)(b.y * 32 + r) * n_pad + b.x * 32 + c] = z;
+        }
+}
+
+// Zero blocks (I, J) and (J, I) of an n x n float64 matrix.
+__global__ void mask_f64_kernel(double* D, int n, const int2* blocks) {
+    const int2 b = blocks[blockIdx.x];
+    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+        const int r = e >> 5, c = e & 31;
+        const int i0 = b.x * 32 + r, j0 = b.y * 32 + c;
+        if (i0 < n && j0 < n) D[(size_t)i0 * n + j0] = 0.0;
+        const int i1 = b.y * 32 + r, j1 = b.x * 32 + c;
+        if (i1 < n && j1 < n) D[(size_t)i1 * n + j1] = 0.0;
+    }
+}
+
+// Block pattern: bit (I, J) of an nb x nb symmetric pattern.
+struct Pattern {
+    int nb = 0, words = 0;
+    std::vector<uint64_t> bits;
+    void init(int nb_) {
+        nb = nb_;
+        words = (nb + 63) / 64;
+        bits.assign((size_t)nb * words, 0);
+    }
+    bool get(int I, int J) const { return (bits[(size_t)I * words + (J >> 6)] >> (J & 63)) & 1u; }
+    void set(int I, int J) { bits[(size_t)I * words + (J >> 6)] |= (uint64_t)1 << (J & 63); }
+    void clear(int I, int J) { bits[(size_t)I * words + (J >> 6)] &= ~((uint64_t)1 << (J & 63)); }
+    const uint64_t* row(int I) const { return &bits[(size_t)I * words]; }
+    uint64_t* row(int I) { return &bits[(size_t)I * words]; }
+    int count_upper() const {
+        int c = 0;
+        for (int I = 0; I < nb; ++I)
+            for (int J = I; J < nb; ++J) c += get(I, J);
+        return c;
+    }
+};
+
+// Pattern of X^2, of X and of the diagonal together (the blocks that Eq. 4
+// and Eq. 5 can make nonzero).
+void output_pattern(const Pattern& X, Pattern& out) {
+    out.init(X.nb);
+    for (int I = 0; I < X.nb; ++I) {
+        uint64_t* o = out.row(I);
+        const uint64_t* xi = X.row(I);
+        for (int w = 0; w < X.words; ++w) {
+            o[w] |= xi[w];
+            uint64_t m = xi[w];
+            while (m) {
+                const int K = w * 64 + __builtin_ctzll(m);
+                m &= m - 1;
+                const uint64_t* xk = X.row(K);
+                for (int v = 0; v < X.words; ++v) o[v] |= xk[v];
+            }
+        }
+        out.set(I, I);
+    }
+}
+
+// Per upper 128 x 128 tile: the 32-wide k-chunks where both row panels hold a
+// nonzero block (-1 when that is every chunk).
+void chunk_lists(const Pattern& X, int T, std::vector<int>& off, std::vector<int>& list) {
+    const int words = X.words, nb = X.nb;
+    std::vector<uint64_t> panel((size_t)T * words, 0);
+    for (int t = 0; t < T; ++t)
+        for (int r = 4 * t; r < 4 * t + 4 && r < nb; ++r)
+            for (int w = 0; w < words; ++w) panel[(size_t)t * words + w] |= X.row(r)[w];
+    off.assign((size_t)T * (T + 1) / 2, 0);
+    list.clear();
+    for (int tj = 0; tj < T; ++tj)
+        for (int ti = 0; ti <= tj; ++ti) {
+            off[(size_t)tj * (tj + 1) / 2 + ti] = (int)list.size();
+            const size_t head = list.size();
+            list.push_back(0);
+            int cnt = 0;
+            for (int w = 0; w < words; ++w) {
+                uint64_t m = panel[(size_t)ti * words + w] & panel[(size_t)tj * words + w];
+                while (m) {
+                    list.push_back(w * 64 + __builtin_ctzll(m));
+                    m &= m - 1;
+                    ++cnt;
+                }
+            }
+            if (cnt == nb) {
+                list.resize(head + 1);
+                cnt = -1;
+            }
+            list[head] = cnt;
+        }
+}
+
+// Error-controlled truncation of the upper blocks of `pat` by their squared
+// norms bn2 (row-major nb x nb, upper part): ascending norm, ties by row then
+// column; drop while the dropped mass stays <= tau^2.  Dropped blocks leave
+// `pat` and are listed in `drop`.
+void select_drops(Pattern& pat, const float* bn2, double tau, std::vector<int2>& drop) {
+    struct Cand {
+        double m;
+        int I, J;
+    };
+    std::vector<Cand> c;
+    for (int I = 0; I < pat.nb; ++I)
+        for (int J = I; J < pat.nb; ++J)
+            if (pat.get(I, J)) c.push_back({(double)bn2[(size_t)I * pat.nb + J], I, J});
+    std::sort(c.begin(), c.end(), [](const Cand& a, const Cand& b) {
+        if (a.m != b.m) return a.m < b.m;
+        if (a.I != b.I) return a.I < b.I;
+        return a.J < b.J;
+    });
+    drop.clear();
+    const double budget = tau * tau;
+    double acc = 0.0;
+    for (const Cand& x : c) {
+        const double m = (x.I == x.J ? 1.0 : 2.0) * x.m;
+        if (m > 0.0 && acc + m > budget) break;
+        acc += m;
+        drop.push_back(make_int2(x.I, x.J));
+        pat.clear(x.I, x.J);
+        pat.clear(x.J, x.I);
+    }
+}
+
+template <typename T>
+int grow(T** p, size_t* cap, size_t n) {
+    if (n <= *cap) return PURIFY_OK;
+    cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    const size_t c = std::max(n, (size_t)1024) * 2;
+    PURIFY_CUDA_TRY(cudaMalloc(p, sizeof(T) * c));
+    *cap = c;
+    return PURIFY_OK;
+}
+
+// Read the block norms, choose the drops, zero them on the device.
+int truncate_step(purify_ctx* h, Pattern& pat, double tau, __nv_bfloat16* planes, int s, int n_pad,
+                  double* out64, int n, std::vector<float>& bn2) {
+    MixedState* ms = h->mixed;
+    const int nb = pat.nb;
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(bn2.data(), ms->bnorm2, sizeof(float) * (size_t)nb * nb,
+                                    cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    std::vector<int2> drop;
+    select_drops(pat, bn2.data(), tau, drop);
+    if (drop.empty()) return PURIFY_OK;
+    PURIFY_TRY(grow(&ms->drops, &ms->drops_cap, drop.size()));
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->drops, drop.data(), sizeof(int2) * drop.size(), cudaMemcpyHostToDevice,
+                                    h->stream));
+    if (planes) {
+        mask_planes_kernel<<<(unsigned)drop.size(), 256, 0, h->stream>>>(planes, s, n_pad, ms->drops);
+        PURIFY_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+    }
+    if (out64) {
+        mask_f64_kernel<<<(unsigned)drop.size(), 256, 0, h->stream>>>(out64, n, ms->drops);
+        PURIFY_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+    }
+    return PURIFY_OK;
+}
+
+void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
+    if (branch) {
+        *cP = (1.0 + a) * (1.0 + a);
+        *cE = -2.0 * a * (1.0 + a);
+        *cI = a * a;
+    } else {
+        *cP = -(1.0 + a) * (1.0 + a);
+        *cE = 2.0 * (1.0 + a);
+        *cI = 0.0;
+    }
+}
+
+// Distinct keys (row * n + col): plain stores.
+__global__ void scatter_coo_kernel(const int64_t* __restrict__ key, const double* __restrict__ v, int64_t nnz,
+                                   double* F) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz; k += (int64_t)gridDim.x * blockDim.x)
+        F[key[k]] = v[k];
+}
+
+}  // namespace
+
+// F[key[k]] = v[k] for distinct keys (device arrays); F zeroed beforehand.
+int launch_scatter_coo(const int64_t* key, const double* v, int64_t nnz, double* F, cudaStream_t s) {
+    if (nnz <= 0) return PURIFY_OK;
+    int64_t blocks = (nnz + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    scatter_coo_kernel<<<(unsigned)blocks, 256, 0, s>>>(key, v, nnz, F);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return PURIFY_OK;
+}
+
+int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std::vector<double>& red) {
+    if (scheme != PURIFY_TC_SF && scheme != PURIFY_TC_MONO) return PURIFY_ERR_UNSUPPORTED;
+    const double tau = h->opt.trunc_tau;
+    if (!(tau >= 0.0)) return PURIFY_ERR_INVALID_ARG;
+    const int n = (int)h->n;
+    const int n_pad = pad128(n);
+    PURIFY_TRY(ensure_mixed(h, n_pad));
+    MixedState* ms = h->mixed;
+    const int nb = n_pad / 32, T = n_pad / 128;
+    const int rb = remainder_bits(n_pad);
+    const int m = (int)S.alpha.size();
+    const int fixed = h->opt.digits;
+    std::vector<int> sd(m + 1);
+    for (int i = 0; i < m; ++i) {
+        const double b = i ? S.beta[i - 1] : S.beta0;
+        const double bb = i ? S.betabar[i - 1] : S.betabar0;
+        sd[i] = digits_for_gap(bb - b, fixed, rb);
+    }
+    sd[m] = sd[m ? m - 1 : 0];
+    int dmax = 0;
+    for (int i = 0; i < m; ++i) dmax = std::max(dmax, sd[i]);
+    h->st.digit_max = dmax;
+    PURIFY_TRY(grow(&ms->bnorm2, &ms->bnorm2_cap, (size_t)nb * nb));
+    const int slots = 2 * m + 2;
+    PURIFY_TRY(ensure_red(h, 4 * (int64_t)slots));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * slots, h->stream));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), h->stream));
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+
+    const double lmin = h->b.lmin, lmax = h->b.lmax;
+    const double c0 = lmax / (lmax - lmin), c1 = -1.0 / (lmax - lmin);
+    std::vector<float> bn2((size_t)nb * nb, 0.f);
+    ms->nnzb_history.clear();
+    // X_0 = c0 I + c1 F: its block pattern, truncated like every iterate
+    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->bnorm2, 0, sizeof(float) * (size_t)nb * nb, h->stream));
+    x0_block_norms_kernel<<<(unsigned)(nb * (nb + 1) / 2), 256, 0, h->stream>>>(h->F, n, nb, c0, c1, ms->bnorm2);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    PURIFY_TRY(launch_split(h->F, n, n, n_pad, c1, c0, 0, std::max(sd[0], 1), rb, ms->Xd[0], nullptr, h->stream));
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(bn2.data(), ms->bnorm2, sizeof(float) * (size_t)nb * nb,
+                                    cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    Pattern X;
+    X.init(nb);
+    for (int I = 0; I < nb; ++I)
+        for (int J = I; J < nb; ++J)
+            if (bn2[(size_t)I * nb + J] > 0.f || I == J) {
+                X.set(I, J);
+                X.set(J, I);
+            }
+    {
+        std::vector<int2> drop;
+        select_drops(X, bn2.data(), tau, drop);
+        if (!drop.empty()) {
+            PURIFY_TRY(grow(&ms->drops, &ms->drops_cap, drop.size()));
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->drops, drop.data(), sizeof(int2) * drop.size(),
+                                            cudaMemcpyHostToDevice, h->stream));
+            mask_planes_kernel<<<(unsigned)drop.size(), 256, 0, h->stream>>>(ms->Xd[0], std::max(sd[0], 1), n_pad,
+                                                                              ms->drops);
+            PURIFY_CUDA_TRY(cudaGetLastError());
+            count_launches(1);
+        }
+    }
+    ms->nnzb_history.push_back(X.count_upper());
+
+    double* D = h->X[0];
+    *cur = 0;
+    int x = 0;
+    std::vector<int> off, list;
+    const double pairs_tile = 2.0 * 128.0 * 128.0 * 32.0;  // one pair, one 32-wide k-chunk
+    for (int i = 0; i < m; ++i) {
+        const int s = sd[i];
+        Pattern out;
+        output_pattern(X, out);
+        chunk_lists(X, T, off, list);
+        size_t need = off.size() + list.size();
+        if (need > ms->kc_list_cap) {
+            cudaFree(ms->kc_list);
+            ms->kc_list = nullptr;
+            ms->kc_list_cap = 0;
+            PURIFY_TRY(grow(&ms->kc_list, &ms->kc_list_cap, need));
+        }
+        // kc_off and kc_list share one device array: offsets first
+        std::vector<int> packed(need);
+        for (size_t k = 0; k < off.size(); ++k) packed[k] = off[k] + (int)off.size();
+        std::copy(list.begin(), list.end(), packed.begin() + off.size());
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->kc_list, packed.data(), sizeof(int) * need, cudaMemcpyHostToDevice,
+                                        h->stream));
+        double chunks = 0.0;
+        for (size_t k = 0; k < off.size(); ++k) {
+            const int c = list[off[k]];
+            chunks += c < 0 ? (double)nb : (double)c;
+        }
+        DigitStep st;
+        st.n = n;
+        st.n_pad = n_pad;
+        st.rbits = rb;
+        st.A = st.B = ms->Xd[x];
+        st.s_in = s;
+        st.eA = st.eB = 0;
+        st.use_E = 1;
+        tc_coeffs(S.branch[i], S.alpha[i], &st.cP, &st.cE, &st.cI);
+        const bool last = (i + 1 == m);
+        st.red = last ? h->red + 4 * (2 * i + 1) : nullptr;
+        st.err = ms->err;
+        st.scratch = ms->scratch;
+        st.max_ctas = ms->ctas;
+        st.kc_off = ms->kc_list;
+        st.kc_list = ms->kc_list;
+        st.bnorm2 = ms->bnorm2;
+        if (last) {
+            st.out64 = D;
+        } else {
+            st.out = ms->Xd[x ^ 1];
+            st.s_out = sd[i + 1];
+            st.e_out = 0;
+        }
+        PURIFY_TRY(product_begin(h));
+        PURIFY_TRY(launch_digit_step(st, h->stream));
+        ++h->st.product_launches;
+        h->st.tensor_flops += 0.5 * s * (s + 1) * pairs_tile * chunks;
+        PURIFY_TRY(product_end(h));
+        PURIFY_TRY(truncate_step(h, out, tau, last ? nullptr : ms->Xd[x ^ 1], last ? 0 : sd[i + 1], n_pad,
+                                 last ? D : nullptr, n, bn2));
+        X = out;
+        ms->nnzb_history.push_back(X.count_upper());
+        x ^= 1;
+    }
+    if (m == 0) PURIFY_TRY(launch_affine_f64(h->F, n, D, n, c1, c0, h->stream));
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+    red.assign(4 * (size_t)slots, 0.0);
+    int err = 0;
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(red.data(), h->red, sizeof(double) * red.size(), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, ms->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (err) return PURIFY_ERR_DEVICE_TIMEOUT;
+    if (m > 0) {
+        h->st.trace = red[4 * (size_t)(2 * (m - 1) + 1)];
+        h->st.idem_err_fro = std::sqrt(std::max(red[4 * (size_t)(2 * (m - 1) + 1) + 1], 0.0));
+    } else {
+        h->st.trace = NAN;
+        h->st.idem_err_fro = NAN;
+    }
+    return PURIFY_OK;
+}
+
+}  // namespace purify

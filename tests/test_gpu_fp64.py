@@ -85,6 +85,9 @@ def test_lanczos_f64(P, n, k):
     T = lambda a_, b_: np.diag(a_) + np.diag(b_[:-1], 1) + np.diag(b_[:-1], -1)
     assert np.max(np.abs(np.linalg.eigvalsh(T(a, b))[[0, -1]]
                          - np.linalg.eigvalsh(T(ao, bo))[[0, -1]])) < 1e-11
+    # reductions in a fixed order: the same coefficients on every call
+    a2, b2 = P.k_lanczos_f64(_cuda(h.F), k)
+    assert np.array_equal(a, a2) and np.array_equal(b, b2)
 
 
 # --- whole purification parity --------------------------------------------------

@@ -1,0 +1,151 @@
+"""GPU tests of the block-sparse mixed path (Algorithm 2 with error-controlled
+truncation of 32 x 32 blocks).
+
+- tau = 0 drops only blocks that are exactly zero, and a product skips only
+  k-chunks whose contributions are exactly zero: the result equals the dense
+  mixed path bit for bit.
+- tau > 0: the same iterations as the oracle's truncated recursion, the
+  density within the mixed path's tolerance plus what a different drop
+  decision at the budget's edge can move, and the distance to the exact
+  density within the bound the truncation budget gives.
+- The COO entry point gives what the dense entry point gives."""
+import numpy as np
+import pytest
+
+from oracle import purify_oracle as O
+from paper_1101_0265_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1101_0265_gb300 import build
+    build.build()
+    import paper_1101_0265_gb300 as P
+    return P
+
+
+def _lattice(L, instance=0):
+    lat = I.lattice_hamiltonian(L, instance=instance)
+    F = lat.dense()
+    lo, hi = O.gershgorin(F)
+    return lat, F, lo, hi
+
+
+def _run(P, lat, lo, hi, tol, block_sparse, tau=0.0, coo=True, F=None, digits=0):
+    pur = P.Purifier(precision="mixed", block_sparse=block_sparse, trunc_tau=tau, digits=digits)
+    g = lat.gap_bound
+    if coo:
+        pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0, lmin=lo,
+                                lmax=hi, homo=-g, lumo=g)
+    else:
+        pur.set_hamiltonian(F, nocc=lat.nocc, mu=0.0, lmin=lo, lmax=hi, homo=-g, lumo=g)
+    pur.run("TC_SF", tol, 200)
+    D = pur.density()
+    st = pur.stats()
+    hist = pur.block_history() if block_sparse else None
+    pur.close()
+    return D, st, hist
+
+
+@pytest.mark.parametrize("L", [8, 12])
+def test_tau_zero_is_the_dense_path(P, L):
+    lat, F, lo, hi = _lattice(L)
+    tol = 1e-9
+    Dd, std, _ = _run(P, lat, lo, hi, tol, block_sparse=False, coo=False, F=F)
+    Ds, sts, hist = _run(P, lat, lo, hi, tol, block_sparse=True, tau=0.0)
+    assert sts["iterations"] == std["iterations"]
+    assert np.array_equal(Ds, Dd), np.max(np.abs(Ds - Dd))
+    assert len(hist) == sts["iterations"] + 1
+    nb = (lat.n + 31) // 32
+    assert hist[0] < nb * (nb + 1) // 2           # X_0 has the lattice's block pattern
+    assert sts["nnz_blocks"] == hist[-1]
+    # chunk lists skip work: fewer tensor flops than the dense product count
+    assert sts["tensor_flops"] < std["tensor_flops"]
+
+
+def test_coo_input_equals_dense_input(P):
+    lat, F, lo, hi = _lattice(8, instance=1)
+    D1, st1, h1 = _run(P, lat, lo, hi, 1e-9, block_sparse=True, tau=1e-6, coo=True)
+    D2, st2, h2 = _run(P, lat, lo, hi, 1e-9, block_sparse=True, tau=1e-6, coo=False, F=F)
+    assert np.array_equal(D1, D2)
+    assert h1 == h2
+    # bounds estimated on the device from the COO input equal those from the dense input
+    pur = P.Purifier(precision="mixed")
+    pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc)
+    a = pur.stats()
+    pur.set_hamiltonian(F, nocc=lat.nocc)
+    b = pur.stats()
+    pur.close()
+    # (the Lanczos reductions run in a fixed order: the estimate is reproducible)
+    for k in ("lmin", "lmax", "homo", "lumo", "mu"):
+        assert a[k] == b[k] or (np.isnan(a[k]) and np.isnan(b[k])), (k, a[k], b[k])
+
+
+@pytest.mark.parametrize("L,tau", [(8, 1e-6), (8, 1e-4), (12, 1e-6), (12, 1e-5)])
+def test_truncated_vs_oracle(P, L, tau):
+    lat, F, lo, hi = _lattice(L)
+    g = lat.gap_bound
+    tol = 1e-9
+    Xo, r, hist_o = O.purify_tc_truncated(F, lo, hi, -g, g, tau, tol=tol)
+    D, st, hist = _run(P, lat, lo, hi, tol, block_sparse=True, tau=tau)
+    assert st["iterations"] == r.iterations
+    assert hist[0] == hist_o[0]
+    # blocks near the budget's edge may go either way: each step's decision
+    # moves X by at most tau in the Frobenius norm on either side, and the
+    # recursion contracts errors in the occupied and unoccupied subspaces;
+    # what survives is bounded by the error growth towards the gap
+    diff = np.max(np.abs(D - Xo))
+    mapped_gap = 2 * g / (hi - lo)
+    assert diff <= 3e-7 + 2 * tau / mapped_gap, diff
+    assert all(abs(a - b) <= max(4, 0.02 * b) for a, b in zip(hist, hist_o)), (hist, hist_o)
+    Dx = O.density_by_eigh(F, 0.0)
+    assert np.linalg.norm(D - Dx, 2) <= 3e-7 + (r.iterations + 1) * tau / mapped_gap
+    assert abs(st["trace"] - lat.nocc) <= 1e-6 * lat.n + (r.iterations + 1) * tau * np.sqrt(lat.n)
+
+
+def test_dense_input_through_block_sparse(P):
+    # no zero blocks: every chunk list is "all chunks" and tau = 0 drops
+    # nothing: the dense path's result
+    h = I.dense_hamiltonian(300, 120, 0.02, config=70)
+    out = []
+    for bs in (False, True):
+        pur = P.Purifier(precision="mixed", block_sparse=bs, trunc_tau=0.0)
+        pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+        pur.run("TC_SF", 1e-10, 200)
+        out.append((pur.density(), pur.stats()))
+        if bs:
+            assert pur.block_history()[-1] == 10 * 11 // 2
+        pur.close()
+    assert np.array_equal(out[0][0], out[1][0])
+    assert out[0][1]["iterations"] == out[1][1]["iterations"]
+
+
+def test_block_sparse_unsupported_combinations(P):
+    lat, F, lo, hi = _lattice(8)
+    pur = P.Purifier(precision="fp64", block_sparse=True)
+    pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc)
+    with pytest.raises(P.PurifyError):
+        pur.run("TC_SF", 1e-9, 200)
+    pur.close()
+    pur = P.Purifier(precision="mixed", block_sparse=True)
+    pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc)
+    with pytest.raises(P.PurifyError):
+        pur.run("FIXED_MU_SF", 1e-9, 200)
+    pur.close()
+    with pytest.raises(P.PurifyError):
+        P.Purifier(precision="mixed", block_sparse=True, trunc_tau=-1.0)
+
+
+def test_coo_rejects_bad_indices(P):
+    pur = P.Purifier(precision="mixed")
+    with pytest.raises(P.PurifyError):
+        pur.set_hamiltonian_coo(4, [0, 4], [0, 1], [1.0, 2.0], nocc=2)
+    with pytest.raises(P.PurifyError):
+        pur.set_hamiltonian_coo(4, [0, 1], [0, -1], [1.0, 2.0], nocc=2)
+    with pytest.raises(P.PurifyError):                       # not symmetric
+        pur.set_hamiltonian_coo(4, [0, 1], [1, 2], [1.0, 2.0], nocc=2)
+    pur.close()

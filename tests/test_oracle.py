@@ -295,3 +295,73 @@ def test_lanczos_bounds_bracket_extremes():
     assert lo <= -1.0 + 1e-12 and hi >= 1.0 - 1e-12
     assert lo > -1.05 and hi < 1.05
     assert g_hi - g_lo > 4.0
+
+
+# --- block truncation (the sparsity discussion: drop small elements while
+# controlling the error each step adds) ---------------------------------------
+
+def _random_blocky(nb, seed, bs=32):
+    rng = np.random.default_rng(seed)
+    scales = 10.0 ** rng.uniform(-9, 0, size=(nb, nb))
+    scales = np.triu(scales) + np.triu(scales, 1).T
+    X = rng.standard_normal((nb * bs, nb * bs)) * np.repeat(np.repeat(scales, bs, 0), bs, 1)
+    return 0.5 * (X + X.T)
+
+
+@pytest.mark.parametrize("tau", [0.0, 1e-8, 1e-6, 1e-4])
+def test_truncation_error_bound_and_greed(tau):
+    X = _random_blocky(6, 3)
+    Xt, keep = O.truncate_blocks(X, tau)
+    assert np.array_equal(keep, keep.T)
+    dropped = X - Xt
+    # the step moves X by at most tau in the Frobenius (hence 2-) norm
+    assert np.linalg.norm(dropped) <= tau * (1 + 1e-12)
+    assert np.linalg.norm(dropped, 2) <= tau * (1 + 1e-12)
+    # greedy and maximal: the smallest kept block would overflow the budget
+    N = O.block_norms(X)
+    kept = [(N[i, j], i, j) for i in range(6) for j in range(i, 6) if keep[i, j]]
+    if kept and tau > 0:
+        m, i, j = min(kept)
+        w = 1.0 if i == j else 2.0
+        assert np.linalg.norm(dropped) ** 2 + w * m * m > tau * tau
+    # every dropped block is no larger than every kept block
+    if kept:
+        drop_norms = [N[i, j] for i in range(6) for j in range(i, 6) if not keep[i, j]]
+        if drop_norms:
+            assert max(drop_norms) <= min(k[0] for k in kept)
+
+
+def test_block_norms_definition():
+    X = _random_blocky(3, 4)
+    N = O.block_norms(X)
+    for i in range(3):
+        for j in range(3):
+            assert abs(N[i, j] - np.sqrt(np.sum(X[32 * i:32 * i + 32, 32 * j:32 * j + 32] ** 2))) < 1e-12
+
+
+def test_truncated_purification_reduces_to_plain_at_tau_zero():
+    h = I.dense_hamiltonian(96, 40, 0.05, config=96)
+    X, r, nnzb = O.purify_tc_truncated(h.F, h.lmin, h.lmax, h.homo, h.lumo, 0.0, tol=1e-12)
+    Xp, rp = O.purify_tc(h.F, h.lmin, h.lmax, h.homo, h.lumo, tol=1e-12)
+    assert r.iterations == rp.iterations
+    assert np.max(np.abs(X - Xp)) < 1e-14
+    assert all(k == 6 for k in nnzb)  # 3 x 3 blocks, none exactly zero: 6 with I <= J
+
+
+def test_lattice_gap_and_truncated_density():
+    # the cubic lattice's spectrum keeps |lambda| >= 0.5 - max|onsite noise|
+    lat = I.lattice_hamiltonian(8)
+    F = lat.dense()
+    lam = np.linalg.eigvalsh(F)
+    assert np.min(np.abs(lam)) >= lat.gap_bound
+    assert np.count_nonzero(lam < 0) == lat.nocc
+    lo, hi = O.gershgorin(F)
+    g = lat.gap_bound
+    tau = 1e-6
+    X, r, nnzb = O.purify_tc_truncated(F, lo, hi, -g, g, tau, tol=1e-10)
+    D = O.density_by_eigh(F, 0.0)
+    # each step adds at most tau; errors in the block coupling occupied and
+    # unoccupied states are amplified by at most 1 / (mapped gap)
+    mapped_gap = 2 * g / (hi - lo)
+    assert np.linalg.norm(X - D, 2) <= 1e-10 + (r.iterations + 1) * tau / mapped_gap
+    assert abs(np.trace(X) - lat.nocc) < 1e-3
