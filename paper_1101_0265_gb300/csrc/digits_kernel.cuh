@@ -225,11 +225,13 @@ struct DigitGemmParams {
     double* out64;           // float64 output n x n (leading dimension n) or null
     double* red;             // [0] trace(Y), [1] ||E - P||_F^2, [2] ||Y||_F^2 (atomics) or null
     // block sparsity (null: dense): per upper tile t = tj (tj + 1) / 2 + ti,
-    // kc_list[kc_off[t]] = number of 32-wide k-chunks (-1: all of them),
-    // followed by their indices; bnorm2[I * nb + J] receives ||out block
-    // (I, J)||_F^2 for upper 32 x 32 blocks I <= J (k-chunk width must be 32)
-    const int* kc_off;
-    const int* kc_list;
+    // kc_cnt[t] = number of 32-wide k-chunks that contribute (-1: all of
+    // them) and kc_mask[t * kc_words ..] their bitmask (bit k of word k / 64);
+    // bnorm2[I * nb + J] receives ||out block (I, J)||_F^2 for upper 32 x 32
+    // blocks I <= J (k-chunk width must be 32)
+    const int* kc_cnt;
+    const unsigned long long* kc_mask;
+    int kc_words;
     float* bnorm2;
     int nb;
 };
@@ -361,13 +363,26 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                 int g, ti, tj;
                 item_of(L, t, g, ti, tj);
                 const DigitGemmParams& Pg = params_of(L, g);
-                const int* kl = Pg.kc_list ? Pg.kc_list + Pg.kc_off[tj * (tj + 1) / 2 + ti] : nullptr;
-                if (kl && kl[0] < 0) kl = nullptr;  // every k-chunk
-                const int nk = kl ? kl[0] : Pg.n_pad / KC;
+                const int tix = tj * (tj + 1) / 2 + ti;
+                const int cnt = Pg.kc_cnt ? Pg.kc_cnt[tix] : -1;  // -1: every k-chunk
+                const unsigned long long* km = cnt >= 0 ? Pg.kc_mask + (size_t)tix * Pg.kc_words : nullptr;
+                const int nk = cnt >= 0 ? cnt : Pg.n_pad / KC;
                 const CUtensorMap* mA = &L.maps[2 * g];
                 const CUtensorMap* mB = &L.maps[2 * g + 1];
+                int w = 0;
+                unsigned long long bits = km ? km[0] : 0ull;
                 for (int c = 0; c < nk; ++c, ++it) {
-                    const int kc = kl ? kl[1 + c] : c;
+                    int kc = c;
+                    if (km) {
+                        while (bits == 0ull && w + 1 < Pg.kc_words) bits = km[++w];
+                        if (bits == 0ull) {  // count and mask disagree
+                            atomicExch(L.err, 4);
+                            *abort_flag = 1;
+                            break;
+                        }
+                        kc = w * 64 + __ffsll((long long)bits) - 1;
+                        bits &= bits - 1;
+                    }
                     const int st = it % stages;
                     if (it >= stages && !mbar_wait_for(smem_u32(&empty_bar[st]), (uint32_t)(((it / stages) & 1) ^ 1))) {
                         atomicExch(L.err, 1);
@@ -397,7 +412,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                 int g, ti, tj;
                 item_of(L, t, g, ti, tj);
                 const DigitGemmParams& Pg = params_of(L, g);
-                const int nl = Pg.kc_list ? Pg.kc_list[Pg.kc_off[tj * (tj + 1) / 2 + ti]] : -1;
+                const int nl = Pg.kc_cnt ? Pg.kc_cnt[tj * (tj + 1) / 2 + ti] : -1;
                 const int nk = nl >= 0 ? nl : Pg.n_pad / KC;
                 if (lt > 0 && !mbar_wait_for(smem_u32(tmem_empty), (uint32_t)((lt - 1) & 1))) {
                     ok = false;
@@ -466,7 +481,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             tc_fence_after();
             // phase 1: accumulators -> double-float P in scratch; release TMEM
             // (a tile with no k-chunk of either operand has P = 0)
-            const bool empty = P.kc_list && P.kc_list[P.kc_off[tj * (tj + 1) / 2 + ti]] == 0;
+            const bool empty = P.kc_cnt && P.kc_cnt[tj * (tj + 1) / 2 + ti] == 0;
             const int nacc = empty ? 0 : (s < NUM_ACC ? s : NUM_ACC);
             for (int c0 = col0; c0 < col0 + TILE / 2; c0 += 16) {
                 float acc[NUM_ACC][16];

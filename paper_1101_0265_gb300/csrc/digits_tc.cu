@@ -155,7 +155,7 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
         return PURIFY_ERR_INVALID_ARG;
     if (st.n <= 0 || st.n_pad % TILE || st.n > st.n_pad) return PURIFY_ERR_INVALID_ARG;
     if (st.rbits < 4 || st.rbits > 8) return PURIFY_ERR_INVALID_ARG;
-    const int kc = digit_kc_for(st.s_in, st.kc_list || st.bnorm2);
+    const int kc = digit_kc_for(st.s_in, st.kc_cnt || st.bnorm2);
     PURIFY_TRY(make_plane_map(ma, st.A, st.n_pad, st.s_in, kc));
     PURIFY_TRY(make_plane_map(mb, st.B, st.n_pad, st.s_in, kc));
     std::memset(p, 0, sizeof(*p));
@@ -179,11 +179,13 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
     p->out = st.out;
     p->out64 = st.out64;
     p->red = st.red;
-    p->kc_off = st.kc_off;
-    p->kc_list = st.kc_list;
+    p->kc_cnt = st.kc_cnt;
+    p->kc_mask = st.kc_mask;
+    p->kc_words = (st.n_pad / 32 + 63) / 64;
     p->bnorm2 = st.bnorm2;
     p->nb = st.n_pad / 32;
-    if ((st.kc_list || st.bnorm2) && kc != 32) return PURIFY_ERR_INVALID_ARG;
+    if (st.kc_cnt && !st.kc_mask) return PURIFY_ERR_INVALID_ARG;
+    if ((st.kc_cnt || st.bnorm2) && kc != 32) return PURIFY_ERR_INVALID_ARG;
     return PURIFY_OK;
 }
 
@@ -204,7 +206,7 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
     L.ngroups = 1;
     const int T = st.n_pad / TILE;
     L.num_items = T * (T + 1) / 2;
-    const int kc = digit_kc_for(st.s_in, st.kc_list || st.bnorm2);
+    const int kc = digit_kc_for(st.s_in, st.kc_cnt || st.bnorm2);
     L.stages = digit_stages(st.s_in, kc);
     L.scratch = st.scratch;
     L.err = st.err;
@@ -220,9 +222,9 @@ int launch_digit_group(int s, const DigitStep* steps, int count, const int4* wor
     if (num_items <= 0) return PURIFY_OK;
     DigitLaunch L;
     std::memset(&L, 0, sizeof(L));
-    const bool sparse = steps[0].kc_list || steps[0].bnorm2;
+    const bool sparse = steps[0].kc_cnt || steps[0].bnorm2;
     for (int g = 0; g < count; ++g) {
-        if (steps[g].s_in != s || (bool)(steps[g].kc_list || steps[g].bnorm2) != sparse)
+        if (steps[g].s_in != s || (bool)(steps[g].kc_cnt || steps[g].bnorm2) != sparse)
             return PURIFY_ERR_INVALID_ARG;
         PURIFY_TRY(fill_digit_params(steps[g], &L.prms[g], &L.maps[2 * g], &L.maps[2 * g + 1]));
     }

@@ -32,8 +32,8 @@ struct DigitStep {
     float2* scratch = nullptr;  // max_ctas x 128 x 128 float2 (digit_scratch_bytes)
     int max_ctas = 0;           // persistent grid size (the SM count)
     // block sparsity (device arrays, see DigitGemmParams); null = dense
-    const int* kc_off = nullptr;
-    const int* kc_list = nullptr;
+    const int* kc_cnt = nullptr;
+    const unsigned long long* kc_mask = nullptr;
     float* bnorm2 = nullptr;
 };
 

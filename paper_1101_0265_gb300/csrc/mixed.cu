@@ -27,7 +27,7 @@ void mixed_free(MixedState* ms) {
     cudaFree(ms->Sd);
     cudaFree(ms->err);
     cudaFree(ms->scratch);
-    cudaFree(ms->kc_list);
+    cudaFree(ms->kc_buf);
     cudaFree(ms->bnorm2);
     cudaFree(ms->drops);
     delete ms;

@@ -19,9 +19,10 @@ struct MixedState {
     int* err = nullptr;
     float2* scratch = nullptr;  // persistent product kernel, one tile per CTA
     int ctas = 0;
-    // block-sparse runs (per-tile offsets and k-chunk lists in one array)
-    int* kc_list = nullptr;
-    size_t kc_list_cap = 0;
+    // block-sparse runs: per-tile k-chunk counts, then (8-byte aligned) the
+    // per-tile k-chunk bitmasks, in one array of 8-byte words
+    unsigned long long* kc_buf = nullptr;
+    size_t kc_buf_cap = 0;
     float* bnorm2 = nullptr;
     size_t bnorm2_cap = 0;
     int2* drops = nullptr;

@@ -1,11 +1,12 @@
 // Block-sparse purification with truncation (Algorithm 2, mixed path).
 //
-// The paper expects sparsity to be "critical" in linear-scaling runs and
-// leaves the truncation scheme to future work, naming control of the forward
-// error.  Here every iterate X_i is kept as a pattern of 32 x 32 blocks:
+// The paper's closing discussion counts on sparsity in the linear-scaling
+// regime and leaves the truncation scheme open, asking only that the forward
+// error stay controlled.  Here every iterate X_i is kept as a pattern of
+// 32 x 32 blocks:
 //   - the product X_{i-1}^2 is formed only over 32-wide k-chunks in which
-//     both row panels of an output tile hold a nonzero block (per-tile chunk
-//     lists fed to the same tensor-core kernel), and tiles with no such
+//     both row panels of an output tile hold a nonzero block (per-tile k-chunk
+//     bitmasks fed to the same tensor-core kernel), and tiles with no such
 //     chunk run the epilogue alone;
 //   - the epilogue reports ||B||_F^2 of every 32 x 32 output block;
 //   - truncation drops the blocks of smallest norm while the dropped mass
@@ -126,35 +127,28 @@ void output_pattern(const Pattern& X, Pattern& out) {
     }
 }
 
-// Per upper 128 x 128 tile: the 32-wide k-chunks where both row panels hold a
-// nonzero block (-1 when that is every chunk).
-void chunk_lists(const Pattern& X, int T, std::vector<int>& off, std::vector<int>& list) {
+// Per upper 128 x 128 tile t = tj (tj + 1) / 2 + ti: the 32-wide k-chunks
+// where both row panels hold a nonzero block, as a bitmask (X.words words per
+// tile) and a count (-1 when that is every chunk).
+void chunk_masks(const Pattern& X, int T, std::vector<int>& cnt, std::vector<uint64_t>& mask) {
     const int words = X.words, nb = X.nb;
     std::vector<uint64_t> panel((size_t)T * words, 0);
     for (int t = 0; t < T; ++t)
         for (int r = 4 * t; r < 4 * t + 4 && r < nb; ++r)
             for (int w = 0; w < words; ++w) panel[(size_t)t * words + w] |= X.row(r)[w];
-    off.assign((size_t)T * (T + 1) / 2, 0);
-    list.clear();
+    const size_t tiles = (size_t)T * (T + 1) / 2;
+    cnt.assign(tiles, 0);
+    mask.assign(tiles * words, 0);
     for (int tj = 0; tj < T; ++tj)
         for (int ti = 0; ti <= tj; ++ti) {
-            off[(size_t)tj * (tj + 1) / 2 + ti] = (int)list.size();
-            const size_t head = list.size();
-            list.push_back(0);
-            int cnt = 0;
+            const size_t t = (size_t)tj * (tj + 1) / 2 + ti;
+            int c = 0;
             for (int w = 0; w < words; ++w) {
-                uint64_t m = panel[(size_t)ti * words + w] & panel[(size_t)tj * words + w];
-                while (m) {
-                    list.push_back(w * 64 + __builtin_ctzll(m));
-                    m &= m - 1;
-                    ++cnt;
-                }
+                const uint64_t m = panel[(size_t)ti * words + w] & panel[(size_t)tj * words + w];
+                mask[t * words + w] = m;
+                c += __builtin_popcountll(m);
             }
-            if (cnt == nb) {
-                list.resize(head + 1);
-                cnt = -1;
-            }
-            list[head] = cnt;
+            cnt[t] = (c == nb) ? -1 : c;
         }
 }
 
@@ -167,17 +161,23 @@ void select_drops(Pattern& pat, const float* bn2, double tau, std::vector<int2>&
         double m;
         int I, J;
     };
+    // a block whose weighted mass alone exceeds the budget is never dropped,
+    // and every block after it in the order is at least as heavy: only the
+    // lighter ones need sorting
+    const double budget = tau * tau;
     std::vector<Cand> c;
     for (int I = 0; I < pat.nb; ++I)
-        for (int J = I; J < pat.nb; ++J)
-            if (pat.get(I, J)) c.push_back({(double)bn2[(size_t)I * pat.nb + J], I, J});
+        for (int J = I; J < pat.nb; ++J) {
+            if (!pat.get(I, J)) continue;
+            const double m = (double)bn2[(size_t)I * pat.nb + J];
+            if ((I == J ? 1.0 : 2.0) * m <= budget) c.push_back({m, I, J});
+        }
     std::sort(c.begin(), c.end(), [](const Cand& a, const Cand& b) {
         if (a.m != b.m) return a.m < b.m;
         if (a.I != b.I) return a.I < b.I;
         return a.J < b.J;
     });
     drop.clear();
-    const double budget = tau * tau;
     double acc = 0.0;
     for (const Cand& x : c) {
         const double m = (x.I == x.J ? 1.0 : 2.0) * x.m;
@@ -328,31 +328,24 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     double* D = h->X[0];
     *cur = 0;
     int x = 0;
-    std::vector<int> off, list;
+    std::vector<int> cnt;
+    std::vector<uint64_t> mask;
+    const size_t tiles = (size_t)T * (T + 1) / 2;
+    const size_t cnt_words = (tiles + 1) / 2;  // the counts, two ints per word
     const double pairs_tile = 2.0 * 128.0 * 128.0 * 32.0;  // one pair, one 32-wide k-chunk
     for (int i = 0; i < m; ++i) {
         const int s = sd[i];
         Pattern out;
         output_pattern(X, out);
-        chunk_lists(X, T, off, list);
-        size_t need = off.size() + list.size();
-        if (need > ms->kc_list_cap) {
-            cudaFree(ms->kc_list);
-            ms->kc_list = nullptr;
-            ms->kc_list_cap = 0;
-            PURIFY_TRY(grow(&ms->kc_list, &ms->kc_list_cap, need));
-        }
-        // kc_off and kc_list share one device array: offsets first
-        std::vector<int> packed(need);
-        for (size_t k = 0; k < off.size(); ++k) packed[k] = off[k] + (int)off.size();
-        std::copy(list.begin(), list.end(), packed.begin() + off.size());
-        PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->kc_list, packed.data(), sizeof(int) * need, cudaMemcpyHostToDevice,
+        chunk_masks(X, T, cnt, mask);
+        PURIFY_TRY(grow(&ms->kc_buf, &ms->kc_buf_cap, cnt_words + mask.size()));
+        int* kc_cnt = (int*)ms->kc_buf;
+        unsigned long long* kc_mask = ms->kc_buf + cnt_words;
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(kc_cnt, cnt.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice, h->stream));
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(kc_mask, mask.data(), sizeof(uint64_t) * mask.size(), cudaMemcpyHostToDevice,
                                         h->stream));
         double chunks = 0.0;
-        for (size_t k = 0; k < off.size(); ++k) {
-            const int c = list[off[k]];
-            chunks += c < 0 ? (double)nb : (double)c;
-        }
+        for (size_t k = 0; k < tiles; ++k) chunks += cnt[k] < 0 ? (double)nb : (double)cnt[k];
         DigitStep st;
         st.n = n;
         st.n_pad = n_pad;
@@ -367,8 +360,8 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
         st.err = ms->err;
         st.scratch = ms->scratch;
         st.max_ctas = ms->ctas;
-        st.kc_off = ms->kc_list;
-        st.kc_list = ms->kc_list;
+        st.kc_cnt = kc_cnt;
+        st.kc_mask = kc_mask;
         st.bnorm2 = ms->bnorm2;
         if (last) {
             st.out64 = D;
