@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--serve-rates", default="30", help="comma list; empty to skip serving")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-lattice", action="store_true", help="skip the 32^3 block-sparse workload")
     return ap.parse_args()
 
 
@@ -161,6 +162,45 @@ def run_serve(P, dev, stream, rate, count, budget_gb=64.0, tol=1e-9):
     return {"rate_per_s": rate, "requests": count, "p50_ms": pct(0.50), "p99_ms": pct(0.99),
             "max_ms": 1e3 * lat[-1], "throughput_per_s": count / total, "rounds": rounds,
             "peak_concurrent": peak_live, "hbm_budget_gb": budget_gb}
+
+
+def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9):
+    """The block-sparse workload: periodic L^3 cubic tight-binding lattice
+    (onsite +-0.5 by sublattice + N(0, 0.05), hopping -1 + U(-0.1, 0.1)),
+    n = L^3, nocc = n/2, mu = 0, loaded from COO, 32 x 32 blocks truncated at
+    tau per step.  Trace-correcting scale-and-fold against its monotonic
+    baseline, both block-sparse, and the dense mixed path at the same size.
+    One warm-up run and one timed run each (device-event time of the run)."""
+    import torch
+    from paper_1101_0265_gb300 import inputs as I
+    lat = I.lattice_hamiltonian(L)
+    g = lat.gap_bound
+    out = {"workload": f"{L}^3 periodic cubic tight-binding lattice, n={lat.n}, COO input, "
+                       f"32x32 blocks, tau {tau:g} per step, tol {tol:g}",
+           "n": lat.n, "tau": tau, "gap_bound": g}
+    for name, scheme, bs in (("TC_SF", "TC_SF", True), ("TC_MONO", "TC_MONO", True),
+                             ("TC_SF_dense", "TC_SF", False)):
+        pur = P.Purifier(device=dev.index, stream=stream.cuda_stream, precision="mixed",
+                         block_sparse=bs, trunc_tau=tau)
+        pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0,
+                                homo=-g, lumo=g)
+        pur.run(scheme, tol, 300)
+        pur.run(scheme, tol, 300)
+        st = pur.stats()
+        r = {"seconds": st["seconds"], "iterations": st["iterations"],
+             "tensor_tflops": st["tensor_flops"] / st["seconds"] / 1e12,
+             "trace_err": abs(st["trace"] - lat.nocc), "idem_err_fro": st["idem_err_fro"]}
+        if bs:
+            h = pur.block_history()
+            nb = lat.n // 32
+            r["nnz_blocks"] = h
+            r["final_fill"] = h[-1] / (nb * (nb + 1) / 2)
+        pur.close()
+        torch.cuda.empty_cache()
+        out[name] = r
+    out["speedup_sf_vs_mono"] = out["TC_MONO"]["seconds"] / out["TC_SF"]["seconds"]
+    out["speedup_sparse_vs_dense"] = out["TC_SF_dense"]["seconds"] / out["TC_SF"]["seconds"]
+    return out
 
 
 def peaks():
@@ -451,6 +491,8 @@ def main():
     if world == 1 and args.precision == "mixed" and args.serve_rates:
         line["serve"] = [run_serve(P, dev, stream, float(r), args.serve_requests)
                          for r in args.serve_rates.split(",")]
+    if world == 1 and args.precision == "mixed" and not args.no_lattice:
+        line["lattice"] = run_lattice(P, dev, stream)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(hs, Fh[0].numpy(), args.tol)
     pur.close()

@@ -94,7 +94,11 @@ typedef struct purify_options {
     int block_sparse;    /* MIXED, Algorithm 2 schemes: keep every iterate as a
                             pattern of 32 x 32 blocks, form products only over
                             nonzero blocks and truncate after every step         */
-    int reserved[9];
+    int split_k;         /* MIXED dense products: cut the tiles of the persistent
+                            grid's last, partial wave into k-ranges that run on
+                            the idle SMs and are added in a fixed order (default 1;
+                            0 = whole tiles, the grouping the batch engine uses) */
+    int reserved[8];
     double trunc_tau;    /* block_sparse: per-step truncation budget: blocks of
                             smallest Frobenius norm are dropped while the dropped
                             mass (off-diagonal blocks twice) stays <= tau^2       */

@@ -56,6 +56,7 @@ constexpr int MAX_STAGES = 8;
 constexpr int NUM_ACC = 4;       // tensor-memory accumulators (levels 0, 1, 2, >= 3)
 constexpr int NTHREADS = 320;
 constexpr int EPI_WARPS = 8;
+constexpr int EW = 8;            // epilogue columns per pass (a multiple of 8)
 constexpr long long WAIT_CYCLES = 1ll << 31;  // one wait gives up after ~1 s at 2 GHz
 
 // ---- PTX wrappers ------------------------------------------------------------
@@ -246,20 +247,40 @@ constexpr int GMAX = 64;
 // One launch: products g = 0 .. ngroups-1 (tensor maps and parameters by
 // value) and the list of work items {g, ti, tj, -} in global memory, or, when
 // `work` is null, all upper tiles of product 0 in banded order.
+//
+// Split tiles (single launches only): the tiles from `split_begin` on in
+// banded order (the last, partial wave of the persistent grid) are each cut
+// into `split_ways` ranges of k-chunks, one work item per range, so that the
+// last wave fills the grid.  Each epilogue warp of a part stores its raw
+// accumulators for its 32 x 64 region in `partial`, then counts itself in
+// split_cnt[slot][region]; the warp that arrives last adds the parts in part
+// order (a fixed order, so the result does not depend on which part finished
+// last) and runs the epilogue for that region.  Nothing waits on another CTA.
 struct DigitLaunch {
     CUtensorMap maps[2 * GMAX];      // A and B map of product g at [2g], [2g + 1]
     DigitGemmParams prms[GMAX];
     int ngroups;
     const int4* work;
-    int num_items;                   // tiles (single) or work items (group)
+    int num_items;                   // work items: tiles, tile parts (single) or list entries (group)
     int stages;                      // depth of the shared-memory ring
     float2* scratch;                 // per CTA 128 x 128 double-float tile
     int* err;                        // device error flag
+    int split_begin;                 // single launches: first split tile (== tiles: none)
+    int split_ways;                  // parts per split tile (1: none)
+    float* partial;                  // [slot][part][region 8][acc 4][16-col group 4][row 32][16]
+    int* split_cnt;                  // [slot][region 8], zero at launch
 };
+
+constexpr int REGION_FLOATS = NUM_ACC * 4 * 32 * 16;  // one epilogue warp's 32 x 64 accumulators
 
 __device__ __forceinline__ void decode_banded(int t, int T, int& ti, int& tj);
 
-__device__ __forceinline__ void item_of(const DigitLaunch& L, int t, int& g, int& ti, int& tj) {
+// Work item t -> product g, tile (ti, tj), and for a part of a split tile
+// its slot (index among the split tiles) and part; slot = -1 otherwise.
+__device__ __forceinline__ void item_of(const DigitLaunch& L, int t, int& g, int& ti, int& tj, int& slot,
+                                        int& part) {
+    slot = -1;
+    part = 0;
     if (L.work) {
         const int4 w = L.work[t];
         g = w.x;
@@ -267,7 +288,25 @@ __device__ __forceinline__ void item_of(const DigitLaunch& L, int t, int& g, int
         tj = w.z;
     } else {
         g = 0;
-        decode_banded(t, L.prms[0].tiles_per_row, ti, tj);
+        int tile = t;
+        if (t >= L.split_begin) {
+            const int u = t - L.split_begin;
+            slot = u / L.split_ways;
+            part = u - slot * L.split_ways;
+            tile = L.split_begin + slot;
+        }
+        decode_banded(tile, L.prms[0].tiles_per_row, ti, tj);
+    }
+}
+
+// The k-chunks of a dense item: all of them, or the part's range.
+__device__ __forceinline__ void dense_k_range(const DigitLaunch& L, int nkt, int slot, int part, int& kb, int& nk) {
+    if (slot < 0) {
+        kb = 0;
+        nk = nkt;
+    } else {
+        kb = part * nkt / L.split_ways;
+        nk = (part + 1) * nkt / L.split_ways - kb;
     }
 }
 
@@ -360,19 +399,21 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             // producer: one continuous ring of k-chunks over all work items
             int it = 0;
             for (int t = blockIdx.x; t < num_items && !*abort_flag; t += gridDim.x) {
-                int g, ti, tj;
-                item_of(L, t, g, ti, tj);
+                int g, ti, tj, slot, part;
+                item_of(L, t, g, ti, tj, slot, part);
                 const DigitGemmParams& Pg = params_of(L, g);
                 const int tix = tj * (tj + 1) / 2 + ti;
                 const int cnt = Pg.kc_cnt ? Pg.kc_cnt[tix] : -1;  // -1: every k-chunk
                 const unsigned long long* km = cnt >= 0 ? Pg.kc_mask + (size_t)tix * Pg.kc_words : nullptr;
-                const int nk = cnt >= 0 ? cnt : Pg.n_pad / KC;
+                int kb, nk;
+                dense_k_range(L, Pg.n_pad / KC, slot, part, kb, nk);
+                if (cnt >= 0) nk = cnt;
                 const CUtensorMap* mA = &L.maps[2 * g];
                 const CUtensorMap* mB = &L.maps[2 * g + 1];
                 int w = 0;
                 unsigned long long bits = km ? km[0] : 0ull;
                 for (int c = 0; c < nk; ++c, ++it) {
-                    int kc = c;
+                    int kc = kb + c;
                     if (km) {
                         while (bits == 0ull && w + 1 < Pg.kc_words) bits = km[++w];
                         if (bits == 0ull) {  // count and mask disagree
@@ -409,11 +450,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             int it = 0, lt = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < num_items && ok; t += gridDim.x, ++lt) {
-                int g, ti, tj;
-                item_of(L, t, g, ti, tj);
+                int g, ti, tj, slot, part;
+                item_of(L, t, g, ti, tj, slot, part);
                 const DigitGemmParams& Pg = params_of(L, g);
                 const int nl = Pg.kc_cnt ? Pg.kc_cnt[tj * (tj + 1) / 2 + ti] : -1;
-                const int nk = nl >= 0 ? nl : Pg.n_pad / KC;
+                int kb, nk;
+                dense_k_range(L, Pg.n_pad / KC, slot, part, kb, nk);
+                if (nl >= 0) nk = nl;
                 if (lt > 0 && !mbar_wait_for(smem_u32(tmem_empty), (uint32_t)((lt - 1) & 1))) {
                     ok = false;
                     break;
@@ -463,11 +506,14 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
         const int quarter = warp & 3;
         const int col0 = ((warp - 2) >> 2) * (TILE / 2);
         const int row_in_tile = quarter * 32 + lane;
-        float2* scr = L.scratch + ((size_t)blockIdx.x * TILE + row_in_tile) * TILE;
+        // the CTA's double-float tile, laid out so that a warp's accesses are
+        // contiguous: region (warp) x 8-column group x lane x 8 columns
+        float2* scr = L.scratch + (size_t)blockIdx.x * TILE * TILE + (size_t)(warp - 2) * 64 * 32 + lane * 8;
         int lt = 0;
+        const int region = warp - 2;
         for (int t = blockIdx.x; t < num_items; t += gridDim.x, ++lt) {
-            int g, ti, tj;
-            item_of(L, t, g, ti, tj);
+            int g, ti, tj, slot, part;
+            item_of(L, t, g, ti, tj, slot, part);
             const DigitGemmParams& P = params_of(L, g);
             const size_t plane = (size_t)P.n_pad * P.n_pad;
             bool ready = mbar_wait_for(smem_u32(tmem_full), (uint32_t)(lt & 1));
@@ -483,7 +529,42 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             // (a tile with no k-chunk of either operand has P = 0)
             const bool empty = P.kc_cnt && P.kc_cnt[tj * (tj + 1) / 2 + ti] == 0;
             const int nacc = empty ? 0 : (s < NUM_ACC ? s : NUM_ACC);
-            for (int c0 = col0; c0 < col0 + TILE / 2; c0 += 16) {
+            if (slot >= 0) {
+                // a part of a split tile: publish this region's accumulators
+                float* mine = L.partial + ((size_t)(slot * L.split_ways + part) * EPI_WARPS + region) * REGION_FLOATS;
+#pragma unroll 1
+                for (int c0 = col0, cg = 0; c0 < col0 + TILE / 2; c0 += 16, ++cg) {
+#pragma unroll
+                    for (int a = 0; a < NUM_ACC; ++a) {
+                        if (a < nacc) {
+                            float v[16];
+                            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * TILE + c0), v);
+                            float4* d = (float4*)(mine + ((size_t)(a * 4 + cg) * 32 + lane) * 16);
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                __stcg(d + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+                        }
+                    }
+                }
+                __threadfence();
+                __syncwarp();
+                int last = 0;
+                if (lane == 0) {
+                    last = atomicAdd(&L.split_cnt[slot * EPI_WARPS + region], 1) == L.split_ways - 1;
+                    if (last) __threadfence();
+                }
+                last = __shfl_sync(0xffffffffu, last, 0);
+                if (!last) {
+                    // another part finishes this region
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0)
+                        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(tmem_empty)) : "memory");
+                    continue;
+                }
+            }
+#pragma unroll 1
+            for (int c0 = col0, cg = 0; c0 < col0 + TILE / 2; c0 += 16, ++cg) {
                 float acc[NUM_ACC][16];
 #pragma unroll
                 for (int a = 0; a < NUM_ACC; ++a) {
@@ -494,7 +575,39 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                         for (int c = 0; c < 16; ++c) acc[a][c] = 0.f;
                     }
                 }
-                float4* dst = (float4*)(scr + c0);
+                if (slot >= 0) {
+                    // the sum of all parts, in part order
+#pragma unroll
+                    for (int a = 0; a < NUM_ACC; ++a) {
+                        if (a >= nacc) continue;
+                        float sum[16];
+                        for (int q = 0; q < L.split_ways; ++q) {
+                            float v[16];
+                            if (q == part) {
+#pragma unroll
+                                for (int c = 0; c < 16; ++c) v[c] = acc[a][c];
+                            } else {
+                                const float4* src = (const float4*)(L.partial +
+                                    ((size_t)(slot * L.split_ways + q) * EPI_WARPS + region) * REGION_FLOATS +
+                                    ((size_t)(a * 4 + cg) * 32 + lane) * 16);
+#pragma unroll
+                                for (int k = 0; k < 4; ++k) {
+                                    const float4 f = __ldcg(src + k);
+                                    v[4 * k] = f.x;
+                                    v[4 * k + 1] = f.y;
+                                    v[4 * k + 2] = f.z;
+                                    v[4 * k + 3] = f.w;
+                                }
+                            }
+#pragma unroll
+                            for (int c = 0; c < 16; ++c) sum[c] = (q == 0) ? v[c] : sum[c] + v[c];
+                        }
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) acc[a][c] = sum[c];
+                    }
+                }
+                // two 8-column groups of 32 lanes x 8 float2 (128 float4 apart)
+                float4* dst = (float4*)(scr + ((c0 - col0) >> 3) * 256);
 #pragma unroll
                 for (int c = 0; c < 16; c += 2) {
                     df P0 = two_sum(acc[0][c], acc[1][c]);
@@ -503,7 +616,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                     df P1 = two_sum(acc[0][c + 1], acc[1][c + 1]);
                     P1 = df_add_f(P1, acc[2][c + 1]);
                     P1 = df_add_f(P1, acc[3][c + 1]);
-                    dst[c / 2] = make_float4(P0.h, P0.l, P1.h, P1.l);
+                    dst[c < 8 ? c / 2 : 128 + (c - 8) / 2] = make_float4(P0.h, P0.l, P1.h, P1.l);
                 }
             }
             tc_fence_before();
@@ -514,59 +627,75 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             const int i = ti * TILE + row_in_tile;
             const bool diag_tile = (ti == tj);
             const int n = P.n, n_pad = P.n_pad;
+            // the step's parameters in registers (as far as the compiler can
+            // tell, the loop's stores might alias the parameter block)
+            const bool use_E = P.use_E, affine = P.affine_out;
+            const __nv_bfloat16* const Ain = P.A;
+            const float scale_in_h = P.scale_in_h, e_scale = P.e_scale;
+            const df cP = P.cP, cE = P.cE, cI = P.cI, dY = P.dY, dI = P.dI;
+            const bool want_bn = P.bnorm2 != nullptr, want_red = P.red != nullptr;
+            double* const out64 = P.out64;
+            __nv_bfloat16* const outp = P.out;
+            const float out_digit_scale = P.out_digit_scale, out_rscale = P.out_rscale;
+            const int s_out = P.s_out;
             double s_tr = 0.0;  // the trace decides the occupation check: float64
             float s_idem = 0.f, s_fro = 0.f;
-            float bn2[2] = {0.f, 0.f};  // this row's share of two 32 x 32 output blocks
-            for (int c0 = col0; c0 < col0 + TILE / 2; c0 += 16) {
+            float bn2_0 = 0.f, bn2_1 = 0.f;  // this row's share of two 32 x 32 output blocks
+            // EW columns per pass: a short loop body keeps the epilogue's
+            // instructions resident while the other warps run
+#pragma unroll 1
+            for (int c0 = col0; c0 < col0 + TILE / 2; c0 += EW) {
                 const int jb = tj * TILE + c0;
-                df Ov[16];
+                df Ov[EW];
                 {
-                    float4 pv[8];
-                    const float4* src = (const float4*)(scr + c0);
+                    float4 pv[EW / 2];
+                    const float4* src = (const float4*)(scr + ((c0 - col0) >> 3) * 256);
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) pv[c] = src[c];
-                    // E = A at (i, jb .. jb + 15): exact two-float sum of its digits
-                    float eh[16], el[16];
+                    for (int c = 0; c < EW / 2; ++c) pv[c] = src[(c >> 2) * 128 + (c & 3)];
+                    // E = A at (i, jb .. jb + EW - 1): exact two-float sum of its digits
+                    float eh[EW], el[EW];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) eh[c] = el[c] = 0.f;
-                    if (P.use_E) {
+                    for (int c = 0; c < EW; ++c) eh[c] = el[c] = 0.f;
+                    if (use_E) {
+#pragma unroll
                         for (int p = 0; p < s; ++p) {
-                            const __nv_bfloat16* srcd = P.A + p * plane + (size_t)i * n_pad + jb;
-                            uint4 u[2];
-                            u[0] = *(const uint4*)srcd;
-                            u[1] = *(const uint4*)(srcd + 8);
+                            const __nv_bfloat16* srcd = Ain + p * plane + (size_t)i * n_pad + jb;
+                            uint4 u[EW / 8];
+#pragma unroll
+                            for (int q = 0; q < EW / 8; ++q) u[q] = ((const uint4*)srcd)[q];
                             const __nv_bfloat16* hv = (const __nv_bfloat16*)u;
                             if (p < 3) {
 #pragma unroll
-                                for (int c = 0; c < 16; ++c) eh[c] += __bfloat162float(hv[c]);
+                                for (int c = 0; c < EW; ++c) eh[c] += __bfloat162float(hv[c]);
                             } else {
 #pragma unroll
-                                for (int c = 0; c < 16; ++c) el[c] += __bfloat162float(hv[c]);
+                                for (int c = 0; c < EW; ++c) el[c] += __bfloat162float(hv[c]);
                             }
                         }
                     }
+                    float bsum = 0.f;
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) {
+                    for (int c = 0; c < EW; ++c) {
                         const int j = jb + c;
                         const float4 q4 = pv[c >> 1];
-                        const df Pv = df_scale((c & 1) ? df{q4.z, q4.w} : df{q4.x, q4.y}, P.scale_in_h);
-                        const df E = df_scale(fast_two_sum(eh[c], el[c]), P.e_scale);
-                        df Y = df_mul(P.cP, Pv);
-                        if (P.use_E) Y = df_add(Y, df_mul(P.cE, E));
-                        if (i == j) Y = df_add(Y, P.cI);
+                        const df Pv = df_scale((c & 1) ? df{q4.z, q4.w} : df{q4.x, q4.y}, scale_in_h);
+                        const df E = df_scale(fast_two_sum(eh[c], el[c]), e_scale);
+                        df Y = df_mul(cP, Pv);
+                        if (use_E) Y = df_add(Y, df_mul(cE, E));
+                        if (i == j) Y = df_add(Y, cI);
                         df O = Y;
-                        if (P.affine_out) {
-                            O = df_mul(P.dY, Y);
-                            if (i == j) O = df_add(O, P.dI);
+                        if (affine) {
+                            O = df_mul(dY, Y);
+                            if (i == j) O = df_add(O, dI);
                         }
                         const bool valid = i < n && j < n;
                         if (!valid) O = {0.f, 0.f};
                         Ov[c] = O;
-                        if (P.bnorm2 && (!diag_tile || i <= j)) {
+                        if (want_bn && (!diag_tile || i <= j)) {
                             const float bw = (i == j || ((i >> 5) != (j >> 5))) ? 1.f : 2.f;
-                            bn2[(c0 - col0) >> 5] += bw * O.h * O.h;
+                            bsum += bw * O.h * O.h;
                         }
-                        if (P.red && valid && (!diag_tile || i <= j)) {
+                        if (want_red && valid && (!diag_tile || i <= j)) {
                             const float w = (i == j) ? 1.f : 2.f;
                             if (i == j) s_tr += (double)Y.h + (double)Y.l;
                             const df dE = df_add(E, {-Pv.h, -Pv.l});
@@ -574,29 +703,35 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                             s_fro += w * Y.h * Y.h;
                         }
                     }
+                    if (c0 - col0 < 32)
+                        bn2_0 += bsum;
+                    else
+                        bn2_1 += bsum;
                 }
                 // float64 output (n x n): row segment and its mirror column
-                if (P.out64 && i < n) {
-                    for (int c = 0; c < 16; ++c) {
+                if (out64 && i < n) {
+#pragma unroll
+                    for (int c = 0; c < EW; ++c) {
                         const int j = jb + c;
                         if (j < n && (!diag_tile || i <= j)) {
                             const double v = (double)Ov[c].h + (double)Ov[c].l;
-                            P.out64[(size_t)i * n + j] = v;
-                            if (i != j) P.out64[(size_t)j * n + i] = v;
+                            out64[(size_t)i * n + j] = v;
+                            if (i != j) out64[(size_t)j * n + i] = v;
                         }
                     }
                 }
                 // digit planes of the output (next step's operand)
-                if (P.out) {
-                    df z[16];
+                if (outp) {
+                    df z[EW];
 #pragma unroll
-                    for (int c = 0; c < 16; ++c) z[c] = df_scale(Ov[c], P.out_digit_scale);
+                    for (int c = 0; c < EW; ++c) z[c] = df_scale(Ov[c], out_digit_scale);
                     float plane_scale = 1.f;
-                    const float rs = P.out_rscale, rinv = 1.f / P.out_rscale;
-                    for (int p = 0; p < P.s_out; ++p) {
-                        __align__(16) __nv_bfloat16 dv[16];
+                    const float rs = out_rscale, rinv = 1.f / out_rscale;
+#pragma unroll 1
+                    for (int p = 0; p < s_out; ++p) {
+                        __align__(16) __nv_bfloat16 dv[EW];
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) {
+                        for (int c = 0; c < EW; ++c) {
                             // z.h - d is exact; |z.l| <= ulp(z.h) / 2, so the
                             // fast two-sum renormalises exactly
                             const float d = rintf(z[c].h);
@@ -604,16 +739,16 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                             dv[c] = __float2bfloat16_rn(d * plane_scale);
                         }
                         plane_scale *= rinv;
-                        __nv_bfloat16* dst = P.out + p * plane;
+                        __nv_bfloat16* dst = outp + p * plane;
                         if (!diag_tile) {
                             uint4* row = (uint4*)(dst + (size_t)i * n_pad + jb);
-                            row[0] = ((const uint4*)dv)[0];
-                            row[1] = ((const uint4*)dv)[1];
 #pragma unroll
-                            for (int c = 0; c < 16; ++c) dst[(size_t)(jb + c) * n_pad + i] = dv[c];
+                            for (int q = 0; q < EW / 8; ++q) row[q] = ((const uint4*)dv)[q];
+#pragma unroll
+                            for (int c = 0; c < EW; ++c) dst[(size_t)(jb + c) * n_pad + i] = dv[c];
                         } else {
 #pragma unroll
-                            for (int c = 0; c < 16; ++c) {
+                            for (int c = 0; c < EW; ++c) {
                                 const int j = jb + c;
                                 if (i <= j) {
                                     dst[(size_t)i * n_pad + j] = dv[c];
@@ -628,7 +763,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                 // lanes are the 32 rows of one block row: reduce each block
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
-                    const float v = warp_sum_f(bn2[b]);
+                    const float v = warp_sum_f(b ? bn2_1 : bn2_0);
                     const int I = (ti * TILE + quarter * 32) >> 5;
                     const int J = (tj * TILE + col0 + 32 * b) >> 5;
                     if (lane == 0 && I <= J) P.bnorm2[(size_t)I * P.nb + J] = v;
@@ -659,6 +794,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
 typedef void (*KernelFn)(const DigitLaunch);
 
 // Kernel pointers of the instantiations in digits_k<KC><lo|hi>.cu.
+KernelFn kernel_k16_hi(int s);
 KernelFn kernel_k32_lo(int s);
 KernelFn kernel_k32_hi(int s);
 KernelFn kernel_k64_lo(int s);

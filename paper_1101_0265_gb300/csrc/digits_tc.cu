@@ -3,6 +3,7 @@
 // is in digits_kernel.cuh (instantiated in digits_k*.cu).
 #include "digits_kernel.cuh"
 
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -105,8 +106,9 @@ int digit_kc(int s) {
     if (forced < 0) {
         const char* e = getenv("PURIFY_DIGIT_KC");
         forced = e ? atoi(e) : 0;
-        if (forced != 32 && forced != 64) forced = 0;
+        if (forced != 16 && forced != 32 && forced != 64) forced = 0;
     }
+    if (forced == 16 && s < 4) return 32;
     if (forced) return forced;
     return s <= 3 ? 64 : 32;
 }
@@ -124,6 +126,7 @@ size_t digit_smem_bytes(int s, int kc) {
 
 KernelFn kernel_for(int kc, int s) {
     if (s < 1 || s > 6) return nullptr;
+    if (kc == 16) return s >= 4 ? kernel_k16_hi(s) : nullptr;
     if (kc == 32) return s <= 3 ? kernel_k32_lo(s) : kernel_k32_hi(s);
     if (kc == 64) return s <= 3 ? kernel_k64_lo(s) : kernel_k64_hi(s);
     return nullptr;
@@ -142,7 +145,7 @@ int prepare_kernel(KernelFn fn) {
 }
 
 int prepare_digit_kernels() {
-    for (int kc : {32, 64})
+    for (int kc : {16, 32, 64})
         for (int s = 1; s <= kMaxDigitPlanes; ++s) {
             KernelFn fn = kernel_for(kc, s);
             if (fn) PURIFY_TRY(prepare_kernel(fn));
@@ -199,18 +202,45 @@ static int launch_kernel(const DigitLaunch& L, int s, int kc, int grid, cudaStre
     return PURIFY_OK;
 }
 
+// Whole waves of the persistent grid stay whole; the tiles of the last,
+// partial wave are cut into up to 4 k-ranges (each at least 4 k-chunks) so
+// that their parts fill the grid.
+void digit_split_plan(int tiles, int ctas, int k_chunks, int* split_begin, int* ways) {
+    *split_begin = tiles;
+    *ways = 1;
+    if (ctas < 2 || tiles <= 0) return;
+    const int full = tiles / ctas * ctas;
+    const int tail = tiles - full;
+    if (tail == 0) return;
+    int w = std::min(4, ctas / tail);
+    while (w > 1 && k_chunks / w < 4) --w;
+    if (w < 2) return;
+    *split_begin = full;
+    *ways = w;
+}
+
 int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
     DigitLaunch L;
     std::memset(&L, 0, sizeof(L));
     PURIFY_TRY(fill_digit_params(st, &L.prms[0], &L.maps[0], &L.maps[1]));
     L.ngroups = 1;
     const int T = st.n_pad / TILE;
-    L.num_items = T * (T + 1) / 2;
+    const int tiles = T * (T + 1) / 2;
     const int kc = digit_kc_for(st.s_in, st.kc_cnt || st.bnorm2);
     L.stages = digit_stages(st.s_in, kc);
     L.scratch = st.scratch;
     L.err = st.err;
     if (!st.scratch || !st.err) return PURIFY_ERR_INVALID_ARG;
+    L.split_begin = tiles;
+    L.split_ways = 1;
+    if (st.partial && st.split_cnt && !st.kc_cnt)
+        digit_split_plan(tiles, st.max_ctas, st.n_pad / kc, &L.split_begin, &L.split_ways);
+    L.num_items = L.split_begin + (tiles - L.split_begin) * L.split_ways;
+    if (L.split_ways > 1) {
+        L.partial = st.partial;
+        L.split_cnt = st.split_cnt;
+        PURIFY_CUDA_TRY(cudaMemsetAsync(st.split_cnt, 0, sizeof(int) * 8 * (size_t)(tiles - L.split_begin), stream));
+    }
     const int grid = L.num_items < st.max_ctas ? L.num_items : st.max_ctas;
     return launch_kernel(L, st.s_in, kc, grid, stream);
 }
@@ -235,6 +265,8 @@ int launch_digit_group(int s, const DigitStep* steps, int count, const int4* wor
     L.stages = digit_stages(s, kc);
     L.scratch = scratch;
     L.err = err;
+    L.split_begin = num_items;  // grouped launches are not split
+    L.split_ways = 1;
     const int grid = num_items < max_ctas ? num_items : max_ctas;
     return launch_kernel(L, s, kc, grid, stream);
 }

@@ -35,7 +35,19 @@ struct DigitStep {
     const int* kc_cnt = nullptr;
     const unsigned long long* kc_mask = nullptr;
     float* bnorm2 = nullptr;
+    // split of the persistent grid's last wave along K (dense single
+    // products): partial holds digit_partial_floats(max_ctas) floats and
+    // split_cnt digit_split_counters(max_ctas) ints; null = no split
+    float* partial = nullptr;
+    int* split_cnt = nullptr;
 };
+
+inline size_t digit_partial_floats(int ctas) { return (size_t)ctas * 8 * 4 * 4 * 32 * 16; }
+inline size_t digit_split_counters(int ctas) { return (size_t)ctas * 8; }
+
+// Split plan of a single dense product: tiles [split_begin, tiles) are cut
+// into `ways` ranges of k-chunks (ways = 1: no split).
+void digit_split_plan(int tiles, int ctas, int k_chunks, int* split_begin, int* ways);
 
 // Device scratch of the persistent product kernel for a grid of `ctas`.
 inline size_t digit_scratch_bytes(int ctas) { return (size_t)ctas * 128 * 128 * sizeof(float2); }

@@ -27,6 +27,8 @@ void mixed_free(MixedState* ms) {
     cudaFree(ms->Sd);
     cudaFree(ms->err);
     cudaFree(ms->scratch);
+    cudaFree(ms->partial);
+    cudaFree(ms->split_cnt);
     cudaFree(ms->kc_buf);
     cudaFree(ms->bnorm2);
     cudaFree(ms->drops);
@@ -42,6 +44,8 @@ int ensure_mixed(purify_ctx* h, int n_pad) {
         PURIFY_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device));
         h->mixed->ctas = sms;
         PURIFY_CUDA_TRY(cudaMalloc(&h->mixed->scratch, digit_scratch_bytes(sms)));
+        PURIFY_CUDA_TRY(cudaMalloc(&h->mixed->partial, sizeof(float) * digit_partial_floats(sms)));
+        PURIFY_CUDA_TRY(cudaMalloc(&h->mixed->split_cnt, sizeof(int) * digit_split_counters(sms)));
     }
     MixedState* ms = h->mixed;
     if (n_pad <= ms->n_pad_cap) return PURIFY_OK;
@@ -84,7 +88,12 @@ static void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) 
     }
 }
 
-static int product(purify_ctx* h, const DigitStep& st, double flops) {
+static int product(purify_ctx* h, const DigitStep& st0, double flops) {
+    DigitStep st = st0;
+    if (h->opt.split_k) {
+        st.partial = h->mixed->partial;
+        st.split_cnt = h->mixed->split_cnt;
+    }
     PURIFY_TRY(product_begin(h));
     PURIFY_TRY(launch_digit_step(st, h->stream));
     ++h->st.product_launches;
@@ -295,6 +304,8 @@ extern "C" int purify_k_digit_product_f64(const double* A, const double* B, doub
     __nv_bfloat16 *pa = nullptr, *pb = nullptr;
     int* err = nullptr;
     float2* scratch = nullptr;
+    float* partial = nullptr;
+    int* split_cnt = nullptr;
     int r = PURIFY_OK;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -302,7 +313,9 @@ extern "C" int purify_k_digit_product_f64(const double* A, const double* B, doub
         return PURIFY_ERR_CUDA;
     if (cudaMalloc(&pa, plane_bytes) != cudaSuccess || cudaMalloc(&pb, plane_bytes) != cudaSuccess ||
         cudaMalloc(&err, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&scratch, digit_scratch_bytes(sms)) != cudaSuccess)
+        cudaMalloc(&scratch, digit_scratch_bytes(sms)) != cudaSuccess ||
+        cudaMalloc(&partial, sizeof(float) * digit_partial_floats(sms)) != cudaSuccess ||
+        cudaMalloc(&split_cnt, sizeof(int) * digit_split_counters(sms)) != cudaSuccess)
         r = PURIFY_ERR_OOM;
     if (r == PURIFY_OK && cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) r = PURIFY_ERR_CUDA;
     const int rb = remainder_bits(n_pad);
@@ -321,6 +334,8 @@ extern "C" int purify_k_digit_product_f64(const double* A, const double* B, doub
         st.err = err;
         st.scratch = scratch;
         st.max_ctas = sms;
+        st.partial = partial;
+        st.split_cnt = split_cnt;
         r = launch_digit_step(st, s);
     }
     int herr = 0;
@@ -335,6 +350,8 @@ extern "C" int purify_k_digit_product_f64(const double* A, const double* B, doub
     cudaFree(pb);
     cudaFree(err);
     cudaFree(scratch);
+    cudaFree(partial);
+    cudaFree(split_cnt);
     if (r == PURIFY_OK && herr) r = PURIFY_ERR_DEVICE_TIMEOUT;
     return r;
 }

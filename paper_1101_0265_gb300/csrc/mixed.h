@@ -19,6 +19,8 @@ struct MixedState {
     int* err = nullptr;
     float2* scratch = nullptr;  // persistent product kernel, one tile per CTA
     int ctas = 0;
+    float* partial = nullptr;   // split last-wave tiles: per-part accumulators
+    int* split_cnt = nullptr;   // and per-region arrival counters
     // block-sparse runs: per-tile k-chunk counts, then (8-byte aligned) the
     // per-tile k-chunk bitmasks, in one array of 8-byte words
     unsigned long long* kc_buf = nullptr;

@@ -291,6 +291,7 @@ void purify_options_default(purify_options* opt) {
     opt->refine_squares = 0;
     opt->digits = 0;
     opt->block_sparse = 0;
+    opt->split_k = 1;
     opt->trunc_tau = 1e-6;
 }
 
@@ -302,6 +303,7 @@ static int check_options(const purify_options* o) {
     if (o->refine_squares < 0 || o->refine_squares > 8) return PURIFY_ERR_INVALID_ARG;
     if (o->digits != 0 && (o->digits < 2 || o->digits > kMaxDigits)) return PURIFY_ERR_INVALID_ARG;
     if (o->block_sparse != 0 && o->block_sparse != 1) return PURIFY_ERR_INVALID_ARG;
+    if (o->split_k != 0 && o->split_k != 1) return PURIFY_ERR_INVALID_ARG;
     if (!(o->trunc_tau >= 0.0)) return PURIFY_ERR_INVALID_ARG;
     return PURIFY_OK;
 }

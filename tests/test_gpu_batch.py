@@ -35,7 +35,9 @@ def _hams():
 
 
 def _alone(P, h, scheme, tol):
-    pur = P.Purifier(precision="mixed")
+    # whole tiles, as in the batch's grouped launches (a split of the last
+    # wave changes the order of the inexact level's additions)
+    pur = P.Purifier(precision="mixed", split_k=False)
     pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
     pur.run(scheme, tol, 300)
     D = pur.density()

@@ -145,3 +145,36 @@ def test_mixed_full_size_vs_fp64(P, gap):
         pur.close()
     err = float((out[0] - out[1]).abs().max())
     assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("n,scheme", [(1000, "TC_SF"), (2200, "FIXED_MU_SF"), (4096, "TC_SF")])
+def test_split_last_wave_matches_whole_tiles(P, n, scheme):
+    # n_pad 1024: 36 tiles < 152 SMs, every tile in 4 k-ranges; n_pad 2304:
+    # 171 tiles, the 19 of the second wave in 4; n 4096: 528 tiles, the last
+    # 72 in 2.  Levels 0-2 are exact sums, so only the shared inexact level's
+    # rounding moves (by ~2^-48 of the leading term per product, then
+    # amplified near the gap like any rounding): both results stay within the
+    # mixed tolerance of the exact density and the difference is of the size
+    # of the path's own rounding error.
+    h = I.dense_hamiltonian(n, n // 2, 0.01, config=71, instance=n)
+    out = []
+    for split in (True, False):
+        pur = P.Purifier(precision="mixed", split_k=split)
+        pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+        pur.run(scheme, 1e-10, 200)
+        out.append((pur.density(), pur.stats()))
+        pur.close()
+    (Ds, ss), (Dw, sw) = out
+    assert ss["iterations"] == sw["iterations"]
+    Dx = O.density_closed_form(h.Q, h.lam, 0.0)
+    err_s, err_w = np.max(np.abs(Ds - Dx)), np.max(np.abs(Dw - Dx))
+    assert err_s <= 3e-7 and err_w <= 3e-7, (err_s, err_w)
+    assert np.max(np.abs(Ds - Dw)) <= max(err_s, err_w)
+    assert np.array_equal(Ds, Ds.T)
+    assert abs(ss["trace"] - h.nocc) < 1e-6
+    # the same split is taken on every run: bitwise reproducible
+    pur = P.Purifier(precision="mixed")
+    pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+    pur.run(scheme, 1e-10, 200)
+    assert np.array_equal(pur.density(), Ds)
+    pur.close()

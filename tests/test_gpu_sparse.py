@@ -36,7 +36,9 @@ def _lattice(L, instance=0):
 
 
 def _run(P, lat, lo, hi, tol, block_sparse, tau=0.0, coo=True, F=None, digits=0):
-    pur = P.Purifier(precision="mixed", block_sparse=block_sparse, trunc_tau=tau, digits=digits)
+    # dense runs with whole tiles: block-sparse products are never split
+    pur = P.Purifier(precision="mixed", block_sparse=block_sparse, trunc_tau=tau, digits=digits,
+                     split_k=False)
     g = lat.gap_bound
     if coo:
         pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0, lmin=lo,
@@ -119,7 +121,7 @@ def test_dense_input_through_block_sparse(P):
     h = I.dense_hamiltonian(300, 120, 0.02, config=70)
     out = []
     for bs in (False, True):
-        pur = P.Purifier(precision="mixed", block_sparse=bs, trunc_tau=0.0)
+        pur = P.Purifier(precision="mixed", block_sparse=bs, trunc_tau=0.0, split_k=False)
         pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
         pur.run("TC_SF", 1e-10, 200)
         out.append((pur.density(), pur.stats()))
