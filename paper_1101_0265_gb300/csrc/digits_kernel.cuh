@@ -26,14 +26,15 @@
 // Exact symmetry matters: antisymmetric rounding errors are not damped by
 // the purification maps.
 //
-// Structure of one CTA (one 128 x 128 output tile, 320 threads):
+// Structure of one CTA (one 128 x 128 output tile at a time, 64 + 32 EPI_WARPS
+// threads):
 //   warp 0  TMA producer: per k-chunk (16, 32 or 64 wide, with a swizzle of
 //           the chunk's row width) one 3D TMA load of all s planes of the A
 //           row panel and one of the B row panel
 //   warp 1  TMEM allocator and MMA issuer (tcgen05.mma kind::f16, bf16 in,
 //           fp32 accumulate, M = N = 128, K = 16)
-//   warps 2-9 epilogue (tcgen05.ld; warp w reads TMEM lane quarter w % 4 and
-//           one half of the tile's columns)
+//   warps 2.. epilogue (tcgen05.ld; warp w reads TMEM lane quarter w % 4 and
+//           the (w - 2) / 4-th group of EPI_COLS columns)
 // Tiles are numbered in bands of 12 tile columns so that the CTAs resident
 // at one time share row panels in L2.
 // Every wait on an mbarrier is bounded; on time-out the CTA records an error
@@ -54,8 +55,12 @@ constexpr int TILE = 128;        // output tile edge
 constexpr int BAND = 12;         // tile columns per rasterisation band
 constexpr int MAX_STAGES = 8;
 constexpr int NUM_ACC = 4;       // tensor-memory accumulators (levels 0, 1, 2, >= 3)
-constexpr int NTHREADS = 320;
-constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARPS = kEpiWarps;      // 8 or 16
+constexpr int NTHREADS = 64 + 32 * EPI_WARPS;
+constexpr int EPI_COLS = TILE * 4 / EPI_WARPS;  // columns of one epilogue warp's region
+// registers per thread: each of the SM's four sub-partitions holds 16384 and
+// takes every fourth warp
+constexpr int MAX_REGS = (16384 / (32 * ((NTHREADS / 32 + 3) / 4))) / 8 * 8;
 constexpr int EW = 8;            // epilogue columns per pass (a multiple of 8)
 constexpr long long WAIT_CYCLES = 1ll << 31;  // one wait gives up after ~1 s at 2 GHz
 
@@ -134,6 +139,17 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 }
 
 // 32 lanes x 32 bits, 16 consecutive columns per thread.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     uint32_t r[16];
     asm volatile(
@@ -271,7 +287,7 @@ struct DigitLaunch {
     int* split_cnt;                  // [slot][region 8], zero at launch
 };
 
-constexpr int REGION_FLOATS = NUM_ACC * 4 * 32 * 16;  // one epilogue warp's 32 x 64 accumulators
+constexpr int REGION_FLOATS = NUM_ACC * EPI_COLS * 32;  // one epilogue warp's accumulators
 
 __device__ __forceinline__ void decode_banded(int t, int T, int& ti, int& tj);
 
@@ -359,7 +375,7 @@ __device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity) {
 // released before the polynomial, the re-split and the stores; those overlap
 // the next tile's MMAs.  All digit counts of a launch are S.
 template <int KC, int S>
-__global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_constant__ DigitLaunch L) {
+__global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ DigitLaunch L) {
     constexpr int PLANE_BYTES = TILE * KC * 2;  // one plane of one operand per stage
     constexpr int s = S;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -502,13 +518,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             mbar_wait_for(smem_u32(drain), 0);
         }
     } else {
-        // epilogue warps 2..9: lane quarter warp % 4, column half (warp - 2) / 4
+        // epilogue warps: lane quarter warp % 4, column group (warp - 2) / 4
         const int quarter = warp & 3;
-        const int col0 = ((warp - 2) >> 2) * (TILE / 2);
+        const int col0 = ((warp - 2) >> 2) * EPI_COLS;
         const int row_in_tile = quarter * 32 + lane;
         // the CTA's double-float tile, laid out so that a warp's accesses are
         // contiguous: region (warp) x 8-column group x lane x 8 columns
-        float2* scr = L.scratch + (size_t)blockIdx.x * TILE * TILE + (size_t)(warp - 2) * 64 * 32 + lane * 8;
+        float2* scr = L.scratch + (size_t)blockIdx.x * TILE * TILE + (size_t)(warp - 2) * EPI_COLS * 32 + lane * 8;
         int lt = 0;
         const int region = warp - 2;
         for (int t = blockIdx.x; t < num_items; t += gridDim.x, ++lt) {
@@ -533,16 +549,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                 // a part of a split tile: publish this region's accumulators
                 float* mine = L.partial + ((size_t)(slot * L.split_ways + part) * EPI_WARPS + region) * REGION_FLOATS;
 #pragma unroll 1
-                for (int c0 = col0, cg = 0; c0 < col0 + TILE / 2; c0 += 16, ++cg) {
+                for (int c0 = col0, cg = 0; c0 < col0 + EPI_COLS; c0 += 8, ++cg) {
 #pragma unroll
                     for (int a = 0; a < NUM_ACC; ++a) {
                         if (a < nacc) {
-                            float v[16];
-                            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * TILE + c0), v);
-                            float4* d = (float4*)(mine + ((size_t)(a * 4 + cg) * 32 + lane) * 16);
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                __stcg(d + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+                            float v[8];
+                            tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * TILE + c0), v);
+                            float4* d = (float4*)(mine + ((size_t)(a * (EPI_COLS / 8) + cg) * 32 + lane) * 8);
+                            __stcg(d, make_float4(v[0], v[1], v[2], v[3]));
+                            __stcg(d + 1, make_float4(v[4], v[5], v[6], v[7]));
                         }
                     }
                 }
@@ -564,15 +579,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
                 }
             }
 #pragma unroll 1
-            for (int c0 = col0, cg = 0; c0 < col0 + TILE / 2; c0 += 16, ++cg) {
-                float acc[NUM_ACC][16];
+            for (int c0 = col0, cg = 0; c0 < col0 + EPI_COLS; c0 += 8, ++cg) {
+                float acc[NUM_ACC][8];
 #pragma unroll
                 for (int a = 0; a < NUM_ACC; ++a) {
                     if (a < nacc) {
-                        tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * TILE + c0), acc[a]);
+                        tmem_ld8(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(a * TILE + c0), acc[a]);
                     } else {
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) acc[a][c] = 0.f;
+                        for (int c = 0; c < 8; ++c) acc[a][c] = 0.f;
                     }
                 }
                 if (slot >= 0) {
@@ -580,43 +595,38 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
 #pragma unroll
                     for (int a = 0; a < NUM_ACC; ++a) {
                         if (a >= nacc) continue;
-                        float sum[16];
+                        float sum[8];
                         for (int q = 0; q < L.split_ways; ++q) {
-                            float v[16];
+                            float v[8];
                             if (q == part) {
 #pragma unroll
-                                for (int c = 0; c < 16; ++c) v[c] = acc[a][c];
+                                for (int c = 0; c < 8; ++c) v[c] = acc[a][c];
                             } else {
                                 const float4* src = (const float4*)(L.partial +
                                     ((size_t)(slot * L.split_ways + q) * EPI_WARPS + region) * REGION_FLOATS +
-                                    ((size_t)(a * 4 + cg) * 32 + lane) * 16);
-#pragma unroll
-                                for (int k = 0; k < 4; ++k) {
-                                    const float4 f = __ldcg(src + k);
-                                    v[4 * k] = f.x;
-                                    v[4 * k + 1] = f.y;
-                                    v[4 * k + 2] = f.z;
-                                    v[4 * k + 3] = f.w;
-                                }
+                                    ((size_t)(a * (EPI_COLS / 8) + cg) * 32 + lane) * 8);
+                                const float4 f0 = __ldcg(src), f1 = __ldcg(src + 1);
+                                v[0] = f0.x; v[1] = f0.y; v[2] = f0.z; v[3] = f0.w;
+                                v[4] = f1.x; v[5] = f1.y; v[6] = f1.z; v[7] = f1.w;
                             }
 #pragma unroll
-                            for (int c = 0; c < 16; ++c) sum[c] = (q == 0) ? v[c] : sum[c] + v[c];
+                            for (int c = 0; c < 8; ++c) sum[c] = (q == 0) ? v[c] : sum[c] + v[c];
                         }
 #pragma unroll
-                        for (int c = 0; c < 16; ++c) acc[a][c] = sum[c];
+                        for (int c = 0; c < 8; ++c) acc[a][c] = sum[c];
                     }
                 }
-                // two 8-column groups of 32 lanes x 8 float2 (128 float4 apart)
+                // one 8-column group: 32 lanes x 8 float2
                 float4* dst = (float4*)(scr + ((c0 - col0) >> 3) * 256);
 #pragma unroll
-                for (int c = 0; c < 16; c += 2) {
+                for (int c = 0; c < 8; c += 2) {
                     df P0 = two_sum(acc[0][c], acc[1][c]);
                     P0 = df_add_f(P0, acc[2][c]);
                     P0 = df_add_f(P0, acc[3][c]);
                     df P1 = two_sum(acc[0][c + 1], acc[1][c + 1]);
                     P1 = df_add_f(P1, acc[2][c + 1]);
                     P1 = df_add_f(P1, acc[3][c + 1]);
-                    dst[c < 8 ? c / 2 : 128 + (c - 8) / 2] = make_float4(P0.h, P0.l, P1.h, P1.l);
+                    dst[c / 2] = make_float4(P0.h, P0.l, P1.h, P1.l);
                 }
             }
             tc_fence_before();
@@ -644,7 +654,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             // EW columns per pass: a short loop body keeps the epilogue's
             // instructions resident while the other warps run
 #pragma unroll 1
-            for (int c0 = col0; c0 < col0 + TILE / 2; c0 += EW) {
+            for (int c0 = col0; c0 < col0 + EPI_COLS; c0 += EW) {
                 const int jb = tj * TILE + c0;
                 df Ov[EW];
                 {
@@ -762,7 +772,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) digit_gemm_kernel(const __grid_co
             if (P.bnorm2) {
                 // lanes are the 32 rows of one block row: reduce each block
 #pragma unroll
-                for (int b = 0; b < 2; ++b) {
+                for (int b = 0; b < EPI_COLS / 32; ++b) {
                     const float v = warp_sum_f(b ? bn2_1 : bn2_0);
                     const int I = (ti * TILE + quarter * 32) >> 5;
                     const int J = (tj * TILE + col0 + 32 * b) >> 5;

@@ -239,7 +239,7 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
     if (L.split_ways > 1) {
         L.partial = st.partial;
         L.split_cnt = st.split_cnt;
-        PURIFY_CUDA_TRY(cudaMemsetAsync(st.split_cnt, 0, sizeof(int) * 8 * (size_t)(tiles - L.split_begin), stream));
+        PURIFY_CUDA_TRY(cudaMemsetAsync(st.split_cnt, 0, sizeof(int) * kEpiWarps * (size_t)(tiles - L.split_begin), stream));
     }
     const int grid = L.num_items < st.max_ctas ? L.num_items : st.max_ctas;
     return launch_kernel(L, st.s_in, kc, grid, stream);

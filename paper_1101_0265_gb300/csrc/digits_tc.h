@@ -42,8 +42,12 @@ struct DigitStep {
     int* split_cnt = nullptr;
 };
 
-inline size_t digit_partial_floats(int ctas) { return (size_t)ctas * 8 * 4 * 4 * 32 * 16; }
-inline size_t digit_split_counters(int ctas) { return (size_t)ctas * 8; }
+// Epilogue warps of the product kernel (each owns a 32-row x (512 / kEpiWarps)
+// column region of the 128 x 128 tile).
+constexpr int kEpiWarps = 8;
+
+inline size_t digit_partial_floats(int ctas) { return (size_t)ctas * 4 * 128 * 128; }
+inline size_t digit_split_counters(int ctas) { return (size_t)ctas * kEpiWarps; }
 
 // Split plan of a single dense product: tiles [split_begin, tiles) are cut
 // into `ways` ranges of k-chunks (ways = 1: no split).
