@@ -34,8 +34,9 @@ SCHEMES = ("TC_SF", "FIXED_MU_SF")
 FP64_PER_BF16 = 1.25 / 2250.0   # nominal dense fp64 : bf16 ratio of GB300
 # DRAM bytes (read + write) of one digit-plane product launch, from one ncu
 # capture of digit_gemm_kernel<32, 5> at n = 4096 (bytes per launch).
-TRAFFIC_DIGIT_GEMM = 716.2e6
-TRAFFIC_SOURCE = "ncu dram__bytes_read+write of digit_gemm_kernel<32,5>, n=4096, one launch"
+TRAFFIC_DIGIT_GEMM = 799.1e6
+TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of digit_gemm_kernel<32,5>, n=4096, one launch "
+                  "(548.3 MB read + 250.8 MB written)")
 
 
 def parse():
@@ -56,7 +57,10 @@ def parse():
     ap.add_argument("--serve-rates", default="30", help="comma list; empty to skip serving")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-lattice", action="store_true", help="skip the 32^3 block-sparse workload")
+    ap.add_argument("--no-lattice", action="store_true", help="skip the L^3 block-sparse workload")
+    ap.add_argument("--lattice-size", type=int, default=32, help="L of the L^3 lattice (multiple of 4)")
+    ap.add_argument("--lattice-only", action="store_true",
+                    help="run only the lattice workload and print its object (profiling)")
     return ap.parse_args()
 
 
@@ -354,6 +358,10 @@ def main():
     else:
         torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.lattice_only:
+        stream = torch.cuda.current_stream(dev)
+        print(json.dumps({"lattice": run_lattice(P, dev, stream, L=args.lattice_size)}), flush=True)
+        return
     n = args.n
     schemes = tuple(args.schemes.split(","))
     hs, Fd = make_device_inputs(n, rank, args.matrices, dev)
@@ -492,7 +500,7 @@ def main():
         line["serve"] = [run_serve(P, dev, stream, float(r), args.serve_requests)
                          for r in args.serve_rates.split(",")]
     if world == 1 and args.precision == "mixed" and not args.no_lattice:
-        line["lattice"] = run_lattice(P, dev, stream)
+        line["lattice"] = run_lattice(P, dev, stream, L=args.lattice_size)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(hs, Fh[0].numpy(), args.tol)
     pur.close()

@@ -224,6 +224,26 @@ __device__ __forceinline__ df df_mul(df x, df y) {
 
 __device__ __forceinline__ df df_scale(df x, float pow2) { return {x.h * pow2, x.l * pow2}; }
 
+// ---- digits: float32 additions and bit operations only ---------------------
+// (both exact for digits, so no rounding or conversion instruction is needed)
+
+// Nearest integer, ties to even, for |x| < 2^22: after adding 1.5 * 2^23 the
+// sum has no fraction bits, and the subtraction is exact.
+__device__ __forceinline__ float round_digit(float x) {
+    constexpr float kMagic = 12582912.f;  // 1.5 * 2^23
+    return __fsub_rn(__fadd_rn(x, kMagic), kMagic);
+}
+
+// bf16 of a float whose low 16 bits are zero (a digit: an integer of at most
+// 8 significant bits times a power of two), exactly.
+__device__ __forceinline__ __nv_bfloat16 digit_to_bf16(float v) {
+    return __ushort_as_bfloat16((unsigned short)(__float_as_uint(v) >> 16));
+}
+
+__device__ __forceinline__ float bf16_to_float(__nv_bfloat16 v) {
+    return __uint_as_float((unsigned int)__bfloat16_as_ushort(v) << 16);
+}
+
 // ---- kernel parameters ------------------------------------------------------
 
 struct DigitGemmParams {
@@ -676,10 +696,10 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                             const __nv_bfloat16* hv = (const __nv_bfloat16*)u;
                             if (p < 3) {
 #pragma unroll
-                                for (int c = 0; c < EW; ++c) eh[c] += __bfloat162float(hv[c]);
+                                for (int c = 0; c < EW; ++c) eh[c] += bf16_to_float(hv[c]);
                             } else {
 #pragma unroll
-                                for (int c = 0; c < EW; ++c) el[c] += __bfloat162float(hv[c]);
+                                for (int c = 0; c < EW; ++c) el[c] += bf16_to_float(hv[c]);
                             }
                         }
                     }
@@ -744,9 +764,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                         for (int c = 0; c < EW; ++c) {
                             // z.h - d is exact; |z.l| <= ulp(z.h) / 2, so the
                             // fast two-sum renormalises exactly
-                            const float d = rintf(z[c].h);
+                            const float d = round_digit(z[c].h);
                             z[c] = df_scale(fast_two_sum(__fsub_rn(z[c].h, d), z[c].l), rs);
-                            dv[c] = __float2bfloat16_rn(d * plane_scale);
+                            dv[c] = digit_to_bf16(d * plane_scale);
                         }
                         plane_scale *= rinv;
                         __nv_bfloat16* dst = outp + p * plane;

@@ -18,37 +18,93 @@ namespace {
 
 // ---- float64 (with affine) -> digit planes ----------------------------------
 // out = a F + b I for i, j < n, 0 in the padding; split into s planes with
-// the scale 2^e.  F and the coefficients enter in float64; the split runs in
-// double-float.
-__global__ void split_kernel(const double* __restrict__ F, int64_t ldf, int n, int n_pad, double a,
-                             double b, float digit_scale, float rscale, int s,
-                             __nv_bfloat16* __restrict__ out, double* red) {
+// the scale 2^e.  GB300's float64 pipe runs at a small fraction of its
+// float32 rate, so the per-element arithmetic is float32 and integer: each
+// float64 F_ij is cut into two floats with integer operations (to 46 bits;
+// the digits carry at most 43), the affine map runs in double-float with a
+// and b as float pairs, and the digits come from the double-float value as in
+// the product epilogue.
+
+// x = h + l with |x - (h + l)| <= 2^-46 |x|, for 2^-74 <= |x| < 2^128 (both
+// floats normal; the caller handles other magnitudes); integer operations
+// only.
+__device__ __forceinline__ df split_double_bits(unsigned long long u) {
+    const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
+    const int E = (int)((u >> 52) & 0x7FF) - 1023;                  // x = m 2^(E - 52)
+    const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const float h = __uint_as_float(sign | (unsigned int)(E + 127) << 23 | ((unsigned int)(m >> 29) & 0x7FFFFFu));
+    // the 29 low mantissa bits times 2^(E - 52): the top 24 of them, normalised
+    const unsigned int lo29 = (unsigned int)(m & 0x1FFFFFFFu);
+    unsigned int lbits = 0;
+    if (lo29) {
+        const int bits = 32 - __clz(lo29);
+        const unsigned int mant = bits > 24 ? lo29 >> (bits - 24) : lo29 << (24 - bits);
+        lbits = sign | (unsigned int)(E - 52 + bits - 1 + 127) << 23 | (mant & 0x7FFFFFu);
+    }
+    return {h, __uint_as_float(lbits)};
+}
+
+// Magnitudes outside [2^-74, 2^128), through the float64 conversions (out of
+// line, so that the common path does not carry them).
+__device__ __noinline__ df split_double_slow(double x) {
+    const float h = (float)x;
+    return {h, (float)(x - (double)h)};
+}
+
+// One warp per 32 x 32 block (lanes on columns, loop over the 32 rows):
+// coalesced row segments of F, and, when bnorm2 is not null, the block's
+// ||.||_F^2 (float, in a fixed order) for blocks I <= J.
+__global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ F, int64_t ldf, int n, int n_pad,
+                                                    df a, df b, float digit_scale, float rscale, int s,
+                                                    __nv_bfloat16* __restrict__ out, double* red,
+                                                    float* __restrict__ bnorm2) {
+    const int nb = n_pad / 32;  // nb^2 <= 2^24: 32-bit block indices
     const int64_t total = (int64_t)n_pad * n_pad;
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
     float tr = 0.f;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)(idx / n_pad), j = (int)(idx - (int64_t)i * n_pad);
-        df z = {0.f, 0.f};
-        if (i < n && j < n) {
-            double x = a * F[(int64_t)i * ldf + j];
-            if (i == j) x += b;
-            const float h = (float)x;
-            z = {h, (float)(x - (double)h)};
-            if (i == j) tr += h + z.l;
+    for (int blk = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); blk < nb * nb; blk += warps) {
+        const int I = blk / nb, J = blk - I * nb;
+        const int j = J * 32 + lane;
+        float bsum = 0.f;
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {  // four rows' loads in flight per warp
+            const int i = I * 32 + r;
+            df z = {0.f, 0.f};
+            if (i < n && j < n) {
+                const double x = F[(int64_t)i * ldf + j];
+                const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+                const int E = (int)((u >> 52) & 0x7FF) - 1023;
+                // zeros (most of a sparse F) and normal magnitudes stay off the
+                // float64 pipe
+                df xv = {0.f, 0.f};
+                if ((u << 1) != 0) xv = (E >= -74 && E <= 127) ? split_double_bits(u) : split_double_slow(x);
+                z = df_mul(a, xv);
+                if (i == j) {
+                    z = df_add(z, b);
+                    tr += z.h + z.l;
+                }
+            }
+            bsum += z.h * z.h;
+            z = df_scale(z, digit_scale);
+            float plane_scale = 1.f;
+            const size_t at = (size_t)i * n_pad + j;
+            for (int p = 0; p < s; ++p) {
+                const float d = round_digit(z.h);
+                z = two_sum(__fsub_rn(z.h, d), z.l);
+                out[(size_t)p * total + at] = digit_to_bf16(d * plane_scale);
+                z = df_scale(z, rscale);
+                plane_scale *= (1.f / rscale);
+            }
         }
-        z = df_scale(z, digit_scale);
-        float plane_scale = 1.f;
-        for (int p = 0; p < s; ++p) {
-            const float d = rintf(z.h);
-            z = two_sum(__fsub_rn(z.h, d), z.l);
-            out[(size_t)p * total + idx] = __float2bfloat16_rn(d * plane_scale);
-            z = df_scale(z, rscale);
-            plane_scale *= (1.f / rscale);
+        if (bnorm2) {
+            bsum = warp_sum_f(bsum);
+            if (lane == 0 && I <= J) bnorm2[(size_t)I * nb + J] = bsum;
         }
     }
     if (red) {
         tr = warp_sum_f(tr);
-        if ((threadIdx.x & 31) == 0) atomicAdd(red, (double)tr);
+        if (lane == 0) atomicAdd(red, (double)tr);
     }
 }
 
@@ -272,13 +328,15 @@ int launch_digit_group(int s, const DigitStep* steps, int count, const int4* wor
 }
 
 int launch_split(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s,
-                 int rbits, __nv_bfloat16* out, double* red, cudaStream_t stream) {
-    if (s < 1 || s > kMaxDigitPlanes || n <= 0 || n_pad < n || rbits < 4 || rbits > 8)
+                 int rbits, __nv_bfloat16* out, double* red, cudaStream_t stream, float* bnorm2) {
+    if (s < 1 || s > kMaxDigitPlanes || n <= 0 || n_pad < n || n_pad % 32 || n_pad > (1 << 17) || rbits < 4 ||
+        rbits > 8)
         return PURIFY_ERR_INVALID_ARG;
-    int64_t blocks = ((int64_t)n_pad * n_pad + 255) / 256;
+    const int64_t nb = n_pad / 32;
+    int64_t blocks = (nb * nb + 7) / 8;  // 8 warps per CTA, one 32 x 32 block each
     if (blocks > 152 * 8) blocks = 152 * 8;
-    split_kernel<<<(unsigned)blocks, 256, 0, stream>>>(F, ldf, n, n_pad, a, b, ldexpf(1.f, 8 - e),
-                                                        ldexpf(1.f, rbits), s, out, red);
+    split_kernel<<<(unsigned)blocks, 256, 0, stream>>>(F, ldf, n, n_pad, to_df(a), to_df(b), ldexpf(1.f, 8 - e),
+                                                        ldexpf(1.f, rbits), s, out, red, bnorm2);
     PURIFY_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return PURIFY_OK;

@@ -72,9 +72,11 @@ int launch_digit_group(int s, const DigitStep* steps, int count, const int4* wor
 constexpr int kGroupMax = 64;
 
 // out planes of a F + b I (i, j < n; zero padding up to n_pad), exponent e,
-// s digits.  red[0] += trace (float accuracy) when red is not null.
+// s digits.  red[0] += trace (float accuracy) when red is not null;
+// bnorm2[I * (n_pad / 32) + J] = ||block (I, J)||_F^2 (float) for I <= J when
+// bnorm2 is not null.
 int launch_split(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s,
-                 int rbits, __nv_bfloat16* out, double* red, cudaStream_t stream);
+                 int rbits, __nv_bfloat16* out, double* red, cudaStream_t stream, float* bnorm2 = nullptr);
 
 // Bits of the remainder digits for a padded size: 7 up to 4096 (level-2
 // sums of squares stay below 2^24), 6 above.

@@ -148,16 +148,16 @@ step_f64_kernel(const double* __restrict__ A, const double* __restrict__ B,
     }
 }
 
+// Rows over the grid, columns over the threads (no 64-bit division: that runs
+// on the float64 pipe).
 __global__ void affine_f64_kernel(const double* __restrict__ F, int64_t ldf, double* __restrict__ out,
                                   int64_t n, double a, double b) {
-    const int64_t total = n * n;
-    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = idx / n, j = idx - i * n;
-        double v = a * F[i * ldf + j];
-        if (i == j) v += b;
-        out[idx] = v;
-    }
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x)
+        for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+            double v = a * F[i * ldf + j];
+            if (i == j) v += b;
+            out[i * n + j] = v;
+        }
 }
 
 // Copy the upper triangle onto the lower one, 32 x 32 tiles through shared
@@ -221,8 +221,7 @@ int launch_step_f64(const double* A, const double* B, const double* E, double* C
 int launch_affine_f64(const double* F, int64_t ldf, double* out, int64_t n, double a, double b,
                       cudaStream_t s) {
     if (n <= 0) return PURIFY_ERR_INVALID_ARG;
-    int64_t blocks = (n * n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    const int64_t blocks = n < 152 * 16 ? n : 152 * 16;
     affine_f64_kernel<<<(unsigned)blocks, 256, 0, s>>>(F, ldf, out, n, a, b);
     PURIFY_CUDA_TRY(cudaGetLastError());
     count_launches(1);

@@ -28,37 +28,6 @@ namespace purify {
 
 namespace {
 
-// ||block (I, J) of c0 I + c1 F||_F^2 for upper blocks, J-major block number.
-__global__ void x0_block_norms_kernel(const double* __restrict__ F, int n, int nb, double c0, double c1,
-                                      float* __restrict__ bn) {
-    const int t = blockIdx.x;
-    int J = (int)((sqrt(8.0 * t + 1.0) - 1.0) * 0.5);
-    while ((J + 1) * (J + 2) / 2 <= t) ++J;
-    while (J * (J + 1) / 2 > t) --J;
-    const int I = t - J * (J + 1) / 2;
-    double s = 0.0;
-    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-        const int i = I * 32 + (e >> 5), j = J * 32 + (e & 31);
-        if (i >= n || j >= n) continue;
-        double w = 1.0;
-        if (I == J) {
-            if (i > j) continue;
-            w = (i == j) ? 1.0 : 2.0;
-        }
-        double x = c1 * F[(size_t)i * n + j];
-        if (i == j) x += c0;
-        s += w * x * x;
-    }
-    __shared__ double red[256];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) bn[(size_t)I * nb + J] = (float)red[0];
-}
-
 // Zero blocks (I, J) and (J, I) in s digit planes.
 __global__ void mask_planes_kernel(__nv_bfloat16* planes, int s, int n_pad, const int2* blocks) {
     const int2 b = blocks[blockIdx.x];
@@ -293,12 +262,10 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     const double c0 = lmax / (lmax - lmin), c1 = -1.0 / (lmax - lmin);
     std::vector<float> bn2((size_t)nb * nb, 0.f);
     ms->nnzb_history.clear();
-    // X_0 = c0 I + c1 F: its block pattern, truncated like every iterate
-    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->bnorm2, 0, sizeof(float) * (size_t)nb * nb, h->stream));
-    x0_block_norms_kernel<<<(unsigned)(nb * (nb + 1) / 2), 256, 0, h->stream>>>(h->F, n, nb, c0, c1, ms->bnorm2);
-    PURIFY_CUDA_TRY(cudaGetLastError());
-    count_launches(1);
-    PURIFY_TRY(launch_split(h->F, n, n, n_pad, c1, c0, 0, std::max(sd[0], 1), rb, ms->Xd[0], nullptr, h->stream));
+    // X_0 = c0 I + c1 F and its block norms (from the split): its block
+    // pattern, truncated like every iterate
+    PURIFY_TRY(launch_split(h->F, n, n, n_pad, c1, c0, 0, std::max(sd[0], 1), rb, ms->Xd[0], nullptr, h->stream,
+                            ms->bnorm2));
     PURIFY_CUDA_TRY(cudaMemcpyAsync(bn2.data(), ms->bnorm2, sizeof(float) * (size_t)nb * nb,
                                     cudaMemcpyDeviceToHost, h->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));

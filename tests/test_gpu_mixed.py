@@ -178,3 +178,22 @@ def test_split_last_wave_matches_whole_tiles(P, n, scheme):
     pur.run(scheme, 1e-10, 200)
     assert np.array_equal(pur.density(), Ds)
     pur.close()
+
+
+@pytest.mark.parametrize("scale", [1e-25, 1e30])
+def test_extreme_magnitudes_split_exactly(P, scale):
+    # entries below 2^-74 take the split's float64 route, entries near 2^100
+    # the top of its integer route; the density of s F with bounds s lambda is
+    # that of F
+    h = I.dense_hamiltonian(300, 120, 0.05, config=73)
+    out = []
+    for sc in (1.0, scale):
+        pur = P.Purifier(precision="mixed")
+        pur.set_hamiltonian(h.F * sc, nocc=h.nocc, mu=0.0, lmin=h.lmin * sc, lmax=h.lmax * sc,
+                            homo=h.homo * sc, lumo=h.lumo * sc)
+        pur.run("TC_SF", 1e-10, 200)
+        out.append(pur.density())
+        pur.close()
+    assert np.max(np.abs(out[0] - out[1])) < 1e-9
+    Dx = O.density_closed_form(h.Q, h.lam, 0.0)
+    assert np.max(np.abs(out[1] - Dx)) < 3e-7
