@@ -68,10 +68,24 @@ def workload_specs(n):
     return [(nocc, gap) for nocc in (n // 2, n // 4) for gap in GAPS]
 
 
+def rank_instance(rank, i):
+    """Seed instance of matrix i on rank `rank`: every replica purifies its own
+    matrices (distinct seeds), the same workload shape on every rank."""
+    return 1000 * rank + i
+
+
+def replica_rate(ms_local, units_per_rank, world, allreduce_max):
+    """Whole-job throughput of independent replicas: all ranks processed
+    units_per_rank units each, and the job took the slowest rank's time
+    (allreduce_max maps a rank's value to the maximum over ranks)."""
+    ms = allreduce_max(ms_local)
+    return world * units_per_rank / (ms * 1e-3), ms
+
+
 def make_inputs(n, rank, count=None):
     from paper_1101_0265_gb300 import inputs as I
     specs = workload_specs(n)[:count]
-    return [I.dense_hamiltonian(n, nocc, gap, config=2, instance=1000 * rank + i)
+    return [I.dense_hamiltonian(n, nocc, gap, config=2, instance=rank_instance(rank, i))
             for i, (nocc, gap) in enumerate(specs)]
 
 
@@ -80,7 +94,7 @@ def make_device_inputs(n, rank, count, dev):
     from paper_1101_0265_gb300 import inputs as I
     hs, Fs = [], []
     for i, (nocc, gap) in enumerate(workload_specs(n)[:count]):
-        spec = I.InstanceSpec(n=n, nocc=nocc, gap=gap, scheme="TC_SF", instance=1000 * rank + i,
+        spec = I.InstanceSpec(n=n, nocc=nocc, gap=gap, scheme="TC_SF", instance=rank_instance(rank, i),
                               config=2)
         F, h = I.dense_hamiltonian_device(spec, dev)
         hs.append(h)
@@ -418,23 +432,25 @@ def main():
         ck = sampler.stop() if sampler else None
         if dist:
             dist.barrier()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, ck
+        return e0.elapsed_time(e1), ck
+
+    def max_over_ranks(ms):
+        if not dist:
+            return ms
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
 
     for _ in range(args.warmup):
         step()
-    ms, clocks = timed(args.steps, record=True, clocks=True)
+    ms_local, clocks = timed(args.steps, record=True, clocks=True)
     per_step = len(hs) * len(schemes)
-    value = world * per_step * args.steps / (ms * 1e-3)
+    value, ms = replica_rate(ms_local, per_step * args.steps, world, max_over_ranks)
     # end to end: host F in, host D out, copies inside the timed region
     step(host=True)
-    ms_e2e, _ = timed(max(1, args.steps // 2), host=True)
     k_e2e = max(1, args.steps // 2)
-    value_e2e = world * per_step * k_e2e / (ms_e2e * 1e-3)
+    ms_e2e_local, _ = timed(k_e2e, host=True)
+    value_e2e, ms_e2e = replica_rate(ms_e2e_local, per_step * k_e2e, world, max_over_ranks)
 
     pk, pk_kind = peaks()
     steps_launched = args.steps

@@ -98,7 +98,12 @@ typedef struct purify_options {
                             grid's last, partial wave into k-ranges that run on
                             the idle SMs and are added in a fixed order (default 1;
                             0 = whole tiles, the grouping the batch engine uses) */
-    int reserved[8];
+    int refine_fp64;     /* MIXED: float64 McWeeny steps X <- 3X^2 - 2X^3 (two float64
+                            products each, on the GPU's float64 pipe) appended to the
+                            run, which set the final idempotency (0 = none, default;
+                            at most 2); stats.trace and stats.idem_err_fro then
+                            describe the last of them                              */
+    int reserved[7];
     double trunc_tau;    /* block_sparse: per-step truncation budget: blocks of
                             smallest Frobenius norm are dropped while the dropped
                             mass (off-diagonal blocks twice) stays <= tau^2       */

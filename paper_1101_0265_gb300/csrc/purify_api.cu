@@ -292,6 +292,7 @@ void purify_options_default(purify_options* opt) {
     opt->digits = 0;
     opt->block_sparse = 0;
     opt->split_k = 1;
+    opt->refine_fp64 = 0;
     opt->trunc_tau = 1e-6;
 }
 
@@ -304,6 +305,7 @@ static int check_options(const purify_options* o) {
     if (o->digits != 0 && (o->digits < 2 || o->digits > kMaxDigits)) return PURIFY_ERR_INVALID_ARG;
     if (o->block_sparse != 0 && o->block_sparse != 1) return PURIFY_ERR_INVALID_ARG;
     if (o->split_k != 0 && o->split_k != 1) return PURIFY_ERR_INVALID_ARG;
+    if (o->refine_fp64 < 0 || o->refine_fp64 > 2) return PURIFY_ERR_INVALID_ARG;
     if (!(o->trunc_tau >= 0.0)) return PURIFY_ERR_INVALID_ARG;
     return PURIFY_OK;
 }
@@ -538,6 +540,34 @@ static void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) 
     }
 }
 
+// Float64 McWeeny steps X <- 3 X^2 - 2 X^3 on the current density (the
+// refinement squares that set the final idempotency after a mixed run).
+// Sets the trace of the last result and ||X - X^2||_F of its input.
+static int refine_f64(purify_ctx* h, int R) {
+    if (R <= 0 || h->cur < 0) return PURIFY_OK;
+    PURIFY_TRY(ensure_red(h, 4 * (int64_t)(2 * R)));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 8 * R, h->stream));
+    int x = h->cur;
+    for (int r = 0; r < R; ++r) {
+        double* X = h->X[x];
+        // S = X^2, reducing ||X - X^2||_F^2 (E = X)
+        PURIFY_TRY(step64(h, X, X, X, h->S, 1.0, 0.0, 0.0, 1.0, 0.0, 2 * r));
+        // X' = 3 S - 2 S X
+        PURIFY_TRY(step64(h, h->S, X, h->S, h->X[x ^ 1], -2.0, 3.0, 0.0, 1.0, 0.0, 2 * r + 1));
+        x ^= 1;
+    }
+    h->cur = x;
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+    std::vector<double> red(8 * (size_t)R);
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(red.data(), h->red, sizeof(double) * red.size(), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->st.trace = red[4 * (size_t)(2 * R - 1)];
+    h->st.idem_err_fro = std::sqrt(std::max(red[4 * (size_t)(2 * R - 2) + 1], 0.0));
+    h->st.refine_multiplications += 2 * R;
+    return PURIFY_OK;
+}
+
 static int run_fp64(purify_ctx* h, int scheme, double tol, int max_iter, double mu, Schedule& S,
                     bool trace_rule, int* iters_out, std::vector<double>& red_host) {
     const int64_t n = h->n;
@@ -699,6 +729,7 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
         } else {
             r = run_mixed(h, scheme, mu, S, &h->cur, red);
         }
+        if (r == PURIFY_OK) r = refine_f64(h, h->opt.refine_fp64);
         iters = (int)S.alpha.size();
     } else {
         r = run_fp64(h, scheme, tol, max_iter, mu, S, trace_rule, &iters, red);

@@ -197,3 +197,29 @@ def test_extreme_magnitudes_split_exactly(P, scale):
     assert np.max(np.abs(out[0] - out[1])) < 1e-9
     Dx = O.density_closed_form(h.Q, h.lam, 0.0)
     assert np.max(np.abs(out[1] - Dx)) < 3e-7
+
+
+def test_fp64_refinement_sets_idempotency(P):
+    # mixed run, then 0, 1 or 2 float64 McWeeny steps: the subspace (error
+    # against the exact density) is that of the mixed run, the idempotency
+    # error falls to float64 rounding
+    h = I.dense_hamiltonian(512, 200, 0.01, config=74)
+    Dx = O.density_closed_form(h.Q, h.lam, 0.0)
+    res = []
+    for R in (0, 1, 2):
+        pur = P.Purifier(precision="mixed", refine_fp64=R)
+        pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+        pur.run("TC_SF", 1e-10, 200)
+        D, st = pur.density(), pur.stats()
+        pur.close()
+        res.append((D, st, np.linalg.norm(D - D @ D)))
+    (D0, s0, e0), (D1, s1, e1), (D2, s2, e2) = res
+    for D, st, _ in res:
+        assert np.max(np.abs(D - Dx)) <= 3e-7
+        assert np.array_equal(D, D.T)
+    assert s1["refine_multiplications"] == 2 and s2["refine_multiplications"] == 4
+    assert s1["multiplications"] == s0["multiplications"] + 2
+    assert e1 < 1e-11 < e0 and e2 < 1e-11
+    # the reported idempotency error is that of the last refinement's input
+    assert abs(s1["idem_err_fro"] - e0) <= 1e-3 * e0
+    assert abs(s1["trace"] - h.nocc) < 1e-9
