@@ -180,7 +180,11 @@ int purify_block_history(purify_t h, int* nnz_blocks, int cap, int* count);
  * PURIFY_BRANCH_TRACE without gap bounds, until ||X - X^2||_F <= tol; at most
  * max_iter iterations.  Returns PURIFY_ERR_NOT_CONVERGED (stats filled,
  * density available) when max_iter is reached, and PURIFY_ERR_BOUNDS when
- * nocc >= 0 and the final trace differs from nocc by more than 0.5. */
+ * nocc >= 0 and the final trace differs from nocc by more than 0.5.
+ * PURIFY_BRANCH_TRACE takes each branch from trace(X_{i-1}) on both
+ * precisions (one host round trip per step; on the mixed path the trace is
+ * reduced in float64 by the previous product's epilogue); it is unsupported
+ * with block_sparse. */
 int purify_run(purify_t h, int scheme, double tol, int max_iter);
 
 /* Copy the current density matrix (the last X_i, symmetric, n x n) into D

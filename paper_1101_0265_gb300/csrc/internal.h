@@ -73,6 +73,11 @@ struct Schedule {
     bool converged = false;
 };
 
+// Algorithm 2's scalar pieces (float64, host): alpha of a branch (1 = P_{1,0},
+// 0 = P_{0,1}) and the branch's map of a scalar (Eq. 4 / Eq. 5).
+double tc_alpha(int branch, double b, double bb);
+double tc_map(int branch, double a, double x);
+
 struct MixedState;
 
 }  // namespace purify

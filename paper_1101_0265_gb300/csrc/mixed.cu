@@ -101,6 +101,113 @@ static int product(purify_ctx* h, const DigitStep& st0, double flops) {
     return product_end(h);
 }
 
+int run_mixed_trace(purify_ctx* h, int scheme, double tol, int max_iter, Schedule& S, int* cur, int* iters) {
+    if (scheme != PURIFY_TC_SF && scheme != PURIFY_TC_MONO) return PURIFY_ERR_UNSUPPORTED;
+    if (h->nocc < 0) return PURIFY_ERR_INVALID_ARG;
+    const int n = (int)h->n;
+    const int n_pad = pad128(n);
+    PURIFY_TRY(ensure_mixed(h, n_pad));
+    MixedState* ms = h->mixed;
+    const int T = n_pad / 128;
+    const int rb = remainder_bits(n_pad);
+    const double tile_flops = 2.0 * 128.0 * 128.0 * (double)n_pad * (double)(T * (T + 1) / 2);
+    const bool have_gap = !std::isnan(h->b.homo) && !std::isnan(h->b.lumo);
+    const bool scaled = scheme == PURIFY_TC_SF;
+    const int fixed = h->opt.digits;
+    const double lmin = h->b.lmin, lmax = h->b.lmax;
+    const double c0 = lmax / (lmax - lmin), c1 = -1.0 / (lmax - lmin);
+    double b = S.beta0, bb = S.betabar0;
+    auto digits = [&](double beta, double betabar) {
+        return have_gap ? digits_for_gap(betabar - beta, fixed, rb) : (fixed > 0 ? fixed : kMaxDigitPlanes);
+    };
+    S.alpha.clear();
+    S.branch.clear();
+    S.beta.clear();
+    S.betabar.clear();
+    // slots 0 .. max_iter - 1: the steps; slot max_iter: trace(F)
+    PURIFY_TRY(ensure_red(h, 4 * (int64_t)(max_iter + 1)));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * (max_iter + 1), h->stream));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), h->stream));
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+    double* trF = h->red + 4 * (int64_t)max_iter;
+    PURIFY_TRY(launch_trace_f64(h->F, n, trF, h->stream));
+    int s = digits(b, bb);
+    PURIFY_TRY(launch_split(h->F, n, n, n_pad, c1, c0, 0, s, rb, ms->Xd[0], nullptr, h->stream));
+    double tf = 0.0;
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(&tf, trF, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    double tr_prev = c0 * (double)n + c1 * tf;  // trace(X_0)
+    double* D = h->X[0];
+    *cur = 0;
+    int x = 0, it = 0, dmax = 0;
+    bool done = have_gap && std::max(b, 1.0 - bb) <= tol;
+    if (done) PURIFY_TRY(launch_affine_f64(h->F, n, D, n, c1, c0, h->stream));
+    while (!done && it < max_iter) {
+        const int br = tr_prev > (double)h->nocc ? 1 : 0;
+        const double a = scaled ? tc_alpha(br, b, bb) : 0.0;
+        double nb = b, nbb = bb;
+        if (have_gap) {
+            nb = tc_map(br, a, b);
+            nbb = tc_map(br, a, bb);
+        }
+        // with gap bounds the last step is known before it runs; without,
+        // every step also writes the float64 density
+        const bool last_known = have_gap && std::max(nb, 1.0 - nbb) <= tol;
+        DigitStep st;
+        st.n = n;
+        st.n_pad = n_pad;
+        st.rbits = rb;
+        st.A = st.B = ms->Xd[x];
+        st.s_in = s;
+        st.eA = st.eB = 0;
+        st.use_E = 1;
+        tc_coeffs(br, a, &st.cP, &st.cE, &st.cI);
+        st.red = h->red + 4 * (int64_t)it;
+        st.err = ms->err;
+        st.scratch = ms->scratch;
+        st.max_ctas = ms->ctas;
+        const int s_next = digits(nb, nbb);
+        if (!have_gap || last_known) st.out64 = D;
+        if (!last_known) {
+            st.out = ms->Xd[x ^ 1];
+            st.s_out = s_next;
+            st.e_out = 0;
+        }
+        PURIFY_TRY(product(h, st, 0.5 * s * (s + 1) * tile_flops));
+        dmax = std::max(dmax, s);
+        double r[4];
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(r, st.red, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        tr_prev = r[0];
+        h->st.trace = r[0];
+        h->st.idem_err_fro = std::sqrt(std::max(r[1], 0.0));
+        b = nb;
+        bb = nbb;
+        S.alpha.push_back(a);
+        S.branch.push_back(br);
+        S.beta.push_back(b);
+        S.betabar.push_back(bb);
+        ++it;
+        x ^= 1;
+        s = s_next;
+        if (have_gap) done = last_known;
+        else done = h->st.idem_err_fro <= tol;
+    }
+    S.converged = done;
+    h->st.digit_max = dmax;
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+    int err = 0;
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, ms->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (err) return PURIFY_ERR_DEVICE_TIMEOUT;
+    if (it == 0) {
+        h->st.trace = tr_prev;
+        h->st.idem_err_fro = NAN;
+    }
+    *iters = it;
+    return PURIFY_OK;
+}
+
 int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
               std::vector<double>& red) {
     const int n = (int)h->n;

@@ -44,6 +44,12 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
 // tcgen05 tensor cores (see mixed.cu).  Sets *cur (index into h->X of the
 // float64 density), fills `red` with the per-step reductions and the
 // mixed-path fields of h->st.
+// Algorithm 2 with Niklasson's trace rule on the mixed path: the branch of
+// each step from trace(X_{i-1}) (reduced in float64 by the previous step's
+// epilogue; for X_0 from trace(F)); one host round trip per step.  With gap
+// bounds beta and beta_bar follow the branches taken; without them the run
+// stops when ||X - X^2||_F <= tol.  Fills S with the steps taken.
+int run_mixed_trace(purify_ctx* h, int scheme, double tol, int max_iter, Schedule& S, int* cur, int* iters);
 int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
               std::vector<double>& red);
 void mixed_free(MixedState* ms);

@@ -61,12 +61,12 @@ static void tc_beta0(double lmin, double lmax, double homo, double lumo, double*
 static int tc_branch(double b, double bb) { return (b + bb) > 1.0 ? 1 : 0; }
 
 // Algorithm 2: alpha of the chosen branch.
-static double tc_alpha(int branch, double b, double bb) {
+double tc_alpha(int branch, double b, double bb) {
     return branch ? b / (2.0 - b) : (1.0 - bb) / (1.0 + bb);
 }
 
 // Eq. 4 (branch 1) / Eq. 5 (branch 0) on a scalar.
-static double tc_map(int branch, double a, double x) {
+double tc_map(int branch, double a, double x) {
     if (branch) {
         const double y = (1.0 + a) * x - a;
         return y * y;
@@ -721,8 +721,10 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
     int r;
     if (h->opt.block_sparse && h->opt.precision != PURIFY_MIXED) return PURIFY_ERR_UNSUPPORTED;
     if (h->opt.precision == PURIFY_MIXED) {
-        if (trace_rule) return PURIFY_ERR_UNSUPPORTED;
-        if (h->opt.block_sparse) {
+        if (trace_rule && h->opt.block_sparse) return PURIFY_ERR_UNSUPPORTED;
+        if (trace_rule) {
+            r = run_mixed_trace(h, scheme, tol, max_iter, S, &h->cur, &iters);
+        } else if (h->opt.block_sparse) {
             r = run_block_sparse(h, scheme, S, &h->cur, red);
             if (r == PURIFY_OK && h->mixed && !h->mixed->nnzb_history.empty())
                 h->st.nnz_blocks = h->mixed->nnzb_history.back();
@@ -730,7 +732,7 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
             r = run_mixed(h, scheme, mu, S, &h->cur, red);
         }
         if (r == PURIFY_OK) r = refine_f64(h, h->opt.refine_fp64);
-        iters = (int)S.alpha.size();
+        if (!trace_rule) iters = (int)S.alpha.size();
     } else {
         r = run_fp64(h, scheme, tol, max_iter, mu, S, trace_rule, &iters, red);
     }

@@ -223,3 +223,28 @@ def test_fp64_refinement_sets_idempotency(P):
     # the reported idempotency error is that of the last refinement's input
     assert abs(s1["idem_err_fro"] - e0) <= 1e-3 * e0
     assert abs(s1["trace"] - h.nocc) < 1e-9
+
+
+@pytest.mark.parametrize("scheme,gap_known", [("TC_MONO", False), ("TC_SF", True), ("TC_MONO", True)])
+def test_trace_rule_on_the_mixed_path(P, scheme, gap_known):
+    # Niklasson's trace rule: each branch from trace(X_{i-1}) versus nocc,
+    # reduced in float64 by the previous product's epilogue; without gap
+    # bounds the run stops when ||X - X^2||_F <= tol (reachable at the mixed
+    # path's precision: 1e-5)
+    h = I.dense_hamiltonian(300, 110, 0.05, config=75)
+    tol = 1e-9 if gap_known else 1e-5
+    kw = dict(homo=h.homo, lumo=h.lumo) if gap_known else {}
+    pur = P.Purifier(precision="mixed", branch_rule="trace")
+    pur.set_hamiltonian(h.F, nocc=h.nocc, lmin=h.lmin, lmax=h.lmax, **kw)
+    pur.run(scheme, tol, 200)
+    D, st = pur.density(), pur.stats()
+    pur.close()
+    Do, r = O.purify_tc(h.F, h.lmin, h.lmax, tol=tol, scaled=scheme == "TC_SF", branch_rule="trace",
+                        nocc=h.nocc, max_iter=200, **kw)
+    assert r.converged
+    assert st["iterations"] == r.iterations
+    assert st["multiplications"] == r.multiplications
+    assert np.max(np.abs(D - Do)) <= 3e-7
+    assert abs(st["trace"] - h.nocc) < 1e-6
+    Dx = O.density_closed_form(h.Q, h.lam, 0.0)
+    assert np.max(np.abs(D - Dx)) <= 3e-7 + (tol if not gap_known else 0.0)
