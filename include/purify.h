@@ -154,6 +154,8 @@ int purify_destroy(purify_t h);
 int purify_set_options(purify_t h, const purify_options* opt);
 
 /* Load F (n x n, leading dimension ld, host or device) and its landmarks.
+ * A host F has been read when the call returns; a device F is read on the
+ * handle's stream after the work already queued on the caller's stream.
  * nocc < 0 means unknown; mu NaN means mu = (homo + lumo) / 2 (fixed-mu
  * schemes).  When b->lmin or b->lmax is NaN, the bounds are estimated here
  * (Gershgorin discs, then `lanczos_steps` Lanczos steps from a SplitMix64
@@ -266,8 +268,9 @@ int64_t purify_batch_footprint(int64_t n);
 int purify_batch_create(purify_batch_t* b, int device, void* cuda_stream, const purify_options* opt);
 int purify_batch_destroy(purify_batch_t b);
 
-/* Add one instance: F (n x n, leading dimension ld, host or device; copied;
- * upper triangle read), nocc (< 0: unknown), mu (fixed-mu schemes; NaN: the
+/* Add one instance: F (n x n, leading dimension ld, host or device; copied,
+ * a host F before the call returns; upper triangle read), nocc (< 0:
+ * unknown), mu (fixed-mu schemes; NaN: the
  * gap centre), all four bounds required, scheme, tol, max_iter.  Allocates
  * the instance's device memory (purify_batch_footprint) and writes its id. */
 int purify_batch_add(purify_batch_t b, const double* F, int64_t n, int64_t ld, int64_t nocc, double mu,

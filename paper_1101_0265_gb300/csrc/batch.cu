@@ -442,10 +442,7 @@ int purify_batch_add(purify_batch_t B, const double* F, int64_t n, int64_t ld, i
         return PURIFY_ERR_OOM;
     }
     in->bytes = 2 * nb + (fixed_mu_scheme(scheme) ? 3 : 2) * plane_bytes;
-    r = PURIFY_OK;
-    if (cudaMemcpy2DAsync(in->F, sizeof(double) * n, F, sizeof(double) * ld, sizeof(double) * n, n,
-                          cudaMemcpyDefault, B->stream) != cudaSuccess)
-        r = PURIFY_ERR_CUDA;
+    r = copy_in_matrix(in->F, F, n, ld, B->stream);
     if (r == PURIFY_OK) r = launch_mirror_upper_f64(in->F, n, B->stream);
     if (r != PURIFY_OK) {
         free_instance(*in);

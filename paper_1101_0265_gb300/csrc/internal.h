@@ -114,6 +114,10 @@ namespace purify {
 // Order `work` after what the caller queued on `user` (join_in) and the
 // caller's stream after the library's work (join_out).
 int join_streams(cudaStream_t after, cudaStream_t before, cudaEvent_t ev);
+// Copy an n x n float64 matrix (leading dimension ld, host or device) into
+// dst (leading dimension n) on `s`.  A host source has been read when this
+// returns (the caller may reuse it); a device source is read in stream order.
+int copy_in_matrix(double* dst, const double* src, int64_t n, int64_t ld, cudaStream_t s);
 // Product timing: bracket one product launch with events when requested.
 int product_begin(purify_ctx* h);
 int product_end(purify_ctx* h);

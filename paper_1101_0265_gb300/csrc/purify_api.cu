@@ -240,6 +240,19 @@ int purify::join_streams(cudaStream_t after, cudaStream_t before, cudaEvent_t ev
     return PURIFY_OK;
 }
 
+int purify::copy_in_matrix(double* dst, const double* src, int64_t n, int64_t ld, cudaStream_t s) {
+    cudaPointerAttributes attr;
+    PURIFY_CUDA_TRY(cudaPointerGetAttributes(&attr, src));
+    const bool host = attr.type == cudaMemoryTypeHost || attr.type == cudaMemoryTypeUnregistered;
+    if (ld == n)
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)n * n, cudaMemcpyDefault, s));
+    else
+        PURIFY_CUDA_TRY(cudaMemcpy2DAsync(dst, sizeof(double) * n, src, sizeof(double) * ld, sizeof(double) * n,
+                                          n, cudaMemcpyDefault, s));
+    if (host) PURIFY_CUDA_TRY(cudaStreamSynchronize(s));
+    return PURIFY_OK;
+}
+
 static int join_in(purify_ctx* h) { return join_streams(h->stream, h->user_stream, h->join_ev); }
 static int join_out(purify_ctx* h) { return join_streams(h->user_stream, h->stream, h->join_ev); }
 
@@ -446,8 +459,7 @@ int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld, i
     PURIFY_TRY(join_in(h));
     PURIFY_TRY(ensure_capacity(h, n));
     h->n = n;
-    PURIFY_CUDA_TRY(cudaMemcpy2DAsync(h->F, sizeof(double) * n, F, sizeof(double) * ld,
-                                      sizeof(double) * n, n, cudaMemcpyDefault, h->stream));
+    PURIFY_TRY(copy_in_matrix(h->F, F, n, ld, h->stream));
     PURIFY_TRY(launch_mirror_upper_f64(h->F, n, h->stream));
     return finish_set(h, n, nocc, mu, b, set_launches0);
 }

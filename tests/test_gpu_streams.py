@@ -53,3 +53,26 @@ def test_batch_waits_for_callers_stream(P):
     B.run(use_graph=True)
     assert np.max(np.abs(B.density(i) - Do)) <= 1e-7
     B.close()
+
+
+def test_host_input_is_read_before_the_call_returns(P):
+    # a pinned host F may be overwritten as soon as set_hamiltonian / batch
+    # add return
+    from paper_1101_0265_gb300 import inputs as I
+    from oracle import purify_oracle as O
+    h = I.dense_hamiltonian(2048, 1000, 0.05, config=76)
+    Dx = O.density_closed_form(h.Q, h.lam, 0.0)
+    F = torch.from_numpy(h.F.copy()).pin_memory()
+    pur = P.Purifier(precision="mixed")
+    pur.set_hamiltonian(F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+    F.fill_(float("nan"))
+    pur.run("TC_SF", 1e-9, 200)
+    assert np.max(np.abs(pur.density() - Dx)) < 3e-7
+    pur.close()
+    F.copy_(torch.from_numpy(h.F))
+    B = P.Batch()
+    i = B.add(F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme="TC_SF", tol=1e-9, mu=0.0)
+    F.fill_(float("nan"))
+    B.run()
+    assert np.max(np.abs(B.density(i) - Dx)) < 3e-7
+    B.close()
