@@ -184,27 +184,27 @@ def run_serve(P, dev, stream, rate, count, budget_gb=64.0, tol=1e-9):
             "peak_concurrent": peak_live, "hbm_budget_gb": budget_gb}
 
 
-def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9):
+def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsite=3.0):
     """The block-sparse workload: periodic L^3 cubic tight-binding lattice
     (onsite +-0.5 by sublattice + N(0, 0.05), hopping -1 + U(-0.1, 0.1)),
-    n = L^3, nocc = n/2, mu = 0, loaded from COO, 32 x 32 blocks truncated at
-    tau per step.  Trace-correcting scale-and-fold against its monotonic
-    baseline, both block-sparse, and the dense mixed path at the same size.
-    One warm-up run and one timed run each (device-event time of the run)."""
+    n = L^3, nocc = n/2, mu = 0, loaded from COO, 32 x 32 blocks.
+
+    - "C3": tau per step; trace-correcting scale-and-fold (TC_SF) against
+      its monotonic baseline (TC_MONO), both block-sparse, and TC_SF dense.
+    - "equal_budget": TC_SF against TC_MONO with the same total truncation
+      budget (tau = budget / (m + 1)), at the C3 onsite splitting and at a
+      wider one (+-wide_onsite), where the density stays sparse.
+    One handle per mode, warmed once; device-event time of one run each."""
     import torch
     from paper_1101_0265_gb300 import inputs as I
-    lat = I.lattice_hamiltonian(L)
-    g = lat.gap_bound
-    out = {"workload": f"{L}^3 periodic cubic tight-binding lattice, n={lat.n}, COO input, "
-                       f"32x32 blocks, tau {tau:g} per step, tol {tol:g}",
-           "n": lat.n, "tau": tau, "gap_bound": g}
-    for name, scheme, bs in (("TC_SF", "TC_SF", True), ("TC_MONO", "TC_MONO", True),
-                             ("TC_SF_dense", "TC_SF", False)):
-        pur = P.Purifier(device=dev.index, stream=stream.cuda_stream, precision="mixed",
-                         block_sparse=bs, trunc_tau=tau)
+
+    def case(lat, scheme, bs, **opt):
+        pur = pool[bs]
+        if bs:
+            pur.set_options(trunc_tau=opt.get("trunc_tau", tau), trunc_budget=opt.get("trunc_budget", 0.0))
+        g = lat.gap_bound
         pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0,
                                 homo=-g, lumo=g)
-        pur.run(scheme, tol, 300)
         pur.run(scheme, tol, 300)
         st = pur.stats()
         r = {"seconds": st["seconds"], "iterations": st["iterations"],
@@ -215,12 +215,36 @@ def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9):
             nb = lat.n // 32
             r["nnz_blocks"] = h
             r["final_fill"] = h[-1] / (nb * (nb + 1) / 2)
+        return r
+
+    lat = I.lattice_hamiltonian(L)
+    pool = {True: P.Purifier(device=dev.index, stream=stream.cuda_stream, precision="mixed",
+                             block_sparse=True, trunc_tau=tau),
+            False: P.Purifier(device=dev.index, stream=stream.cuda_stream, precision="mixed")}
+    case(lat, "TC_SF", True)       # warm-up (allocations, kernel set-up)
+    case(lat, "TC_SF", False)
+    c3 = {"onsite": 0.5, "gap_bound": lat.gap_bound, "tau": tau,
+          "TC_SF": case(lat, "TC_SF", True), "TC_MONO": case(lat, "TC_MONO", True),
+          "TC_SF_dense": case(lat, "TC_SF", False)}
+    c3["speedup_sf_vs_mono"] = c3["TC_MONO"]["seconds"] / c3["TC_SF"]["seconds"]
+    c3["speedup_sparse_vs_dense"] = c3["TC_SF_dense"]["seconds"] / c3["TC_SF"]["seconds"]
+    eq = []
+    for onsite in (0.5, wide_onsite):
+        lt = lat if onsite == 0.5 else I.lattice_hamiltonian(L, onsite=onsite)
+        e = {"onsite": onsite, "gap_bound": lt.gap_bound, "budget": budget,
+             "TC_SF": case(lt, "TC_SF", True, trunc_budget=budget),
+             "TC_MONO": case(lt, "TC_MONO", True, trunc_budget=budget)}
+        if onsite != 0.5:
+            e["TC_SF_dense"] = case(lt, "TC_SF", False)
+            e["speedup_sparse_vs_dense"] = e["TC_SF_dense"]["seconds"] / e["TC_SF"]["seconds"]
+        e["speedup_sf_vs_mono"] = e["TC_MONO"]["seconds"] / e["TC_SF"]["seconds"]
+        eq.append(e)
+    for pur in pool.values():
         pur.close()
-        torch.cuda.empty_cache()
-        out[name] = r
-    out["speedup_sf_vs_mono"] = out["TC_MONO"]["seconds"] / out["TC_SF"]["seconds"]
-    out["speedup_sparse_vs_dense"] = out["TC_SF_dense"]["seconds"] / out["TC_SF"]["seconds"]
-    return out
+    torch.cuda.empty_cache()
+    return {"workload": f"{L}^3 periodic cubic tight-binding lattice, n={lat.n}, COO input, "
+                        f"32x32 blocks, tol {tol:g}",
+            "n": lat.n, "C3": c3, "equal_budget": eq}
 
 
 def peaks():

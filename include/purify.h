@@ -107,6 +107,12 @@ typedef struct purify_options {
     double trunc_tau;    /* block_sparse: per-step truncation budget: blocks of
                             smallest Frobenius norm are dropped while the dropped
                             mass (off-diagonal blocks twice) stays <= tau^2       */
+    double trunc_budget; /* block_sparse: when > 0, a total budget for all of the
+                            run's truncations instead: tau = trunc_budget / (m + 1)
+                            for the m scheduled iterations and X_0, so a scheme
+                            that needs fewer iterations truncates harder at the
+                            same bound on the accumulated truncation (the closing
+                            discussion's argument for sparsity)                 */
 } purify_options;
 
 typedef struct purify_stats_t {

@@ -91,6 +91,7 @@ class Result:
     beta0: float = float("nan")
     betabar0: float = float("nan")
     f0: tuple = ()                                 # (c0, c1): X_0 = c0 I + c1 F
+    tau: float = float("nan")                      # truncation per step (truncated runs)
 
     @property
     def err_bound(self) -> float:
@@ -434,20 +435,30 @@ def truncate_blocks(X, tau: float, bs: int = 32):
 
 
 def purify_tc_truncated(F, lmin, lmax, homo, lumo, tau, tol=1e-9, max_iter=200, scaled=True,
-                        bs: int = 32):
+                        bs: int = 32, tau_budget=None):
     """Algorithm 2 with the truncation above applied to every iterate
     (X_0 included).  Returns X, the Result and the kept-block counts (blocks
-    I <= J) after each truncation."""
+    I <= J) after each truncation.
+
+    tau_budget: a total budget for all truncations instead of tau, spread
+    evenly over X_0 and the m scheduled iterations (tau = budget / (m + 1)),
+    so that a schedule with fewer iterations truncates harder at the same
+    bound on the accumulated truncation (closing discussion: fewer iterations
+    allow more aggressive truncation in each)."""
     F = np.asarray(F, dtype=np.float64)
     n = F.shape[0]
     I = np.eye(n)
+    beta, betabar = tc_beta0(lmin, lmax, homo, lumo)
+    steps = list(tc_schedule(beta, betabar, tol, max_iter, scaled))
+    if tau_budget is not None:
+        tau = tau_budget / (len(steps) + 1)
     X = (lmax * I - F) / (lmax - lmin)
     X, keep = truncate_blocks(X, tau, bs)
     nnzb = [int(np.triu(keep).sum())]
-    beta, betabar = tc_beta0(lmin, lmax, homo, lumo)
     res = Result(scheme="TC_SF" if scaled else "TC_MONO", beta0=beta, betabar0=betabar,
                  f0=tc_f0(lmin, lmax))
-    for branch, alpha, b, bb in tc_schedule(beta, betabar, tol, max_iter, scaled):
+    res.tau = tau
+    for branch, alpha, b, bb in steps:
         X2 = X @ X
         res.idem.append(float(np.linalg.norm(X - X2)))
         if branch == "P10":

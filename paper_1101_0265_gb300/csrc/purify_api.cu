@@ -307,6 +307,7 @@ void purify_options_default(purify_options* opt) {
     opt->split_k = 1;
     opt->refine_fp64 = 0;
     opt->trunc_tau = 1e-6;
+    opt->trunc_budget = 0.0;
 }
 
 static int check_options(const purify_options* o) {
@@ -319,7 +320,7 @@ static int check_options(const purify_options* o) {
     if (o->block_sparse != 0 && o->block_sparse != 1) return PURIFY_ERR_INVALID_ARG;
     if (o->split_k != 0 && o->split_k != 1) return PURIFY_ERR_INVALID_ARG;
     if (o->refine_fp64 < 0 || o->refine_fp64 > 2) return PURIFY_ERR_INVALID_ARG;
-    if (!(o->trunc_tau >= 0.0)) return PURIFY_ERR_INVALID_ARG;
+    if (!(o->trunc_tau >= 0.0) || !(o->trunc_budget >= 0.0)) return PURIFY_ERR_INVALID_ARG;
     return PURIFY_OK;
 }
 

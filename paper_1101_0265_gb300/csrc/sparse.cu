@@ -231,7 +231,9 @@ int launch_scatter_coo(const int64_t* key, const double* v, int64_t nnz, double*
 
 int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std::vector<double>& red) {
     if (scheme != PURIFY_TC_SF && scheme != PURIFY_TC_MONO) return PURIFY_ERR_UNSUPPORTED;
-    const double tau = h->opt.trunc_tau;
+    const int m_sched = (int)S.alpha.size();
+    // a total budget spreads over X_0 and the m scheduled steps
+    const double tau = h->opt.trunc_budget > 0.0 ? h->opt.trunc_budget / (m_sched + 1) : h->opt.trunc_tau;
     if (!(tau >= 0.0)) return PURIFY_ERR_INVALID_ARG;
     const int n = (int)h->n;
     const int n_pad = pad128(n);

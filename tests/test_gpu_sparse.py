@@ -195,3 +195,26 @@ def test_full_size_lattice_invariants(P):
         torch.cuda.empty_cache()
     # truncation at tau = 1e-6 per step moves the sampled columns little
     assert (Ds[True] - Ds[False]).abs().max().item() < 1e-6
+
+
+@pytest.mark.parametrize("L,scheme", [(8, "TC_SF"), (8, "TC_MONO"), (12, "TC_SF")])
+def test_truncation_budget_vs_oracle(P, L, scheme):
+    # a total truncation budget: tau = budget / (m + 1) on both sides
+    lat, F, lo, hi = _lattice(L)
+    g = lat.gap_bound
+    eps = 1e-4
+    Xo, r, hist_o = O.purify_tc_truncated(F, lo, hi, -g, g, None, tol=1e-9, scaled=scheme == "TC_SF",
+                                          tau_budget=eps)
+    pur = P.Purifier(precision="mixed", block_sparse=True, trunc_budget=eps, split_k=False)
+    pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0, lmin=lo, lmax=hi,
+                            homo=-g, lumo=g)
+    pur.run(scheme, 1e-9, 200)
+    D, st, hist = pur.density(), pur.stats(), pur.block_history()
+    pur.close()
+    assert st["iterations"] == r.iterations
+    assert hist[0] == hist_o[0]
+    diff = np.max(np.abs(D - Xo))
+    if hist == hist_o:
+        assert diff <= 1e-8, diff
+    else:
+        assert diff <= 3e-7 + 2 * r.tau * (hi - lo) / (2 * g), diff

@@ -365,3 +365,29 @@ def test_lattice_gap_and_truncated_density():
     mapped_gap = 2 * g / (hi - lo)
     assert np.linalg.norm(X - D, 2) <= 1e-10 + (r.iterations + 1) * tau / mapped_gap
     assert abs(np.trace(X) - lat.nocc) < 1e-3
+
+
+def test_truncation_budget_spreads_over_the_schedule():
+    # a total budget eps: tau = eps / (m + 1) for the m scheduled iterations
+    # and X_0; the scaled schedule (fewer iterations) truncates harder, and
+    # the result stays within eps / (mapped gap) of the exact density
+    lat = I.lattice_hamiltonian(8)
+    F = lat.dense()
+    lo, hi = O.gershgorin(F)
+    g = lat.gap_bound
+    eps = 1e-4
+    D = O.density_by_eigh(F, 0.0)
+    mapped_gap = 2 * g / (hi - lo)
+    runs = {}
+    for scaled in (True, False):
+        X, r, nnzb = O.purify_tc_truncated(F, lo, hi, -g, g, None, tol=1e-10, scaled=scaled,
+                                           tau_budget=eps)
+        assert r.tau == pytest.approx(eps / (r.iterations + 1), rel=1e-15)
+        assert np.linalg.norm(X - D, 2) <= 1e-10 + eps / mapped_gap
+        runs[scaled] = (r, nnzb)
+    assert runs[True][0].iterations < runs[False][0].iterations
+    assert runs[True][0].tau > runs[False][0].tau
+    # a zero budget truncates only exact zeros: the untruncated recursion
+    X0, r0, _ = O.purify_tc_truncated(F, lo, hi, -g, g, None, tol=1e-10, tau_budget=0.0)
+    Xp, rp = O.purify_tc(F, lo, hi, -g, g, tol=1e-10)
+    assert np.max(np.abs(X0 - Xp)) < 1e-13
