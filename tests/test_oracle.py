@@ -391,3 +391,45 @@ def test_truncation_budget_spreads_over_the_schedule():
     X0, r0, _ = O.purify_tc_truncated(F, lo, hi, -g, g, None, tol=1e-10, tau_budget=0.0)
     Xp, rp = O.purify_tc(F, lo, hi, -g, g, tol=1e-10)
     assert np.max(np.abs(X0 - Xp)) < 1e-13
+
+
+# --- gap edges from the purification (interior eigenvalues) -----------------
+
+@pytest.mark.parametrize("n,nocc,gap,cfg", [(300, 120, 0.05, 1), (500, 250, 0.01, 2), (400, 100, 2e-3, 3),
+                                            (256, 128, 0.1, 4), (200, 60, 1e-4, 5)])
+def test_gap_estimate_is_inner_and_tight(n, nocc, gap, cfg):
+    h = I.dense_hamiltonian(n, nocc, gap, config=cfg)
+    he, le, steps = O.estimate_gap(h.F, h.lmin, h.lmax, h.nocc)
+    w = h.lmax - h.lmin
+    assert h.homo <= he < le <= h.lumo
+    assert he - h.homo <= 1e-12 * w and h.lumo - le <= 1e-12 * w
+    assert steps > 0
+
+
+def test_gap_estimate_diagonal_and_lattice():
+    # diagonal F: the recursion acts entry by entry
+    lam = np.sort(np.concatenate([np.linspace(-1, -0.03, 70), np.linspace(0.02, 1, 50)]))
+    h = I.diagonal_hamiltonian(lam, 0.0)
+    he, le, _ = O.estimate_gap(h.F, -1.0, 1.0, 70)
+    assert -0.03 <= he < le <= 0.02 and he + 0.03 < 1e-12 and 0.02 - le < 1e-12
+    # the 8^3 lattice against its eigendecomposition
+    lat = I.lattice_hamiltonian(8)
+    F = lat.dense()
+    ev = np.linalg.eigvalsh(F)
+    lo, hi = O.gershgorin(F)
+    he, le, _ = O.estimate_gap(F, lo, hi, lat.nocc)
+    assert ev[lat.nocc - 1] <= he < le <= ev[lat.nocc]
+    assert he - ev[lat.nocc - 1] < 1e-8 and ev[lat.nocc] - le < 1e-8
+
+
+def test_gap_filters_pick_their_side():
+    # the occupied filter x^4 (1 - x) peaks for the occupied eigenvalue
+    # nearest 1/2 and the unoccupied one x (1 - x)^4 for the unoccupied one,
+    # on spectra where every eigenvalue has x (1 - x) < 1/16
+    rng = np.random.default_rng(0)
+    occ = 1.0 - rng.uniform(1e-6, 0.06, 40)
+    unocc = rng.uniform(1e-6, 0.06, 30)
+    x = np.concatenate([occ, unocc])
+    p = O.GAP_FILTER_POWER
+    assert np.argmax(x ** p * (1 - x)) == np.argmin(occ)
+    assert np.argmax(x * (1 - x) ** p) - 40 == np.argmax(unocc)
