@@ -179,6 +179,21 @@ int purify_set_hamiltonian_coo(purify_t h, int64_t n, int64_t nnz, const int64_t
                                const int64_t* cols, const double* vals, int64_t nocc, double mu,
                                const purify_bounds* b);
 
+/* Gap edges from the purification (Algorithms 1 and 2 need a lower bound of
+ * the gap's lower edge and an upper bound of its upper edge; the paper's
+ * discussion points to techniques for interior eigenvalues).  Needs F, nocc
+ * (0 < nocc < n) and lmin/lmax from purify_set_hamiltonian.  Runs steps of
+ * the alpha = 0 scheme with the trace rule until ||X - X^2||_F < 1 / (4
+ * sqrt(n)) and round(trace X) = nocc, then `lanczos_steps` Lanczos steps on
+ * X^4 (I - X) and on X (I - X)^4, whose largest eigenvalues belong to the
+ * images of homo and lumo; Ritz values raised by their residual norms are
+ * mapped back through the steps taken.  The results lie inside the gap
+ * (homo <= *homo_est < *lumo_est <= lumo, up to the iterate's rounding on the
+ * mixed path) and become the handle's gap bounds for purify_run.  Uses the
+ * handle's precision; the handle holds no density afterwards.  Returns
+ * PURIFY_ERR_NOT_CONVERGED when the sides are not resolved within 200 steps. */
+int purify_estimate_gap(purify_t h, int lanczos_steps, double* homo_est, double* lumo_est);
+
 /* Block-sparse runs: the number of upper 32 x 32 blocks kept after the
  * truncation of X_0 and of every step (count <= cap entries written). */
 int purify_block_history(purify_t h, int* nnz_blocks, int cap, int* count);

@@ -31,7 +31,7 @@ BRANCH_RULES = {"beta": 0, "trace": 1}
 
 EXPORTED = (
     "purify_options_default", "purify_create", "purify_destroy", "purify_set_options",
-    "purify_set_hamiltonian", "purify_set_hamiltonian_coo", "purify_block_history",
+    "purify_set_hamiltonian", "purify_set_hamiltonian_coo", "purify_block_history", "purify_estimate_gap",
     "purify_run", "purify_get_density", "purify_stats",
     "purify_density_device_ptr", "purify_strerror", "purify_schedule", "purify_tridiag_eig",
     "purify_k_symm_product_f64", "purify_k_step_f64", "purify_k_gershgorin_f64",
@@ -97,6 +97,7 @@ def load(path: str = LIB_PATH):
         "purify_run": (ip, [vp, ip, dbl, ip]),
         "purify_set_hamiltonian_coo": (ip, [vp, i64, i64, vp, vp, vp, i64, dbl, C.POINTER(Bounds)]),
         "purify_block_history": (ip, [vp, C.POINTER(C.c_int), ip, C.POINTER(C.c_int)]),
+        "purify_estimate_gap": (ip, [vp, ip, dp, dp]),
         "purify_get_density": (ip, [vp, vp, i64]),
         "purify_stats": (ip, [vp, C.POINTER(Stats)]),
         "purify_density_device_ptr": (vp, [vp]),
@@ -262,6 +263,14 @@ class Purifier:
         _check(code, "purify_set_hamiltonian_coo")
         self.n = int(n)
         return code
+
+    def estimate_gap(self, lanczos_steps: int = 40):
+        """Inner estimates (homo, lumo) of the gap edges; they become the
+        handle's gap bounds."""
+        ho, lu = C.c_double(0.0), C.c_double(0.0)
+        _check(self._lib.purify_estimate_gap(self._h, int(lanczos_steps), C.byref(ho), C.byref(lu)),
+               "purify_estimate_gap")
+        return ho.value, lu.value
 
     def block_history(self):
         cnt = C.c_int(0)

@@ -73,6 +73,11 @@ struct Schedule {
     bool converged = false;
 };
 
+// Eigenpairs of the symmetric tridiagonal matrix (diagonal a[0..m),
+// off-diagonal b[0..m-1)) by cyclic Jacobi: w ascending, Z[j * m + i] the i-th
+// component of the j-th normalised eigenvector (host).
+void tridiag_eig_full(const double* a, const double* b, int m, std::vector<double>& w, std::vector<double>& Z);
+
 // Algorithm 2's scalar pieces (float64, host): alpha of a branch (1 = P_{1,0},
 // 0 = P_{0,1}) and the branch's map of a scalar (Eq. 4 / Eq. 5).
 double tc_alpha(int branch, double b, double bb);

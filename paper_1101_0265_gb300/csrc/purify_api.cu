@@ -165,6 +165,26 @@ static void jacobi_eig(std::vector<double>& A, int m, std::vector<double>& V) {
     }
 }
 
+void tridiag_eig_full(const double* a, const double* b, int m, std::vector<double>& w, std::vector<double>& Z) {
+    std::vector<double> A((size_t)m * m, 0.0), V;
+    for (int i = 0; i < m; ++i) {
+        A[(size_t)i * m + i] = a[i];
+        if (i + 1 < m) A[(size_t)i * m + i + 1] = A[(size_t)(i + 1) * m + i] = b[i];
+    }
+    jacobi_eig(A, m, V);
+    std::vector<int> order(m);
+    for (int i = 0; i < m; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(),
+              [&](int x, int y) { return A[(size_t)x * m + x] < A[(size_t)y * m + y]; });
+    w.assign(m, 0.0);
+    Z.assign((size_t)m * m, 0.0);
+    for (int j = 0; j < m; ++j) {
+        const int c = order[j];
+        w[j] = A[(size_t)c * m + c];
+        for (int i = 0; i < m; ++i) Z[(size_t)j * m + i] = V[(size_t)i * m + c];
+    }
+}
+
 int host_bounds_from_lanczos(const double* a, const double* bsq, int k, double g_lo, double g_hi,
                              double* lo, double* hi) {
     // Truncate at an exact breakdown (b_j == 0: invariant subspace found).
