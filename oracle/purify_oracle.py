@@ -72,6 +72,41 @@ def P11(x):
     return 3.0 * x * x - 2.0 * x * x * x
 
 
+def P_ij(i: int, j: int, x):
+    """P_{i,j}(x) = x^(i+1) sum_{k=0..j} C(i+k, k) (1-x)^k: the polynomial of
+    degree 1 + i + j with fixed points 0 and 1 and i and j vanishing
+    derivatives there (the tests check this closed form against that
+    definition).  Evaluated with a Horner sum in t = 1 - x, then the power of x
+    by repeated multiplication (the library uses the same order)."""
+    t = 1.0 - x
+    acc = 0.0 * x
+    for k in range(j, -1, -1):
+        acc = acc * t + math.comb(i + k, k)
+    p = x
+    for _ in range(i):
+        p = p * x
+    return p * acc
+
+
+def pmm_alpha(m: int, beta: float) -> float:
+    """The alpha >= 1 with P_{m,m}(alpha (beta - 1/2) + 1/2) = P_{m,m}((1 - alpha)/2)
+    (the scaling equation stated with Algorithm 1, for odd m): bisection on
+    [1, 1 / (1 - 2 beta)], where the difference of the two sides goes from
+    positive to negative, down to the last bit."""
+    def g(a):
+        return P_ij(m, m, a * (beta - 0.5) + 0.5) - P_ij(m, m, 0.5 * (1.0 - a))
+    lo, hi = 1.0, 1.0 / (1.0 - 2.0 * beta)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid == lo or mid == hi:
+            break
+        if g(mid) > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
 # ---------------------------------------------------------------------------
 # Result record
 # ---------------------------------------------------------------------------
@@ -160,6 +195,68 @@ def purify_fixed_mu(F, lmin, lmax, mu, homo, lumo, tol=1e-12, max_iter=200, scal
         res.multiplications += 2
     res.converged = bool(betas) and betas[-1] <= tol or (not betas and beta <= tol)
     return X, res
+
+
+def pmm_schedule(m: int, beta: float, tol: float, max_iter: int, scaled: bool = True):
+    """Scalar part of the fixed-mu scheme with P_{m,m} (odd m): the alpha of
+    each iteration and the beta after it, beta <- P_{m,m}(alpha (beta - 1/2)
+    + 1/2); stops once beta <= tol or at max_iter."""
+    alphas, betas = [], []
+    while beta > tol and len(alphas) < max_iter:
+        alpha = pmm_alpha(m, beta) if scaled else 1.0
+        beta = P_ij(m, m, alpha * (beta - 0.5) + 0.5)
+        alphas.append(alpha)
+        betas.append(beta)
+    return alphas, betas
+
+
+# Matrix products per iteration of the fixed-mu scheme with P_{m,m}: m = 1 as
+# in Algorithm 1 (X_s^2, then X_s^2 X_s); m = 3 as the library evaluates
+# P_{3,3}(x) = x^4 (35 - 84 x + 70 x^2 - 20 x^3): V = 70 X_s - 20 X_s^2,
+# Q = X_s V - 84 X_s + 35 I, S = X_s^2, T = S^2, X = T Q.
+PMM_PRODUCTS = {1: 2, 3: 5}
+
+
+def purify_fixed_mu_pmm(F, lmin, lmax, mu, homo, lumo, m: int = 3, tol=1e-12, max_iter=200,
+                        scaled=True):
+    """Fixed-mu purification with f_i(X) = P_{m,m}(alpha (X - 1/2) + 1/2), m
+    odd (the scheme stated with Algorithm 1 for general m; Algorithm 1 is
+    m = 1).  X_0 and beta as in Algorithm 1."""
+    F = np.asarray(F, dtype=np.float64)
+    n = F.shape[0]
+    I = np.eye(n)
+    gamma = fixed_mu_gamma(lmin, lmax, mu)
+    X = (mu * I - F) / gamma + 0.5 * I
+    beta = fixed_mu_beta0(gamma, mu, homo, lumo)
+    res = Result(scheme=f"FIXED_MU_P{m}{m}" + ("_SF" if scaled else "_MONO"), beta0=beta,
+                 betabar0=1.0 - beta, f0=(mu / gamma + 0.5, -1.0 / gamma))
+    alphas, betas = pmm_schedule(m, beta, tol, max_iter, scaled)
+    for alpha, beta_i in zip(alphas, betas):
+        Xs = alpha * (X - 0.5 * I) + 0.5 * I
+        X = _matrix_P(m, m, Xs)
+        res.alphas.append(alpha)
+        res.betas.append(beta_i)
+        res.betabars.append(1.0 - beta_i)
+        res.traces.append(float(np.trace(X)))
+        res.iterations += 1
+        res.multiplications += PMM_PRODUCTS.get(m, 2 * m)
+    res.converged = (bool(betas) and betas[-1] <= tol) or (not betas and beta <= tol)
+    return X, res
+
+
+def _matrix_P(i: int, j: int, Xs):
+    """P_{i,j} of a symmetric matrix, from its definition as a polynomial:
+    Xs^(i+1) (sum_k C(i+k, k) (I - Xs)^k), products in plain numpy."""
+    n = Xs.shape[0]
+    I = np.eye(n)
+    T = I - Xs
+    acc = np.zeros_like(Xs)
+    for k in range(j, -1, -1):
+        acc = acc @ T + math.comb(i + k, k) * I
+    Pw = Xs.copy()
+    for _ in range(i):
+        Pw = Pw @ Xs
+    return Pw @ acc
 
 
 # ---------------------------------------------------------------------------

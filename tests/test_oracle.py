@@ -433,3 +433,57 @@ def test_gap_filters_pick_their_side():
     p = O.GAP_FILTER_POWER
     assert np.argmax(x ** p * (1 - x)) == np.argmin(occ)
     assert np.argmax(x * (1 - x) ** p) - 40 == np.argmax(unocc)
+
+
+# --- higher-order fixed-mu polynomials P_{m,m} ---------------------------------
+
+@pytest.mark.parametrize("i,j", [(1, 0), (0, 1), (1, 1), (3, 3), (1, 3), (3, 1), (2, 2), (5, 5)])
+def test_P_ij_closed_form_matches_definition(i, j):
+    # degree 1 + i + j, P(0) = 0, P(1) = 1, i vanishing derivatives at 0 and j
+    # at 1: 2 + i + j conditions fix the polynomial
+    sympy = pytest.importorskip("sympy")
+    x = sympy.symbols("x")
+    P = sympy.nsimplify(sympy.expand(O.P_ij(i, j, x)), rational=True)
+    assert sympy.degree(P, x) == 1 + i + j
+    assert P.subs(x, 0) == 0 and P.subs(x, 1) == 1
+    for d in range(1, i + 1):
+        assert sympy.diff(P, x, d).subs(x, 0) == 0
+    for d in range(1, j + 1):
+        assert sympy.diff(P, x, d).subs(x, 1) == 0
+    assert O.P_ij(1, 1, 0.3) == pytest.approx(O.P11(0.3), rel=1e-15)
+
+
+def test_pmm_alpha_solves_the_scaling_equation():
+    for beta in np.linspace(0.01, 0.499, 40):
+        # m = 1 is Algorithm 1's closed form
+        assert O.pmm_alpha(1, beta) == pytest.approx(O.fixed_mu_alpha(beta), rel=4e-16, abs=0)
+        a = O.pmm_alpha(3, beta)
+        assert 1.0 <= a <= 1.0 / (1.0 - 2.0 * beta)
+        lhs = O.P_ij(3, 3, a * (beta - 0.5) + 0.5)
+        rhs = O.P_ij(3, 3, 0.5 * (1.0 - a))
+        assert abs(lhs - rhs) <= 1e-14
+
+
+def test_pmm_scheme():
+    h = I.dense_hamiltonian(160, 60, 1e-3, config=10)
+    Dx = O.density_closed_form(h.Q, h.lam, 0.0)
+    # m = 1 is Algorithm 1
+    X1, r1 = O.purify_fixed_mu_pmm(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, m=1, tol=1e-12)
+    Xa, ra = O.purify_fixed_mu(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, tol=1e-12)
+    assert r1.iterations == ra.iterations and r1.multiplications == ra.multiplications
+    assert np.max(np.abs(X1 - Xa)) < 1e-12
+    # m = 3: converges to D; scaling saves iterations; per multiplication it
+    # is no better than m = 1 (the finding the bench reports)
+    X3, r3 = O.purify_fixed_mu_pmm(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, m=3, tol=1e-12)
+    _, r3m = O.purify_fixed_mu_pmm(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, m=3, tol=1e-12, scaled=False)
+    assert r3.converged and np.max(np.abs(X3 - Dx)) < 1e-11
+    assert r3.iterations < r3m.iterations and r3.iterations < r1.iterations
+    assert r3.multiplications > r1.multiplications
+    # functional calculus: on a diagonal F the recursion acts entry by entry
+    lam = np.concatenate([np.linspace(-1, -0.05, 20), np.linspace(0.05, 1, 20)])
+    hd = I.diagonal_hamiltonian(lam, 0.0)
+    Xd, rd = O.purify_fixed_mu_pmm(hd.F, -1.0, 1.0, 0.0, -0.05, 0.05, m=3, tol=1e-12)
+    x = (0.0 - lam) / O.fixed_mu_gamma(-1.0, 1.0, 0.0) + 0.5
+    for a in rd.alphas:
+        x = O.P_ij(3, 3, a * (x - 0.5) + 0.5)
+    assert np.max(np.abs(np.diag(Xd) - x)) < 1e-13
