@@ -56,6 +56,12 @@ extern "C" {
 #define PURIFY_FIXED_MU_MONO  1  /* Algorithm 1 with alpha = 1 (regular McWeeny)     */
 #define PURIFY_TC_SF          2  /* Algorithm 2: Eq. 4 / Eq. 5 with scaling alpha    */
 #define PURIFY_TC_MONO        3  /* Algorithm 2 with alpha = 0 (trace-correcting)    */
+/* The fixed-mu scheme with the higher-order P_{3,3}(x) = x^4 (35 - 84x + 70x^2
+ * - 20x^3) (the scheme stated with Algorithm 1 for odd m; alpha >= 1 solves
+ * P_{3,3}(alpha(beta - 1/2) + 1/2) = P_{3,3}((1 - alpha)/2) by bisection);
+ * five products per iteration. */
+#define PURIFY_FIXED_MU_P33_SF   4
+#define PURIFY_FIXED_MU_P33_MONO 5  /* the same with alpha = 1                     */
 
 /* ---- arithmetic of the matrix products -------------------------------- */
 #define PURIFY_FP64    0  /* float64 FMA on the SIMT pipes                          */

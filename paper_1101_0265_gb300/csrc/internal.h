@@ -82,6 +82,12 @@ void tridiag_eig_full(const double* a, const double* b, int m, std::vector<doubl
 // 0 = P_{0,1}) and the branch's map of a scalar (Eq. 4 / Eq. 5).
 double tc_alpha(int branch, double b, double bb);
 double tc_map(int branch, double a, double x);
+// The fixed-mu polynomial order of a scheme (1: P_{1,1}, 3: P_{3,3}), its
+// products per iteration, P_{i,j} on a scalar and the P_{m,m} scaling alpha.
+int pmm_order(int scheme);
+int products_per_iteration(int scheme);
+double P_ij_scalar(int i, int j, double x);
+double pmm_alpha(int m, double beta);
 
 struct MixedState;
 
@@ -99,6 +105,8 @@ struct purify_ctx {
     double* F = nullptr;
     double* X[2] = {nullptr, nullptr};
     double* S = nullptr;
+    double* P3[2] = {nullptr, nullptr};  // float64 P_{3,3} intermediates, allocated on use
+    int64_t p3_cap = 0;
     double* red = nullptr;
     int64_t red_cap = 0;  // doubles
     double* scratch = nullptr;

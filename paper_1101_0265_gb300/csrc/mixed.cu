@@ -25,6 +25,8 @@ void mixed_free(MixedState* ms) {
     cudaFree(ms->Xd[0]);
     cudaFree(ms->Xd[1]);
     cudaFree(ms->Sd);
+    cudaFree(ms->Pd[0]);
+    cudaFree(ms->Pd[1]);
     cudaFree(ms->err);
     cudaFree(ms->scratch);
     cudaFree(ms->partial);
@@ -205,6 +207,166 @@ int run_mixed_trace(purify_ctx* h, int scheme, double tol, int max_iter, Schedul
         h->st.idem_err_fro = NAN;
     }
     *iters = it;
+    return PURIFY_OK;
+}
+
+// Smallest e with 2^e >= 1.01 max |p(x)| over x in [lo, hi] (sampled; the
+// polynomials' slopes keep the sampling error far below the 1 % margin).
+template <typename Fn>
+static int bound_exponent(Fn p, double lo, double hi) {
+    double mx = 0.0;
+    for (int k = 0; k <= 4096; ++k) mx = std::max(mx, std::fabs(p(lo + (hi - lo) * k / 4096.0)));
+    int e = 0;
+    while (std::ldexp(1.0, e) < 1.01 * mx) ++e;
+    return e;
+}
+
+int run_mixed_p33(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur, std::vector<double>& red) {
+    if (h->opt.refine_squares) return PURIFY_ERR_UNSUPPORTED;
+    const int n = (int)h->n;
+    const int n_pad = pad128(n);
+    PURIFY_TRY(ensure_mixed(h, n_pad));
+    MixedState* ms = h->mixed;
+    if (ms->pd_cap < ms->n_pad_cap) {
+        cudaFree(ms->Pd[0]);
+        cudaFree(ms->Pd[1]);
+        ms->Pd[0] = ms->Pd[1] = nullptr;
+        ms->pd_cap = 0;
+        const size_t bytes = sizeof(__nv_bfloat16) * (size_t)kMaxDigitPlanes * ms->n_pad_cap * ms->n_pad_cap;
+        PURIFY_CUDA_TRY(cudaMalloc(&ms->Pd[0], bytes));
+        PURIFY_CUDA_TRY(cudaMalloc(&ms->Pd[1], bytes));
+        ms->pd_cap = ms->n_pad_cap;
+    }
+    const int m = (int)S.alpha.size();
+    const int fixed = h->opt.digits;
+    const int T = n_pad / 128;
+    const int rb = remainder_bits(n_pad);
+    const double tile_flops = 2.0 * 128.0 * 128.0 * (double)n_pad * (double)(T * (T + 1) / 2);
+    // exponents of X_s and of the intermediates over the spectrum of X_s,
+    // within [(1 - alpha)/2, (1 + alpha)/2] for the run's largest alpha
+    double amax = 1.0;
+    for (double a : S.alpha) amax = std::max(amax, a);
+    if (amax > 3.0) return PURIFY_ERR_UNSUPPORTED;
+    const double lo = 0.5 * (1.0 - amax) - 1e-3, hi = 0.5 * (1.0 + amax) + 1e-3;
+    const int eX = bound_exponent([](double x) { return x; }, lo, hi);
+    const int eV = bound_exponent([](double x) { return 70.0 * x - 20.0 * x * x; }, lo, hi);
+    const int eQ = bound_exponent([](double x) { return 35.0 - 84.0 * x + 70.0 * x * x - 20.0 * x * x * x; }, lo, hi);
+    const int eS = bound_exponent([](double x) { return x * x; }, lo, hi);
+    const int eT = bound_exponent([](double x) { return x * x * x * x; }, lo, hi);
+    // digits per iteration: the mapped-gap rule plus one (V and Q sit up to
+    // 7 bits above X_s)
+    std::vector<int> sd(m + 1);
+    for (int i = 0; i < m; ++i) {
+        const double b = i ? S.beta[i - 1] : S.beta0;
+        const double bb = i ? S.betabar[i - 1] : S.betabar0;
+        sd[i] = std::min(kMaxDigitPlanes, digits_for_gap(bb - b, fixed, rb) + (fixed > 0 ? 0 : 1));
+    }
+    sd[m] = sd[m ? m - 1 : 0];
+    int dmax = 0;
+    for (int i = 0; i < m; ++i) dmax = std::max(dmax, sd[i]);
+    h->st.digit_max = dmax;
+    const int slots = 2 * m + 2;
+    PURIFY_TRY(ensure_red(h, 4 * (int64_t)slots));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * slots, h->stream));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), h->stream));
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+    const double gamma = 2.0 * std::max(h->b.lmax - mu, mu - h->b.lmin);
+    const double c0 = mu / gamma + 0.5, c1 = -1.0 / gamma;
+    double* D = h->X[0];
+    *cur = 0;
+    if (m == 0) {
+        PURIFY_TRY(launch_affine_f64(h->F, n, D, n, c1, c0, h->stream));
+    } else {
+        const double a1 = S.alpha[0];
+        PURIFY_TRY(launch_split(h->F, n, n, n_pad, a1 * c1, a1 * (c0 - 0.5) + 0.5, eX, sd[0], rb, ms->Xd[0], nullptr,
+                                h->stream));
+        int x = 0;
+        for (int i = 0; i < m; ++i) {
+            const int s = sd[i];
+            const double fl = pairs_of(s) * tile_flops;
+            DigitStep base;
+            base.n = n;
+            base.n_pad = n_pad;
+            base.rbits = rb;
+            base.s_in = s;
+            base.s_out = s;
+            base.err = ms->err;
+            base.scratch = ms->scratch;
+            base.max_ctas = ms->ctas;
+            // V = 70 X_s - 20 X_s^2
+            DigitStep p = base;
+            p.A = p.B = ms->Xd[x];
+            p.eA = p.eB = eX;
+            p.use_E = 1;
+            p.cP = -20.0;
+            p.cE = 70.0;
+            p.out = ms->Pd[0];
+            p.e_out = eV;
+            PURIFY_TRY(product(h, p, fl));
+            // Q = X_s V - 84 X_s + 35 I
+            p = base;
+            p.A = ms->Xd[x];
+            p.eA = eX;
+            p.B = ms->Pd[0];
+            p.eB = eV;
+            p.use_E = 1;
+            p.cP = 1.0;
+            p.cE = -84.0;
+            p.cI = 35.0;
+            p.out = ms->Pd[1];
+            p.e_out = eQ;
+            PURIFY_TRY(product(h, p, fl));
+            // S = X_s^2
+            p = base;
+            p.A = p.B = ms->Xd[x];
+            p.eA = p.eB = eX;
+            p.cP = 1.0;
+            p.out = ms->Sd;
+            p.e_out = eS;
+            PURIFY_TRY(product(h, p, fl));
+            // T = S^2 (over V, no longer needed)
+            p = base;
+            p.A = p.B = ms->Sd;
+            p.eA = p.eB = eS;
+            p.cP = 1.0;
+            p.out = ms->Pd[0];
+            p.e_out = eT;
+            PURIFY_TRY(product(h, p, fl));
+            // X_i = T Q, emitted as the next X_s (or as D after the last)
+            p = base;
+            p.A = ms->Pd[0];
+            p.eA = eT;
+            p.B = ms->Pd[1];
+            p.eB = eQ;
+            p.cP = 1.0;
+            const bool last = (i + 1 == m);
+            if (last) {
+                p.red = h->red + 4 * (2 * i + 1);
+                p.out = nullptr;
+                p.s_out = 0;
+                p.out64 = D;
+            } else {
+                const double an = S.alpha[i + 1];
+                p.dY = an;
+                p.dI = 0.5 * (1.0 - an);
+                p.out = ms->Xd[x ^ 1];
+                p.s_out = sd[i + 1];
+                p.e_out = eX;
+            }
+            PURIFY_TRY(product(h, p, fl));
+            x ^= 1;
+        }
+    }
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+    red.assign(4 * (size_t)slots, 0.0);
+    int err = 0;
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(red.data(), h->red, sizeof(double) * red.size(), cudaMemcpyDeviceToHost,
+                                    h->stream));
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, ms->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (err) return PURIFY_ERR_DEVICE_TIMEOUT;
+    h->st.trace = m > 0 ? red[4 * (size_t)(2 * (m - 1) + 1)] : NAN;
+    h->st.idem_err_fro = NAN;
     return PURIFY_OK;
 }
 

@@ -19,6 +19,8 @@ struct MixedState {
     int* err = nullptr;
     float2* scratch = nullptr;  // persistent product kernel, one tile per CTA
     int ctas = 0;
+    __nv_bfloat16* Pd[2] = {nullptr, nullptr};  // P_{3,3} intermediates (V then T, and Q)
+    int pd_cap = 0;
     float* partial = nullptr;   // split last-wave tiles: per-part accumulators
     int* split_cnt = nullptr;   // and per-region arrival counters
     // block-sparse runs: per-tile k-chunk counts, then (8-byte aligned) the
@@ -50,6 +52,9 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
 // bounds beta and beta_bar follow the branches taken; without them the run
 // stops when ||X - X^2||_F <= tol.  Fills S with the steps taken.
 int run_mixed_trace(purify_ctx* h, int scheme, double tol, int max_iter, Schedule& S, int* cur, int* iters);
+// The fixed-mu scheme with P_{3,3} on the digit planes (five products per
+// iteration; see purify.h).
+int run_mixed_p33(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur, std::vector<double>& red);
 int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
               std::vector<double>& red);
 void mixed_free(MixedState* ms);

@@ -75,9 +75,52 @@ double tc_map(int branch, double a, double x) {
 }
 
 static bool is_fixed_mu(int scheme) {
-    return scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_FIXED_MU_MONO;
+    return scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_FIXED_MU_MONO || scheme == PURIFY_FIXED_MU_P33_SF ||
+           scheme == PURIFY_FIXED_MU_P33_MONO;
 }
-static bool is_scaled(int scheme) { return scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_TC_SF; }
+static bool is_scaled(int scheme) {
+    return scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_TC_SF || scheme == PURIFY_FIXED_MU_P33_SF;
+}
+
+int pmm_order(int scheme) {
+    return (scheme == PURIFY_FIXED_MU_P33_SF || scheme == PURIFY_FIXED_MU_P33_MONO) ? 3 : 1;
+}
+
+int products_per_iteration(int scheme) {
+    if (!is_fixed_mu(scheme)) return 1;
+    return pmm_order(scheme) == 3 ? 5 : 2;
+}
+
+// P_{i,j}(x) = x^(i+1) sum_{k=0..j} C(i+k, k) (1 - x)^k: Horner in t = 1 - x,
+// then the power of x by repeated multiplication (the oracle's order).
+double P_ij_scalar(int i, int j, double x) {
+    const double t = 1.0 - x;
+    double acc = 0.0 * x;
+    for (int k = j; k >= 0; --k) {
+        double c = 1.0;  // C(i + k, k), exact in float64 for these orders
+        for (int q = 1; q <= k; ++q) c = c * (double)(i + q) / (double)q;
+        acc = acc * t + c;
+    }
+    double p = x;
+    for (int q = 0; q < i; ++q) p = p * x;
+    return p * acc;
+}
+
+// The alpha >= 1 with P_{m,m}(alpha (beta - 1/2) + 1/2) = P_{m,m}((1 - alpha)/2):
+// bisection on [1, 1 / (1 - 2 beta)] down to the last bit.
+double pmm_alpha(int m, double beta) {
+    double lo = 1.0, hi = 1.0 / (1.0 - 2.0 * beta);
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        const double g = P_ij_scalar(m, m, mid * (beta - 0.5) + 0.5) - P_ij_scalar(m, m, 0.5 * (1.0 - mid));
+        if (g > 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
 
 static int build_schedule(int scheme, double lmin, double lmax, double mu, double homo, double lumo,
                           double tol, int max_iter, Schedule& S) {
@@ -87,10 +130,11 @@ static int build_schedule(int scheme, double lmin, double lmax, double mu, doubl
         S.beta0 = beta;
         S.betabar0 = 1.0 - beta;
         const bool scaled = is_scaled(scheme);
+        const int m = pmm_order(scheme);
         while (beta > tol && (int)S.alpha.size() < max_iter) {
-            const double alpha = scaled ? fixed_mu_alpha(beta) : 1.0;
+            const double alpha = scaled ? (m == 1 ? fixed_mu_alpha(beta) : pmm_alpha(m, beta)) : 1.0;
             const double bs = alpha * (beta - 0.5) + 0.5;
-            beta = 3.0 * bs * bs - 2.0 * bs * bs * bs;
+            beta = m == 1 ? 3.0 * bs * bs - 2.0 * bs * bs * bs : P_ij_scalar(m, m, bs);
             S.alpha.push_back(alpha);
             S.beta.push_back(beta);
             S.betabar.push_back(1.0 - beta);
@@ -218,8 +262,11 @@ static void free_buffers(purify_ctx* h) {
     cudaFree(h->X[0]);
     cudaFree(h->X[1]);
     cudaFree(h->S);
-    h->F = h->X[0] = h->X[1] = h->S = nullptr;
+    cudaFree(h->P3[0]);
+    cudaFree(h->P3[1]);
+    h->F = h->X[0] = h->X[1] = h->S = h->P3[0] = h->P3[1] = nullptr;
     h->cap = 0;
+    h->p3_cap = 0;
 }
 
 static int ensure_capacity(purify_ctx* h, int64_t n) {
@@ -606,6 +653,53 @@ static int run_fp64(purify_ctx* h, int scheme, double tol, int max_iter, double 
     const int64_t n = h->n;
     const double lmin = h->b.lmin, lmax = h->b.lmax;
     int m = (int)S.alpha.size();
+    if (is_fixed_mu(scheme) && pmm_order(scheme) == 3) {
+        // P_{3,3}(x) = x^4 (35 - 84 x + 70 x^2 - 20 x^3) in five products:
+        // V = 70 X_s - 20 X_s^2, Q = X_s V - 84 X_s + 35 I, S = X_s^2,
+        // T = S^2 (over V), X_i = T Q (emitted as the next X_s)
+        if (h->p3_cap < n) {
+            cudaFree(h->P3[0]);
+            cudaFree(h->P3[1]);
+            h->P3[0] = h->P3[1] = nullptr;
+            h->p3_cap = 0;
+            PURIFY_CUDA_TRY(cudaMalloc(&h->P3[0], sizeof(double) * (size_t)n * n));
+            PURIFY_CUDA_TRY(cudaMalloc(&h->P3[1], sizeof(double) * (size_t)n * n));
+            h->p3_cap = n;
+        }
+        const double gamma = fixed_mu_gamma(lmin, lmax, mu);
+        const double c0 = mu / gamma + 0.5, c1 = -1.0 / gamma;
+        PURIFY_TRY(ensure_red(h, 4 * (int64_t)(5 * m + 2)));
+        PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * (5 * m + 2), h->stream));
+        PURIFY_CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+        if (m == 0) {
+            PURIFY_TRY(launch_affine_f64(h->F, n, h->X[0], n, c1, c0, h->stream));
+            h->cur = 0;
+        } else {
+            const double a1 = S.alpha[0];
+            PURIFY_TRY(launch_affine_f64(h->F, n, h->X[0], n, a1 * c1, a1 * (c0 - 0.5) + 0.5, h->stream));
+            int xs = 0;
+            double* V = h->P3[0];
+            double* Q = h->P3[1];
+            for (int i = 0; i < m; ++i) {
+                double* Xs = h->X[xs];
+                PURIFY_TRY(step64(h, Xs, Xs, Xs, V, -20.0, 70.0, 0.0, 1.0, 0.0, 5 * i));
+                PURIFY_TRY(step64(h, Xs, V, Xs, Q, 1.0, -84.0, 35.0, 1.0, 0.0, 5 * i + 1));
+                PURIFY_TRY(step64(h, Xs, Xs, nullptr, h->S, 1.0, 0.0, 0.0, 1.0, 0.0, 5 * i + 2));
+                PURIFY_TRY(step64(h, h->S, h->S, nullptr, V, 1.0, 0.0, 0.0, 1.0, 0.0, 5 * i + 3));
+                const double an = (i + 1 < m) ? S.alpha[i + 1] : 1.0;
+                PURIFY_TRY(step64(h, V, Q, nullptr, h->X[xs ^ 1], 1.0, 0.0, 0.0, an, 0.5 * (1.0 - an), 5 * i + 4));
+                xs ^= 1;
+            }
+            h->cur = xs;
+        }
+        PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+        red_host.assign(4 * (size_t)(5 * m + 2), 0.0);
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(red_host.data(), h->red, sizeof(double) * red_host.size(),
+                                        cudaMemcpyDeviceToHost, h->stream));
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        *iters_out = m;
+        return PURIFY_OK;
+    }
     if (is_fixed_mu(scheme)) {
         // X_s of the first iteration straight from F: X_0 = c0 I + c1 F.
         const double gamma = fixed_mu_gamma(lmin, lmax, mu);
@@ -718,7 +812,7 @@ static int run_fp64(purify_ctx* h, int scheme, double tol, int max_iter, double 
 int purify_run(purify_t h, int scheme, double tol, int max_iter) {
     if (!h) return PURIFY_ERR_INVALID_ARG;
     if (!h->have_F) return PURIFY_ERR_STATE;
-    if (scheme < PURIFY_FIXED_MU_SF || scheme > PURIFY_TC_MONO) return PURIFY_ERR_INVALID_ARG;
+    if (scheme < PURIFY_FIXED_MU_SF || scheme > PURIFY_FIXED_MU_P33_MONO) return PURIFY_ERR_INVALID_ARG;
     if (!(tol >= 0.0) || max_iter < 0 || max_iter > 10000) return PURIFY_ERR_INVALID_ARG;
     PURIFY_TRY(set_device(h));
     const purify_bounds& bb = h->b;
@@ -757,6 +851,10 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
         if (trace_rule && h->opt.block_sparse) return PURIFY_ERR_UNSUPPORTED;
         if (trace_rule) {
             r = run_mixed_trace(h, scheme, tol, max_iter, S, &h->cur, &iters);
+        } else if (h->opt.block_sparse && pmm_order(scheme) == 3) {
+            r = PURIFY_ERR_UNSUPPORTED;
+        } else if (pmm_order(scheme) == 3) {
+            r = run_mixed_p33(h, scheme, mu, S, &h->cur, red);
         } else if (h->opt.block_sparse) {
             r = run_block_sparse(h, scheme, S, &h->cur, red);
             if (r == PURIFY_OK && h->mixed && !h->mixed->nnzb_history.empty())
@@ -776,7 +874,7 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
     float ms = 0.f;
     PURIFY_CUDA_TRY(cudaEventElapsedTime(&ms, h->e0, h->e1));
     purify_stats_t& st = h->st;
-    const int mult_per_it = is_fixed_mu(scheme) ? 2 : 1;
+    const int mult_per_it = products_per_iteration(scheme);
     st.iterations = iters;
     st.multiplications = mult_per_it * iters + st.refine_multiplications;
     st.seconds = 1e-3 * ms;
@@ -792,7 +890,8 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
         idem = st.idem_err_fro;
     } else if (iters > 0) {
         if (is_fixed_mu(scheme)) {
-            trace = red[4 * (size_t)(2 * (iters - 1) + 1) + 0];
+            const int ppi = products_per_iteration(scheme);
+            trace = red[4 * (size_t)(ppi * (iters - 1) + ppi - 1) + 0];
         } else {
             trace = red[4 * (size_t)(iters - 1) + 0];
             idem = std::sqrt(std::max(red[4 * (size_t)(iters - 1) + 1], 0.0));
@@ -846,7 +945,7 @@ const char* purify_strerror(int code) {
 int purify_schedule(int scheme, double lmin, double lmax, double mu, double homo, double lumo,
                     double tol, int max_iter, double* alpha, int* branch, double* beta,
                     double* beta_bar, int* iterations) {
-    if (scheme < PURIFY_FIXED_MU_SF || scheme > PURIFY_TC_MONO) return PURIFY_ERR_INVALID_ARG;
+    if (scheme < PURIFY_FIXED_MU_SF || scheme > PURIFY_FIXED_MU_P33_MONO) return PURIFY_ERR_INVALID_ARG;
     if (max_iter < 0 || !(tol >= 0.0)) return PURIFY_ERR_INVALID_ARG;
     if (!(lmax > lmin) || !(homo < lumo)) return PURIFY_ERR_BOUNDS;
     if (is_fixed_mu(scheme)) {

@@ -244,3 +244,21 @@ def test_purify_fp64_full_size_closed_form(P, nocc):
     # rounding of F itself (~1e-16 |F| sqrt(n)) is amplified by 1 / gap
     assert np.max(np.abs(D - Dc)) < 1e-10
     assert st["trace_err"] < 1e-8
+
+
+@pytest.mark.parametrize("scheme,gap", [("FIXED_MU_P33_SF", 1e-2), ("FIXED_MU_P33_MONO", 1e-2),
+                                        ("FIXED_MU_P33_SF", 1e-4)])
+def test_p33_fixed_mu_parity(P, scheme, gap):
+    # the fixed-mu scheme with P_{3,3}: five float64 products per iteration
+    h = I.dense_hamiltonian(260, 100, gap, config=88)
+    pur = P.Purifier(precision="fp64")
+    pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+    pur.run(scheme, 1e-12, 200)
+    D, st = pur.density(), pur.stats()
+    pur.close()
+    Do, r = O.purify_fixed_mu_pmm(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, m=3, tol=1e-12,
+                                  scaled=scheme.endswith("_SF"))
+    assert st["iterations"] == r.iterations
+    assert st["multiplications"] == r.multiplications == 5 * r.iterations
+    assert np.max(np.abs(D - Do)) < 1e-10
+    assert abs(st["trace"] - h.nocc) < 1e-9

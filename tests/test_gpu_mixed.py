@@ -248,3 +248,19 @@ def test_trace_rule_on_the_mixed_path(P, scheme, gap_known):
     assert abs(st["trace"] - h.nocc) < 1e-6
     Dx = O.density_closed_form(h.Q, h.lam, 0.0)
     assert np.max(np.abs(D - Dx)) <= 3e-7 + (tol if not gap_known else 0.0)
+
+
+@pytest.mark.parametrize("n,gap", [(300, 1e-2), (1000, 1e-3)])
+def test_p33_fixed_mu_on_digit_planes(P, n, gap):
+    # V and Q of P_{3,3} sit up to 7 bits above X_s: per-buffer exponents and
+    # one more digit per iteration keep the result at the mixed tolerance
+    h = I.dense_hamiltonian(n, n // 2 - 10, gap, config=89)
+    pur = P.Purifier(precision="mixed")
+    pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+    pur.run("FIXED_MU_P33_SF", 1e-10, 200)
+    D, st = pur.density(), pur.stats()
+    pur.close()
+    Do, r = O.purify_fixed_mu_pmm(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, m=3, tol=1e-10)
+    assert st["iterations"] == r.iterations and st["multiplications"] == 5 * r.iterations
+    assert np.max(np.abs(D - Do)) <= 3e-7
+    assert abs(st["trace"] - h.nocc) < 1e-6

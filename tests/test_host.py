@@ -47,6 +47,11 @@ def test_strerror_names_codes():
 
 
 def _oracle_schedule(scheme, lmin, lmax, mu, homo, lumo, tol, max_iter):
+    if scheme.startswith("FIXED_MU_P33"):
+        g = O.fixed_mu_gamma(lmin, lmax, mu)
+        b = O.fixed_mu_beta0(g, mu, homo, lumo)
+        al, be = O.pmm_schedule(3, b, tol, max_iter, scheme == "FIXED_MU_P33_SF")
+        return np.array(al), np.zeros(len(al), int), np.array(be)
     if scheme.startswith("FIXED_MU"):
         g = O.fixed_mu_gamma(lmin, lmax, mu)
         b = O.fixed_mu_beta0(g, mu, homo, lumo)
@@ -63,7 +68,7 @@ CASES = [(-1.0, 1.0, 0.0, -g / 2, g / 2) for g in (1e-1, 1e-2, 1e-3, 1e-4)] + [
     (-3.0, 2.0, -0.4, -0.45, -0.2), (-1.0, 1.0, 0.3, 0.25, 0.31)]
 
 
-@pytest.mark.parametrize("scheme", O.SCHEMES)
+@pytest.mark.parametrize("scheme", O.SCHEMES + ("FIXED_MU_P33_SF", "FIXED_MU_P33_MONO"))
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("tol", [1e-12, 1e-9, 1e-6])
 def test_schedule_bitwise_equal_to_oracle(scheme, case, tol):
