@@ -158,12 +158,11 @@ df to_df(double x) {
 int digit_kc_for(int s, bool sparse) { return sparse ? 32 : digit_kc(s); }
 
 int digit_kc(int s) {
-    static int forced = -1;
-    if (forced < 0) {
+    static const int forced = [] {  // read once (thread-safe initialisation)
         const char* e = getenv("PURIFY_DIGIT_KC");
-        forced = e ? atoi(e) : 0;
-        if (forced != 16 && forced != 32 && forced != 64) forced = 0;
-    }
+        const int v = e ? atoi(e) : 0;
+        return (v == 16 || v == 32 || v == 64) ? v : 0;
+    }();
     if (forced == 16 && s < 4) return 32;
     if (forced) return forced;
     return s <= 3 ? 64 : 32;

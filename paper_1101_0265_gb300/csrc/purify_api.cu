@@ -20,9 +20,12 @@ namespace purify {
 
 static thread_local char g_last_error[256] = "";
 
-static std::atomic<long long> g_launches{0};
-void count_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
-long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+// Kernel launches of the calling thread: a handle is used by one thread at a
+// time, so differences of this count are the handle's own launches even when
+// other threads drive other handles.
+static thread_local long long g_launches = 0;
+void count_launches(int k) { g_launches += k; }
+long long launches_so_far() { return g_launches; }
 
 int cuda_status(cudaError_t e, const char* what) {
     std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
