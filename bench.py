@@ -336,18 +336,30 @@ def _blas_threads():
     return int(env) if env else os.cpu_count()
 
 
+def main_config(n, count, schemes, tol, precision, world):
+    """The `config` of the dense workload (both arms report the same one)."""
+    return {"workload": f"dense F=Q diag(lambda) Q^T n={n}, nocc in {{n/2,n/4}} x gap in "
+                        f"{{1e-1,1e-2,1e-3,1e-4}} ({count} matrices) x schemes "
+                        f"{', '.join(schemes)}; tol {tol:g}",
+            "n": n, "matrices_per_step": count * len(schemes),
+            "tol": tol, "parallelism": f"replicas x{world}",
+            "l2": "inputs larger than L2 (each F is 134 MB, 8 distinct per step)"}
+
+
 def run_reference(args, rank, world):
     """The reference arm: the CPU oracle (no GPU work), rank 0 only."""
     if rank != 0:
         return
     n = args.n
+    schemes = tuple(args.schemes.split(","))
     count = min(args.steps + args.warmup, len(workload_specs(n)))
     hs = make_inputs(n, 0, count)
     from oracle import purify_oracle as O
 
     def one(i):
         h = hs[i % count]
-        O.purify(h.F, "TC_SF", h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=args.tol)
+        O.purify(h.F, schemes[i % len(schemes)], h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo,
+                 tol=args.tol)
     for i in range(args.warmup):
         one(i)
     t0 = time.perf_counter()
@@ -361,11 +373,11 @@ def run_reference(args, rank, world):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"dense F n={n} sweep, one TC_SF purification per step (CPU oracle)",
-                   "n": n, "tol": args.tol},
+        "config": main_config(n, len(workload_specs(n)), schemes, args.tol, "f64", world),
         "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": cores, "kind": "oracle",
-                         "sample": f"one purification per step, cycling the first {count} "
-                                   "matrices of the sweep"},
+                         "sample": f"a bounded sample of the step: one purification per step "
+                                   f"(CPU oracle, numpy float64), cycling the first {count} "
+                                   f"matrices of the sweep and the schemes {', '.join(schemes)}"},
         "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -556,12 +568,7 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": f"dense F=Q diag(lambda) Q^T n={n}, nocc in {{n/2,n/4}} x gap in "
-                               f"{{1e-1,1e-2,1e-3,1e-4}} ({len(hs)} matrices) x schemes "
-                               f"{', '.join(schemes)}; tol {args.tol:g}",
-                   "n": n, "matrices_per_step": per_step, "precision": args.precision,
-                   "tol": args.tol, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (each F is 134 MB, 8 distinct per step)"},
+        "config": main_config(n, len(hs), schemes, args.tol, args.precision, world),
         "clocks": clocks,
         "e2e": {"value": value_e2e, "unit": "matrices/s",
                 "h2d_bytes_per_step": per_step * n * n * 8,
