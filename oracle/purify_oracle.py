@@ -244,6 +244,100 @@ def purify_fixed_mu_pmm(F, lmin, lmax, mu, homo, lumo, m: int = 3, tol=1e-12, ma
     return X, res
 
 
+def pij_fixed_point(i: int, j: int) -> float:
+    """The unstable fixed point c in (0, 1) of P_{i,j} (i, j >= 1): P(x) - x is
+    negative near 0 and positive near 1 and changes sign once; bisection."""
+    lo, hi = 1e-12, 1.0 - 1e-12
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid == lo or mid == hi:
+            break
+        if P_ij(i, j, mid) - mid < 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def _fold_root(g, lo: float, hi: float) -> float:
+    """The alpha in [lo, hi] where g goes from positive to negative (bisection)."""
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mid == lo or mid == hi:
+            break
+        if g(mid) > 0.0:
+            lo = mid
+        else:
+            hi = mid
+    return lo
+
+
+def pij_alpha(i: int, j: int, c: float, beta: float, betabar: float) -> float:
+    """Scaling about the unstable fixed point c for P_{i,j}, i and j odd: the
+    unoccupied side folds at P(alpha (beta - c) + c) = P(c (1 - alpha)) (its
+    lower end meets its edge), the occupied side at P(alpha (betabar - c) + c)
+    = P(c + alpha (1 - c)); one alpha serves both, so the smaller.  With
+    i = j, c = 1/2 and betabar = 1 - beta this is pmm_alpha."""
+    a_u = _fold_root(lambda a: P_ij(i, j, a * (beta - c) + c) - P_ij(i, j, c * (1.0 - a)),
+                     1.0, c / (c - beta))
+    a_o = _fold_root(lambda a: P_ij(i, j, c + a * (1.0 - c)) - P_ij(i, j, a * (betabar - c) + c),
+                     1.0, (1.0 - c) / (betabar - c))
+    return min(a_u, a_o)
+
+
+def pij_schedule(i: int, j: int, beta: float, betabar: float, tol: float, max_iter: int,
+                 scaled: bool = True):
+    """Scalar part of the fixed-mu scheme with P_{i,j} (i, j odd) scaled about
+    its unstable fixed point c: per iteration alpha, then beta (upper bound of
+    the unoccupied images: the larger of its edge's and its folded end's
+    image) and betabar (lower bound of the occupied ones, likewise).  Stops
+    once max(beta, 1 - betabar) <= tol."""
+    c = pij_fixed_point(i, j)
+    out = []
+    while max(beta, 1.0 - betabar) > tol and len(out) < max_iter:
+        a = pij_alpha(i, j, c, beta, betabar) if scaled else 1.0
+        beta = max(P_ij(i, j, a * (beta - c) + c), P_ij(i, j, c * (1.0 - a)))
+        betabar = min(P_ij(i, j, a * (betabar - c) + c), P_ij(i, j, c + a * (1.0 - c)))
+        out.append((a, beta, betabar))
+    return c, out
+
+
+def purify_fixed_mu_pij(F, lmin, lmax, mu, homo, lumo, i: int, j: int, tol=1e-12, max_iter=200,
+                        scaled=True):
+    """Fixed-mu purification with f(X) = P_{i,j}(alpha (X - c I) + c I), i and
+    j odd, c the unstable fixed point of P_{i,j}; X_0 maps mu to c and the
+    spectrum into [0, 1]: X_0 = c I + (mu I - F) / gamma with gamma =
+    max((mu - lmin) / (1 - c), (lmax - mu) / c); beta_0 = c - (lumo - mu) /
+    gamma, betabar_0 = c + (mu - homo) / gamma."""
+    F = np.asarray(F, dtype=np.float64)
+    n = F.shape[0]
+    Id = np.eye(n)
+    c = pij_fixed_point(i, j)
+    gamma = max((mu - lmin) / (1.0 - c), (lmax - mu) / c)
+    X = c * Id + (mu * Id - F) / gamma
+    beta, betabar = c - (lumo - mu) / gamma, c + (mu - homo) / gamma
+    res = Result(scheme=f"FIXED_MU_P{i}{j}" + ("_SF" if scaled else "_MONO"), beta0=beta,
+                 betabar0=betabar, f0=(c + mu / gamma, -1.0 / gamma))
+    _, steps = pij_schedule(i, j, beta, betabar, tol, max_iter, scaled)
+    for a, b, bb in steps:
+        X = _matrix_P(i, j, a * (X - c * Id) + c * Id)
+        res.alphas.append(a)
+        res.betas.append(b)
+        res.betabars.append(bb)
+        res.traces.append(float(np.trace(X)))
+        res.iterations += 1
+        res.multiplications += PIJ_PRODUCTS.get((i, j), i + j + 1)
+    res.converged = max(res.betas[-1], 1.0 - res.betabars[-1]) <= tol if steps else \
+        max(beta, 1.0 - betabar) <= tol
+    return X, res
+
+
+# Products per iteration as the library evaluates them: P_{3,1} = x^4 (5 - 4x):
+# S = X^2, T = S^2, X = 5 T - 4 T X; P_{1,3} = x^2 (10 - 20x + 15x^2 - 4x^3):
+# V = 15 X - 4 X^2, Q = X V - 20 X + 10 I, S = X^2, X = S Q.
+PIJ_PRODUCTS = {(1, 1): 2, (3, 3): 5, (3, 1): 3, (1, 3): 4}
+
+
 def _matrix_P(i: int, j: int, Xs):
     """P_{i,j} of a symmetric matrix, from its definition as a polynomial:
     Xs^(i+1) (sum_k C(i+k, k) (I - Xs)^k), products in plain numpy."""

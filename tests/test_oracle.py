@@ -487,3 +487,63 @@ def test_pmm_scheme():
     for a in rd.alphas:
         x = O.P_ij(3, 3, a * (x - 0.5) + 0.5)
     assert np.max(np.abs(np.diag(Xd) - x)) < 1e-13
+
+
+# --- asymmetric P_{i,j}: scaling about the unstable fixed point ----------------
+
+def test_pij_fixed_points():
+    for i, j in ((1, 3), (3, 1), (1, 5), (3, 5)):
+        c = O.pij_fixed_point(i, j)
+        assert 0.0 < c < 1.0 and abs(O.P_ij(i, j, c) - c) < 1e-15
+        assert O.pij_fixed_point(j, i) == pytest.approx(1.0 - c, abs=1e-15)  # P_ij(x) = 1 - P_ji(1 - x)
+    assert O.pij_fixed_point(3, 3) == pytest.approx(0.5, abs=1e-15)
+
+
+def test_pij_alpha_reduces_and_folds():
+    for beta in np.linspace(0.02, 0.49, 25):
+        assert O.pij_alpha(1, 1, 0.5, beta, 1.0 - beta) == pytest.approx(O.fixed_mu_alpha(beta), rel=1e-15)
+        assert O.pij_alpha(3, 3, 0.5, beta, 1.0 - beta) == pytest.approx(O.pmm_alpha(3, beta), rel=1e-14)
+    # asymmetric: the binding side folds exactly, the other not past its edge
+    c = O.pij_fixed_point(3, 1)
+    for beta, betabar in ((0.2, 0.9), (0.7, 0.95), (0.5, 0.99)):
+        a = O.pij_alpha(3, 1, c, beta, betabar)
+        gu = O.P_ij(3, 1, a * (beta - c) + c) - O.P_ij(3, 1, c * (1 - a))
+        go = O.P_ij(3, 1, c + a * (1 - c)) - O.P_ij(3, 1, a * (betabar - c) + c)
+        assert a >= 1.0 and gu >= -1e-15 and go >= -1e-15 and min(gu, go) < 1e-12
+
+
+@pytest.mark.parametrize("i,j", [(1, 3), (3, 1), (3, 3)])
+def test_pij_scheme_bounds_track_the_eigenvalues(i, j):
+    # on a diagonal F the recursion acts entry by entry: after every iteration
+    # the unoccupied images lie in [0, beta] and the occupied in [betabar, 1]
+    lam = np.concatenate([np.linspace(-1, -0.02, 30), np.linspace(0.03, 1, 25)])
+    h = I.diagonal_hamiltonian(lam, 0.0)
+    c = O.pij_fixed_point(i, j)
+    gamma = max((0.0 + 1.0) / (1.0 - c), (1.0 - 0.0) / c)
+    x = c + (0.0 - lam) / gamma
+    beta, betabar = c - 0.03 / gamma, c + 0.02 / gamma
+    _, steps = O.pij_schedule(i, j, beta, betabar, 1e-12, 200)
+    occ = lam < 0
+    for a, b, bb in steps:
+        x = O.P_ij(i, j, a * (x - c) + c)
+        assert np.all(x[~occ] <= b + 1e-15) and np.all(x[~occ] >= -1e-15)
+        assert np.all(x[occ] >= bb - 1e-15) and np.all(x[occ] <= 1 + 1e-15)
+    X, r = O.purify_fixed_mu_pij(h.F, -1.0, 1.0, 0.0, -0.02, 0.03, i, j, tol=1e-12)
+    assert r.converged and np.max(np.abs(np.diag(X) - occ)) < 1e-12
+    assert np.max(np.abs(np.diag(X) - x)) < 1e-13
+
+
+def test_pij_scheme_dense():
+    h = I.dense_hamiltonian(150, 50, 1e-3, config=11)
+    Dx = O.density_closed_form(h.Q, h.lam, 0.0)
+    for i, j in ((1, 3), (3, 1)):
+        X, r = O.purify_fixed_mu_pij(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, i, j, tol=1e-12)
+        _, rm = O.purify_fixed_mu_pij(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, i, j, tol=1e-12,
+                                      scaled=False)
+        assert r.converged and np.max(np.abs(X - Dx)) < 1e-11
+        assert r.iterations < rm.iterations
+        assert r.multiplications == O.PIJ_PRODUCTS[(i, j)] * r.iterations
+    # i = j = 3 through the general route is the P_{m,m} scheme
+    X3, r3 = O.purify_fixed_mu_pij(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, 3, 3, tol=1e-12)
+    Xm, rm3 = O.purify_fixed_mu_pmm(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, m=3, tol=1e-12)
+    assert r3.iterations == rm3.iterations and np.max(np.abs(X3 - Xm)) < 1e-11
