@@ -62,6 +62,18 @@ extern "C" {
  * five products per iteration. */
 #define PURIFY_FIXED_MU_P33_SF   4
 #define PURIFY_FIXED_MU_P33_MONO 5  /* the same with alpha = 1                     */
+/* Asymmetric P_{i,j} (i, j odd, i != j) scaled about their unstable fixed
+ * point c (the paper: for i != j the scaling is about that point rather than
+ * 1/2): X_0 = c I + (mu I - F) / gamma, gamma = max((mu - lmin) / (1 - c),
+ * (lmax - mu) / c); per iteration alpha = the smaller of the two sides' fold
+ * solutions, and beta (unoccupied) and beta_bar (occupied) follow their
+ * edges' and folded ends' images.  P_{1,3} = x^2 (10 - 20x + 15x^2 - 4x^3):
+ * four products per iteration; P_{3,1} = x^4 (5 - 4x): three. */
+#define PURIFY_FIXED_MU_P13_SF   6
+#define PURIFY_FIXED_MU_P13_MONO 7
+#define PURIFY_FIXED_MU_P31_SF   8
+#define PURIFY_FIXED_MU_P31_MONO 9
+#define PURIFY_SCHEME_LAST       9
 
 /* ---- arithmetic of the matrix products -------------------------------- */
 #define PURIFY_FP64    0  /* float64 FMA on the SIMT pipes                          */

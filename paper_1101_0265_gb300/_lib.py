@@ -26,7 +26,8 @@ ERR_STATE = -7
 ERR_UNSUPPORTED = -8
 
 SCHEMES = {"FIXED_MU_SF": 0, "FIXED_MU_MONO": 1, "TC_SF": 2, "TC_MONO": 3, "FIXED_MU_P33_SF": 4,
-           "FIXED_MU_P33_MONO": 5}
+           "FIXED_MU_P33_MONO": 5, "FIXED_MU_P13_SF": 6, "FIXED_MU_P13_MONO": 7, "FIXED_MU_P31_SF": 8,
+           "FIXED_MU_P31_MONO": 9}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 BRANCH_RULES = {"beta": 0, "trace": 1}
 

@@ -85,9 +85,13 @@ double tc_map(int branch, double a, double x);
 // The fixed-mu polynomial order of a scheme (1: P_{1,1}, 3: P_{3,3}), its
 // products per iteration, P_{i,j} on a scalar and the P_{m,m} scaling alpha.
 int pmm_order(int scheme);
+void pij_orders(int scheme, int* i, int* j);
+bool is_asymmetric(int scheme);
 int products_per_iteration(int scheme);
 double P_ij_scalar(int i, int j, double x);
 double pmm_alpha(int m, double beta);
+double pij_fixed_point(int i, int j);
+double pij_alpha(int i, int j, double c, double b, double bb);
 
 struct MixedState;
 

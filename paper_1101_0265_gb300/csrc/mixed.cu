@@ -221,8 +221,48 @@ static int bound_exponent(Fn p, double lo, double hi) {
     return e;
 }
 
-int run_mixed_p33(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur, std::vector<double>& red) {
+// One product of a polynomial's plan: operands and output name buffers
+// (kX: X_s, kB0 / kB1: the two intermediates, kS: X_s^2, kOut: the
+// iteration's result), Y = cP A B + cE A + cI I; `val` is the buffer's value
+// as a function of x (an eigenvalue of X_s), which bounds its exponent.
+enum { kX = 0, kB0 = 1, kB1 = 2, kS = 3, kOut = 4 };
+struct PlanStep {
+    int a, b, out;
+    int use_E;
+    double cP, cE, cI;
+    double (*val)(double);
+};
+
+static double v_x2(double x) { return x * x; }
+static double v_x4(double x) { return x * x * x * x; }
+static double v_p33_v(double x) { return 70.0 * x - 20.0 * x * x; }
+static double v_p33_q(double x) { return 35.0 - 84.0 * x + 70.0 * x * x - 20.0 * x * x * x; }
+static double v_p13_v(double x) { return 15.0 * x - 4.0 * x * x; }
+static double v_p13_q(double x) { return 10.0 - 20.0 * x + 15.0 * x * x - 4.0 * x * x * x; }
+
+// P_{3,3} = x^4 (35 - 84x + 70x^2 - 20x^3)
+static const PlanStep kPlan33[] = {{kX, kX, kB0, 1, -20.0, 70.0, 0.0, v_p33_v},
+                                   {kX, kB0, kB1, 1, 1.0, -84.0, 35.0, v_p33_q},
+                                   {kX, kX, kS, 0, 1.0, 0.0, 0.0, v_x2},
+                                   {kS, kS, kB0, 0, 1.0, 0.0, 0.0, v_x4},
+                                   {kB0, kB1, kOut, 0, 1.0, 0.0, 0.0, nullptr}};
+// P_{3,1} = x^4 (5 - 4x)
+static const PlanStep kPlan31[] = {{kX, kX, kS, 0, 1.0, 0.0, 0.0, v_x2},
+                                   {kS, kS, kB0, 0, 1.0, 0.0, 0.0, v_x4},
+                                   {kB0, kX, kOut, 1, -4.0, 5.0, 0.0, nullptr}};
+// P_{1,3} = x^2 (10 - 20x + 15x^2 - 4x^3)
+static const PlanStep kPlan13[] = {{kX, kX, kB0, 1, -4.0, 15.0, 0.0, v_p13_v},
+                                   {kX, kB0, kB1, 1, 1.0, -20.0, 10.0, v_p13_q},
+                                   {kX, kX, kS, 0, 1.0, 0.0, 0.0, v_x2},
+                                   {kS, kB1, kOut, 0, 1.0, 0.0, 0.0, nullptr}};
+
+int run_mixed_poly(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur, std::vector<double>& red) {
     if (h->opt.refine_squares) return PURIFY_ERR_UNSUPPORTED;
+    int pi, pj;
+    pij_orders(scheme, &pi, &pj);
+    const PlanStep* plan = pi == 3 && pj == 3 ? kPlan33 : (pi == 3 ? kPlan31 : kPlan13);
+    const int np = products_per_iteration(scheme);
+    const double c = pi == pj ? 0.5 : pij_fixed_point(pi, pj);
     const int n = (int)h->n;
     const int n_pad = pad128(n);
     PURIFY_TRY(ensure_mixed(h, n_pad));
@@ -242,19 +282,24 @@ int run_mixed_p33(purify_ctx* h, int scheme, double mu, const Schedule& S, int* 
     const int T = n_pad / 128;
     const int rb = remainder_bits(n_pad);
     const double tile_flops = 2.0 * 128.0 * 128.0 * (double)n_pad * (double)(T * (T + 1) / 2);
-    // exponents of X_s and of the intermediates over the spectrum of X_s,
-    // within [(1 - alpha)/2, (1 + alpha)/2] for the run's largest alpha
+    // exponents: the eigenvalues of X_s lie in [c (1 - alpha), c + alpha (1 - c)]
     double amax = 1.0;
     for (double a : S.alpha) amax = std::max(amax, a);
     if (amax > 3.0) return PURIFY_ERR_UNSUPPORTED;
-    const double lo = 0.5 * (1.0 - amax) - 1e-3, hi = 0.5 * (1.0 + amax) + 1e-3;
+    const double lo = c * (1.0 - amax) - 1e-3, hi = c + amax * (1.0 - c) + 1e-3;
+    // a buffer's exponent is that of its latest content (V and T share one),
+    // so each step's operand and output exponents come from walking the plan
     const int eX = bound_exponent([](double x) { return x; }, lo, hi);
-    const int eV = bound_exponent([](double x) { return 70.0 * x - 20.0 * x * x; }, lo, hi);
-    const int eQ = bound_exponent([](double x) { return 35.0 - 84.0 * x + 70.0 * x * x - 20.0 * x * x * x; }, lo, hi);
-    const int eS = bound_exponent([](double x) { return x * x; }, lo, hi);
-    const int eT = bound_exponent([](double x) { return x * x * x * x; }, lo, hi);
-    // digits per iteration: the mapped-gap rule plus one (V and Q sit up to
-    // 7 bits above X_s)
+    int ecur[4] = {eX, 0, 0, 0};
+    int e_a[8], e_b[8], e_o[8];
+    for (int k = 0; k < np; ++k) {
+        e_a[k] = ecur[plan[k].a];
+        e_b[k] = ecur[plan[k].b];
+        e_o[k] = plan[k].out == kOut ? eX : bound_exponent(plan[k].val, lo, hi);
+        if (plan[k].out != kOut) ecur[plan[k].out] = e_o[k];
+    }
+    // digits per iteration: the mapped-gap rule plus one (intermediates sit
+    // several bits above X_s)
     std::vector<int> sd(m + 1);
     for (int i = 0; i < m; ++i) {
         const double b = i ? S.beta[i - 1] : S.beta0;
@@ -270,90 +315,56 @@ int run_mixed_p33(purify_ctx* h, int scheme, double mu, const Schedule& S, int* 
     PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * slots, h->stream));
     PURIFY_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), h->stream));
     PURIFY_CUDA_TRY(cudaEventRecord(h->e0, h->stream));
-    const double gamma = 2.0 * std::max(h->b.lmax - mu, mu - h->b.lmin);
-    const double c0 = mu / gamma + 0.5, c1 = -1.0 / gamma;
+    const double gamma = std::max((mu - h->b.lmin) / (1.0 - c), (h->b.lmax - mu) / c);
     double* D = h->X[0];
     *cur = 0;
-    if (m == 0) {
-        PURIFY_TRY(launch_affine_f64(h->F, n, D, n, c1, c0, h->stream));
+    if (m == 0) {  // X_0 = c I + (mu I - F) / gamma
+        PURIFY_TRY(launch_affine_f64(h->F, n, D, n, -1.0 / gamma, c + mu / gamma, h->stream));
     } else {
+        // X_s = c I + alpha_1 (X_0 - c I)
         const double a1 = S.alpha[0];
-        PURIFY_TRY(launch_split(h->F, n, n, n_pad, a1 * c1, a1 * (c0 - 0.5) + 0.5, eX, sd[0], rb, ms->Xd[0], nullptr,
-                                h->stream));
+        PURIFY_TRY(launch_split(h->F, n, n, n_pad, -a1 / gamma, c + a1 * mu / gamma, eX, sd[0], rb, ms->Xd[0],
+                                nullptr, h->stream));
         int x = 0;
         for (int i = 0; i < m; ++i) {
             const int s = sd[i];
             const double fl = pairs_of(s) * tile_flops;
-            DigitStep base;
-            base.n = n;
-            base.n_pad = n_pad;
-            base.rbits = rb;
-            base.s_in = s;
-            base.s_out = s;
-            base.err = ms->err;
-            base.scratch = ms->scratch;
-            base.max_ctas = ms->ctas;
-            // V = 70 X_s - 20 X_s^2
-            DigitStep p = base;
-            p.A = p.B = ms->Xd[x];
-            p.eA = p.eB = eX;
-            p.use_E = 1;
-            p.cP = -20.0;
-            p.cE = 70.0;
-            p.out = ms->Pd[0];
-            p.e_out = eV;
-            PURIFY_TRY(product(h, p, fl));
-            // Q = X_s V - 84 X_s + 35 I
-            p = base;
-            p.A = ms->Xd[x];
-            p.eA = eX;
-            p.B = ms->Pd[0];
-            p.eB = eV;
-            p.use_E = 1;
-            p.cP = 1.0;
-            p.cE = -84.0;
-            p.cI = 35.0;
-            p.out = ms->Pd[1];
-            p.e_out = eQ;
-            PURIFY_TRY(product(h, p, fl));
-            // S = X_s^2
-            p = base;
-            p.A = p.B = ms->Xd[x];
-            p.eA = p.eB = eX;
-            p.cP = 1.0;
-            p.out = ms->Sd;
-            p.e_out = eS;
-            PURIFY_TRY(product(h, p, fl));
-            // T = S^2 (over V, no longer needed)
-            p = base;
-            p.A = p.B = ms->Sd;
-            p.eA = p.eB = eS;
-            p.cP = 1.0;
-            p.out = ms->Pd[0];
-            p.e_out = eT;
-            PURIFY_TRY(product(h, p, fl));
-            // X_i = T Q, emitted as the next X_s (or as D after the last)
-            p = base;
-            p.A = ms->Pd[0];
-            p.eA = eT;
-            p.B = ms->Pd[1];
-            p.eB = eQ;
-            p.cP = 1.0;
-            const bool last = (i + 1 == m);
-            if (last) {
-                p.red = h->red + 4 * (2 * i + 1);
-                p.out = nullptr;
-                p.s_out = 0;
-                p.out64 = D;
-            } else {
-                const double an = S.alpha[i + 1];
-                p.dY = an;
-                p.dI = 0.5 * (1.0 - an);
-                p.out = ms->Xd[x ^ 1];
-                p.s_out = sd[i + 1];
-                p.e_out = eX;
+            __nv_bfloat16* buf[4] = {ms->Xd[x], ms->Pd[0], ms->Pd[1], ms->Sd};
+            for (int k = 0; k < np; ++k) {
+                const PlanStep& ps = plan[k];
+                DigitStep st;
+                st.n = n;
+                st.n_pad = n_pad;
+                st.rbits = rb;
+                st.s_in = s;
+                st.err = ms->err;
+                st.scratch = ms->scratch;
+                st.max_ctas = ms->ctas;
+                st.A = buf[ps.a];
+                st.eA = e_a[k];
+                st.B = buf[ps.b];
+                st.eB = e_b[k];
+                st.use_E = ps.use_E;
+                st.cP = ps.cP;
+                st.cE = ps.cE;
+                st.cI = ps.cI;
+                if (ps.out != kOut) {
+                    st.out = buf[ps.out];
+                    st.s_out = s;
+                    st.e_out = e_o[k];
+                } else if (i + 1 == m) {
+                    st.red = h->red + 4 * (2 * i + 1);
+                    st.out64 = D;
+                } else {  // the next iteration's X_s = alpha (X - c I) + c I
+                    const double an = S.alpha[i + 1];
+                    st.dY = an;
+                    st.dI = c * (1.0 - an);
+                    st.out = ms->Xd[x ^ 1];
+                    st.s_out = sd[i + 1];
+                    st.e_out = eX;
+                }
+                PURIFY_TRY(product(h, st, fl));
             }
-            PURIFY_TRY(product(h, p, fl));
             x ^= 1;
         }
     }

@@ -52,9 +52,9 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
 // bounds beta and beta_bar follow the branches taken; without them the run
 // stops when ||X - X^2||_F <= tol.  Fills S with the steps taken.
 int run_mixed_trace(purify_ctx* h, int scheme, double tol, int max_iter, Schedule& S, int* cur, int* iters);
-// The fixed-mu scheme with P_{3,3} on the digit planes (five products per
-// iteration; see purify.h).
-int run_mixed_p33(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur, std::vector<double>& red);
+// The fixed-mu schemes with P_{3,3}, P_{1,3} and P_{3,1} on the digit planes
+// (product plans in mixed.cu; see purify.h).
+int run_mixed_poly(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur, std::vector<double>& red);
 int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
               std::vector<double>& red);
 void mixed_free(MixedState* ms);

@@ -77,21 +77,37 @@ double tc_map(int branch, double a, double x) {
     return 2.0 * (1.0 + a) * x - (1.0 + a) * (1.0 + a) * x * x;
 }
 
-static bool is_fixed_mu(int scheme) {
-    return scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_FIXED_MU_MONO || scheme == PURIFY_FIXED_MU_P33_SF ||
-           scheme == PURIFY_FIXED_MU_P33_MONO;
-}
+static bool is_fixed_mu(int scheme) { return scheme != PURIFY_TC_SF && scheme != PURIFY_TC_MONO; }
 static bool is_scaled(int scheme) {
-    return scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_TC_SF || scheme == PURIFY_FIXED_MU_P33_SF;
+    return scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_TC_SF || scheme == PURIFY_FIXED_MU_P33_SF ||
+           scheme == PURIFY_FIXED_MU_P13_SF || scheme == PURIFY_FIXED_MU_P31_SF;
 }
 
 int pmm_order(int scheme) {
     return (scheme == PURIFY_FIXED_MU_P33_SF || scheme == PURIFY_FIXED_MU_P33_MONO) ? 3 : 1;
 }
 
+void pij_orders(int scheme, int* i, int* j) {
+    *i = *j = 1;
+    if (scheme == PURIFY_FIXED_MU_P33_SF || scheme == PURIFY_FIXED_MU_P33_MONO) *i = *j = 3;
+    if (scheme == PURIFY_FIXED_MU_P13_SF || scheme == PURIFY_FIXED_MU_P13_MONO) *j = 3;
+    if (scheme == PURIFY_FIXED_MU_P31_SF || scheme == PURIFY_FIXED_MU_P31_MONO) *i = 3;
+}
+
+bool is_asymmetric(int scheme) {
+    int i, j;
+    pij_orders(scheme, &i, &j);
+    return i != j;
+}
+
 int products_per_iteration(int scheme) {
     if (!is_fixed_mu(scheme)) return 1;
-    return pmm_order(scheme) == 3 ? 5 : 2;
+    int i, j;
+    pij_orders(scheme, &i, &j);
+    if (i == 3 && j == 3) return 5;
+    if (i == 1 && j == 3) return 4;
+    if (i == 3 && j == 1) return 3;
+    return 2;
 }
 
 // P_{i,j}(x) = x^(i+1) sum_{k=0..j} C(i+k, k) (1 - x)^k: Horner in t = 1 - x,
@@ -107,6 +123,48 @@ double P_ij_scalar(int i, int j, double x) {
     double p = x;
     for (int q = 0; q < i; ++q) p = p * x;
     return p * acc;
+}
+
+// The unstable fixed point c in (0, 1) of P_{i,j} (i, j >= 1): bisection on
+// the sign of P(x) - x.
+double pij_fixed_point(int i, int j) {
+    double lo = 1e-12, hi = 1.0 - 1e-12;
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (P_ij_scalar(i, j, mid) - mid < 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// The alpha in [lo, hi] where g goes from positive to negative (bisection).
+template <typename G>
+static double fold_root(G g, double lo, double hi) {
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid == lo || mid == hi) break;
+        if (g(mid) > 0.0)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Scaling about c for asymmetric P_{i,j}: the smaller of the unoccupied
+// side's fold (P(alpha (beta - c) + c) = P(c (1 - alpha))) and the occupied
+// side's (P(c + alpha (1 - c)) = P(alpha (beta_bar - c) + c)).
+double pij_alpha(int i, int j, double c, double b, double bb) {
+    const double au = fold_root(
+        [&](double a) { return P_ij_scalar(i, j, a * (b - c) + c) - P_ij_scalar(i, j, c * (1.0 - a)); }, 1.0,
+        c / (c - b));
+    const double ao = fold_root(
+        [&](double a) { return P_ij_scalar(i, j, c + a * (1.0 - c)) - P_ij_scalar(i, j, a * (bb - c) + c); }, 1.0,
+        (1.0 - c) / (bb - c));
+    return std::min(au, ao);
 }
 
 // The alpha >= 1 with P_{m,m}(alpha (beta - 1/2) + 1/2) = P_{m,m}((1 - alpha)/2):
@@ -127,6 +185,27 @@ double pmm_alpha(int m, double beta) {
 
 static int build_schedule(int scheme, double lmin, double lmax, double mu, double homo, double lumo,
                           double tol, int max_iter, Schedule& S) {
+    if (is_asymmetric(scheme)) {
+        int i, j;
+        pij_orders(scheme, &i, &j);
+        const double c = pij_fixed_point(i, j);
+        const double gamma = std::max((mu - lmin) / (1.0 - c), (lmax - mu) / c);
+        double b = c - (lumo - mu) / gamma, bb = c + (mu - homo) / gamma;
+        S.beta0 = b;
+        S.betabar0 = bb;
+        const bool scaled = is_scaled(scheme);
+        while (std::max(b, 1.0 - bb) > tol && (int)S.alpha.size() < max_iter) {
+            const double a = scaled ? pij_alpha(i, j, c, b, bb) : 1.0;
+            b = std::max(P_ij_scalar(i, j, a * (b - c) + c), P_ij_scalar(i, j, c * (1.0 - a)));
+            bb = std::min(P_ij_scalar(i, j, a * (bb - c) + c), P_ij_scalar(i, j, c + a * (1.0 - c)));
+            S.alpha.push_back(a);
+            S.beta.push_back(b);
+            S.betabar.push_back(bb);
+            S.branch.push_back(0);
+        }
+        S.converged = std::max(b, 1.0 - bb) <= tol;
+        return PURIFY_OK;
+    }
     if (is_fixed_mu(scheme)) {
         const double gamma = fixed_mu_gamma(lmin, lmax, mu);
         double beta = fixed_mu_beta0(gamma, mu, homo, lumo);
@@ -656,10 +735,19 @@ static int run_fp64(purify_ctx* h, int scheme, double tol, int max_iter, double 
     const int64_t n = h->n;
     const double lmin = h->b.lmin, lmax = h->b.lmax;
     int m = (int)S.alpha.size();
-    if (is_fixed_mu(scheme) && pmm_order(scheme) == 3) {
-        // P_{3,3}(x) = x^4 (35 - 84 x + 70 x^2 - 20 x^3) in five products:
-        // V = 70 X_s - 20 X_s^2, Q = X_s V - 84 X_s + 35 I, S = X_s^2,
-        // T = S^2 (over V), X_i = T Q (emitted as the next X_s)
+    if (is_fixed_mu(scheme) && (pmm_order(scheme) == 3 || is_asymmetric(scheme))) {
+        // Higher-order and asymmetric P_{i,j}, scaled about c (1/2 when i = j):
+        //   P_{3,3} = x^4 (35 - 84x + 70x^2 - 20x^3): V = 70 X_s - 20 X_s^2,
+        //     Q = X_s V - 84 X_s + 35 I, S = X_s^2, T = S^2 (over V), X = T Q;
+        //   P_{3,1} = x^4 (5 - 4x): S = X_s^2, T = S^2, X = 5 T - 4 T X_s;
+        //   P_{1,3} = x^2 (10 - 20x + 15x^2 - 4x^3): V = 15 X_s - 4 X_s^2,
+        //     Q = X_s V - 20 X_s + 10 I, S = X_s^2, X = S Q;
+        // the last product also applies the next iteration's scaling.
+        int pi, pj;
+        pij_orders(scheme, &pi, &pj);
+        const double c = pi == pj ? 0.5 : pij_fixed_point(pi, pj);
+        const double gamma = std::max((mu - lmin) / (1.0 - c), (lmax - mu) / c);
+        const int ppi = products_per_iteration(scheme);
         if (h->p3_cap < n) {
             cudaFree(h->P3[0]);
             cudaFree(h->P3[1]);
@@ -669,34 +757,47 @@ static int run_fp64(purify_ctx* h, int scheme, double tol, int max_iter, double 
             PURIFY_CUDA_TRY(cudaMalloc(&h->P3[1], sizeof(double) * (size_t)n * n));
             h->p3_cap = n;
         }
-        const double gamma = fixed_mu_gamma(lmin, lmax, mu);
-        const double c0 = mu / gamma + 0.5, c1 = -1.0 / gamma;
-        PURIFY_TRY(ensure_red(h, 4 * (int64_t)(5 * m + 2)));
-        PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * (5 * m + 2), h->stream));
+        PURIFY_TRY(ensure_red(h, 4 * (int64_t)(ppi * m + 2)));
+        PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * (ppi * m + 2), h->stream));
         PURIFY_CUDA_TRY(cudaEventRecord(h->e0, h->stream));
-        if (m == 0) {
-            PURIFY_TRY(launch_affine_f64(h->F, n, h->X[0], n, c1, c0, h->stream));
+        if (m == 0) {  // X_0 = c I + (mu I - F) / gamma
+            PURIFY_TRY(launch_affine_f64(h->F, n, h->X[0], n, -1.0 / gamma, c + mu / gamma, h->stream));
             h->cur = 0;
         } else {
+            // X_s = c I + alpha_1 (X_0 - c I)
             const double a1 = S.alpha[0];
-            PURIFY_TRY(launch_affine_f64(h->F, n, h->X[0], n, a1 * c1, a1 * (c0 - 0.5) + 0.5, h->stream));
+            PURIFY_TRY(launch_affine_f64(h->F, n, h->X[0], n, -a1 / gamma, c + a1 * mu / gamma, h->stream));
             int xs = 0;
             double* V = h->P3[0];
             double* Q = h->P3[1];
             for (int i = 0; i < m; ++i) {
                 double* Xs = h->X[xs];
-                PURIFY_TRY(step64(h, Xs, Xs, Xs, V, -20.0, 70.0, 0.0, 1.0, 0.0, 5 * i));
-                PURIFY_TRY(step64(h, Xs, V, Xs, Q, 1.0, -84.0, 35.0, 1.0, 0.0, 5 * i + 1));
-                PURIFY_TRY(step64(h, Xs, Xs, nullptr, h->S, 1.0, 0.0, 0.0, 1.0, 0.0, 5 * i + 2));
-                PURIFY_TRY(step64(h, h->S, h->S, nullptr, V, 1.0, 0.0, 0.0, 1.0, 0.0, 5 * i + 3));
+                double* Xn = h->X[xs ^ 1];
                 const double an = (i + 1 < m) ? S.alpha[i + 1] : 1.0;
-                PURIFY_TRY(step64(h, V, Q, nullptr, h->X[xs ^ 1], 1.0, 0.0, 0.0, an, 0.5 * (1.0 - an), 5 * i + 4));
+                const double dY = an, dI = c * (1.0 - an);
+                const int sl = ppi * i;
+                if (pi == 3 && pj == 3) {
+                    PURIFY_TRY(step64(h, Xs, Xs, Xs, V, -20.0, 70.0, 0.0, 1.0, 0.0, sl));
+                    PURIFY_TRY(step64(h, Xs, V, Xs, Q, 1.0, -84.0, 35.0, 1.0, 0.0, sl + 1));
+                    PURIFY_TRY(step64(h, Xs, Xs, nullptr, h->S, 1.0, 0.0, 0.0, 1.0, 0.0, sl + 2));
+                    PURIFY_TRY(step64(h, h->S, h->S, nullptr, V, 1.0, 0.0, 0.0, 1.0, 0.0, sl + 3));
+                    PURIFY_TRY(step64(h, V, Q, nullptr, Xn, 1.0, 0.0, 0.0, dY, dI, sl + 4));
+                } else if (pi == 3) {  // P_{3,1}
+                    PURIFY_TRY(step64(h, Xs, Xs, nullptr, h->S, 1.0, 0.0, 0.0, 1.0, 0.0, sl));
+                    PURIFY_TRY(step64(h, h->S, h->S, nullptr, V, 1.0, 0.0, 0.0, 1.0, 0.0, sl + 1));
+                    PURIFY_TRY(step64(h, V, Xs, V, Xn, -4.0, 5.0, 0.0, dY, dI, sl + 2));
+                } else {  // P_{1,3}
+                    PURIFY_TRY(step64(h, Xs, Xs, Xs, V, -4.0, 15.0, 0.0, 1.0, 0.0, sl));
+                    PURIFY_TRY(step64(h, Xs, V, Xs, Q, 1.0, -20.0, 10.0, 1.0, 0.0, sl + 1));
+                    PURIFY_TRY(step64(h, Xs, Xs, nullptr, h->S, 1.0, 0.0, 0.0, 1.0, 0.0, sl + 2));
+                    PURIFY_TRY(step64(h, h->S, Q, nullptr, Xn, 1.0, 0.0, 0.0, dY, dI, sl + 3));
+                }
                 xs ^= 1;
             }
             h->cur = xs;
         }
         PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
-        red_host.assign(4 * (size_t)(5 * m + 2), 0.0);
+        red_host.assign(4 * (size_t)(ppi * m + 2), 0.0);
         PURIFY_CUDA_TRY(cudaMemcpyAsync(red_host.data(), h->red, sizeof(double) * red_host.size(),
                                         cudaMemcpyDeviceToHost, h->stream));
         PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -815,7 +916,7 @@ static int run_fp64(purify_ctx* h, int scheme, double tol, int max_iter, double 
 int purify_run(purify_t h, int scheme, double tol, int max_iter) {
     if (!h) return PURIFY_ERR_INVALID_ARG;
     if (!h->have_F) return PURIFY_ERR_STATE;
-    if (scheme < PURIFY_FIXED_MU_SF || scheme > PURIFY_FIXED_MU_P33_MONO) return PURIFY_ERR_INVALID_ARG;
+    if (scheme < PURIFY_FIXED_MU_SF || scheme > PURIFY_SCHEME_LAST) return PURIFY_ERR_INVALID_ARG;
     if (!(tol >= 0.0) || max_iter < 0 || max_iter > 10000) return PURIFY_ERR_INVALID_ARG;
     PURIFY_TRY(set_device(h));
     const purify_bounds& bb = h->b;
@@ -854,10 +955,10 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
         if (trace_rule && h->opt.block_sparse) return PURIFY_ERR_UNSUPPORTED;
         if (trace_rule) {
             r = run_mixed_trace(h, scheme, tol, max_iter, S, &h->cur, &iters);
-        } else if (h->opt.block_sparse && pmm_order(scheme) == 3) {
+        } else if (h->opt.block_sparse && (pmm_order(scheme) == 3 || is_asymmetric(scheme))) {
             r = PURIFY_ERR_UNSUPPORTED;
-        } else if (pmm_order(scheme) == 3) {
-            r = run_mixed_p33(h, scheme, mu, S, &h->cur, red);
+        } else if (pmm_order(scheme) == 3 || is_asymmetric(scheme)) {
+            r = run_mixed_poly(h, scheme, mu, S, &h->cur, red);
         } else if (h->opt.block_sparse) {
             r = run_block_sparse(h, scheme, S, &h->cur, red);
             if (r == PURIFY_OK && h->mixed && !h->mixed->nnzb_history.empty())
@@ -948,7 +1049,7 @@ const char* purify_strerror(int code) {
 int purify_schedule(int scheme, double lmin, double lmax, double mu, double homo, double lumo,
                     double tol, int max_iter, double* alpha, int* branch, double* beta,
                     double* beta_bar, int* iterations) {
-    if (scheme < PURIFY_FIXED_MU_SF || scheme > PURIFY_FIXED_MU_P33_MONO) return PURIFY_ERR_INVALID_ARG;
+    if (scheme < PURIFY_FIXED_MU_SF || scheme > PURIFY_SCHEME_LAST) return PURIFY_ERR_INVALID_ARG;
     if (max_iter < 0 || !(tol >= 0.0)) return PURIFY_ERR_INVALID_ARG;
     if (!(lmax > lmin) || !(homo < lumo)) return PURIFY_ERR_BOUNDS;
     if (is_fixed_mu(scheme)) {

@@ -262,3 +262,20 @@ def test_p33_fixed_mu_parity(P, scheme, gap):
     assert st["multiplications"] == r.multiplications == 5 * r.iterations
     assert np.max(np.abs(D - Do)) < 1e-10
     assert abs(st["trace"] - h.nocc) < 1e-9
+
+
+@pytest.mark.parametrize("scheme,ij", [("FIXED_MU_P13_SF", (1, 3)), ("FIXED_MU_P31_SF", (3, 1)),
+                                       ("FIXED_MU_P31_MONO", (3, 1))])
+def test_asymmetric_pij_parity(P, scheme, ij):
+    # scaled about the unstable fixed point c != 1/2; mu placed off-centre
+    h = I.dense_hamiltonian(240, 90, 5e-3, config=90)
+    pur = P.Purifier(precision="fp64")
+    pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+    pur.run(scheme, 1e-12, 200)
+    D, st = pur.density(), pur.stats()
+    pur.close()
+    Do, r = O.purify_fixed_mu_pij(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, *ij, tol=1e-12,
+                                  scaled=scheme.endswith("_SF"))
+    assert st["iterations"] == r.iterations and st["multiplications"] == r.multiplications
+    assert np.max(np.abs(D - Do)) < 1e-10
+    assert abs(st["trace"] - h.nocc) < 1e-9

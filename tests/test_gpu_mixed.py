@@ -264,3 +264,17 @@ def test_p33_fixed_mu_on_digit_planes(P, n, gap):
     assert st["iterations"] == r.iterations and st["multiplications"] == 5 * r.iterations
     assert np.max(np.abs(D - Do)) <= 3e-7
     assert abs(st["trace"] - h.nocc) < 1e-6
+
+
+@pytest.mark.parametrize("scheme,ij", [("FIXED_MU_P13_SF", (1, 3)), ("FIXED_MU_P31_SF", (3, 1))])
+def test_asymmetric_pij_on_digit_planes(P, scheme, ij):
+    h = I.dense_hamiltonian(700, 300, 2e-3, config=91)
+    pur = P.Purifier(precision="mixed")
+    pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+    pur.run(scheme, 1e-10, 200)
+    D, st = pur.density(), pur.stats()
+    pur.close()
+    Do, r = O.purify_fixed_mu_pij(h.F, h.lmin, h.lmax, 0.0, h.homo, h.lumo, *ij, tol=1e-10)
+    assert st["iterations"] == r.iterations and st["multiplications"] == r.multiplications
+    assert np.max(np.abs(D - Do)) <= 3e-7
+    assert abs(st["trace"] - h.nocc) < 1e-6

@@ -47,6 +47,14 @@ def test_strerror_names_codes():
 
 
 def _oracle_schedule(scheme, lmin, lmax, mu, homo, lumo, tol, max_iter):
+    if scheme.startswith("FIXED_MU_P13") or scheme.startswith("FIXED_MU_P31"):
+        i, j = (1, 3) if "P13" in scheme else (3, 1)
+        c = O.pij_fixed_point(i, j)
+        gamma = max((mu - lmin) / (1.0 - c), (lmax - mu) / c)
+        b, bb = c - (lumo - mu) / gamma, c + (mu - homo) / gamma
+        _, steps = O.pij_schedule(i, j, b, bb, tol, max_iter, scheme.endswith("_SF"))
+        return (np.array([x[0] for x in steps]), np.zeros(len(steps), int),
+                np.array([x[1] for x in steps]))
     if scheme.startswith("FIXED_MU_P33"):
         g = O.fixed_mu_gamma(lmin, lmax, mu)
         b = O.fixed_mu_beta0(g, mu, homo, lumo)
@@ -68,7 +76,8 @@ CASES = [(-1.0, 1.0, 0.0, -g / 2, g / 2) for g in (1e-1, 1e-2, 1e-3, 1e-4)] + [
     (-3.0, 2.0, -0.4, -0.45, -0.2), (-1.0, 1.0, 0.3, 0.25, 0.31)]
 
 
-@pytest.mark.parametrize("scheme", O.SCHEMES + ("FIXED_MU_P33_SF", "FIXED_MU_P33_MONO"))
+@pytest.mark.parametrize("scheme", O.SCHEMES + ("FIXED_MU_P33_SF", "FIXED_MU_P33_MONO", "FIXED_MU_P13_SF",
+                                         "FIXED_MU_P13_MONO", "FIXED_MU_P31_SF", "FIXED_MU_P31_MONO"))
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("tol", [1e-12, 1e-9, 1e-6])
 def test_schedule_bitwise_equal_to_oracle(scheme, case, tol):
