@@ -54,12 +54,16 @@ def parse():
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-size", type=int, default=256)
-    ap.add_argument("--serve-rates", default="30", help="comma list; empty to skip serving")
+    ap.add_argument("--serve-rates", default="10,100,1000", help="comma list; empty to skip serving")
     ap.add_argument("--serve-requests", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pipelines", type=int, default=2,
-                    help="handles (own stream and host thread each) in the end-to-end measurement")
+                    help="handles (own stream and host thread each) sharing a step's purifications")
     ap.add_argument("--no-lattice", action="store_true", help="skip the L^3 block-sparse workload")
+    ap.add_argument("--bits-floor", type=int, default=0,
+                    help="per-step digit rule: fewest bits of a step's operands (0: library default)")
+    ap.add_argument("--bits-gap", type=int, default=0,
+                    help="per-step digit rule: bits beyond log2(1/mapped gap) (0: library default)")
     ap.add_argument("--lattice-size", type=int, default=32, help="L of the L^3 lattice (multiple of 4)")
     ap.add_argument("--lattice-only", action="store_true",
                     help="run only the lattice workload and print its object (profiling)")
@@ -420,8 +424,9 @@ def main():
     Fh = [F.cpu().pin_memory() for F in Fd]
     Dh = torch.empty((n, n), dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream(dev)
+    rule = {"bits_floor": args.bits_floor, "bits_gap": args.bits_gap}
     pur = P.Purifier(device=local, stream=stream.cuda_stream, precision=args.precision,
-                     time_products=True)
+                     time_products=True, **rule)
 
     acc = {"launches": 0, "prod_s": 0.0, "prod_n": 0, "tensor_flops": 0.0, "useful": 0.0,
            "mults": 0, "digit_max": 0}
@@ -479,74 +484,90 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
+    # Pipelines: `pipelines` handles, each on its own stream and host thread,
+    # share a step's purifications (one purification's host work and copies
+    # overlap another's products).
+    npipe = max(1, args.pipelines)
+    per_step = len(hs) * len(schemes)
+    work = [(i, sc) for i in range(len(hs)) for sc in schemes]
+    pipes = []
+    for p in range(npipe if npipe > 1 else 0):
+        sp = torch.cuda.Stream(dev)
+        pipes.append((sp, P.Purifier(device=local, stream=sp.cuda_stream, precision=args.precision, **rule),
+                      torch.empty((n, n), dtype=torch.float64).pin_memory()))
+
+    def pipe_run(p, k, host, errs, launches):
+        sp, pp, Dp = pipes[p]
+        try:
+            for _ in range(k):
+                for q in range(p, len(work), npipe):
+                    i, sc = work[q]
+                    h = hs[i]
+                    pp.set_hamiltonian(Fh[i] if host else Fd[i], nocc=h.nocc, mu=0.0, lmin=h.lmin,
+                                       lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+                    n_set = pp.stats()["kernel_launches"]
+                    if pp.run(sc, args.tol, 200) != P.OK:
+                        raise RuntimeError(f"{sc} did not converge")
+                    launches[p] += n_set + pp.stats()["kernel_launches"]
+                    if host:
+                        pp.density(Dp)
+        except Exception as e:  # reported after the join
+            errs.append(e)
+
+    def pipelined(k, host, clocks=False):
+        import threading
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        sampler = ClockSampler(local) if clocks else None
+        if sampler:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        errs, launches = [], [0] * npipe
+        ths = [threading.Thread(target=pipe_run, args=(p, k, host, errs, launches)) for p in range(npipe)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        if errs:
+            raise errs[0]
+        ends = []
+        for sp, _, _ in pipes:
+            e = torch.cuda.Event(enable_timing=True)
+            e.record(sp)
+            ends.append(e)
+        torch.cuda.synchronize(dev)
+        ck = sampler.stop() if sampler else None
+        if dist:
+            dist.barrier()
+        return max(e0.elapsed_time(e) for e in ends), ck, sum(launches)
+
     for _ in range(args.warmup):
         step()
-    ms_local, clocks = timed(args.steps, record=True, clocks=True)
-    per_step = len(hs) * len(schemes)
-    value, ms = replica_rate(ms_local, per_step * args.steps, world, max_over_ranks)
-    # end to end: host F in, host D out, copies inside the timed region; one
-    # handle in order, then `pipelines` handles each on its own stream and
-    # host thread (a purification's copies and host work overlap another's
-    # products)
+    # one handle in order: the roofline, per-product statistics and launches
+    ms1_local, clocks = timed(args.steps, record=True, clocks=npipe == 1)
+    value1, ms1 = replica_rate(ms1_local, per_step * args.steps, world, max_over_ranks)
+    launches_timed = acc["launches"]
+    if npipe > 1:
+        for _ in range(max(1, args.warmup // 2)):
+            pipelined(1, host=False)
+        ms_local, clocks, launches_timed = pipelined(args.steps, host=False, clocks=True)
+        value, ms = replica_rate(ms_local, per_step * args.steps, world, max_over_ranks)
+    else:
+        value, ms = value1, ms1
+    # end to end: host F in, host D out, copies inside the timed region
     step(host=True)
     k_e2e = max(1, args.steps // 2)
     ms_e2e_local, _ = timed(k_e2e, host=True)
     value_e2e_serial, _ = replica_rate(ms_e2e_local, per_step * k_e2e, world, max_over_ranks)
-    npipe = max(1, args.pipelines)
     value_e2e = value_e2e_serial
     if npipe > 1:
-        pipes = []
-        for p in range(npipe):
-            sp = torch.cuda.Stream(dev)
-            pipes.append((sp, P.Purifier(device=local, stream=sp.cuda_stream, precision=args.precision),
-                          torch.empty((n, n), dtype=torch.float64).pin_memory()))
-        work = [(i, sc) for i in range(len(hs)) for sc in schemes]
-
-        def pipe_run(p, k, errs):
-            sp, pp, Dp = pipes[p]
-            try:
-                for _ in range(k):
-                    for q in range(p, len(work), npipe):
-                        i, sc = work[q]
-                        h = hs[i]
-                        pp.set_hamiltonian(Fh[i], nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax,
-                                           homo=h.homo, lumo=h.lumo)
-                        if pp.run(sc, args.tol, 200) != P.OK:
-                            raise RuntimeError(f"{sc} did not converge")
-                        pp.density(Dp)
-            except Exception as e:  # reported after the join
-                errs.append(e)
-
-        def pipelined(k):
-            import threading
-            if dist:
-                dist.barrier()
-            torch.cuda.synchronize(dev)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            errs = []
-            ths = [threading.Thread(target=pipe_run, args=(p, k, errs)) for p in range(npipe)]
-            for t in ths:
-                t.start()
-            for t in ths:
-                t.join()
-            if errs:
-                raise errs[0]
-            ends = []
-            for sp, _, _ in pipes:
-                e = torch.cuda.Event(enable_timing=True)
-                e.record(sp)
-                ends.append(e)
-            torch.cuda.synchronize(dev)
-            if dist:
-                dist.barrier()
-            return max(e0.elapsed_time(e) for e in ends)
-
-        pipelined(1)
-        ms_pipe_local = pipelined(k_e2e)
+        pipelined(1, host=True)
+        ms_pipe_local, _, _ = pipelined(k_e2e, host=True)
         value_e2e, _ = replica_rate(ms_pipe_local, per_step * k_e2e, world, max_over_ranks)
-        for _, pp, _ in pipes:
-            pp.close()
+    for _, pp, _ in pipes:
+        pp.close()
 
     pk, pk_kind = peaks()
     steps_launched = args.steps
@@ -576,8 +597,12 @@ def main():
                 "pipelines": npipe, "serial_value": value_e2e_serial,
                 "note": "pinned host F in and D out through purify_set_hamiltonian / "
                         "purify_get_density; `pipelines` handles, each on its own stream and "
-                        "host thread, share the step's purifications"},
-        "gpu_launches": acc["launches"],
+                        "host thread, share the step's purifications (as for `value`)"},
+        "gpu_launches": launches_timed,
+        "pipelines": npipe,
+        "single_handle": {"value": value1, "ms_per_step": ms1 / args.steps,
+                          "note": "one handle, purifications in order; the roofline, per-product "
+                                  "statistics and digit counts come from this run"},
         "roofline": roof,
         "multiplications_per_step": acc["mults"] / steps_launched,
         "useful_tflops": acc["useful"] / (ms * 1e-3) / 1e12,
@@ -585,6 +610,7 @@ def main():
     if args.precision == "mixed":
         line["tensor_pipe_frac_of_step"] = acc["tensor_flops"] / (ms * 1e-3) / 1e12 / pk["bf16_tflops"]
         line["digit_max"] = acc["digit_max"]
+        line["digit_rule"] = {"bits_floor": args.bits_floor or 30, "bits_gap": args.bits_gap or 26}
     # max error against the plain float64 GPU recursion, and its throughput
     if not args.no_fp64_check and args.precision == "mixed":
         ref = P.Purifier(device=local, stream=stream.cuda_stream, precision="fp64")

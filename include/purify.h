@@ -121,7 +121,13 @@ typedef struct purify_options {
                             run, which set the final idempotency (0 = none, default;
                             at most 2); stats.trace and stats.idem_err_fro then
                             describe the last of them                              */
-    int reserved[7];
+    int bits_floor;      /* MIXED, per-step digit count (digits = 0): the fewest bits a
+                            step's operands carry (0 = 30, else 16..43)              */
+    int bits_gap;        /* MIXED, per-step digit count: bits beyond log2(1 / mapped
+                            gap) that a step's operands carry (0 = 26, else 16..43);
+                            a step takes the fewest digits (3..6) whose bits cover
+                            max(bits_floor, bits_gap + log2(1 / gap))              */
+    int reserved[5];
     double trunc_tau;    /* block_sparse: per-step truncation budget: blocks of
                             smallest Frobenius norm are dropped while the dropped
                             mass (off-diagonal blocks twice) stays <= tau^2       */

@@ -53,7 +53,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("branch_rule", C.c_int), ("lanczos_steps", C.c_int),
                 ("refine_squares", C.c_int), ("digits", C.c_int), ("time_products", C.c_int),
                 ("block_sparse", C.c_int), ("split_k", C.c_int), ("refine_fp64", C.c_int),
-                ("reserved", C.c_int * 7), ("trunc_tau", C.c_double), ("trunc_budget", C.c_double)]
+                ("bits_floor", C.c_int), ("bits_gap", C.c_int), ("reserved", C.c_int * 5),
+                ("trunc_tau", C.c_double), ("trunc_budget", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -190,7 +191,7 @@ class Purifier:
                  branch_rule: str = "beta", lanczos_steps: int = 32, refine_squares: int = 0,
                  digits: int = 0, time_products: bool = False, block_sparse: bool = False,
                  trunc_tau: float = 1e-6, split_k: bool = True, refine_fp64: int = 0,
-                 trunc_budget: float = 0.0):
+                 trunc_budget: float = 0.0, bits_floor: int = 0, bits_gap: int = 0):
         lib = load()
         self._lib = lib
         self.options = Options()
@@ -206,6 +207,8 @@ class Purifier:
         self.options.refine_fp64 = int(refine_fp64)
         self.options.trunc_tau = float(trunc_tau)
         self.options.trunc_budget = float(trunc_budget)
+        self.options.bits_floor = int(bits_floor)
+        self.options.bits_gap = int(bits_gap)
         h = C.c_void_p()
         _check(lib.purify_create(C.byref(h), device, _caller_stream(stream), C.byref(self.options)),
                "purify_create")

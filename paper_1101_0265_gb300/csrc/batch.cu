@@ -22,7 +22,7 @@
 using namespace purify;
 
 namespace purify {
-int digits_for_gap(double g, int fixed, int rbits);
+int digits_for_gap(double g, const purify_options& o, int rbits);
 int build_schedule_public(int scheme, double lmin, double lmax, double mu, double homo, double lumo,
                           double tol, int max_iter, Schedule& S);
 }  // namespace purify
@@ -121,7 +121,7 @@ void plan_steps(purify_batch* B, Instance& in) {
     for (int i = 0; i < m; ++i) {
         const double b = i ? in.S.beta[i - 1] : in.S.beta0;
         const double bb = i ? in.S.betabar[i - 1] : in.S.betabar0;
-        sd[i] = digits_for_gap(bb - b, B->opt.digits, in.rbits);
+        sd[i] = digits_for_gap(bb - b, B->opt, in.rbits);
     }
     sd[m] = sd[m ? m - 1 : 0];
     in.digit_max = 0;
@@ -323,6 +323,8 @@ int purify_batch_create(purify_batch_t* out, int device, void* cuda_stream, cons
     purify_options_default(&o);
     if (opt) o = *opt;
     if (o.digits != 0 && (o.digits < 2 || o.digits > kMaxDigitPlanes)) return PURIFY_ERR_INVALID_ARG;
+    if (o.bits_floor != 0 && (o.bits_floor < 16 || o.bits_floor > 43)) return PURIFY_ERR_INVALID_ARG;
+    if (o.bits_gap != 0 && (o.bits_gap < 16 || o.bits_gap > 43)) return PURIFY_ERR_INVALID_ARG;
     int ndev = 0;
     PURIFY_CUDA_TRY(cudaGetDeviceCount(&ndev));
     if (device < 0 || device >= ndev) return PURIFY_ERR_INVALID_ARG;
@@ -427,7 +429,7 @@ int purify_batch_add(purify_batch_t B, const double* F, int64_t n, int64_t ld, i
         for (int i = 0; i < m; ++i) {
             const double bb0 = i ? in->S.betabar[i - 1] : in->S.betabar0;
             const double b0 = i ? in->S.beta[i - 1] : in->S.beta0;
-            smax = std::max(smax, digits_for_gap(bb0 - b0, B->opt.digits, in->rbits));
+            smax = std::max(smax, digits_for_gap(bb0 - b0, B->opt, in->rbits));
         }
     }
     const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)smax * in->n_pad * in->n_pad;

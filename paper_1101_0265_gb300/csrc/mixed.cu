@@ -65,11 +65,14 @@ int ensure_mixed(purify_ctx* h, int n_pad) {
 }
 
 // Digits for a step whose mapped gap (distance between the images of the
-// gap edges) is g.
-int digits_for_gap(double g, int fixed, int rbits) {
-    if (fixed > 0) return fixed;
+// gap edges) is g: options.digits when fixed, else the fewest digits whose
+// bits cover max(bits_floor, bits_gap + log2(1 / g)).
+int digits_for_gap(double g, const purify_options& o, int rbits) {
+    if (o.digits > 0) return o.digits;
     if (!(g > 0.0)) return kMaxDigitPlanes;
-    const double need = std::max(30.0, 26.0 + std::log2(1.0 / g));
+    const double floor_bits = o.bits_floor > 0 ? o.bits_floor : kBitsFloor;
+    const double gap_bits = o.bits_gap > 0 ? o.bits_gap : kBitsGap;
+    const double need = std::max(floor_bits, gap_bits + std::log2(1.0 / g));
     for (int s = 3; s < kMaxDigitPlanes; ++s)
         if (digit_bits(s, rbits) >= need) return s;
     return kMaxDigitPlanes;
@@ -120,7 +123,7 @@ int run_mixed_trace(purify_ctx* h, int scheme, double tol, int max_iter, Schedul
     const double c0 = lmax / (lmax - lmin), c1 = -1.0 / (lmax - lmin);
     double b = S.beta0, bb = S.betabar0;
     auto digits = [&](double beta, double betabar) {
-        return have_gap ? digits_for_gap(betabar - beta, fixed, rb) : (fixed > 0 ? fixed : kMaxDigitPlanes);
+        return have_gap ? digits_for_gap(betabar - beta, h->opt, rb) : (fixed > 0 ? fixed : kMaxDigitPlanes);
     };
     S.alpha.clear();
     S.branch.clear();
@@ -304,7 +307,7 @@ int run_mixed_poly(purify_ctx* h, int scheme, double mu, const Schedule& S, int*
     for (int i = 0; i < m; ++i) {
         const double b = i ? S.beta[i - 1] : S.beta0;
         const double bb = i ? S.betabar[i - 1] : S.betabar0;
-        sd[i] = std::min(kMaxDigitPlanes, digits_for_gap(bb - b, fixed, rb) + (fixed > 0 ? 0 : 1));
+        sd[i] = std::min(kMaxDigitPlanes, digits_for_gap(bb - b, h->opt, rb) + (fixed > 0 ? 0 : 1));
     }
     sd[m] = sd[m ? m - 1 : 0];
     int dmax = 0;
@@ -400,7 +403,7 @@ int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
     for (int i = 0; i < m; ++i) {
         const double b = i ? S.beta[i - 1] : S.beta0;
         const double bb = i ? S.betabar[i - 1] : S.betabar0;
-        sd[i] = digits_for_gap(bb - b, fixed, rb);
+        sd[i] = digits_for_gap(bb - b, h->opt, rb);
     }
     for (int i = m; i <= m + R; ++i) sd[i] = fixed > 0 ? fixed : kMaxDigitPlanes;
     int dmax = 0;

@@ -36,7 +36,11 @@ struct MixedState {
 
 // Allocate (or grow) the handle's mixed-path buffers for a padded size.
 int ensure_mixed(purify_ctx* h, int n_pad);
-int digits_for_gap(double g, int fixed, int rbits);
+// Default per-step digit rule: a step's operands carry at least kBitsFloor
+// bits and kBitsGap bits beyond log2(1 / mapped gap).
+constexpr double kBitsFloor = 30.0;
+constexpr double kBitsGap = 26.0;
+int digits_for_gap(double g, const purify_options& o, int rbits);
 // F[key[k]] = v[k] for distinct keys row * n + col (device arrays).
 int launch_scatter_coo(const int64_t* key, const double* v, int64_t nnz, double* F, cudaStream_t s);
 // Block-sparse Algorithm 2 run (sparse.cu).

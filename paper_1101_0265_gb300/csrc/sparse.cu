@@ -242,12 +242,11 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     const int nb = n_pad / 32, T = n_pad / 128;
     const int rb = remainder_bits(n_pad);
     const int m = (int)S.alpha.size();
-    const int fixed = h->opt.digits;
     std::vector<int> sd(m + 1);
     for (int i = 0; i < m; ++i) {
         const double b = i ? S.beta[i - 1] : S.beta0;
         const double bb = i ? S.betabar[i - 1] : S.betabar0;
-        sd[i] = digits_for_gap(bb - b, fixed, rb);
+        sd[i] = digits_for_gap(bb - b, h->opt, rb);
     }
     sd[m] = sd[m ? m - 1 : 0];
     int dmax = 0;
