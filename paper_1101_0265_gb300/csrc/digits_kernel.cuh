@@ -305,7 +305,14 @@ struct DigitLaunch {
     int split_ways;                  // parts per split tile (1: none)
     float* partial;                  // [slot][part][region 8][acc 4][16-col group 4][row 32][16]
     int* split_cnt;                  // [slot][region 8], zero at launch
+    int* claim;                      // split launches: counter of claimed split items, zero at launch
 };
+
+// Items of a split launch's last wave are claimed at run time (an atomic
+// counter), at most MAX_CLAIMS per CTA: a CTA whose whole tiles ran slow
+// leaves the parts to CTAs that are free.  The producer claims and hands each
+// claimed item to the MMA and epilogue warps through shared memory.
+constexpr int MAX_CLAIMS = 8;
 
 constexpr int REGION_FLOATS = NUM_ACC * EPI_COLS * 32;  // one epilogue warp's accumulators
 
@@ -404,14 +411,16 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
     constexpr int stage_bytes = 2 * S * PLANE_BYTES;
     const int stages = L.stages;
     uint64_t* bars = (uint64_t*)(base + (size_t)stages * stage_bytes);
-    // bars: full[stages] | empty[stages] | tmem_full | tmem_empty | drain
+    // bars: full[stages] | empty[stages] | tmem_full | tmem_empty | drain | claim[MAX_CLAIMS]
     uint64_t* full_bar = bars;
     uint64_t* empty_bar = bars + stages;
     uint64_t* tmem_full = bars + 2 * stages;
     uint64_t* tmem_empty = tmem_full + 1;
     uint64_t* drain = tmem_full + 2;
-    uint32_t* tmem_slot = (uint32_t*)(drain + 1);
+    uint64_t* claim_bar = drain + 1;  // [MAX_CLAIMS], one phase each
+    uint32_t* tmem_slot = (uint32_t*)(claim_bar + MAX_CLAIMS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+    volatile int* claimed = abort_flag + 1;  // [MAX_CLAIMS] item (-1: none left)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int num_items = L.num_items;
@@ -421,6 +430,7 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
         mbar_init(smem_u32(tmem_full), 1);
         mbar_init(smem_u32(tmem_empty), EPI_WARPS);
         mbar_init(smem_u32(drain), 1);
+        for (int i = 0; i < MAX_CLAIMS; ++i) mbar_init(smem_u32(&claim_bar[i]), 1);
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -428,13 +438,48 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+
+    // Work items of this CTA, the same sequence in every role: whole waves
+    // round-robin (blockIdx.x + k gridDim.x), then, in a split launch, parts
+    // claimed by the producer (-1 ends the sequence).
+    const bool claiming = L.claim != nullptr;
+    const int static_end = claiming ? L.split_begin : num_items;
+    int n_claims = 0;  // producer: claims published; consumers: claims taken
+    auto producer_claim = [&]() -> int {
+        if (n_claims >= MAX_CLAIMS) return -1;
+        int t = L.split_begin + atomicAdd(L.claim, 1);
+        if (t >= num_items) t = -1;
+        claimed[n_claims] = t;
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&claim_bar[n_claims])) : "memory");
+        ++n_claims;
+        return t;
+    };
+    auto consumer_take = [&]() -> int {  // one thread per role
+        if (n_claims >= MAX_CLAIMS || *abort_flag) return -1;
+        if (!mbar_wait_for(smem_u32(&claim_bar[n_claims]), 0)) {
+            atomicExch(L.err, 5);
+            *abort_flag = 1;
+            return -1;
+        }
+        return claimed[n_claims++];
+    };
+    auto first_item = [&](bool producer) -> int {
+        if ((int)blockIdx.x < static_end) return blockIdx.x;
+        if (!claiming) return -1;
+        return producer ? producer_claim() : consumer_take();
+    };
+    auto next_item = [&](int t, bool producer) -> int {
+        if (t + (int)gridDim.x < static_end) return t + gridDim.x;
+        if (!claiming) return -1;
+        return producer ? producer_claim() : consumer_take();
+    };
     const uint32_t tmem = *tmem_slot;
 
     if (warp == 0) {
         if (lane == 0) {
             // producer: one continuous ring of k-chunks over all work items
             int it = 0;
-            for (int t = blockIdx.x; t < num_items && !*abort_flag; t += gridDim.x) {
+            for (int t = first_item(true); t >= 0 && !*abort_flag; t = next_item(t, true)) {
                 int g, ti, tj, slot, part;
                 item_of(L, t, g, ti, tj, slot, part);
                 const DigitGemmParams& Pg = params_of(L, g);
@@ -474,6 +519,15 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     tma_load_3d(smem_u32(sa + s * PLANE_BYTES), mB, fb, kc * KC, tj * TILE, 0);
                 }
             }
+            // unclaimed slots end the other roles' sequences (also after an abort)
+            if (claiming) {
+                while (n_claims < MAX_CLAIMS) {
+                    claimed[n_claims] = -1;
+                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&claim_bar[n_claims]))
+                                 : "memory");
+                    ++n_claims;
+                }
+            }
             // wait (bounded) for the copies still in flight
             for (int k = (it > stages ? it - stages : 0); k < it; ++k)
                 mbar_wait_for(smem_u32(&full_bar[k % stages]), (uint32_t)((k / stages) & 1));
@@ -485,7 +539,7 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             const uint64_t desc_base = smem_desc<KC>(smem_u32(base));
             int it = 0, lt = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < num_items && ok; t += gridDim.x, ++lt) {
+            for (int t = first_item(false); t >= 0 && ok; t = next_item(t, false), ++lt) {
                 int g, ti, tj, slot, part;
                 item_of(L, t, g, ti, tj, slot, part);
                 const DigitGemmParams& Pg = params_of(L, g);
@@ -547,7 +601,13 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
         float2* scr = L.scratch + (size_t)blockIdx.x * TILE * TILE + (size_t)(warp - 2) * EPI_COLS * 32 + lane * 8;
         int lt = 0;
         const int region = warp - 2;
-        for (int t = blockIdx.x; t < num_items; t += gridDim.x, ++lt) {
+        // lane 0 follows the item sequence for the warp (tcgen05.ld is warp-collective)
+        auto warp_item = [&](int t, bool first) -> int {
+            int v = 0;
+            if (lane == 0) v = first ? first_item(false) : next_item(t, false);
+            return __shfl_sync(0xffffffffu, v, 0);
+        };
+        for (int t = warp_item(0, true); t >= 0; t = warp_item(t, false), ++lt) {
             int g, ti, tj, slot, part;
             item_of(L, t, g, ti, tj, slot, part);
             const DigitGemmParams& P = params_of(L, g);
@@ -598,6 +658,24 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     continue;
                 }
             }
+            // a tile split in two: the other part's accumulators for the next
+            // 8-column group are loaded while this group is summed (the loads
+            // come from L2 and their latency would otherwise add up over the
+            // groups); fp32 addition commutes, so acc + other is the part-order sum
+            const bool two = slot >= 0 && L.split_ways == 2;
+            const float4* oth = nullptr;
+            float4 nx[NUM_ACC][2];
+            if (two) {
+                oth = (const float4*)(L.partial +
+                      ((size_t)(slot * 2 + (1 - part)) * EPI_WARPS + region) * REGION_FLOATS) + lane * 2;
+#pragma unroll
+                for (int a = 0; a < NUM_ACC; ++a) {
+                    if (a < nacc) {
+                        nx[a][0] = __ldcg(oth + (size_t)a * (EPI_COLS / 8) * 64);
+                        nx[a][1] = __ldcg(oth + (size_t)a * (EPI_COLS / 8) * 64 + 1);
+                    }
+                }
+            }
 #pragma unroll 1
             for (int c0 = col0, cg = 0; c0 < col0 + EPI_COLS; c0 += 8, ++cg) {
                 float acc[NUM_ACC][8];
@@ -610,7 +688,21 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                         for (int c = 0; c < 8; ++c) acc[a][c] = 0.f;
                     }
                 }
-                if (slot >= 0) {
+                if (two) {
+#pragma unroll
+                    for (int a = 0; a < NUM_ACC; ++a) {
+                        if (a < nacc) {
+                            acc[a][0] += nx[a][0].x; acc[a][1] += nx[a][0].y;
+                            acc[a][2] += nx[a][0].z; acc[a][3] += nx[a][0].w;
+                            acc[a][4] += nx[a][1].x; acc[a][5] += nx[a][1].y;
+                            acc[a][6] += nx[a][1].z; acc[a][7] += nx[a][1].w;
+                            if (cg + 1 < EPI_COLS / 8) {
+                                nx[a][0] = __ldcg(oth + (size_t)(a * (EPI_COLS / 8) + cg + 1) * 64);
+                                nx[a][1] = __ldcg(oth + (size_t)(a * (EPI_COLS / 8) + cg + 1) * 64 + 1);
+                            }
+                        }
+                    }
+                } else if (slot >= 0) {
                     // the sum of all parts, in part order
 #pragma unroll
                     for (int a = 0; a < NUM_ACC; ++a) {

@@ -292,9 +292,14 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
         digit_split_plan(tiles, st.max_ctas, st.n_pad / kc, &L.split_begin, &L.split_ways);
     L.num_items = L.split_begin + (tiles - L.split_begin) * L.split_ways;
     if (L.split_ways > 1) {
+        // per-region arrival counters of the split tiles, then the claim
+        // counter (tiles - split_begin < max_ctas, so both fit in
+        // digit_split_counters(max_ctas))
+        const size_t counters = (size_t)kEpiWarps * (size_t)(tiles - L.split_begin);
         L.partial = st.partial;
         L.split_cnt = st.split_cnt;
-        PURIFY_CUDA_TRY(cudaMemsetAsync(st.split_cnt, 0, sizeof(int) * kEpiWarps * (size_t)(tiles - L.split_begin), stream));
+        L.claim = st.split_cnt + counters;
+        PURIFY_CUDA_TRY(cudaMemsetAsync(st.split_cnt, 0, sizeof(int) * (counters + 1), stream));
     }
     const int grid = L.num_items < st.max_ctas ? L.num_items : st.max_ctas;
     return launch_kernel(L, st.s_in, kc, grid, stream);

@@ -39,6 +39,26 @@ def test_library_exports_every_header_symbol():
     assert set(P.EXPORTED) == set(syms)
 
 
+@pytest.mark.parametrize("field,value", [
+    ("digits", 7), ("digits", 1), ("split_k", 2), ("refine_fp64", 3), ("bits_floor", 15),
+    ("bits_floor", 44), ("bits_gap", 15), ("bits_gap", 44), ("trunc_tau", -1.0),
+    ("trunc_budget", float("nan")), ("precision", 5), ("lanczos_steps", -1)])
+def test_invalid_options_rejected_before_the_device(field, value):
+    # option checks come first: no device is touched, so this runs without a GPU
+    import ctypes as C
+    _ensure_built()
+    lib = P.load()
+    o = P._lib.Options()
+    lib.purify_options_default(C.byref(o))
+    setattr(o, field, value)
+    h = C.c_void_p()
+    assert lib.purify_create(C.byref(h), 0, None, C.byref(o)) == P.ERR_INVALID_ARG
+    assert not h.value
+    if field in ("digits", "bits_floor", "bits_gap"):
+        b = C.c_void_p()
+        assert lib.purify_batch_create(C.byref(b), 0, None, C.byref(o)) == P.ERR_INVALID_ARG
+
+
 def test_strerror_names_codes():
     _ensure_built()
     for code in (P.OK, P.ERR_INVALID_ARG, P.ERR_BOUNDS, P.ERR_NOT_CONVERGED, P.ERR_OOM,
