@@ -76,3 +76,41 @@ def test_host_input_is_read_before_the_call_returns(P):
     B.run()
     assert np.max(np.abs(B.density(i) - Dx)) < 3e-7
     B.close()
+
+
+@pytest.mark.parametrize("n,scheme", [(1000, "TC_SF"), (2200, "FIXED_MU_SF"), (4096, "TC_SF")])
+def test_concurrent_handles_equal_solo_runs(P, n, scheme):
+    # Two handles on their own streams, driven from two host threads, run
+    # split products at the same time, so a launch's CTAs need not all be
+    # resident and the split parts go to whichever CTAs claim them: the
+    # densities must still equal solo runs bit for bit (split parts are added
+    # in part order, whoever computes them).
+    import threading
+    hs = [I.dense_hamiltonian(n, n // 2, 0.01, config=72, instance=k) for k in range(2)]
+
+    def run(h, stream=None):
+        pur = P.Purifier(precision="mixed", stream=stream)
+        pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+        assert pur.run(scheme, 1e-10, 200) == P.OK
+        D = pur.density()
+        pur.close()
+        return D
+
+    solo = [run(h) for h in hs]
+    streams = [torch.cuda.Stream() for _ in hs]
+    got = [None, None]
+    errs = []
+
+    def worker(k):
+        try:
+            for _ in range(3):
+                got[k] = run(hs[k], streams[k].cuda_stream)
+                assert np.array_equal(got[k], solo[k])
+        except Exception as e:  # reported after the join
+            errs.append(e)
+    ths = [threading.Thread(target=worker, args=(k,)) for k in range(2)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    assert not errs, errs
