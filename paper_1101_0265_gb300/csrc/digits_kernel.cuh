@@ -62,6 +62,7 @@ constexpr int EPI_COLS = TILE * 4 / EPI_WARPS;  // columns of one epilogue warp'
 // takes every fourth warp
 constexpr int MAX_REGS = (16384 / (32 * ((NTHREADS / 32 + 3) / 4))) / 8 * 8;
 constexpr int EW = 8;            // epilogue columns per pass (a multiple of 8)
+constexpr int BAR_AREA = 512;    // bytes of barriers and flags after the operand stages
 constexpr long long WAIT_CYCLES = 1ll << 31;  // one wait gives up after ~1 s at 2 GHz
 
 // ---- PTX wrappers ------------------------------------------------------------
@@ -102,6 +103,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         "l"((uint64_t)map), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
         : "memory");
 }
+
+// 16-byte asynchronous copy global -> shared (L2 only), its group commit and wait.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
@@ -421,6 +431,8 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
     uint32_t* tmem_slot = (uint32_t*)(claim_bar + MAX_CLAIMS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     volatile int* claimed = abort_flag + 1;  // [MAX_CLAIMS] item (-1: none left)
+    // phase 2's E digits, fetched one pass ahead: [epilogue warp][plane][lane] x EW / 8 uint4
+    uint4* e_stage = (uint4*)((uint8_t*)bars + BAR_AREA);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int num_items = L.num_items;
@@ -763,6 +775,27 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             double s_tr = 0.0;  // the trace decides the occupation check: float64
             float s_idem = 0.f, s_fro = 0.f;
             float bn2_0 = 0.f, bn2_1 = 0.f;  // this row's share of two 32 x 32 output blocks
+            // E for a pass is copied to shared memory while the previous pass
+            // computes (each lane copies and reads only its own 16-byte pieces)
+            uint4* const e_mine = e_stage + (size_t)region * s * 32 * (EW / 8) + lane * (EW / 8);
+            const __nv_bfloat16* const e_row = Ain + (size_t)i * n_pad + tj * TILE;
+            auto fetch_E = [&](int c_first) {
+#pragma unroll
+                for (int p = 0; p < s; ++p)
+#pragma unroll
+                    for (int q = 0; q < EW / 8; ++q)
+                        cp_async16(smem_u32(e_mine + p * 32 * (EW / 8) + q), e_row + p * plane + c_first + 8 * q);
+                cp_async_commit();
+            };
+            if (use_E) fetch_E(col0);
+            // the double-float P of the next pass is loaded while this pass
+            // re-splits and stores
+            float4 pv_next[EW / 2];
+            {
+                const float4* src = (const float4*)scr;
+#pragma unroll
+                for (int c = 0; c < EW / 2; ++c) pv_next[c] = src[(c >> 2) * 128 + (c & 3)];
+            }
             // EW columns per pass: a short loop body keeps the epilogue's
             // instructions resident while the other warps run
 #pragma unroll 1
@@ -771,20 +804,19 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 df Ov[EW];
                 {
                     float4 pv[EW / 2];
-                    const float4* src = (const float4*)(scr + ((c0 - col0) >> 3) * 256);
 #pragma unroll
-                    for (int c = 0; c < EW / 2; ++c) pv[c] = src[(c >> 2) * 128 + (c & 3)];
+                    for (int c = 0; c < EW / 2; ++c) pv[c] = pv_next[c];
                     // E = A at (i, jb .. jb + EW - 1): exact two-float sum of its digits
                     float eh[EW], el[EW];
 #pragma unroll
                     for (int c = 0; c < EW; ++c) eh[c] = el[c] = 0.f;
                     if (use_E) {
+                        cp_async_wait_all();
 #pragma unroll
                         for (int p = 0; p < s; ++p) {
-                            const __nv_bfloat16* srcd = Ain + p * plane + (size_t)i * n_pad + jb;
                             uint4 u[EW / 8];
 #pragma unroll
-                            for (int q = 0; q < EW / 8; ++q) u[q] = ((const uint4*)srcd)[q];
+                            for (int q = 0; q < EW / 8; ++q) u[q] = e_mine[p * 32 * (EW / 8) + q];
                             const __nv_bfloat16* hv = (const __nv_bfloat16*)u;
                             if (p < 3) {
 #pragma unroll
@@ -794,6 +826,8 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                                 for (int c = 0; c < EW; ++c) el[c] += bf16_to_float(hv[c]);
                             }
                         }
+                        // this pass's pieces are in registers: fetch the next pass's
+                        if (c0 + EW < col0 + EPI_COLS) fetch_E(c0 + EW);
                     }
                     float bsum = 0.f;
 #pragma unroll
@@ -829,6 +863,11 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                         bn2_0 += bsum;
                     else
                         bn2_1 += bsum;
+                }
+                if (c0 + EW < col0 + EPI_COLS) {
+                    const float4* src = (const float4*)(scr + ((c0 + EW - col0) >> 3) * 256);
+#pragma unroll
+                    for (int c = 0; c < EW / 2; ++c) pv_next[c] = src[(c >> 2) * 128 + (c & 3)];
                 }
                 // float64 output (n x n): row segment and its mirror column
                 if (out64 && i < n) {

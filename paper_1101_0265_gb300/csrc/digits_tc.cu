@@ -176,7 +176,10 @@ int digit_stages(int s, int kc) {
 }
 
 size_t digit_smem_bytes(int s, int kc) {
-    return 1024 + (size_t)digit_stages(s, kc) * 2 * s * TILE * kc * 2 + 512;
+    // alignment slack, operand stages, barriers and flags, then phase 2's E
+    // staging (one EW-column piece per epilogue warp, digit plane and lane)
+    return 1024 + (size_t)digit_stages(s, kc) * 2 * s * TILE * kc * 2 + BAR_AREA +
+           (size_t)kEpiWarps * s * 32 * EW * 2;
 }
 
 KernelFn kernel_for(int kc, int s) {
