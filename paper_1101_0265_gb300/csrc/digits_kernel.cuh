@@ -901,21 +901,25 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                         }
                         plane_scale *= rinv;
                         __nv_bfloat16* dst = outp + p * plane;
-                        if (!diag_tile) {
+                        // the row segment (i, jb ..) and its mirror column; in a
+                        // diagonal tile only j >= i is written here (j < i is
+                        // the mirror of another row's element)
+                        if (!diag_tile || jb >= i) {
                             uint4* row = (uint4*)(dst + (size_t)i * n_pad + jb);
 #pragma unroll
                             for (int q = 0; q < EW / 8; ++q) row[q] = ((const uint4*)dv)[q];
+                        } else if (jb + EW > i) {
+#pragma unroll
+                            for (int c = 0; c < EW; ++c)
+                                if (jb + c >= i) dst[(size_t)i * n_pad + jb + c] = dv[c];
+                        }
+                        if (!diag_tile) {
 #pragma unroll
                             for (int c = 0; c < EW; ++c) dst[(size_t)(jb + c) * n_pad + i] = dv[c];
-                        } else {
+                        } else if (jb + EW > i + 1) {
 #pragma unroll
-                            for (int c = 0; c < EW; ++c) {
-                                const int j = jb + c;
-                                if (i <= j) {
-                                    dst[(size_t)i * n_pad + j] = dv[c];
-                                    if (i != j) dst[(size_t)j * n_pad + i] = dv[c];
-                                }
-                            }
+                            for (int c = 0; c < EW; ++c)
+                                if (jb + c > i) dst[(size_t)(jb + c) * n_pad + i] = dv[c];
                         }
                     }
                 }
