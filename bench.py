@@ -34,9 +34,9 @@ SCHEMES = ("TC_SF", "FIXED_MU_SF")
 FP64_PER_BF16 = 1.25 / 2250.0   # nominal dense fp64 : bf16 ratio of GB300
 # DRAM bytes (read + write) of one digit-plane product launch, from one ncu
 # capture of digit_gemm_kernel<32, 5> at n = 4096 (bytes per launch).
-TRAFFIC_DIGIT_GEMM = 800.4e6
+TRAFFIC_DIGIT_GEMM = 776.5e6
 TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of digit_gemm_kernel<32,5>, n=4096, one launch "
-                  "(547.8 MB read + 252.6 MB written)")
+                  "(525.6 MB read + 250.9 MB written)")
 
 
 def parse():
