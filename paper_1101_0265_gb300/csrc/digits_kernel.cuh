@@ -34,9 +34,14 @@
 //   warp 1  TMEM allocator and MMA issuer (tcgen05.mma kind::f16, bf16 in,
 //           fp32 accumulate, M = N = 128, K = 16)
 //   warps 2.. epilogue (tcgen05.ld; warp w reads TMEM lane quarter w % 4 and
-//           the (w - 2) / 4-th group of EPI_COLS columns)
+//           the (w - 2) / 4-th group of EPI_COLS columns).  Phase 1 drains
+//           the accumulators into a double-float tile in global scratch and
+//           releases TMEM; phase 2 (polynomial, re-split, stores) then
+//           overlaps the next tile's MMAs, with the E digits of the next pass
+//           copied into shared memory while the current pass computes.
 // Tiles are numbered in bands of 12 tile columns so that the CTAs resident
-// at one time share row panels in L2.
+// at one time share row panels in L2.  Whole waves of tiles go round-robin
+// over the CTAs; the parts of a split last wave are claimed at run time.
 // Every wait on an mbarrier is bounded; on time-out the CTA records an error
 // flag, waits (bounded) for its own copies and MMAs, frees its tensor memory
 // and exits.
