@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--pipelines", type=int, default=2,
                     help="handles (own stream and host thread each) sharing a step's purifications")
     ap.add_argument("--no-lattice", action="store_true", help="skip the L^3 block-sparse workload")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="launch products with the fixed shape rule instead of measured shapes")
     ap.add_argument("--bits-floor", type=int, default=0,
                     help="per-step digit rule: fewest bits of a step's operands (0: library default)")
     ap.add_argument("--bits-gap", type=int, default=0,
@@ -424,7 +426,7 @@ def main():
     Fh = [F.cpu().pin_memory() for F in Fd]
     Dh = torch.empty((n, n), dtype=torch.float64).pin_memory()
     stream = torch.cuda.current_stream(dev)
-    rule = {"bits_floor": args.bits_floor, "bits_gap": args.bits_gap}
+    rule = {"bits_floor": args.bits_floor, "bits_gap": args.bits_gap, "autotune": not args.no_autotune}
     pur = P.Purifier(device=local, stream=stream.cuda_stream, precision=args.precision,
                      time_products=True, **rule)
 
@@ -611,6 +613,12 @@ def main():
         line["tensor_pipe_frac_of_step"] = acc["tensor_flops"] / (ms * 1e-3) / 1e12 / pk["bf16_tflops"]
         line["digit_max"] = acc["digit_max"]
         line["digit_rule"] = {"bits_floor": args.bits_floor or 30, "bits_gap": args.bits_gap or 26}
+        shapes = {}
+        for s_ in range(1, 7):
+            t = P.tuned_shape(local, s_, n)
+            if t is not None:
+                shapes[str(s_)] = {"kc": t[0], "split_ways": t[1]}
+        line["launch_shapes"] = shapes if shapes else "fixed rule"
     # max error against the plain float64 GPU recursion, and its throughput
     if not args.no_fp64_check and args.precision == "mixed":
         ref = P.Purifier(device=local, stream=stream.cuda_stream, precision="fp64")

@@ -127,7 +127,16 @@ typedef struct purify_options {
                             gap) that a step's operands carry (0 = 26, else 16..43);
                             a step takes the fewest digits (3..6) whose bits cover
                             max(bits_floor, bits_gap + log2(1 / gap))              */
-    int reserved[5];
+    int autotune;        /* MIXED dense products: 1 = time the candidate launch shapes
+                            (k-chunk width 16 / 32 / 64; the last wave's tiles split
+                            by the rule or whole) at the first product
+                            of each digit count and padded size in this process, and
+                            launch every later product of that kind with the fastest
+                            (0 = the fixed rule, default).  Shapes differ only in the
+                            summation order of the inexact digit levels, so results
+                            stay within the mixed path's tolerance; within a process
+                            one shape per kind is used, so runs are reproducible    */
+    int reserved[4];
     double trunc_tau;    /* block_sparse: per-step truncation budget: blocks of
                             smallest Frobenius norm are dropped while the dropped
                             mass (off-diagonal blocks twice) stays <= tau^2       */
@@ -159,7 +168,8 @@ typedef struct purify_stats_t {
     int kernel_launches;        /* kernels launched by the last set/run call             */
     int product_launches;       /* matrix-product kernels among them (last run)          */
     int nnz_blocks;             /* block_sparse: upper 32 x 32 blocks of the result      */
-    int reserved[4];
+    int digit_kc;               /* MIXED: k-chunk width of the last product launch        */
+    int reserved[3];
     double product_seconds;     /* summed event time of the product launches
                                    (time_products = 1; else NaN)                         */
 } purify_stats_t;
@@ -217,6 +227,13 @@ int purify_set_hamiltonian_coo(purify_t h, int64_t n, int64_t nnz, const int64_t
  * handle's precision; the handle holds no density afterwards.  Returns
  * PURIFY_ERR_NOT_CONVERGED when the sides are not resolved within 200 steps. */
 int purify_estimate_gap(purify_t h, int lanczos_steps, double* homo_est, double* lumo_est);
+
+/* The launch shape that purify_options.autotune measured on `device` for
+ * products of `digits` digit planes at size n (padded to 128): k-chunk width
+ * (*kc) and the last wave's split (*split_ways: 0 = the rule, 1 = whole
+ * tiles).  Host only.  PURIFY_ERR_STATE when nothing was measured
+ * for that kind in this process. */
+int purify_tuned_shape(int device, int digits, int64_t n, int* kc, int* split_ways);
 
 /* Block-sparse runs: the number of upper 32 x 32 blocks kept after the
  * truncation of X_0 and of every step (count <= cap entries written). */

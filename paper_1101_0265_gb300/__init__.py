@@ -9,5 +9,5 @@ from ._lib import (  # noqa: F401
     ERR_OOM, ERR_STATE, ERR_UNSUPPORTED, EXPORTED, LIB_PATH, OK, PRECISIONS, SCHEMES, Purifier,
     PurifyError, k_digit_product_f64, k_gershgorin_f64, k_gershgorin_f64_noalloc,
     GERSHGORIN_NOALLOC_MAX_N, k_lanczos_f64, k_step_f64, k_symm_product_f64, load, schedule,
-    strerror, tridiag_eig,
+    strerror, tridiag_eig, tuned_shape,
 )

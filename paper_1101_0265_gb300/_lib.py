@@ -34,6 +34,7 @@ BRANCH_RULES = {"beta": 0, "trace": 1}
 EXPORTED = (
     "purify_options_default", "purify_create", "purify_destroy", "purify_set_options",
     "purify_set_hamiltonian", "purify_set_hamiltonian_coo", "purify_block_history", "purify_estimate_gap",
+    "purify_tuned_shape",
     "purify_run", "purify_get_density", "purify_stats",
     "purify_density_device_ptr", "purify_strerror", "purify_schedule", "purify_tridiag_eig",
     "purify_k_symm_product_f64", "purify_k_step_f64", "purify_k_gershgorin_f64",
@@ -53,7 +54,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("branch_rule", C.c_int), ("lanczos_steps", C.c_int),
                 ("refine_squares", C.c_int), ("digits", C.c_int), ("time_products", C.c_int),
                 ("block_sparse", C.c_int), ("split_k", C.c_int), ("refine_fp64", C.c_int),
-                ("bits_floor", C.c_int), ("bits_gap", C.c_int), ("reserved", C.c_int * 5),
+                ("bits_floor", C.c_int), ("bits_gap", C.c_int), ("autotune", C.c_int),
+                ("reserved", C.c_int * 4),
                 ("trunc_tau", C.c_double), ("trunc_budget", C.c_double)]
 
 
@@ -65,7 +67,8 @@ class Stats(C.Structure):
                 ("homo", C.c_double), ("lumo", C.c_double), ("mu", C.c_double),
                 ("useful_flops", C.c_double), ("tensor_flops", C.c_double),
                 ("digit_max", C.c_int), ("kernel_launches", C.c_int),
-                ("product_launches", C.c_int), ("nnz_blocks", C.c_int), ("reserved", C.c_int * 4),
+                ("product_launches", C.c_int), ("nnz_blocks", C.c_int), ("digit_kc", C.c_int),
+                ("reserved", C.c_int * 3),
                 ("product_seconds", C.c_double)]
 
     def as_dict(self) -> dict:
@@ -100,6 +103,7 @@ def load(path: str = LIB_PATH):
         "purify_run": (ip, [vp, ip, dbl, ip]),
         "purify_set_hamiltonian_coo": (ip, [vp, i64, i64, vp, vp, vp, i64, dbl, C.POINTER(Bounds)]),
         "purify_block_history": (ip, [vp, C.POINTER(C.c_int), ip, C.POINTER(C.c_int)]),
+        "purify_tuned_shape": (ip, [ip, ip, i64, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "purify_estimate_gap": (ip, [vp, ip, dp, dp]),
         "purify_get_density": (ip, [vp, vp, i64]),
         "purify_stats": (ip, [vp, C.POINTER(Stats)]),
@@ -191,7 +195,8 @@ class Purifier:
                  branch_rule: str = "beta", lanczos_steps: int = 32, refine_squares: int = 0,
                  digits: int = 0, time_products: bool = False, block_sparse: bool = False,
                  trunc_tau: float = 1e-6, split_k: bool = True, refine_fp64: int = 0,
-                 trunc_budget: float = 0.0, bits_floor: int = 0, bits_gap: int = 0):
+                 trunc_budget: float = 0.0, bits_floor: int = 0, bits_gap: int = 0,
+                 autotune: bool = False):
         lib = load()
         self._lib = lib
         self.options = Options()
@@ -209,6 +214,7 @@ class Purifier:
         self.options.trunc_budget = float(trunc_budget)
         self.options.bits_floor = int(bits_floor)
         self.options.bits_gap = int(bits_gap)
+        self.options.autotune = int(autotune)
         h = C.c_void_p()
         _check(lib.purify_create(C.byref(h), device, _caller_stream(stream), C.byref(self.options)),
                "purify_create")
@@ -312,6 +318,18 @@ class Purifier:
 # ---------------------------------------------------------------------------
 # Host-only entry points
 # ---------------------------------------------------------------------------
+
+def tuned_shape(device: int, digits: int, n: int):
+    """The launch shape autotuning measured for products of `digits` digit
+    planes at size n on `device` in this process: (kc, split_ways), or None."""
+    lib = load()
+    kc, ways = C.c_int(0), C.c_int(0)
+    code = lib.purify_tuned_shape(int(device), int(digits), int(n), C.byref(kc), C.byref(ways))
+    if code == ERR_STATE:
+        return None
+    _check(code, "purify_tuned_shape")
+    return kc.value, ways.value
+
 
 def schedule(scheme: str, lmin, lmax, mu, homo, lumo, tol, max_iter=500):
     lib = load()

@@ -153,9 +153,27 @@ df to_df(double x) {
 
 }  // namespace
 
+KernelFn kernel_for(int kc, int s);
+
 // k-chunk width for a digit count: the widest chunk that still leaves at
 // least two pipeline stages, unless overridden (tuning).
 int digit_kc_for(int s, bool sparse) { return sparse ? 32 : digit_kc(s); }
+
+int digit_step_kc(const DigitStep& st) {
+    const bool sparse = st.kc_cnt || st.bnorm2;
+    if (!sparse && (st.kc == 16 || st.kc == 32 || st.kc == 64) && kernel_for(st.kc, st.s_in)) return st.kc;
+    return digit_kc_for(st.s_in, sparse);
+}
+
+int digit_kc_candidates(int s, int* kc) {
+    int n = 0;
+    for (int c : {16, 32, 64}) {
+        // a width whose stage ring holds a single k-chunk cannot overlap its
+        // loads with the MMAs: not a candidate
+        if (kernel_for(c, s) && digit_stages(s, c) >= 2) kc[n++] = c;
+    }
+    return n;
+}
 
 int digit_kc(int s) {
     static const int forced = [] {  // read once (thread-safe initialisation)
@@ -216,7 +234,7 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
         return PURIFY_ERR_INVALID_ARG;
     if (st.n <= 0 || st.n_pad % TILE || st.n > st.n_pad) return PURIFY_ERR_INVALID_ARG;
     if (st.rbits < 4 || st.rbits > 8) return PURIFY_ERR_INVALID_ARG;
-    const int kc = digit_kc_for(st.s_in, st.kc_cnt || st.bnorm2);
+    const int kc = digit_step_kc(st);
     PURIFY_TRY(make_plane_map(ma, st.A, st.n_pad, st.s_in, kc));
     PURIFY_TRY(make_plane_map(mb, st.B, st.n_pad, st.s_in, kc));
     std::memset(p, 0, sizeof(*p));
@@ -284,16 +302,32 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
     L.ngroups = 1;
     const int T = st.n_pad / TILE;
     const int tiles = T * (T + 1) / 2;
-    const int kc = digit_kc_for(st.s_in, st.kc_cnt || st.bnorm2);
+    const int kc = digit_step_kc(st);
     L.stages = digit_stages(st.s_in, kc);
     L.scratch = st.scratch;
     L.err = st.err;
     if (!st.scratch || !st.err) return PURIFY_ERR_INVALID_ARG;
     L.split_begin = tiles;
     L.split_ways = 1;
-    if (st.partial && st.split_cnt && !st.kc_cnt)
+    if (st.partial && st.split_cnt && !st.kc_cnt && st.split_ways != 1) {
         digit_split_plan(tiles, st.max_ctas, st.n_pad / kc, &L.split_begin, &L.split_ways);
+        if (st.split_ways > 1 && L.split_ways > 1) {
+            // a chosen number of ranges: at most 4, each of at least 4
+            // k-chunks, and at most max_ctas parts in all (the partial buffer
+            // holds digit_partial_floats(max_ctas))
+            const int tail = tiles - L.split_begin;
+            int w = st.split_ways < 4 ? st.split_ways : 4;
+            while (w > 1 && ((st.n_pad / kc) / w < 4 || tail * w > st.max_ctas)) --w;
+            L.split_ways = w;
+            if (w < 2) L.split_begin = tiles;
+        }
+    }
+    if (L.split_ways < 2) {
+        L.split_begin = tiles;
+        L.split_ways = 1;
+    }
     L.num_items = L.split_begin + (tiles - L.split_begin) * L.split_ways;
+    if (L.split_ways > 1 && (tiles - L.split_begin) * L.split_ways > st.max_ctas) return PURIFY_ERR_INVALID_ARG;
     if (L.split_ways > 1) {
         // per-region arrival counters of the split tiles, then the claim
         // counter (tiles - split_begin < max_ctas, so both fit in

@@ -40,6 +40,11 @@ struct DigitStep {
     // split_cnt digit_split_counters(max_ctas) ints; null = no split
     float* partial = nullptr;
     int* split_cnt = nullptr;
+    // launch shape (dense products): k-chunk width 16, 32 or 64 and the
+    // number of k-ranges of the last wave's tiles (1 = whole tiles); 0 = the
+    // rule (digit_kc, digit_split_plan)
+    int kc = 0;
+    int split_ways = 0;
 };
 
 // Epilogue warps of the product kernel (each owns a 32-row x (512 / kEpiWarps)
@@ -86,6 +91,11 @@ inline int remainder_bits(int n_pad) { return n_pad <= 4096 ? 7 : 6; }
 inline int digit_bits(int s, int rbits) { return 8 + rbits * (s - 1); }
 
 int digit_kc(int s);
+// The k-chunk width a step launches with (its own, or the rule's).
+int digit_step_kc(const DigitStep& st);
+// k-chunk widths worth timing for s digits (dense products; at least one
+// stage pair must fit): writes up to 3 and returns the count.
+int digit_kc_candidates(int s, int* kc);
 int digit_stages(int s, int kc);
 size_t digit_smem_bytes(int s, int kc);
 

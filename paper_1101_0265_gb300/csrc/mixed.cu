@@ -14,7 +14,10 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 
 #include "digits_tc.h"
 
@@ -93,12 +96,92 @@ static void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) 
     }
 }
 
+// ---- launch-shape autotuning ----------------------------------------------
+// Shapes measured in this process, per (device, digits, padded size): the
+// first product of a kind times every candidate and all later products of
+// that kind use the fastest.  The mutex also serialises the measurement, so
+// every handle of the process gets the same shape for a kind.
+namespace {
+struct TunedShape {
+    int kc, ways;
+};
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, TunedShape> g_tuned;
+
+// Device time of one launch of `st` (the smaller of two, after one warm-up).
+int time_launch(const DigitStep& st, cudaStream_t stream, cudaEvent_t a, cudaEvent_t b, float* ms) {
+    PURIFY_TRY(launch_digit_step(st, stream));
+    *ms = INFINITY;
+    for (int r = 0; r < 2; ++r) {
+        PURIFY_CUDA_TRY(cudaEventRecord(a, stream));
+        PURIFY_TRY(launch_digit_step(st, stream));
+        PURIFY_CUDA_TRY(cudaEventRecord(b, stream));
+        PURIFY_CUDA_TRY(cudaEventSynchronize(b));
+        float t = 0.f;
+        PURIFY_CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+        *ms = std::min(*ms, t);
+    }
+    return PURIFY_OK;
+}
+
+// Times the candidates on the step itself (its inputs are read, its output
+// planes written; reductions, float64 output and block norms are left out,
+// so the real launch that follows is unaffected).
+int tune_shape(const DigitStep& st, cudaStream_t stream, TunedShape* best) {
+    int kcs[3];
+    const int nk = digit_kc_candidates(st.s_in, kcs);
+    cudaEvent_t a = nullptr, b = nullptr;
+    PURIFY_CUDA_TRY(cudaEventCreate(&a));
+    if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return PURIFY_ERR_CUDA;
+    }
+    float best_ms = INFINITY;
+    *best = {0, 0};
+    int rc = PURIFY_OK;
+    for (int i = 0; i < nk && rc == PURIFY_OK; ++i) {
+        for (int ways : {0, 1}) {
+            if (ways != 0 && !st.partial) continue;
+            DigitStep c = st;
+            c.kc = kcs[i];
+            c.split_ways = ways;
+            c.red = nullptr;
+            c.out64 = nullptr;
+            c.bnorm2 = nullptr;
+            float ms = INFINITY;
+            rc = time_launch(c, stream, a, b, &ms);
+            if (rc != PURIFY_OK) break;
+            if (ms < best_ms) {
+                best_ms = ms;
+                *best = {kcs[i], ways};
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return rc;
+}
+}  // namespace
+
 static int product(purify_ctx* h, const DigitStep& st0, double flops) {
     DigitStep st = st0;
     if (h->opt.split_k) {
         st.partial = h->mixed->partial;
         st.split_cnt = h->mixed->split_cnt;
     }
+    if (h->opt.autotune && !st.kc_cnt && !st.bnorm2 && st.kc == 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        const auto key = std::make_tuple(h->device, st.s_in, st.n_pad);
+        auto f = g_tuned.find(key);
+        if (f == g_tuned.end()) {
+            TunedShape t;
+            PURIFY_TRY(tune_shape(st, h->stream, &t));
+            f = g_tuned.emplace(key, t).first;
+        }
+        st.kc = f->second.kc;
+        st.split_ways = f->second.ways;
+    }
+    h->st.digit_kc = digit_step_kc(st);
     PURIFY_TRY(product_begin(h));
     PURIFY_TRY(launch_digit_step(st, h->stream));
     ++h->st.product_launches;
@@ -637,4 +720,15 @@ extern "C" int purify_k_digit_product_f64(const double* A, const double* B, doub
     cudaFree(split_cnt);
     if (r == PURIFY_OK && herr) r = PURIFY_ERR_DEVICE_TIMEOUT;
     return r;
+}
+
+int purify_tuned_shape(int device, int digits, int64_t n, int* kc, int* split_ways) {
+    using namespace purify;
+    if (!kc || !split_ways || n <= 0 || digits < 1 || digits > kMaxDigitPlanes) return PURIFY_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const auto f = g_tuned.find(std::make_tuple(device, digits, pad128(n)));
+    if (f == g_tuned.end()) return PURIFY_ERR_STATE;
+    *kc = f->second.kc;
+    *split_ways = f->second.ways;
+    return PURIFY_OK;
 }

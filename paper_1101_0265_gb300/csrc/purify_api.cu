@@ -471,6 +471,7 @@ static int check_options(const purify_options* o) {
     if (o->refine_fp64 < 0 || o->refine_fp64 > 2) return PURIFY_ERR_INVALID_ARG;
     if (o->bits_floor != 0 && (o->bits_floor < 16 || o->bits_floor > 43)) return PURIFY_ERR_INVALID_ARG;
     if (o->bits_gap != 0 && (o->bits_gap < 16 || o->bits_gap > 43)) return PURIFY_ERR_INVALID_ARG;
+    if (o->autotune != 0 && o->autotune != 1) return PURIFY_ERR_INVALID_ARG;
     if (!(o->trunc_tau >= 0.0) || !(o->trunc_budget >= 0.0)) return PURIFY_ERR_INVALID_ARG;
     return PURIFY_OK;
 }

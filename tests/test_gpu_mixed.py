@@ -278,3 +278,59 @@ def test_asymmetric_pij_on_digit_planes(P, scheme, ij):
     assert st["iterations"] == r.iterations and st["multiplications"] == r.multiplications
     assert np.max(np.abs(D - Do)) <= 3e-7
     assert abs(st["trace"] - h.nocc) < 1e-6
+
+
+def test_autotuned_launch_shapes(P):
+    # autotune: the first product of each digit count and size times the
+    # candidate launch shapes (k-chunk width, split of the last wave); the
+    # chosen shape only reorders the inexact level's sums, so the density
+    # stays within the mixed tolerance, and a second handle of the process
+    # reuses the shapes: the same density bit for bit
+    h = I.dense_hamiltonian(1200, 600, 0.01, config=73)
+    out = []
+    for _ in range(2):
+        pur = P.Purifier(precision="mixed", autotune=True)
+        pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+        assert pur.run("TC_SF", 1e-10, 200) == P.OK
+        out.append((pur.density(), pur.stats()))
+        pur.close()
+    (D0, s0), (D1, s1) = out
+    assert np.array_equal(D0, D1)
+    Dx = O.density_closed_form(h.Q, h.lam, 0.0)
+    assert np.max(np.abs(D0 - Dx)) <= 3e-7
+    assert s0["digit_kc"] in (16, 32, 64)
+    shape = P.tuned_shape(0, s0["digit_max"], 1200)
+    assert shape is not None and shape[0] in (16, 32, 64) and shape[1] in (0, 1)
+
+
+@pytest.mark.parametrize("kc", [16, 32, 64])
+def test_forced_k_chunk_widths(kc):
+    # every k-chunk width a launch shape can take gives the density within the
+    # mixed tolerance (the width is read once per process, so each runs in a
+    # child process)
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import numpy as np\n"
+        "from oracle import purify_oracle as O\n"
+        "from paper_1101_0265_gb300 import inputs as I\n"
+        "import paper_1101_0265_gb300 as P\n"
+        "h = I.dense_hamiltonian(600, 300, 0.01, config=74)\n"
+        "for sc in ('TC_SF', 'FIXED_MU_SF'):\n"
+        "    pur = P.Purifier(precision='mixed')\n"
+        "    pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)\n"
+        "    assert pur.run(sc, 1e-10, 200) == P.OK\n"
+        "    D, st = pur.density(), pur.stats()\n"
+        "    pur.close()\n"
+        "    err = np.max(np.abs(D - O.density_closed_form(h.Q, h.lam, 0.0)))\n"
+        "    print(sc, st['digit_kc'], err)\n"
+        "    assert err <= 3e-7 and np.array_equal(D, D.T)\n")
+    env = dict(os.environ, PURIFY_DIGIT_KC=str(kc), PYTHONPATH=root)
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, env=env, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    # the forced width was the one launched (16 needs at least 4 digits)
+    kcs = {int(line.split()[1]) for line in r.stdout.splitlines() if line.strip()}
+    assert kcs <= {kc, 32}

@@ -42,7 +42,7 @@ def test_library_exports_every_header_symbol():
 @pytest.mark.parametrize("field,value", [
     ("digits", 7), ("digits", 1), ("split_k", 2), ("refine_fp64", 3), ("bits_floor", 15),
     ("bits_floor", 44), ("bits_gap", 15), ("bits_gap", 44), ("trunc_tau", -1.0),
-    ("trunc_budget", float("nan")), ("precision", 5), ("lanczos_steps", -1)])
+    ("trunc_budget", float("nan")), ("precision", 5), ("lanczos_steps", -1), ("autotune", 2)])
 def test_invalid_options_rejected_before_the_device(field, value):
     # option checks come first: no device is touched, so this runs without a GPU
     import ctypes as C
@@ -57,6 +57,14 @@ def test_invalid_options_rejected_before_the_device(field, value):
     if field in ("digits", "bits_floor", "bits_gap"):
         b = C.c_void_p()
         assert lib.purify_batch_create(C.byref(b), 0, None, C.byref(o)) == P.ERR_INVALID_ARG
+
+
+def test_tuned_shape_query_without_measurements():
+    # nothing measured in this process: STATE; bad arguments: INVALID_ARG
+    _ensure_built()
+    assert P.tuned_shape(0, 5, 4096) is None
+    with pytest.raises(P.PurifyError):
+        P.tuned_shape(0, 9, 4096)
 
 
 def test_strerror_names_codes():
