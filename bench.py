@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pipelines", type=int, default=2,
                     help="handles (own stream and host thread each) sharing a step's purifications")
+    ap.add_argument("--e2e-pipelines", type=int, default=2,
+                    help="the same for the end-to-end run (host copies to overlap as well)")
     ap.add_argument("--no-lattice", action="store_true", help="skip the L^3 block-sparse workload")
     ap.add_argument("--no-autotune", action="store_true",
                     help="launch products with the fixed shape rule instead of measured shapes")
@@ -490,19 +492,21 @@ def main():
     # share a step's purifications (one purification's host work and copies
     # overlap another's products).
     npipe = max(1, args.pipelines)
+    ne2e = max(1, args.e2e_pipelines)
     per_step = len(hs) * len(schemes)
     work = [(i, sc) for i in range(len(hs)) for sc in schemes]
     pipes = []
-    for p in range(npipe if npipe > 1 else 0):
+    nhandles = max(npipe, ne2e)
+    for p in range(nhandles if nhandles > 1 else 0):
         sp = torch.cuda.Stream(dev)
         pipes.append((sp, P.Purifier(device=local, stream=sp.cuda_stream, precision=args.precision, **rule),
                       torch.empty((n, n), dtype=torch.float64).pin_memory()))
 
-    def pipe_run(p, k, host, errs, launches):
+    def pipe_run(p, k, host, errs, launches, use):
         sp, pp, Dp = pipes[p]
         try:
             for _ in range(k):
-                for q in range(p, len(work), npipe):
+                for q in range(p, len(work), use):
                     i, sc = work[q]
                     h = hs[i]
                     pp.set_hamiltonian(Fh[i] if host else Fd[i], nocc=h.nocc, mu=0.0, lmin=h.lmin,
@@ -516,7 +520,7 @@ def main():
         except Exception as e:  # reported after the join
             errs.append(e)
 
-    def pipelined(k, host, clocks=False):
+    def pipelined(k, host, use, clocks=False):
         import threading
         if dist:
             dist.barrier()
@@ -526,8 +530,8 @@ def main():
             sampler.start()
         e0 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        errs, launches = [], [0] * npipe
-        ths = [threading.Thread(target=pipe_run, args=(p, k, host, errs, launches)) for p in range(npipe)]
+        errs, launches = [], [0] * use
+        ths = [threading.Thread(target=pipe_run, args=(p, k, host, errs, launches, use)) for p in range(use)]
         for t in ths:
             t.start()
         for t in ths:
@@ -535,7 +539,7 @@ def main():
         if errs:
             raise errs[0]
         ends = []
-        for sp, _, _ in pipes:
+        for sp, _, _ in pipes[:use]:
             e = torch.cuda.Event(enable_timing=True)
             e.record(sp)
             ends.append(e)
@@ -553,8 +557,8 @@ def main():
     launches_timed = acc["launches"]
     if npipe > 1:
         for _ in range(max(1, args.warmup // 2)):
-            pipelined(1, host=False)
-        ms_local, clocks, launches_timed = pipelined(args.steps, host=False, clocks=True)
+            pipelined(1, host=False, use=npipe)
+        ms_local, clocks, launches_timed = pipelined(args.steps, host=False, use=npipe, clocks=True)
         value, ms = replica_rate(ms_local, per_step * args.steps, world, max_over_ranks)
     else:
         value, ms = value1, ms1
@@ -564,9 +568,9 @@ def main():
     ms_e2e_local, _ = timed(k_e2e, host=True)
     value_e2e_serial, _ = replica_rate(ms_e2e_local, per_step * k_e2e, world, max_over_ranks)
     value_e2e = value_e2e_serial
-    if npipe > 1:
-        pipelined(1, host=True)
-        ms_pipe_local, _, _ = pipelined(k_e2e, host=True)
+    if ne2e > 1:
+        pipelined(1, host=True, use=ne2e)
+        ms_pipe_local, _, _ = pipelined(k_e2e, host=True, use=ne2e)
         value_e2e, _ = replica_rate(ms_pipe_local, per_step * k_e2e, world, max_over_ranks)
     for _, pp, _ in pipes:
         pp.close()
@@ -596,10 +600,10 @@ def main():
         "e2e": {"value": value_e2e, "unit": "matrices/s",
                 "h2d_bytes_per_step": per_step * n * n * 8,
                 "d2h_bytes_per_step": per_step * n * n * 8,
-                "pipelines": npipe, "serial_value": value_e2e_serial,
+                "pipelines": ne2e, "serial_value": value_e2e_serial,
                 "note": "pinned host F in and D out through purify_set_hamiltonian / "
                         "purify_get_density; `pipelines` handles, each on its own stream and "
-                        "host thread, share the step's purifications (as for `value`)"},
+                        "host thread, share the step's purifications"},
         "gpu_launches": launches_timed,
         "pipelines": npipe,
         "single_handle": {"value": value1, "ms_per_step": ms1 / args.steps,
