@@ -120,6 +120,22 @@ def test_schedule_bitwise_equal_to_oracle(scheme, case, tol):
     assert np.array_equal(s["beta"], be)
 
 
+def test_library_schedule_reproduces_golden_counts():
+    # the library's own scalar schedule gives the stored multiplication counts
+    # (tests/golden/scalar_counts.txt, from the oracle): Algorithm 1 two
+    # products per iteration, Algorithm 2 one
+    from test_oracle import golden_counts
+    _ensure_built()
+    for mu, xi, mm, ms, tm, ts in golden_counts():
+        homo, lumo = mu - xi / 2, mu + xi / 2
+        got = []
+        for scheme, per in (("FIXED_MU_MONO", 2), ("FIXED_MU_SF", 2), ("TC_MONO", 1), ("TC_SF", 1)):
+            sch = P.schedule(scheme, 0.0, 1.0, mu if scheme.startswith("FIXED") else float("nan"), homo, lumo,
+                             1e-9, max_iter=10_000)
+            got.append(per * len(sch["alpha"]))
+        assert tuple(got) == (mm, ms, tm, ts), (mu, xi, got)
+
+
 def test_schedule_not_converged_and_bad_bounds():
     _ensure_built()
     s = P.schedule("TC_SF", -1, 1, 0, -0.05, 0.05, 1e-12, max_iter=3)

@@ -8,6 +8,7 @@ from a claim the paper states (half the multiplications, speedup growing as
 the gap closes, independent of mu).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -196,6 +197,33 @@ def _counts(mu, xi, tol=1e-9):
     tc_sf = len(O.tc_schedule(tb, tbb, tol, 10_000, True))
     tc_mono = len(O.tc_schedule(tb, tbb, tol, 10_000, False))
     return mcw_mono, mcw_sf, tc_mono, tc_sf
+
+
+def golden_counts():
+    """Rows (mu, xi, mcweeny_mono, mcweeny_scaled, tc_mono, tc_scaled) of
+    tests/golden/scalar_counts.txt (written from the oracle by
+    tests/golden/make_scalar_counts.py)."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "scalar_counts.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    return [(float(r[0]), float(r[1])) + tuple(int(v) for v in r[2:]) for r in rows]
+
+
+def test_scalar_counts_golden():
+    # the stored counts are reproduced exactly; they show the paper's claims
+    # (about half the multiplications; cost growing with 1/xi) and the mirror
+    # symmetry of both schemes in mu about the middle of the spectrum
+    rows = golden_counts()
+    assert len(rows) == 12
+    by = {}
+    for mu, xi, mm, ms, tm, ts in rows:
+        assert _counts(mu, xi) == (mm, ms, tm, ts), (mu, xi)
+        assert 0.4 <= ms / mm <= 0.65 and 0.4 <= ts / tm <= 0.65
+        by[(round(mu, 2), xi)] = (mm, ms, tm, ts)
+    for mu in (0.1, 0.25, 0.4):
+        assert by[(mu, 0.01)] == by[(round(1 - mu, 2), 0.01)]
+    gap_sweep = [by[(0.5, 10.0 ** -k)] for k in range(1, 7)]
+    for col in range(4):
+        assert all(a[col] <= b[col] for a, b in zip(gap_sweep, gap_sweep[1:]))
 
 
 def test_half_the_multiplications():
