@@ -226,6 +226,26 @@ def test_scalar_counts_golden():
         assert all(a[col] <= b[col] for a, b in zip(gap_sweep, gap_sweep[1:]))
 
 
+def test_config_counts_golden():
+    # the dense configurations' counts (spectrum [-1, 1], mu = 0) stored in
+    # tests/golden/config_counts.txt are reproduced exactly; scaling never
+    # costs more, a tighter tolerance never costs less
+    from tests.golden.make_scalar_counts import config_counts
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "config_counts.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 12
+    by = {}
+    for r in rows:
+        gap, tol = float(r[0]), float(r[1])
+        c = tuple(int(v) for v in r[2:])
+        assert config_counts(gap, tol) == c, (gap, tol)
+        assert c[1] <= c[0] and c[3] <= c[2]
+        by[(gap, tol)] = c
+    for gap in (1e-1, 1e-2, 1e-3, 1e-4):
+        for col in range(4):
+            assert by[(gap, 1e-6)][col] <= by[(gap, 1e-9)][col] <= by[(gap, 1e-12)][col]
+
+
 def test_half_the_multiplications():
     # Abstract and Fig. 3b: about half the multiplications, "around twice as fast"
     for xi in (1e-1, 1e-2, 1e-3, 1e-4, 1e-5, 1e-6):
