@@ -63,3 +63,25 @@ def test_single_process_rate():
     a = I.dense_hamiltonian(32, 16, 0.1, config=2, instance=bench.rank_instance(0, 0))
     b = I.dense_hamiltonian(32, 16, 0.1, config=2, instance=bench.rank_instance(1, 0))
     assert a.F.shape == b.F.shape and not np.array_equal(a.F, b.F)
+
+
+def test_reference_arm_line_contract():
+    # `bench.py --impl reference` times the oracle on the host cores and prints
+    # one JSON line with the main arm's metric, unit and config, plus its own
+    # cpu_baseline and a zero-copy e2e object
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--n", "256", "--steps", "1",
+                        "--warmup", "3"], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "matrices/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1 and d["warmup"] == 3
+    assert d["config"] == bench.main_config(256, 8, ("TC_SF", "FIXED_MU_SF"), 1e-9, "mixed", 1)
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
