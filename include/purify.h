@@ -410,6 +410,14 @@ int purify_k_lanczos_f64(const double* F, int64_t n, int k, double* a, double* b
 int purify_k_digit_product_f64(const double* A, const double* B, double* C, int64_t n, int digits,
                                int eA, int eB, void* stream);
 
+/* The product kernel's work plan for a persistent grid of `ctas` CTAs over
+ * `tiles` output tiles of `k_chunks` k-chunks each (host only): whole waves
+ * of tiles [0, *split_begin) go round-robin over the CTAs; the tiles of the
+ * last, partial wave are cut into *ways ranges of k-chunks (ways = 1: none),
+ * at most 4, each of at least 4 k-chunks, and at most `ctas` parts in all.
+ * INVALID_ARG for non-positive arguments. */
+int purify_k_split_plan(int tiles, int ctas, int k_chunks, int* split_begin, int* ways);
+
 #ifdef __cplusplus
 }
 #endif

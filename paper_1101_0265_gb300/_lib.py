@@ -34,7 +34,7 @@ BRANCH_RULES = {"beta": 0, "trace": 1}
 EXPORTED = (
     "purify_options_default", "purify_create", "purify_destroy", "purify_set_options",
     "purify_set_hamiltonian", "purify_set_hamiltonian_coo", "purify_block_history", "purify_estimate_gap",
-    "purify_tuned_shape",
+    "purify_tuned_shape", "purify_k_split_plan",
     "purify_run", "purify_get_density", "purify_stats",
     "purify_density_device_ptr", "purify_strerror", "purify_schedule", "purify_tridiag_eig",
     "purify_k_symm_product_f64", "purify_k_step_f64", "purify_k_gershgorin_f64",
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH):
         "purify_set_hamiltonian_coo": (ip, [vp, i64, i64, vp, vp, vp, i64, dbl, C.POINTER(Bounds)]),
         "purify_block_history": (ip, [vp, C.POINTER(C.c_int), ip, C.POINTER(C.c_int)]),
         "purify_tuned_shape": (ip, [ip, ip, i64, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "purify_k_split_plan": (ip, [ip, ip, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "purify_estimate_gap": (ip, [vp, ip, dp, dp]),
         "purify_get_density": (ip, [vp, vp, i64]),
         "purify_stats": (ip, [vp, C.POINTER(Stats)]),

@@ -732,3 +732,9 @@ int purify_tuned_shape(int device, int digits, int64_t n, int* kc, int* split_wa
     *split_ways = f->second.ways;
     return PURIFY_OK;
 }
+
+extern "C" int purify_k_split_plan(int tiles, int ctas, int k_chunks, int* split_begin, int* ways) {
+    if (tiles <= 0 || ctas <= 0 || k_chunks <= 0 || !split_begin || !ways) return PURIFY_ERR_INVALID_ARG;
+    purify::digit_split_plan(tiles, ctas, k_chunks, split_begin, ways);
+    return PURIFY_OK;
+}

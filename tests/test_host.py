@@ -161,3 +161,31 @@ def test_tridiag_eig_against_lapack(m):
     w, last = P.tridiag_eig(a, b[:max(m - 1, 1)])
     assert np.max(np.abs(w - lam)) < 1e-12 * max(1.0, np.max(np.abs(lam)))
     assert np.max(np.abs(np.abs(last) - np.abs(V[-1, :]))) < 1e-10
+
+
+def test_split_plan_invariants():
+    # the product kernel's plan: whole waves stay whole, the last wave's tiles
+    # are cut into at most 4 k-ranges of at least 4 chunks, never more parts
+    # than CTAs (the split buffers' capacity), and the cut happens only when
+    # the last wave leaves CTAs idle
+    import ctypes as C
+    _ensure_built()
+    lib = P.load()
+    b, w = C.c_int(), C.c_int()
+    for ctas in (1, 2, 76, 148, 152):
+        for T in range(1, 65):
+            tiles = T * (T + 1) // 2
+            for k_chunks in (4, 8, 16, 32, 64, 128, 256):
+                assert lib.purify_k_split_plan(tiles, ctas, k_chunks, C.byref(b), C.byref(w)) == P.OK
+                begin, ways = b.value, w.value
+                assert 1 <= ways <= 4
+                if ways == 1:
+                    assert begin == tiles
+                    continue
+                assert begin % ctas == 0 and begin == tiles // ctas * ctas
+                assert (tiles - begin) * ways <= ctas
+                assert k_chunks // ways >= 4
+    # n = 4096 on 152 SMs: 528 tiles, 3 whole waves, the last 72 tiles in 2
+    assert lib.purify_k_split_plan(528, 152, 128, C.byref(b), C.byref(w)) == P.OK
+    assert (b.value, w.value) == (456, 2)
+    assert lib.purify_k_split_plan(0, 152, 128, C.byref(b), C.byref(w)) == P.ERR_INVALID_ARG
