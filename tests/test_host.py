@@ -189,3 +189,23 @@ def test_split_plan_invariants():
     assert lib.purify_k_split_plan(528, 152, 128, C.byref(b), C.byref(w)) == P.OK
     assert (b.value, w.value) == (456, 2)
     assert lib.purify_k_split_plan(0, 152, 128, C.byref(b), C.byref(w)) == P.ERR_INVALID_ARG
+
+
+def test_options_struct_layout_matches_the_library():
+    # the binding's Options mirrors purify_options field by field: the
+    # library's defaults land in the right fields and nothing past the end of
+    # the Python struct is written
+    import ctypes as C
+    _ensure_built()
+    lib = P.load()
+    size = C.sizeof(P._lib.Options)
+    buf = (C.c_ubyte * (size + 64))(*([0xAB] * (size + 64)))
+    lib.purify_options_default(C.cast(buf, C.POINTER(P._lib.Options)))
+    assert bytes(buf[size:]) == b"\xab" * 64
+    o = P._lib.Options.from_buffer(buf)
+    assert o.precision == 0 and o.branch_rule == 0      # PURIFY_FP64, PURIFY_BRANCH_BETA
+    assert o.lanczos_steps == 32 and o.refine_squares == 0 and o.digits == 0
+    assert o.split_k == 1 and o.refine_fp64 == 0 and o.block_sparse == 0 and o.time_products == 0
+    assert o.bits_floor == 0 and o.bits_gap == 0 and o.autotune == 0
+    assert list(o.reserved) == [0] * len(o.reserved)
+    assert o.trunc_tau == 1e-6 and o.trunc_budget == 0.0
