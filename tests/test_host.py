@@ -209,3 +209,34 @@ def test_options_struct_layout_matches_the_library():
     assert o.bits_floor == 0 and o.bits_gap == 0 and o.autotune == 0
     assert list(o.reserved) == [0] * len(o.reserved)
     assert o.trunc_tau == 1e-6 and o.trunc_budget == 0.0
+
+
+def _header_struct(name):
+    """(field, ctype name, count) of a struct in include/purify.h, in order."""
+    src = open(os.path.join(ROOT, "include", "purify.h")).read()
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), src, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        typ, rest = decl.split(None, 1)
+        for part in rest.split(","):
+            part = part.strip()
+            m = re.match(r"(\w+)(?:\[(\d+)\])?$", part)
+            out.append((m.group(1), typ, int(m.group(2) or 1)))
+    return out
+
+
+@pytest.mark.parametrize("cname,pyname", [("purify_options", "Options"), ("purify_stats_t", "Stats"),
+                                          ("purify_bounds", "Bounds")])
+def test_binding_structs_follow_the_header(cname, pyname):
+    import ctypes as C
+    ctypes_of = {"int": C.c_int, "double": C.c_double, "int64_t": C.c_int64}
+    fields = getattr(P._lib, pyname)._fields_
+    hdr = _header_struct(cname)
+    assert [f[0] for f in fields] == [h[0] for h in hdr]
+    for (name, ct), (_, typ, cnt) in zip(fields, hdr):
+        want = ctypes_of[typ] * cnt if cnt > 1 else ctypes_of[typ]
+        assert C.sizeof(ct) == C.sizeof(want) and getattr(ct, "_type_", ct) == getattr(want, "_type_", want), name
