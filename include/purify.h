@@ -231,8 +231,10 @@ int purify_estimate_gap(purify_t h, int lanczos_steps, double* homo_est, double*
 /* The launch shape that purify_options.autotune measured on `device` for
  * products of `digits` digit planes at size n (padded to 128): k-chunk width
  * (*kc) and the last wave's split (*split_ways: 0 = the rule, 1 = whole
- * tiles).  Host only.  PURIFY_ERR_STATE when nothing was measured
- * for that kind in this process. */
+ * tiles).  Host only; a launch setting of this library, not an operation of
+ * the paper.  PURIFY_ERR_STATE when nothing was measured for that kind in
+ * this process, PURIFY_ERR_INVALID_ARG for null outputs, n <= 0 or digits
+ * outside 1..6. */
 int purify_tuned_shape(int device, int digits, int64_t n, int* kc, int* split_ways);
 
 /* Block-sparse runs: the number of upper 32 x 32 blocks kept after the
@@ -415,7 +417,9 @@ int purify_k_digit_product_f64(const double* A, const double* B, double* C, int6
  * of tiles [0, *split_begin) go round-robin over the CTAs; the tiles of the
  * last, partial wave are cut into *ways ranges of k-chunks (ways = 1: none),
  * at most 4, each of at least 4 k-chunks, and at most `ctas` parts in all.
- * INVALID_ARG for non-positive arguments. */
+ * A launch setting of this library, not an operation of the paper (exposed
+ * for tests).  PURIFY_ERR_INVALID_ARG for non-positive arguments or null
+ * outputs. */
 int purify_k_split_plan(int tiles, int ctas, int k_chunks, int* split_begin, int* ways);
 
 #ifdef __cplusplus
