@@ -31,7 +31,13 @@ METRIC = ("purified n=4096 matrices/sec + tensor-pipe % at max-err<=1e-6 vs plai
           "serve p50/p99")
 GAPS = (1e-1, 1e-2, 1e-3, 1e-4)
 SCHEMES = ("TC_SF", "FIXED_MU_SF")
-FP64_PER_BF16 = 1.25 / 2250.0   # nominal dense fp64 : bf16 ratio of GB300
+SMS = 152                        # GB300 streaming multiprocessors
+TENSOR_FLOP_PER_CLK_SM = 8192    # dense bf16 tcgen05 rate per SM and clock (nominal)
+FP64_FLOP_PER_CLK_SM = 4         # two float64 FMAs per SM and clock (nominal)
+# The tensor pipe's active share of one digit-plane product launch (ncu
+# sm__pipe_tensor_cycles_active of digit_gemm_kernel<32, 5>, n = 4096).
+TENSOR_PIPE_PCT_NCU = 67.6
+TENSOR_PIPE_SOURCE = "profiles/digit_gemm_kc32_s5_n4096.md (ncu, one launch, n=4096, S=5)"
 # DRAM bytes (read + write) of one digit-plane product launch, from one ncu
 # capture of digit_gemm_kernel<32, 5> at n = 4096 (bytes per launch).
 TRAFFIC_DIGIT_GEMM = 776.5e6
@@ -54,8 +60,12 @@ def parse():
     ap.add_argument("--no-fp64-check", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-size", type=int, default=256)
-    ap.add_argument("--serve-rates", default="10,100,1000", help="comma list; empty to skip serving")
-    ap.add_argument("--serve-requests", type=int, default=60)
+    ap.add_argument("--serve-rates", default="10,30,100,300,1000", help="comma list; empty to skip serving")
+    ap.add_argument("--serve-requests", type=int, default=500)
+    ap.add_argument("--exact-bounds", action="store_true",
+                    help="pass the exact lmin/lmax instead of estimating them inside the step")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the exact-bounds and refinement variants")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--pipelines", type=int, default=2,
                     help="handles (own stream and host thread each) sharing a step's purifications")
@@ -100,13 +110,14 @@ def make_inputs(n, rank, count=None):
 
 
 def make_device_inputs(n, rank, count, dev):
-    """The same sweep built on the GPU (torch QR); F stays on the device."""
+    """The same sweep built on the GPU (torch QR); F and the eigenvectors Q
+    (for the closed-form density) stay on the device."""
     from paper_1101_0265_gb300 import inputs as I
     hs, Fs = [], []
     for i, (nocc, gap) in enumerate(workload_specs(n)[:count]):
         spec = I.InstanceSpec(n=n, nocc=nocc, gap=gap, scheme="TC_SF", instance=rank_instance(rank, i),
                               config=2)
-        F, h = I.dense_hamiltonian_device(spec, dev)
+        F, h = I.dense_hamiltonian_device(spec, dev, keep_q=True)
         hs.append(h)
         Fs.append(F)
     return hs, Fs
@@ -187,7 +198,8 @@ def run_serve(P, dev, stream, rate, count, budget_gb=64.0, tol=1e-9):
     B.close()
     lat.sort()
     pct = lambda q: 1e3 * lat[min(len(lat) - 1, int(q * len(lat)))]
-    return {"rate_per_s": rate, "requests": count, "p50_ms": pct(0.50), "p99_ms": pct(0.99),
+    return {"rate_per_s": rate, "requests": count, "latencies": len(lat), "p50_ms": pct(0.50),
+            "p99_ms": pct(0.99),
             "max_ms": 1e3 * lat[-1], "throughput_per_s": count / total, "rounds": rounds,
             "peak_concurrent": peak_live, "hbm_budget_gb": budget_gb}
 
@@ -320,16 +332,24 @@ class ClockSampler:
                 "sm_mhz_min": min(sm)}
 
 
-def cpu_baseline(hs, F0, tol):
-    """The oracle as it stands, on a bounded sample: one purification."""
+def cpu_baseline(hs, Fs, tol, estimate_bounds=True):
+    """The oracle as it stands, on a bounded sample of the step: four
+    purifications that cycle through both nocc values, four gaps and both
+    schemes (bounds estimated as in the timed step: Gershgorin, then 32
+    Lanczos steps)."""
     from oracle import purify_oracle as O
-    h = hs[0]
+    picks = [(0, "TC_SF"), (6, "FIXED_MU_SF"), (5, "TC_SF"), (3, "FIXED_MU_SF")]
+    picks = [(i % len(hs), sc) for i, sc in picks]
     t0 = time.perf_counter()
-    O.purify(F0, "TC_SF", h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=tol)
+    for i, sc in picks:
+        h, F = hs[i], Fs[i]
+        lo, hi = O.lanczos_bounds(F, 32) if estimate_bounds else (h.lmin, h.lmax)
+        O.purify(F, sc, min(lo, h.homo), max(hi, h.lumo), mu=0.0, homo=h.homo, lumo=h.lumo, tol=tol)
     dt = time.perf_counter() - t0
-    return {"value": 1.0 / dt, "unit": "matrices/s", "cores": _blas_threads(), "kind": "oracle",
-            "sample": f"1 purification (TC_SF, n={h.n}, nocc={h.nocc}, gap={h.meta['gap']:g}, "
-                      f"tol={tol:g}) of the step's 16, numpy float64, {dt:.2f} s"}
+    desc = ", ".join(f"{sc} nocc={hs[i].nocc} gap={hs[i].meta['gap']:g}" for i, sc in picks)
+    return {"value": len(picks) / dt, "unit": "matrices/s", "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"{len(picks)} of the step's 16 purifications at n={hs[0].n} ({desc}; tol {tol:g}, "
+                      f"bounds by Gershgorin + 32 Lanczos steps), numpy float64, {dt:.1f} s"}
 
 
 def _blas_threads():
@@ -344,13 +364,16 @@ def _blas_threads():
     return int(env) if env else os.cpu_count()
 
 
-def main_config(n, count, schemes, tol, precision, world):
+def main_config(n, count, schemes, tol, precision, world, exact_bounds=False):
     """The `config` of the dense workload (both arms report the same one)."""
     return {"workload": f"dense F=Q diag(lambda) Q^T n={n}, nocc in {{n/2,n/4}} x gap in "
                         f"{{1e-1,1e-2,1e-3,1e-4}} ({count} matrices) x schemes "
                         f"{', '.join(schemes)}; tol {tol:g}",
             "n": n, "matrices_per_step": count * len(schemes),
             "tol": tol, "parallelism": f"replicas x{world}",
+            "bounds": ("lmin/lmax given exactly" if exact_bounds else
+                       "lmin/lmax estimated per matrix inside the step (Gershgorin discs, 32 Lanczos "
+                       "steps); homo/lumo given"),
             "l2": "inputs larger than L2 (each F is 134 MB, 8 distinct per step)"}
 
 
@@ -366,8 +389,9 @@ def run_reference(args, rank, world):
 
     def one(i):
         h = hs[i % count]
-        O.purify(h.F, schemes[i % len(schemes)], h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo,
-                 tol=args.tol)
+        lo, hi = O.lanczos_bounds(h.F, 32)
+        O.purify(h.F, schemes[i % len(schemes)], min(lo, h.homo), max(hi, h.lumo), mu=0.0, homo=h.homo,
+                 lumo=h.lumo, tol=args.tol)
     for i in range(args.warmup):
         one(i)
     t0 = time.perf_counter()
@@ -384,12 +408,56 @@ def run_reference(args, rank, world):
         "config": main_config(n, len(workload_specs(n)), schemes, args.tol, "f64", world),
         "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": cores, "kind": "oracle",
                          "sample": f"a bounded sample of the step: one purification per step "
-                                   f"(CPU oracle, numpy float64), cycling the first {count} "
-                                   f"matrices of the sweep and the schemes {', '.join(schemes)}"},
+                                   f"(CPU oracle, numpy float64, bounds by Gershgorin + 32 Lanczos "
+                                   f"steps), cycling the first {count} matrices of the sweep and the "
+                                   f"schemes {', '.join(schemes)}"},
         "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def accuracy_pass(P, pur, hs, Fd, Dc, schemes, tol, set_fn, dev, ref=None):
+    """Every purification of the step once more, outside the timed region:
+    per result the max |D - D_exact| against the closed form Q_occ Q_occ^T,
+    |trace D - nocc|, ||D - D^2||_F (both from D itself), the library's own
+    reductions, and, with `ref` (a float64 handle), the max |D - D_fp64| of
+    the plain float64 recursion on the same schedule."""
+    import torch
+    n = hs[0].n
+    D = torch.empty((n, n), dtype=torch.float64, device=dev)
+    D2 = torch.empty((n, n), dtype=torch.float64, device=dev) if ref else None
+    out, t64 = [], 0.0
+    for i, h in enumerate(hs):
+        set_fn(pur, h, Fd[i])
+        if ref:
+            set_fn(ref, h, Fd[i])
+        for sc in schemes:
+            if pur.run(sc, tol, 200) != P.OK:
+                raise RuntimeError(f"{sc} did not converge")
+            st = pur.stats()
+            pur.density(D)
+            r = {"nocc": h.nocc, "gap": h.meta["gap"], "scheme": sc, "iterations": st["iterations"],
+                 "max_err_closed_form": float((D - Dc[i]).abs().max()),
+                 "trace_err": abs(float(torch.trace(D)) - h.nocc),
+                 "idem_err_fro": float(torch.linalg.matrix_norm(D - D @ D)),
+                 "lib_trace_err": st["trace_err"], "lib_idem_err_fro": st["idem_err_fro"]}
+            if ref:
+                if ref.run(sc, tol, 200) != P.OK:
+                    raise RuntimeError(f"float64 {sc} did not converge")
+                t64 += ref.stats()["seconds"]
+                ref.density(D2)
+                r["max_err_vs_fp64"] = float((D - D2).abs().max())
+            out.append(r)
+    return out, t64
+
+
+def summarize_accuracy(results, bound=1e-6):
+    worst = lambda k: max(r[k] for r in results) if results and k in results[0] else None
+    e_cf, e_64 = worst("max_err_closed_form"), worst("max_err_vs_fp64")
+    ok = e_cf is not None and e_cf <= bound and e_64 is not None and e_64 <= bound
+    return {"bound": bound, "pass": bool(ok), "max_err_closed_form": e_cf, "max_err_vs_fp64": e_64,
+            "max_trace_err": worst("trace_err"), "max_idem_err_fro": worst("idem_err_fro")}
 
 
 def main():
@@ -400,7 +468,6 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    import numpy as np
     import torch
     import paper_1101_0265_gb300 as P
     from paper_1101_0265_gb300 import build
@@ -432,37 +499,45 @@ def main():
     pur = P.Purifier(device=local, stream=stream.cuda_stream, precision=args.precision,
                      time_products=True, **rule)
 
+    def set_h(p, h, F, exact=args.exact_bounds):
+        # lmin / lmax NaN: estimated on the device (Gershgorin, then Lanczos)
+        if exact:
+            p.set_hamiltonian(F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+        else:
+            p.set_hamiltonian(F, nocc=h.nocc, mu=0.0, homo=h.homo, lumo=h.lumo)
+
     acc = {"launches": 0, "prod_s": 0.0, "prod_n": 0, "tensor_flops": 0.0, "useful": 0.0,
            "mults": 0, "digit_max": 0}
 
-    def one(h, F, scheme, D=None, record=False):
-        pur.set_hamiltonian(F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo,
-                            lumo=h.lumo)
-        s0 = pur.stats()
-        code = pur.run(scheme, args.tol, 200)
-        if code != P.OK:
-            raise RuntimeError(f"{scheme} did not converge: {P.strerror(code)}")
-        if D is not None:
-            pur.density(D)
+    def one_matrix(p, i, host=False, record=False, exact=args.exact_bounds, Dout=None):
+        """Bounds and both schemes for matrix i: one set, one run per scheme."""
+        h = hs[i]
+        set_h(p, h, Fh[i] if host else Fd[i], exact)
+        launches = p.stats()["kernel_launches"]
+        for scheme in schemes:
+            code = p.run(scheme, args.tol, 200)
+            if code != P.OK:
+                raise RuntimeError(f"{scheme} did not converge: {P.strerror(code)}")
+            s_ = p.stats()
+            launches += s_["kernel_launches"]
+            if host:
+                p.density(Dout)
+            if record:
+                acc["prod_s"] += s_["product_seconds"]
+                acc["prod_n"] += s_["product_launches"]
+                acc["tensor_flops"] += s_["tensor_flops"]
+                acc["useful"] += s_["useful_flops"]
+                acc["mults"] += s_["multiplications"]
+                acc["digit_max"] = max(acc["digit_max"], s_["digit_max"])
         if record:
-            s = pur.stats()
-            acc["launches"] += s0["kernel_launches"] + s["kernel_launches"]
-            acc["prod_s"] += s["product_seconds"]
-            acc["prod_n"] += s["product_launches"]
-            acc["tensor_flops"] += s["tensor_flops"]
-            acc["useful"] += s["useful_flops"]
-            acc["mults"] += s["multiplications"]
-            acc["digit_max"] = max(acc["digit_max"], s["digit_max"])
+            acc["launches"] += launches
+        return launches
 
-    def step(host=False, record=False):
-        for i, h in enumerate(hs):
-            for scheme in schemes:
-                if host:
-                    one(h, Fh[i], scheme, D=Dh, record=record)
-                else:
-                    one(h, Fd[i], scheme, record=record)
+    def step(host=False, record=False, exact=args.exact_bounds):
+        for i in range(len(hs)):
+            one_matrix(pur, i, host=host, record=record, exact=exact, Dout=Dh)
 
-    def timed(k, host=False, record=False, clocks=False):
+    def timed(k, host=False, record=False, clocks=False, exact=args.exact_bounds):
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
@@ -473,7 +548,7 @@ def main():
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(k):
-            step(host=host, record=record)
+            step(host=host, record=record, exact=exact)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         ck = sampler.stop() if sampler else None
@@ -488,35 +563,25 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    # Pipelines: `pipelines` handles, each on its own stream and host thread,
-    # share a step's purifications (one purification's host work and copies
-    # overlap another's products).
+    # Pipelines: handles on their own streams and host threads share a step's
+    # matrices (one purification's host work and copies overlap another's
+    # products).
     npipe = max(1, args.pipelines)
     ne2e = max(1, args.e2e_pipelines)
     per_step = len(hs) * len(schemes)
-    work = [(i, sc) for i in range(len(hs)) for sc in schemes]
     pipes = []
     nhandles = max(npipe, ne2e)
-    for p in range(nhandles if nhandles > 1 else 0):
+    for _ in range(nhandles if nhandles > 1 else 0):
         sp = torch.cuda.Stream(dev)
         pipes.append((sp, P.Purifier(device=local, stream=sp.cuda_stream, precision=args.precision, **rule),
                       torch.empty((n, n), dtype=torch.float64).pin_memory()))
 
     def pipe_run(p, k, host, errs, launches, use):
-        sp, pp, Dp = pipes[p]
+        _, pp, Dp = pipes[p]
         try:
             for _ in range(k):
-                for q in range(p, len(work), use):
-                    i, sc = work[q]
-                    h = hs[i]
-                    pp.set_hamiltonian(Fh[i] if host else Fd[i], nocc=h.nocc, mu=0.0, lmin=h.lmin,
-                                       lmax=h.lmax, homo=h.homo, lumo=h.lumo)
-                    n_set = pp.stats()["kernel_launches"]
-                    if pp.run(sc, args.tol, 200) != P.OK:
-                        raise RuntimeError(f"{sc} did not converge")
-                    launches[p] += n_set + pp.stats()["kernel_launches"]
-                    if host:
-                        pp.density(Dp)
+                for i in range(p, len(hs), use):
+                    launches[p] += one_matrix(pp, i, host=host, Dout=Dp)
         except Exception as e:  # reported after the join
             errs.append(e)
 
@@ -576,45 +641,53 @@ def main():
         pp.close()
 
     pk, pk_kind = peaks()
-    steps_launched = args.steps
+    sm_mhz = (clocks or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     if args.precision == "mixed":
         achieved = acc["tensor_flops"] / acc["prod_s"] / 1e12
         peak = pk["bf16_tflops_sustained"]
+        at_clock = SMS * TENSOR_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_DIGIT_GEMM,
                 "kernel": "digit-plane tcgen05 product", "peak_kind": f"{pk_kind} bf16 sustained",
-                "traffic_source": TRAFFIC_SOURCE}
+                "traffic_source": TRAFFIC_SOURCE,
+                "tensor_pipe_pct_ncu": TENSOR_PIPE_PCT_NCU, "tensor_pipe_source": TENSOR_PIPE_SOURCE,
+                "per_clock": {"sm_mhz": sm_mhz, "peak_tflops_at_clock": at_clock,
+                              "frac": achieved / at_clock,
+                              "rate": f"{TENSOR_FLOP_PER_CLK_SM} dense bf16 flop per clock per SM "
+                                      f"x {SMS} SMs (the nominal dense rate)"}}
     else:
         achieved = acc["useful"] / acc["prod_s"] / 1e12
-        peak = pk["bf16_tflops_sustained"] * FP64_PER_BF16
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+        peak = SMS * FP64_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": "step_f64_kernel",
-                "peak_kind": f"{pk_kind} bf16 sustained x nominal fp64:bf16 (1.25/2250)"}
+                "peak_kind": f"float64 FMA pipe: {SMS} SMs x {FP64_FLOP_PER_CLK_SM // 2} DFMA per clock x 2 "
+                             f"x the median SM clock under load ({sm_mhz:.0f} MHz)"}
     line = {
         "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": main_config(n, len(hs), schemes, args.tol, args.precision, world),
+        "config": main_config(n, len(hs), schemes, args.tol, args.precision, world, args.exact_bounds),
         "clocks": clocks,
         "e2e": {"value": value_e2e, "unit": "matrices/s",
-                "h2d_bytes_per_step": per_step * n * n * 8,
+                "h2d_bytes_per_step": len(hs) * n * n * 8,
                 "d2h_bytes_per_step": per_step * n * n * 8,
                 "pipelines": ne2e, "serial_value": value_e2e_serial,
-                "note": "pinned host F in and D out through purify_set_hamiltonian / "
-                        "purify_get_density; `pipelines` handles, each on its own stream and "
-                        "host thread, share the step's purifications"},
+                "note": "pinned host F in (once per matrix) and D out (once per purification) through "
+                        "purify_set_hamiltonian / purify_get_density; `pipelines` handles, each on its own "
+                        "stream and host thread, share the step's matrices"},
         "gpu_launches": launches_timed,
         "pipelines": npipe,
         "single_handle": {"value": value1, "ms_per_step": ms1 / args.steps,
                           "note": "one handle, purifications in order; the roofline, per-product "
                                   "statistics and digit counts come from this run"},
         "roofline": roof,
-        "multiplications_per_step": acc["mults"] / steps_launched,
-        "useful_tflops": acc["useful"] / (ms * 1e-3) / 1e12,
+        "multiplications_per_step": acc["mults"] / args.steps,
+        "useful_tflops": acc["useful"] / (ms1 * 1e-3) / 1e12,
     }
     if args.precision == "mixed":
-        line["tensor_pipe_frac_of_step"] = acc["tensor_flops"] / (ms * 1e-3) / 1e12 / pk["bf16_tflops"]
+        line["tensor_pipe_pct_of_step_est"] = 100.0 * acc["tensor_flops"] / (ms1 * 1e-3) / (
+            SMS * TENSOR_FLOP_PER_CLK_SM * sm_mhz * 1e6)
         line["digit_max"] = acc["digit_max"]
         line["digit_rule"] = {"bits_floor": args.bits_floor or 30, "bits_gap": args.bits_gap or 26}
         shapes = {}
@@ -623,26 +696,55 @@ def main():
             if t is not None:
                 shapes[str(s_)] = {"kc": t[0], "split_ways": t[1]}
         line["launch_shapes"] = shapes if shapes else "fixed rule"
-    # max error against the plain float64 GPU recursion, and its throughput
+    # accuracy of every result: closed form, trace, idempotency, float64 path
+    Dc = []
+    for i, h in enumerate(hs):
+        occ = h.Q[:, torch.from_numpy(h.lam < 0.0).to(dev)]
+        Dc.append(occ @ occ.T)
+    ref = None
     if not args.no_fp64_check and args.precision == "mixed":
         ref = P.Purifier(device=local, stream=stream.cuda_stream, precision="fp64")
-        D1 = torch.empty((n, n), dtype=torch.float64, device=dev)
-        D2 = torch.empty((n, n), dtype=torch.float64, device=dev)
-        worst = 0.0
-        t64 = 0.0
-        for i, h in enumerate(hs):
-            for scheme in schemes:
-                one(h, Fd[i], scheme, D=D1)
-                ref.set_hamiltonian(Fd[i], nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax,
-                                    homo=h.homo, lumo=h.lumo)
-                ref.run(scheme, args.tol, 200)
-                t64 += ref.stats()["seconds"]
-                ref.density(D2)
-                worst = max(worst, float((D1 - D2).abs().max()))
+    results, t64 = accuracy_pass(P, pur, hs, Fd, Dc, schemes, args.tol, set_h, dev, ref=ref)
+    if ref:
         ref.close()
-        line["max_err_vs_fp64"] = worst
         line["fp64_path"] = {"value": per_step / t64, "unit": "matrices/s",
                              "note": "same schedules through the float64 SIMT path, same GPU"}
+    elif args.precision == "fp64":
+        for r in results:
+            r["max_err_vs_fp64"] = 0.0
+    accuracy = summarize_accuracy(results)
+    line["accuracy"] = accuracy
+    line["results"] = results
+    line["max_err_vs_fp64"] = accuracy["max_err_vs_fp64"]
+    if not accuracy["pass"]:
+        # the metric is defined at max-err <= 1e-6: no throughput without it
+        line["value_unchecked"] = line["value"]
+        line["value"] = None
+        line["e2e"]["value"] = None
+    # the whole path with other bounds / refinement settings, one pass each
+    if world == 1 and args.precision == "mixed" and not args.no_variants:
+        variants = {}
+        k_var = max(1, args.steps // 4)
+
+        def variant(name, exact, **opt):
+            pur.set_options(**opt)
+            step(exact=exact)                       # warm-up (allocations)
+            ms_v, _ = timed(k_var, exact=exact)
+            res, _ = accuracy_pass(P, pur, hs, Fd, Dc, schemes, args.tol,
+                                   lambda p, h, F: set_h(p, h, F, exact), dev)
+            pur.set_options(**{k: 0 for k in opt})
+            a = summarize_accuracy([dict(r, max_err_vs_fp64=0.0) for r in res])
+            variants[name] = {"value": per_step * k_var / (ms_v * 1e-3), "unit": "matrices/s",
+                              "ms_per_step": ms_v / k_var, "max_err_closed_form": a["max_err_closed_form"],
+                              "max_trace_err": a["max_trace_err"], "max_idem_err_fro": a["max_idem_err_fro"]}
+        variant("exact_bounds", not args.exact_bounds)
+        variant("refine_tc_6digits", args.exact_bounds, refine_squares=1)
+        variant("refine_fp64", args.exact_bounds, refine_fp64=1)
+        variants["note"] = ("one handle in order, the same 16 purifications: exact_bounds flips how "
+                            "lmin/lmax are obtained; refine_tc_6digits appends one McWeeny step at 6 digits "
+                            "on the tensor cores; refine_fp64 appends one float64 McWeeny step (two DFMA "
+                            "products) on the float64 pipe")
+        line["variants"] = variants
     if world == 1 and args.precision == "mixed" and not args.no_batch:
         line["batch"] = run_batch(P, dev, stream, count=args.batch_size)
     if world == 1 and args.precision == "mixed" and args.serve_rates:
@@ -651,7 +753,8 @@ def main():
     if world == 1 and args.precision == "mixed" and not args.no_lattice:
         line["lattice"] = run_lattice(P, dev, stream, L=args.lattice_size)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(hs, Fh[0].numpy(), args.tol)
+        line["cpu_baseline"] = cpu_baseline(hs, [F.numpy() for F in Fh], args.tol,
+                                            estimate_bounds=not args.exact_bounds)
     pur.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

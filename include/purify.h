@@ -50,6 +50,9 @@ extern "C" {
 #define PURIFY_ERR_DEVICE_TIMEOUT  -6  /* a bounded device-side wait ran out       */
 #define PURIFY_ERR_STATE           -7  /* call order (e.g. run before set)         */
 #define PURIFY_ERR_UNSUPPORTED     -8  /* no sm_103a device / feature not built    */
+#define PURIFY_ERR_INTERNAL        -9  /* a consistency check inside a kernel failed
+                                          (a library bug; purify_stats_t.device_flag
+                                          has the raw flag)                       */
 
 /* ---- schemes (Algorithm 1, Algorithm 2 and their reference forms) ------- */
 #define PURIFY_FIXED_MU_SF    0  /* Algorithm 1: P_{1,1}(alpha(X - I/2) + I/2)      */
@@ -136,7 +139,21 @@ typedef struct purify_options {
                             summation order of the inexact digit levels, so results
                             stay within the mixed path's tolerance; within a process
                             one shape per kind is used, so runs are reproducible    */
-    int reserved[4];
+    int wait_kcycles;    /* MIXED: bound of one device-side work wait of the product
+                            kernel (a stage, tensor-memory or work-claim hand-off), in
+                            thousands of SM cycles (0 = 2^31 cycles, about one second).
+                            A wait that runs out stops the kernel cleanly and the call
+                            returns PURIFY_ERR_DEVICE_TIMEOUT; waits for copies and
+                            MMAs already in flight at teardown keep the full bound.
+                            Short values exist to exercise failure detection; a
+                            nonzero value also disables autotune                   */
+    int host_schedule;   /* MIXED with PURIFY_BRANCH_TRACE: 1 = decide every step's
+                            branch and coefficients on the host (one device-to-host
+                            round trip per step); 0 (default) = a one-thread kernel
+                            decides them on the device from the previous product's
+                            float64 trace and the steps replay from a CUDA graph,
+                            with one host read per 16 steps                        */
+    int reserved[2];
     double trunc_tau;    /* block_sparse: per-step truncation budget: blocks of
                             smallest Frobenius norm are dropped while the dropped
                             mass (off-diagonal blocks twice) stays <= tau^2       */
@@ -169,7 +186,11 @@ typedef struct purify_stats_t {
     int product_launches;       /* matrix-product kernels among them (last run)          */
     int nnz_blocks;             /* block_sparse: upper 32 x 32 blocks of the result      */
     int digit_kc;               /* MIXED: k-chunk width of the last product launch        */
-    int reserved[3];
+    int device_flag;            /* MIXED: device error flag of the last run (0 = none;
+                                   bits 1, 2, 4, 16: a TMA-producer, MMA, epilogue or
+                                   work-claim wait gave up; bit 8: a tile's k-chunk
+                                   count and bitmask disagreed)                         */
+    int reserved[2];
     double product_seconds;     /* summed event time of the product launches
                                    (time_products = 1; else NaN)                         */
 } purify_stats_t;
@@ -259,6 +280,18 @@ int purify_get_density(purify_t h, double* D, int64_t ld);
 
 /* Copy the statistics of the last set/run into *out. */
 int purify_stats(purify_t h, purify_stats_t* out);
+
+/* Per-iteration reductions of the last purify_run, as the fused epilogue of
+ * each step's product reduced them in float64 (Eq. 1's X_i; for Algorithm 2
+ * the square of Eq. 4 / Eq. 5 is X_{i-1}^2):
+ *   trace[i] = trace(X_{i+1}) for i = 0 .. iterations-1,
+ *   idem[i]  = ||X_i - X_i^2||_F, the idempotency of the iterate that step
+ *              i + 1 squared (Algorithm 2 schemes; NaN for the fixed-mu
+ *              schemes, whose products square the scaled X_s).
+ * Refinement steps are not included.  Either array may be NULL; at most cap
+ * entries are written and *count receives the number of iterations.
+ * PURIFY_ERR_STATE before a successful run. */
+int purify_step_history(purify_t h, double* trace, double* idem, int cap, int* count);
 
 /* Device pointer of the handle's current density (n x n, leading dimension
  * n, float64), valid until the next set/run/destroy; NULL before a run. */
@@ -382,8 +415,10 @@ int64_t purify_batch_bytes_in_use(purify_batch_t b);
  * (128 KiB), which every GPU that loads the library holds until the process
  * exits.  n > PURIFY_GERSHGORIN_NOALLOC_MAX_N is rejected with
  * PURIFY_ERR_INVALID_ARG before anything is launched.  The first call on a
- * device looks up that array's device address (once per device, with the
- * device current); make that first call before any stream capture begins.
+ * device looks up that array's device address (once per device and CUDA
+ * context, with the device current; after a device reset or a recreated
+ * primary context the next call looks it up again); make that first call
+ * before any stream capture begins.
  * The work is queued on `stream` and the call returns without synchronising;
  * lohi (device, 2 doubles) is valid once the stream reaches that point.
  * Every call shares the one array and nothing in it needs to start at zero,

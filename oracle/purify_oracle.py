@@ -77,7 +77,7 @@ def P_ij(i: int, j: int, x):
     degree 1 + i + j with fixed points 0 and 1 and i and j vanishing
     derivatives there (the tests check this closed form against that
     definition).  Evaluated with a Horner sum in t = 1 - x, then the power of x
-    by repeated multiplication (the library uses the same order)."""
+    by repeated multiplication."""
     t = 1.0 - x
     acc = 0.0 * x
     for k in range(j, -1, -1):
@@ -210,8 +210,9 @@ def pmm_schedule(m: int, beta: float, tol: float, max_iter: int, scaled: bool = 
     return alphas, betas
 
 
-# Matrix products per iteration of the fixed-mu scheme with P_{m,m}: m = 1 as
-# in Algorithm 1 (X_s^2, then X_s^2 X_s); m = 3 as the library evaluates
+# Matrix products per iteration of the fixed-mu scheme with P_{m,m} (a
+# reading: the paper counts products only for m = 1): m = 1 as in Algorithm 1
+# (X_s^2, then X_s^2 X_s); m = 3 for the evaluation order of
 # P_{3,3}(x) = x^4 (35 - 84 x + 70 x^2 - 20 x^3): V = 70 X_s - 20 X_s^2,
 # Q = X_s V - 84 X_s + 35 I, S = X_s^2, T = S^2, X = T Q.
 PMM_PRODUCTS = {1: 2, 3: 5}
@@ -332,7 +333,8 @@ def purify_fixed_mu_pij(F, lmin, lmax, mu, homo, lumo, i: int, j: int, tol=1e-12
     return X, res
 
 
-# Products per iteration as the library evaluates them: P_{3,1} = x^4 (5 - 4x):
+# Products per iteration for these evaluation orders (a reading, as for
+# P_{m,m}): P_{3,1} = x^4 (5 - 4x):
 # S = X^2, T = S^2, X = 5 T - 4 T X; P_{1,3} = x^2 (10 - 20x + 15x^2 - 4x^3):
 # V = 15 X - 4 X^2, Q = X V - 20 X + 10 I, S = X^2, X = S Q.
 PIJ_PRODUCTS = {(1, 1): 2, (3, 3): 5, (3, 1): 3, (1, 3): 4}
@@ -389,7 +391,7 @@ def tc_map(branch: str, alpha: float, x: float) -> float:
     if branch == "P10":
         y = (1.0 + alpha) * x - alpha
         return y * y
-    return 2.0 * (1.0 + alpha) * x - (1.0 + alpha) * (1.0 + alpha) * x * x
+    return 2.0 * (1.0 + alpha) * x - (1.0 + alpha) ** 2 * x * x
 
 
 def tc_schedule(beta: float, betabar: float, tol: float, max_iter: int, scaled: bool = True):
@@ -442,9 +444,9 @@ def purify_tc(F, lmin, lmax, homo=None, lumo=None, tol=1e-12, max_iter=200, scal
         res.idem.append(float(np.linalg.norm(X - X2)))
         if branch == "P10":
             # ((1 + alpha) X - alpha I)^2 expanded over the square X^2
-            X = (1.0 + alpha) * (1.0 + alpha) * X2 - 2.0 * alpha * (1.0 + alpha) * X + alpha * alpha * I
+            X = (1.0 + alpha) ** 2 * X2 - 2.0 * alpha * (1.0 + alpha) * X + alpha * alpha * I
         else:
-            X = 2.0 * (1.0 + alpha) * X - (1.0 + alpha) * (1.0 + alpha) * X2
+            X = 2.0 * (1.0 + alpha) * X - (1.0 + alpha) ** 2 * X2
         if have_bounds:
             beta, betabar = tc_map(branch, alpha, beta), tc_map(branch, alpha, betabar)
         res.alphas.append(alpha)
@@ -774,9 +776,9 @@ def purify_tc_truncated(F, lmin, lmax, homo, lumo, tau, tol=1e-9, max_iter=200, 
         X2 = X @ X
         res.idem.append(float(np.linalg.norm(X - X2)))
         if branch == "P10":
-            X = (1.0 + alpha) * (1.0 + alpha) * X2 - 2.0 * alpha * (1.0 + alpha) * X + alpha * alpha * I
+            X = (1.0 + alpha) ** 2 * X2 - 2.0 * alpha * (1.0 + alpha) * X + alpha * alpha * I
         else:
-            X = 2.0 * (1.0 + alpha) * X - (1.0 + alpha) * (1.0 + alpha) * X2
+            X = 2.0 * (1.0 + alpha) * X - (1.0 + alpha) ** 2 * X2
         X, keep = truncate_blocks(X, tau, bs)
         nnzb.append(int(np.triu(keep).sum()))
         res.alphas.append(alpha)

@@ -24,6 +24,7 @@ ERR_CUDA = -5
 ERR_DEVICE_TIMEOUT = -6
 ERR_STATE = -7
 ERR_UNSUPPORTED = -8
+ERR_INTERNAL = -9
 
 SCHEMES = {"FIXED_MU_SF": 0, "FIXED_MU_MONO": 1, "TC_SF": 2, "TC_MONO": 3, "FIXED_MU_P33_SF": 4,
            "FIXED_MU_P33_MONO": 5, "FIXED_MU_P13_SF": 6, "FIXED_MU_P13_MONO": 7, "FIXED_MU_P31_SF": 8,
@@ -35,7 +36,7 @@ EXPORTED = (
     "purify_options_default", "purify_create", "purify_destroy", "purify_set_options",
     "purify_set_hamiltonian", "purify_set_hamiltonian_coo", "purify_block_history", "purify_estimate_gap",
     "purify_tuned_shape", "purify_k_split_plan",
-    "purify_run", "purify_get_density", "purify_stats",
+    "purify_run", "purify_get_density", "purify_stats", "purify_step_history",
     "purify_density_device_ptr", "purify_strerror", "purify_schedule", "purify_tridiag_eig",
     "purify_k_symm_product_f64", "purify_k_step_f64", "purify_k_gershgorin_f64",
     "purify_k_lanczos_f64", "purify_k_digit_product_f64", "purify_k_gershgorin_f64_noalloc",
@@ -55,7 +56,7 @@ class Options(C.Structure):
                 ("refine_squares", C.c_int), ("digits", C.c_int), ("time_products", C.c_int),
                 ("block_sparse", C.c_int), ("split_k", C.c_int), ("refine_fp64", C.c_int),
                 ("bits_floor", C.c_int), ("bits_gap", C.c_int), ("autotune", C.c_int),
-                ("reserved", C.c_int * 4),
+                ("wait_kcycles", C.c_int), ("host_schedule", C.c_int), ("reserved", C.c_int * 2),
                 ("trunc_tau", C.c_double), ("trunc_budget", C.c_double)]
 
 
@@ -68,7 +69,7 @@ class Stats(C.Structure):
                 ("useful_flops", C.c_double), ("tensor_flops", C.c_double),
                 ("digit_max", C.c_int), ("kernel_launches", C.c_int),
                 ("product_launches", C.c_int), ("nnz_blocks", C.c_int), ("digit_kc", C.c_int),
-                ("reserved", C.c_int * 3),
+                ("device_flag", C.c_int), ("reserved", C.c_int * 2),
                 ("product_seconds", C.c_double)]
 
     def as_dict(self) -> dict:
@@ -108,6 +109,7 @@ def load(path: str = LIB_PATH):
         "purify_estimate_gap": (ip, [vp, ip, dp, dp]),
         "purify_get_density": (ip, [vp, vp, i64]),
         "purify_stats": (ip, [vp, C.POINTER(Stats)]),
+        "purify_step_history": (ip, [vp, dp, dp, ip, C.POINTER(C.c_int)]),
         "purify_density_device_ptr": (vp, [vp]),
         "purify_strerror": (C.c_char_p, [ip]),
         "purify_schedule": (ip, [ip, dbl, dbl, dbl, dbl, dbl, dbl, ip, dp, C.POINTER(C.c_int), dp,
@@ -197,7 +199,7 @@ class Purifier:
                  digits: int = 0, time_products: bool = False, block_sparse: bool = False,
                  trunc_tau: float = 1e-6, split_k: bool = True, refine_fp64: int = 0,
                  trunc_budget: float = 0.0, bits_floor: int = 0, bits_gap: int = 0,
-                 autotune: bool = False):
+                 autotune: bool = False, wait_kcycles: int = 0, host_schedule: bool = False):
         lib = load()
         self._lib = lib
         self.options = Options()
@@ -216,6 +218,8 @@ class Purifier:
         self.options.bits_floor = int(bits_floor)
         self.options.bits_gap = int(bits_gap)
         self.options.autotune = int(autotune)
+        self.options.wait_kcycles = int(wait_kcycles)
+        self.options.host_schedule = int(host_schedule)
         h = C.c_void_p()
         _check(lib.purify_create(C.byref(h), device, _caller_stream(stream), C.byref(self.options)),
                "purify_create")
@@ -314,6 +318,18 @@ class Purifier:
         s = Stats()
         _check(self._lib.purify_stats(self._h, C.byref(s)), "purify_stats")
         return s.as_dict()
+
+    def step_history(self):
+        """Per-iteration reductions of the last run: (trace(X_i), ||X_{i-1} -
+        X_{i-1}^2||_F) as two float64 arrays (the second NaN for fixed-mu)."""
+        cnt = C.c_int(0)
+        _check(self._lib.purify_step_history(self._h, None, None, 0, C.byref(cnt)), "purify_step_history")
+        m = cnt.value
+        tr = np.zeros(max(m, 1))
+        idem = np.zeros(max(m, 1))
+        _check(self._lib.purify_step_history(self._h, _dptr(tr), _dptr(idem), m, C.byref(cnt)),
+               "purify_step_history")
+        return tr[:m], idem[:m]
 
 
 # ---------------------------------------------------------------------------
@@ -442,12 +458,13 @@ def batch_footprint(n: int) -> int:
 class Batch:
     """A libpurify batch: many purifications of uneven size on one device."""
 
-    def __init__(self, device: int = 0, stream: int | None = None, digits: int = 0):
+    def __init__(self, device: int = 0, stream: int | None = None, digits: int = 0, wait_kcycles: int = 0):
         lib = load()
         self._lib = lib
         o = Options()
         lib.purify_options_default(C.byref(o))
         o.digits = digits
+        o.wait_kcycles = int(wait_kcycles)
         h = C.c_void_p()
         _check(lib.purify_batch_create(C.byref(h), device, _caller_stream(stream), C.byref(o)),
                "purify_batch_create")

@@ -100,11 +100,11 @@ int64_t footprint(int64_t n, int digits) {
 // Algorithm 2 coefficients: Y = cP X^2 + cE X + cI I.
 void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
     if (branch) {
-        *cP = (1.0 + a) * (1.0 + a);
+        *cP = sq1p(a);
         *cE = -2.0 * a * (1.0 + a);
         *cI = a * a;
     } else {
-        *cP = -(1.0 + a) * (1.0 + a);
+        *cP = -sq1p(a);
         *cE = 2.0 * (1.0 + a);
         *cI = 0.0;
     }
@@ -288,7 +288,8 @@ int launch_groups(purify_batch* B, const std::vector<GroupPlan>& groups) {
     const uint8_t* dev = (const uint8_t*)B->dev_buf;
     for (const GroupPlan& g : groups)
         PURIFY_TRY(launch_digit_group(g.s, g.steps.data(), (int)g.steps.size(), (const int4*)(dev + g.work_off),
-                                      g.items, B->scratch, B->ctas, B->err, B->stream));
+                                      g.items, B->scratch, B->ctas, B->err, B->stream,
+                                      1000ll * B->opt.wait_kcycles));
     return PURIFY_OK;
 }
 
@@ -304,7 +305,7 @@ int check_err(purify_batch* B) {
     int e = 0;
     PURIFY_CUDA_TRY(cudaMemcpyAsync(&e, B->err, sizeof(int), cudaMemcpyDeviceToHost, B->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(B->stream));
-    return e ? PURIFY_ERR_DEVICE_TIMEOUT : PURIFY_OK;
+    return device_flag_status(e);
 }
 
 }  // namespace

@@ -69,6 +69,9 @@ constexpr int MAX_REGS = (16384 / (32 * ((NTHREADS / 32 + 3) / 4))) / 8 * 8;
 constexpr int EW = 8;            // epilogue columns per pass (a multiple of 8)
 constexpr int BAR_AREA = 512;    // bytes of barriers and flags after the operand stages
 constexpr long long WAIT_CYCLES = 1ll << 31;  // one wait gives up after ~1 s at 2 GHz
+// Bits of the device error flag (OR-ed into *L.err): which role's wait gave
+// up, and the internal check that a tile's k-chunk count matches its bitmask.
+constexpr int ERR_PRODUCER_WAIT = 1, ERR_MMA_WAIT = 2, ERR_EPI_WAIT = 4, ERR_PLAN = 8, ERR_CLAIM_WAIT = 16;
 
 // ---- PTX wrappers ------------------------------------------------------------
 
@@ -239,6 +242,12 @@ __device__ __forceinline__ df df_mul(df x, df y) {
 
 __device__ __forceinline__ df df_scale(df x, float pow2) { return {x.h * pow2, x.l * pow2}; }
 
+// float64 -> double-float: the nearest float and the float of the remainder
+__device__ __forceinline__ df dev_df(double x) {
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+}
+
 // ---- digits: float32 additions and bit operations only ---------------------
 // (both exact for digits, so no rounding or conversion instruction is needed)
 
@@ -286,6 +295,8 @@ struct DigitGemmParams {
     int kc_words;
     float* bnorm2;
     int nb;
+    // device-side control of a single product (null: the fields above)
+    const DevStep* ctl;
 };
 
 // Products per launch whose tensor maps and parameters travel as kernel
@@ -315,7 +326,10 @@ struct DigitLaunch {
     int num_items;                   // work items: tiles, tile parts (single) or list entries (group)
     int stages;                      // depth of the shared-memory ring
     float2* scratch;                 // per CTA 128 x 128 double-float tile
-    int* err;                        // device error flag
+    int* err;                        // device error flag (ERR_* bits)
+    long long wait_cycles;           // bound of one work wait (claim, stage, tensor-memory
+                                     // hand-offs); the waits for copies and MMAs in flight at
+                                     // teardown keep WAIT_CYCLES
     int split_begin;                 // single launches: first split tile (== tiles: none)
     int split_ways;                  // parts per split tile (1: none)
     float* partial;                  // [slot][part][region 8][acc 4][16-col group 4][row 32][16]
@@ -403,10 +417,10 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 }
 
 // Bounded wait measured from its own start: false when it gives up.
-__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, long long limit = WAIT_CYCLES) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > WAIT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -441,6 +455,14 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int num_items = L.num_items;
+    const long long wait = L.wait_cycles > 0 ? L.wait_cycles : WAIT_CYCLES;
+    // a step controlled on the device: only the launch whose digit count the
+    // schedule chose runs, and none once the run has stopped (uniform over
+    // the grid: the control was written by an earlier kernel)
+    if (L.prms[0].ctl) {
+        const DevStep* c = L.prms[0].ctl;
+        if (c->done || c->s_in != S) return;
+    }
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2 * stages; ++i) mbar_init(smem_u32(&bars[i]), 1);
@@ -473,8 +495,8 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
     };
     auto consumer_take = [&]() -> int {  // one thread per role
         if (n_claims >= MAX_CLAIMS || *abort_flag) return -1;
-        if (!mbar_wait_for(smem_u32(&claim_bar[n_claims]), 0)) {
-            atomicExch(L.err, 5);
+        if (!mbar_wait_for(smem_u32(&claim_bar[n_claims]), 0, wait)) {
+            atomicOr(L.err, ERR_CLAIM_WAIT);
             *abort_flag = 1;
             return -1;
         }
@@ -515,7 +537,7 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     if (km) {
                         while (bits == 0ull && w + 1 < Pg.kc_words) bits = km[++w];
                         if (bits == 0ull) {  // count and mask disagree
-                            atomicExch(L.err, 4);
+                            atomicOr(L.err, ERR_PLAN);
                             *abort_flag = 1;
                             break;
                         }
@@ -523,8 +545,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                         bits &= bits - 1;
                     }
                     const int st = it % stages;
-                    if (it >= stages && !mbar_wait_for(smem_u32(&empty_bar[st]), (uint32_t)(((it / stages) & 1) ^ 1))) {
-                        atomicExch(L.err, 1);
+                    if (it >= stages &&
+                        !mbar_wait_for(smem_u32(&empty_bar[st]), (uint32_t)(((it / stages) & 1) ^ 1), wait)) {
+                        atomicOr(L.err, ERR_PRODUCER_WAIT);
                         *abort_flag = 1;
                         break;
                     }
@@ -564,14 +587,14 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 int kb, nk;
                 dense_k_range(L, Pg.n_pad / KC, slot, part, kb, nk);
                 if (nl >= 0) nk = nl;
-                if (lt > 0 && !mbar_wait_for(smem_u32(tmem_empty), (uint32_t)((lt - 1) & 1))) {
+                if (lt > 0 && !mbar_wait_for(smem_u32(tmem_empty), (uint32_t)((lt - 1) & 1), wait)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int st = it % stages;
-                    if (!mbar_wait_for(smem_u32(&full_bar[st]), (uint32_t)((it / stages) & 1)) || *abort_flag) {
+                    if (!mbar_wait_for(smem_u32(&full_bar[st]), (uint32_t)((it / stages) & 1), wait) || *abort_flag) {
                         ok = false;
                         break;
                     }
@@ -601,7 +624,7 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 mma_commit(smem_u32(tmem_full));
             }
             if (!ok) {
-                atomicExch(L.err, 2);
+                atomicOr(L.err, ERR_MMA_WAIT);
                 *abort_flag = 1;
             }
             // every MMA this thread issued has completed before teardown
@@ -629,9 +652,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             item_of(L, t, g, ti, tj, slot, part);
             const DigitGemmParams& P = params_of(L, g);
             const size_t plane = (size_t)P.n_pad * P.n_pad;
-            bool ready = mbar_wait_for(smem_u32(tmem_full), (uint32_t)(lt & 1));
+            bool ready = mbar_wait_for(smem_u32(tmem_full), (uint32_t)(lt & 1), wait);
             if (!ready) {
-                atomicExch(L.err, 3);
+                atomicOr(L.err, ERR_EPI_WAIT);
                 *abort_flag = 1;
             }
             // tcgen05.ld is warp-collective: decide once per warp
@@ -771,12 +794,21 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             const bool use_E = P.use_E, affine = P.affine_out;
             const __nv_bfloat16* const Ain = P.A;
             const float scale_in_h = P.scale_in_h, e_scale = P.e_scale;
-            const df cP = P.cP, cE = P.cE, cI = P.cI, dY = P.dY, dI = P.dI;
+            df cP = P.cP, cE = P.cE, cI = P.cI;
+            const df dY = P.dY, dI = P.dI;
             const bool want_bn = P.bnorm2 != nullptr, want_red = P.red != nullptr;
-            double* const out64 = P.out64;
-            __nv_bfloat16* const outp = P.out;
+            double* out64 = P.out64;
+            __nv_bfloat16* outp = P.out;
             const float out_digit_scale = P.out_digit_scale, out_rscale = P.out_rscale;
-            const int s_out = P.s_out;
+            int s_out = P.s_out;
+            if (P.ctl) {  // this step's coefficients and outputs, chosen on the device
+                cP = dev_df(P.ctl->cP);
+                cE = dev_df(P.ctl->cE);
+                cI = dev_df(P.ctl->cI);
+                s_out = P.ctl->s_out;
+                if (s_out == 0) outp = nullptr;
+                if (!P.ctl->write64) out64 = nullptr;
+            }
             double s_tr = 0.0;  // the trace decides the occupation check: float64
             float s_idem = 0.f, s_fro = 0.f;
             float bn2_0 = 0.f, bn2_1 = 0.f;  // this row's share of two 32 x 32 output blocks

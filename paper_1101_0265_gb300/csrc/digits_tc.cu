@@ -51,55 +51,89 @@ __device__ __noinline__ df split_double_slow(double x) {
     return {h, (float)(x - (double)h)};
 }
 
-// One warp per 32 x 32 block (lanes on columns, loop over the 32 rows):
-// coalesced row segments of F, and, when bnorm2 is not null, the block's
-// ||.||_F^2 (float, in a fixed order) for blocks I <= J.
+// One warp per strip of 32 rows x 128 columns, each lane on four consecutive
+// columns: 32-byte pieces of F's rows per lane (two 16-byte loads when F's
+// rows are 16-byte aligned), one 8-byte store per digit plane and row, and,
+// when bnorm2 is not null, ||.||_F^2 of the strip's four 32 x 32 blocks
+// (float, in a fixed order) for blocks I <= J.
+__device__ __forceinline__ df split_entry(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const int E = (int)((u >> 52) & 0x7FF) - 1023;
+    // zeros (most of a sparse F) and normal magnitudes stay off the float64 pipe
+    if ((u << 1) == 0) return {0.f, 0.f};
+    return (E >= -74 && E <= 127) ? split_double_bits(u) : split_double_slow(x);
+}
+
 __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ F, int64_t ldf, int n, int n_pad,
                                                     df a, df b, float digit_scale, float rscale, int s,
                                                     __nv_bfloat16* __restrict__ out, double* red,
                                                     float* __restrict__ bnorm2) {
-    const int nb = n_pad / 32;  // nb^2 <= 2^24: 32-bit block indices
+    const int nb = n_pad / 32, ns = n_pad / 128;  // nb^2 <= 2^24: 32-bit block indices
     const int64_t total = (int64_t)n_pad * n_pad;
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
+    const bool vec = (ldf & 1) == 0 && ((uintptr_t)F & 15) == 0;
+    const float rinv = 1.f / rscale;
     float tr = 0.f;
-    for (int blk = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); blk < nb * nb; blk += warps) {
-        const int I = blk / nb, J = blk - I * nb;
-        const int j = J * 32 + lane;
+    for (int strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); strip < nb * ns; strip += warps) {
+        const int I = strip / ns, Jq = strip - I * ns;
+        const int j0 = Jq * 128 + lane * 4;
         float bsum = 0.f;
-#pragma unroll 4
-        for (int r = 0; r < 32; ++r) {  // four rows' loads in flight per warp
+#pragma unroll 2
+        for (int r = 0; r < 32; ++r) {  // two rows' loads in flight per warp
             const int i = I * 32 + r;
-            df z = {0.f, 0.f};
-            if (i < n && j < n) {
-                const double x = F[(int64_t)i * ldf + j];
-                const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-                const int E = (int)((u >> 52) & 0x7FF) - 1023;
-                // zeros (most of a sparse F) and normal magnitudes stay off the
-                // float64 pipe
-                df xv = {0.f, 0.f};
-                if ((u << 1) != 0) xv = (E >= -74 && E <= 127) ? split_double_bits(u) : split_double_slow(x);
-                z = df_mul(a, xv);
-                if (i == j) {
-                    z = df_add(z, b);
-                    tr += z.h + z.l;
+            double x[4] = {0.0, 0.0, 0.0, 0.0};
+            if (i < n) {
+                const double* row = F + (int64_t)i * ldf + j0;
+                if (vec && j0 + 3 < n) {
+                    const double2 u0 = __ldg((const double2*)row), u1 = __ldg((const double2*)row + 1);
+                    x[0] = u0.x;
+                    x[1] = u0.y;
+                    x[2] = u1.x;
+                    x[3] = u1.y;
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (j0 + c < n) x[c] = __ldg(row + c);
                 }
             }
-            bsum += z.h * z.h;
-            z = df_scale(z, digit_scale);
+            df z[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = j0 + c;
+                z[c] = {0.f, 0.f};
+                if (i < n && j < n) {
+                    z[c] = df_mul(a, split_entry(x[c]));
+                    if (i == j) {
+                        z[c] = df_add(z[c], b);
+                        tr += z[c].h + z[c].l;
+                    }
+                }
+                bsum += z[c].h * z[c].h;
+                z[c] = df_scale(z[c], digit_scale);
+            }
+            __nv_bfloat16* dst = out + (size_t)i * n_pad + j0;
             float plane_scale = 1.f;
-            const size_t at = (size_t)i * n_pad + j;
             for (int p = 0; p < s; ++p) {
-                const float d = round_digit(z.h);
-                z = two_sum(__fsub_rn(z.h, d), z.l);
-                out[(size_t)p * total + at] = digit_to_bf16(d * plane_scale);
-                z = df_scale(z, rscale);
-                plane_scale *= (1.f / rscale);
+                __align__(8) __nv_bfloat16 dv[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float d = round_digit(z[c].h);
+                    z[c] = two_sum(__fsub_rn(z[c].h, d), z[c].l);
+                    dv[c] = digit_to_bf16(d * plane_scale);
+                    z[c] = df_scale(z[c], rscale);
+                }
+                *(uint2*)(dst + (size_t)p * total) = *(const uint2*)dv;
+                plane_scale *= rinv;
             }
         }
         if (bnorm2) {
-            bsum = warp_sum_f(bsum);
-            if (lane == 0 && I <= J) bnorm2[(size_t)I * nb + J] = bsum;
+            // lanes 8q .. 8q + 7 hold block column Jq * 4 + q
+            bsum += __shfl_xor_sync(0xffffffffu, bsum, 4);
+            bsum += __shfl_xor_sync(0xffffffffu, bsum, 2);
+            bsum += __shfl_xor_sync(0xffffffffu, bsum, 1);
+            const int J = Jq * 4 + (lane >> 3);
+            if ((lane & 7) == 0 && I <= J) bnorm2[(size_t)I * nb + J] = bsum;
         }
     }
     if (red) {
@@ -263,6 +297,7 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
     p->kc_words = (st.n_pad / 32 + 63) / 64;
     p->bnorm2 = st.bnorm2;
     p->nb = st.n_pad / 32;
+    p->ctl = st.ctl;
     if (st.kc_cnt && !st.kc_mask) return PURIFY_ERR_INVALID_ARG;
     if ((st.kc_cnt || st.bnorm2) && kc != 32) return PURIFY_ERR_INVALID_ARG;
     return PURIFY_OK;
@@ -306,6 +341,7 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
     L.stages = digit_stages(st.s_in, kc);
     L.scratch = st.scratch;
     L.err = st.err;
+    L.wait_cycles = st.wait_cycles;
     if (!st.scratch || !st.err) return PURIFY_ERR_INVALID_ARG;
     L.split_begin = tiles;
     L.split_ways = 1;
@@ -343,7 +379,7 @@ int launch_digit_step(const DigitStep& st, cudaStream_t stream) {
 }
 
 int launch_digit_group(int s, const DigitStep* steps, int count, const int4* work, int num_items,
-                       float2* scratch, int max_ctas, int* err, cudaStream_t stream) {
+                       float2* scratch, int max_ctas, int* err, cudaStream_t stream, long long wait_cycles) {
     if (s < 1 || s > kMaxDigitPlanes || count < 1 || count > GMAX || !work || !scratch || !err)
         return PURIFY_ERR_INVALID_ARG;
     if (num_items <= 0) return PURIFY_OK;
@@ -362,6 +398,7 @@ int launch_digit_group(int s, const DigitStep* steps, int count, const int4* wor
     L.stages = digit_stages(s, kc);
     L.scratch = scratch;
     L.err = err;
+    L.wait_cycles = wait_cycles;
     L.split_begin = num_items;  // grouped launches are not split
     L.split_ways = 1;
     const int grid = num_items < max_ctas ? num_items : max_ctas;
@@ -370,11 +407,11 @@ int launch_digit_group(int s, const DigitStep* steps, int count, const int4* wor
 
 int launch_split(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s,
                  int rbits, __nv_bfloat16* out, double* red, cudaStream_t stream, float* bnorm2) {
-    if (s < 1 || s > kMaxDigitPlanes || n <= 0 || n_pad < n || n_pad % 32 || n_pad > (1 << 17) || rbits < 4 ||
+    if (s < 1 || s > kMaxDigitPlanes || n <= 0 || n_pad < n || n_pad % 128 || n_pad > (1 << 17) || rbits < 4 ||
         rbits > 8)
         return PURIFY_ERR_INVALID_ARG;
-    const int64_t nb = n_pad / 32;
-    int64_t blocks = (nb * nb + 7) / 8;  // 8 warps per CTA, one 32 x 32 block each
+    const int64_t strips = (int64_t)(n_pad / 32) * (n_pad / 128);
+    int64_t blocks = (strips + 7) / 8;  // 8 warps per CTA, one 32 x 128 strip each
     if (blocks > 152 * 8) blocks = 152 * 8;
     split_kernel<<<(unsigned)blocks, 256, 0, stream>>>(F, ldf, n, n_pad, to_df(a), to_df(b), ldexpf(1.f, 8 - e),
                                                         ldexpf(1.f, rbits), s, out, red, bnorm2);

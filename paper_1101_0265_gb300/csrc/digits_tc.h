@@ -10,6 +10,20 @@ namespace purify {
 
 constexpr int kMaxDigitPlanes = 6;
 
+// Control of one product written on the device by the trace-rule schedule
+// kernel (trace_sched.cu), so that a whole run can be replayed from a CUDA
+// graph with no host decision between steps.  A launch that carries it runs
+// only when s_in is its digit count and done is 0 (every other launch of the
+// step exits at once); it takes its coefficients, output digit count and
+// float64-output switch from here instead of its parameters.
+struct DevStep {
+    double cP, cE, cI;  // Y = cP P + cE E + cI I
+    int s_in;           // digit planes of the operands
+    int s_out;          // digit planes of the output (0: none)
+    int write64;        // 1: write the float64 result
+    int done;           // 1: the run has stopped
+};
+
 // One fused step: P = A B (A, B symmetric, held as s_in digit planes each,
 // scale exponents eA, eB), Y = cP P + cE E + cI I with E = A when use_E,
 // out = dY Y + dI I written as s_out digit planes with exponent e_out and
@@ -45,6 +59,10 @@ struct DigitStep {
     // rule (digit_kc, digit_split_plan)
     int kc = 0;
     int split_ways = 0;
+    // bound of the kernel's work waits in SM cycles (0: about one second)
+    long long wait_cycles = 0;
+    // device-side control (null: the fields above decide)
+    const DevStep* ctl = nullptr;
 };
 
 // Epilogue warps of the product kernel (each owns a 32-row x (512 / kEpiWarps)
@@ -71,7 +89,8 @@ int prepare_digit_kernels();
 // `count` <= 64 products that all have s digits; their tensor maps and
 // parameters are passed by value.
 int launch_digit_group(int s, const DigitStep* steps, int count, const int4* work, int num_items,
-                       float2* scratch, int max_ctas, int* err, cudaStream_t stream);
+                       float2* scratch, int max_ctas, int* err, cudaStream_t stream,
+                       long long wait_cycles = 0);
 
 // Products per grouped launch.
 constexpr int kGroupMax = 64;

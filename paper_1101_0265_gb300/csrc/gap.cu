@@ -383,6 +383,7 @@ extern "C" int purify_estimate_gap(purify_t h, int lanczos_steps, double* homo_o
                 st.partial = ms->partial;
                 st.split_cnt = ms->split_cnt;
             }
+            st.wait_cycles = 1000ll * h->opt.wait_kcycles;
             r = launch_digit_step(st, s);
         } else {
             const double* Xi = Xf[(i + 1) & 1];
@@ -443,7 +444,8 @@ extern "C" int purify_estimate_gap(purify_t h, int lanczos_steps, double* homo_o
         PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, h->mixed->err, sizeof(int), cudaMemcpyDeviceToHost, s));
         PURIFY_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    if (err) return PURIFY_ERR_DEVICE_TIMEOUT;
+    h->st.device_flag = err;
+    if (err) return device_flag_status(err);
     if (rc == PURIFY_OK) {
         h->b.homo = homo;
         h->b.lumo = lumo;

@@ -27,6 +27,15 @@ int cuda_status(cudaError_t e, const char* what);
         if (r_ != PURIFY_OK) return r_;                                        \
     } while (0)
 
+// Status of a product kernel's device error flag: bit 8 is the internal check
+// that a tile's k-chunk count matches its bitmask (a library bug, not a
+// timeout); the other bits name bounded waits that gave up.
+constexpr int kDeviceFlagPlan = 8;
+inline int device_flag_status(int flag) {
+    if (flag == 0) return PURIFY_OK;
+    return (flag & kDeviceFlagPlan) ? PURIFY_ERR_INTERNAL : PURIFY_ERR_DEVICE_TIMEOUT;
+}
+
 // Number of upper-triangle tiles (ti <= tj) for a T x T tile grid.
 inline int64_t upper_tiles(int64_t T) { return T * (T + 1) / 2; }
 
@@ -81,6 +90,8 @@ void tridiag_eig_full(const double* a, const double* b, int m, std::vector<doubl
 // Algorithm 2's scalar pieces (float64, host): alpha of a branch (1 = P_{1,0},
 // 0 = P_{0,1}) and the branch's map of a scalar (Eq. 4 / Eq. 5).
 double tc_alpha(int branch, double b, double bb);
+// (1 + a)^2 of Eq. 4 / Eq. 5, evaluated by the C library's pow.
+double sq1p(double a);
 double tc_map(int branch, double a, double x);
 // The fixed-mu polynomial order of a scheme (1: P_{1,1}, 3: P_{3,3}), its
 // products per iteration, P_{i,j} on a scalar and the P_{m,m} scaling alpha.
@@ -125,6 +136,8 @@ struct purify_ctx {
     std::vector<cudaEvent_t> pev;  // product timing events (pairs)
     int pev_used = 0;
     purify::MixedState* mixed = nullptr;
+    // per-iteration reductions of the last run (purify_step_history)
+    std::vector<double> hist_trace, hist_idem;
 };
 
 namespace purify {

@@ -4,6 +4,8 @@
 //
 // Both kernels stream F once per pass and are bound by HBM bandwidth: one
 // warp per row reads the row with coalesced 8-byte loads.
+#include <cuda.h>
+
 #include "internal.h"
 
 #include <cmath>
@@ -283,21 +285,64 @@ static __device__ __align__(256) double g_gershgorin_scratch[2 * ((kNoAllocMaxN 
 
 std::mutex g_scratch_mu;
 constexpr int kMaxDevices = 64;
-double* g_scratch_dev[kMaxDevices] = {};
+// Per device: the context the address was looked up in (its unique ID) and
+// the address.  A device reset or a recreated primary context gives a new
+// context ID, so the lookup is repeated instead of reusing a dead address.
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    double* ptr;
+};
+ScratchAddr g_scratch_dev[kMaxDevices] = {};
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+// Unique ID of the calling thread's current context (driver entry points
+// fetched through the runtime, so the library links no driver library);
+// *have = false when no context is current yet.
+int current_context_id(unsigned long long* id, bool* have) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = (CtxGetCurrentFn)p;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (CtxGetIdFn)p;
+    });
+    if (!get_current || !get_id) return PURIFY_ERR_UNSUPPORTED;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS) return PURIFY_ERR_CUDA;
+    *have = ctx != nullptr;
+    if (ctx && get_id(ctx, id) != CUDA_SUCCESS) return PURIFY_ERR_CUDA;
+    return PURIFY_OK;
+}
 
 // Device address of the static scratch on the current device, looked up once
-// per device.
+// per device and context.
 int noalloc_scratch(double** out) {
     int dev = 0;
     PURIFY_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return PURIFY_ERR_UNSUPPORTED;
+    unsigned long long id = 0;
+    bool have = false;
+    PURIFY_TRY(current_context_id(&id, &have));
     std::lock_guard<std::mutex> g(g_scratch_mu);
-    if (!g_scratch_dev[dev]) {
+    ScratchAddr& a = g_scratch_dev[dev];
+    if (!have || !a.ptr || a.ctx_id != id) {
+        // the lookup makes the device's primary context current if none was
         void* p = nullptr;
         PURIFY_CUDA_TRY(cudaGetSymbolAddress(&p, g_gershgorin_scratch));
-        g_scratch_dev[dev] = (double*)p;
+        PURIFY_TRY(current_context_id(&id, &have));
+        if (!have) return PURIFY_ERR_CUDA;
+        a.ptr = (double*)p;
+        a.ctx_id = id;
     }
-    *out = g_scratch_dev[dev];
+    *out = a.ptr;
     return PURIFY_OK;
 }
 

@@ -37,6 +37,8 @@ void mixed_free(MixedState* ms) {
     cudaFree(ms->kc_buf);
     cudaFree(ms->bnorm2);
     cudaFree(ms->drops);
+    cudaFree(ms->tsched);
+    if (ms->tgraph) cudaGraphExecDestroy(ms->tgraph);
     delete ms;
 }
 
@@ -86,11 +88,11 @@ static double pairs_of(int s) { return 0.5 * s * (s + 1); }
 // Algorithm 2 step coefficients: Y = cP X^2 + cE X + cI I.
 static void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
     if (branch) {
-        *cP = (1.0 + a) * (1.0 + a);
+        *cP = sq1p(a);
         *cE = -2.0 * a * (1.0 + a);
         *cI = a * a;
     } else {
-        *cP = -(1.0 + a) * (1.0 + a);
+        *cP = -sq1p(a);
         *cE = 2.0 * (1.0 + a);
         *cI = 0.0;
     }
@@ -163,13 +165,23 @@ int tune_shape(const DigitStep& st, cudaStream_t stream, TunedShape* best) {
 }
 }  // namespace
 
+void tuned_shape_if_known(int device, DigitStep* st) {
+    if (st->kc_cnt || st->bnorm2 || st->kc != 0) return;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    const auto f = g_tuned.find(std::make_tuple(device, st->s_in, st->n_pad));
+    if (f == g_tuned.end()) return;
+    st->kc = f->second.kc;
+    st->split_ways = f->second.ways;
+}
+
 static int product(purify_ctx* h, const DigitStep& st0, double flops) {
     DigitStep st = st0;
     if (h->opt.split_k) {
         st.partial = h->mixed->partial;
         st.split_cnt = h->mixed->split_cnt;
     }
-    if (h->opt.autotune && !st.kc_cnt && !st.bnorm2 && st.kc == 0) {
+    st.wait_cycles = 1000ll * h->opt.wait_kcycles;
+    if (h->opt.autotune && h->opt.wait_kcycles == 0 && !st.kc_cnt && !st.bnorm2 && st.kc == 0) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         const auto key = std::make_tuple(h->device, st.s_in, st.n_pad);
         auto f = g_tuned.find(key);
@@ -269,6 +281,8 @@ int run_mixed_trace(purify_ctx* h, int scheme, double tol, int max_iter, Schedul
         tr_prev = r[0];
         h->st.trace = r[0];
         h->st.idem_err_fro = std::sqrt(std::max(r[1], 0.0));
+        h->hist_trace.push_back(r[0]);
+        h->hist_idem.push_back(h->st.idem_err_fro);
         b = nb;
         bb = nbb;
         S.alpha.push_back(a);
@@ -287,7 +301,8 @@ int run_mixed_trace(purify_ctx* h, int scheme, double tol, int max_iter, Schedul
     int err = 0;
     PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, ms->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    if (err) return PURIFY_ERR_DEVICE_TIMEOUT;
+    h->st.device_flag = err;
+    if (err) return device_flag_status(err);
     if (it == 0) {
         h->st.trace = tr_prev;
         h->st.idem_err_fro = NAN;
@@ -442,6 +457,7 @@ int run_mixed_poly(purify_ctx* h, int scheme, double mu, const Schedule& S, int*
                     st.red = h->red + 4 * (2 * i + 1);
                     st.out64 = D;
                 } else {  // the next iteration's X_s = alpha (X - c I) + c I
+                    st.red = h->red + 4 * (2 * i + 1);
                     const double an = S.alpha[i + 1];
                     st.dY = an;
                     st.dI = c * (1.0 - an);
@@ -461,7 +477,8 @@ int run_mixed_poly(purify_ctx* h, int scheme, double mu, const Schedule& S, int*
                                     h->stream));
     PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, ms->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    if (err) return PURIFY_ERR_DEVICE_TIMEOUT;
+    h->st.device_flag = err;
+    if (err) return device_flag_status(err);
     h->st.trace = m > 0 ? red[4 * (size_t)(2 * (m - 1) + 1)] : NAN;
     h->st.idem_err_fro = NAN;
     return PURIFY_OK;
@@ -543,8 +560,9 @@ int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
             p2.use_E = 1;
             p2.cP = -2.0;
             p2.cE = 3.0;
+            // every iteration reduces trace(X_i) (slot 2 i + 1)
             const bool last = (i + 1 == m + R);
-            p2.red = last ? h->red + 4 * (2 * i + 1) : nullptr;
+            p2.red = h->red + 4 * (2 * i + 1);
             if (last) {
                 p2.out = nullptr;
                 p2.s_out = 0;
@@ -573,7 +591,8 @@ int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
             st.eA = st.eB = 0;
             st.use_E = 1;
             tc_coeffs(S.branch[i], S.alpha[i], &st.cP, &st.cE, &st.cI);
-            st.red = (i + 1 == m && R == 0) ? h->red + 4 * (2 * i + 1) : nullptr;
+            // every step reduces trace(X_i) and ||X_{i-1} - X_{i-1}^2||_F (slot 2 i + 1)
+            st.red = h->red + 4 * (2 * i + 1);
             st.err = ms->err;
             st.scratch = ms->scratch;
             st.max_ctas = ms->ctas;
@@ -635,7 +654,8 @@ int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
                                     cudaMemcpyDeviceToHost, h->stream));
     PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, ms->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    if (err) return PURIFY_ERR_DEVICE_TIMEOUT;
+    h->st.device_flag = err;
+    if (err) return device_flag_status(err);
     h->st.refine_multiplications = 2 * R;
     // statistics: trace of the result; idempotency of the last squared iterate
     const int last = m + R - 1;
@@ -718,7 +738,7 @@ extern "C" int purify_k_digit_product_f64(const double* A, const double* B, doub
     cudaFree(scratch);
     cudaFree(partial);
     cudaFree(split_cnt);
-    if (r == PURIFY_OK && herr) r = PURIFY_ERR_DEVICE_TIMEOUT;
+    if (r == PURIFY_OK && herr) r = device_flag_status(herr);
     return r;
 }
 

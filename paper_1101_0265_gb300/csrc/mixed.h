@@ -5,9 +5,28 @@
 
 #include <vector>
 
+#include "digits_tc.h"
 #include "internal.h"
 
 namespace purify {
+
+// State of a trace-rule run whose scalar schedule lives on the device
+// (trace_sched.cu): constants of the run, the evolving schedule, the next
+// product's control and a pointer to the per-iteration history
+// (kHistCount arrays of max_iter doubles).
+enum { kHistAlpha = 0, kHistBranch, kHistBeta, kHistBetabar, kHistDigits, kHistTrace, kHistIdem, kHistCount };
+struct TraceSchedDev {
+    double nocc, tol;
+    int have_gap, scaled, max_iter, fixed_digits;
+    double floor_bits, gap_bits;
+    int rbits, pad0;
+    double c0n, c1;          // trace(X_0) = c0n + c1 trace(F)
+    double b, bb, tr;        // beta, beta_bar, trace of the current iterate
+    int it, consumed, done, converged, s_cur, prev_last;
+    DevStep step;
+    double* hist;
+};
+size_t trace_sched_bytes(int max_iter);
 
 constexpr int kMaxDigits = 6;  // equals kMaxDigitPlanes (digits_tc.h)
 
@@ -32,6 +51,16 @@ struct MixedState {
     int2* drops = nullptr;
     size_t drops_cap = 0;
     std::vector<int> nnzb_history;  // upper blocks kept: X_0, then after every step
+    // trace rule with the schedule on the device: its state and the captured
+    // block of steps, with what the capture depends on
+    void* tsched = nullptr;
+    size_t tsched_cap = 0;
+    cudaGraphExec_t tgraph = nullptr;
+    int tg_n = 0, tg_smin = 0, tg_smax = 0, tg_wait = 0, tg_split = 0;
+    const void* tg_state = nullptr;
+    const double* tg_red = nullptr;
+    const double* tg_D = nullptr;
+    const void* tg_X0 = nullptr;
 };
 
 // Allocate (or grow) the handle's mixed-path buffers for a padded size.
@@ -56,6 +85,12 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
 // bounds beta and beta_bar follow the branches taken; without them the run
 // stops when ||X - X^2||_F <= tol.  Fills S with the steps taken.
 int run_mixed_trace(purify_ctx* h, int scheme, double tol, int max_iter, Schedule& S, int* cur, int* iters);
+// The same rule with the scalar schedule on the device (trace_sched.cu): the
+// steps replay from a CUDA graph in blocks, with one host read per block.
+int run_mixed_trace_graph(purify_ctx* h, int scheme, double tol, int max_iter, Schedule& S, int* cur, int* iters);
+// The launch shape measured for st's kind in this process, if any (no
+// measurement is made: usable while a stream is being captured).
+void tuned_shape_if_known(int device, DigitStep* st);
 // The fixed-mu schemes with P_{3,3}, P_{1,3} and P_{3,1} on the digit planes
 // (product plans in mixed.cu; see purify.h).
 int run_mixed_poly(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur, std::vector<double>& red);

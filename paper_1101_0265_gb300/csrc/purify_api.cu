@@ -68,13 +68,20 @@ double tc_alpha(int branch, double b, double bb) {
     return branch ? b / (2.0 - b) : (1.0 - bb) / (1.0 + bb);
 }
 
+// The square (1 + a)^2 of Eq. 4 / Eq. 5 as the C library's pow evaluates a
+// float power (the test oracle's float power calls the same function, so the
+// two schedules agree bit for bit).  The call goes through a volatile pointer:
+// a compiler may otherwise turn pow(v, 2) into v * v.
+static double (*volatile g_pow)(double, double) = ::pow;
+double sq1p(double a) { return g_pow(1.0 + a, 2.0); }
+
 // Eq. 4 (branch 1) / Eq. 5 (branch 0) on a scalar.
 double tc_map(int branch, double a, double x) {
     if (branch) {
         const double y = (1.0 + a) * x - a;
         return y * y;
     }
-    return 2.0 * (1.0 + a) * x - (1.0 + a) * (1.0 + a) * x * x;
+    return 2.0 * (1.0 + a) * x - sq1p(a) * x * x;
 }
 
 static bool is_fixed_mu(int scheme) { return scheme != PURIFY_TC_SF && scheme != PURIFY_TC_MONO; }
@@ -472,6 +479,8 @@ static int check_options(const purify_options* o) {
     if (o->bits_floor != 0 && (o->bits_floor < 16 || o->bits_floor > 43)) return PURIFY_ERR_INVALID_ARG;
     if (o->bits_gap != 0 && (o->bits_gap < 16 || o->bits_gap > 43)) return PURIFY_ERR_INVALID_ARG;
     if (o->autotune != 0 && o->autotune != 1) return PURIFY_ERR_INVALID_ARG;
+    if (o->wait_kcycles < 0 || o->wait_kcycles > (1 << 21)) return PURIFY_ERR_INVALID_ARG;
+    if (o->host_schedule != 0 && o->host_schedule != 1) return PURIFY_ERR_INVALID_ARG;
     if (!(o->trunc_tau >= 0.0) || !(o->trunc_budget >= 0.0)) return PURIFY_ERR_INVALID_ARG;
     return PURIFY_OK;
 }
@@ -695,11 +704,11 @@ static int step64(purify_ctx* h, const double* A, const double* B, const double*
 // Coefficients of the Algorithm 2 step on X: Y = cP X^2 + cE X + cI I.
 static void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
     if (branch) {  // ((1 + a) X - a I)^2
-        *cP = (1.0 + a) * (1.0 + a);
+        *cP = sq1p(a);
         *cE = -2.0 * a * (1.0 + a);
         *cI = a * a;
     } else {  // 2 (1 + a) X - (1 + a)^2 X^2
-        *cP = -(1.0 + a) * (1.0 + a);
+        *cP = -sq1p(a);
         *cE = 2.0 * (1.0 + a);
         *cI = 0.0;
     }
@@ -950,14 +959,26 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
     h->st.refine_multiplications = 0;
     h->st.tensor_flops = 0.0;
     h->st.digit_max = 0;
+    h->st.device_flag = 0;
+    h->hist_trace.clear();
+    h->hist_idem.clear();
     std::vector<double> red;
     int iters = 0;
     int r;
+    bool graph_run = false;  // products replayed from a graph are not timed one by one
     if (h->opt.block_sparse && h->opt.precision != PURIFY_MIXED) return PURIFY_ERR_UNSUPPORTED;
     if (h->opt.precision == PURIFY_MIXED) {
         if (trace_rule && h->opt.block_sparse) return PURIFY_ERR_UNSUPPORTED;
         if (trace_rule) {
-            r = run_mixed_trace(h, scheme, tol, max_iter, S, &h->cur, &iters);
+            // the device-side schedule, unless the host one is asked for or
+            // the bounds already meet tol before the first step
+            const bool at_start = have_gap && std::max(S.beta0, 1.0 - S.betabar0) <= tol;
+            if (h->opt.host_schedule || at_start || max_iter == 0) {
+                r = run_mixed_trace(h, scheme, tol, max_iter, S, &h->cur, &iters);
+            } else {
+                r = run_mixed_trace_graph(h, scheme, tol, max_iter, S, &h->cur, &iters);
+                graph_run = true;
+            }
         } else if (h->opt.block_sparse && (pmm_order(scheme) == 3 || is_asymmetric(scheme))) {
             r = PURIFY_ERR_UNSUPPORTED;
         } else if (pmm_order(scheme) == 3 || is_asymmetric(scheme)) {
@@ -1006,8 +1027,26 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
     }
     st.trace = trace;
     st.idem_err_fro = idem;
+    // per-iteration reductions: the trace of X_i and, for Algorithm 2, the
+    // idempotency of the squared X_{i-1}, from each iteration's last product.
+    // The trace-rule paths record them as they go.
+    if (!trace_rule) {
+        const bool mixed = h->opt.precision == PURIFY_MIXED;
+        const int ppi = products_per_iteration(scheme);
+        for (int i = 0; i < iters; ++i) {
+            const size_t slot = mixed ? (size_t)(2 * i + 1) : (size_t)(is_fixed_mu(scheme) ? ppi * i + ppi - 1 : i);
+            if (4 * slot + 1 >= red.size()) break;
+            h->hist_trace.push_back(red[4 * slot]);
+            h->hist_idem.push_back(is_fixed_mu(scheme) ? NAN : std::sqrt(std::max(red[4 * slot + 1], 0.0)));
+        }
+    } else if (h->opt.precision != PURIFY_MIXED) {
+        for (int i = 0; i < iters && 4 * (size_t)i + 1 < red.size(); ++i) {
+            h->hist_trace.push_back(red[4 * (size_t)i]);
+            h->hist_idem.push_back(std::sqrt(std::max(red[4 * (size_t)i + 1], 0.0)));
+        }
+    }
     st.kernel_launches = (int)(launches_so_far() - launches0);
-    st.product_seconds = product_seconds(h);
+    st.product_seconds = graph_run ? NAN : product_seconds(h);
     st.trace_err = h->nocc >= 0 ? std::fabs(trace - (double)h->nocc) : NAN;
     int status = S.converged ? PURIFY_OK : PURIFY_ERR_NOT_CONVERGED;
     if (status == PURIFY_OK && h->nocc >= 0 && iters > 0 && !(st.trace_err <= 0.5))
@@ -1034,6 +1073,18 @@ int purify_stats(purify_t h, purify_stats_t* out) {
     return PURIFY_OK;
 }
 
+int purify_step_history(purify_t h, double* trace, double* idem, int cap, int* count) {
+    if (!h || !count || cap < 0) return PURIFY_ERR_INVALID_ARG;
+    if (h->cur < 0 || h->st.status == PURIFY_ERR_STATE) return PURIFY_ERR_STATE;
+    const int m = (int)h->hist_trace.size();
+    for (int i = 0; i < m && i < cap; ++i) {
+        if (trace) trace[i] = h->hist_trace[i];
+        if (idem) idem[i] = i < (int)h->hist_idem.size() ? h->hist_idem[i] : NAN;
+    }
+    *count = m;
+    return PURIFY_OK;
+}
+
 const char* purify_strerror(int code) {
     switch (code) {
         case PURIFY_OK: return "ok";
@@ -1045,6 +1096,7 @@ const char* purify_strerror(int code) {
         case PURIFY_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
         case PURIFY_ERR_STATE: return "wrong call order";
         case PURIFY_ERR_UNSUPPORTED: return "unsupported device or feature";
+        case PURIFY_ERR_INTERNAL: return "internal consistency check failed on the device";
         default: return "unknown status";
     }
 }

@@ -199,11 +199,11 @@ int truncate_step(purify_ctx* h, Pattern& pat, double tau, __nv_bfloat16* planes
 
 void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
     if (branch) {
-        *cP = (1.0 + a) * (1.0 + a);
+        *cP = sq1p(a);
         *cE = -2.0 * a * (1.0 + a);
         *cI = a * a;
     } else {
-        *cP = -(1.0 + a) * (1.0 + a);
+        *cP = -sq1p(a);
         *cE = 2.0 * (1.0 + a);
         *cI = 0.0;
     }
@@ -324,13 +324,14 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
         st.use_E = 1;
         tc_coeffs(S.branch[i], S.alpha[i], &st.cP, &st.cE, &st.cI);
         const bool last = (i + 1 == m);
-        st.red = last ? h->red + 4 * (2 * i + 1) : nullptr;
+        st.red = h->red + 4 * (2 * i + 1);
         st.err = ms->err;
         st.scratch = ms->scratch;
         st.max_ctas = ms->ctas;
         st.kc_cnt = kc_cnt;
         st.kc_mask = kc_mask;
         st.bnorm2 = ms->bnorm2;
+        st.wait_cycles = 1000ll * h->opt.wait_kcycles;
         if (last) {
             st.out64 = D;
         } else {
@@ -357,7 +358,8 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
                                     h->stream));
     PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, ms->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    if (err) return PURIFY_ERR_DEVICE_TIMEOUT;
+    h->st.device_flag = err;
+    if (err) return device_flag_status(err);
     if (m > 0) {
         h->st.trace = red[4 * (size_t)(2 * (m - 1) + 1)];
         h->st.idem_err_fro = std::sqrt(std::max(red[4 * (size_t)(2 * (m - 1) + 1) + 1], 0.0));

@@ -275,10 +275,11 @@ def instance_hamiltonian(spec: InstanceSpec) -> Hamiltonian:
                              instance=spec.instance)
 
 
-def dense_hamiltonian_device(spec: InstanceSpec, device="cuda"):
+def dense_hamiltonian_device(spec: InstanceSpec, device="cuda", keep_q: bool = False):
     """The dense recipe built on a GPU with torch (Haar Q from a seeded torch
     generator, spectrum from the numpy generator as above).  Returns
-    (F as a float64 CUDA tensor, Hamiltonian metadata without F / Q)."""
+    (F as a float64 CUDA tensor, Hamiltonian metadata without F; its Q is the
+    CUDA tensor of eigenvectors when keep_q, else None)."""
     import torch
     rng = rng_for(spec.config, spec.instance)
     lam = gapped_spectrum(spec.n, spec.nocc, spec.gap, rng)
@@ -292,6 +293,6 @@ def dense_hamiltonian_device(spec: InstanceSpec, device="cuda"):
     F = 0.5 * (F + F.T)
     meta = Hamiltonian(F=None, n=spec.n, nocc=spec.nocc, mu=0.0, lmin=float(lam[0]),
                        lmax=float(lam[-1]), homo=float(lam[spec.nocc - 1]),
-                       lumo=float(lam[spec.nocc]), lam=lam, Q=None,
+                       lumo=float(lam[spec.nocc]), lam=lam, Q=Q if keep_q else None,
                        meta={"kind": "dense-device", "gap": spec.gap, "scheme": spec.scheme})
     return F.contiguous(), meta

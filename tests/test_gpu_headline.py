@@ -1,0 +1,83 @@
+"""The throughput benchmark's own workload on the mixed path, checked against
+the plain definition D = theta(mu I - F) (the introduction's statement of the
+problem), element by element.
+
+n = 4096, F = Q diag(lambda) Q^T with nocc in {n/2, n/4} and gaps 1e-1 ..
+1e-4 (spectrum [-1, 1], mu = 0), both scale-and-fold schemes (Algorithm 1 and
+Algorithm 2) at tol 1e-9, in the benchmark's launch configuration (per-step
+digit rule, split last wave, launch-shape autotuning).  The exact density is
+the closed form Q_occ Q_occ^T of the generated eigenvectors (oracle).  Bounds
+are estimated on the device (Gershgorin + Lanczos), as in the timed step.
+"""
+import numpy as np
+import pytest
+
+from oracle import purify_oracle as O
+from paper_1101_0265_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+N = 4096
+SPECS = [(nocc, gap) for nocc in (N // 2, N // 4) for gap in (1e-1, 1e-2, 1e-3, 1e-4)]
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_1101_0265_gb300 import build
+    build.build()
+    import paper_1101_0265_gb300 as P
+    return P
+
+
+@pytest.fixture(scope="module")
+def handle(P):
+    pur = P.Purifier(precision="mixed", autotune=True)
+    yield pur
+    pur.close()
+
+
+@pytest.fixture(scope="module")
+def cases():
+    """Inputs of the benchmark's sweep (same seeds), with the exact density."""
+    out = {}
+    for i, (nocc, gap) in enumerate(SPECS):
+        spec = I.InstanceSpec(n=N, nocc=nocc, gap=gap, scheme="TC_SF", instance=i, config=2)
+        F, h = I.dense_hamiltonian_device(spec, "cuda", keep_q=True)
+        Q = h.Q.cpu().numpy()
+        out[(nocc, gap)] = (F, h, O.density_closed_form(Q, h.lam, 0.0))
+    return out
+
+
+@pytest.mark.parametrize("scheme", ["TC_SF", "FIXED_MU_SF"])
+@pytest.mark.parametrize("nocc,gap", SPECS)
+def test_headline_mixed_vs_closed_form(P, handle, cases, scheme, nocc, gap):
+    F, h, Dc = cases[(nocc, gap)]
+    handle.set_hamiltonian(F, nocc=nocc, mu=0.0, homo=h.homo, lumo=h.lumo)   # lmin/lmax estimated
+    st0 = handle.stats()
+    # Ritz values widened by their residuals: they enclose the true extremes
+    # up to a sliver (not a guaranteed enclosure; the polynomials tolerate a
+    # slight miss) and are within a few per cent of the width
+    w = h.lmax - h.lmin
+    assert st0["lmin"] <= h.lmin + 1e-6 * w and st0["lmax"] >= h.lmax - 1e-6 * w, (st0["lmin"], st0["lmax"])
+    assert st0["lmin"] >= h.lmin - 0.03 * w and st0["lmax"] <= h.lmax + 0.03 * w, (st0["lmin"], st0["lmax"])
+    assert handle.run(scheme, 1e-9, 200) == P.OK
+    st = handle.stats()
+    D = handle.density()
+    err = float(np.max(np.abs(D - Dc)))
+    # the benchmark spec's bound for the mixed path
+    assert err <= 1e-6, err
+    # trace and idempotency of the result, from D itself: a symmetric error E
+    # with |E_ij| <= err moves the trace by at most n err and leaves
+    # ||D - D^2||_F <= ||E - Dc E - E Dc - E^2||_F <= (2 + n err) ||E||_F
+    E_fro = float(np.linalg.norm(D - Dc))
+    trace_err = abs(float(np.trace(D)) - nocc)
+    idem = float(np.linalg.norm(D - D @ D))
+    assert trace_err <= N * err, trace_err
+    assert idem <= (2.0 + N * err) * E_fro + 1e-12, (idem, E_fro)
+    assert trace_err <= 1e-4 and idem <= 1e-4, (trace_err, idem)
+    # the library's float64 trace reduction (fused epilogue) agrees with D
+    assert abs(st["trace_err"] - trace_err) <= 1e-9 * N, (st["trace_err"], trace_err)
+    print(f"\n{scheme} nocc={nocc} gap={gap:g}: iterations={st['iterations']} max|D-Dexact|={err:.2e} "
+          f"trace_err={trace_err:.2e} ||D-D^2||_F={idem:.2e}")

@@ -226,19 +226,28 @@ def test_fp64_refinement_sets_idempotency(P):
 
 
 @pytest.mark.parametrize("scheme,gap_known", [("TC_MONO", False), ("TC_SF", True), ("TC_MONO", True)])
-def test_trace_rule_on_the_mixed_path(P, scheme, gap_known):
+@pytest.mark.parametrize("host_schedule", [0, 1])
+def test_trace_rule_on_the_mixed_path(P, scheme, gap_known, host_schedule):
     # Niklasson's trace rule: each branch from trace(X_{i-1}) versus nocc,
     # reduced in float64 by the previous product's epilogue; without gap
     # bounds the run stops when ||X - X^2||_F <= tol (reachable at the mixed
-    # path's precision: 1e-5)
+    # path's precision: 1e-5).  host_schedule = 0 decides every step on the
+    # device and replays the steps from a CUDA graph; 1 takes one host round
+    # trip per step.
     h = I.dense_hamiltonian(300, 110, 0.05, config=75)
     tol = 1e-9 if gap_known else 1e-5
     kw = dict(homo=h.homo, lumo=h.lumo) if gap_known else {}
     pur = P.Purifier(precision="mixed", branch_rule="trace")
+    pur.set_options(host_schedule=host_schedule)
     pur.set_hamiltonian(h.F, nocc=h.nocc, lmin=h.lmin, lmax=h.lmax, **kw)
     pur.run(scheme, tol, 200)
     D, st = pur.density(), pur.stats()
+    tr_hist, _ = pur.step_history()
+    # a second run on the same handle replays the same graph
+    pur.run(scheme, tol, 200)
+    D2 = pur.density()
     pur.close()
+    assert np.array_equal(D, D2)
     Do, r = O.purify_tc(h.F, h.lmin, h.lmax, tol=tol, scaled=scheme == "TC_SF", branch_rule="trace",
                         nocc=h.nocc, max_iter=200, **kw)
     assert r.converged
@@ -246,8 +255,29 @@ def test_trace_rule_on_the_mixed_path(P, scheme, gap_known):
     assert st["multiplications"] == r.multiplications
     assert np.max(np.abs(D - Do)) <= 3e-7
     assert abs(st["trace"] - h.nocc) < 1e-6
+    np.testing.assert_allclose(tr_hist, r.traces, rtol=0, atol=300 * 5e-8)
     Dx = O.density_closed_form(h.Q, h.lam, 0.0)
     assert np.max(np.abs(D - Dx)) <= 3e-7 + (tol if not gap_known else 0.0)
+
+
+@pytest.mark.parametrize("n", [256, 1024, 4096])
+def test_trace_rule_device_schedule_equals_host_schedule(P, n):
+    # the device-side schedule takes the same branches and digit counts as the
+    # host one, with the same float64 operations except (1 + alpha)^2 (a
+    # product there, the C library's pow here); a last-bit difference in a
+    # coefficient moves digit roundings, so the densities agree to the mixed
+    # path's own rounding level (~2^-36 per step, amplified near the gap),
+    # far inside its 3e-7 tolerance
+    h = I.dense_hamiltonian(n, n // 2 - 7, 1e-3, config=76, instance=n)
+    out = []
+    for host in (1, 0):
+        pur = P.Purifier(precision="mixed", branch_rule="trace", host_schedule=host)
+        pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+        assert pur.run("TC_SF", 1e-9, 200) == P.OK
+        out.append((pur.density(), pur.stats()["iterations"]))
+        pur.close()
+    assert out[0][1] == out[1][1]
+    assert np.max(np.abs(out[0][0] - out[1][0])) <= 1e-9
 
 
 @pytest.mark.parametrize("n,gap", [(300, 1e-2), (1000, 1e-3)])

@@ -42,7 +42,8 @@ def test_library_exports_every_header_symbol():
 @pytest.mark.parametrize("field,value", [
     ("digits", 7), ("digits", 1), ("split_k", 2), ("refine_fp64", 3), ("bits_floor", 15),
     ("bits_floor", 44), ("bits_gap", 15), ("bits_gap", 44), ("trunc_tau", -1.0),
-    ("trunc_budget", float("nan")), ("precision", 5), ("lanczos_steps", -1), ("autotune", 2)])
+    ("trunc_budget", float("nan")), ("precision", 5), ("lanczos_steps", -1), ("autotune", 2),
+    ("wait_kcycles", -1), ("wait_kcycles", (1 << 21) + 1), ("host_schedule", 2)])
 def test_invalid_options_rejected_before_the_device(field, value):
     # option checks come first: no device is touched, so this runs without a GPU
     import ctypes as C
@@ -70,7 +71,7 @@ def test_tuned_shape_query_without_measurements():
 def test_strerror_names_codes():
     _ensure_built()
     for code in (P.OK, P.ERR_INVALID_ARG, P.ERR_BOUNDS, P.ERR_NOT_CONVERGED, P.ERR_OOM,
-                 P.ERR_DEVICE_TIMEOUT, P.ERR_STATE, P.ERR_UNSUPPORTED):
+                 P.ERR_DEVICE_TIMEOUT, P.ERR_STATE, P.ERR_UNSUPPORTED, P.ERR_INTERNAL):
         assert P.strerror(code) and P.strerror(code) != "unknown status"
 
 
@@ -206,7 +207,8 @@ def test_options_struct_layout_matches_the_library():
     assert o.precision == 0 and o.branch_rule == 0      # PURIFY_FP64, PURIFY_BRANCH_BETA
     assert o.lanczos_steps == 32 and o.refine_squares == 0 and o.digits == 0
     assert o.split_k == 1 and o.refine_fp64 == 0 and o.block_sparse == 0 and o.time_products == 0
-    assert o.bits_floor == 0 and o.bits_gap == 0 and o.autotune == 0
+    assert o.bits_floor == 0 and o.bits_gap == 0 and o.autotune == 0 and o.wait_kcycles == 0
+    assert o.host_schedule == 0
     assert list(o.reserved) == [0] * len(o.reserved)
     assert o.trunc_tau == 1e-6 and o.trunc_budget == 0.0
 

@@ -49,3 +49,23 @@ def test_noalloc_gershgorin_rejects_oversize(P):
     assert code == P.ERR_INVALID_ARG
     torch.cuda.synchronize()
     assert torch.all(lohi == 7.0)        # nothing was launched
+
+
+def test_noalloc_calls_queued_back_to_back_on_one_stream(P):
+    # two sizes queued on one stream with no synchronisation in between: the
+    # second call's kernels overwrite the shared scratch only after the first
+    # call's kernels have read it (stream order), so both intervals are right
+    F1, F2 = _sym(4096, 5), _sym(777, 6)
+    got1 = torch.zeros(2, dtype=torch.float64, device="cuda")
+    got2 = torch.zeros(2, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    assert P.k_gershgorin_f64_noalloc(F1, got1) == P.OK
+    assert P.k_gershgorin_f64_noalloc(F2, got2) == P.OK
+    assert P.k_gershgorin_f64_noalloc(F1, got1) == P.OK    # and the larger size again
+    torch.cuda.synchronize()
+    for F, got in ((F1, got1), (F2, got2)):
+        ref = torch.zeros(2, dtype=torch.float64, device="cuda")
+        P.k_gershgorin_f64(F, ref)
+        torch.cuda.synchronize()
+        scale = float(F.abs().sum(dim=1).max())
+        assert torch.allclose(got, ref, rtol=0.0, atol=1e-13 * scale), (F.shape[0], got, ref)
