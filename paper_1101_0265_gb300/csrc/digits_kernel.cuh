@@ -416,8 +416,11 @@ __device__ __forceinline__ float warp_sum_f(float v) {
     return v;
 }
 
-// Bounded wait measured from its own start: false when it gives up.
+// Bounded wait measured from its own start: false when it gives up.  A phase
+// that has completed already returns at the first test, without reading the
+// clock (the fast path of the pipeline's hand-offs).
 __device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, long long limit = WAIT_CYCLES) {
+    if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (clock64() - t0 > limit) return false;
@@ -594,7 +597,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 tc_fence_after();
                 for (int kc = 0; kc < nk; ++kc, ++it) {
                     const int st = it % stages;
-                    if (!mbar_wait_for(smem_u32(&full_bar[st]), (uint32_t)((it / stages) & 1), wait) || *abort_flag) {
+                    // (an aborting role stops feeding this wait, so it runs out;
+                    // the abort flag is not read on this path)
+                    if (!mbar_wait_for(smem_u32(&full_bar[st]), (uint32_t)((it / stages) & 1), wait)) {
                         ok = false;
                         break;
                     }
