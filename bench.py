@@ -335,7 +335,7 @@ class ClockSampler:
 def cpu_baseline(hs, Fs, tol, estimate_bounds=True):
     """The oracle as it stands, on a bounded sample of the step: four
     purifications that cycle through both nocc values, four gaps and both
-    schemes (bounds estimated as in the timed step: Gershgorin, then 32
+    schemes (bounds estimated as in the timed step: Gershgorin, then 16
     Lanczos steps)."""
     from oracle import purify_oracle as O
     picks = [(0, "TC_SF"), (6, "FIXED_MU_SF"), (5, "TC_SF"), (3, "FIXED_MU_SF")]
@@ -343,13 +343,13 @@ def cpu_baseline(hs, Fs, tol, estimate_bounds=True):
     t0 = time.perf_counter()
     for i, sc in picks:
         h, F = hs[i], Fs[i]
-        lo, hi = O.lanczos_bounds(F, 32) if estimate_bounds else (h.lmin, h.lmax)
+        lo, hi = O.lanczos_bounds(F, 16) if estimate_bounds else (h.lmin, h.lmax)
         O.purify(F, sc, min(lo, h.homo), max(hi, h.lumo), mu=0.0, homo=h.homo, lumo=h.lumo, tol=tol)
     dt = time.perf_counter() - t0
     desc = ", ".join(f"{sc} nocc={hs[i].nocc} gap={hs[i].meta['gap']:g}" for i, sc in picks)
     return {"value": len(picks) / dt, "unit": "matrices/s", "cores": _blas_threads(), "kind": "oracle",
             "sample": f"{len(picks)} of the step's 16 purifications at n={hs[0].n} ({desc}; tol {tol:g}, "
-                      f"bounds by Gershgorin + 32 Lanczos steps), numpy float64, {dt:.1f} s"}
+                      f"bounds by Gershgorin + 16 Lanczos steps), numpy float64, {dt:.1f} s"}
 
 
 def _blas_threads():
@@ -372,7 +372,7 @@ def main_config(n, count, schemes, tol, precision, world, exact_bounds=False):
             "n": n, "matrices_per_step": count * len(schemes),
             "tol": tol, "parallelism": f"replicas x{world}",
             "bounds": ("lmin/lmax given exactly" if exact_bounds else
-                       "lmin/lmax estimated per matrix inside the step (Gershgorin discs, 32 Lanczos "
+                       "lmin/lmax estimated per matrix inside the step (Gershgorin discs, 16 Lanczos "
                        "steps); homo/lumo given"),
             "l2": "inputs larger than L2 (each F is 134 MB, 8 distinct per step)"}
 
@@ -389,7 +389,7 @@ def run_reference(args, rank, world):
 
     def one(i):
         h = hs[i % count]
-        lo, hi = O.lanczos_bounds(h.F, 32)
+        lo, hi = O.lanczos_bounds(h.F, 16)
         O.purify(h.F, schemes[i % len(schemes)], min(lo, h.homo), max(hi, h.lumo), mu=0.0, homo=h.homo,
                  lumo=h.lumo, tol=args.tol)
     for i in range(args.warmup):
@@ -408,7 +408,7 @@ def run_reference(args, rank, world):
         "config": main_config(n, len(workload_specs(n)), schemes, args.tol, "f64", world),
         "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": cores, "kind": "oracle",
                          "sample": f"a bounded sample of the step: one purification per step "
-                                   f"(CPU oracle, numpy float64, bounds by Gershgorin + 32 Lanczos "
+                                   f"(CPU oracle, numpy float64, bounds by Gershgorin + 16 Lanczos "
                                    f"steps), cycling the first {count} matrices of the sweep and the "
                                    f"schemes {', '.join(schemes)}"},
         "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0,

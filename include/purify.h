@@ -105,7 +105,11 @@ typedef struct purify_bounds {
 typedef struct purify_options {
     int precision;       /* PURIFY_FP64 (default) or PURIFY_MIXED                        */
     int branch_rule;     /* PURIFY_BRANCH_BETA (default) or PURIFY_BRANCH_TRACE          */
-    int lanczos_steps;   /* Lanczos steps when lmin/lmax are NaN (default 32, 0 = none)  */
+    int lanczos_steps;   /* Lanczos steps when lmin/lmax are NaN (default 16, 0 = none):
+                            the Ritz values widened by their residuals land within a
+                            few per cent of the spectral ends, and a few per cent of
+                            width moves an iteration count by log2(1.0x), i.e. not at
+                            all in practice                                          */
     int refine_squares;  /* MIXED: extra unscaled McWeeny steps at the finest digit
                             count after the schedule ends (default 0)                  */
     int digits;          /* MIXED: 0 = per-step digit count from the mapped gap

@@ -195,7 +195,7 @@ class Purifier:
     """One libpurify handle on one device."""
 
     def __init__(self, device: int = 0, stream: int | None = None, precision: str = "fp64",
-                 branch_rule: str = "beta", lanczos_steps: int = 32, refine_squares: int = 0,
+                 branch_rule: str = "beta", lanczos_steps: int = 16, refine_squares: int = 0,
                  digits: int = 0, time_products: bool = False, block_sparse: bool = False,
                  trunc_tau: float = 1e-6, split_k: bool = True, refine_fp64: int = 0,
                  trunc_budget: float = 0.0, bits_floor: int = 0, bits_gap: int = 0,

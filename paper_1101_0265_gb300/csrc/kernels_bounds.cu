@@ -15,7 +15,8 @@ namespace purify {
 
 namespace {
 
-constexpr int ROWS_PER_CTA = 8;  // one warp per row
+constexpr int ROWS_PER_CTA = 8;  // Gershgorin: one warp per row
+constexpr int LZ_ROWS = 4;       // Lanczos matvec: one warp per row, 6-7 CTAs per SM at n = 4096
 constexpr unsigned long long GOLDEN = 0x9E3779B97F4A7C15ull;
 constexpr unsigned long long LANCZOS_KEY = 0x11010265ull;
 
@@ -33,10 +34,18 @@ gershgorin_rows_kernel(const double* __restrict__ F, int64_t n, int64_t ld, doub
     const int64_t i = (int64_t)blockIdx.x * ROWS_PER_CTA + warp;
     double lo = INFINITY, hi = -INFINITY;
     if (i < n) {
+        // four independent partial sums per lane keep the float64 pipe fed
         const double* row = F + i * ld;
-        double r = 0.0;
-        for (int64_t j = lane; j < n; j += 32) r += (j == i) ? 0.0 : fabs(row[j]);
-        r = warp_sum(r);
+        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+        int64_t j = lane;
+        for (; j + 96 < n; j += 128) {  // the disc radius leaves out the diagonal
+            r0 += (j == i) ? 0.0 : fabs(row[j]);
+            r1 += (j + 32 == i) ? 0.0 : fabs(row[j + 32]);
+            r2 += (j + 64 == i) ? 0.0 : fabs(row[j + 64]);
+            r3 += (j + 96 == i) ? 0.0 : fabs(row[j + 96]);
+        }
+        for (; j < n; j += 32) r0 += (j == i) ? 0.0 : fabs(row[j]);
+        const double r = warp_sum((r0 + r1) + (r2 + r3));
         const double d = row[i];
         lo = d - r;
         hi = d + r;
@@ -158,14 +167,22 @@ lanczos_matvec_kernel(const double* __restrict__ F, int64_t n, const double* __r
                       const double* __restrict__ vprev, double* __restrict__ w,
                       const double* bsq_prev, double* pa) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * ROWS_PER_CTA + warp;
-    __shared__ double sdot[ROWS_PER_CTA];
+    const int64_t i = (int64_t)blockIdx.x * LZ_ROWS + warp;
+    __shared__ double sdot[LZ_ROWS];
     double dot = 0.0;
     if (i < n) {
+        // four independent chains per lane keep the float64 pipe fed
         const double* row = F + i * n;
-        double s = 0.0;
-        for (int64_t j = lane; j < n; j += 32) s = fma(row[j], v[j], s);
-        s = warp_sum(s);
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int64_t j = lane;
+        for (; j + 96 < n; j += 128) {
+            s0 = fma(row[j], v[j], s0);
+            s1 = fma(row[j + 32], v[j + 32], s1);
+            s2 = fma(row[j + 64], v[j + 64], s2);
+            s3 = fma(row[j + 96], v[j + 96], s3);
+        }
+        for (; j < n; j += 32) s0 = fma(row[j], v[j], s0);
+        const double s = warp_sum((s0 + s1) + (s2 + s3));
         const double bprev = bsq_prev ? sqrt(*bsq_prev) : 0.0;
         const double wi = s - bprev * vprev[i];
         if (lane == 0) w[i] = wi;
@@ -175,7 +192,7 @@ lanczos_matvec_kernel(const double* __restrict__ F, int64_t n, const double* __r
     __syncthreads();
     if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int q = 0; q < ROWS_PER_CTA; ++q) t += sdot[q];
+        for (int q = 0; q < LZ_ROWS; ++q) t += sdot[q];
         pa[blockIdx.x] = t;
     }
 }
@@ -239,7 +256,7 @@ int launch_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi, 
 }
 
 int64_t lanczos_scratch_doubles(int64_t n, int k) {
-    return 3 * n + 1 + 2 * (int64_t)k + (n + ROWS_PER_CTA - 1) / ROWS_PER_CTA + kVecBlocksMax;
+    return 3 * n + 1 + 2 * (int64_t)k + (n + LZ_ROWS - 1) / LZ_ROWS + kVecBlocksMax;
 }
 
 int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaStream_t s) {
@@ -250,15 +267,15 @@ int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaS
     double* qn = scratch + 3 * n;
     double* a = scratch + lanczos_a_offset(n);
     double* bsq = scratch + lanczos_bsq_offset(n, k);
-    const int64_t rows = (n + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
+    const int64_t rows = (n + LZ_ROWS - 1) / LZ_ROWS;
     double* pa = bsq + k;
     double* pb = pa + rows;
     const unsigned vb = vec_blocks(n);
     lanczos_start_kernel<<<vb, 256, 0, s>>>(v, vprev, n, pb);
     scale_by_norm_kernel<<<vb, 256, 0, s>>>(v, n, pb, (int)vb, qn);
     for (int j = 0; j < k; ++j) {
-        lanczos_matvec_kernel<<<(unsigned)rows, 32 * ROWS_PER_CTA, 0, s>>>(F, n, v, vprev, w,
-                                                                             j ? bsq + j - 1 : nullptr, pa);
+        lanczos_matvec_kernel<<<(unsigned)rows, 32 * LZ_ROWS, 0, s>>>(F, n, v, vprev, w, j ? bsq + j - 1 : nullptr,
+                                                                        pa);
         lanczos_orth_kernel<<<vb, 256, 0, s>>>(w, v, n, pa, rows, a + j, pb);
         lanczos_shift_kernel<<<vb, 256, 0, s>>>(vprev, v, w, n, pb, (int)vb, bsq + j);
     }

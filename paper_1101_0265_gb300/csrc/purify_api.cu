@@ -265,10 +265,14 @@ static void jacobi_eig(std::vector<double>& A, int m, std::vector<double>& V) {
     V.assign((size_t)m * m, 0.0);
     for (int i = 0; i < m; ++i) V[(size_t)i * m + i] = 1.0;
     for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int p = 0; p < m; ++p)
+        // converged once the off-diagonal mass is below rounding relative to
+        // the diagonal's (it falls quadratically: a handful of sweeps)
+        double off = 0.0, diag = 0.0;
+        for (int p = 0; p < m; ++p) {
+            diag += A[(size_t)p * m + p] * A[(size_t)p * m + p];
             for (int q = p + 1; q < m; ++q) off += A[(size_t)p * m + q] * A[(size_t)p * m + q];
-        if (off == 0.0) break;
+        }
+        if (off == 0.0 || off <= 1e-36 * diag) break;
         for (int p = 0; p < m; ++p) {
             for (int q = p + 1; q < m; ++q) {
                 const double apq = A[(size_t)p * m + q];
@@ -456,7 +460,7 @@ void purify_options_default(purify_options* opt) {
     std::memset(opt, 0, sizeof(*opt));
     opt->precision = PURIFY_FP64;
     opt->branch_rule = PURIFY_BRANCH_BETA;
-    opt->lanczos_steps = 32;
+    opt->lanczos_steps = 16;
     opt->refine_squares = 0;
     opt->digits = 0;
     opt->block_sparse = 0;
@@ -566,11 +570,13 @@ static int finish_set(purify_t h, int64_t n, int64_t nocc, double mu, const puri
         double* gs = h->scratch + 2;
         PURIFY_TRY(launch_gershgorin_f64(h->F, n, n, lohi, gs, h->stream));
         double g[2];
-        PURIFY_CUDA_TRY(cudaMemcpyAsync(g, lohi, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
-        double lo = g[0], hi = g[1];
+        double lo, hi;
         if (k > 0) {
+            // the Lanczos steps are queued before any result is read back, so
+            // the device runs the whole estimate without a host round trip
             double* ls = h->scratch + 2;  // Gershgorin partials are consumed already
             PURIFY_TRY(launch_lanczos_f64(h->F, n, k, ls, h->stream));
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(g, lohi, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
             std::vector<double> a(k), bsq(k);
             PURIFY_CUDA_TRY(cudaMemcpyAsync(a.data(), ls + lanczos_a_offset(n), sizeof(double) * k,
                                             cudaMemcpyDeviceToHost, h->stream));
@@ -579,7 +585,10 @@ static int finish_set(purify_t h, int64_t n, int64_t nocc, double mu, const puri
             PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
             PURIFY_TRY(host_bounds_from_lanczos(a.data(), bsq.data(), k, g[0], g[1], &lo, &hi));
         } else {
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(g, lohi, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
             PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+            lo = g[0];
+            hi = g[1];
         }
         if (std::isnan(bb.lmin)) bb.lmin = lo;
         if (std::isnan(bb.lmax)) bb.lmax = hi;

@@ -205,7 +205,7 @@ def test_options_struct_layout_matches_the_library():
     assert bytes(buf[size:]) == b"\xab" * 64
     o = P._lib.Options.from_buffer(buf)
     assert o.precision == 0 and o.branch_rule == 0      # PURIFY_FP64, PURIFY_BRANCH_BETA
-    assert o.lanczos_steps == 32 and o.refine_squares == 0 and o.digits == 0
+    assert o.lanczos_steps == 16 and o.refine_squares == 0 and o.digits == 0
     assert o.split_k == 1 and o.refine_fp64 == 0 and o.block_sparse == 0 and o.time_products == 0
     assert o.bits_floor == 0 and o.bits_gap == 0 and o.autotune == 0 and o.wait_kcycles == 0
     assert o.host_schedule == 0
