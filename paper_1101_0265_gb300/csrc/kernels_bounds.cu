@@ -26,6 +26,12 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
+// |x| by clearing the sign bit (an integer operation: GB300's float64 pipe is
+// the bound of this pass, and it then carries only the additions).
+__device__ __forceinline__ double abs_bits(double x) {
+    return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll);
+}
+
 // Per-CTA partial (min lo, max hi) of the Gershgorin interval.
 __global__ void __launch_bounds__(256)
 gershgorin_rows_kernel(const double* __restrict__ F, int64_t n, int64_t ld, double* __restrict__ part) {
@@ -39,12 +45,12 @@ gershgorin_rows_kernel(const double* __restrict__ F, int64_t n, int64_t ld, doub
         double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
         int64_t j = lane;
         for (; j + 96 < n; j += 128) {  // the disc radius leaves out the diagonal
-            r0 += (j == i) ? 0.0 : fabs(row[j]);
-            r1 += (j + 32 == i) ? 0.0 : fabs(row[j + 32]);
-            r2 += (j + 64 == i) ? 0.0 : fabs(row[j + 64]);
-            r3 += (j + 96 == i) ? 0.0 : fabs(row[j + 96]);
+            r0 += (j == i) ? 0.0 : abs_bits(row[j]);
+            r1 += (j + 32 == i) ? 0.0 : abs_bits(row[j + 32]);
+            r2 += (j + 64 == i) ? 0.0 : abs_bits(row[j + 64]);
+            r3 += (j + 96 == i) ? 0.0 : abs_bits(row[j + 96]);
         }
-        for (; j < n; j += 32) r0 += (j == i) ? 0.0 : fabs(row[j]);
+        for (; j < n; j += 32) r0 += (j == i) ? 0.0 : abs_bits(row[j]);
         const double r = warp_sum((r0 + r1) + (r2 + r3));
         const double d = row[i];
         lo = d - r;

@@ -37,6 +37,8 @@ void mixed_free(MixedState* ms) {
     cudaFree(ms->kc_buf);
     cudaFree(ms->bnorm2);
     cudaFree(ms->drops);
+    cudaFree(ms->pat_dev);
+    cudaFree(ms->tsel);
     cudaFree(ms->tsched);
     if (ms->tgraph) cudaGraphExecDestroy(ms->tgraph);
     delete ms;

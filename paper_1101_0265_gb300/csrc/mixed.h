@@ -50,6 +50,9 @@ struct MixedState {
     size_t bnorm2_cap = 0;
     int2* drops = nullptr;
     size_t drops_cap = 0;
+    unsigned long long* pat_dev = nullptr;  // a step's block pattern (device truncation selection)
+    size_t pat_dev_cap = 0;
+    void* tsel = nullptr;                   // selection state: histograms and the selected key
     std::vector<int> nnzb_history;  // upper blocks kept: X_0, then after every step
     // trace rule with the schedule on the device: its state and the captured
     // block of steps, with what the capture depends on

@@ -17,6 +17,7 @@
 // the pattern.  Patterns are bitsets on the host: the pattern of X^2 is the
 // union over K in row I of the rows K.
 #include <algorithm>
+#include <cstddef>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -50,6 +51,137 @@ __global__ void mask_f64_kernel(double* D, int n, const int2* blocks) {
         if (i0 < n && j0 < n) D[(size_t)i0 * n + j0] = 0.0;
         const int i1 = b.y * 32 + r, j1 = b.x * 32 + c;
         if (i1 < n && j1 < n) D[(size_t)i1 * n + j1] = 0.0;
+    }
+}
+
+// ---- truncation selection on the device -------------------------------------
+// The greedy reading of the truncation (blocks in ascending norm, ties by
+// row then column, dropped while the dropped mass stays within tau^2) picks a
+// prefix of that order.  Its end is found by a two-pass radix select on the
+// float bits of the norms: masses are summed as fixed-point integers (the
+// budget is 2^40 units), so every sum is exact and independent of the order
+// in which the device adds them.  Candidates are the upper blocks of the
+// step's pattern whose weighted mass (off-diagonal blocks twice) is within the
+// budget; lighter ones than the selected key are dropped, and blocks of
+// exactly that key are handed to the host, which walks them in (row, column)
+// order.
+constexpr int kHistBins = 1 << 16;
+constexpr double kBudgetUnits = 1099511627776.0;  // 2^40
+
+struct TruncSel {
+    unsigned long long hist_fx[kHistBins];
+    unsigned int hist_cnt[kHistBins];
+    unsigned long long cum_before;  // mass of the keys below the found bin
+    int found, bin;                 // bin of the crossing (found = 0: none)
+    int hi;                         // pass 0's bin: the key's high 16 bits
+    unsigned key;                   // the selected key (after pass 1)
+    int ndrop, ntie;
+};
+
+__device__ __forceinline__ bool trunc_candidate(const float* bn2, const unsigned long long* pat, int words, int nb,
+                                                int idx, double budget, unsigned* key, unsigned long long* fx, int* I,
+                                                int* J) {
+    *I = idx / nb;
+    *J = idx - *I * nb;
+    if (*J < *I) return false;
+    if (!((pat[(size_t)*I * words + (*J >> 6)] >> (*J & 63)) & 1ull)) return false;
+    const float m = bn2[idx];
+    const double mass = (*I == *J ? 1.0 : 2.0) * (double)m;
+    if (!(mass <= budget)) return false;
+    *key = __float_as_uint(m);
+    *fx = budget > 0.0 ? (unsigned long long)(mass / budget * kBudgetUnits) : 0ull;
+    return true;
+}
+
+// pass 0: histogram of the high 16 key bits; pass 1: of the low 16 bits of
+// the keys whose high bits are sel->bin
+__global__ void trunc_hist_kernel(const float* __restrict__ bn2, const unsigned long long* __restrict__ pat, int words,
+                                  int nb, double budget, int pass, TruncSel* sel) {
+    if (pass && !sel->found) return;
+    const int hi = pass ? sel->hi : 0;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nb * nb; idx += gridDim.x * blockDim.x) {
+        unsigned key;
+        unsigned long long fx;
+        int I, J;
+        if (!trunc_candidate(bn2, pat, words, nb, idx, budget, &key, &fx, &I, &J)) continue;
+        if (pass && (int)(key >> 16) != hi) continue;
+        const int bin = pass ? (int)(key & 0xFFFFu) : (int)(key >> 16);
+        if (fx) atomicAdd(&sel->hist_fx[bin], fx);
+        atomicAdd(&sel->hist_cnt[bin], 1u);
+    }
+}
+
+// One CTA of 1024 threads: the first bin whose cumulative mass (added to
+// `base`) exceeds the budget; clears the histogram for the next pass.
+__global__ void __launch_bounds__(1024) trunc_scan_kernel(TruncSel* sel, int pass) {
+    __shared__ unsigned long long part[1024];
+    __shared__ int first;
+    const int t = threadIdx.x;
+    constexpr int per = kHistBins / 1024;
+    const unsigned long long base = pass ? sel->cum_before : 0ull;
+    unsigned long long sum = 0;
+    for (int b = t * per; b < (t + 1) * per; ++b) sum += sel->hist_fx[b];
+    part[t] = sum;
+    if (t == 0) first = kHistBins;
+    __syncthreads();
+    // exclusive prefix of the 1024 partial sums (fixed order)
+    for (int o = 1; o < 1024; o <<= 1) {
+        const unsigned long long v = t >= o ? part[t - o] : 0ull;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned long long cum = base + (t ? part[t - 1] : 0ull);
+    const unsigned long long budget = (unsigned long long)kBudgetUnits;
+    int mine = kHistBins;
+    unsigned long long before = 0;
+    for (int b = t * per; b < (t + 1) * per; ++b) {
+        const unsigned long long v = sel->hist_fx[b];
+        if (sel->hist_cnt[b] && cum + v > budget) {
+            mine = b;
+            before = cum;
+            break;
+        }
+        cum += v;
+    }
+    if (mine < kHistBins) atomicMin(&first, mine);
+    __syncthreads();
+    if (mine < kHistBins && mine == first) {
+        sel->found = 1;
+        sel->bin = mine;
+        sel->cum_before = before;
+        if (pass == 0)
+            sel->hi = mine;
+        else
+            sel->key = ((unsigned)sel->hi << 16) | (unsigned)mine;
+    }
+    __syncthreads();
+    if (t == 0 && first == kHistBins) sel->found = 0;
+    for (int b = t; b < kHistBins; b += 1024) {
+        sel->hist_fx[b] = 0;
+        sel->hist_cnt[b] = 0;
+    }
+}
+
+// Candidates below the selected key are dropped; those of exactly that key
+// are listed for the host.  Without a crossing every candidate is dropped.
+__global__ void trunc_collect_kernel(const float* __restrict__ bn2, const unsigned long long* __restrict__ pat,
+                                     int words, int nb, double budget, TruncSel* sel, int2* drop, int drop_cap, int2* tie,
+                                     int tie_cap) {
+    const bool all = sel->found == 0;
+    const unsigned sel_key = sel->key;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < nb * nb; idx += gridDim.x * blockDim.x) {
+        unsigned key;
+        unsigned long long fx;
+        int I, J;
+        if (!trunc_candidate(bn2, pat, words, nb, idx, budget, &key, &fx, &I, &J)) continue;
+        if (all || key < sel_key) {
+            const int k = atomicAdd(&sel->ndrop, 1);
+            if (k < drop_cap) drop[k] = make_int2(I, J);
+        } else if (key == sel_key) {
+            const int k = atomicAdd(&sel->ntie, 1);
+            if (k < tie_cap) tie[k] = make_int2(I, J);
+        }
     }
 }
 
@@ -170,31 +302,97 @@ int grow(T** p, size_t* cap, size_t n) {
     return PURIFY_OK;
 }
 
-// Read the block norms, choose the drops, zero them on the device.
-int truncate_step(purify_ctx* h, Pattern& pat, double tau, __nv_bfloat16* planes, int s, int n_pad,
-                  double* out64, int n, std::vector<float>& bn2) {
+// Zero the chosen blocks in the digit planes and / or the float64 result.
+int apply_drops(purify_ctx* h, size_t count, __nv_bfloat16* planes, int s, int n_pad, double* out64, int n) {
     MixedState* ms = h->mixed;
-    const int nb = pat.nb;
-    PURIFY_CUDA_TRY(cudaMemcpyAsync(bn2.data(), ms->bnorm2, sizeof(float) * (size_t)nb * nb,
-                                    cudaMemcpyDeviceToHost, h->stream));
-    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    std::vector<int2> drop;
-    select_drops(pat, bn2.data(), tau, drop);
-    if (drop.empty()) return PURIFY_OK;
-    PURIFY_TRY(grow(&ms->drops, &ms->drops_cap, drop.size()));
-    PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->drops, drop.data(), sizeof(int2) * drop.size(), cudaMemcpyHostToDevice,
-                                    h->stream));
+    if (count == 0) return PURIFY_OK;
     if (planes) {
-        mask_planes_kernel<<<(unsigned)drop.size(), 256, 0, h->stream>>>(planes, s, n_pad, ms->drops);
+        mask_planes_kernel<<<(unsigned)count, 256, 0, h->stream>>>(planes, s, n_pad, ms->drops);
         PURIFY_CUDA_TRY(cudaGetLastError());
         count_launches(1);
     }
     if (out64) {
-        mask_f64_kernel<<<(unsigned)drop.size(), 256, 0, h->stream>>>(out64, n, ms->drops);
+        mask_f64_kernel<<<(unsigned)count, 256, 0, h->stream>>>(out64, n, ms->drops);
         PURIFY_CUDA_TRY(cudaGetLastError());
         count_launches(1);
     }
     return PURIFY_OK;
+}
+
+// Choose the drops of one step on the device (see trunc_hist_kernel) and
+// zero them; the host receives the dropped blocks for its pattern and walks
+// the blocks tied at the selected norm in (row, column) order.
+int truncate_step(purify_ctx* h, Pattern& pat, double tau, __nv_bfloat16* planes, int s, int n_pad,
+                  double* out64, int n, std::vector<float>&) {
+    MixedState* ms = h->mixed;
+    const int nb = pat.nb, words = pat.words;
+    const double budget = tau * tau;
+    const size_t upper = (size_t)nb * (nb + 1) / 2;
+    constexpr int kTieCap = 1 << 16;
+    PURIFY_TRY(grow(&ms->drops, &ms->drops_cap, upper + kTieCap));
+    PURIFY_TRY(grow(&ms->pat_dev, &ms->pat_dev_cap, pat.bits.size()));
+    if (!ms->tsel) PURIFY_CUDA_TRY(cudaMalloc(&ms->tsel, sizeof(TruncSel)));
+    TruncSel* sel = (TruncSel*)ms->tsel;
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->pat_dev, pat.bits.data(), sizeof(uint64_t) * pat.bits.size(),
+                                    cudaMemcpyHostToDevice, h->stream));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(sel, 0, sizeof(TruncSel), h->stream));
+    int64_t grid = ((int64_t)nb * nb + 255) / 256;
+    if (grid > 152 * 8) grid = 152 * 8;
+    int2* tie_dev = ms->drops + upper;
+    for (int pass = 0; pass < 2; ++pass) {
+        trunc_hist_kernel<<<(unsigned)grid, 256, 0, h->stream>>>(ms->bnorm2, ms->pat_dev, words, nb, budget, pass, sel);
+        trunc_scan_kernel<<<1, 1024, 0, h->stream>>>(sel, pass);
+    }
+    trunc_collect_kernel<<<(unsigned)grid, 256, 0, h->stream>>>(ms->bnorm2, ms->pat_dev, words, nb, budget, sel,
+                                                                ms->drops, (int)upper, tie_dev, kTieCap);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(6);
+    struct {
+        unsigned long long cum_before;
+        int found, bin, hi;
+        unsigned key;
+        int ndrop, ntie;
+    } head;
+    static_assert(sizeof(head) == sizeof(TruncSel) - offsetof(TruncSel, cum_before), "TruncSel tail layout");
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(&head, &sel->cum_before, sizeof(head), cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (head.ntie > kTieCap) return PURIFY_ERR_INTERNAL;
+    size_t nd = (size_t)head.ndrop;
+    std::vector<int2> drop(nd);
+    if (nd)
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(drop.data(), ms->drops, sizeof(int2) * nd, cudaMemcpyDeviceToHost, h->stream));
+    std::vector<int2> tie((size_t)head.ntie);
+    if (head.ntie)
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(tie.data(), tie_dev, sizeof(int2) * tie.size(), cudaMemcpyDeviceToHost,
+                                        h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (head.found && !tie.empty()) {
+        // the tied blocks in (row, column) order, each with its fixed-point
+        // mass, while the budget holds
+        std::sort(tie.begin(), tie.end(), [](int2 a, int2 b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
+        float mk;
+        std::memcpy(&mk, &head.key, sizeof(mk));
+        unsigned long long acc = head.cum_before;
+        const unsigned long long cap = (unsigned long long)kBudgetUnits;
+        size_t k = 0;
+        for (; k < tie.size(); ++k) {
+            const double mass = (tie[k].x == tie[k].y ? 1.0 : 2.0) * (double)mk;
+            const unsigned long long fx = budget > 0.0 ? (unsigned long long)(mass / budget * kBudgetUnits) : 0ull;
+            if (mass > 0.0 && acc + fx > cap) break;
+            acc += fx;
+        }
+        if (k) {
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->drops + nd, tie.data(), sizeof(int2) * k, cudaMemcpyHostToDevice,
+                                            h->stream));
+            drop.insert(drop.end(), tie.begin(), tie.begin() + (ptrdiff_t)k);
+            nd += k;
+        }
+    }
+    for (const int2& b : drop) {
+        pat.clear(b.x, b.y);
+        pat.clear(b.y, b.x);
+    }
+    return apply_drops(h, nd, planes, s, n_pad, out64, n);
 }
 
 void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
