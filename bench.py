@@ -36,13 +36,13 @@ TENSOR_FLOP_PER_CLK_SM = 8192    # dense bf16 tcgen05 rate per SM and clock (nom
 FP64_FLOP_PER_CLK_SM = 4         # two float64 FMAs per SM and clock (nominal)
 # The tensor pipe's active share of one digit-plane product launch (ncu
 # sm__pipe_tensor_cycles_active of digit_gemm_kernel<32, 5>, n = 4096).
-TENSOR_PIPE_PCT_NCU = 67.6
+TENSOR_PIPE_PCT_NCU = 67.1
 TENSOR_PIPE_SOURCE = "profiles/digit_gemm_kc32_s5_n4096.md (ncu, one launch, n=4096, S=5)"
 # DRAM bytes (read + write) of one digit-plane product launch, from one ncu
 # capture of digit_gemm_kernel<32, 5> at n = 4096 (bytes per launch).
-TRAFFIC_DIGIT_GEMM = 776.5e6
+TRAFFIC_DIGIT_GEMM = 783.8e6
 TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of digit_gemm_kernel<32,5>, n=4096, one launch "
-                  "(525.6 MB read + 250.9 MB written)")
+                  "(530.2 MB read + 253.7 MB written)")
 
 
 def parse():
@@ -126,7 +126,10 @@ def make_device_inputs(n, rank, count, dev):
 def run_batch(P, dev, stream, count=256, reps=3, tol=1e-9):
     """The batch workload: `count` dense Hamiltonians, n log-uniform in
     [64, 2048], gap log-uniform in [1e-3, 1e-1], nocc = round(U(0.3, 0.7) n),
-    TC_SF, all in one CUDA-graph replay of grouped launches."""
+    TC_SF.  The value is one CUDA-graph replay of the single queue launch in
+    which every instance advances on its own; the same batch with one grouped
+    launch per round is timed beside it."""
+    import numpy as np
     import torch
     from paper_1101_0265_gb300 import inputs as I
     specs = I.batch_specs(count)
@@ -138,21 +141,31 @@ def run_batch(P, dev, stream, count=256, reps=3, tol=1e-9):
         metas.append(h)
         del F
     torch.cuda.synchronize(dev)
-    B.run(use_graph=True)        # capture + first replay (warm-up)
-    times = []
-    for _ in range(reps):
-        B.run(use_graph=True)
-        times.append(B.stats(ids[0])["seconds"])
-    t = statistics.median(times)
+    out = {}
+    for rounds in (False, True):
+        B.run(use_graph=True, rounds=rounds)        # capture + first replay (warm-up)
+        times = []
+        for _ in range(reps):
+            B.run(use_graph=True, rounds=rounds)
+            times.append(B.stats(ids[0])["seconds"])
+        out[rounds] = statistics.median(times)
+        if not rounds:
+            D0 = [B.density(i) for i in ids[:4]]
+        else:   # the two modes give the same densities, bit for bit
+            same = all(np.array_equal(B.density(i), d) for i, d in zip(ids[:4], D0))
+    t = out[False]
     st = [B.stats(i) for i in ids]
     B.close()
     tensor = sum(x["tensor_flops"] for x in st)
     return {"workload": f"{count} dense F, n log-uniform [64, 2048], gap log-uniform [1e-3, 1e-1], "
-                        f"TC_SF tol {tol:g}, one CUDA-graph replay per batch",
+                        f"TC_SF tol {tol:g}, one CUDA-graph replay of one queue launch per batch",
             "value": count / t, "unit": "purifications/s", "ms_per_batch": 1e3 * t,
             "replays": reps, "tensor_tflops": tensor / t / 1e12,
             "multiplications": sum(x["multiplications"] for x in st),
-            "max_trace_err": max(x["trace_err"] for x in st)}
+            "max_trace_err": max(x["trace_err"] for x in st),
+            "grouped_per_round": {"value": count / out[True], "ms_per_batch": 1e3 * out[True],
+                                  "tensor_tflops": tensor / out[True] / 1e12,
+                                  "same_densities": bool(same)}}
 
 
 def run_serve(P, dev, stream, rate, count, budget_gb=64.0, tol=1e-9):
@@ -204,7 +217,8 @@ def run_serve(P, dev, stream, rate, count, budget_gb=64.0, tol=1e-9):
             "peak_concurrent": peak_live, "hbm_budget_gb": budget_gb}
 
 
-def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsite=3.0):
+def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsite=3.0,
+                sweep_sizes=(16, 20, 24, 28, 32), sweep_onsite=6.0):
     """The block-sparse workload: periodic L^3 cubic tight-binding lattice
     (onsite +-0.5 by sublattice + N(0, 0.05), hopping -1 + U(-0.1, 0.1)),
     n = L^3, nocc = n/2, mu = 0, loaded from COO, 32 x 32 blocks.
@@ -214,6 +228,9 @@ def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsi
     - "equal_budget": TC_SF against TC_MONO with the same total truncation
       budget (tau = budget / (m + 1)), at the C3 onsite splitting and at a
       wider one (+-wide_onsite), where the density stays sparse.
+    - "n_sweep": TC_SF block-sparse at tau per step on L^3 lattices of
+      growing L with onsite +-sweep_onsite: time per step and the kept
+      blocks per block row against n.
     One handle per mode, warmed once; device-event time of one run each."""
     import torch
     from paper_1101_0265_gb300 import inputs as I
@@ -259,12 +276,30 @@ def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsi
             e["speedup_sparse_vs_dense"] = e["TC_SF_dense"]["seconds"] / e["TC_SF"]["seconds"]
         e["speedup_sf_vs_mono"] = e["TC_MONO"]["seconds"] / e["TC_SF"]["seconds"]
         eq.append(e)
+    # n-sweep: the same construction at growing L with a wide onsite
+    # splitting (short decay length of D against the box), tau per step
+    sweep = []
+    for Ls in sweep_sizes:
+        lt = I.lattice_hamiltonian(Ls, onsite=sweep_onsite)
+        r = case(lt, "TC_SF", True, trunc_tau=tau)
+        nb = lt.n // 32
+        kept = r["nnz_blocks"][-1]
+        n_pad = (lt.n + 127) // 128 * 128
+        sweep.append({"L": Ls, "n": lt.n, "seconds": r["seconds"], "iterations": r["iterations"],
+                      "seconds_per_step": r["seconds"] / max(1, r["iterations"]),
+                      "kept_blocks_per_block_row": 2 * kept / nb, "final_fill": r["final_fill"],
+                      "kept_block_bytes_per_plane": kept * 2 * 32 * 32 * 2,
+                      "dense_plane_bytes": n_pad * n_pad * 2, "trace_err": r["trace_err"]})
     for pur in pool.values():
         pur.close()
     torch.cuda.empty_cache()
     return {"workload": f"{L}^3 periodic cubic tight-binding lattice, n={lat.n}, COO input, "
                         f"32x32 blocks, tol {tol:g}",
-            "n": lat.n, "C3": c3, "equal_budget": eq}
+            "n": lat.n, "C3": c3, "equal_budget": eq,
+            "n_sweep": {"onsite": sweep_onsite, "tau": tau, "scheme": "TC_SF block-sparse", "runs": sweep,
+                        "note": "kept_block_bytes_per_plane is what the kept blocks of the last iterate take "
+                                "(both triangles); the digit planes are allocated dense (dense_plane_bytes "
+                                "per plane)"}}
 
 
 def peaks():
@@ -461,6 +496,7 @@ def summarize_accuracy(results, bound=1e-6):
 
 
 def main():
+    t_start = time.perf_counter()
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -704,7 +740,10 @@ def main():
     ref = None
     if not args.no_fp64_check and args.precision == "mixed":
         ref = P.Purifier(device=local, stream=stream.cuda_stream, precision="fp64")
+    wall = {"headline": time.perf_counter() - t_start}
+    t_sec = time.perf_counter()
     results, t64 = accuracy_pass(P, pur, hs, Fd, Dc, schemes, args.tol, set_h, dev, ref=ref)
+    wall["accuracy"] = time.perf_counter() - t_sec
     if ref:
         ref.close()
         line["fp64_path"] = {"value": per_step / t64, "unit": "matrices/s",
@@ -722,6 +761,7 @@ def main():
         line["value"] = None
         line["e2e"]["value"] = None
     # the whole path with other bounds / refinement settings, one pass each
+    t_sec = time.perf_counter()
     if world == 1 and args.precision == "mixed" and not args.no_variants:
         variants = {}
         k_var = max(1, args.steps // 4)
@@ -745,16 +785,26 @@ def main():
                             "on the tensor cores; refine_fp64 appends one float64 McWeeny step (two DFMA "
                             "products) on the float64 pipe")
         line["variants"] = variants
+    wall["variants"] = time.perf_counter() - t_sec
+    t_sec = time.perf_counter()
     if world == 1 and args.precision == "mixed" and not args.no_batch:
         line["batch"] = run_batch(P, dev, stream, count=args.batch_size)
+    wall["batch"] = time.perf_counter() - t_sec
+    t_sec = time.perf_counter()
     if world == 1 and args.precision == "mixed" and args.serve_rates:
         line["serve"] = [run_serve(P, dev, stream, float(r), args.serve_requests)
                          for r in args.serve_rates.split(",")]
+    wall["serve"] = time.perf_counter() - t_sec
+    t_sec = time.perf_counter()
     if world == 1 and args.precision == "mixed" and not args.no_lattice:
         line["lattice"] = run_lattice(P, dev, stream, L=args.lattice_size)
+    wall["lattice"] = time.perf_counter() - t_sec
+    t_sec = time.perf_counter()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(hs, [F.numpy() for F in Fh], args.tol,
                                             estimate_bounds=not args.exact_bounds)
+    wall["cpu_baseline"] = time.perf_counter() - t_sec
+    line["wall_seconds"] = {k: round(v, 1) for k, v in wall.items()}
     pur.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -383,10 +383,26 @@ int purify_batch_add(purify_batch_t b, const double* F, int64_t n, int64_t ld, i
  * completed in this round. */
 int purify_batch_step(purify_batch_t b, int* active, int* finished);
 
-/* Run every instance of the batch from f_0 to completion.  use_graph = 1
- * captures the splits and all rounds into one CUDA graph, replayed by later
- * calls while the set of instances is unchanged. */
-int purify_batch_run(purify_batch_t b, int use_graph);
+/* Run every instance of the batch from f_0 to completion.
+ *
+ * mode = PURIFY_BATCH_QUEUE (0): the f_0 splits, then ONE persistent launch of
+ *   the product kernel over a device queue holding every product of every
+ *   instance (round-major, larger instances first).  An item of product k of
+ *   an instance waits on the device, with the bounded wait of
+ *   opt->wait_kcycles, until product k-1 of that instance has completed, so
+ *   each instance advances on its own and retires on the device.
+ * mode | PURIFY_BATCH_GRAPH (1): the launches are captured once into a CUDA
+ *   graph and replayed by later calls while the set of instances is
+ *   unchanged.
+ * mode | PURIFY_BATCH_ROUNDS (2): one grouped launch per round (the next
+ *   product of every unfinished instance), ordered by the host.
+ * Every mode gives the same densities, bit for bit.  Errors: INVALID_ARG for
+ * another mode; TIMEOUT when a device wait ran out (see purify_stats_t
+ * device_flag of purify_get_stats for the single-matrix analogue). */
+#define PURIFY_BATCH_QUEUE 0
+#define PURIFY_BATCH_GRAPH 1
+#define PURIFY_BATCH_ROUNDS 2
+int purify_batch_run(purify_batch_t b, int mode);
 
 /* 1 when instance `id` has finished, 0 while it is pending or running. */
 int purify_batch_status(purify_batch_t b, int id);

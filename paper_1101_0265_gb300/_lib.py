@@ -500,8 +500,12 @@ class Batch:
         _check(self._lib.purify_batch_step(self._h, C.byref(a), C.byref(f)), "purify_batch_step")
         return a.value, f.value
 
-    def run(self, use_graph: bool = True):
-        _check(self._lib.purify_batch_run(self._h, int(use_graph)), "purify_batch_run")
+    def run(self, use_graph: bool = True, rounds: bool = False):
+        """Run every instance to completion: one queue launch in which each
+        instance advances on its own (rounds=False), or one grouped launch
+        per round (rounds=True); captured in a CUDA graph with use_graph."""
+        mode = (1 if use_graph else 0) | (2 if rounds else 0)
+        _check(self._lib.purify_batch_run(self._h, mode), "purify_batch_run")
 
     def done(self, i: int) -> bool:
         r = self._lib.purify_batch_status(self._h, int(i))

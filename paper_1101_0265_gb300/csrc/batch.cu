@@ -14,6 +14,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <queue>
 #include <vector>
 
 #include "digits_kernel.cuh"
@@ -65,6 +66,14 @@ void free_instance(Instance& in) {
     in.Xd[0] = in.Xd[1] = in.Sd = nullptr;
 }
 
+// Staging of a whole-batch queue launch (offsets into the staging buffers).
+struct QueuePlan {
+    int smax = 0;
+    int products = 0;
+    int items = 0;
+    size_t maps_off = 0, prm_off = 0, dep_off = 0, need_off = 0, cnt_off = 0, work_off = 0, end = 0;
+};
+
 }  // namespace
 
 struct purify_batch {
@@ -83,6 +92,12 @@ struct purify_batch {
     void* dev_buf = nullptr;
     size_t dev_cap = 0;
     std::vector<uint8_t> host_buf;
+    // staging of the last whole-batch queue (own buffer: a captured graph
+    // reads it on every replay)
+    void* qdev_buf = nullptr;
+    size_t qdev_cap = 0;
+    QueuePlan last_queue;
+    int last_mode = -1;
     // graph of the last full run
     cudaGraphExec_t graph = nullptr;
     std::vector<int> graph_ids;
@@ -293,6 +308,133 @@ int launch_groups(purify_batch* B, const std::vector<GroupPlan>& groups) {
     return PURIFY_OK;
 }
 
+// The whole batch as one persistent launch (queue mode of the product
+// kernel): every product of every instance in one work list, claimed in list
+// order by the persistent CTAs.  Each product's parameters and tensor maps
+// are staged in device memory; on the device an item of product k of an
+// instance waits until product k-1 of that instance has completed, so each
+// instance advances on its own.  The list order comes from a list-scheduling
+// simulation of the launch on the host: CTAs take the next item when they
+// come free, an instance's next product becomes available once its previous
+// one has finished, and among available products the one with the longest
+// items goes first.  An item is listed only after every item of the product
+// it waits for, so the CTAs holding those items are always running (no
+// deadlock whatever number of CTAs is resident).
+// Layout in host_buf / qdev_buf: maps | params | dep | need | cnt | work.
+int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueuePlan& q) {
+    q = QueuePlan();
+    for (Instance* in : all)
+        for (const DigitStep& st : in->steps) q.smax = std::max(q.smax, st.s_in);
+    // products: instance-major; product p of instance i depends on p - 1
+    struct Prod {
+        Instance* in;
+        int k;         // step index
+        int T;         // tile rows
+        int items;     // upper tiles
+        double cost;   // modelled cycles of one item
+        int dep;       // product index it waits for, -1: none
+        int next = -1; // the instance's following product
+    };
+    std::vector<Prod> prods;
+    for (Instance* in : all) {
+        const int T = in->n_pad / 128;
+        for (int k = 0; k < (int)in->steps.size(); ++k) {
+            const int s = in->steps[k].s_in;
+            // MMA: s(s+1)/2 digit pairs of a 128 x 128 x n_pad product at 8192
+            // flop per clock; plus a fixed epilogue
+            const double cost = 0.5 * s * (s + 1) * 4.0 * in->n_pad + 3000.0;
+            Prod p{in, k, T, T * (T + 1) / 2, cost, k ? (int)prods.size() - 1 : -1};
+            if (k) prods.back().next = (int)prods.size();
+            prods.push_back(p);
+        }
+    }
+    q.products = (int)prods.size();
+    size_t items = 0;
+    for (const Prod& p : prods) items += (size_t)p.items;
+    q.items = (int)items;
+    q.maps_off = 0;
+    q.prm_off = align_up(q.maps_off + sizeof(CUtensorMap) * 2 * (size_t)q.products, 128);
+    q.dep_off = align_up(q.prm_off + sizeof(dk::DigitGemmParams) * (size_t)q.products, 128);
+    q.need_off = align_up(q.dep_off + sizeof(int) * (size_t)q.products, 128);
+    q.cnt_off = align_up(q.need_off + sizeof(int) * (size_t)q.products, 128);
+    q.work_off = align_up(q.cnt_off + sizeof(int) * (size_t)(q.products + 1), 128);  // + the claim ticket
+    q.end = q.work_off + sizeof(int4) * items;
+    if (B->host_buf.size() < q.end) B->host_buf.resize(q.end);
+    uint8_t* hb = B->host_buf.data();
+    CUtensorMap* maps = (CUtensorMap*)(hb + q.maps_off);
+    dk::DigitGemmParams* prm = (dk::DigitGemmParams*)(hb + q.prm_off);
+    int* dep = (int*)(hb + q.dep_off);
+    int* need = (int*)(hb + q.need_off);
+    int4* work = (int4*)(hb + q.work_off);
+    for (int pi = 0; pi < q.products; ++pi) {
+        const Prod& p = prods[pi];
+        PURIFY_TRY(fill_queue_product(p.in->steps[p.k], q.smax, &prm[pi], &maps[2 * pi]));
+        dep[pi] = p.dep;
+        need[pi] = kEpiWarps * p.items;
+    }
+    // list scheduling over B->ctas simulated CTAs
+    using TP = std::pair<double, int>;
+    std::priority_queue<double, std::vector<double>, std::greater<double>> cta;
+    for (int c = 0; c < std::max(1, B->ctas); ++c) cta.push(0.0);
+    std::priority_queue<TP, std::vector<TP>, std::greater<TP>> future;  // (ready time, product)
+    std::priority_queue<TP> ready;                                      // (item cost, -product)
+    std::vector<int> placed(q.products, 0);
+    std::vector<double> finish(q.products, 0.0);
+    for (int pi = 0; pi < q.products; ++pi)
+        if (prods[pi].dep < 0) future.push({0.0, pi});
+    size_t w = 0;
+    while (w < items) {
+        double f = cta.top();
+        cta.pop();
+        while (!future.empty() && future.top().first <= f) {
+            ready.push({prods[future.top().second].cost, -future.top().second});
+            future.pop();
+        }
+        if (ready.empty()) {  // this CTA idles until the next product is available
+            f = future.top().first;
+            ready.push({prods[future.top().second].cost, -future.top().second});
+            future.pop();
+        }
+        const int pi = -ready.top().second;
+        Prod& p = prods[pi];
+        const int r = placed[pi]++;
+        // items of a product in order: tile column tj, rows ti <= tj
+        int tj = 0;
+        while ((tj + 1) * (tj + 2) / 2 <= r) ++tj;
+        const int ti = r - tj * (tj + 1) / 2;
+        work[w++] = make_int4(pi, ti, tj, 0);
+        const double done = f + p.cost;
+        finish[pi] = std::max(finish[pi], done);
+        cta.push(done);
+        if (placed[pi] == p.items) {
+            ready.pop();
+            if (p.next >= 0) future.push({finish[pi], p.next});
+        }
+    }
+    // the device waits rely on this: every item after all items of the
+    // product it waits for, and every item listed exactly once
+    std::vector<int> seen(q.products, 0);
+    for (size_t k = 0; k < items; ++k) {
+        const int4 v = work[k];
+        if (v.x < 0 || v.x >= q.products || v.y < 0 || v.y > v.z || v.z >= prods[v.x].T) return PURIFY_ERR_INTERNAL;
+        if (dep[v.x] >= 0 && seen[dep[v.x]] != prods[dep[v.x]].items) return PURIFY_ERR_INTERNAL;
+        ++seen[v.x];
+    }
+    for (int pi = 0; pi < q.products; ++pi)
+        if (seen[pi] != prods[pi].items) return PURIFY_ERR_INTERNAL;
+    return PURIFY_OK;
+}
+
+int launch_queue(purify_batch* B, const QueuePlan& q) {
+    if (q.items == 0) return PURIFY_OK;
+    uint8_t* dev = (uint8_t*)B->qdev_buf;
+    PURIFY_CUDA_TRY(cudaMemsetAsync(dev + q.cnt_off, 0, sizeof(int) * (size_t)(q.products + 1), B->stream));
+    return launch_digit_queue(q.smax, (const dk::DigitGemmParams*)(dev + q.prm_off), (const CUtensorMap*)(dev + q.maps_off),
+                              (const int*)(dev + q.dep_off), (const int*)(dev + q.need_off), (int*)(dev + q.cnt_off),
+                              q.products, (const int4*)(dev + q.work_off), q.items, B->scratch, B->ctas, B->err,
+                              B->stream, 1000ll * B->opt.wait_kcycles);
+}
+
 int queue_split(purify_batch* B, Instance& in) {
     PURIFY_CUDA_TRY(cudaMemsetAsync(in.red, 0, 4 * sizeof(double), B->stream));
     return launch_split(in.F, in.n, in.n, in.n_pad, in.split_a, in.split_b, in.split_e, in.split_s, in.rbits,
@@ -376,6 +518,7 @@ int purify_batch_destroy(purify_batch_t B) {
     cudaFree(B->scratch);
     cudaFree(B->err);
     cudaFree(B->dev_buf);
+    cudaFree(B->qdev_buf);
     if (B->e0) cudaEventDestroy(B->e0);
     if (B->e1) cudaEventDestroy(B->e1);
     if (B->join_ev) cudaEventDestroy(B->join_ev);
@@ -498,11 +641,27 @@ int purify_batch_step(purify_batch_t B, int* active_out, int* finished_out) {
     return join_streams(B->user_stream, B->stream, B->join_ev);
 }
 
-// Run every added instance from its start to completion.  With use_graph,
-// the whole run (splits and all rounds) is captured once into a CUDA graph
-// and replayed while the set of instances is unchanged.
-int purify_batch_run(purify_batch_t B, int use_graph) {
-    if (!B) return PURIFY_ERR_INVALID_ARG;
+int ensure_qdev(purify_batch* B, size_t bytes) {
+    if (bytes <= B->qdev_cap) return PURIFY_OK;
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(B->stream));
+    cudaFree(B->qdev_buf);
+    B->qdev_buf = nullptr;
+    B->qdev_cap = 0;
+    const size_t cap = std::max(bytes, (size_t)1 << 16) * 2;
+    PURIFY_CUDA_TRY(cudaMalloc(&B->qdev_buf, cap));
+    B->qdev_cap = cap;
+    return PURIFY_OK;
+}
+
+// Run every added instance from its start to completion.  mode bit 0: the
+// whole run is captured once into a CUDA graph and replayed while the set of
+// instances is unchanged.  mode bit 1: one grouped launch per round (the
+// products of all instances at the same step, host-ordered) instead of the
+// single queue launch in which every instance advances on its own.
+int purify_batch_run(purify_batch_t B, int mode) {
+    if (!B || mode < 0 || mode > 3) return PURIFY_ERR_INVALID_ARG;
+    const bool use_graph = mode & 1;
+    const bool rounds_mode = mode & 2;
     PURIFY_CUDA_TRY(cudaSetDevice(B->device));
     PURIFY_TRY(join_streams(B->stream, B->user_stream, B->join_ev));
     std::vector<Instance*> all;
@@ -513,38 +672,52 @@ int purify_batch_run(purify_batch_t B, int use_graph) {
             ids.push_back(in->id);
         }
     if (all.empty()) return PURIFY_OK;
-    const bool reuse = use_graph && B->graph && ids == B->graph_ids;
+    const bool reuse = use_graph && B->graph && ids == B->graph_ids && B->last_mode == mode;
     std::vector<std::vector<GroupPlan>> rounds;
     if (!reuse) {
-        // stage every round up front (host arithmetic, untimed)
-        size_t off = 0;
-        for (Instance* in : all) in->k = 0;
-        for (;;) {
-            std::vector<Instance*> act;
-            for (Instance* in : all)
-                if (in->k < (int)in->steps.size()) act.push_back(in);
-            if (act.empty()) break;
-            std::vector<GroupPlan> groups;
-            PURIFY_TRY(stage_round(B, act, off, groups));
-            rounds.push_back(groups);
-            for (Instance* in : act) ++in->k;
-        }
-        PURIFY_TRY(ensure_dev(B, off));
-        PURIFY_CUDA_TRY(cudaMemcpyAsync(B->dev_buf, B->host_buf.data(), off, cudaMemcpyHostToDevice, B->stream));
-        PURIFY_CUDA_TRY(cudaStreamSynchronize(B->stream));
+        // stage the whole batch up front (host arithmetic, untimed)
         if (B->graph) {
             cudaGraphExecDestroy(B->graph);
             B->graph = nullptr;
             B->graph_ids.clear();
         }
+        if (rounds_mode) {
+            size_t off = 0;
+            for (Instance* in : all) in->k = 0;
+            for (;;) {
+                std::vector<Instance*> act;
+                for (Instance* in : all)
+                    if (in->k < (int)in->steps.size()) act.push_back(in);
+                if (act.empty()) break;
+                std::vector<GroupPlan> groups;
+                PURIFY_TRY(stage_round(B, act, off, groups));
+                rounds.push_back(groups);
+                for (Instance* in : act) ++in->k;
+            }
+            PURIFY_TRY(ensure_dev(B, off));
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(B->dev_buf, B->host_buf.data(), off, cudaMemcpyHostToDevice, B->stream));
+        } else {
+            QueuePlan q;
+            PURIFY_TRY(stage_queue(B, all, q));
+            PURIFY_TRY(ensure_qdev(B, q.end));
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(B->qdev_buf, B->host_buf.data(), q.end, cudaMemcpyHostToDevice, B->stream));
+            B->last_queue = q;
+        }
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(B->stream));
+        B->last_mode = mode;
         if (use_graph) {
+            PURIFY_TRY(prepare_digit_kernels());
             cudaGraph_t g = nullptr;
             PURIFY_CUDA_TRY(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
             int r = PURIFY_OK;
             for (Instance* in : all)
                 if (r == PURIFY_OK) r = queue_split(B, *in);
-            for (auto& groups : rounds)
-                if (r == PURIFY_OK) r = launch_groups(B, groups);
+            if (rounds_mode) {
+                for (auto& groups : rounds)
+                    if (r == PURIFY_OK) r = launch_groups(B, groups);
+            } else if (r == PURIFY_OK) {
+                r = launch_queue(B, B->last_queue);
+            }
             cudaError_t e = cudaStreamEndCapture(B->stream, &g);
             if (r == PURIFY_OK && e != cudaSuccess) r = cuda_status(e, "cudaStreamEndCapture");
             if (r == PURIFY_OK) {
@@ -561,7 +734,11 @@ int purify_batch_run(purify_batch_t B, int use_graph) {
         PURIFY_CUDA_TRY(cudaGraphLaunch(B->graph, B->stream));
     } else {
         for (Instance* in : all) PURIFY_TRY(queue_split(B, *in));
-        for (auto& groups : rounds) PURIFY_TRY(launch_groups(B, groups));
+        if (rounds_mode) {
+            for (auto& groups : rounds) PURIFY_TRY(launch_groups(B, groups));
+        } else {
+            PURIFY_TRY(launch_queue(B, B->last_queue));
+        }
     }
     PURIFY_CUDA_TRY(cudaEventRecord(B->e1, B->stream));
     PURIFY_TRY(check_err(B));

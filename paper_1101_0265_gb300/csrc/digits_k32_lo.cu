@@ -7,9 +7,9 @@ namespace dk {
 
 KernelFn kernel_k32_lo(int s) {
     switch (s) {
-        case 1: return digit_gemm_kernel<32, 1>;
-        case 2: return digit_gemm_kernel<32, 2>;
-        case 3: return digit_gemm_kernel<32, 3>;
+        case 1: return digit_gemm_kernel<32, 1, false>;
+        case 2: return digit_gemm_kernel<32, 2, false>;
+        case 3: return digit_gemm_kernel<32, 3, false>;
         default: return nullptr;
     }
 }

@@ -7,9 +7,9 @@ namespace dk {
 
 KernelFn kernel_k64_hi(int s) {
     switch (s) {
-        case 4: return digit_gemm_kernel<64, 4>;
-        case 5: return digit_gemm_kernel<64, 5>;
-        case 6: return digit_gemm_kernel<64, 6>;
+        case 4: return digit_gemm_kernel<64, 4, false>;
+        case 5: return digit_gemm_kernel<64, 5, false>;
+        case 6: return digit_gemm_kernel<64, 6, false>;
         default: return nullptr;
     }
 }

@@ -335,12 +335,24 @@ struct DigitLaunch {
     float* partial;                  // [slot][part][region 8][acc 4][16-col group 4][row 32][16]
     int* split_cnt;                  // [slot][region 8], zero at launch
     int* claim;                      // split launches: counter of claimed split items, zero at launch
+    // queue mode (a whole batch of purifications in one launch; null: off):
+    // every product's parameters and its A and B tensor maps in global
+    // memory (prms and maps are unused), each product with its own digit
+    // count <= the kernel's S; an item's operands are loaded only once the
+    // instance's previous product (qdep, -1: none) is complete, i.e. its qcnt
+    // has counted qneed epilogue-warp completions
+    const DigitGemmParams* qprm;
+    const CUtensorMap* qmaps;        // [2 * products]
+    const int* qdep;
+    const int* qneed;
+    int* qcnt;                       // zero at launch
 };
 
-// Items of a split launch's last wave are claimed at run time (an atomic
-// counter), at most MAX_CLAIMS per CTA: a CTA whose whole tiles ran slow
-// leaves the parts to CTAs that are free.  The producer claims and hands each
-// claimed item to the MMA and epilogue warps through shared memory.
+// Items of a split launch's last wave, and every item of a queue launch, are
+// claimed at run time (an atomic counter): a CTA whose earlier items ran slow
+// leaves the rest to CTAs that are free.  The producer claims and hands each
+// claimed item to the MMA and epilogue warps through a ring of MAX_CLAIMS
+// shared-memory slots.
 constexpr int MAX_CLAIMS = 8;
 
 constexpr int REGION_FLOATS = NUM_ACC * EPI_COLS * 32;  // one epilogue warp's accumulators
@@ -382,8 +394,89 @@ __device__ __forceinline__ void dense_k_range(const DigitLaunch& L, int nkt, int
     }
 }
 
+template <bool Q>
 __device__ __forceinline__ const DigitGemmParams& params_of(const DigitLaunch& L, int g) {
-    return L.prms[g];
+    if constexpr (Q)
+        return L.qprm[g];
+    else
+        return L.prms[g];
+}
+
+// Queue mode: wait (bounded) until product d's epilogue warps have all
+// counted themselves done; false when the wait gives up.  The acquire orders
+// their plane stores before this thread's later copies, and the proxy fence
+// makes them visible to the tensor copies (async proxy).
+__device__ __forceinline__ bool wait_product(const DigitLaunch& L, int d, long long limit) {
+    const int need = L.qneed[d];
+    const int* c = L.qcnt + d;
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+    if (v < need) {
+        const long long t0 = clock64();
+        do {
+            // give up at the bound, or at once when another CTA has failed
+            // (the product may then never complete)
+            if (clock64() - t0 > limit || *(volatile int*)L.err) return false;
+            __nanosleep(64);
+            asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
+        } while (v < need);
+    }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    return true;
+}
+
+// A tensor map in global memory, written by the host before the launch, is
+// read by the copy engine through the tensor-map proxy: acquire it first.
+__device__ __forceinline__ void acquire_map(const CUtensorMap* m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m) : "memory");
+}
+
+template <int KC, int SS>
+__device__ __forceinline__ void issue_chunk(uint32_t tmem, uint64_t da, uint64_t db, uint32_t later);
+
+// issue_chunk for a digit count known at run time (<= SS)
+template <int KC, int SS>
+__device__ __forceinline__ void issue_chunk_runtime(int s, uint32_t tmem, uint64_t da, uint64_t db, uint32_t later) {
+    if constexpr (SS >= 1) {
+        if (s == SS) {
+            issue_chunk<KC, SS>(tmem, da, db, later);
+            return;
+        }
+        issue_chunk_runtime<KC, SS - 1>(s, tmem, da, db, later);
+    }
+}
+
+// The unrolled MMA issue of one k-chunk for SS digit planes (pairs p + q <
+// SS; levels 0..2 in their own accumulators, >= 3 in the fourth).  A and B
+// planes are TILE x KC bf16 each, B after the kernel's S planes of A.  The
+// chunk is issued in 32-wide k-blocks, inside a block pair by pair with the
+// pair's two 16-wide k-steps back to back (runs of MMAs into one accumulator
+// keep the tensor pipe busier than alternating accumulators): every
+// accumulator then receives its additions in the same order for 32- and
+// 64-wide chunks, so results do not depend on that choice of launch shape.
+template <int KC, int SS>
+__device__ __forceinline__ void issue_chunk(uint32_t tmem, uint64_t da, uint64_t db, uint32_t later) {
+    constexpr int PLANE_BYTES = TILE * KC * 2;
+    constexpr int KB = KC < 32 ? KC : 32;
+#pragma unroll
+    for (int kb = 0; kb < KC / KB; ++kb) {
+#pragma unroll
+        for (int p = 0; p < SS; ++p) {
+#pragma unroll
+            for (int q = 0; q < SS - p; ++q) {
+                const int a = (p + q < NUM_ACC - 1) ? p + q : NUM_ACC - 1;
+#pragma unroll
+                for (int k2 = 0; k2 < KB / 16; ++k2) {
+                    const int kk = kb * (KB / 16) + k2;
+                    // the first write of accumulator a in a tile is pair (0, a) at
+                    // k = 0; all later ones accumulate
+                    const uint32_t acc_in = (kk > 0 || p > 0 || q > NUM_ACC - 1) ? 1u : later;
+                    mma_bf16(tmem + (uint32_t)(a * TILE), da + (uint64_t)((p * PLANE_BYTES + kk * 32) >> 4),
+                             db + (uint64_t)((q * PLANE_BYTES + kk * 32) >> 4), IDESC, acc_in);
+                }
+            }
+        }
+    }
 }
 
 // Tile t of the upper triangle (ti <= tj) of a T x T tile grid, in bands of
@@ -433,24 +526,29 @@ __device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, lon
 // CTA's scratch (global, 128 x 128 x 8 bytes) so that tensor memory is
 // released before the polynomial, the re-split and the stores; those overlap
 // the next tile's MMAs.  All digit counts of a launch are S.
-template <int KC, int S>
+// Q: a queue launch (per-product parameters, tensor maps and digit counts in
+// device memory, dependency waits and completion counts); a separate
+// instantiation, so that the other launches keep their compile-time digit
+// count S throughout.
+template <int KC, int S, bool Q>
 __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ DigitLaunch L) {
     constexpr int PLANE_BYTES = TILE * KC * 2;  // one plane of one operand per stage
-    constexpr int s = S;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned operand area: stages x (A planes | B planes)
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int stage_bytes = 2 * S * PLANE_BYTES;
     const int stages = L.stages;
     uint64_t* bars = (uint64_t*)(base + (size_t)stages * stage_bytes);
-    // bars: full[stages] | empty[stages] | tmem_full | tmem_empty | drain | claim[MAX_CLAIMS]
+    // bars: full[stages] | empty[stages] | tmem_full | tmem_empty | drain | claim[MAX_CLAIMS] |
+    // claim_free[MAX_CLAIMS]
     uint64_t* full_bar = bars;
     uint64_t* empty_bar = bars + stages;
     uint64_t* tmem_full = bars + 2 * stages;
     uint64_t* tmem_empty = tmem_full + 1;
     uint64_t* drain = tmem_full + 2;
-    uint64_t* claim_bar = drain + 1;  // [MAX_CLAIMS], one phase each
-    uint32_t* tmem_slot = (uint32_t*)(claim_bar + MAX_CLAIMS);
+    uint64_t* claim_bar = drain + 1;                // [MAX_CLAIMS] ring: slot published
+    uint64_t* claim_free = claim_bar + MAX_CLAIMS;  // [MAX_CLAIMS] ring: slot read by every consumer
+    uint32_t* tmem_slot = (uint32_t*)(claim_free + MAX_CLAIMS);
     volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
     volatile int* claimed = abort_flag + 1;  // [MAX_CLAIMS] item (-1: none left)
     // phase 2's E digits, fetched one pass ahead: [epilogue warp][plane][lane] x EW / 8 uint4
@@ -472,7 +570,10 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
         mbar_init(smem_u32(tmem_full), 1);
         mbar_init(smem_u32(tmem_empty), EPI_WARPS);
         mbar_init(smem_u32(drain), 1);
-        for (int i = 0; i < MAX_CLAIMS; ++i) mbar_init(smem_u32(&claim_bar[i]), 1);
+        for (int i = 0; i < MAX_CLAIMS; ++i) {
+            mbar_init(smem_u32(&claim_bar[i]), 1);
+            mbar_init(smem_u32(&claim_free[i]), 1 + EPI_WARPS);  // the MMA thread and each epilogue warp
+        }
         *abort_flag = 0;
         fence_barrier_init();
     }
@@ -482,28 +583,48 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
     tc_fence_after();
 
     // Work items of this CTA, the same sequence in every role: whole waves
-    // round-robin (blockIdx.x + k gridDim.x), then, in a split launch, parts
-    // claimed by the producer (-1 ends the sequence).
+    // round-robin (blockIdx.x + k gridDim.x), then, in a launch with a claim
+    // counter, items claimed in ticket order by the producer (-1 ends the
+    // sequence) and handed to the MMA thread and the epilogue warps through a
+    // ring of MAX_CLAIMS slots.  A queue launch claims every item: an item is
+    // then only ever claimed after every item before it, so the items it
+    // waits for are held by CTAs that are running.
     const bool claiming = L.claim != nullptr;
     const int static_end = claiming ? L.split_begin : num_items;
     int n_claims = 0;  // producer: claims published; consumers: claims taken
+    bool ended = false;  // producer: a -1 has been published
+    auto publish = [&](int t) -> bool {
+        const int slot = n_claims % MAX_CLAIMS;
+        const int round = n_claims / MAX_CLAIMS;
+        if (round > 0 && !mbar_wait_for(smem_u32(&claim_free[slot]), (uint32_t)((round - 1) & 1), wait)) {
+            atomicOr(L.err, ERR_CLAIM_WAIT);
+            *abort_flag = 1;
+            return false;
+        }
+        claimed[slot] = t;
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&claim_bar[slot])) : "memory");
+        ++n_claims;
+        if (t < 0) ended = true;
+        return true;
+    };
     auto producer_claim = [&]() -> int {
-        if (n_claims >= MAX_CLAIMS) return -1;
+        if (*abort_flag) return -1;
         int t = L.split_begin + atomicAdd(L.claim, 1);
         if (t >= num_items) t = -1;
-        claimed[n_claims] = t;
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&claim_bar[n_claims])) : "memory");
-        ++n_claims;
-        return t;
+        return publish(t) ? t : -1;
     };
     auto consumer_take = [&]() -> int {  // one thread per role
-        if (n_claims >= MAX_CLAIMS || *abort_flag) return -1;
-        if (!mbar_wait_for(smem_u32(&claim_bar[n_claims]), 0, wait)) {
+        if (*abort_flag) return -1;
+        const int slot = n_claims % MAX_CLAIMS;
+        if (!mbar_wait_for(smem_u32(&claim_bar[slot]), (uint32_t)((n_claims / MAX_CLAIMS) & 1), wait)) {
             atomicOr(L.err, ERR_CLAIM_WAIT);
             *abort_flag = 1;
             return -1;
         }
-        return claimed[n_claims++];
+        const int t = claimed[slot];
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&claim_free[slot])) : "memory");
+        ++n_claims;
+        return t;
     };
     auto first_item = [&](bool producer) -> int {
         if ((int)blockIdx.x < static_end) return blockIdx.x;
@@ -524,15 +645,25 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             for (int t = first_item(true); t >= 0 && !*abort_flag; t = next_item(t, true)) {
                 int g, ti, tj, slot, part;
                 item_of(L, t, g, ti, tj, slot, part);
-                const DigitGemmParams& Pg = params_of(L, g);
+                const DigitGemmParams& Pg = params_of<Q>(L, g);
                 const int tix = tj * (tj + 1) / 2 + ti;
                 const int cnt = Pg.kc_cnt ? Pg.kc_cnt[tix] : -1;  // -1: every k-chunk
                 const unsigned long long* km = cnt >= 0 ? Pg.kc_mask + (size_t)tix * Pg.kc_words : nullptr;
                 int kb, nk;
                 dense_k_range(L, Pg.n_pad / KC, slot, part, kb, nk);
                 if (cnt >= 0) nk = cnt;
-                const CUtensorMap* mA = &L.maps[2 * g];
-                const CUtensorMap* mB = &L.maps[2 * g + 1];
+                const CUtensorMap* mA = Q ? &L.qmaps[2 * g] : &L.maps[2 * g];
+                const CUtensorMap* mB = Q ? &L.qmaps[2 * g + 1] : &L.maps[2 * g + 1];
+                const int s_it = Q ? Pg.s_in : S;  // this item's digit planes
+                if constexpr (Q) {
+                    acquire_map(mA);
+                    acquire_map(mB);
+                    if (L.qdep[g] >= 0 && !wait_product(L, L.qdep[g], wait)) {
+                        atomicOr(L.err, ERR_PRODUCER_WAIT);
+                        *abort_flag = 1;
+                        break;
+                    }
+                }
                 int w = 0;
                 unsigned long long bits = km ? km[0] : 0ull;
                 for (int c = 0; c < nk; ++c, ++it) {
@@ -557,20 +688,14 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     if (*abort_flag) break;
                     const uint32_t fb = smem_u32(&full_bar[st]);
                     uint8_t* sa = base + (size_t)st * stage_bytes;
-                    mbar_arrive_expect_tx(fb, (uint32_t)stage_bytes);
+                    mbar_arrive_expect_tx(fb, (uint32_t)(2 * s_it * PLANE_BYTES));
                     tma_load_3d(smem_u32(sa), mA, fb, kc * KC, ti * TILE, 0);
-                    tma_load_3d(smem_u32(sa + s * PLANE_BYTES), mB, fb, kc * KC, tj * TILE, 0);
+                    tma_load_3d(smem_u32(sa + S * PLANE_BYTES), mB, fb, kc * KC, tj * TILE, 0);
                 }
             }
-            // unclaimed slots end the other roles' sequences (also after an abort)
-            if (claiming) {
-                while (n_claims < MAX_CLAIMS) {
-                    claimed[n_claims] = -1;
-                    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&claim_bar[n_claims]))
-                                 : "memory");
-                    ++n_claims;
-                }
-            }
+            // a -1 ends the other roles' sequences (also after an abort; if
+            // its slot does not come free in time they give up on their own)
+            if (claiming && !ended) publish(-1);
             // wait (bounded) for the copies still in flight
             for (int k = (it > stages ? it - stages : 0); k < it; ++k)
                 mbar_wait_for(smem_u32(&full_bar[k % stages]), (uint32_t)((k / stages) & 1));
@@ -585,8 +710,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             for (int t = first_item(false); t >= 0 && ok; t = next_item(t, false), ++lt) {
                 int g, ti, tj, slot, part;
                 item_of(L, t, g, ti, tj, slot, part);
-                const DigitGemmParams& Pg = params_of(L, g);
+                const DigitGemmParams& Pg = params_of<Q>(L, g);
                 const int nl = Pg.kc_cnt ? Pg.kc_cnt[tj * (tj + 1) / 2 + ti] : -1;
+                const int s_it = Q ? Pg.s_in : S;
                 int kb, nk;
                 dense_k_range(L, Pg.n_pad / KC, slot, part, kb, nk);
                 if (nl >= 0) nk = nl;
@@ -607,22 +733,10 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     const uint64_t da = desc_base + (uint64_t)((st * stage_bytes) >> 4);
                     const uint64_t db = da + (uint64_t)((S * PLANE_BYTES) >> 4);
                     const uint32_t later = kc > 0 ? 1u : 0u;
-#pragma unroll
-                    for (int p = 0; p < S; ++p) {
-#pragma unroll
-                        for (int q = 0; q < S - p; ++q) {
-                            const int a = (p + q < NUM_ACC - 1) ? p + q : NUM_ACC - 1;
-#pragma unroll
-                            for (int kk = 0; kk < KC / 16; ++kk) {
-                                // the first write of accumulator a in a tile is pair
-                                // (0, a) at k = 0; all later ones accumulate
-                                const uint32_t acc_in = (kk > 0 || p > 0 || q > NUM_ACC - 1) ? 1u : later;
-                                mma_bf16(tmem + (uint32_t)(a * TILE),
-                                         da + (uint64_t)((p * PLANE_BYTES + kk * 32) >> 4),
-                                         db + (uint64_t)((q * PLANE_BYTES + kk * 32) >> 4), IDESC, acc_in);
-                            }
-                        }
-                    }
+                    if (!Q || s_it == S)
+                        issue_chunk<KC, S>(tmem, da, db, later);
+                    else if constexpr (Q)
+                        issue_chunk_runtime<KC, S - 1>(s_it, tmem, da, db, later);
                     mma_commit(smem_u32(&empty_bar[st]));
                 }
                 if (!ok) break;
@@ -655,7 +769,8 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
         for (int t = warp_item(0, true); t >= 0; t = warp_item(t, false), ++lt) {
             int g, ti, tj, slot, part;
             item_of(L, t, g, ti, tj, slot, part);
-            const DigitGemmParams& P = params_of(L, g);
+            const DigitGemmParams& P = params_of<Q>(L, g);
+            const int s = Q ? P.s_in : S;  // this item's digit planes
             const size_t plane = (size_t)P.n_pad * P.n_pad;
             bool ready = mbar_wait_for(smem_u32(tmem_full), (uint32_t)(lt & 1), wait);
             if (!ready) {
@@ -987,6 +1102,15 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     atomicAdd(&P.red[2], (double)s_fro);
                 }
             }
+            if constexpr (Q) {
+                // this warp's share of the item is stored: count it, so that
+                // the instance's next product may load the planes (tensor
+                // copies read through the async proxy)
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) atomicAdd(&L.qcnt[g], 1);
+            }
         }
     }
     tc_fence_before();
@@ -1006,6 +1130,9 @@ KernelFn kernel_k32_lo(int s);
 KernelFn kernel_k32_hi(int s);
 KernelFn kernel_k64_lo(int s);
 KernelFn kernel_k64_hi(int s);
+// queue launches: k-chunk 32 for 4..6 digits, 64 for 1..3 (digits_queue_<hi|lo>.cu)
+KernelFn kernel_queue_hi(int s);
+KernelFn kernel_queue_lo(int s);
 
 }  // namespace dk
 }  // namespace purify

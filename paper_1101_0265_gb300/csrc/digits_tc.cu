@@ -254,12 +254,17 @@ int prepare_kernel(KernelFn fn) {
     return PURIFY_OK;
 }
 
+// The queue-launch instantiation for a largest digit count s (k-chunk
+// queue_kc(s)).
+static KernelFn queue_kernel(int s) { return s <= 3 ? kernel_queue_lo(s) : kernel_queue_hi(s); }
+
 int prepare_digit_kernels() {
     for (int kc : {16, 32, 64})
         for (int s = 1; s <= kMaxDigitPlanes; ++s) {
             KernelFn fn = kernel_for(kc, s);
             if (fn) PURIFY_TRY(prepare_kernel(fn));
         }
+    for (int s = 1; s <= kMaxDigitPlanes; ++s) PURIFY_TRY(prepare_kernel(queue_kernel(s)));
     return PURIFY_OK;
 }
 
@@ -304,7 +309,7 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
 }
 
 static int launch_kernel(const DigitLaunch& L, int s, int kc, int grid, cudaStream_t stream) {
-    KernelFn fn = kernel_for(kc, s);
+    KernelFn fn = L.qprm ? queue_kernel(s) : kernel_for(kc, s);
     if (!fn || grid < 1 || L.stages < 1) return PURIFY_ERR_INVALID_ARG;
     PURIFY_TRY(prepare_kernel(fn));
     fn<<<grid, NTHREADS, digit_smem_bytes(s, kc), stream>>>(L);
@@ -403,6 +408,45 @@ int launch_digit_group(int s, const DigitStep* steps, int count, const int4* wor
     L.split_ways = 1;
     const int grid = num_items < max_ctas ? num_items : max_ctas;
     return launch_kernel(L, s, kc, grid, stream);
+}
+
+int queue_kc(int smax) { return smax <= 3 ? 64 : 32; }  // the instantiations of digits_queue_<lo|hi>.cu
+
+int fill_queue_product(const DigitStep& st0, int smax, DigitGemmParams* p, CUtensorMap* maps) {
+    if (st0.s_in > smax || st0.kc_cnt || st0.bnorm2) return PURIFY_ERR_INVALID_ARG;
+    DigitStep st = st0;
+    st.kc = queue_kc(smax);  // one k-chunk width for the whole launch
+    CUtensorMap m[2];        // encoded at their own alignment, then copied to the staging area
+    PURIFY_TRY(fill_digit_params(st, p, &m[0], &m[1]));
+    std::memcpy(maps, m, sizeof(m));
+    return PURIFY_OK;
+}
+
+int launch_digit_queue(int smax, const DigitGemmParams* prm, const CUtensorMap* maps, const int* dep, const int* need,
+                       int* cnt, int num_products, const int4* work, int num_items, float2* scratch, int max_ctas,
+                       int* err, cudaStream_t stream, long long wait_cycles) {
+    if (smax < 1 || smax > kMaxDigitPlanes || !prm || !maps || !dep || !need || !cnt || num_products < 1 || !work ||
+        !scratch || !err)
+        return PURIFY_ERR_INVALID_ARG;
+    if (num_items <= 0) return PURIFY_OK;
+    DigitLaunch L;
+    std::memset(&L, 0, sizeof(L));
+    L.qprm = prm;
+    L.qmaps = maps;
+    L.qdep = dep;
+    L.qneed = need;
+    L.qcnt = cnt;
+    L.work = work;
+    L.num_items = num_items;
+    L.stages = digit_stages(smax, queue_kc(smax));
+    L.scratch = scratch;
+    L.err = err;
+    L.wait_cycles = wait_cycles;
+    L.claim = cnt + num_products;  // every item claimed in ticket order
+    L.split_begin = 0;             // (item_of reads the work list: no split parts)
+    L.split_ways = 1;
+    const int grid = num_items < max_ctas ? num_items : max_ctas;
+    return launch_kernel(L, smax, queue_kc(smax), grid, stream);
 }
 
 int launch_split(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s,

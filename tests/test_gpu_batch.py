@@ -1,5 +1,6 @@
-"""GPU tests of the batch engine: many purifications of uneven size in
-grouped tensor-core launches (CUDA graph), and continuous batching.  Every
+"""GPU tests of the batch engine: many purifications of uneven size in one
+queue launch or in grouped tensor-core launches per round (with and without
+a CUDA graph), and continuous batching.  Every
 result must equal the same purification run alone, bit for bit, and the
 CPU oracle to the mixed path's tolerance."""
 import numpy as np
@@ -46,15 +47,17 @@ def _alone(P, h, scheme, tol):
     return D, st
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_equals_alone_and_oracle(P, use_graph):
+@pytest.mark.parametrize("use_graph,rounds", [(True, False), (False, False), (True, True), (False, True)])
+def test_batch_equals_alone_and_oracle(P, use_graph, rounds):
+    # rounds=False: one queue launch, each instance advancing on its own;
+    # rounds=True: one grouped launch per round
     hs = _hams()
     tol = 1e-10
     B = P.Batch()
     ids = [B.add(h.F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme=sp[3], tol=tol, mu=0.0)
            for h, sp in zip(hs, SPECS)]
     for rep in range(2):  # the second run replays the captured graph
-        B.run(use_graph=use_graph)
+        B.run(use_graph=use_graph, rounds=rounds)
         for i, h, sp in zip(ids, hs, SPECS):
             assert B.done(i)
             D = B.density(i)
@@ -116,4 +119,35 @@ def test_batch_device_inputs_and_footprint(P):
     assert np.array_equal(Dd.cpu().numpy(), Da)
     with pytest.raises(P.PurifyError):
         B.add(h.F, h.nocc, h.lmin, h.lmax, h.lumo, h.homo)       # homo > lumo
+    B.close()
+
+
+def test_queue_many_products_per_cta(P):
+    # more instances and products than CTAs can hold claims for at once: the
+    # claim ring wraps many times; mixed digit counts in one launch (the
+    # small-gap instances need more digit planes than the wide-gap ones)
+    specs = [(96 + 32 * (k % 7), 40 + k, 10 ** (-1 - (k % 3)), "TC_SF" if k % 2 else "FIXED_MU_SF")
+             for k in range(24)]
+    hs = [I.dense_hamiltonian(n, nocc, gap, config=64, instance=k) for k, (n, nocc, gap, _) in enumerate(specs)]
+    B = P.Batch()
+    ids = [B.add(h.F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme=sp[3], tol=1e-10, mu=0.0)
+           for h, sp in zip(hs, specs)]
+    B.run(use_graph=True)
+    digits = set()
+    alone = {}
+    for k, (i, h, sp) in enumerate(zip(ids, hs, specs)):
+        D = B.density(i)
+        alone[k] = _alone(P, h, sp[3], 1e-10)[0]
+        assert np.array_equal(D, alone[k]), sp
+        digits.add(B.stats(i)["digit_max"])
+    assert len(digits) > 1, digits
+    # a changed set of instances is staged again into the same device buffer
+    # (the tensor maps change under the same addresses): still exact
+    for i in ids[::2]:
+        B.release(i)
+    keep = {k: i for k, i in enumerate(ids) if k % 2}
+    for use_graph in (False, True):
+        B.run(use_graph=use_graph)
+        for k, i in keep.items():
+            assert np.array_equal(B.density(i), alone[k]), (use_graph, specs[k])
     B.close()

@@ -52,19 +52,23 @@ def test_short_device_waits_time_out_then_recover(P, scheme):
     assert err <= 5e-8, err
 
 
-def test_timeout_in_a_batch_round(P):
-    # the grouped launches of the batch engine honour the same bound
+@pytest.mark.parametrize("rounds", [False, True])
+def test_timeout_in_a_batch(P, rounds):
+    # the batch engine's launches (one queue launch, whose items also wait on
+    # the device for their instance's previous product, or one grouped launch
+    # per round) honour the same bound
     hs = [I.dense_hamiltonian(n, n // 2, 0.1, config=83, instance=n) for n in (130, 260)]
     B = P.Batch(wait_kcycles=1)
     ids = [B.add(h.F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme="TC_SF", tol=1e-10, mu=0.0) for h in hs]
     with pytest.raises(P.PurifyError) as e:
-        B.run(use_graph=False)
+        B.run(use_graph=False, rounds=rounds)
     assert e.value.code == P.ERR_DEVICE_TIMEOUT
     B.close()
+    torch.cuda.synchronize()            # the context is intact
     # a fresh batch with the default bound is correct
     B = P.Batch()
     ids = [B.add(h.F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme="TC_SF", tol=1e-10, mu=0.0) for h in hs]
-    B.run(use_graph=False)
+    B.run(use_graph=False, rounds=rounds)
     for i, h in zip(ids, hs):
         ref, _ = O.purify(h.F, "TC_SF", h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=1e-10)
         assert np.max(np.abs(B.density(i) - ref)) <= 5e-8
