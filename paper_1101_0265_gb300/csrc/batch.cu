@@ -576,7 +576,7 @@ int purify_batch_add(purify_batch_t B, const double* F, int64_t n, int64_t ld, i
             smax = std::max(smax, digits_for_gap(bb0 - b0, B->opt, in->rbits));
         }
     }
-    const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)smax * in->n_pad * in->n_pad;
+    const size_t plane_bytes = plane_buffer_bytes(smax, in->n_pad);
     const size_t nb = sizeof(double) * (size_t)n * n;
     bool ok = cudaMalloc(&in->F, nb) == cudaSuccess && cudaMalloc(&in->D, nb) == cudaSuccess &&
               cudaMalloc(&in->red, 4 * sizeof(double)) == cudaSuccess &&

@@ -28,9 +28,9 @@
 //
 // Structure of one CTA (one 128 x 128 output tile at a time, 64 + 32 EPI_WARPS
 // threads):
-//   warp 0  TMA producer: per k-chunk (16, 32 or 64 wide, with a swizzle of
-//           the chunk's row width) one 3D TMA load of all s planes of the A
-//           row panel and one of the B row panel
+//   warp 0  TMA producer: per 32-wide k-chunk one 3D TMA load of the A row
+//           panel's plane pairs (128-byte box rows: two planes' chunks side
+//           by side, 128-byte swizzle) and one of the B row panel's
 //   warp 1  TMEM allocator and MMA issuer (tcgen05.mma kind::f16, bf16 in,
 //           fp32 accumulate, M = N = 128, K = 16)
 //   warps 2.. epilogue (tcgen05.ld; warp w reads TMEM lane quarter w % 4 and
@@ -182,19 +182,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Shared-memory matrix descriptor for a K-major operand tile written by TMA
-// with a swizzle as wide as its rows (KC bf16 = 2 KC bytes: 32, 64 or 128):
-// 8-row groups 16 KC bytes apart; one K = 16 step advances 32 bytes.
-template <int KC>
+// Shared-memory matrix descriptor for a K-major operand tile of 128-byte
+// rows written by TMA with the 128-byte swizzle (a plane pair: two planes'
+// 32-wide k-chunks side by side): 8-row groups 1024 bytes apart; one K = 16
+// step advances 32 bytes, the pair's second plane starts 64 bytes in.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-    constexpr uint64_t layout = KC == 16 ? 6 : (KC == 32 ? 4 : 2);  // 32B / 64B / 128B swizzle
+    constexpr uint64_t layout = 2;                   // 128-byte swizzle
     uint64_t d = 0;
     d |= (uint64_t)((addr & 0x3FFFF) >> 4);          // start address
     d |= (uint64_t)1 << 16;                          // leading byte offset (unused here)
-    d |= (uint64_t)((16 * KC) >> 4) << 32;           // stride byte offset
+    d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
     d |= (uint64_t)1 << 46;                          // descriptor version (tcgen05)
     d |= layout << 61;
     return d;
+}
+
+constexpr int PAIR_BYTES = TILE * 128;  // one plane pair of a 128-row panel, one 32-wide k-chunk
+
+// Descriptor offset (16-byte units) of plane p's 16-wide k-step kk inside an
+// operand's stage region.
+__host__ __device__ constexpr int plane_desc_off(int p, int kk) {
+    return ((p >> 1) * PAIR_BYTES + (p & 1) * 64 + kk * 32) >> 4;
 }
 
 // Instruction descriptor: kind::f16, bf16 A and B (K-major), fp32 D,
@@ -281,8 +289,8 @@ struct DigitGemmParams {
     df cP, cE, cI, dY, dI;   // Y = cP P + cE E + cI I;  out = dY Y + dI I
     int use_E;               // E = A (the matrix in the A operand)
     int affine_out;          // (dY, dI) != (1, 0)
-    const __nv_bfloat16* A;  // A's planes (for E), [s_in][n_pad][n_pad]
-    __nv_bfloat16* out;      // output planes [s_out][n_pad][n_pad] (may be null)
+    const __nv_bfloat16* A;  // A's s_in planes (for E), paired layout (plane_index)
+    __nv_bfloat16* out;      // output's s_out planes, paired layout (may be null)
     double* out64;           // float64 output n x n (leading dimension n) or null
     double* red;             // [0] trace(Y), [1] ||E - P||_F^2, [2] ||Y||_F^2 (atomics) or null
     // block sparsity (null: dense): per upper tile t = tj (tj + 1) / 2 + ti,
@@ -431,49 +439,39 @@ __device__ __forceinline__ void acquire_map(const CUtensorMap* m) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m) : "memory");
 }
 
-template <int KC, int SS>
+template <int SS>
 __device__ __forceinline__ void issue_chunk(uint32_t tmem, uint64_t da, uint64_t db, uint32_t later);
 
 // issue_chunk for a digit count known at run time (<= SS)
-template <int KC, int SS>
+template <int SS>
 __device__ __forceinline__ void issue_chunk_runtime(int s, uint32_t tmem, uint64_t da, uint64_t db, uint32_t later) {
     if constexpr (SS >= 1) {
         if (s == SS) {
-            issue_chunk<KC, SS>(tmem, da, db, later);
+            issue_chunk<SS>(tmem, da, db, later);
             return;
         }
-        issue_chunk_runtime<KC, SS - 1>(s, tmem, da, db, later);
+        issue_chunk_runtime<SS - 1>(s, tmem, da, db, later);
     }
 }
 
-// The unrolled MMA issue of one k-chunk for SS digit planes (pairs p + q <
-// SS; levels 0..2 in their own accumulators, >= 3 in the fourth).  A and B
-// planes are TILE x KC bf16 each, B after the kernel's S planes of A.  The
-// chunk is issued in 32-wide k-blocks, inside a block pair by pair with the
-// pair's two 16-wide k-steps back to back (runs of MMAs into one accumulator
-// keep the tensor pipe busier than alternating accumulators): every
-// accumulator then receives its additions in the same order for 32- and
-// 64-wide chunks, so results do not depend on that choice of launch shape.
-template <int KC, int SS>
+// The unrolled MMA issue of one 32-wide k-chunk for SS digit planes (pairs
+// p + q < SS; levels 0..2 in their own accumulators, >= 3 in the fourth),
+// pair by pair with a pair's two 16-wide k-steps back to back (runs of MMAs
+// into one accumulator).  A's plane pairs at da, B's at db.
+template <int SS>
 __device__ __forceinline__ void issue_chunk(uint32_t tmem, uint64_t da, uint64_t db, uint32_t later) {
-    constexpr int PLANE_BYTES = TILE * KC * 2;
-    constexpr int KB = KC < 32 ? KC : 32;
 #pragma unroll
-    for (int kb = 0; kb < KC / KB; ++kb) {
+    for (int p = 0; p < SS; ++p) {
 #pragma unroll
-        for (int p = 0; p < SS; ++p) {
+        for (int q = 0; q < SS - p; ++q) {
+            const int a = (p + q < NUM_ACC - 1) ? p + q : NUM_ACC - 1;
 #pragma unroll
-            for (int q = 0; q < SS - p; ++q) {
-                const int a = (p + q < NUM_ACC - 1) ? p + q : NUM_ACC - 1;
-#pragma unroll
-                for (int k2 = 0; k2 < KB / 16; ++k2) {
-                    const int kk = kb * (KB / 16) + k2;
-                    // the first write of accumulator a in a tile is pair (0, a) at
-                    // k = 0; all later ones accumulate
-                    const uint32_t acc_in = (kk > 0 || p > 0 || q > NUM_ACC - 1) ? 1u : later;
-                    mma_bf16(tmem + (uint32_t)(a * TILE), da + (uint64_t)((p * PLANE_BYTES + kk * 32) >> 4),
-                             db + (uint64_t)((q * PLANE_BYTES + kk * 32) >> 4), IDESC, acc_in);
-                }
+            for (int kk = 0; kk < 2; ++kk) {
+                // the first write of accumulator a in a tile is pair (0, a) at
+                // k = 0; all later ones accumulate
+                const uint32_t acc_in = (kk > 0 || p > 0 || q > NUM_ACC - 1) ? 1u : later;
+                mma_bf16(tmem + (uint32_t)(a * TILE), da + (uint64_t)plane_desc_off(p, kk),
+                         db + (uint64_t)plane_desc_off(q, kk), IDESC, acc_in);
             }
         }
     }
@@ -532,11 +530,12 @@ __device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, lon
 // count S throughout.
 template <int KC, int S, bool Q>
 __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ DigitLaunch L) {
-    constexpr int PLANE_BYTES = TILE * KC * 2;  // one plane of one operand per stage
+    static_assert(KC == 32, "digit planes are stored for 32-wide k-chunks");
+    constexpr int NP = plane_pairs(S);           // plane pairs of one operand per stage
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte aligned operand area: stages x (A planes | B planes)
     uint8_t* base = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int stage_bytes = 2 * S * PLANE_BYTES;
+    constexpr int stage_bytes = 2 * NP * PAIR_BYTES;
     const int stages = L.stages;
     uint64_t* bars = (uint64_t*)(base + (size_t)stages * stage_bytes);
     // bars: full[stages] | empty[stages] | tmem_full | tmem_empty | drain | claim[MAX_CLAIMS] |
@@ -688,9 +687,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     if (*abort_flag) break;
                     const uint32_t fb = smem_u32(&full_bar[st]);
                     uint8_t* sa = base + (size_t)st * stage_bytes;
-                    mbar_arrive_expect_tx(fb, (uint32_t)(2 * s_it * PLANE_BYTES));
-                    tma_load_3d(smem_u32(sa), mA, fb, kc * KC, ti * TILE, 0);
-                    tma_load_3d(smem_u32(sa + S * PLANE_BYTES), mB, fb, kc * KC, tj * TILE, 0);
+                    mbar_arrive_expect_tx(fb, (uint32_t)(2 * plane_pairs(s_it) * PAIR_BYTES));
+                    tma_load_3d(smem_u32(sa), mA, fb, kc * 64, ti * TILE, 0);
+                    tma_load_3d(smem_u32(sa + NP * PAIR_BYTES), mB, fb, kc * 64, tj * TILE, 0);
                 }
             }
             // a -1 ends the other roles' sequences (also after an abort; if
@@ -704,7 +703,7 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
         if (lane == 0) {
             // MMA issuer.  Descriptors are one base plus compile-time offsets
             // (the start address sits in the low 14 bits and never carries).
-            const uint64_t desc_base = smem_desc<KC>(smem_u32(base));
+            const uint64_t desc_base = smem_desc(smem_u32(base));
             int it = 0, lt = 0;
             bool ok = true;
             for (int t = first_item(false); t >= 0 && ok; t = next_item(t, false), ++lt) {
@@ -731,12 +730,12 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     }
                     tc_fence_after();
                     const uint64_t da = desc_base + (uint64_t)((st * stage_bytes) >> 4);
-                    const uint64_t db = da + (uint64_t)((S * PLANE_BYTES) >> 4);
+                    const uint64_t db = da + (uint64_t)((NP * PAIR_BYTES) >> 4);
                     const uint32_t later = kc > 0 ? 1u : 0u;
                     if (!Q || s_it == S)
-                        issue_chunk<KC, S>(tmem, da, db, later);
+                        issue_chunk<S>(tmem, da, db, later);
                     else if constexpr (Q)
-                        issue_chunk_runtime<KC, S - 1>(s_it, tmem, da, db, later);
+                        issue_chunk_runtime<S - 1>(s_it, tmem, da, db, later);
                     mma_commit(smem_u32(&empty_bar[st]));
                 }
                 if (!ok) break;
@@ -935,13 +934,17 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             // E for a pass is copied to shared memory while the previous pass
             // computes (each lane copies and reads only its own 16-byte pieces)
             uint4* const e_mine = e_stage + (size_t)region * s * 32 * (EW / 8) + lane * (EW / 8);
-            const __nv_bfloat16* const e_row = Ain + (size_t)i * n_pad + tj * TILE;
+            // row i of A's planes (paired layout, see plane_index)
+            const __nv_bfloat16* const e_row = Ain + (size_t)i * 2 * n_pad;
             auto fetch_E = [&](int c_first) {
 #pragma unroll
                 for (int p = 0; p < s; ++p)
 #pragma unroll
-                    for (int q = 0; q < EW / 8; ++q)
-                        cp_async16(smem_u32(e_mine + p * 32 * (EW / 8) + q), e_row + p * plane + c_first + 8 * q);
+                    for (int q = 0; q < EW / 8; ++q) {
+                        const int j = tj * TILE + c_first + 8 * q;
+                        cp_async16(smem_u32(e_mine + p * 32 * (EW / 8) + q),
+                                   e_row + (size_t)(p >> 1) * 2 * plane + ((j >> 5) << 6) + ((p & 1) << 5) + (j & 31));
+                    }
                 cp_async_commit();
             };
             if (use_E) fetch_E(col0);
@@ -1057,26 +1060,30 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                             dv[c] = digit_to_bf16(d * plane_scale);
                         }
                         plane_scale *= rinv;
-                        __nv_bfloat16* dst = outp + p * plane;
+                        // plane p in the paired layout (see plane_index): row r,
+                        // column j at dst + r 2 n_pad + (j / 32) 64 + j % 32
+                        __nv_bfloat16* dst = outp + (size_t)(p >> 1) * 2 * plane + ((p & 1) << 5);
                         // the row segment (i, jb ..) and its mirror column; in a
                         // diagonal tile only j >= i is written here (j < i is
                         // the mirror of another row's element)
+                        __nv_bfloat16* const seg = dst + (size_t)i * 2 * n_pad + ((jb >> 5) << 6) + (jb & 31);
                         if (!diag_tile || jb >= i) {
-                            uint4* row = (uint4*)(dst + (size_t)i * n_pad + jb);
+                            uint4* row = (uint4*)seg;
 #pragma unroll
                             for (int q = 0; q < EW / 8; ++q) row[q] = ((const uint4*)dv)[q];
                         } else if (jb + EW > i) {
 #pragma unroll
                             for (int c = 0; c < EW; ++c)
-                                if (jb + c >= i) dst[(size_t)i * n_pad + jb + c] = dv[c];
+                                if (jb + c >= i) seg[c] = dv[c];
                         }
+                        __nv_bfloat16* const col = dst + ((i >> 5) << 6) + (i & 31);
                         if (!diag_tile) {
 #pragma unroll
-                            for (int c = 0; c < EW; ++c) dst[(size_t)(jb + c) * n_pad + i] = dv[c];
+                            for (int c = 0; c < EW; ++c) col[(size_t)(jb + c) * 2 * n_pad] = dv[c];
                         } else if (jb + EW > i + 1) {
 #pragma unroll
                             for (int c = 0; c < EW; ++c)
-                                if (jb + c > i) dst[(size_t)(jb + c) * n_pad + i] = dv[c];
+                                if (jb + c > i) col[(size_t)(jb + c) * 2 * n_pad] = dv[c];
                         }
                     }
                 }
@@ -1124,13 +1131,10 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
 
 typedef void (*KernelFn)(const DigitLaunch);
 
-// Kernel pointers of the instantiations in digits_k<KC><lo|hi>.cu.
-KernelFn kernel_k16_hi(int s);
+// Kernel pointers of the instantiations in digits_k32_<lo|hi>.cu (1..3 and
+// 4..6 digits) and, for queue launches, digits_queue_<lo|hi>.cu.
 KernelFn kernel_k32_lo(int s);
 KernelFn kernel_k32_hi(int s);
-KernelFn kernel_k64_lo(int s);
-KernelFn kernel_k64_hi(int s);
-// queue launches: k-chunk 32 for 4..6 digits, 64 for 1..3 (digits_queue_<hi|lo>.cu)
 KernelFn kernel_queue_hi(int s);
 KernelFn kernel_queue_lo(int s);
 

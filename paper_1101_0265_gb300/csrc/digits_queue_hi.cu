@@ -1,5 +1,5 @@
 // Instantiations of the product kernel for queue launches (a whole batch in
-// one launch): k-chunk 32, largest digit count 4..6.
+// one launch): largest digit count 4..6.
 #include "digits_kernel.cuh"
 
 namespace purify {

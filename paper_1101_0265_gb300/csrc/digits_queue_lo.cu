@@ -1,5 +1,5 @@
 // Instantiations of the product kernel for queue launches (a whole batch in
-// one launch): k-chunk 64, largest digit count 1..3.
+// one launch): largest digit count 1..3.
 #include "digits_kernel.cuh"
 
 namespace purify {
@@ -7,9 +7,9 @@ namespace dk {
 
 KernelFn kernel_queue_lo(int s) {
     switch (s) {
-        case 1: return digit_gemm_kernel<64, 1, true>;
-        case 2: return digit_gemm_kernel<64, 2, true>;
-        case 3: return digit_gemm_kernel<64, 3, true>;
+        case 1: return digit_gemm_kernel<32, 1, true>;
+        case 2: return digit_gemm_kernel<32, 2, true>;
+        case 3: return digit_gemm_kernel<32, 3, true>;
         default: return nullptr;
     }
 }

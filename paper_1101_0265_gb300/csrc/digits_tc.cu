@@ -112,7 +112,8 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ F
                 bsum += z[c].h * z[c].h;
                 z[c] = df_scale(z[c], digit_scale);
             }
-            __nv_bfloat16* dst = out + (size_t)i * n_pad + j0;
+            // plane p at out + plane_index(p, i, j0, n_pad): pairs 2 total apart
+            __nv_bfloat16* dst = out + (size_t)i * 2 * n_pad + ((j0 >> 5) << 6) + (j0 & 31);
             float plane_scale = 1.f;
             for (int p = 0; p < s; ++p) {
                 __align__(8) __nv_bfloat16 dv[4];
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ F
                     dv[c] = digit_to_bf16(d * plane_scale);
                     z[c] = df_scale(z[c], rscale);
                 }
-                *(uint2*)(dst + (size_t)p * total) = *(const uint2*)dv;
+                *(uint2*)(dst + (size_t)(p >> 1) * 2 * total + ((p & 1) << 5)) = *(const uint2*)dv;
                 plane_scale *= rinv;
             }
         }
@@ -162,20 +163,20 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 3D map over planes [s][n_pad][n_pad] bf16, box {kc, 128, s}, with a
-// swizzle of 2 kc bytes.
+// 3D map over the plane pairs of an s-plane buffer (plane_index): dims
+// {2 n_pad, n_pad, pairs}, box {64, 128, pairs}: one box row is 128 bytes, a
+// 32-wide k-chunk of two planes; 128-byte swizzle.
 int make_plane_map(CUtensorMap* map, const __nv_bfloat16* planes, int n_pad, int s, int kc) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return PURIFY_ERR_UNSUPPORTED;
-    if (((uintptr_t)planes & 15) || n_pad % TILE) return PURIFY_ERR_INVALID_ARG;
-    cuuint64_t dims[3] = {(cuuint64_t)n_pad, (cuuint64_t)n_pad, (cuuint64_t)s};
-    cuuint64_t strides[2] = {(cuuint64_t)n_pad * 2, (cuuint64_t)n_pad * n_pad * 2};
-    cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)TILE, (cuuint32_t)s};
-    const CUtensorMapSwizzle sw = kc == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
-                                 : (kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B);
+    if (((uintptr_t)planes & 15) || n_pad % TILE || kc != 32) return PURIFY_ERR_INVALID_ARG;
+    const int np = plane_pairs(s);
+    cuuint64_t dims[3] = {(cuuint64_t)2 * n_pad, (cuuint64_t)n_pad, (cuuint64_t)np};
+    cuuint64_t strides[2] = {(cuuint64_t)n_pad * 4, (cuuint64_t)n_pad * n_pad * 4};
+    cuuint32_t box[3] = {64, (cuuint32_t)TILE, (cuuint32_t)np};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)planes, dims, strides, box, estr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? PURIFY_OK : PURIFY_ERR_CUDA;
 }
@@ -189,39 +190,22 @@ df to_df(double x) {
 
 KernelFn kernel_for(int kc, int s);
 
-// k-chunk width for a digit count: the widest chunk that still leaves at
-// least two pipeline stages, unless overridden (tuning).
-int digit_kc_for(int s, bool sparse) { return sparse ? 32 : digit_kc(s); }
+// k-chunk width: 32 (the paired plane layout stores 32-wide chunks).
+int digit_kc_for(int, bool) { return 32; }
 
-int digit_step_kc(const DigitStep& st) {
-    const bool sparse = st.kc_cnt || st.bnorm2;
-    if (!sparse && (st.kc == 16 || st.kc == 32 || st.kc == 64) && kernel_for(st.kc, st.s_in)) return st.kc;
-    return digit_kc_for(st.s_in, sparse);
-}
+int digit_step_kc(const DigitStep&) { return 32; }
 
 int digit_kc_candidates(int s, int* kc) {
-    int n = 0;
-    for (int c : {16, 32, 64}) {
-        // a width whose stage ring holds a single k-chunk cannot overlap its
-        // loads with the MMAs: not a candidate
-        if (kernel_for(c, s) && digit_stages(s, c) >= 2) kc[n++] = c;
-    }
-    return n;
+    if (!kernel_for(32, s)) return 0;
+    kc[0] = 32;
+    return 1;
 }
 
-int digit_kc(int s) {
-    static const int forced = [] {  // read once (thread-safe initialisation)
-        const char* e = getenv("PURIFY_DIGIT_KC");
-        const int v = e ? atoi(e) : 0;
-        return (v == 16 || v == 32 || v == 64) ? v : 0;
-    }();
-    if (forced == 16 && s < 4) return 32;
-    if (forced) return forced;
-    return s <= 3 ? 64 : 32;
-}
+int digit_kc(int) { return 32; }
 
 int digit_stages(int s, int kc) {
-    const int stage_bytes = 2 * s * TILE * kc * 2;
+    if (kc != 32) return 0;
+    const int stage_bytes = 2 * plane_pairs(s) * PAIR_BYTES;
     int st = (200 * 1024) / stage_bytes;
     if (st > MAX_STAGES) st = MAX_STAGES;
     return st;
@@ -230,16 +214,13 @@ int digit_stages(int s, int kc) {
 size_t digit_smem_bytes(int s, int kc) {
     // alignment slack, operand stages, barriers and flags, then phase 2's E
     // staging (one EW-column piece per epilogue warp, digit plane and lane)
-    return 1024 + (size_t)digit_stages(s, kc) * 2 * s * TILE * kc * 2 + BAR_AREA +
+    return 1024 + (size_t)digit_stages(s, kc) * 2 * plane_pairs(s) * PAIR_BYTES + BAR_AREA +
            (size_t)kEpiWarps * s * 32 * EW * 2;
 }
 
 KernelFn kernel_for(int kc, int s) {
-    if (s < 1 || s > 6) return nullptr;
-    if (kc == 16) return s >= 4 ? kernel_k16_hi(s) : nullptr;
-    if (kc == 32) return s <= 3 ? kernel_k32_lo(s) : kernel_k32_hi(s);
-    if (kc == 64) return s <= 3 ? kernel_k64_lo(s) : kernel_k64_hi(s);
-    return nullptr;
+    if (s < 1 || s > 6 || kc != 32) return nullptr;
+    return s <= 3 ? kernel_k32_lo(s) : kernel_k32_hi(s);
 }
 
 // Opt every instantiation into the full 227 KB of shared memory (once).
@@ -254,16 +235,14 @@ int prepare_kernel(KernelFn fn) {
     return PURIFY_OK;
 }
 
-// The queue-launch instantiation for a largest digit count s (k-chunk
-// queue_kc(s)).
+// The queue-launch instantiation for a largest digit count s.
 static KernelFn queue_kernel(int s) { return s <= 3 ? kernel_queue_lo(s) : kernel_queue_hi(s); }
 
 int prepare_digit_kernels() {
-    for (int kc : {16, 32, 64})
-        for (int s = 1; s <= kMaxDigitPlanes; ++s) {
-            KernelFn fn = kernel_for(kc, s);
-            if (fn) PURIFY_TRY(prepare_kernel(fn));
-        }
+    for (int s = 1; s <= kMaxDigitPlanes; ++s) {
+        KernelFn fn = kernel_for(32, s);
+        if (fn) PURIFY_TRY(prepare_kernel(fn));
+    }
     for (int s = 1; s <= kMaxDigitPlanes; ++s) PURIFY_TRY(prepare_kernel(queue_kernel(s)));
     return PURIFY_OK;
 }
@@ -410,7 +389,7 @@ int launch_digit_group(int s, const DigitStep* steps, int count, const int4* wor
     return launch_kernel(L, s, kc, grid, stream);
 }
 
-int queue_kc(int smax) { return smax <= 3 ? 64 : 32; }  // the instantiations of digits_queue_<lo|hi>.cu
+int queue_kc(int) { return 32; }
 
 int fill_queue_product(const DigitStep& st0, int smax, DigitGemmParams* p, CUtensorMap* maps) {
     if (st0.s_in > smax || st0.kc_cnt || st0.bnorm2) return PURIFY_ERR_INVALID_ARG;

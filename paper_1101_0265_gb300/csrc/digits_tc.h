@@ -24,6 +24,20 @@ struct DevStep {
     int done;           // 1: the run has stopped
 };
 
+// Digit planes in HBM are stored in pairs (2m, 2m + 1).  A pair is an
+// n_pad x 2 n_pad bf16 matrix whose 128-byte row pieces hold the two planes'
+// 32-wide k-chunks side by side, so that one tensor-map box row (128 bytes)
+// carries two planes: element (p, i, j) sits at
+//   (p / 2) 2 n_pad^2 + i 2 n_pad + (j / 32) 64 + (p % 2) 32 + j % 32.
+// A buffer for s planes holds plane_pairs(s) pairs (an odd count leaves the
+// last pair's second half unused and unread).
+__host__ __device__ constexpr int plane_pairs(int s) { return (s + 1) >> 1; }
+__host__ __device__ inline size_t plane_index(int p, int i, int j, int n_pad) {
+    return (size_t)(p >> 1) * 2 * n_pad * n_pad + (size_t)i * 2 * n_pad + ((j >> 5) << 6) + ((p & 1) << 5) + (j & 31);
+}
+// Bytes of a buffer of s digit planes at size n_pad.
+inline size_t plane_buffer_bytes(int s, int n_pad) { return (size_t)plane_pairs(s) * 2 * n_pad * n_pad * 2; }
+
 // One fused step: P = A B (A, B symmetric, held as s_in digit planes each,
 // scale exponents eA, eB), Y = cP P + cE E + cI I with E = A when use_E,
 // out = dY Y + dI I written as s_out digit planes with exponent e_out and

@@ -63,7 +63,7 @@ int ensure_mixed(purify_ctx* h, int n_pad) {
     cudaFree(ms->Sd);
     ms->Xd[0] = ms->Xd[1] = ms->Sd = nullptr;
     ms->n_pad_cap = 0;
-    const size_t bytes = sizeof(__nv_bfloat16) * (size_t)kMaxDigitPlanes * n_pad * n_pad;
+    const size_t bytes = plane_buffer_bytes(kMaxDigitPlanes, n_pad);
     PURIFY_CUDA_TRY(cudaMalloc(&ms->Xd[0], bytes));
     PURIFY_CUDA_TRY(cudaMalloc(&ms->Xd[1], bytes));
     PURIFY_CUDA_TRY(cudaMalloc(&ms->Sd, bytes));
@@ -375,7 +375,7 @@ int run_mixed_poly(purify_ctx* h, int scheme, double mu, const Schedule& S, int*
         cudaFree(ms->Pd[1]);
         ms->Pd[0] = ms->Pd[1] = nullptr;
         ms->pd_cap = 0;
-        const size_t bytes = sizeof(__nv_bfloat16) * (size_t)kMaxDigitPlanes * ms->n_pad_cap * ms->n_pad_cap;
+        const size_t bytes = plane_buffer_bytes(kMaxDigitPlanes, ms->n_pad_cap);
         PURIFY_CUDA_TRY(cudaMalloc(&ms->Pd[0], bytes));
         PURIFY_CUDA_TRY(cudaMalloc(&ms->Pd[1], bytes));
         ms->pd_cap = ms->n_pad_cap;
@@ -688,7 +688,7 @@ extern "C" int purify_k_digit_product_f64(const double* A, const double* B, doub
         return PURIFY_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int n_pad = pad128(n);
-    const size_t plane_bytes = sizeof(__nv_bfloat16) * (size_t)digits * n_pad * n_pad;
+    const size_t plane_bytes = plane_buffer_bytes(digits, n_pad);
     __nv_bfloat16 *pa = nullptr, *pb = nullptr;
     int* err = nullptr;
     float2* scratch = nullptr;

@@ -29,16 +29,16 @@ namespace purify {
 
 namespace {
 
-// Zero blocks (I, J) and (J, I) in s digit planes.
+// Zero blocks (I, J) and (J, I) in s digit planes (paired layout, see
+// plane_index: a block's row in one plane is 32 contiguous elements).
 __global__ void mask_planes_kernel(__nv_bfloat16* planes, int s, int n_pad, const int2* blocks) {
     const int2 b = blocks[blockIdx.x];
-    const size_t plane = (size_t)n_pad * n_pad;
     const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
     for (int p = 0; p < s; ++p)
         for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
             const int r = e >> 5, c = e & 31;
-            planes[p * plane + (size_t)(b.x * 32 + r) * n_pad + b.y * 32 + c] = z;
-            planes[p * plane + (size_t)(b.y * 32 + r) * n_pad + b.x * 32 + c] = z;
+            planes[plane_index(p, b.x * 32 + r, b.y * 32 + c, n_pad)] = z;
+            planes[plane_index(p, b.y * 32 + r, b.x * 32 + c, n_pad)] = z;
         }
 }
 
