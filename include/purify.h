@@ -135,8 +135,8 @@ typedef struct purify_options {
                             a step takes the fewest digits (3..6) whose bits cover
                             max(bits_floor, bits_gap + log2(1 / gap))              */
     int autotune;        /* MIXED dense products: 1 = time the candidate launch shapes
-                            (k-chunk width 16 / 32 / 64; the last wave's tiles split
-                            by the rule or whole) at the first product
+                            (the last wave's tiles split by the rule or whole) at the
+                            first product
                             of each digit count and padded size in this process, and
                             launch every later product of that kind with the fastest
                             (0 = the fixed rule, default).  Shapes differ only in the
@@ -157,7 +157,15 @@ typedef struct purify_options {
                             decides them on the device from the previous product's
                             float64 trace and the steps replay from a CUDA graph,
                             with one host read per 16 steps                        */
-    int reserved[2];
+    int launch_per_product; /* MIXED dense runs (Algorithms 1 and 2 with the beta-based
+                            schedule): 0 (default) = the run's products in queue
+                            launches (one per run of equal digit counts), consecutive
+                            products overlapping: an item waits on the device only for
+                            the two row panels of the previous product that it reads
+                            (used when a product has at least two waves of tiles);
+                            1 = one launch per product (also what time_products
+                            implies)                                               */
+    int reserved;
     double trunc_tau;    /* block_sparse: per-step truncation budget: blocks of
                             smallest Frobenius norm are dropped while the dropped
                             mass (off-diagonal blocks twice) stays <= tau^2       */

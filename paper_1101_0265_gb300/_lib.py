@@ -56,7 +56,8 @@ class Options(C.Structure):
                 ("refine_squares", C.c_int), ("digits", C.c_int), ("time_products", C.c_int),
                 ("block_sparse", C.c_int), ("split_k", C.c_int), ("refine_fp64", C.c_int),
                 ("bits_floor", C.c_int), ("bits_gap", C.c_int), ("autotune", C.c_int),
-                ("wait_kcycles", C.c_int), ("host_schedule", C.c_int), ("reserved", C.c_int * 2),
+                ("wait_kcycles", C.c_int), ("host_schedule", C.c_int), ("launch_per_product", C.c_int),
+                ("reserved", C.c_int),
                 ("trunc_tau", C.c_double), ("trunc_budget", C.c_double)]
 
 
@@ -199,7 +200,8 @@ class Purifier:
                  digits: int = 0, time_products: bool = False, block_sparse: bool = False,
                  trunc_tau: float = 1e-6, split_k: bool = True, refine_fp64: int = 0,
                  trunc_budget: float = 0.0, bits_floor: int = 0, bits_gap: int = 0,
-                 autotune: bool = False, wait_kcycles: int = 0, host_schedule: bool = False):
+                 autotune: bool = False, wait_kcycles: int = 0, host_schedule: bool = False,
+                 launch_per_product: bool = False):
         lib = load()
         self._lib = lib
         self.options = Options()
@@ -220,6 +222,7 @@ class Purifier:
         self.options.autotune = int(autotune)
         self.options.wait_kcycles = int(wait_kcycles)
         self.options.host_schedule = int(host_schedule)
+        self.options.launch_per_product = int(launch_per_product)
         h = C.c_void_p()
         _check(lib.purify_create(C.byref(h), device, _caller_stream(stream), C.byref(self.options)),
                "purify_create")

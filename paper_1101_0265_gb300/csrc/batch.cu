@@ -19,6 +19,7 @@
 
 #include "digits_kernel.cuh"
 #include "mixed.h"
+#include "queue_plan.h"
 
 using namespace purify;
 
@@ -66,13 +67,6 @@ void free_instance(Instance& in) {
     in.Xd[0] = in.Xd[1] = in.Sd = nullptr;
 }
 
-// Staging of a whole-batch queue launch (offsets into the staging buffers).
-struct QueuePlan {
-    int smax = 0;
-    int products = 0;
-    int items = 0;
-    size_t maps_off = 0, prm_off = 0, dep_off = 0, need_off = 0, cnt_off = 0, work_off = 0, end = 0;
-};
 
 }  // namespace
 
@@ -96,7 +90,7 @@ struct purify_batch {
     // reads it on every replay)
     void* qdev_buf = nullptr;
     size_t qdev_cap = 0;
-    QueuePlan last_queue;
+    QueueStaging last_queue;
     int last_mode = -1;
     // graph of the last full run
     cudaGraphExec_t graph = nullptr;
@@ -310,22 +304,18 @@ int launch_groups(purify_batch* B, const std::vector<GroupPlan>& groups) {
 
 // The whole batch as one persistent launch (queue mode of the product
 // kernel): every product of every instance in one work list, claimed in list
-// order by the persistent CTAs.  Each product's parameters and tensor maps
-// are staged in device memory; on the device an item of product k of an
+// order by the persistent CTAs; on the device an item of product k of an
 // instance waits until product k-1 of that instance has completed, so each
 // instance advances on its own.  The list order comes from a list-scheduling
 // simulation of the launch on the host: CTAs take the next item when they
 // come free, an instance's next product becomes available once its previous
 // one has finished, and among available products the one with the longest
-// items goes first.  An item is listed only after every item of the product
-// it waits for, so the CTAs holding those items are always running (no
-// deadlock whatever number of CTAs is resident).
-// Layout in host_buf / qdev_buf: maps | params | dep | need | cnt | work.
-int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueuePlan& q) {
-    q = QueuePlan();
-    for (Instance* in : all)
-        for (const DigitStep& st : in->steps) q.smax = std::max(q.smax, st.s_in);
-    // products: instance-major; product p of instance i depends on p - 1
+// items goes first.  stage_queue_products checks that no item precedes one
+// it waits for.
+int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueueStaging& q) {
+    // products: instance-major; an instance's product waits for every item
+    // of its previous one (which reads the buffer it overwrites, and wrote
+    // what it reads)
     struct Prod {
         Instance* in;
         int k;         // step index
@@ -336,6 +326,7 @@ int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueuePlan& q
         int next = -1; // the instance's following product
     };
     std::vector<Prod> prods;
+    std::vector<QueueProduct> qp;
     for (Instance* in : all) {
         const int T = in->n_pad / 128;
         for (int k = 0; k < (int)in->steps.size(); ++k) {
@@ -346,44 +337,28 @@ int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueuePlan& q
             Prod p{in, k, T, T * (T + 1) / 2, cost, k ? (int)prods.size() - 1 : -1};
             if (k) prods.back().next = (int)prods.size();
             prods.push_back(p);
+            QueueProduct x;
+            x.st = in->steps[k];
+            x.war0 = p.dep;
+            qp.push_back(x);
         }
     }
-    q.products = (int)prods.size();
+    const int products = (int)prods.size();
     size_t items = 0;
     for (const Prod& p : prods) items += (size_t)p.items;
-    q.items = (int)items;
-    q.maps_off = 0;
-    q.prm_off = align_up(q.maps_off + sizeof(CUtensorMap) * 2 * (size_t)q.products, 128);
-    q.dep_off = align_up(q.prm_off + sizeof(dk::DigitGemmParams) * (size_t)q.products, 128);
-    q.need_off = align_up(q.dep_off + sizeof(int) * (size_t)q.products, 128);
-    q.cnt_off = align_up(q.need_off + sizeof(int) * (size_t)q.products, 128);
-    q.work_off = align_up(q.cnt_off + sizeof(int) * (size_t)(q.products + 1), 128);  // + the claim ticket
-    q.end = q.work_off + sizeof(int4) * items;
-    if (B->host_buf.size() < q.end) B->host_buf.resize(q.end);
-    uint8_t* hb = B->host_buf.data();
-    CUtensorMap* maps = (CUtensorMap*)(hb + q.maps_off);
-    dk::DigitGemmParams* prm = (dk::DigitGemmParams*)(hb + q.prm_off);
-    int* dep = (int*)(hb + q.dep_off);
-    int* need = (int*)(hb + q.need_off);
-    int4* work = (int4*)(hb + q.work_off);
-    for (int pi = 0; pi < q.products; ++pi) {
-        const Prod& p = prods[pi];
-        PURIFY_TRY(fill_queue_product(p.in->steps[p.k], q.smax, &prm[pi], &maps[2 * pi]));
-        dep[pi] = p.dep;
-        need[pi] = kEpiWarps * p.items;
-    }
+    std::vector<int4> work;
+    work.reserve(items);
     // list scheduling over B->ctas simulated CTAs
     using TP = std::pair<double, int>;
     std::priority_queue<double, std::vector<double>, std::greater<double>> cta;
     for (int c = 0; c < std::max(1, B->ctas); ++c) cta.push(0.0);
     std::priority_queue<TP, std::vector<TP>, std::greater<TP>> future;  // (ready time, product)
     std::priority_queue<TP> ready;                                      // (item cost, -product)
-    std::vector<int> placed(q.products, 0);
-    std::vector<double> finish(q.products, 0.0);
-    for (int pi = 0; pi < q.products; ++pi)
+    std::vector<int> placed(products, 0);
+    std::vector<double> finish(products, 0.0);
+    for (int pi = 0; pi < products; ++pi)
         if (prods[pi].dep < 0) future.push({0.0, pi});
-    size_t w = 0;
-    while (w < items) {
+    while (work.size() < items) {
         double f = cta.top();
         cta.pop();
         while (!future.empty() && future.top().first <= f) {
@@ -402,7 +377,7 @@ int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueuePlan& q
         int tj = 0;
         while ((tj + 1) * (tj + 2) / 2 <= r) ++tj;
         const int ti = r - tj * (tj + 1) / 2;
-        work[w++] = make_int4(pi, ti, tj, 0);
+        work.push_back(make_int4(pi, ti, tj, 0));
         const double done = f + p.cost;
         finish[pi] = std::max(finish[pi], done);
         cta.push(done);
@@ -411,28 +386,11 @@ int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueuePlan& q
             if (p.next >= 0) future.push({finish[pi], p.next});
         }
     }
-    // the device waits rely on this: every item after all items of the
-    // product it waits for, and every item listed exactly once
-    std::vector<int> seen(q.products, 0);
-    for (size_t k = 0; k < items; ++k) {
-        const int4 v = work[k];
-        if (v.x < 0 || v.x >= q.products || v.y < 0 || v.y > v.z || v.z >= prods[v.x].T) return PURIFY_ERR_INTERNAL;
-        if (dep[v.x] >= 0 && seen[dep[v.x]] != prods[dep[v.x]].items) return PURIFY_ERR_INTERNAL;
-        ++seen[v.x];
-    }
-    for (int pi = 0; pi < q.products; ++pi)
-        if (seen[pi] != prods[pi].items) return PURIFY_ERR_INTERNAL;
-    return PURIFY_OK;
+    return stage_queue_products(qp, work, B->host_buf, q);
 }
 
-int launch_queue(purify_batch* B, const QueuePlan& q) {
-    if (q.items == 0) return PURIFY_OK;
-    uint8_t* dev = (uint8_t*)B->qdev_buf;
-    PURIFY_CUDA_TRY(cudaMemsetAsync(dev + q.cnt_off, 0, sizeof(int) * (size_t)(q.products + 1), B->stream));
-    return launch_digit_queue(q.smax, (const dk::DigitGemmParams*)(dev + q.prm_off), (const CUtensorMap*)(dev + q.maps_off),
-                              (const int*)(dev + q.dep_off), (const int*)(dev + q.need_off), (int*)(dev + q.cnt_off),
-                              q.products, (const int4*)(dev + q.work_off), q.items, B->scratch, B->ctas, B->err,
-                              B->stream, 1000ll * B->opt.wait_kcycles);
+int launch_queue(purify_batch* B, const QueueStaging& q) {
+    return launch_staged_queue(q, B->qdev_buf, B->scratch, B->ctas, B->err, B->stream, 1000ll * B->opt.wait_kcycles);
 }
 
 int queue_split(purify_batch* B, Instance& in) {
@@ -697,7 +655,7 @@ int purify_batch_run(purify_batch_t B, int mode) {
             PURIFY_TRY(ensure_dev(B, off));
             PURIFY_CUDA_TRY(cudaMemcpyAsync(B->dev_buf, B->host_buf.data(), off, cudaMemcpyHostToDevice, B->stream));
         } else {
-            QueuePlan q;
+            QueueStaging q;
             PURIFY_TRY(stage_queue(B, all, q));
             PURIFY_TRY(ensure_qdev(B, q.end));
             PURIFY_CUDA_TRY(cudaMemcpyAsync(B->qdev_buf, B->host_buf.data(), q.end, cudaMemcpyHostToDevice, B->stream));

@@ -7,9 +7,9 @@ namespace dk {
 
 KernelFn kernel_k32_hi(int s) {
     switch (s) {
-        case 4: return digit_gemm_kernel<32, 4, false>;
-        case 5: return digit_gemm_kernel<32, 5, false>;
-        case 6: return digit_gemm_kernel<32, 6, false>;
+        case 4: return digit_gemm_kernel<32, 4, 0>;
+        case 5: return digit_gemm_kernel<32, 5, 0>;
+        case 6: return digit_gemm_kernel<32, 6, 0>;
         default: return nullptr;
     }
 }

@@ -7,9 +7,9 @@ namespace dk {
 
 KernelFn kernel_k32_lo(int s) {
     switch (s) {
-        case 1: return digit_gemm_kernel<32, 1, false>;
-        case 2: return digit_gemm_kernel<32, 2, false>;
-        case 3: return digit_gemm_kernel<32, 3, false>;
+        case 1: return digit_gemm_kernel<32, 1, 0>;
+        case 2: return digit_gemm_kernel<32, 2, 0>;
+        case 3: return digit_gemm_kernel<32, 3, 0>;
         default: return nullptr;
     }
 }

@@ -305,13 +305,20 @@ struct DigitGemmParams {
     int nb;
     // device-side control of a single product (null: the fields above)
     const DevStep* ctl;
+    // queue launches: the products whose outputs this one reads as A and as B
+    // (-1: written before the launch; an item waits for the two row panels
+    // it reads), up to two products whose every item must have finished
+    // before this one starts (they read the buffer this one overwrites; -1:
+    // none), and the offset of this product's counters in DigitLaunch::qcnt
+    // (tiles_per_row row-panel counts, then the total).  Unused elsewhere.
+    int q_depA, q_depB, q_war0, q_war1, q_cnt;
 };
 
-// Products per launch whose tensor maps and parameters travel as kernel
-// parameters (grid constants).  TMA reads a tensor map written to global
-// memory by the host through a proxy that is not ordered with that write;
-// maps reused at the same address across launches were seen stale, so no
-// launch takes its maps from global memory.
+// Products per grouped launch, whose tensor maps and parameters travel as
+// kernel parameters (grid constants).  Queue launches read theirs from
+// global memory instead, each CTA fencing a map through the tensor-map proxy
+// before its copies use it (maps rewritten at the same address were seen
+// stale by TMA without that fence).
 constexpr int GMAX = 64;
 
 // One launch: products g = 0 .. ngroups-1 (tensor maps and parameters by
@@ -343,16 +350,15 @@ struct DigitLaunch {
     float* partial;                  // [slot][part][region 8][acc 4][16-col group 4][row 32][16]
     int* split_cnt;                  // [slot][region 8], zero at launch
     int* claim;                      // split launches: counter of claimed split items, zero at launch
-    // queue mode (a whole batch of purifications in one launch; null: off):
-    // every product's parameters and its A and B tensor maps in global
-    // memory (prms and maps are unused), each product with its own digit
-    // count <= the kernel's S; an item's operands are loaded only once the
-    // instance's previous product (qdep, -1: none) is complete, i.e. its qcnt
-    // has counted qneed epilogue-warp completions
+    // queue mode (many products in one launch; null: off): every product's
+    // parameters and its A and B tensor maps in global memory (prms and maps
+    // are unused), each product with its own digit count <= the kernel's S.
+    // An item's operands are loaded once the row panels it reads are
+    // complete (see DigitGemmParams::q_depA): each epilogue warp of a tile
+    // (ti, tj) counts itself in the product's counters of panels ti and tj and
+    // in its total after its stores.
     const DigitGemmParams* qprm;
     const CUtensorMap* qmaps;        // [2 * products]
-    const int* qdep;
-    const int* qneed;
     int* qcnt;                       // zero at launch
 };
 
@@ -410,20 +416,17 @@ __device__ __forceinline__ const DigitGemmParams& params_of(const DigitLaunch& L
         return L.prms[g];
 }
 
-// Queue mode: wait (bounded) until product d's epilogue warps have all
-// counted themselves done; false when the wait gives up.  The acquire orders
-// their plane stores before this thread's later copies, and the proxy fence
-// makes them visible to the tensor copies (async proxy).
-__device__ __forceinline__ bool wait_product(const DigitLaunch& L, int d, long long limit) {
-    const int need = L.qneed[d];
-    const int* c = L.qcnt + d;
+// Queue mode: wait (bounded) until a counter reaches `need` epilogue-warp
+// completions; false when the wait gives up (at the bound, or at once when
+// another CTA has failed: the count may then never be reached).  The acquire
+// orders the counted warps' plane stores before this thread's later copies,
+// and the proxy fence makes them visible to the tensor copies (async proxy).
+__device__ __forceinline__ bool wait_count(const DigitLaunch& L, const int* c, int need, long long limit) {
     int v;
     asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
     if (v < need) {
         const long long t0 = clock64();
         do {
-            // give up at the bound, or at once when another CTA has failed
-            // (the product may then never complete)
             if (clock64() - t0 > limit || *(volatile int*)L.err) return false;
             __nanosleep(64);
             asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(c) : "memory");
@@ -431,6 +434,20 @@ __device__ __forceinline__ bool wait_product(const DigitLaunch& L, int d, long l
     }
     asm volatile("fence.proxy.async.global;" ::: "memory");
     return true;
+}
+
+// Row panel r of product d complete: every tile touching it (tiles_per_row
+// of them) counted by all epilogue warps.
+__device__ __forceinline__ bool wait_panel(const DigitLaunch& L, int d, int r, long long limit) {
+    const DigitGemmParams& D = L.qprm[d];
+    return wait_count(L, L.qcnt + D.q_cnt + r, EPI_WARPS * D.tiles_per_row, limit);
+}
+
+// Every item of product d finished.
+__device__ __forceinline__ bool wait_all(const DigitLaunch& L, int d, long long limit) {
+    const DigitGemmParams& D = L.qprm[d];
+    const int T = D.tiles_per_row;
+    return wait_count(L, L.qcnt + D.q_cnt + T, EPI_WARPS * (T * (T + 1) / 2), limit);
 }
 
 // A tensor map in global memory, written by the host before the launch, is
@@ -524,12 +541,17 @@ __device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, lon
 // CTA's scratch (global, 128 x 128 x 8 bytes) so that tensor memory is
 // released before the polynomial, the re-split and the stores; those overlap
 // the next tile's MMAs.  All digit counts of a launch are S.
-// Q: a queue launch (per-product parameters, tensor maps and digit counts in
-// device memory, dependency waits and completion counts); a separate
-// instantiation, so that the other launches keep their compile-time digit
-// count S throughout.
-template <int KC, int S, bool Q>
+// QM: 0 = a single or grouped launch; 1 = a queue launch (per-product
+// parameters and tensor maps in device memory, dependency waits and
+// completion counts) whose products have digit counts up to S, read at run
+// time; 2 = a queue launch whose products all have S digits.  Separate
+// instantiations, so that launches with one digit count keep it a
+// compile-time constant throughout (a run-time count in the epilogue costs
+// about 4 % of a product).
+template <int KC, int S, int QM>
 __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ DigitLaunch L) {
+    constexpr bool Q = QM != 0;     // queue launch
+    constexpr bool QRT = QM == 1;   // digit counts read at run time
     static_assert(KC == 32, "digit planes are stored for 32-wide k-chunks");
     constexpr int NP = plane_pairs(S);           // plane pairs of one operand per stage
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -653,11 +675,15 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 if (cnt >= 0) nk = cnt;
                 const CUtensorMap* mA = Q ? &L.qmaps[2 * g] : &L.maps[2 * g];
                 const CUtensorMap* mB = Q ? &L.qmaps[2 * g + 1] : &L.maps[2 * g + 1];
-                const int s_it = Q ? Pg.s_in : S;  // this item's digit planes
+                const int s_it = QRT ? Pg.s_in : S;  // this item's digit planes
                 if constexpr (Q) {
                     acquire_map(mA);
                     acquire_map(mB);
-                    if (L.qdep[g] >= 0 && !wait_product(L, L.qdep[g], wait)) {
+                    const bool ready = (Pg.q_war0 < 0 || wait_all(L, Pg.q_war0, wait)) &&
+                                       (Pg.q_war1 < 0 || wait_all(L, Pg.q_war1, wait)) &&
+                                       (Pg.q_depA < 0 || wait_panel(L, Pg.q_depA, ti, wait)) &&
+                                       (Pg.q_depB < 0 || wait_panel(L, Pg.q_depB, tj, wait));
+                    if (!ready) {
                         atomicOr(L.err, ERR_PRODUCER_WAIT);
                         *abort_flag = 1;
                         break;
@@ -711,7 +737,7 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 item_of(L, t, g, ti, tj, slot, part);
                 const DigitGemmParams& Pg = params_of<Q>(L, g);
                 const int nl = Pg.kc_cnt ? Pg.kc_cnt[tj * (tj + 1) / 2 + ti] : -1;
-                const int s_it = Q ? Pg.s_in : S;
+                const int s_it = QRT ? Pg.s_in : S;
                 int kb, nk;
                 dense_k_range(L, Pg.n_pad / KC, slot, part, kb, nk);
                 if (nl >= 0) nk = nl;
@@ -732,9 +758,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     const uint64_t da = desc_base + (uint64_t)((st * stage_bytes) >> 4);
                     const uint64_t db = da + (uint64_t)((NP * PAIR_BYTES) >> 4);
                     const uint32_t later = kc > 0 ? 1u : 0u;
-                    if (!Q || s_it == S)
+                    if (!QRT || s_it == S)
                         issue_chunk<S>(tmem, da, db, later);
-                    else if constexpr (Q)
+                    else if constexpr (QRT)
                         issue_chunk_runtime<S - 1>(s_it, tmem, da, db, later);
                     mma_commit(smem_u32(&empty_bar[st]));
                 }
@@ -769,7 +795,7 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             int g, ti, tj, slot, part;
             item_of(L, t, g, ti, tj, slot, part);
             const DigitGemmParams& P = params_of<Q>(L, g);
-            const int s = Q ? P.s_in : S;  // this item's digit planes
+            const int s = QRT ? P.s_in : S;  // this item's digit planes
             const size_t plane = (size_t)P.n_pad * P.n_pad;
             bool ready = mbar_wait_for(smem_u32(tmem_full), (uint32_t)(lt & 1), wait);
             if (!ready) {
@@ -1116,7 +1142,12 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 asm volatile("fence.proxy.async.global;" ::: "memory");
                 __threadfence();
                 __syncwarp();
-                if (lane == 0) atomicAdd(&L.qcnt[g], 1);
+                if (lane == 0) {
+                    int* c = L.qcnt + P.q_cnt;
+                    atomicAdd(c + ti, 1);
+                    if (tj != ti) atomicAdd(c + tj, 1);
+                    atomicAdd(c + P.tiles_per_row, 1);
+                }
             }
         }
     }
@@ -1137,6 +1168,8 @@ KernelFn kernel_k32_lo(int s);
 KernelFn kernel_k32_hi(int s);
 KernelFn kernel_queue_hi(int s);
 KernelFn kernel_queue_lo(int s);
+KernelFn kernel_queue_uniform_hi(int s);  // digits_queue_uniform_<lo|hi>.cu (QM = 2)
+KernelFn kernel_queue_uniform_lo(int s);
 
 }  // namespace dk
 }  // namespace purify

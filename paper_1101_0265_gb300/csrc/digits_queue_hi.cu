@@ -7,9 +7,9 @@ namespace dk {
 
 KernelFn kernel_queue_hi(int s) {
     switch (s) {
-        case 4: return digit_gemm_kernel<32, 4, true>;
-        case 5: return digit_gemm_kernel<32, 5, true>;
-        case 6: return digit_gemm_kernel<32, 6, true>;
+        case 4: return digit_gemm_kernel<32, 4, 1>;
+        case 5: return digit_gemm_kernel<32, 5, 1>;
+        case 6: return digit_gemm_kernel<32, 6, 1>;
         default: return nullptr;
     }
 }

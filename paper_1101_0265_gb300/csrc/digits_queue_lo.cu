@@ -7,9 +7,9 @@ namespace dk {
 
 KernelFn kernel_queue_lo(int s) {
     switch (s) {
-        case 1: return digit_gemm_kernel<32, 1, true>;
-        case 2: return digit_gemm_kernel<32, 2, true>;
-        case 3: return digit_gemm_kernel<32, 3, true>;
+        case 1: return digit_gemm_kernel<32, 1, 1>;
+        case 2: return digit_gemm_kernel<32, 2, 1>;
+        case 3: return digit_gemm_kernel<32, 3, 1>;
         default: return nullptr;
     }
 }

@@ -235,15 +235,22 @@ int prepare_kernel(KernelFn fn) {
     return PURIFY_OK;
 }
 
-// The queue-launch instantiation for a largest digit count s.
-static KernelFn queue_kernel(int s) { return s <= 3 ? kernel_queue_lo(s) : kernel_queue_hi(s); }
+// The queue-launch instantiation for a largest digit count s (uniform: every
+// product has s digits).
+static KernelFn queue_kernel(int s, bool uniform) {
+    if (uniform) return s <= 3 ? kernel_queue_uniform_lo(s) : kernel_queue_uniform_hi(s);
+    return s <= 3 ? kernel_queue_lo(s) : kernel_queue_hi(s);
+}
 
 int prepare_digit_kernels() {
     for (int s = 1; s <= kMaxDigitPlanes; ++s) {
         KernelFn fn = kernel_for(32, s);
         if (fn) PURIFY_TRY(prepare_kernel(fn));
     }
-    for (int s = 1; s <= kMaxDigitPlanes; ++s) PURIFY_TRY(prepare_kernel(queue_kernel(s)));
+    for (int s = 1; s <= kMaxDigitPlanes; ++s) {
+        PURIFY_TRY(prepare_kernel(queue_kernel(s, false)));
+        PURIFY_TRY(prepare_kernel(queue_kernel(s, true)));
+    }
     return PURIFY_OK;
 }
 
@@ -287,8 +294,8 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
     return PURIFY_OK;
 }
 
-static int launch_kernel(const DigitLaunch& L, int s, int kc, int grid, cudaStream_t stream) {
-    KernelFn fn = L.qprm ? queue_kernel(s) : kernel_for(kc, s);
+static int launch_kernel(const DigitLaunch& L, int s, int kc, int grid, cudaStream_t stream, bool uniform = false) {
+    KernelFn fn = L.qprm ? queue_kernel(s, uniform) : kernel_for(kc, s);
     if (!fn || grid < 1 || L.stages < 1) return PURIFY_ERR_INVALID_ARG;
     PURIFY_TRY(prepare_kernel(fn));
     fn<<<grid, NTHREADS, digit_smem_bytes(s, kc), stream>>>(L);
@@ -401,19 +408,16 @@ int fill_queue_product(const DigitStep& st0, int smax, DigitGemmParams* p, CUten
     return PURIFY_OK;
 }
 
-int launch_digit_queue(int smax, const DigitGemmParams* prm, const CUtensorMap* maps, const int* dep, const int* need,
-                       int* cnt, int num_products, const int4* work, int num_items, float2* scratch, int max_ctas,
-                       int* err, cudaStream_t stream, long long wait_cycles) {
-    if (smax < 1 || smax > kMaxDigitPlanes || !prm || !maps || !dep || !need || !cnt || num_products < 1 || !work ||
-        !scratch || !err)
+int launch_digit_queue(int smax, bool uniform, const DigitGemmParams* prm, const CUtensorMap* maps, int* cnt,
+                       int* ticket, const int4* work, int num_items, float2* scratch, int max_ctas, int* err,
+                       cudaStream_t stream, long long wait_cycles) {
+    if (smax < 1 || smax > kMaxDigitPlanes || !prm || !maps || !cnt || !ticket || !work || !scratch || !err)
         return PURIFY_ERR_INVALID_ARG;
     if (num_items <= 0) return PURIFY_OK;
     DigitLaunch L;
     std::memset(&L, 0, sizeof(L));
     L.qprm = prm;
     L.qmaps = maps;
-    L.qdep = dep;
-    L.qneed = need;
     L.qcnt = cnt;
     L.work = work;
     L.num_items = num_items;
@@ -421,11 +425,11 @@ int launch_digit_queue(int smax, const DigitGemmParams* prm, const CUtensorMap* 
     L.scratch = scratch;
     L.err = err;
     L.wait_cycles = wait_cycles;
-    L.claim = cnt + num_products;  // every item claimed in ticket order
+    L.claim = ticket;  // every item claimed in ticket order
     L.split_begin = 0;             // (item_of reads the work list: no split parts)
     L.split_ways = 1;
     const int grid = num_items < max_ctas ? num_items : max_ctas;
-    return launch_kernel(L, smax, queue_kc(smax), grid, stream);
+    return launch_kernel(L, smax, queue_kc(smax), grid, stream, uniform);
 }
 
 int launch_split(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s,

@@ -114,19 +114,20 @@ namespace purify {
 namespace dk {
 struct DigitGemmParams;
 }
-// Queue launches (a whole batch in one persistent launch, see DigitLaunch):
-// the k-chunk width of a launch whose largest digit count is smax; one
-// product's parameters and its A and B tensor maps (maps[0], maps[1]) for
-// such a launch; and the launch itself over `num_items` work items {product,
-// ti, tj, -} in device memory, claimed in order, each product waiting for its
-// instance's previous one (dep, -1: none) to have counted need completions in
-// cnt.  cnt holds num_products + 1 ints, zero at launch (the last one is the
-// claim ticket).  All arrays are in device memory.
+// Queue launches (many products in one persistent launch, see DigitLaunch):
+// the k-chunk width of such a launch; one product's parameters (without the
+// q_* dependency fields, which the caller sets) and its A and B tensor maps
+// (maps[0], maps[1]); and the launch itself over `num_items` work items
+// {product, ti, tj, -} in device memory, claimed in order from *ticket
+// (uniform: every product has smax digits, the kernel then holds the count
+// as a compile-time constant).  cnt holds every product's counters
+// (DigitGemmParams::q_cnt); cnt and *ticket are zero at launch.  All arrays
+// are in device memory.
 int queue_kc(int smax);
 int fill_queue_product(const DigitStep& st, int smax, dk::DigitGemmParams* p, CUtensorMap* maps);
-int launch_digit_queue(int smax, const dk::DigitGemmParams* prm, const CUtensorMap* maps, const int* dep,
-                       const int* need, int* cnt, int num_products, const int4* work, int num_items, float2* scratch,
-                       int max_ctas, int* err, cudaStream_t stream, long long wait_cycles);
+int launch_digit_queue(int smax, bool uniform, const dk::DigitGemmParams* prm, const CUtensorMap* maps, int* cnt,
+                       int* ticket, const int4* work, int num_items, float2* scratch, int max_ctas, int* err,
+                       cudaStream_t stream, long long wait_cycles);
 
 // out planes of a F + b I (i, j < n; zero padding up to n_pad), exponent e,
 // s digits.  red[0] += trace (float accuracy) when red is not null;

@@ -20,6 +20,7 @@
 #include <tuple>
 
 #include "digits_tc.h"
+#include "queue_plan.h"
 
 namespace purify {
 
@@ -40,6 +41,7 @@ void mixed_free(MixedState* ms) {
     cudaFree(ms->pat_dev);
     cudaFree(ms->tsel);
     cudaFree(ms->tsched);
+    cudaFree(ms->qdev);
     if (ms->tgraph) cudaGraphExecDestroy(ms->tgraph);
     delete ms;
 }
@@ -86,6 +88,21 @@ int digits_for_gap(double g, const purify_options& o, int rbits) {
 }
 
 static double pairs_of(int s) { return 0.5 * s * (s + 1); }
+
+// The two further plane buffers (P_{3,3} intermediates; the queue run's
+// third X and second S buffer), at the handle's capacity.
+static int ensure_pd(MixedState* ms) {
+    if (ms->pd_cap >= ms->n_pad_cap) return PURIFY_OK;
+    cudaFree(ms->Pd[0]);
+    cudaFree(ms->Pd[1]);
+    ms->Pd[0] = ms->Pd[1] = nullptr;
+    ms->pd_cap = 0;
+    const size_t bytes = plane_buffer_bytes(kMaxDigitPlanes, ms->n_pad_cap);
+    PURIFY_CUDA_TRY(cudaMalloc(&ms->Pd[0], bytes));
+    PURIFY_CUDA_TRY(cudaMalloc(&ms->Pd[1], bytes));
+    ms->pd_cap = ms->n_pad_cap;
+    return PURIFY_OK;
+}
 
 // Algorithm 2 step coefficients: Y = cP X^2 + cE X + cI I.
 static void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
@@ -370,16 +387,7 @@ int run_mixed_poly(purify_ctx* h, int scheme, double mu, const Schedule& S, int*
     const int n_pad = pad128(n);
     PURIFY_TRY(ensure_mixed(h, n_pad));
     MixedState* ms = h->mixed;
-    if (ms->pd_cap < ms->n_pad_cap) {
-        cudaFree(ms->Pd[0]);
-        cudaFree(ms->Pd[1]);
-        ms->Pd[0] = ms->Pd[1] = nullptr;
-        ms->pd_cap = 0;
-        const size_t bytes = plane_buffer_bytes(kMaxDigitPlanes, ms->n_pad_cap);
-        PURIFY_CUDA_TRY(cudaMalloc(&ms->Pd[0], bytes));
-        PURIFY_CUDA_TRY(cudaMalloc(&ms->Pd[1], bytes));
-        ms->pd_cap = ms->n_pad_cap;
-    }
+    PURIFY_TRY(ensure_pd(ms));
     const int m = (int)S.alpha.size();
     const int fixed = h->opt.digits;
     const int T = n_pad / 128;
@@ -486,12 +494,285 @@ int run_mixed_poly(purify_ctx* h, int scheme, double mu, const Schedule& S, int*
     return PURIFY_OK;
 }
 
+// A dense run (Algorithm 1 or 2 with the beta-based schedule, optional
+// refinement squares) as queue launches of the product kernel after the f_0
+// split: one per run of consecutive products with the same digit count
+// (usually two: the first steps at 6 digits, the rest at 5).  The products
+// are the same as the per-product path's; they differ in two ways:
+//  - plane buffers rotate so that no product overwrites planes a running
+//    product may still read: X over three buffers, Algorithm 1's S (and the
+//    refinement's square) over two;
+//  - every product's tiles run in chain_tile_order, and an item waits on the
+//    device only for the two row panels of the products it reads (plus the
+//    completion of the products that read the buffer it overwrites), so a
+//    product's first items start while the previous product's last wave is
+//    still running.
+// The arithmetic of every tile is the per-product path's (whole tiles, no
+// split of the last wave).
+static int run_mixed_queue(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
+                           std::vector<double>& red) {
+    const int n = (int)h->n;
+    const int n_pad = pad128(n);
+    MixedState* ms = h->mixed;
+    PURIFY_TRY(ensure_pd(ms));
+    const bool fixed_mu = scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_FIXED_MU_MONO;
+    const int m = (int)S.alpha.size();
+    const int R = h->opt.refine_squares;
+    const int fixed = h->opt.digits;
+    const int T = n_pad / 128;
+    const int rb = remainder_bits(n_pad);
+    const double tile_flops = 2.0 * 128.0 * 128.0 * (double)n_pad * (double)(T * (T + 1) / 2);
+
+    std::vector<int> sd(m + R + 1);
+    for (int i = 0; i < m; ++i) {
+        const double b = i ? S.beta[i - 1] : S.beta0;
+        const double bb = i ? S.betabar[i - 1] : S.betabar0;
+        sd[i] = digits_for_gap(bb - b, h->opt, rb);
+    }
+    for (int i = m; i <= m + R; ++i) sd[i] = fixed > 0 ? fixed : kMaxDigitPlanes;
+    int dmax = 0;
+    for (int i = 0; i < m + R; ++i) dmax = sd[i] > dmax ? sd[i] : dmax;
+    h->st.digit_max = dmax;
+    h->st.digit_kc = 32;
+
+    const int slots = 2 * (m + R) + 2;
+    PURIFY_TRY(ensure_red(h, 4 * (int64_t)slots));
+
+    // buffers 0..2 hold X values, 3..4 S values; the writer and the readers
+    // of each buffer's current content give the dependencies
+    __nv_bfloat16* buf[5] = {ms->Xd[0], ms->Xd[1], ms->Pd[0], ms->Sd, ms->Pd[1]};
+    int writer[5] = {-1, -1, -1, -1, -1};
+    std::vector<int> readers[5];
+    std::vector<QueueProduct> prods;
+    double flops = 0.0;
+    auto add = [&](DigitStep st, int a, int b, int out) -> int {
+        QueueProduct q;
+        st.n = n;
+        st.n_pad = n_pad;
+        st.rbits = rb;
+        st.A = buf[a];
+        st.B = buf[b];
+        st.err = ms->err;
+        st.scratch = ms->scratch;
+        st.max_ctas = ms->ctas;
+        if (out >= 0) st.out = buf[out];
+        q.st = st;
+        q.depA = writer[a];
+        q.depB = writer[b];
+        if (out >= 0) {
+            if (readers[out].size() > 2) return PURIFY_ERR_INTERNAL;
+            if (readers[out].size() > 0) q.war0 = readers[out][0];
+            if (readers[out].size() > 1) q.war1 = readers[out][1];
+        }
+        const int g = (int)prods.size();
+        readers[a].push_back(g);
+        if (b != a) readers[b].push_back(g);
+        if (out >= 0) {
+            writer[out] = g;
+            readers[out].clear();
+        }
+        prods.push_back(q);
+        flops += pairs_of(st.s_in) * tile_flops;
+        return PURIFY_OK;
+    };
+
+    const double lmin = h->b.lmin, lmax = h->b.lmax;
+    double c0, c1;  // X_0 = c0 I + c1 F
+    if (fixed_mu) {
+        const double gamma = 2.0 * std::max(lmax - mu, mu - lmin);
+        c0 = mu / gamma + 0.5;
+        c1 = -1.0 / gamma;
+    } else {
+        c0 = lmax / (lmax - lmin);
+        c1 = -1.0 / (lmax - lmin);
+    }
+    double* D = h->X[0];
+    *cur = 0;
+    int x = 0;  // X buffer of the current iterate
+    if (fixed_mu) {
+        for (int i = 0; i < m + R; ++i) {
+            const int s = sd[i];
+            const int sb = 3 + (i & 1), xn = (x + 1) % 3;
+            DigitStep p1;
+            p1.s_in = s;
+            p1.eA = p1.eB = 1;
+            p1.s_out = s;
+            p1.e_out = 1;
+            PURIFY_TRY(add(p1, x, x, sb));
+            // X_i = 3 S - 2 S X_s, emitted as the next X_s (or as D)
+            DigitStep p2;
+            p2.s_in = s;
+            p2.eA = p2.eB = 1;
+            p2.e_out = 1;
+            p2.use_E = 1;
+            p2.cP = -2.0;
+            p2.cE = 3.0;
+            p2.red = h->red + 4 * (2 * i + 1);
+            if (i + 1 == m + R) {
+                p2.out64 = D;
+                PURIFY_TRY(add(p2, sb, x, -1));
+            } else {
+                const double an = (i + 1 < m) ? S.alpha[i + 1] : 1.0;
+                p2.dY = an;
+                p2.dI = 0.5 * (1.0 - an);
+                p2.s_out = sd[i + 1];
+                PURIFY_TRY(add(p2, sb, x, xn));
+            }
+            x = xn;
+        }
+    } else {
+        for (int i = 0; i < m; ++i) {
+            const int s = sd[i];
+            const int xn = (x + 1) % 3;
+            DigitStep st;
+            st.s_in = s;
+            st.eA = st.eB = 0;
+            st.use_E = 1;
+            tc_coeffs(S.branch[i], S.alpha[i], &st.cP, &st.cE, &st.cI);
+            st.red = h->red + 4 * (2 * i + 1);
+            if ((i + 1 == m) && R == 0) {
+                st.out64 = D;
+                PURIFY_TRY(add(st, x, x, -1));
+            } else {
+                st.s_out = sd[i + 1];
+                st.e_out = 0;
+                PURIFY_TRY(add(st, x, x, xn));
+            }
+            x = xn;
+        }
+        // refinement: unscaled McWeeny X <- 3 X^2 - 2 X^3 at the finest digits
+        for (int r = 0; r < R; ++r) {
+            const int i = m + r;
+            const int s = sd[i];
+            const int sb = 3 + (r & 1), xn = (x + 1) % 3;
+            DigitStep p1;
+            p1.s_in = s;
+            p1.eA = p1.eB = 0;
+            p1.s_out = s;
+            p1.e_out = 0;
+            p1.use_E = 1;  // ||X - X^2|| of the iterate
+            p1.cP = 1.0;
+            p1.cE = 0.0;
+            p1.red = (r + 1 == R) ? h->red + 4 * (2 * i) : nullptr;
+            PURIFY_TRY(add(p1, x, x, sb));
+            DigitStep p2;
+            p2.s_in = s;
+            p2.eA = p2.eB = 0;
+            p2.e_out = 0;
+            p2.use_E = 1;
+            p2.cP = -2.0;
+            p2.cE = 3.0;
+            p2.red = (r + 1 == R) ? h->red + 4 * (2 * i + 1) : nullptr;
+            if (r + 1 == R) {
+                p2.out64 = D;
+                PURIFY_TRY(add(p2, sb, x, -1));
+            } else {
+                p2.s_out = sd[i + 1];
+                PURIFY_TRY(add(p2, sb, x, xn));
+            }
+            x = xn;
+        }
+    }
+    // one queue launch per run of products with the same digit count (the
+    // kernel then holds the count as a compile-time constant); a dependency
+    // on a product of an earlier launch is met by stream order
+    std::vector<int2> order;
+    chain_tile_order(T, ms->ctas, order);
+    struct Segment {
+        QueueStaging q;
+        size_t off;
+    };
+    std::vector<Segment> segs;
+    std::vector<uint8_t> seg_host;
+    size_t total = 0;
+    ms->qhost.clear();
+    for (int a = 0; a < (int)prods.size();) {
+        int b = a + 1;
+        while (b < (int)prods.size() && prods[b].st.s_in == prods[a].st.s_in) ++b;
+        std::vector<QueueProduct> part(prods.begin() + a, prods.begin() + b);
+        for (QueueProduct& p : part)
+            for (int* d : {&p.depA, &p.depB, &p.war0, &p.war1}) *d = *d >= a ? *d - a : -1;
+        std::vector<int4> work;
+        work.reserve(order.size() * part.size());
+        for (int g = 0; g < (int)part.size(); ++g)
+            for (const int2& t : order) work.push_back(make_int4(g, t.x, t.y, 0));
+        Segment sg;
+        PURIFY_TRY(stage_queue_products(part, work, seg_host, sg.q));
+        sg.off = total;
+        total += (sg.q.end + 255) / 256 * 256;
+        ms->qhost.resize(total);
+        std::memcpy(ms->qhost.data() + sg.off, seg_host.data(), sg.q.end);
+        segs.push_back(sg);
+        a = b;
+    }
+    if (total > ms->qdev_cap) {
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+        cudaFree(ms->qdev);
+        ms->qdev = nullptr;
+        ms->qdev_cap = 0;
+        const size_t cap = std::max(total, (size_t)1 << 20) * 2;
+        PURIFY_CUDA_TRY(cudaMalloc(&ms->qdev, cap));
+        ms->qdev_cap = cap;
+    }
+
+    PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * slots, h->stream));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->err, 0, sizeof(int), h->stream));
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e0, h->stream));
+    if (fixed_mu) {
+        // X_s of the first iteration, e = 1 (eigenvalues in [(1-a)/2, (1+a)/2])
+        const double a1 = m ? S.alpha[0] : 1.0;
+        PURIFY_TRY(launch_split(h->F, n, n, n_pad, a1 * c1, a1 * (c0 - 0.5) + 0.5, 1, sd[0], rb, buf[0], nullptr,
+                                h->stream));
+    } else {
+        PURIFY_TRY(launch_split(h->F, n, n, n_pad, c1, c0, 0, sd[0], rb, buf[0], nullptr, h->stream));
+    }
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->qdev, ms->qhost.data(), total, cudaMemcpyHostToDevice, h->stream));
+    for (const Segment& sg : segs)
+        PURIFY_TRY(launch_staged_queue(sg.q, (uint8_t*)ms->qdev + sg.off, ms->scratch, ms->ctas, ms->err, h->stream,
+                                       1000ll * h->opt.wait_kcycles));
+    h->st.product_launches += (int)prods.size();
+    h->st.tensor_flops += flops;
+    PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
+    red.assign(4 * (size_t)slots, 0.0);
+    int err = 0;
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(red.data(), h->red, sizeof(double) * red.size(),
+                                    cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, ms->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    h->st.device_flag = err;
+    if (err) return device_flag_status(err);
+    h->st.refine_multiplications = 2 * R;
+    const int last = m + R - 1;
+    if (last >= 0) {
+        h->st.trace = red[4 * (size_t)(2 * last + 1)];
+        if (!fixed_mu && R == 0) {
+            h->st.idem_err_fro = std::sqrt(std::max(red[4 * (size_t)(2 * last + 1) + 1], 0.0));
+        } else if (R > 0) {
+            h->st.idem_err_fro = std::sqrt(std::max(red[4 * (size_t)(2 * last) + 1], 0.0));
+        } else {
+            h->st.idem_err_fro = NAN;
+        }
+    } else {
+        h->st.trace = NAN;
+        h->st.idem_err_fro = NAN;
+    }
+    return PURIFY_OK;
+}
+
 int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
               std::vector<double>& red) {
     const int n = (int)h->n;
     const int n_pad = pad128(n);
     PURIFY_TRY(ensure_mixed(h, n_pad));
     MixedState* ms = h->mixed;
+    {
+        // queue launches for the whole run when a product has at least two
+        // waves of tiles (below that the split of the last wave pays more)
+        const int Tq = n_pad / 128;
+        if (!h->opt.launch_per_product && !h->opt.time_products && S.alpha.size() + h->opt.refine_squares > 0 &&
+            Tq * (Tq + 1) / 2 >= 2 * ms->ctas)
+            return run_mixed_queue(h, scheme, mu, S, cur, red);
+    }
     const bool fixed_mu = scheme == PURIFY_FIXED_MU_SF || scheme == PURIFY_FIXED_MU_MONO;
     const int m = (int)S.alpha.size();
     const int R = h->opt.refine_squares;

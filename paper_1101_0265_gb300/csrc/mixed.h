@@ -64,6 +64,10 @@ struct MixedState {
     const double* tg_red = nullptr;
     const double* tg_D = nullptr;
     const void* tg_X0 = nullptr;
+    // a whole run as queue launches: staging (host and device copies)
+    std::vector<uint8_t> qhost;
+    void* qdev = nullptr;
+    size_t qdev_cap = 0;
 };
 
 // Allocate (or grow) the handle's mixed-path buffers for a padded size.

@@ -331,3 +331,27 @@ def test_autotuned_launch_shapes(P):
     assert s0["digit_kc"] == 32
     shape = P.tuned_shape(0, s0["digit_max"], 1200)
     assert shape is not None and shape[0] == 32 and shape[1] in (0, 1)
+
+
+@pytest.mark.parametrize("scheme,refine", [("TC_SF", 0), ("FIXED_MU_SF", 0), ("TC_MONO", 1)])
+def test_run_as_queue_launches_equals_per_product(P, scheme, refine):
+    # n = 3200: 325 tiles per product, at least two waves on 152 SMs, so the
+    # run goes through queue launches (products overlapping, an item waiting
+    # on the device for the row panels it reads); with whole tiles the
+    # per-product launches compute the same tiles with the same additions
+    h = I.dense_hamiltonian(3200, 1300, 0.01, config=75)
+    out = []
+    for per_product in (False, True):
+        pur = P.Purifier(precision="mixed", launch_per_product=per_product, split_k=False,
+                         refine_squares=refine)
+        pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+        assert pur.run(scheme, 1e-10, 200) == P.OK
+        out.append((pur.density(), pur.stats(), pur.step_history()))
+        pur.close()
+    (Dq, sq, hq), (Dp, sp, hp) = out
+    assert np.array_equal(Dq, Dp)
+    assert sq["multiplications"] == sp["multiplications"] and sq["iterations"] == sp["iterations"]
+    assert sq["trace"] == pytest.approx(sp["trace"], abs=1e-9)
+    assert np.allclose(hq[0], hp[0], rtol=0, atol=1e-9)
+    Dx = O.density_closed_form(h.Q, h.lam, 0.0)
+    assert np.max(np.abs(Dq - Dx)) <= 1e-6

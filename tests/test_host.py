@@ -208,8 +208,8 @@ def test_options_struct_layout_matches_the_library():
     assert o.lanczos_steps == 16 and o.refine_squares == 0 and o.digits == 0
     assert o.split_k == 1 and o.refine_fp64 == 0 and o.block_sparse == 0 and o.time_products == 0
     assert o.bits_floor == 0 and o.bits_gap == 0 and o.autotune == 0 and o.wait_kcycles == 0
-    assert o.host_schedule == 0
-    assert list(o.reserved) == [0] * len(o.reserved)
+    assert o.host_schedule == 0 and o.launch_per_product == 0
+    assert o.reserved == 0
     assert o.trunc_tau == 1e-6 and o.trunc_budget == 0.0
 
 
