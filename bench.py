@@ -34,15 +34,16 @@ SCHEMES = ("TC_SF", "FIXED_MU_SF")
 SMS = 152                        # GB300 streaming multiprocessors
 TENSOR_FLOP_PER_CLK_SM = 8192    # dense bf16 tcgen05 rate per SM and clock (nominal)
 FP64_FLOP_PER_CLK_SM = 4         # two float64 FMAs per SM and clock (nominal)
-# The tensor pipe's active share of one digit-plane product launch (ncu
-# sm__pipe_tensor_cycles_active of digit_gemm_kernel<32, 5>, n = 4096).
-TENSOR_PIPE_PCT_NCU = 67.1
-TENSOR_PIPE_SOURCE = "profiles/digit_gemm_kc32_s5_n4096.md (ncu, one launch, n=4096, S=5)"
-# DRAM bytes (read + write) of one digit-plane product launch, from one ncu
-# capture of digit_gemm_kernel<32, 5> at n = 4096 (bytes per launch).
-TRAFFIC_DIGIT_GEMM = 783.8e6
-TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of digit_gemm_kernel<32,5>, n=4096, one launch "
-                  "(530.2 MB read + 253.7 MB written)")
+# The tensor pipe's active share of one queue launch of the digit-plane
+# product (ncu sm__pipe_tensor_cycles_active of digit_gemm_kernel<32, 5, 2>:
+# one TC_SF run at n = 4096, 14 products in one launch).
+TENSOR_PIPE_PCT_NCU = 75.5
+TENSOR_PIPE_SOURCE = "profiles/digit_gemm_queue_s5_n4096.md (ncu, one queue launch, n=4096, S=5, 14 products)"
+# DRAM bytes (read + write) of that launch, from the same ncu capture.
+TRAFFIC_DIGIT_GEMM = 17.769e9
+TRAFFIC_PRODUCTS = 14
+TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of digit_gemm_kernel<32,5,2>, n=4096, one queue launch of 14 "
+                  "products (14.445 GB read + 3.324 GB written; 1.269 GB per product)")
 
 
 def parse():
@@ -684,7 +685,9 @@ def main():
         at_clock = SMS * TENSOR_FLOP_PER_CLK_SM * sm_mhz * 1e6 / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_DIGIT_GEMM,
-                "kernel": "digit-plane tcgen05 product", "peak_kind": f"{pk_kind} bf16 sustained",
+                "traffic_products_per_launch": TRAFFIC_PRODUCTS,
+                "kernel": "digit-plane tcgen05 product (queue launches: a run's products overlapping)",
+                "peak_kind": f"{pk_kind} bf16 sustained",
                 "traffic_source": TRAFFIC_SOURCE,
                 "tensor_pipe_pct_ncu": TENSOR_PIPE_PCT_NCU, "tensor_pipe_source": TENSOR_PIPE_SOURCE,
                 "per_clock": {"sm_mhz": sm_mhz, "peak_tflops_at_clock": at_clock,

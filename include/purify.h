@@ -115,7 +115,8 @@ typedef struct purify_options {
     int digits;          /* MIXED: 0 = per-step digit count from the mapped gap
                             (default); 2..6 = fixed count                             */
     int time_products;   /* 1 = bracket every matrix-product launch with CUDA events
-                            on the handle's stream and report their total time      */
+                            on the handle's stream and report their total time (a
+                            dense run's queue launches: one interval)               */
     int block_sparse;    /* MIXED, Algorithm 2 schemes: keep every iterate as a
                             pattern of 32 x 32 blocks, form products only over
                             nonzero blocks and truncate after every step         */
@@ -162,9 +163,9 @@ typedef struct purify_options {
                             launches (one per run of equal digit counts), consecutive
                             products overlapping: an item waits on the device only for
                             the two row panels of the previous product that it reads
-                            (used when a product has at least two waves of tiles);
-                            1 = one launch per product (also what time_products
-                            implies)                                               */
+                            (used when a product has at least two waves of tiles;
+                            time_products then times the queue launches as one
+                            interval); 1 = one launch per product              */
     int reserved;
     double trunc_tau;    /* block_sparse: per-step truncation budget: blocks of
                             smallest Frobenius norm are dropped while the dropped

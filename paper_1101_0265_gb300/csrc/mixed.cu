@@ -727,9 +727,13 @@ static int run_mixed_queue(purify_ctx* h, int scheme, double mu, const Schedule&
         PURIFY_TRY(launch_split(h->F, n, n, n_pad, c1, c0, 0, sd[0], rb, buf[0], nullptr, h->stream));
     }
     PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->qdev, ms->qhost.data(), total, cudaMemcpyHostToDevice, h->stream));
+    // with time_products, one interval covers the queue launches (the
+    // products overlap, so they have no times of their own)
+    PURIFY_TRY(product_begin(h));
     for (const Segment& sg : segs)
         PURIFY_TRY(launch_staged_queue(sg.q, (uint8_t*)ms->qdev + sg.off, ms->scratch, ms->ctas, ms->err, h->stream,
                                        1000ll * h->opt.wait_kcycles));
+    PURIFY_TRY(product_end(h));
     h->st.product_launches += (int)prods.size();
     h->st.tensor_flops += flops;
     PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
@@ -769,7 +773,7 @@ int run_mixed(purify_ctx* h, int scheme, double mu, const Schedule& S, int* cur,
         // queue launches for the whole run when a product has at least two
         // waves of tiles (below that the split of the last wave pays more)
         const int Tq = n_pad / 128;
-        if (!h->opt.launch_per_product && !h->opt.time_products && S.alpha.size() + h->opt.refine_squares > 0 &&
+        if (!h->opt.launch_per_product && S.alpha.size() + h->opt.refine_squares > 0 &&
             Tq * (Tq + 1) / 2 >= 2 * ms->ctas)
             return run_mixed_queue(h, scheme, mu, S, cur, red);
     }
