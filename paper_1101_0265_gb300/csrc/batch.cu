@@ -91,6 +91,8 @@ struct purify_batch {
     void* qdev_buf = nullptr;
     size_t qdev_cap = 0;
     QueueStaging last_queue;
+    size_t split_jobs_off = 0;  // the queue's f_0 splits, staged after it
+    int split_jobs = 0, split_strips = 0;
     int last_mode = -1;
     // graph of the last full run
     cudaGraphExec_t graph = nullptr;
@@ -331,9 +333,9 @@ int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueueStaging
         const int T = in->n_pad / 128;
         for (int k = 0; k < (int)in->steps.size(); ++k) {
             const int s = in->steps[k].s_in;
-            // MMA: s(s+1)/2 digit pairs of a 128 x 128 x n_pad product at 8192
-            // flop per clock; plus a fixed epilogue
-            const double cost = 0.5 * s * (s + 1) * 4.0 * in->n_pad + 3000.0;
+            // MMA cycles: s(s+1)/2 digit pairs of a 128 x 128 x n_pad product
+            // at 8192 flop per clock
+            const double cost = 0.5 * s * (s + 1) * 4.0 * in->n_pad;
             Prod p{in, k, T, T * (T + 1) / 2, cost, k ? (int)prods.size() - 1 : -1};
             if (k) prods.back().next = (int)prods.size();
             prods.push_back(p);
@@ -348,10 +350,22 @@ int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueueStaging
     for (const Prod& p : prods) items += (size_t)p.items;
     std::vector<int4> work;
     work.reserve(items);
-    // list scheduling over B->ctas simulated CTAs
+    // List scheduling over B->ctas simulated CTAs.  A CTA has two resources:
+    // its MMA pipe, free again once an item's accumulators are drained
+    // (phase 1), and its epilogue warps, busy until phase 2 ends; it claims
+    // its next item when its current MMAs end.  An instance's next product
+    // becomes ready when the last phase 2 of its current one ends.  Epilogue
+    // costs in SM cycles, measured on a stamped copy of the kernel (~5 and
+    // ~40 us at 1.9 GHz).
+    constexpr double kPhase1 = 10000.0, kPhase2 = 76000.0;
+    struct Cta {
+        double claim, mma_free, epi_free;
+    };
+    auto later = [](const std::pair<double, int>& x, const std::pair<double, int>& y) { return x.first > y.first; };
+    std::vector<Cta> ctas(std::max(1, B->ctas), Cta{0.0, 0.0, 0.0});
+    std::priority_queue<std::pair<double, int>, std::vector<std::pair<double, int>>, decltype(later)> next_cta(later);
+    for (int c = 0; c < (int)ctas.size(); ++c) next_cta.push({0.0, c});
     using TP = std::pair<double, int>;
-    std::priority_queue<double, std::vector<double>, std::greater<double>> cta;
-    for (int c = 0; c < std::max(1, B->ctas); ++c) cta.push(0.0);
     std::priority_queue<TP, std::vector<TP>, std::greater<TP>> future;  // (ready time, product)
     std::priority_queue<TP> ready;                                      // (item cost, -product)
     std::vector<int> placed(products, 0);
@@ -359,13 +373,15 @@ int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueueStaging
     for (int pi = 0; pi < products; ++pi)
         if (prods[pi].dep < 0) future.push({0.0, pi});
     while (work.size() < items) {
-        double f = cta.top();
-        cta.pop();
+        const int c = next_cta.top().second;
+        next_cta.pop();
+        Cta& C = ctas[c];
+        double f = C.claim;
         while (!future.empty() && future.top().first <= f) {
             ready.push({prods[future.top().second].cost, -future.top().second});
             future.pop();
         }
-        if (ready.empty()) {  // this CTA idles until the next product is available
+        if (ready.empty()) {  // this CTA waits until the next product is ready
             f = future.top().first;
             ready.push({prods[future.top().second].cost, -future.top().second});
             future.pop();
@@ -378,15 +394,26 @@ int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueueStaging
         while ((tj + 1) * (tj + 2) / 2 <= r) ++tj;
         const int ti = r - tj * (tj + 1) / 2;
         work.push_back(make_int4(pi, ti, tj, 0));
-        const double done = f + p.cost;
-        finish[pi] = std::max(finish[pi], done);
-        cta.push(done);
+        const double mma_start = std::max(f, C.mma_free);
+        const double mma_end = mma_start + p.cost;
+        const double p1_end = std::max(mma_end, C.epi_free) + kPhase1;
+        const double p2_end = p1_end + kPhase2;
+        C.claim = mma_end;
+        C.mma_free = p1_end;
+        C.epi_free = p2_end;
+        next_cta.push({C.claim, c});
+        finish[pi] = std::max(finish[pi], p2_end);
         if (placed[pi] == p.items) {
             ready.pop();
             if (p.next >= 0) future.push({finish[pi], p.next});
         }
     }
     return stage_queue_products(qp, work, B->host_buf, q);
+}
+
+int launch_batch_splits(purify_batch* B) {
+    return launch_split_group((const SplitJob*)((uint8_t*)B->qdev_buf + B->split_jobs_off), B->split_jobs,
+                              B->split_strips, B->stream);
 }
 
 int launch_queue(purify_batch* B, const QueueStaging& q) {
@@ -657,9 +684,25 @@ int purify_batch_run(purify_batch_t B, int mode) {
         } else {
             QueueStaging q;
             PURIFY_TRY(stage_queue(B, all, q));
-            PURIFY_TRY(ensure_qdev(B, q.end));
-            PURIFY_CUDA_TRY(cudaMemcpyAsync(B->qdev_buf, B->host_buf.data(), q.end, cudaMemcpyHostToDevice, B->stream));
+            // every instance's f_0 split as one launch: its jobs after the queue
+            const size_t jobs_off = (q.end + 255) / 256 * 256;
+            std::vector<SplitJob> jobs(all.size());
+            int strips = 0;
+            for (size_t k = 0; k < all.size(); ++k) {
+                Instance& in = *all[k];
+                PURIFY_TRY(make_split_job(in.F, in.n, in.n, in.n_pad, in.split_a, in.split_b, in.split_e, in.split_s,
+                                          in.rbits, in.Xd[0], in.red, strips, &jobs[k]));
+                strips += split_strips(in.n_pad);
+            }
+            const size_t end = jobs_off + sizeof(SplitJob) * jobs.size();
+            if (B->host_buf.size() < end) B->host_buf.resize(end);
+            std::memcpy(B->host_buf.data() + jobs_off, jobs.data(), sizeof(SplitJob) * jobs.size());
+            PURIFY_TRY(ensure_qdev(B, end));
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(B->qdev_buf, B->host_buf.data(), end, cudaMemcpyHostToDevice, B->stream));
             B->last_queue = q;
+            B->split_jobs_off = jobs_off;
+            B->split_jobs = (int)jobs.size();
+            B->split_strips = strips;
         }
         PURIFY_CUDA_TRY(cudaStreamSynchronize(B->stream));
         B->last_mode = mode;
@@ -668,13 +711,14 @@ int purify_batch_run(purify_batch_t B, int mode) {
             cudaGraph_t g = nullptr;
             PURIFY_CUDA_TRY(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal));
             int r = PURIFY_OK;
-            for (Instance* in : all)
-                if (r == PURIFY_OK) r = queue_split(B, *in);
             if (rounds_mode) {
+                for (Instance* in : all)
+                    if (r == PURIFY_OK) r = queue_split(B, *in);
                 for (auto& groups : rounds)
                     if (r == PURIFY_OK) r = launch_groups(B, groups);
-            } else if (r == PURIFY_OK) {
-                r = launch_queue(B, B->last_queue);
+            } else {
+                r = launch_batch_splits(B);
+                if (r == PURIFY_OK) r = launch_queue(B, B->last_queue);
             }
             cudaError_t e = cudaStreamEndCapture(B->stream, &g);
             if (r == PURIFY_OK && e != cudaSuccess) r = cuda_status(e, "cudaStreamEndCapture");
@@ -691,10 +735,11 @@ int purify_batch_run(purify_batch_t B, int mode) {
     if (use_graph) {
         PURIFY_CUDA_TRY(cudaGraphLaunch(B->graph, B->stream));
     } else {
-        for (Instance* in : all) PURIFY_TRY(queue_split(B, *in));
         if (rounds_mode) {
+            for (Instance* in : all) PURIFY_TRY(queue_split(B, *in));
             for (auto& groups : rounds) PURIFY_TRY(launch_groups(B, groups));
         } else {
+            PURIFY_TRY(launch_batch_splits(B));
             PURIFY_TRY(launch_queue(B, B->last_queue));
         }
     }

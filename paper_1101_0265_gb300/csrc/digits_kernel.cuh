@@ -959,7 +959,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             float bn2_0 = 0.f, bn2_1 = 0.f;  // this row's share of two 32 x 32 output blocks
             // E for a pass is copied to shared memory while the previous pass
             // computes (each lane copies and reads only its own 16-byte pieces)
-            uint4* const e_mine = e_stage + (size_t)region * s * 32 * (EW / 8) + lane * (EW / 8);
+            // (regions laid out for the kernel's S planes: in a queue launch the
+            // epilogue warps may be on items with different digit counts)
+            uint4* const e_mine = e_stage + (size_t)region * S * 32 * (EW / 8) + lane * (EW / 8);
             // row i of A's planes (paired layout, see plane_index)
             const __nv_bfloat16* const e_row = Ain + (size_t)i * 2 * n_pad;
             auto fetch_E = [&](int c_first) {

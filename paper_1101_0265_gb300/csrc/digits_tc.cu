@@ -64,82 +64,118 @@ __device__ __forceinline__ df split_entry(double x) {
     return (E >= -74 && E <= 127) ? split_double_bits(u) : split_double_slow(x);
 }
 
+// One 32 x 128 strip of the split (see split_kernel); tr accumulates the
+// diagonal's trace (float), the strip's block norms go to bnorm2 when set.
+__device__ __forceinline__ void split_strip(const double* __restrict__ F, int64_t ldf, int n, int n_pad, df a, df b,
+                                            float digit_scale, float rscale, float rinv, int s,
+                                            __nv_bfloat16* __restrict__ out, float* __restrict__ bnorm2, bool vec,
+                                            int strip, int lane, float& tr) {
+    const int nb = n_pad / 32, ns = n_pad / 128;  // nb^2 <= 2^24: 32-bit block indices
+    const int64_t total = (int64_t)n_pad * n_pad;
+    const int I = strip / ns, Jq = strip - I * ns;
+    const int j0 = Jq * 128 + lane * 4;
+    float bsum = 0.f;
+#pragma unroll 2
+    for (int r = 0; r < 32; ++r) {  // two rows' loads in flight per warp
+        const int i = I * 32 + r;
+        double x[4] = {0.0, 0.0, 0.0, 0.0};
+        if (i < n) {
+            const double* row = F + (int64_t)i * ldf + j0;
+            if (vec && j0 + 3 < n) {
+                const double2 u0 = __ldg((const double2*)row), u1 = __ldg((const double2*)row + 1);
+                x[0] = u0.x;
+                x[1] = u0.y;
+                x[2] = u1.x;
+                x[3] = u1.y;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (j0 + c < n) x[c] = __ldg(row + c);
+            }
+        }
+        df z[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = j0 + c;
+            z[c] = {0.f, 0.f};
+            if (i < n && j < n) {
+                z[c] = df_mul(a, split_entry(x[c]));
+                if (i == j) {
+                    z[c] = df_add(z[c], b);
+                    tr += z[c].h + z[c].l;
+                }
+            }
+            bsum += z[c].h * z[c].h;
+            z[c] = df_scale(z[c], digit_scale);
+        }
+        // plane p at out + plane_index(p, i, j0, n_pad): pairs 2 total apart
+        __nv_bfloat16* dst = out + (size_t)i * 2 * n_pad + ((j0 >> 5) << 6) + (j0 & 31);
+        float plane_scale = 1.f;
+        for (int p = 0; p < s; ++p) {
+            __align__(8) __nv_bfloat16 dv[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float d = round_digit(z[c].h);
+                z[c] = two_sum(__fsub_rn(z[c].h, d), z[c].l);
+                dv[c] = digit_to_bf16(d * plane_scale);
+                z[c] = df_scale(z[c], rscale);
+            }
+            *(uint2*)(dst + (size_t)(p >> 1) * 2 * total + ((p & 1) << 5)) = *(const uint2*)dv;
+            plane_scale *= rinv;
+        }
+    }
+    if (bnorm2) {
+        // lanes 8q .. 8q + 7 hold block column Jq * 4 + q
+        bsum += __shfl_xor_sync(0xffffffffu, bsum, 4);
+        bsum += __shfl_xor_sync(0xffffffffu, bsum, 2);
+        bsum += __shfl_xor_sync(0xffffffffu, bsum, 1);
+        const int J = Jq * 4 + (lane >> 3);
+        if ((lane & 7) == 0 && I <= J) bnorm2[(size_t)I * nb + J] = bsum;
+    }
+}
+
 __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ F, int64_t ldf, int n, int n_pad,
                                                     df a, df b, float digit_scale, float rscale, int s,
                                                     __nv_bfloat16* __restrict__ out, double* red,
                                                     float* __restrict__ bnorm2) {
-    const int nb = n_pad / 32, ns = n_pad / 128;  // nb^2 <= 2^24: 32-bit block indices
-    const int64_t total = (int64_t)n_pad * n_pad;
+    const int nb = n_pad / 32, ns = n_pad / 128;
     const int lane = threadIdx.x & 31;
     const int warps = gridDim.x * (blockDim.x >> 5);
     const bool vec = (ldf & 1) == 0 && ((uintptr_t)F & 15) == 0;
     const float rinv = 1.f / rscale;
     float tr = 0.f;
-    for (int strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); strip < nb * ns; strip += warps) {
-        const int I = strip / ns, Jq = strip - I * ns;
-        const int j0 = Jq * 128 + lane * 4;
-        float bsum = 0.f;
-#pragma unroll 2
-        for (int r = 0; r < 32; ++r) {  // two rows' loads in flight per warp
-            const int i = I * 32 + r;
-            double x[4] = {0.0, 0.0, 0.0, 0.0};
-            if (i < n) {
-                const double* row = F + (int64_t)i * ldf + j0;
-                if (vec && j0 + 3 < n) {
-                    const double2 u0 = __ldg((const double2*)row), u1 = __ldg((const double2*)row + 1);
-                    x[0] = u0.x;
-                    x[1] = u0.y;
-                    x[2] = u1.x;
-                    x[3] = u1.y;
-                } else {
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (j0 + c < n) x[c] = __ldg(row + c);
-                }
-            }
-            df z[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const int j = j0 + c;
-                z[c] = {0.f, 0.f};
-                if (i < n && j < n) {
-                    z[c] = df_mul(a, split_entry(x[c]));
-                    if (i == j) {
-                        z[c] = df_add(z[c], b);
-                        tr += z[c].h + z[c].l;
-                    }
-                }
-                bsum += z[c].h * z[c].h;
-                z[c] = df_scale(z[c], digit_scale);
-            }
-            // plane p at out + plane_index(p, i, j0, n_pad): pairs 2 total apart
-            __nv_bfloat16* dst = out + (size_t)i * 2 * n_pad + ((j0 >> 5) << 6) + (j0 & 31);
-            float plane_scale = 1.f;
-            for (int p = 0; p < s; ++p) {
-                __align__(8) __nv_bfloat16 dv[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float d = round_digit(z[c].h);
-                    z[c] = two_sum(__fsub_rn(z[c].h, d), z[c].l);
-                    dv[c] = digit_to_bf16(d * plane_scale);
-                    z[c] = df_scale(z[c], rscale);
-                }
-                *(uint2*)(dst + (size_t)(p >> 1) * 2 * total + ((p & 1) << 5)) = *(const uint2*)dv;
-                plane_scale *= rinv;
-            }
-        }
-        if (bnorm2) {
-            // lanes 8q .. 8q + 7 hold block column Jq * 4 + q
-            bsum += __shfl_xor_sync(0xffffffffu, bsum, 4);
-            bsum += __shfl_xor_sync(0xffffffffu, bsum, 2);
-            bsum += __shfl_xor_sync(0xffffffffu, bsum, 1);
-            const int J = Jq * 4 + (lane >> 3);
-            if ((lane & 7) == 0 && I <= J) bnorm2[(size_t)I * nb + J] = bsum;
-        }
-    }
+    for (int strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); strip < nb * ns; strip += warps)
+        split_strip(F, ldf, n, n_pad, a, b, digit_scale, rscale, rinv, s, out, bnorm2, vec, strip, lane, tr);
     if (red) {
         tr = warp_sum_f(tr);
         if (lane == 0) atomicAdd(red, (double)tr);
+    }
+}
+
+// The splits of many matrices in one launch (a batch's f_0 for every
+// instance): strip u of the launch belongs to the job with the largest
+// strip0 <= u; the warp that takes a job's first strip also clears its
+// four-double reduction slot.
+__global__ void __launch_bounds__(256) split_group_kernel(const SplitJob* __restrict__ jobs, int njobs,
+                                                          int total_strips) {
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < total_strips; u += warps) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].strip0 <= u)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const SplitJob& J = jobs[lo];
+        const int strip = u - J.strip0;
+        if (strip == 0 && J.zero4 && lane < 4) J.zero4[lane] = 0.0;
+        const bool vec = (J.ldf & 1) == 0 && ((uintptr_t)J.F & 15) == 0;
+        float tr = 0.f;
+        split_strip(J.F, J.ldf, J.n, J.n_pad, df{J.a_h, J.a_l}, df{J.b_h, J.b_l}, J.digit_scale, J.rscale,
+                    1.f / J.rscale, J.s, J.out, nullptr, vec, strip, lane, tr);
     }
 }
 
@@ -430,6 +466,42 @@ int launch_digit_queue(int smax, bool uniform, const DigitGemmParams* prm, const
     L.split_ways = 1;
     const int grid = num_items < max_ctas ? num_items : max_ctas;
     return launch_kernel(L, smax, queue_kc(smax), grid, stream, uniform);
+}
+
+int split_strips(int n_pad) { return (n_pad / 32) * (n_pad / 128); }
+
+int make_split_job(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s, int rbits,
+                   __nv_bfloat16* out, double* zero4, int strip0, SplitJob* job) {
+    if (s < 1 || s > kMaxDigitPlanes || n <= 0 || n_pad < n || n_pad % 128 || n_pad > (1 << 17) || rbits < 4 ||
+        rbits > 8 || !F || !out || ldf < n || strip0 < 0)
+        return PURIFY_ERR_INVALID_ARG;
+    const df ad = to_df(a), bd = to_df(b);
+    job->F = F;
+    job->ldf = ldf;
+    job->n = n;
+    job->n_pad = n_pad;
+    job->a_h = ad.h;
+    job->a_l = ad.l;
+    job->b_h = bd.h;
+    job->b_l = bd.l;
+    job->digit_scale = ldexpf(1.f, 8 - e);
+    job->rscale = ldexpf(1.f, rbits);
+    job->s = s;
+    job->out = out;
+    job->zero4 = zero4;
+    job->strip0 = strip0;
+    return PURIFY_OK;
+}
+
+int launch_split_group(const SplitJob* jobs, int njobs, int total_strips, cudaStream_t stream) {
+    if (njobs <= 0 || total_strips <= 0) return PURIFY_OK;
+    if (!jobs) return PURIFY_ERR_INVALID_ARG;
+    int64_t blocks = ((int64_t)total_strips + 7) / 8;  // 8 warps per CTA, one strip each
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    split_group_kernel<<<(unsigned)blocks, 256, 0, stream>>>(jobs, njobs, total_strips);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return PURIFY_OK;
 }
 
 int launch_split(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s,

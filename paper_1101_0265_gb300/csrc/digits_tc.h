@@ -129,6 +129,26 @@ int launch_digit_queue(int smax, bool uniform, const dk::DigitGemmParams* prm, c
                        int* ticket, const int4* work, int num_items, float2* scratch, int max_ctas, int* err,
                        cudaStream_t stream, long long wait_cycles);
 
+// Many splits in one launch (see launch_split): a job per matrix, its strips
+// (32 x 128 pieces of the padded matrix, split_strips of them) numbered from
+// strip0 in the launch; zero4 (4 doubles, may be null) is cleared.  The jobs
+// array is in device memory; jobs are in increasing strip0.
+struct SplitJob {
+    const double* F;
+    long long ldf;
+    int n, n_pad;
+    float a_h, a_l, b_h, b_l;  // a and b as float pairs
+    float digit_scale, rscale;
+    int s;
+    __nv_bfloat16* out;
+    double* zero4;
+    int strip0;
+};
+int split_strips(int n_pad);
+int make_split_job(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s, int rbits,
+                   __nv_bfloat16* out, double* zero4, int strip0, SplitJob* job);
+int launch_split_group(const SplitJob* jobs, int njobs, int total_strips, cudaStream_t stream);
+
 // out planes of a F + b I (i, j < n; zero padding up to n_pad), exponent e,
 // s digits.  red[0] += trace (float accuracy) when red is not null;
 // bnorm2[I * (n_pad / 32) + J] = ||block (I, J)||_F^2 (float) for I <= J when

@@ -151,3 +151,28 @@ def test_queue_many_products_per_cta(P):
         for k, i in keep.items():
             assert np.array_equal(B.density(i), alone[k]), (use_graph, specs[k])
     B.close()
+
+
+def test_queue_equals_rounds_on_a_mixed_batch(P):
+    # 96 instances of the batch workload (n log-uniform in [64, 2048], gaps
+    # log-uniform in [1e-3, 1e-1]): products of 5 and 6 digits share the
+    # queue launch and its CTAs, so an epilogue warp can be on an item of one
+    # digit count while another warp of the CTA is on the other; every
+    # density must still equal the per-round engine's, bit for bit
+    dev = torch.device("cuda:0")
+    specs = I.batch_specs(96)
+    B = P.Batch()
+    ids = []
+    for sp in specs:
+        F, h = I.dense_hamiltonian_device(sp, dev)
+        ids.append(B.add(F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme="TC_SF", tol=1e-9, mu=0.0))
+        del F
+    B.run(use_graph=False, rounds=True)
+    ref = [B.density(i) for i in ids]
+    digits = {B.stats(i)["digit_max"] for i in ids}
+    assert len(digits) > 1, digits
+    for use_graph in (False, True, True):
+        B.run(use_graph=use_graph, rounds=False)
+        bad = [k for k, i in enumerate(ids) if not np.array_equal(B.density(i), ref[k])]
+        assert not bad, (use_graph, bad[:8])
+    B.close()
