@@ -179,7 +179,7 @@ def run_serve(P, dev, stream, rate, count, budget_gb=64.0, tol=1e-9):
     from collections import deque
     from paper_1101_0265_gb300 import inputs as I
     specs = I.serve_specs(rate, count)
-    reqs = [I.dense_hamiltonian_device(sp, dev) for sp in specs]   # untimed
+    reqs = [I.reflected_hamiltonian_device(sp, dev) for sp in specs]   # untimed, O(n^2) each
     torch.cuda.synchronize(dev)
     B = P.Batch(device=dev.index, stream=stream.cuda_stream)
     budget = budget_gb * 2 ** 30

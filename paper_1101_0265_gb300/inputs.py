@@ -275,6 +275,35 @@ def instance_hamiltonian(spec: InstanceSpec) -> Hamiltonian:
                              instance=spec.instance)
 
 
+def reflected_hamiltonian_device(spec: InstanceSpec, device="cuda", reflections: int = 3):
+    """A cheaper dense recipe for long request streams: F = H_k .. H_1
+    diag(lambda) H_1 .. H_k with k random Householder reflections H = I - 2 v
+    v^T (|v| = 1, v from a seeded torch generator), each applied to both
+    sides in O(n^2).  The spectrum is exactly that of the dense recipe (the
+    same numpy generator), F is dense and symmetric; the eigenvectors are not
+    Haar-distributed, which purification does not depend on.  Returns (F as a
+    float64 CUDA tensor, Hamiltonian metadata without F or Q)."""
+    import torch
+    rng = rng_for(spec.config, spec.instance)
+    lam = gapped_spectrum(spec.n, spec.nocc, spec.gap, rng)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed_for(spec.config, spec.instance) & ((1 << 63) - 1))
+    F = torch.diag(torch.from_numpy(lam).to(device))
+    for _ in range(reflections):
+        v = torch.randn(spec.n, generator=g, dtype=torch.float64, device=device)
+        v = v / torch.linalg.vector_norm(v)
+        w = F @ v                       # H F H = F - 2 v w^T - 2 w v^T + 4 (v^T w) v v^T
+        c = torch.dot(v, w)
+        F = F - 2.0 * torch.outer(v, w) - 2.0 * torch.outer(w, v) + 4.0 * c * torch.outer(v, v)
+    F = 0.5 * (F + F.T)
+    meta = Hamiltonian(F=None, n=spec.n, nocc=spec.nocc, mu=0.0, lmin=float(lam[0]),
+                       lmax=float(lam[-1]), homo=float(lam[spec.nocc - 1]),
+                       lumo=float(lam[spec.nocc]), lam=lam, Q=None,
+                       meta={"kind": "reflected-device", "gap": spec.gap, "scheme": spec.scheme,
+                             "reflections": reflections})
+    return F.contiguous(), meta
+
+
 def dense_hamiltonian_device(spec: InstanceSpec, device="cuda", keep_q: bool = False):
     """The dense recipe built on a GPU with torch (Haar Q from a seeded torch
     generator, spectrum from the numpy generator as above).  Returns

@@ -99,3 +99,21 @@ def test_batch_and_serve_distributions():
     assert 0.4 < schemes.count("TC_SF") / len(schemes) < 0.6
     ns = np.array([s.n for s in sv])
     assert ns.min() >= 128 and ns.max() <= 8192
+
+
+def test_reflected_recipe_keeps_the_spectrum():
+    # the serving stream's O(n^2) recipe: dense, symmetric, exactly the dense
+    # recipe's spectrum, reproducible per instance
+    torch = pytest.importorskip("torch")
+    sp = I.serve_specs(100.0, 3)[1]
+    sp = I.InstanceSpec(n=96, nocc=40, gap=sp.gap, scheme=sp.scheme, arrival=0.0, instance=sp.instance,
+                        config=sp.config)
+    F, h = I.reflected_hamiltonian_device(sp, "cpu")
+    F2, _ = I.reflected_hamiltonian_device(sp, "cpu")
+    A = F.numpy()
+    assert np.array_equal(A, F2.numpy())
+    assert np.array_equal(A, A.T)
+    ev = np.linalg.eigvalsh(A)
+    assert np.max(np.abs(ev - np.sort(h.lam))) <= 1e-12
+    assert h.homo == h.lam[h.nocc - 1] and h.lumo == h.lam[h.nocc]
+    assert np.count_nonzero(np.abs(A - np.diag(np.diag(A))) > 1e-14) > 0.9 * 96 * 95
