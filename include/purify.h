@@ -392,6 +392,16 @@ int purify_batch_add(purify_batch_t b, const double* F, int64_t n, int64_t ld, i
  * completed in this round. */
 int purify_batch_step(purify_batch_t b, int* active, int* finished);
 
+/* Continuous batching with fewer host round trips: queue f_0 for instances
+ * added since the last call, then advance every active instance by up to
+ * max_products products (the rest of its schedule if fewer remain) in one
+ * queue launch of the product kernel, in which an instance's products run in
+ * order and different instances overlap; synchronise.  *active and *finished
+ * as for purify_batch_step.  Densities equal those of a run alone, bit for
+ * bit.  A CUDA graph captured by purify_batch_run is dropped (its staging is
+ * reused).  INVALID_ARG for max_products < 1. */
+int purify_batch_advance(purify_batch_t b, int max_products, int* active, int* finished);
+
 /* Run every instance of the batch from f_0 to completion.
  *
  * mode = PURIFY_BATCH_QUEUE (0): the f_0 splits, then ONE persistent launch of

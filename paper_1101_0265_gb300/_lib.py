@@ -41,7 +41,7 @@ EXPORTED = (
     "purify_k_symm_product_f64", "purify_k_step_f64", "purify_k_gershgorin_f64",
     "purify_k_lanczos_f64", "purify_k_digit_product_f64", "purify_k_gershgorin_f64_noalloc",
     "purify_batch_footprint", "purify_batch_create", "purify_batch_destroy", "purify_batch_add",
-    "purify_batch_step", "purify_batch_run", "purify_batch_status", "purify_batch_get_density",
+    "purify_batch_step", "purify_batch_advance", "purify_batch_run", "purify_batch_status", "purify_batch_get_density",
     "purify_batch_stats", "purify_batch_release", "purify_batch_bytes_in_use",
 )
 
@@ -128,6 +128,7 @@ def load(path: str = LIB_PATH):
         "purify_batch_add": (ip, [vp, vp, i64, i64, i64, dbl, C.POINTER(Bounds), ip, dbl, ip,
                                   C.POINTER(C.c_int)]),
         "purify_batch_step": (ip, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "purify_batch_advance": (ip, [vp, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "purify_batch_run": (ip, [vp, ip]),
         "purify_batch_status": (ip, [vp, ip]),
         "purify_batch_get_density": (ip, [vp, ip, vp, i64]),
@@ -501,6 +502,14 @@ class Batch:
     def step(self):
         a, f = C.c_int(0), C.c_int(0)
         _check(self._lib.purify_batch_step(self._h, C.byref(a), C.byref(f)), "purify_batch_step")
+        return a.value, f.value
+
+    def advance(self, max_products: int = 4):
+        """Advance every active instance by up to max_products products in one
+        queue launch; returns (active, finished) like step()."""
+        a, f = C.c_int(0), C.c_int(0)
+        _check(self._lib.purify_batch_advance(self._h, int(max_products), C.byref(a), C.byref(f)),
+               "purify_batch_advance")
         return a.value, f.value
 
     def run(self, use_graph: bool = True, rounds: bool = False):

@@ -314,7 +314,13 @@ int launch_groups(purify_batch* B, const std::vector<GroupPlan>& groups) {
 // one has finished, and among available products the one with the longest
 // items goes first.  stage_queue_products checks that no item precedes one
 // it waits for.
-int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueueStaging& q) {
+// Steps [k0, k1) of one instance, for a queue launch.
+struct StepRange {
+    Instance* in;
+    int k0, k1;
+};
+
+int stage_queue(purify_batch* B, const std::vector<StepRange>& ranges, QueueStaging& q) {
     // products: instance-major; an instance's product waits for every item
     // of its previous one (which reads the buffer it overwrites, and wrote
     // what it reads)
@@ -329,15 +335,16 @@ int stage_queue(purify_batch* B, const std::vector<Instance*>& all, QueueStaging
     };
     std::vector<Prod> prods;
     std::vector<QueueProduct> qp;
-    for (Instance* in : all) {
+    for (const StepRange& rg : ranges) {
+        Instance* in = rg.in;
         const int T = in->n_pad / 128;
-        for (int k = 0; k < (int)in->steps.size(); ++k) {
+        for (int k = rg.k0; k < rg.k1; ++k) {
             const int s = in->steps[k].s_in;
             // MMA cycles: s(s+1)/2 digit pairs of a 128 x 128 x n_pad product
             // at 8192 flop per clock
             const double cost = 0.5 * s * (s + 1) * 4.0 * in->n_pad;
-            Prod p{in, k, T, T * (T + 1) / 2, cost, k ? (int)prods.size() - 1 : -1};
-            if (k) prods.back().next = (int)prods.size();
+            Prod p{in, k, T, T * (T + 1) / 2, cost, k > rg.k0 ? (int)prods.size() - 1 : -1};
+            if (k > rg.k0) prods.back().next = (int)prods.size();
             prods.push_back(p);
             QueueProduct x;
             x.st = in->steps[k];
@@ -626,6 +633,55 @@ int purify_batch_step(purify_batch_t B, int* active_out, int* finished_out) {
     return join_streams(B->user_stream, B->stream, B->join_ev);
 }
 
+int ensure_qdev(purify_batch* B, size_t bytes);
+
+// Continuous batching with fewer host round trips: one queue launch advances
+// every active instance by up to max_products products (an instance's
+// products chained on the device, instances independent), then
+// synchronises.  Instances added since the last call get their f_0 split
+// first.
+int purify_batch_advance(purify_batch_t B, int max_products, int* active_out, int* finished_out) {
+    if (!B || max_products < 1) return PURIFY_ERR_INVALID_ARG;
+    PURIFY_CUDA_TRY(cudaSetDevice(B->device));
+    PURIFY_TRY(join_streams(B->stream, B->user_stream, B->join_ev));
+    std::vector<StepRange> ranges;
+    for (Instance* in : B->inst) {
+        if (!in || in->state >= 2 || in->state < 0) continue;
+        if (in->state == 0) {
+            in->k = 0;
+            PURIFY_TRY(queue_split(B, *in));
+            in->state = 1;
+        }
+        ranges.push_back({in, in->k, std::min((int)in->steps.size(), in->k + max_products)});
+    }
+    int finished = 0;
+    if (!ranges.empty()) {
+        if (B->graph) {  // the staging buffer a captured run reads is about to change
+            PURIFY_CUDA_TRY(cudaStreamSynchronize(B->stream));
+            cudaGraphExecDestroy(B->graph);
+            B->graph = nullptr;
+            B->graph_ids.clear();
+        }
+        QueueStaging q;
+        PURIFY_TRY(stage_queue(B, ranges, q));
+        PURIFY_TRY(ensure_qdev(B, q.end));
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(B->qdev_buf, B->host_buf.data(), q.end, cudaMemcpyHostToDevice, B->stream));
+        PURIFY_TRY(launch_staged_queue(q, B->qdev_buf, B->scratch, B->ctas, B->err, B->stream,
+                                       1000ll * B->opt.wait_kcycles));
+        PURIFY_TRY(check_err(B));
+        for (const StepRange& rg : ranges) {
+            rg.in->k = rg.k1;
+            if (rg.in->k == (int)rg.in->steps.size()) {
+                finish_instance(*rg.in);
+                ++finished;
+            }
+        }
+    }
+    if (active_out) *active_out = (int)ranges.size() - finished;
+    if (finished_out) *finished_out = finished;
+    return join_streams(B->user_stream, B->stream, B->join_ev);
+}
+
 int ensure_qdev(purify_batch* B, size_t bytes) {
     if (bytes <= B->qdev_cap) return PURIFY_OK;
     PURIFY_CUDA_TRY(cudaStreamSynchronize(B->stream));
@@ -683,7 +739,9 @@ int purify_batch_run(purify_batch_t B, int mode) {
             PURIFY_CUDA_TRY(cudaMemcpyAsync(B->dev_buf, B->host_buf.data(), off, cudaMemcpyHostToDevice, B->stream));
         } else {
             QueueStaging q;
-            PURIFY_TRY(stage_queue(B, all, q));
+            std::vector<StepRange> ranges;
+            for (Instance* in : all) ranges.push_back({in, 0, (int)in->steps.size()});
+            PURIFY_TRY(stage_queue(B, ranges, q));
             // every instance's f_0 split as one launch: its jobs after the queue
             const size_t jobs_off = (q.end + 255) / 256 * 256;
             std::vector<SplitJob> jobs(all.size());

@@ -106,6 +106,34 @@ def test_continuous_batching_equals_alone(P):
     B.close()
 
 
+@pytest.mark.parametrize("k", [1, 3])
+def test_continuous_batching_with_queue_advance_equals_alone(P, k):
+    # requests arrive while others run; every call advances each active one
+    # by up to k products in one queue launch; results are those alone
+    hs = _hams()
+    tol = 1e-9
+    B = P.Batch()
+    pending = list(range(len(hs)))
+    live = {}
+    calls = 0
+    while pending or live:
+        for _ in range(min(3, len(pending))):
+            j = pending.pop(0)
+            h = hs[j]
+            live[j] = B.add(h.F, h.nocc, h.lmin, h.lmax, h.homo, h.lumo, scheme=SPECS[j][3], tol=tol, mu=0.0)
+        active, finished = B.advance(k)
+        calls += 1
+        for j, i in list(live.items()):
+            if B.done(i):
+                Da, _ = _alone(P, hs[j], SPECS[j][3], tol)
+                assert np.array_equal(B.density(i), Da), SPECS[j]
+                B.release(i)
+                del live[j]
+        assert calls < 500
+    assert B.bytes_in_use() == 0
+    B.close()
+
+
 def test_batch_device_inputs_and_footprint(P):
     h = I.dense_hamiltonian(300, 100, 0.05, config=61)
     B = P.Batch()
