@@ -28,13 +28,16 @@ namespace {
 // x = h + l with |x - (h + l)| <= 2^-46 |x|, for 2^-74 <= |x| < 2^128 (both
 // floats normal; the caller handles other magnitudes); integer operations
 // only.
-__device__ __forceinline__ df split_double_bits(unsigned long long u) {
-    const unsigned int sign = (unsigned int)(u >> 32) & 0x80000000u;
-    const int E = (int)((u >> 52) & 0x7FF) - 1023;                  // x = m 2^(E - 52)
-    const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const float h = __uint_as_float(sign | (unsigned int)(E + 127) << 23 | ((unsigned int)(m >> 29) & 0x7FFFFFu));
+__device__ __forceinline__ df split_double_bits(unsigned int hi, unsigned int lo) {
+    // 32-bit halves only: 64-bit integer operations would occupy the float64
+    // pipe, which this pass otherwise leaves idle
+    const unsigned int sign = hi & 0x80000000u;
+    const int E = (int)((hi >> 20) & 0x7FFu) - 1023;                 // x = m 2^(E - 52)
+    // the 24 leading mantissa bits (with the hidden one): m >> 29
+    const unsigned int top = ((hi & 0xFFFFFu) | 0x100000u) << 3 | (lo >> 29);
+    const float h = __uint_as_float(sign | (unsigned int)(E + 127) << 23 | (top & 0x7FFFFFu));
     // the 29 low mantissa bits times 2^(E - 52): the top 24 of them, normalised
-    const unsigned int lo29 = (unsigned int)(m & 0x1FFFFFFFu);
+    const unsigned int lo29 = lo & 0x1FFFFFFFu;
     unsigned int lbits = 0;
     if (lo29) {
         const int bits = 32 - __clz(lo29);
@@ -57,11 +60,11 @@ __device__ __noinline__ df split_double_slow(double x) {
 // when bnorm2 is not null, ||.||_F^2 of the strip's four 32 x 32 blocks
 // (float, in a fixed order) for blocks I <= J.
 __device__ __forceinline__ df split_entry(double x) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
-    const int E = (int)((u >> 52) & 0x7FF) - 1023;
+    const unsigned int hi = (unsigned int)__double2hiint(x), lo = (unsigned int)__double2loint(x);
+    const int E = (int)((hi >> 20) & 0x7FFu) - 1023;
     // zeros (most of a sparse F) and normal magnitudes stay off the float64 pipe
-    if ((u << 1) == 0) return {0.f, 0.f};
-    return (E >= -74 && E <= 127) ? split_double_bits(u) : split_double_slow(x);
+    if (((hi << 1) | lo) == 0u) return {0.f, 0.f};
+    return (E >= -74 && E <= 127) ? split_double_bits(hi, lo) : split_double_slow(x);
 }
 
 // One 32 x 128 strip of the split (see split_kernel); tr accumulates the
@@ -116,7 +119,9 @@ __device__ __forceinline__ void split_strip(const double* __restrict__ F, int64_
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
                 const float d = round_digit(z[c].h);
-                z[c] = two_sum(__fsub_rn(z[c].h, d), z[c].l);
+                // z.h - d is exact and either 0 or at least ulp(z.h) >= 2 |z.l|,
+                // so the fast two-sum is exact (the same bits as two_sum)
+                z[c] = fast_two_sum(__fsub_rn(z[c].h, d), z[c].l);
                 dv[c] = digit_to_bf16(d * plane_scale);
                 z[c] = df_scale(z[c], rscale);
             }
