@@ -796,7 +796,6 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             item_of(L, t, g, ti, tj, slot, part);
             const DigitGemmParams& P = params_of<Q>(L, g);
             const int s = QRT ? P.s_in : S;  // this item's digit planes
-            const size_t plane = (size_t)P.n_pad * P.n_pad;
             bool ready = mbar_wait_for(smem_u32(tmem_full), (uint32_t)(lt & 1), wait);
             if (!ready) {
                 atomicOr(L.err, ERR_EPI_WAIT);
@@ -962,17 +961,24 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             // (regions laid out for the kernel's S planes: in a queue launch the
             // epilogue warps may be on items with different digit counts)
             uint4* const e_mine = e_stage + (size_t)region * S * 32 * (EW / 8) + lane * (EW / 8);
+            // Addresses: 64-bit products once per item (or per pass), 32-bit
+            // offsets inside (64-bit integer operations run on the float64 pipe).
+            const int two_np = 2 * n_pad;                    // one row of a plane pair
+            const size_t pair_stride = (size_t)two_np * n_pad;  // one plane pair
             // row i of A's planes (paired layout, see plane_index)
-            const __nv_bfloat16* const e_row = Ain + (size_t)i * 2 * n_pad;
+            const __nv_bfloat16* const e_row = Ain + (size_t)i * two_np;
             auto fetch_E = [&](int c_first) {
+                const __nv_bfloat16* ep = e_row;
 #pragma unroll
-                for (int p = 0; p < s; ++p)
+                for (int p = 0; p < s; ++p) {
 #pragma unroll
                     for (int q = 0; q < EW / 8; ++q) {
                         const int j = tj * TILE + c_first + 8 * q;
                         cp_async16(smem_u32(e_mine + p * 32 * (EW / 8) + q),
-                                   e_row + (size_t)(p >> 1) * 2 * plane + ((j >> 5) << 6) + ((p & 1) << 5) + (j & 31));
+                                   ep + (((j >> 5) << 6) + ((p & 1) << 5) + (j & 31)));
                     }
+                    if (p & 1) ep += pair_stride;
+                }
                 cp_async_commit();
             };
             if (use_E) fetch_E(col0);
@@ -1059,13 +1065,15 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 }
                 // float64 output (n x n): row segment and its mirror column
                 if (out64 && i < n) {
+                    double* const o_row = out64 + (size_t)i * n;
+                    double* const o_col = out64 + (size_t)jb * n + i;
 #pragma unroll
                     for (int c = 0; c < EW; ++c) {
                         const int j = jb + c;
                         if (j < n && (!diag_tile || i <= j)) {
                             const double v = (double)Ov[c].h + (double)Ov[c].l;
-                            out64[(size_t)i * n + j] = v;
-                            if (i != j) out64[(size_t)j * n + i] = v;
+                            o_row[j] = v;
+                            if (i != j) o_col[c * n] = v;
                         }
                     }
                 }
@@ -1076,6 +1084,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     for (int c = 0; c < EW; ++c) z[c] = df_scale(Ov[c], out_digit_scale);
                     float plane_scale = 1.f;
                     const float rs = out_rscale, rinv = 1.f / out_rscale;
+                    // plane pair 0's row segment (i, jb ..) and mirror column base
+                    __nv_bfloat16* seg0 = outp + (size_t)i * two_np + (((jb >> 5) << 6) + (jb & 31));
+                    __nv_bfloat16* col0p = outp + (size_t)jb * two_np + (((i >> 5) << 6) + (i & 31));
 #pragma unroll 1
                     for (int p = 0; p < s_out; ++p) {
                         __align__(16) __nv_bfloat16 dv[EW];
@@ -1089,12 +1100,11 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                         }
                         plane_scale *= rinv;
                         // plane p in the paired layout (see plane_index): row r,
-                        // column j at dst + r 2 n_pad + (j / 32) 64 + j % 32
-                        __nv_bfloat16* dst = outp + (size_t)(p >> 1) * 2 * plane + ((p & 1) << 5);
-                        // the row segment (i, jb ..) and its mirror column; in a
+                        // column j at pair base + r 2 n_pad + (j / 32) 64 + (p % 2) 32 + j % 32.
+                        // The row segment (i, jb ..) and its mirror column; in a
                         // diagonal tile only j >= i is written here (j < i is
                         // the mirror of another row's element)
-                        __nv_bfloat16* const seg = dst + (size_t)i * 2 * n_pad + ((jb >> 5) << 6) + (jb & 31);
+                        __nv_bfloat16* const seg = seg0 + ((p & 1) << 5);
                         if (!diag_tile || jb >= i) {
                             uint4* row = (uint4*)seg;
 #pragma unroll
@@ -1104,14 +1114,18 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                             for (int c = 0; c < EW; ++c)
                                 if (jb + c >= i) seg[c] = dv[c];
                         }
-                        __nv_bfloat16* const col = dst + ((i >> 5) << 6) + (i & 31);
+                        __nv_bfloat16* const col = col0p + ((p & 1) << 5);
                         if (!diag_tile) {
 #pragma unroll
-                            for (int c = 0; c < EW; ++c) col[(size_t)(jb + c) * 2 * n_pad] = dv[c];
+                            for (int c = 0; c < EW; ++c) col[c * two_np] = dv[c];
                         } else if (jb + EW > i + 1) {
 #pragma unroll
                             for (int c = 0; c < EW; ++c)
-                                if (jb + c > i) col[(size_t)(jb + c) * 2 * n_pad] = dv[c];
+                                if (jb + c > i) col[c * two_np] = dv[c];
+                        }
+                        if (p & 1) {
+                            seg0 += pair_stride;
+                            col0p += pair_stride;
                         }
                     }
                 }
