@@ -29,7 +29,9 @@ __device__ __forceinline__ double warp_sum(double v) {
 // |x| by clearing the sign bit (an integer operation: GB300's float64 pipe is
 // the bound of this pass, and it then carries only the additions).
 __device__ __forceinline__ double abs_bits(double x) {
-    return __longlong_as_double(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll);
+    // the sign bit of the high 32-bit half (64-bit integer operations would
+    // run on the float64 pipe too)
+    return __hiloint2double(__double2hiint(x) & 0x7FFFFFFF, __double2loint(x));
 }
 
 // Per-CTA partial (min lo, max hi) of the Gershgorin interval.
@@ -37,20 +39,24 @@ __global__ void __launch_bounds__(256)
 gershgorin_rows_kernel(const double* __restrict__ F, int64_t n, int64_t ld, double* __restrict__ part) {
     __shared__ double slo[ROWS_PER_CTA], shi[ROWS_PER_CTA];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * ROWS_PER_CTA + warp;
+    // 32-bit row and column indices (any n whose n x n matrix fits in memory
+    // is below 2^31): 64-bit integer arithmetic
+    // would share the float64 pipe that bounds this pass
+    const int nn = (int)n;
+    const int i = (int)blockIdx.x * ROWS_PER_CTA + warp;
     double lo = INFINITY, hi = -INFINITY;
-    if (i < n) {
+    if (i < nn) {
         // four independent partial sums per lane keep the float64 pipe fed
-        const double* row = F + i * ld;
+        const double* row = F + (int64_t)i * ld;
         double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
-        int64_t j = lane;
-        for (; j + 96 < n; j += 128) {  // the disc radius leaves out the diagonal
+        int j = lane;
+        for (; j + 96 < nn; j += 128) {  // the disc radius leaves out the diagonal
             r0 += (j == i) ? 0.0 : abs_bits(row[j]);
             r1 += (j + 32 == i) ? 0.0 : abs_bits(row[j + 32]);
             r2 += (j + 64 == i) ? 0.0 : abs_bits(row[j + 64]);
             r3 += (j + 96 == i) ? 0.0 : abs_bits(row[j + 96]);
         }
-        for (; j < n; j += 32) r0 += (j == i) ? 0.0 : abs_bits(row[j]);
+        for (; j < nn; j += 32) r0 += (j == i) ? 0.0 : abs_bits(row[j]);
         const double r = warp_sum((r0 + r1) + (r2 + r3));
         const double d = row[i];
         lo = d - r;
@@ -173,21 +179,24 @@ lanczos_matvec_kernel(const double* __restrict__ F, int64_t n, const double* __r
                       const double* __restrict__ vprev, double* __restrict__ w,
                       const double* bsq_prev, double* pa) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * LZ_ROWS + warp;
+    // 32-bit indices (n below 2^31): 64-bit integer arithmetic would share the
+    // float64 pipe that bounds this pass
+    const int nn = (int)n;
+    const int i = (int)blockIdx.x * LZ_ROWS + warp;
     __shared__ double sdot[LZ_ROWS];
     double dot = 0.0;
-    if (i < n) {
+    if (i < nn) {
         // four independent chains per lane keep the float64 pipe fed
-        const double* row = F + i * n;
+        const double* row = F + (int64_t)i * nn;
         double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-        int64_t j = lane;
-        for (; j + 96 < n; j += 128) {
+        int j = lane;
+        for (; j + 96 < nn; j += 128) {
             s0 = fma(row[j], v[j], s0);
             s1 = fma(row[j + 32], v[j + 32], s1);
             s2 = fma(row[j + 64], v[j + 64], s2);
             s3 = fma(row[j + 96], v[j + 96], s3);
         }
-        for (; j < n; j += 32) s0 = fma(row[j], v[j], s0);
+        for (; j < nn; j += 32) s0 = fma(row[j], v[j], s0);
         const double s = warp_sum((s0 + s1) + (s2 + s3));
         const double bprev = bsq_prev ? sqrt(*bsq_prev) : 0.0;
         const double wi = s - bprev * vprev[i];
