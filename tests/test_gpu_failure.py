@@ -73,3 +73,26 @@ def test_timeout_in_a_batch(P, rounds):
         ref, _ = O.purify(h.F, "TC_SF", h.lmin, h.lmax, mu=0.0, homo=h.homo, lumo=h.lumo, tol=1e-10)
         assert np.max(np.abs(B.density(i) - ref)) <= 5e-8
     B.close()
+
+
+@pytest.mark.parametrize("scheme", ["TC_SF", "FIXED_MU_SF"])
+def test_short_waits_in_a_queue_launch_run(P, scheme):
+    # n = 3200 runs as queue launches (consecutive products overlapping, items
+    # waiting on the device for the row panels they read): with 1000-cycle
+    # waits the dependency and hand-off waits give up, the call returns
+    # PURIFY_ERR_DEVICE_TIMEOUT, the context stays usable, and the same
+    # handle with the default bound matches the closed form
+    h = I.dense_hamiltonian(3200, 1500, 0.05, config=84)
+    pur = P.Purifier(precision="mixed", wait_kcycles=1)
+    pur.set_hamiltonian(h.F, nocc=h.nocc, mu=0.0, lmin=h.lmin, lmax=h.lmax, homo=h.homo, lumo=h.lumo)
+    code = pur.run(scheme, 1e-10, 200, check=False)
+    assert code == P.ERR_DEVICE_TIMEOUT, P.strerror(code)
+    flag = pur.stats()["device_flag"]
+    assert flag and not flag & PLAN, flag
+    torch.cuda.synchronize()
+    pur.set_options(wait_kcycles=0)
+    assert pur.run(scheme, 1e-10, 200) == P.OK
+    assert pur.stats()["device_flag"] == 0
+    err = float(np.max(np.abs(pur.density() - O.density_closed_form(h.Q, h.lam, 0.0))))
+    pur.close()
+    assert err <= 1e-6, err
