@@ -261,6 +261,7 @@ def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsi
             nb = lat.n // 32
             r["nnz_blocks"] = h
             r["final_fill"] = h[-1] / (nb * (nb + 1) / 2)
+            r["plane_pool_mib"] = st["plane_pool_mib"]
         return r
 
     lat = I.lattice_hamiltonian(L)
@@ -297,8 +298,8 @@ def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsi
         sweep.append({"L": Ls, "n": lt.n, "seconds": r["seconds"], "iterations": r["iterations"],
                       "seconds_per_step": r["seconds"] / max(1, r["iterations"]),
                       "kept_blocks_per_block_row": 2 * kept / nb, "final_fill": r["final_fill"],
-                      "kept_block_bytes_per_plane": kept * 2 * 32 * 32 * 2,
-                      "dense_plane_bytes": n_pad * n_pad * 2, "trace_err": r["trace_err"]})
+                      "plane_pool_mib": r["plane_pool_mib"],
+                      "dense_planes_mib": 2 * 6 * n_pad * n_pad * 2 / 2**20, "trace_err": r["trace_err"]})
     for pur in pool.values():
         pur.close()
     torch.cuda.empty_cache()
@@ -306,9 +307,9 @@ def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsi
                         f"32x32 blocks, tol {tol:g}",
             "n": lat.n, "C3": c3, "equal_budget": eq,
             "n_sweep": {"onsite": sweep_onsite, "tau": tau, "scheme": "TC_SF block-sparse", "runs": sweep,
-                        "note": "kept_block_bytes_per_plane is what the kept blocks of the last iterate take "
-                                "(both triangles); the digit planes are allocated dense (dense_plane_bytes "
-                                "per plane)"}}
+                        "note": "plane_pool_mib: peak of the two block pools that hold the iterates' digit "
+                                "planes (12 KB per kept 32x32 block, both triangles); dense_planes_mib: two "
+                                "dense 6-plane buffers at the same size"}}
 
 
 def peaks():

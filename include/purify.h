@@ -203,7 +203,9 @@ typedef struct purify_stats_t {
                                    bits 1, 2, 4, 16: a TMA-producer, MMA, epilogue or
                                    work-claim wait gave up; bit 8: a tile's k-chunk
                                    count and bitmask disagreed)                         */
-    int reserved[2];
+    int plane_pool_mib;         /* block_sparse: peak MiB of the pooled digit planes of
+                                   the iterates (both pools; 0 otherwise)                */
+    int reserved;
     double product_seconds;     /* summed event time of the product launches
                                    (time_products = 1; else NaN)                         */
 } purify_stats_t;

@@ -70,7 +70,7 @@ class Stats(C.Structure):
                 ("useful_flops", C.c_double), ("tensor_flops", C.c_double),
                 ("digit_max", C.c_int), ("kernel_launches", C.c_int),
                 ("product_launches", C.c_int), ("nnz_blocks", C.c_int), ("digit_kc", C.c_int),
-                ("device_flag", C.c_int), ("reserved", C.c_int * 2),
+                ("device_flag", C.c_int), ("plane_pool_mib", C.c_int), ("reserved", C.c_int),
                 ("product_seconds", C.c_double)]
 
     def as_dict(self) -> dict:

@@ -312,7 +312,22 @@ struct DigitGemmParams {
     // none), and the offset of this product's counters in DigitLaunch::qcnt
     // (tiles_per_row row-panel counts, then the total).  Unused elsewhere.
     int q_depA, q_depB, q_war0, q_war1, q_cnt;
+    // pooled planes (block-sparse runs, QM = 3): A, B and the output as pools
+    // of 32 x 32 block slots (pool_index), found through nb x nb slot tables
+    // (slot 0: the shared zero block; an output block with slot 0 is not
+    // stored); maps[0] and maps[1] are then tensor maps over A's and B's
+    // pools (make_pool_map).  Null elsewhere.
+    const int* a_idx;
+    const int* b_idx;
+    const int* out_idx;
 };
+
+// Element offset of (plane p, row r, column c) of the 32 x 32 block in pool
+// slot k: a slot holds plane pairs 0..2, each 32 rows of 64 elements (the two
+// planes' 32 columns side by side, as in the dense paired layout).
+__host__ __device__ inline size_t pool_index(int k, int p, int r, int c) {
+    return ((size_t)(k * 3 + (p >> 1)) * 32 + r) * 64 + ((p & 1) << 5) + c;
+}
 
 // Products per grouped launch, whose tensor maps and parameters travel as
 // kernel parameters (grid constants).  Queue launches read theirs from
@@ -550,8 +565,9 @@ __device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, lon
 // about 4 % of a product).
 template <int KC, int S, int QM>
 __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ DigitLaunch L) {
-    constexpr bool Q = QM != 0;     // queue launch
-    constexpr bool QRT = QM == 1;   // digit counts read at run time
+    constexpr bool Q = QM == 1 || QM == 2;  // queue launch
+    constexpr bool QRT = QM == 1;           // digit counts read at run time
+    constexpr bool POOL = QM == 3;          // pooled planes (block-sparse runs)
     static_assert(KC == 32, "digit planes are stored for 32-wide k-chunks");
     constexpr int NP = plane_pairs(S);           // plane pairs of one operand per stage
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -714,8 +730,28 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     const uint32_t fb = smem_u32(&full_bar[st]);
                     uint8_t* sa = base + (size_t)st * stage_bytes;
                     mbar_arrive_expect_tx(fb, (uint32_t)(2 * plane_pairs(s_it) * PAIR_BYTES));
-                    tma_load_3d(smem_u32(sa), mA, fb, kc * 64, ti * TILE, 0);
-                    tma_load_3d(smem_u32(sa + NP * PAIR_BYTES), mB, fb, kc * 64, tj * TILE, 0);
+                    if constexpr (POOL) {
+                        // the panels' four 32-row blocks of k-block kc, one box per
+                        // block and plane pair (absent blocks: the zero slot)
+                        int ka[4], kb2[4];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            ka[r] = Pg.a_idx[(size_t)(4 * ti + r) * Pg.nb + kc];
+                            kb2[r] = Pg.b_idx[(size_t)(4 * tj + r) * Pg.nb + kc];
+                        }
+#pragma unroll
+                        for (int r = 0; r < 4; ++r)
+#pragma unroll
+                            for (int m = 0; m < NP; ++m) {
+                                tma_load_3d(smem_u32(sa + m * PAIR_BYTES + r * (PAIR_BYTES / 4)), mA, fb, 0, 0,
+                                            ka[r] * 3 + m);
+                                tma_load_3d(smem_u32(sa + (NP + m) * PAIR_BYTES + r * (PAIR_BYTES / 4)), mB, fb,
+                                            0, 0, kb2[r] * 3 + m);
+                            }
+                    } else {
+                        tma_load_3d(smem_u32(sa), mA, fb, kc * 64, ti * TILE, 0);
+                        tma_load_3d(smem_u32(sa + NP * PAIR_BYTES), mB, fb, kc * 64, tj * TILE, 0);
+                    }
                 }
             }
             // a -1 ends the other roles' sequences (also after an abort; if
@@ -968,16 +1004,28 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             // row i of A's planes (paired layout, see plane_index)
             const __nv_bfloat16* const e_row = Ain + (size_t)i * two_np;
             auto fetch_E = [&](int c_first) {
-                const __nv_bfloat16* ep = e_row;
+                if constexpr (POOL) {
+                    // the warp's block row i / 32 and the pass's block column
+                    const int j0 = tj * TILE + c_first;
+                    const int k = P.a_idx[(size_t)(i >> 5) * P.nb + (j0 >> 5)];
 #pragma unroll
-                for (int p = 0; p < s; ++p) {
+                    for (int p = 0; p < s; ++p)
 #pragma unroll
-                    for (int q = 0; q < EW / 8; ++q) {
-                        const int j = tj * TILE + c_first + 8 * q;
-                        cp_async16(smem_u32(e_mine + p * 32 * (EW / 8) + q),
-                                   ep + (((j >> 5) << 6) + ((p & 1) << 5) + (j & 31)));
+                        for (int q = 0; q < EW / 8; ++q)
+                            cp_async16(smem_u32(e_mine + p * 32 * (EW / 8) + q),
+                                       Ain + pool_index(k, p, i & 31, (j0 & 31) + 8 * q));
+                } else {
+                    const __nv_bfloat16* ep = e_row;
+#pragma unroll
+                    for (int p = 0; p < s; ++p) {
+#pragma unroll
+                        for (int q = 0; q < EW / 8; ++q) {
+                            const int j = tj * TILE + c_first + 8 * q;
+                            cp_async16(smem_u32(e_mine + p * 32 * (EW / 8) + q),
+                                       ep + (((j >> 5) << 6) + ((p & 1) << 5) + (j & 31)));
+                        }
+                        if (p & 1) ep += pair_stride;
                     }
-                    if (p & 1) ep += pair_stride;
                 }
                 cp_async_commit();
             };
@@ -1085,8 +1133,26 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     float plane_scale = 1.f;
                     const float rs = out_rscale, rinv = 1.f / out_rscale;
                     // plane pair 0's row segment (i, jb ..) and mirror column base
-                    __nv_bfloat16* seg0 = outp + (size_t)i * two_np + (((jb >> 5) << 6) + (jb & 31));
-                    __nv_bfloat16* col0p = outp + (size_t)jb * two_np + (((i >> 5) << 6) + (i & 31));
+                    __nv_bfloat16* seg0 = nullptr;
+                    __nv_bfloat16* col0p = nullptr;
+                    int col_step = two_np;     // elements between rows of the mirror column
+                    size_t pair_step = pair_stride;
+                    bool store_row = true, store_col = true;
+                    if constexpr (POOL) {
+                        // blocks (i / 32, jb / 32) and (jb / 32, i / 32) in the output
+                        // pool (slot 0: not stored; the product is zero there)
+                        const int kr = P.out_idx[(size_t)(i >> 5) * P.nb + (jb >> 5)];
+                        const int kcl = P.out_idx[(size_t)(jb >> 5) * P.nb + (i >> 5)];
+                        store_row = kr != 0;
+                        store_col = kcl != 0;
+                        seg0 = outp + pool_index(kr, 0, i & 31, jb & 31);
+                        col0p = outp + pool_index(kcl, 0, jb & 31, i & 31);
+                        col_step = 64;
+                        pair_step = 32 * 64;
+                    } else {
+                        seg0 = outp + (size_t)i * two_np + (((jb >> 5) << 6) + (jb & 31));
+                        col0p = outp + (size_t)jb * two_np + (((i >> 5) << 6) + (i & 31));
+                    }
 #pragma unroll 1
                     for (int p = 0; p < s_out; ++p) {
                         __align__(16) __nv_bfloat16 dv[EW];
@@ -1105,7 +1171,8 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                         // diagonal tile only j >= i is written here (j < i is
                         // the mirror of another row's element)
                         __nv_bfloat16* const seg = seg0 + ((p & 1) << 5);
-                        if (!diag_tile || jb >= i) {
+                        if (!store_row) {
+                        } else if (!diag_tile || jb >= i) {
                             uint4* row = (uint4*)seg;
 #pragma unroll
                             for (int q = 0; q < EW / 8; ++q) row[q] = ((const uint4*)dv)[q];
@@ -1115,17 +1182,18 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                                 if (jb + c >= i) seg[c] = dv[c];
                         }
                         __nv_bfloat16* const col = col0p + ((p & 1) << 5);
-                        if (!diag_tile) {
+                        if (!store_col) {
+                        } else if (!diag_tile) {
 #pragma unroll
-                            for (int c = 0; c < EW; ++c) col[c * two_np] = dv[c];
+                            for (int c = 0; c < EW; ++c) col[c * col_step] = dv[c];
                         } else if (jb + EW > i + 1) {
 #pragma unroll
                             for (int c = 0; c < EW; ++c)
-                                if (jb + c > i) col[c * two_np] = dv[c];
+                                if (jb + c > i) col[c * col_step] = dv[c];
                         }
                         if (p & 1) {
-                            seg0 += pair_stride;
-                            col0p += pair_stride;
+                            seg0 += pair_step;
+                            col0p += pair_step;
                         }
                     }
                 }
@@ -1186,6 +1254,8 @@ KernelFn kernel_queue_hi(int s);
 KernelFn kernel_queue_lo(int s);
 KernelFn kernel_queue_uniform_hi(int s);  // digits_queue_uniform_<lo|hi>.cu (QM = 2)
 KernelFn kernel_queue_uniform_lo(int s);
+KernelFn kernel_pool_lo(int s);           // digits_pool_<lo|hi>.cu (QM = 3)
+KernelFn kernel_pool_hi(int s);
 
 }  // namespace dk
 }  // namespace purify

@@ -69,14 +69,19 @@ __device__ __forceinline__ df split_entry(double x) {
 
 // One 32 x 128 strip of the split (see split_kernel); tr accumulates the
 // diagonal's trace (float), the strip's block norms go to bnorm2 when set.
+// POOLED: the planes go to the pool slots that pidx (nb x nb) gives the
+// blocks (slot 0: not written); a null pidx writes nothing (norms only).
+template <bool POOLED>
 __device__ __forceinline__ void split_strip(const double* __restrict__ F, int64_t ldf, int n, int n_pad, df a, df b,
                                             float digit_scale, float rscale, float rinv, int s,
                                             __nv_bfloat16* __restrict__ out, float* __restrict__ bnorm2, bool vec,
-                                            int strip, int lane, float& tr) {
+                                            int strip, int lane, float& tr, const int* __restrict__ pidx = nullptr) {
     const int nb = n_pad / 32, ns = n_pad / 128;  // nb^2 <= 2^24: 32-bit block indices
     const int64_t total = (int64_t)n_pad * n_pad;
     const int I = strip / ns, Jq = strip - I * ns;
     const int j0 = Jq * 128 + lane * 4;
+    // the pool slot of this lane's block (I, j0 / 32); 0: not written
+    const int slot = (POOLED && pidx) ? pidx[(size_t)I * nb + (j0 >> 5)] : 0;
     float bsum = 0.f;
 #pragma unroll 2
     for (int r = 0; r < 32; ++r) {  // two rows' loads in flight per warp
@@ -111,6 +116,7 @@ __device__ __forceinline__ void split_strip(const double* __restrict__ F, int64_
             bsum += z[c].h * z[c].h;
             z[c] = df_scale(z[c], digit_scale);
         }
+        if (POOLED && slot == 0) continue;
         // plane p at out + plane_index(p, i, j0, n_pad): pairs 2 total apart
         __nv_bfloat16* dst = out + (size_t)i * 2 * n_pad + ((j0 >> 5) << 6) + (j0 & 31);
         float plane_scale = 1.f;
@@ -125,7 +131,10 @@ __device__ __forceinline__ void split_strip(const double* __restrict__ F, int64_
                 dv[c] = digit_to_bf16(d * plane_scale);
                 z[c] = df_scale(z[c], rscale);
             }
-            *(uint2*)(dst + (size_t)(p >> 1) * 2 * total + ((p & 1) << 5)) = *(const uint2*)dv;
+            if constexpr (POOLED)
+                *(uint2*)(out + pool_index(slot, p, r, j0 & 31)) = *(const uint2*)dv;
+            else
+                *(uint2*)(dst + (size_t)(p >> 1) * 2 * total + ((p & 1) << 5)) = *(const uint2*)dv;
             plane_scale *= rinv;
         }
     }
@@ -150,7 +159,7 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ F
     const float rinv = 1.f / rscale;
     float tr = 0.f;
     for (int strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); strip < nb * ns; strip += warps)
-        split_strip(F, ldf, n, n_pad, a, b, digit_scale, rscale, rinv, s, out, bnorm2, vec, strip, lane, tr);
+        split_strip<false>(F, ldf, n, n_pad, a, b, digit_scale, rscale, rinv, s, out, bnorm2, vec, strip, lane, tr);
     if (red) {
         tr = warp_sum_f(tr);
         if (lane == 0) atomicAdd(red, (double)tr);
@@ -179,9 +188,26 @@ __global__ void __launch_bounds__(256) split_group_kernel(const SplitJob* __rest
         if (strip == 0 && J.zero4 && lane < 4) J.zero4[lane] = 0.0;
         const bool vec = (J.ldf & 1) == 0 && ((uintptr_t)J.F & 15) == 0;
         float tr = 0.f;
-        split_strip(J.F, J.ldf, J.n, J.n_pad, df{J.a_h, J.a_l}, df{J.b_h, J.b_l}, J.digit_scale, J.rscale,
-                    1.f / J.rscale, J.s, J.out, nullptr, vec, strip, lane, tr);
+        split_strip<false>(J.F, J.ldf, J.n, J.n_pad, df{J.a_h, J.a_l}, df{J.b_h, J.b_l}, J.digit_scale, J.rscale,
+                           1.f / J.rscale, J.s, J.out, nullptr, vec, strip, lane, tr);
     }
+}
+
+// The split into pooled planes (block-sparse runs); pidx null: block norms
+// only.
+__global__ void __launch_bounds__(256) split_pool_kernel(const double* __restrict__ F, int64_t ldf, int n, int n_pad,
+                                                         df a, df b, float digit_scale, float rscale, int s,
+                                                         __nv_bfloat16* __restrict__ pool, const int* __restrict__ pidx,
+                                                         float* __restrict__ bnorm2) {
+    const int nb = n_pad / 32, ns = n_pad / 128;
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const bool vec = (ldf & 1) == 0 && ((uintptr_t)F & 15) == 0;
+    const float rinv = 1.f / rscale;
+    float tr = 0.f;
+    for (int strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); strip < nb * ns; strip += warps)
+        split_strip<true>(F, ldf, n, n_pad, a, b, digit_scale, rscale, rinv, s, pool, bnorm2, vec, strip, lane, tr,
+                          pidx);
 }
 
 // ---- tensor maps --------------------------------------------------------------
@@ -217,6 +243,23 @@ int make_plane_map(CUtensorMap* map, const __nv_bfloat16* planes, int n_pad, int
     cuuint32_t box[3] = {64, (cuuint32_t)TILE, (cuuint32_t)np};
     cuuint32_t estr[3] = {1, 1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)planes, dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? PURIFY_OK : PURIFY_ERR_CUDA;
+}
+
+// 3D map over a pool of 32 x 32 block slots (pool_index): dims {64, 32,
+// 3 slots}, box {64, 32, 1}: one block of one plane pair per box, 128-byte
+// swizzle (the same shared-memory image as the rows of a dense panel).
+int make_pool_map(CUtensorMap* map, const __nv_bfloat16* pool, int slots) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return PURIFY_ERR_UNSUPPORTED;
+    if (((uintptr_t)pool & 15) || slots < 1) return PURIFY_ERR_INVALID_ARG;
+    cuuint64_t dims[3] = {64, 32, (cuuint64_t)slots * 3};
+    cuuint64_t strides[2] = {128, 32 * 128};
+    cuuint32_t box[3] = {64, 32, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)pool, dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? PURIFY_OK : PURIFY_ERR_CUDA;
@@ -291,6 +334,7 @@ int prepare_digit_kernels() {
     for (int s = 1; s <= kMaxDigitPlanes; ++s) {
         PURIFY_TRY(prepare_kernel(queue_kernel(s, false)));
         PURIFY_TRY(prepare_kernel(queue_kernel(s, true)));
+        PURIFY_TRY(prepare_kernel(s <= 3 ? kernel_pool_lo(s) : kernel_pool_hi(s)));
     }
     return PURIFY_OK;
 }
@@ -301,8 +345,14 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
     if (st.n <= 0 || st.n_pad % TILE || st.n > st.n_pad) return PURIFY_ERR_INVALID_ARG;
     if (st.rbits < 4 || st.rbits > 8) return PURIFY_ERR_INVALID_ARG;
     const int kc = digit_step_kc(st);
-    PURIFY_TRY(make_plane_map(ma, st.A, st.n_pad, st.s_in, kc));
-    PURIFY_TRY(make_plane_map(mb, st.B, st.n_pad, st.s_in, kc));
+    if (st.a_idx) {
+        if (!st.b_idx || (st.out && !st.out_idx) || st.a_slots < 1 || st.b_slots < 1) return PURIFY_ERR_INVALID_ARG;
+        PURIFY_TRY(make_pool_map(ma, st.A, st.a_slots));
+        PURIFY_TRY(make_pool_map(mb, st.B, st.b_slots));
+    } else {
+        PURIFY_TRY(make_plane_map(ma, st.A, st.n_pad, st.s_in, kc));
+        PURIFY_TRY(make_plane_map(mb, st.B, st.n_pad, st.s_in, kc));
+    }
     std::memset(p, 0, sizeof(*p));
     p->n = st.n;
     p->n_pad = st.n_pad;
@@ -330,13 +380,18 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
     p->bnorm2 = st.bnorm2;
     p->nb = st.n_pad / 32;
     p->ctl = st.ctl;
+    p->a_idx = st.a_idx;
+    p->b_idx = st.b_idx;
+    p->out_idx = st.out_idx;
     if (st.kc_cnt && !st.kc_mask) return PURIFY_ERR_INVALID_ARG;
     if ((st.kc_cnt || st.bnorm2) && kc != 32) return PURIFY_ERR_INVALID_ARG;
     return PURIFY_OK;
 }
 
+static KernelFn pool_kernel(int s) { return s <= 3 ? kernel_pool_lo(s) : kernel_pool_hi(s); }
+
 static int launch_kernel(const DigitLaunch& L, int s, int kc, int grid, cudaStream_t stream, bool uniform = false) {
-    KernelFn fn = L.qprm ? queue_kernel(s, uniform) : kernel_for(kc, s);
+    KernelFn fn = L.qprm ? queue_kernel(s, uniform) : (L.prms[0].a_idx ? pool_kernel(s) : kernel_for(kc, s));
     if (!fn || grid < 1 || L.stages < 1) return PURIFY_ERR_INVALID_ARG;
     PURIFY_TRY(prepare_kernel(fn));
     fn<<<grid, NTHREADS, digit_smem_bytes(s, kc), stream>>>(L);
@@ -504,6 +559,21 @@ int launch_split_group(const SplitJob* jobs, int njobs, int total_strips, cudaSt
     int64_t blocks = ((int64_t)total_strips + 7) / 8;  // 8 warps per CTA, one strip each
     if (blocks > 152 * 8) blocks = 152 * 8;
     split_group_kernel<<<(unsigned)blocks, 256, 0, stream>>>(jobs, njobs, total_strips);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return PURIFY_OK;
+}
+
+int launch_split_pool(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s, int rbits,
+                      __nv_bfloat16* pool, const int* pidx, float* bnorm2, cudaStream_t stream) {
+    if (s < 1 || s > kMaxDigitPlanes || n <= 0 || n_pad < n || n_pad % 128 || n_pad > (1 << 17) || rbits < 4 ||
+        rbits > 8 || (pidx && !pool) || (!pidx && !bnorm2))
+        return PURIFY_ERR_INVALID_ARG;
+    const int64_t strips = (int64_t)(n_pad / 32) * (n_pad / 128);
+    int64_t blocks = (strips + 7) / 8;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    split_pool_kernel<<<(unsigned)blocks, 256, 0, stream>>>(F, ldf, n, n_pad, to_df(a), to_df(b), ldexpf(1.f, 8 - e),
+                                                             ldexpf(1.f, rbits), s, pool, pidx, bnorm2);
     PURIFY_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return PURIFY_OK;

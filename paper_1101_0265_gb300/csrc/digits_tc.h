@@ -75,6 +75,14 @@ struct DigitStep {
     int split_ways = 0;
     // bound of the kernel's work waits in SM cycles (0: about one second)
     long long wait_cycles = 0;
+    // pooled planes (block-sparse runs): A, B and out are pools of 32 x 32
+    // block slots (slot 0 the zero block) with nb x nb slot tables in device
+    // memory; a_slots and b_slots are the pools' capacities.  Null: dense
+    // paired planes.
+    const int* a_idx = nullptr;
+    const int* b_idx = nullptr;
+    const int* out_idx = nullptr;
+    int a_slots = 0, b_slots = 0;
     // device-side control (null: the fields above decide)
     const DevStep* ctl = nullptr;
 };
@@ -128,6 +136,17 @@ int fill_queue_product(const DigitStep& st, int smax, dk::DigitGemmParams* p, CU
 int launch_digit_queue(int smax, bool uniform, const dk::DigitGemmParams* prm, const CUtensorMap* maps, int* cnt,
                        int* ticket, const int4* work, int num_items, float2* scratch, int max_ctas, int* err,
                        cudaStream_t stream, long long wait_cycles);
+
+// Bytes of one pool slot: the six digit planes (three pairs) of a 32 x 32
+// block.
+constexpr size_t kPoolSlotBytes = 3 * 32 * 64 * 2;
+
+// The split into pooled planes (block-sparse runs): block (I, J) of the s
+// planes of a F + b I goes to pool slot pidx[I nb + J] (pool_index; slot 0:
+// not written); bnorm2 (may be null) receives the blocks' ||.||_F^2 for
+// I <= J.  pidx null: the norms only.
+int launch_split_pool(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s, int rbits,
+                      __nv_bfloat16* pool, const int* pidx, float* bnorm2, cudaStream_t stream);
 
 // Many splits in one launch (see launch_split): a job per matrix, its strips
 // (32 x 128 pieces of the padded matrix, split_strips of them) numbered from

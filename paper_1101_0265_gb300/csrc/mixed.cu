@@ -42,11 +42,16 @@ void mixed_free(MixedState* ms) {
     cudaFree(ms->tsel);
     cudaFree(ms->tsched);
     cudaFree(ms->qdev);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(ms->pool[k]);
+        cudaFree(ms->pidx[k]);
+    }
+    cudaFree(ms->pwork);
     if (ms->tgraph) cudaGraphExecDestroy(ms->tgraph);
     delete ms;
 }
 
-int ensure_mixed(purify_ctx* h, int n_pad) {
+int ensure_mixed(purify_ctx* h, int n_pad, bool planes) {
     if (!h->mixed) {
         h->mixed = new (std::nothrow) MixedState();
         if (!h->mixed) return PURIFY_ERR_OOM;
@@ -59,7 +64,7 @@ int ensure_mixed(purify_ctx* h, int n_pad) {
         PURIFY_CUDA_TRY(cudaMalloc(&h->mixed->split_cnt, sizeof(int) * digit_split_counters(sms)));
     }
     MixedState* ms = h->mixed;
-    if (n_pad <= ms->n_pad_cap) return PURIFY_OK;
+    if (!planes || n_pad <= ms->n_pad_cap) return PURIFY_OK;
     cudaFree(ms->Xd[0]);
     cudaFree(ms->Xd[1]);
     cudaFree(ms->Sd);

@@ -68,10 +68,21 @@ struct MixedState {
     std::vector<uint8_t> qhost;
     void* qdev = nullptr;
     size_t qdev_cap = 0;
+    // block-sparse runs: the iterates' digit planes as pools of 32 x 32 block
+    // slots (slot 0 the zero block), their nb x nb slot tables, and the work
+    // list of a product's tiles
+    __nv_bfloat16* pool[2] = {nullptr, nullptr};
+    size_t pool_slots[2] = {0, 0};
+    int* pidx[2] = {nullptr, nullptr};
+    size_t pidx_cap = 0;
+    int4* pwork = nullptr;
+    size_t pwork_cap = 0;
+    double pool_bytes_peak = 0.0;  // largest pool bytes held in the last run
 };
 
-// Allocate (or grow) the handle's mixed-path buffers for a padded size.
-int ensure_mixed(purify_ctx* h, int n_pad);
+// Allocate (or grow) the handle's mixed-path buffers for a padded size
+// (planes = false: the state without the dense digit planes).
+int ensure_mixed(purify_ctx* h, int n_pad, bool planes = true);
 // Default per-step digit rule: a step's operands carry at least kBitsFloor
 // bits and kBitsGap bits beyond log2(1 / mapped gap).
 constexpr double kBitsFloor = 30.0;

@@ -13,9 +13,11 @@
 //     (off-diagonal blocks twice, for B and B^T) stays <= tau^2, so each step
 //     moves X by at most tau in the Frobenius norm; dropped blocks are zeroed
 //     in the digit planes and leave the pattern.
-// Digit planes stay dense in memory (n_pad^2 per plane); the work follows
-// the pattern.  Patterns are bitsets on the host: the pattern of X^2 is the
-// union over K in row I of the rows K.
+// The digit planes of an iterate are a pool of 32 x 32 block slots (all
+// planes of a block in one 12 KB slot, pool_index) found through an nb x nb
+// slot table; absent blocks map to slot 0, which holds zeros.  Memory and
+// work both follow the pattern.  Patterns are bitsets on the host: the
+// pattern of X^2 is the union over K in row I of the rows K.
 #include <algorithm>
 #include <cstddef>
 #include <cmath>
@@ -24,22 +26,20 @@
 
 #include "digits_tc.h"
 #include "mixed.h"
+#include "queue_plan.h"
 
 namespace purify {
 
 namespace {
 
-// Zero blocks (I, J) and (J, I) in s digit planes (paired layout, see
-// plane_index: a block's row in one plane is 32 contiguous elements).
-__global__ void mask_planes_kernel(__nv_bfloat16* planes, int s, int n_pad, const int2* blocks) {
-    const int2 b = blocks[blockIdx.x];
-    const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-    for (int p = 0; p < s; ++p)
-        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-            const int r = e >> 5, c = e & 31;
-            planes[plane_index(p, b.x * 32 + r, b.y * 32 + c, n_pad)] = z;
-            planes[plane_index(p, b.y * 32 + r, b.x * 32 + c, n_pad)] = z;
-        }
+// Blocks (I, J) and (J, I) leave a pool's slot table: from then on they
+// read as slot 0, the zero block.
+__global__ void drop_slots_kernel(int* idx, int nb, const int2* blocks, int count) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
+        const int2 b = blocks[k];
+        idx[(size_t)b.x * nb + b.y] = 0;
+        idx[(size_t)b.y * nb + b.x] = 0;
+    }
 }
 
 // Zero blocks (I, J) and (J, I) of an n x n float64 matrix.
@@ -302,12 +302,14 @@ int grow(T** p, size_t* cap, size_t n) {
     return PURIFY_OK;
 }
 
-// Zero the chosen blocks in the digit planes and / or the float64 result.
-int apply_drops(purify_ctx* h, size_t count, __nv_bfloat16* planes, int s, int n_pad, double* out64, int n) {
+// Remove the chosen blocks from a pool's slot table and / or zero them in
+// the float64 result.
+int apply_drops(purify_ctx* h, size_t count, int* idx, int nb, double* out64, int n) {
     MixedState* ms = h->mixed;
     if (count == 0) return PURIFY_OK;
-    if (planes) {
-        mask_planes_kernel<<<(unsigned)count, 256, 0, h->stream>>>(planes, s, n_pad, ms->drops);
+    if (idx) {
+        const unsigned grid = (unsigned)std::min<size_t>((count + 255) / 256, 152 * 4);
+        drop_slots_kernel<<<grid, 256, 0, h->stream>>>(idx, nb, ms->drops, (int)count);
         PURIFY_CUDA_TRY(cudaGetLastError());
         count_launches(1);
     }
@@ -322,8 +324,7 @@ int apply_drops(purify_ctx* h, size_t count, __nv_bfloat16* planes, int s, int n
 // Choose the drops of one step on the device (see trunc_hist_kernel) and
 // zero them; the host receives the dropped blocks for its pattern and walks
 // the blocks tied at the selected norm in (row, column) order.
-int truncate_step(purify_ctx* h, Pattern& pat, double tau, __nv_bfloat16* planes, int s, int n_pad,
-                  double* out64, int n, std::vector<float>&) {
+int truncate_step(purify_ctx* h, Pattern& pat, double tau, int* idx, double* out64, int n) {
     MixedState* ms = h->mixed;
     const int nb = pat.nb, words = pat.words;
     const double budget = tau * tau;
@@ -392,7 +393,7 @@ int truncate_step(purify_ctx* h, Pattern& pat, double tau, __nv_bfloat16* planes
         pat.clear(b.x, b.y);
         pat.clear(b.y, b.x);
     }
-    return apply_drops(h, nd, planes, s, n_pad, out64, n);
+    return apply_drops(h, nd, idx, nb, out64, n);
 }
 
 void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
@@ -427,6 +428,59 @@ int launch_scatter_coo(const int64_t* key, const double* v, int64_t nnz, double*
     return PURIFY_OK;
 }
 
+namespace {
+
+// Pool k holds at least `slots` slots; a new allocation starts with slot 0
+// (the zero block) cleared.  Slots are never written across the reallocation:
+// the pool being resized is the one about to be filled.
+int ensure_pool(purify_ctx* h, int k, size_t slots) {
+    MixedState* ms = h->mixed;
+    if (slots <= ms->pool_slots[k]) return PURIFY_OK;
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    cudaFree(ms->pool[k]);
+    ms->pool[k] = nullptr;
+    ms->pool_slots[k] = 0;
+    const size_t c = slots + slots / 4 + 16;
+    PURIFY_CUDA_TRY(cudaMalloc(&ms->pool[k], c * kPoolSlotBytes));
+    ms->pool_slots[k] = c;
+    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->pool[k], 0, kPoolSlotBytes, h->stream));
+    return PURIFY_OK;
+}
+
+// Slot table of a pattern (every block of it, both triangles): slots 1, 2,
+// .. in row-major block order.  Returns the slots used, slot 0 included.
+size_t assign_slots(const Pattern& P, std::vector<int>& idx) {
+    idx.assign((size_t)P.nb * P.nb, 0);
+    int k = 1;
+    for (int I = 0; I < P.nb; ++I)
+        for (int J = 0; J < P.nb; ++J)
+            if (P.get(I, J)) idx[(size_t)I * P.nb + J] = k++;
+    return (size_t)k;
+}
+
+// The upper 128 x 128 tiles holding a block of `out`, in banded order: the
+// product's work items {0, ti, tj, 0}.
+void pattern_tiles(const Pattern& out, int T, std::vector<int4>& work) {
+    std::vector<int2> band;
+    banded_tiles(T, band);
+    work.clear();
+    for (const int2& t : band) {
+        bool any = false;
+        for (int r = 4 * t.x; r < 4 * t.x + 4 && !any; ++r)
+            any = ((out.row(r)[(4 * t.y) >> 6] >> ((4 * t.y) & 63)) & 0xFull) != 0;
+        if (any) work.push_back(make_int4(0, t.x, t.y, 0));
+    }
+}
+
+int upload_slots(purify_ctx* h, int k, const std::vector<int>& idx) {
+    return cudaMemcpyAsync(h->mixed->pidx[k], idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice,
+                           h->stream) == cudaSuccess
+               ? PURIFY_OK
+               : PURIFY_ERR_CUDA;
+}
+
+}  // namespace
+
 int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std::vector<double>& red) {
     if (scheme != PURIFY_TC_SF && scheme != PURIFY_TC_MONO) return PURIFY_ERR_UNSUPPORTED;
     const int m_sched = (int)S.alpha.size();
@@ -435,7 +489,7 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     if (!(tau >= 0.0)) return PURIFY_ERR_INVALID_ARG;
     const int n = (int)h->n;
     const int n_pad = pad128(n);
-    PURIFY_TRY(ensure_mixed(h, n_pad));
+    PURIFY_TRY(ensure_mixed(h, n_pad, false));
     MixedState* ms = h->mixed;
     const int nb = n_pad / 32, T = n_pad / 128;
     const int rb = remainder_bits(n_pad);
@@ -451,6 +505,15 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     for (int i = 0; i < m; ++i) dmax = std::max(dmax, sd[i]);
     h->st.digit_max = dmax;
     PURIFY_TRY(grow(&ms->bnorm2, &ms->bnorm2_cap, (size_t)nb * nb));
+    if (ms->pidx_cap < (size_t)nb * nb) {
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(ms->pidx[k]);
+            ms->pidx[k] = nullptr;
+        }
+        ms->pidx_cap = 0;
+        for (int k = 0; k < 2; ++k) PURIFY_CUDA_TRY(cudaMalloc(&ms->pidx[k], sizeof(int) * (size_t)nb * nb));
+        ms->pidx_cap = (size_t)nb * nb;
+    }
     const int slots = 2 * m + 2;
     PURIFY_TRY(ensure_red(h, 4 * (int64_t)slots));
     PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * slots, h->stream));
@@ -461,10 +524,12 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     const double c0 = lmax / (lmax - lmin), c1 = -1.0 / (lmax - lmin);
     std::vector<float> bn2((size_t)nb * nb, 0.f);
     ms->nnzb_history.clear();
-    // X_0 = c0 I + c1 F and its block norms (from the split): its block
-    // pattern, truncated like every iterate
-    PURIFY_TRY(launch_split(h->F, n, n, n_pad, c1, c0, 0, std::max(sd[0], 1), rb, ms->Xd[0], nullptr, h->stream,
-                            ms->bnorm2));
+    ms->pool_bytes_peak = 0.0;
+    // X_0 = c0 I + c1 F: its block norms first (the split without planes),
+    // then its pattern, truncated like every iterate, and its planes in the
+    // pool slots of the kept blocks
+    const int s0 = std::max(sd[0], 1);
+    PURIFY_TRY(launch_split_pool(h->F, n, n, n_pad, c1, c0, 0, s0, rb, nullptr, nullptr, ms->bnorm2, h->stream));
     PURIFY_CUDA_TRY(cudaMemcpyAsync(bn2.data(), ms->bnorm2, sizeof(float) * (size_t)nb * nb,
                                     cudaMemcpyDeviceToHost, h->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -479,49 +544,66 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     {
         std::vector<int2> drop;
         select_drops(X, bn2.data(), tau, drop);
-        if (!drop.empty()) {
-            PURIFY_TRY(grow(&ms->drops, &ms->drops_cap, drop.size()));
-            PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->drops, drop.data(), sizeof(int2) * drop.size(),
-                                            cudaMemcpyHostToDevice, h->stream));
-            mask_planes_kernel<<<(unsigned)drop.size(), 256, 0, h->stream>>>(ms->Xd[0], std::max(sd[0], 1), n_pad,
-                                                                              ms->drops);
-            PURIFY_CUDA_TRY(cudaGetLastError());
-            count_launches(1);
-        }
     }
     ms->nnzb_history.push_back(X.count_upper());
+    std::vector<int> idx;
+    size_t used[2] = {assign_slots(X, idx), 0};
+    PURIFY_TRY(ensure_pool(h, 0, used[0]));
+    PURIFY_TRY(upload_slots(h, 0, idx));
+    PURIFY_TRY(launch_split_pool(h->F, n, n, n_pad, c1, c0, 0, s0, rb, ms->pool[0], ms->pidx[0], nullptr,
+                                 h->stream));
 
     double* D = h->X[0];
     *cur = 0;
     int x = 0;
     std::vector<int> cnt;
     std::vector<uint64_t> mask;
+    std::vector<int4> work;
     const size_t tiles = (size_t)T * (T + 1) / 2;
     const size_t cnt_words = (tiles + 1) / 2;  // the counts, two ints per word
     const double pairs_tile = 2.0 * 128.0 * 128.0 * 32.0;  // one pair, one 32-wide k-chunk
     for (int i = 0; i < m; ++i) {
         const int s = sd[i];
+        const bool last = (i + 1 == m);
         Pattern out;
         output_pattern(X, out);
         chunk_masks(X, T, cnt, mask);
+        pattern_tiles(out, T, work);
         PURIFY_TRY(grow(&ms->kc_buf, &ms->kc_buf_cap, cnt_words + mask.size()));
+        PURIFY_TRY(grow(&ms->pwork, &ms->pwork_cap, work.size()));
         int* kc_cnt = (int*)ms->kc_buf;
         unsigned long long* kc_mask = ms->kc_buf + cnt_words;
         PURIFY_CUDA_TRY(cudaMemcpyAsync(kc_cnt, cnt.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice, h->stream));
         PURIFY_CUDA_TRY(cudaMemcpyAsync(kc_mask, mask.data(), sizeof(uint64_t) * mask.size(), cudaMemcpyHostToDevice,
                                         h->stream));
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->pwork, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice,
+                                        h->stream));
         double chunks = 0.0;
-        for (size_t k = 0; k < tiles; ++k) chunks += cnt[k] < 0 ? (double)nb : (double)cnt[k];
+        for (const int4& w : work) {
+            const int c = cnt[(size_t)w.z * (w.z + 1) / 2 + w.y];
+            chunks += c < 0 ? (double)nb : (double)c;
+        }
+        if (!last) {
+            used[x ^ 1] = assign_slots(out, idx);
+            PURIFY_TRY(ensure_pool(h, x ^ 1, used[x ^ 1]));
+            PURIFY_TRY(upload_slots(h, x ^ 1, idx));
+        } else if (work.size() < tiles) {
+            // tiles outside the work list are not written
+            PURIFY_CUDA_TRY(cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, h->stream));
+        }
+        ms->pool_bytes_peak =
+            std::max(ms->pool_bytes_peak, (double)(used[0] + (last ? 0 : used[1])) * kPoolSlotBytes);
         DigitStep st;
         st.n = n;
         st.n_pad = n_pad;
         st.rbits = rb;
-        st.A = st.B = ms->Xd[x];
+        st.A = st.B = ms->pool[x];
+        st.a_idx = st.b_idx = ms->pidx[x];
+        st.a_slots = st.b_slots = (int)ms->pool_slots[x];
         st.s_in = s;
         st.eA = st.eB = 0;
         st.use_E = 1;
         tc_coeffs(S.branch[i], S.alpha[i], &st.cP, &st.cE, &st.cI);
-        const bool last = (i + 1 == m);
         st.red = h->red + 4 * (2 * i + 1);
         st.err = ms->err;
         st.scratch = ms->scratch;
@@ -533,17 +615,18 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
         if (last) {
             st.out64 = D;
         } else {
-            st.out = ms->Xd[x ^ 1];
+            st.out = ms->pool[x ^ 1];
+            st.out_idx = ms->pidx[x ^ 1];
             st.s_out = sd[i + 1];
             st.e_out = 0;
         }
         PURIFY_TRY(product_begin(h));
-        PURIFY_TRY(launch_digit_step(st, h->stream));
+        PURIFY_TRY(launch_digit_group(s, &st, 1, ms->pwork, (int)work.size(), ms->scratch, ms->ctas, ms->err,
+                                      h->stream, st.wait_cycles));
         ++h->st.product_launches;
         h->st.tensor_flops += 0.5 * s * (s + 1) * pairs_tile * chunks;
         PURIFY_TRY(product_end(h));
-        PURIFY_TRY(truncate_step(h, out, tau, last ? nullptr : ms->Xd[x ^ 1], last ? 0 : sd[i + 1], n_pad,
-                                 last ? D : nullptr, n, bn2));
+        PURIFY_TRY(truncate_step(h, out, tau, last ? nullptr : ms->pidx[x ^ 1], last ? D : nullptr, n));
         X = out;
         ms->nnzb_history.push_back(X.count_upper());
         x ^= 1;
@@ -557,6 +640,7 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     PURIFY_CUDA_TRY(cudaMemcpyAsync(&err, ms->err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
     h->st.device_flag = err;
+    h->st.plane_pool_mib = (int)std::ceil(ms->pool_bytes_peak / (1024.0 * 1024.0));
     if (err) return device_flag_status(err);
     if (m > 0) {
         h->st.trace = red[4 * (size_t)(2 * (m - 1) + 1)];

@@ -181,6 +181,11 @@ def test_full_size_lattice_invariants(P):
         if bs:
             hist = pur.block_history()
             assert len(hist) == st["iterations"] + 1 and hist[0] < hist[-1]
+            # the pools hold at most every block of both iterates (12 KB each)
+            nb = n // 32
+            assert 0 < st["plane_pool_mib"] <= -(-2 * (nb * nb + 1) * 12288 // 2**20)
+        else:
+            assert st["plane_pool_mib"] == 0
         pur.close()
         assert abs(st["trace"] - lat.nocc) < 1e-4
         DE = D @ E
