@@ -227,7 +227,7 @@ def run_serve(P, dev, stream, rate, count, budget_gb=64.0, tol=1e-9, advance=4):
 
 
 def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsite=3.0,
-                sweep_sizes=(16, 20, 24, 28, 32), sweep_onsite=6.0):
+                sweeps=((6.0, (16, 20, 24, 28, 32)), (3.0, (16, 24, 32, 40)))):
     """The block-sparse workload: periodic L^3 cubic tight-binding lattice
     (onsite +-0.5 by sublattice + N(0, 0.05), hopping -1 + U(-0.1, 0.1)),
     n = L^3, nocc = n/2, mu = 0, loaded from COO, 32 x 32 blocks.
@@ -238,8 +238,8 @@ def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsi
       budget (tau = budget / (m + 1)), at the C3 onsite splitting and at a
       wider one (+-wide_onsite), where the density stays sparse.
     - "n_sweep": TC_SF block-sparse at tau per step on L^3 lattices of
-      growing L with onsite +-sweep_onsite: time per step and the kept
-      blocks per block row against n.
+      growing L for each (onsite, sizes) of `sweeps`: time per step, the
+      kept blocks per block row and the digit-plane pool bytes against n.
     One handle per mode, warmed once; device-event time of one run each."""
     import torch
     from paper_1101_0265_gb300 import inputs as I
@@ -286,27 +286,34 @@ def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsi
             e["speedup_sparse_vs_dense"] = e["TC_SF_dense"]["seconds"] / e["TC_SF"]["seconds"]
         e["speedup_sf_vs_mono"] = e["TC_MONO"]["seconds"] / e["TC_SF"]["seconds"]
         eq.append(e)
-    # n-sweep: the same construction at growing L with a wide onsite
-    # splitting (short decay length of D against the box), tau per step
+    # n-sweeps: the same construction at growing L with wider onsite
+    # splittings (shorter decay length of D against the box), tau per step;
+    # the dense handle is closed first (the largest lattice needs the room)
+    pool[False].close()
+    del pool[False]
+    torch.cuda.empty_cache()
     sweep = []
-    for Ls in sweep_sizes:
-        lt = I.lattice_hamiltonian(Ls, onsite=sweep_onsite)
-        r = case(lt, "TC_SF", True, trunc_tau=tau)
-        nb = lt.n // 32
-        kept = r["nnz_blocks"][-1]
-        n_pad = (lt.n + 127) // 128 * 128
-        sweep.append({"L": Ls, "n": lt.n, "seconds": r["seconds"], "iterations": r["iterations"],
-                      "seconds_per_step": r["seconds"] / max(1, r["iterations"]),
-                      "kept_blocks_per_block_row": 2 * kept / nb, "final_fill": r["final_fill"],
-                      "plane_pool_mib": r["plane_pool_mib"],
-                      "dense_planes_mib": 2 * 6 * n_pad * n_pad * 2 / 2**20, "trace_err": r["trace_err"]})
+    for onsite, sizes in sweeps:
+        for Ls in sizes:
+            lt = I.lattice_hamiltonian(Ls, onsite=onsite)
+            r = case(lt, "TC_SF", True, trunc_tau=tau)
+            nb = lt.n // 32
+            kept = r["nnz_blocks"][-1]
+            n_pad = (lt.n + 127) // 128 * 128
+            sweep.append({"onsite": onsite, "L": Ls, "n": lt.n, "seconds": r["seconds"],
+                          "iterations": r["iterations"],
+                          "seconds_per_step": r["seconds"] / max(1, r["iterations"]),
+                          "kept_blocks_per_block_row": 2 * kept / nb, "final_fill": r["final_fill"],
+                          "max_fill": max(r["nnz_blocks"]) / (nb * (nb + 1) / 2),
+                          "plane_pool_mib": r["plane_pool_mib"],
+                          "dense_planes_mib": 2 * 6 * n_pad * n_pad * 2 / 2**20, "trace_err": r["trace_err"]})
     for pur in pool.values():
         pur.close()
     torch.cuda.empty_cache()
     return {"workload": f"{L}^3 periodic cubic tight-binding lattice, n={lat.n}, COO input, "
                         f"32x32 blocks, tol {tol:g}",
             "n": lat.n, "C3": c3, "equal_budget": eq,
-            "n_sweep": {"onsite": sweep_onsite, "tau": tau, "scheme": "TC_SF block-sparse", "runs": sweep,
+            "n_sweep": {"tau": tau, "scheme": "TC_SF block-sparse", "runs": sweep,
                         "note": "plane_pool_mib: peak of the two block pools that hold the iterates' digit "
                                 "planes (12 KB per kept 32x32 block, both triangles); dense_planes_mib: two "
                                 "dense 6-plane buffers at the same size"}}

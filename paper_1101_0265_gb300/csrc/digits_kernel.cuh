@@ -323,10 +323,11 @@ struct DigitGemmParams {
 };
 
 // Element offset of (plane p, row r, column c) of the 32 x 32 block in pool
-// slot k: a slot holds plane pairs 0..2, each 32 rows of 64 elements (the two
-// planes' 32 columns side by side, as in the dense paired layout).
-__host__ __device__ inline size_t pool_index(int k, int p, int r, int c) {
-    return ((size_t)(k * 3 + (p >> 1)) * 32 + r) * 64 + ((p & 1) << 5) + c;
+// slot k of a pool with np plane pairs per slot: a slot holds its block's
+// plane pairs, each 32 rows of 64 elements (the two planes' 32 columns side by
+// side, as in the dense paired layout).
+__host__ __device__ inline size_t pool_index(int k, int np, int p, int r, int c) {
+    return ((size_t)(k * np + (p >> 1)) * 32 + r) * 64 + ((p & 1) << 5) + c;
 }
 
 // Products per grouped launch, whose tensor maps and parameters travel as
@@ -744,9 +745,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
 #pragma unroll
                             for (int m = 0; m < NP; ++m) {
                                 tma_load_3d(smem_u32(sa + m * PAIR_BYTES + r * (PAIR_BYTES / 4)), mA, fb, 0, 0,
-                                            ka[r] * 3 + m);
+                                            ka[r] * NP + m);
                                 tma_load_3d(smem_u32(sa + (NP + m) * PAIR_BYTES + r * (PAIR_BYTES / 4)), mB, fb,
-                                            0, 0, kb2[r] * 3 + m);
+                                            0, 0, kb2[r] * NP + m);
                             }
                     } else {
                         tma_load_3d(smem_u32(sa), mA, fb, kc * 64, ti * TILE, 0);
@@ -1013,7 +1014,7 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
 #pragma unroll
                         for (int q = 0; q < EW / 8; ++q)
                             cp_async16(smem_u32(e_mine + p * 32 * (EW / 8) + q),
-                                       Ain + pool_index(k, p, i & 31, (j0 & 31) + 8 * q));
+                                       Ain + pool_index(k, NP, p, i & 31, (j0 & 31) + 8 * q));
                 } else {
                     const __nv_bfloat16* ep = e_row;
 #pragma unroll
@@ -1145,8 +1146,9 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                         const int kcl = P.out_idx[(size_t)(jb >> 5) * P.nb + (i >> 5)];
                         store_row = kr != 0;
                         store_col = kcl != 0;
-                        seg0 = outp + pool_index(kr, 0, i & 31, jb & 31);
-                        col0p = outp + pool_index(kcl, 0, jb & 31, i & 31);
+                        const int onp = plane_pairs(s_out);
+                        seg0 = outp + pool_index(kr, onp, 0, i & 31, jb & 31);
+                        col0p = outp + pool_index(kcl, onp, 0, jb & 31, i & 31);
                         col_step = 64;
                         pair_step = 32 * 64;
                     } else {

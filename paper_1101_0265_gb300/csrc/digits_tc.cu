@@ -132,7 +132,7 @@ __device__ __forceinline__ void split_strip(const double* __restrict__ F, int64_
                 z[c] = df_scale(z[c], rscale);
             }
             if constexpr (POOLED)
-                *(uint2*)(out + pool_index(slot, p, r, j0 & 31)) = *(const uint2*)dv;
+                *(uint2*)(out + pool_index(slot, plane_pairs(s), p, r, j0 & 31)) = *(const uint2*)dv;
             else
                 *(uint2*)(dst + (size_t)(p >> 1) * 2 * total + ((p & 1) << 5)) = *(const uint2*)dv;
             plane_scale *= rinv;
@@ -248,14 +248,15 @@ int make_plane_map(CUtensorMap* map, const __nv_bfloat16* planes, int n_pad, int
     return r == CUDA_SUCCESS ? PURIFY_OK : PURIFY_ERR_CUDA;
 }
 
-// 3D map over a pool of 32 x 32 block slots (pool_index): dims {64, 32,
-// 3 slots}, box {64, 32, 1}: one block of one plane pair per box, 128-byte
-// swizzle (the same shared-memory image as the rows of a dense panel).
-int make_pool_map(CUtensorMap* map, const __nv_bfloat16* pool, int slots) {
+// 3D map over a pool of 32 x 32 block slots of np plane pairs (pool_index):
+// dims {64, 32, np slots}, box {64, 32, 1}: one block of one plane pair per
+// box, 128-byte swizzle (the same shared-memory image as the rows of a dense
+// panel).
+int make_pool_map(CUtensorMap* map, const __nv_bfloat16* pool, int slots, int np) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return PURIFY_ERR_UNSUPPORTED;
-    if (((uintptr_t)pool & 15) || slots < 1) return PURIFY_ERR_INVALID_ARG;
-    cuuint64_t dims[3] = {64, 32, (cuuint64_t)slots * 3};
+    if (((uintptr_t)pool & 15) || slots < 1 || np < 1 || np > 3) return PURIFY_ERR_INVALID_ARG;
+    cuuint64_t dims[3] = {64, 32, (cuuint64_t)slots * np};
     cuuint64_t strides[2] = {128, 32 * 128};
     cuuint32_t box[3] = {64, 32, 1};
     cuuint32_t estr[3] = {1, 1, 1};
@@ -347,8 +348,8 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
     const int kc = digit_step_kc(st);
     if (st.a_idx) {
         if (!st.b_idx || (st.out && !st.out_idx) || st.a_slots < 1 || st.b_slots < 1) return PURIFY_ERR_INVALID_ARG;
-        PURIFY_TRY(make_pool_map(ma, st.A, st.a_slots));
-        PURIFY_TRY(make_pool_map(mb, st.B, st.b_slots));
+        PURIFY_TRY(make_pool_map(ma, st.A, st.a_slots, plane_pairs(st.s_in)));
+        PURIFY_TRY(make_pool_map(mb, st.B, st.b_slots, plane_pairs(st.s_in)));
     } else {
         PURIFY_TRY(make_plane_map(ma, st.A, st.n_pad, st.s_in, kc));
         PURIFY_TRY(make_plane_map(mb, st.B, st.n_pad, st.s_in, kc));

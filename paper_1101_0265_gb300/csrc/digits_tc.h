@@ -77,7 +77,8 @@ struct DigitStep {
     long long wait_cycles = 0;
     // pooled planes (block-sparse runs): A, B and out are pools of 32 x 32
     // block slots (slot 0 the zero block) with nb x nb slot tables in device
-    // memory; a_slots and b_slots are the pools' capacities.  Null: dense
+    // memory; a_slots and b_slots are the pools' capacities in slots of
+    // pool_slot_bytes(s_in), the output pool's slots hold s_out planes.  Null: dense
     // paired planes.
     const int* a_idx = nullptr;
     const int* b_idx = nullptr;
@@ -137,9 +138,9 @@ int launch_digit_queue(int smax, bool uniform, const dk::DigitGemmParams* prm, c
                        int* ticket, const int4* work, int num_items, float2* scratch, int max_ctas, int* err,
                        cudaStream_t stream, long long wait_cycles);
 
-// Bytes of one pool slot: the six digit planes (three pairs) of a 32 x 32
-// block.
-constexpr size_t kPoolSlotBytes = 3 * 32 * 64 * 2;
+// Bytes of one pool slot: the s digit planes (plane_pairs(s) pairs) of a
+// 32 x 32 block.
+inline size_t pool_slot_bytes(int s) { return (size_t)plane_pairs(s) * 32 * 64 * 2; }
 
 // The split into pooled planes (block-sparse runs): block (I, J) of the s
 // planes of a F + b I goes to pool slot pidx[I nb + J] (pool_index; slot 0:

@@ -325,6 +325,7 @@ extern "C" int purify_estimate_gap(purify_t h, int lanczos_steps, double* homo_o
     PURIFY_CUDA_TRY(cudaStreamSynchronize(s));
     double tr_prev = c0 * (double)n + c1 * tf;
     // iterates in float64: X_i in Xf[(i + 1) & 1] (X_0 in Xf[1])
+    PURIFY_TRY(ensure_work(h));
     double* Xf[2] = {h->X[0], h->X[1]};
     int x = 0;
     const int n_pad = pad128(n);

@@ -154,4 +154,7 @@ int product_end(purify_ctx* h);
 // Sum of the bracketed product times of the last run (seconds), NaN if off.
 double product_seconds(purify_ctx* h);
 int ensure_red(purify_ctx* h, int64_t doubles);
+// Allocate the handle's second float64 iterate X[1] and product buffer S (at
+// its capacity) if they are not yet allocated.
+int ensure_work(purify_ctx* h);
 }  // namespace purify

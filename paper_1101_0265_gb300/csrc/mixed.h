@@ -72,12 +72,12 @@ struct MixedState {
     // slots (slot 0 the zero block), their nb x nb slot tables, and the work
     // list of a product's tiles
     __nv_bfloat16* pool[2] = {nullptr, nullptr};
-    size_t pool_slots[2] = {0, 0};
+    size_t pool_cap[2] = {0, 0};  // bytes
     int* pidx[2] = {nullptr, nullptr};
     size_t pidx_cap = 0;
     int4* pwork = nullptr;
     size_t pwork_cap = 0;
-    double pool_bytes_peak = 0.0;  // largest pool bytes held in the last run
+    double pool_bytes_peak = 0.0;  // most pool bytes in use at once in the last run
 };
 
 // Allocate (or grow) the handle's mixed-path buffers for a padded size

@@ -368,9 +368,18 @@ static int ensure_capacity(purify_ctx* h, int64_t n) {
     const size_t bytes = sizeof(double) * (size_t)n * (size_t)n;
     PURIFY_CUDA_TRY(cudaMalloc(&h->F, bytes));
     PURIFY_CUDA_TRY(cudaMalloc(&h->X[0], bytes));
-    PURIFY_CUDA_TRY(cudaMalloc(&h->X[1], bytes));
-    PURIFY_CUDA_TRY(cudaMalloc(&h->S, bytes));
     h->cap = n;
+    return PURIFY_OK;
+}
+
+// The second iterate and the product buffer (float64 runs, refinement, gap
+// estimation) at the handle's capacity, allocated on first use: block-sparse
+// and mixed runs hold only F and the density.
+int purify::ensure_work(purify_ctx* h) {
+    if (h->X[1] && h->S) return PURIFY_OK;
+    const size_t bytes = sizeof(double) * (size_t)h->cap * (size_t)h->cap;
+    if (!h->X[1]) PURIFY_CUDA_TRY(cudaMalloc(&h->X[1], bytes));
+    if (!h->S) PURIFY_CUDA_TRY(cudaMalloc(&h->S, bytes));
     return PURIFY_OK;
 }
 
@@ -728,6 +737,7 @@ static void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) 
 // Sets the trace of the last result and ||X - X^2||_F of its input.
 static int refine_f64(purify_ctx* h, int R) {
     if (R <= 0 || h->cur < 0) return PURIFY_OK;
+    PURIFY_TRY(ensure_work(h));
     PURIFY_TRY(ensure_red(h, 4 * (int64_t)(2 * R)));
     PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 8 * R, h->stream));
     int x = h->cur;
@@ -753,6 +763,7 @@ static int refine_f64(purify_ctx* h, int R) {
 
 static int run_fp64(purify_ctx* h, int scheme, double tol, int max_iter, double mu, Schedule& S,
                     bool trace_rule, int* iters_out, std::vector<double>& red_host) {
+    PURIFY_TRY(ensure_work(h));
     const int64_t n = h->n;
     const double lmin = h->b.lmin, lmax = h->b.lmax;
     int m = (int)S.alpha.size();

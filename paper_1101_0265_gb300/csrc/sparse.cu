@@ -430,21 +430,37 @@ int launch_scatter_coo(const int64_t* key, const double* v, int64_t nnz, double*
 
 namespace {
 
-// Pool k holds at least `slots` slots; a new allocation starts with slot 0
-// (the zero block) cleared.  Slots are never written across the reallocation:
-// the pool being resized is the one about to be filled.
-int ensure_pool(purify_ctx* h, int k, size_t slots) {
+// Pool k holds at least `bytes` bytes (capacity grows by a quarter beyond the
+// request, up to `max_bytes`).  The pool being resized is the one about to be
+// filled: nothing in it is kept.
+int ensure_pool(purify_ctx* h, int k, size_t bytes, size_t max_bytes) {
     MixedState* ms = h->mixed;
-    if (slots <= ms->pool_slots[k]) return PURIFY_OK;
+    if (bytes <= ms->pool_cap[k]) return PURIFY_OK;
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
     cudaFree(ms->pool[k]);
     ms->pool[k] = nullptr;
-    ms->pool_slots[k] = 0;
-    const size_t c = slots + slots / 4 + 16;
-    PURIFY_CUDA_TRY(cudaMalloc(&ms->pool[k], c * kPoolSlotBytes));
-    ms->pool_slots[k] = c;
-    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->pool[k], 0, kPoolSlotBytes, h->stream));
+    ms->pool_cap[k] = 0;
+    const size_t c = std::max(bytes, std::min(bytes + bytes / 4 + (64 << 10), max_bytes));
+    PURIFY_CUDA_TRY(cudaMalloc(&ms->pool[k], c));
+    ms->pool_cap[k] = c;
     return PURIFY_OK;
+}
+
+// Copy the kept blocks of a pool into a compact one: block (I, J) with slot
+// d = didx[I nb + J] != 0 receives slot sidx[I nb + J] of src (np plane
+// pairs per slot).  One warp per table entry.
+__global__ void compact_slots_kernel(const __nv_bfloat16* __restrict__ src, const int* __restrict__ sidx,
+                                     __nv_bfloat16* __restrict__ dst, const int* __restrict__ didx, int nb, int np) {
+    const int lane = threadIdx.x & 31;
+    const int total = nb * nb;  // nb <= 4096
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total; e += warps) {
+        const int d = didx[e];
+        if (d == 0) continue;
+        const uint4* from = (const uint4*)(src + (size_t)sidx[e] * np * 2048);
+        uint4* to = (uint4*)(dst + (size_t)d * np * 2048);
+        for (int q = lane; q < np * 256; q += 32) to[q] = from[q];
+    }
 }
 
 // Slot table of a pattern (every block of it, both triangles): slots 1, 2,
@@ -472,11 +488,14 @@ void pattern_tiles(const Pattern& out, int T, std::vector<int4>& work) {
     }
 }
 
-int upload_slots(purify_ctx* h, int k, const std::vector<int>& idx) {
-    return cudaMemcpyAsync(h->mixed->pidx[k], idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice,
-                           h->stream) == cudaSuccess
-               ? PURIFY_OK
-               : PURIFY_ERR_CUDA;
+// Table k and a zero slot 0 for a pool whose slots hold s planes (slot 0
+// is cleared each time: slots of another size may have overlapped it).
+int upload_slots(purify_ctx* h, int k, const std::vector<int>& idx, int s) {
+    MixedState* ms = h->mixed;
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->pidx[k], idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice,
+                                    h->stream));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->pool[k], 0, pool_slot_bytes(s), h->stream));
+    return PURIFY_OK;
 }
 
 }  // namespace
@@ -546,16 +565,20 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
         select_drops(X, bn2.data(), tau, drop);
     }
     ms->nnzb_history.push_back(X.count_upper());
+    // pool 0 holds the current iterate compactly (its kept blocks), pool 1
+    // the product's output pattern before truncation; after each truncation
+    // the kept blocks move from pool 1 into pool 0
+    const size_t max_bytes = ((size_t)nb * nb + 1) * pool_slot_bytes(kMaxDigitPlanes);
     std::vector<int> idx;
-    size_t used[2] = {assign_slots(X, idx), 0};
-    PURIFY_TRY(ensure_pool(h, 0, used[0]));
-    PURIFY_TRY(upload_slots(h, 0, idx));
+    size_t used0 = assign_slots(X, idx);
+    PURIFY_TRY(ensure_pool(h, 0, used0 * pool_slot_bytes(s0), max_bytes));
+    PURIFY_TRY(upload_slots(h, 0, idx, s0));
     PURIFY_TRY(launch_split_pool(h->F, n, n, n_pad, c1, c0, 0, s0, rb, ms->pool[0], ms->pidx[0], nullptr,
                                  h->stream));
+    ms->pool_bytes_peak = (double)(used0 * pool_slot_bytes(s0));
 
     double* D = h->X[0];
     *cur = 0;
-    int x = 0;
     std::vector<int> cnt;
     std::vector<uint64_t> mask;
     std::vector<int4> work;
@@ -563,7 +586,7 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     const size_t cnt_words = (tiles + 1) / 2;  // the counts, two ints per word
     const double pairs_tile = 2.0 * 128.0 * 128.0 * 32.0;  // one pair, one 32-wide k-chunk
     for (int i = 0; i < m; ++i) {
-        const int s = sd[i];
+        const int s = sd[i], so = sd[i + 1];
         const bool last = (i + 1 == m);
         Pattern out;
         output_pattern(X, out);
@@ -583,23 +606,24 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
             const int c = cnt[(size_t)w.z * (w.z + 1) / 2 + w.y];
             chunks += c < 0 ? (double)nb : (double)c;
         }
+        size_t used1 = 0;
         if (!last) {
-            used[x ^ 1] = assign_slots(out, idx);
-            PURIFY_TRY(ensure_pool(h, x ^ 1, used[x ^ 1]));
-            PURIFY_TRY(upload_slots(h, x ^ 1, idx));
+            used1 = assign_slots(out, idx);
+            PURIFY_TRY(ensure_pool(h, 1, used1 * pool_slot_bytes(so), max_bytes));
+            PURIFY_TRY(upload_slots(h, 1, idx, so));
         } else if (work.size() < tiles) {
             // tiles outside the work list are not written
             PURIFY_CUDA_TRY(cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, h->stream));
         }
-        ms->pool_bytes_peak =
-            std::max(ms->pool_bytes_peak, (double)(used[0] + (last ? 0 : used[1])) * kPoolSlotBytes);
+        ms->pool_bytes_peak = std::max(ms->pool_bytes_peak,
+                                       (double)(used0 * pool_slot_bytes(s) + used1 * pool_slot_bytes(so)));
         DigitStep st;
         st.n = n;
         st.n_pad = n_pad;
         st.rbits = rb;
-        st.A = st.B = ms->pool[x];
-        st.a_idx = st.b_idx = ms->pidx[x];
-        st.a_slots = st.b_slots = (int)ms->pool_slots[x];
+        st.A = st.B = ms->pool[0];
+        st.a_idx = st.b_idx = ms->pidx[0];
+        st.a_slots = st.b_slots = (int)(ms->pool_cap[0] / pool_slot_bytes(s));
         st.s_in = s;
         st.eA = st.eB = 0;
         st.use_E = 1;
@@ -615,9 +639,9 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
         if (last) {
             st.out64 = D;
         } else {
-            st.out = ms->pool[x ^ 1];
-            st.out_idx = ms->pidx[x ^ 1];
-            st.s_out = sd[i + 1];
+            st.out = ms->pool[1];
+            st.out_idx = ms->pidx[1];
+            st.s_out = so;
             st.e_out = 0;
         }
         PURIFY_TRY(product_begin(h));
@@ -626,10 +650,24 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
         ++h->st.product_launches;
         h->st.tensor_flops += 0.5 * s * (s + 1) * pairs_tile * chunks;
         PURIFY_TRY(product_end(h));
-        PURIFY_TRY(truncate_step(h, out, tau, last ? nullptr : ms->pidx[x ^ 1], last ? D : nullptr, n));
+        PURIFY_TRY(truncate_step(h, out, tau, last ? nullptr : ms->pidx[1], last ? D : nullptr, n));
         X = out;
         ms->nnzb_history.push_back(X.count_upper());
-        x ^= 1;
+        if (!last) {
+            // the kept blocks into pool 0 (the step that read it is complete:
+            // truncate_step waited for the stream)
+            used0 = assign_slots(X, idx);
+            PURIFY_TRY(ensure_pool(h, 0, used0 * pool_slot_bytes(so), max_bytes));
+            PURIFY_TRY(upload_slots(h, 0, idx, so));
+            const int total_warps = nb * nb;
+            const unsigned grid = (unsigned)std::min(152 * 8, (total_warps + 7) / 8);
+            compact_slots_kernel<<<grid, 256, 0, h->stream>>>(ms->pool[1], ms->pidx[1], ms->pool[0], ms->pidx[0], nb,
+                                                               plane_pairs(so));
+            PURIFY_CUDA_TRY(cudaGetLastError());
+            count_launches(1);
+            ms->pool_bytes_peak = std::max(ms->pool_bytes_peak,
+                                           (double)((used0 + used1) * pool_slot_bytes(so)));
+        }
     }
     if (m == 0) PURIFY_TRY(launch_affine_f64(h->F, n, D, n, c1, c0, h->stream));
     PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
