@@ -227,7 +227,7 @@ def run_serve(P, dev, stream, rate, count, budget_gb=64.0, tol=1e-9, advance=4):
 
 
 def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsite=3.0,
-                sweeps=((6.0, (16, 20, 24, 28, 32)), (3.0, (16, 24, 32, 40)))):
+                sweeps=((6.0, (16, 20, 24, 28, 32, 40, 48, 56)), (3.0, (16, 24, 32, 40)))):
     """The block-sparse workload: periodic L^3 cubic tight-binding lattice
     (onsite +-0.5 by sublattice + N(0, 0.05), hopping -1 + U(-0.1, 0.1)),
     n = L^3, nocc = n/2, mu = 0, loaded from COO, 32 x 32 blocks.
@@ -306,7 +306,8 @@ def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsi
                           "kept_blocks_per_block_row": 2 * kept / nb, "final_fill": r["final_fill"],
                           "max_fill": max(r["nnz_blocks"]) / (nb * (nb + 1) / 2),
                           "plane_pool_mib": r["plane_pool_mib"],
-                          "dense_planes_mib": 2 * 6 * n_pad * n_pad * 2 / 2**20, "trace_err": r["trace_err"]})
+                          "dense_planes_mib": 2 * 6 * n_pad * n_pad * 2 / 2**20,
+                          "dense_fd_mib": 2 * 8 * lt.n * lt.n / 2**20, "trace_err": r["trace_err"]})
     for pur in pool.values():
         pur.close()
     torch.cuda.empty_cache()
@@ -314,9 +315,10 @@ def run_lattice(P, dev, stream, L=32, tau=1e-6, tol=1e-9, budget=2e-5, wide_onsi
                         f"32x32 blocks, tol {tol:g}",
             "n": lat.n, "C3": c3, "equal_budget": eq,
             "n_sweep": {"tau": tau, "scheme": "TC_SF block-sparse", "runs": sweep,
-                        "note": "plane_pool_mib: peak of the two block pools that hold the iterates' digit "
-                                "planes (12 KB per kept 32x32 block, both triangles); dense_planes_mib: two "
-                                "dense 6-plane buffers at the same size"}}
+                        "note": "plane_pool_mib: peak MiB of the block pools (the iterates' digit planes, "
+                                "plane_pairs(s) x 4 KB per 32x32 block, and the last step's float64 density "
+                                "blocks, 8 KB each); dense_planes_mib: two dense 6-plane buffers; dense_fd_mib: "
+                                "a dense float64 F and D, which a CSR-loaded block-sparse handle does not hold"}}
 
 
 def peaks():

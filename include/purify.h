@@ -244,7 +244,10 @@ int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld,
  * cols[k], vals[k], 0-based, both triangles present) into the handle's dense
  * float64 copy; otherwise as purify_set_hamiltonian.  Duplicates are summed in
  * input order; the summed (i, j) and (j, i) entries must be equal, else
- * PURIFY_ERR_INVALID_ARG (so is an index outside [0, n)). */
+ * PURIFY_ERR_INVALID_ARG (so is an index outside [0, n)).  A handle with
+ * block_sparse = 1 and MIXED precision keeps F in CSR form instead (no n x n
+ * array; n up to 2^18): the bound estimate and the block-sparse run read the
+ * CSR form, and any other path makes the dense copy when it first needs it. */
 int purify_set_hamiltonian_coo(purify_t h, int64_t n, int64_t nnz, const int64_t* rows,
                                const int64_t* cols, const double* vals, int64_t nocc, double mu,
                                const purify_bounds* b);
@@ -276,6 +279,16 @@ int purify_tuned_shape(int device, int digits, int64_t n, int* kc, int* split_wa
 /* Block-sparse runs: the number of upper 32 x 32 blocks kept after the
  * truncation of X_0 and of every step (count <= cap entries written). */
 int purify_block_history(purify_t h, int* nnz_blocks, int cap, int* count);
+
+/* Block-sparse runs keep the density as its kept 32 x 32 blocks (the blocks
+ * that survived the last truncation; purify_get_density expands them into
+ * an n x n array).  This copies them out: *count receives the number of kept
+ * blocks with I <= J (their (I, J) in row-major order); at most cap of them
+ * are written, block_ij[2k], block_ij[2k + 1] = (I, J) and values[1024 k ..
+ * 1024 k + 1023] = the block's rows (row-major, entries at rows or columns
+ * >= n are 0).  block_ij and values may be host or device memory, either may
+ * be NULL.  PURIFY_ERR_STATE unless the last run was block-sparse. */
+int purify_get_density_blocks(purify_t h, int32_t* block_ij, double* values, int64_t cap, int64_t* count);
 
 /* Run `scheme` until the bound of the scheme's scalar recursion (beta for
  * Algorithm 1, max(beta, 1 - beta_bar) for Algorithm 2) is <= tol, or, for
@@ -309,7 +322,8 @@ int purify_stats(purify_t h, purify_stats_t* out);
 int purify_step_history(purify_t h, double* trace, double* idem, int cap, int* count);
 
 /* Device pointer of the handle's current density (n x n, leading dimension
- * n, float64), valid until the next set/run/destroy; NULL before a run. */
+ * n, float64), valid until the next set/run/destroy; NULL before a run and
+ * after a block-sparse run (see purify_get_density_blocks). */
 const double* purify_density_device_ptr(purify_t h);
 
 /* Human-readable name of a status code (static string). */

@@ -34,7 +34,8 @@ BRANCH_RULES = {"beta": 0, "trace": 1}
 
 EXPORTED = (
     "purify_options_default", "purify_create", "purify_destroy", "purify_set_options",
-    "purify_set_hamiltonian", "purify_set_hamiltonian_coo", "purify_block_history", "purify_estimate_gap",
+    "purify_set_hamiltonian", "purify_set_hamiltonian_coo", "purify_block_history", "purify_get_density_blocks",
+    "purify_estimate_gap",
     "purify_tuned_shape", "purify_k_split_plan",
     "purify_run", "purify_get_density", "purify_stats", "purify_step_history",
     "purify_density_device_ptr", "purify_strerror", "purify_schedule", "purify_tridiag_eig",
@@ -105,6 +106,7 @@ def load(path: str = LIB_PATH):
         "purify_run": (ip, [vp, ip, dbl, ip]),
         "purify_set_hamiltonian_coo": (ip, [vp, i64, i64, vp, vp, vp, i64, dbl, C.POINTER(Bounds)]),
         "purify_block_history": (ip, [vp, C.POINTER(C.c_int), ip, C.POINTER(C.c_int)]),
+        "purify_get_density_blocks": (ip, [vp, vp, vp, i64, C.POINTER(C.c_int64)]),
         "purify_tuned_shape": (ip, [ip, ip, i64, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "purify_k_split_plan": (ip, [ip, ip, ip, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "purify_estimate_gap": (ip, [vp, ip, dp, dp]),
@@ -314,6 +316,20 @@ class Purifier:
         ld = int(out.strides[0] // 8) if isinstance(out, np.ndarray) else int(out.stride(0))
         _check(self._lib.purify_get_density(self._h, _ptr(out), ld), "purify_get_density")
         return out
+
+    def density_blocks(self, values: bool = True):
+        """The kept 32 x 32 blocks of a block-sparse run's density: an
+        (m, 2) int32 array of (I, J), I <= J, and an (m, 32, 32) float64
+        array of the blocks (None when values is False)."""
+        cnt = C.c_int64(0)
+        _check(self._lib.purify_get_density_blocks(self._h, None, None, 0, C.byref(cnt)),
+               "purify_get_density_blocks")
+        m = cnt.value
+        ij = np.empty((max(m, 1), 2), dtype=np.int32)
+        vals = np.empty((max(m, 1), 32, 32), dtype=np.float64) if values else None
+        _check(self._lib.purify_get_density_blocks(self._h, _ptr(ij), _ptr(vals) if values else None, m,
+                                                    C.byref(cnt)), "purify_get_density_blocks")
+        return ij[:m], (vals[:m] if values else None)
 
     def density_device_ptr(self) -> int:
         return self._lib.purify_density_device_ptr(self._h) or 0

@@ -330,6 +330,24 @@ __host__ __device__ inline size_t pool_index(int k, int np, int p, int r, int c)
     return ((size_t)(k * np + (p >> 1)) * 32 + r) * 64 + ((p & 1) << 5) + c;
 }
 
+// Pooled runs: kc_mask holds one bitset of kc_words words per 128-row panel
+// (the block columns in which one of the panel's four block rows has a
+// block); tile (ti, tj) walks the k-chunks set in both panels' bitsets.
+__device__ __forceinline__ unsigned long long pool_chunk_word(const DigitGemmParams& P, int ti, int tj, int w) {
+    return P.kc_mask[(size_t)ti * P.kc_words + w] & P.kc_mask[(size_t)tj * P.kc_words + w];
+}
+__device__ __forceinline__ int pool_chunk_count(const DigitGemmParams& P, int ti, int tj) {
+    int c = 0;
+    for (int w = 0; w < P.kc_words; ++w) c += __popcll(pool_chunk_word(P, ti, tj, w));
+    return c;
+}
+// (warp-collective) whether tile (ti, tj) has any k-chunk
+__device__ __forceinline__ bool pool_chunks_any(const DigitGemmParams& P, int ti, int tj, int lane) {
+    unsigned long long a = 0ull;
+    for (int w = lane; w < P.kc_words; w += 32) a |= pool_chunk_word(P, ti, tj, w);
+    return __any_sync(0xffffffffu, a != 0ull);
+}
+
 // Products per grouped launch, whose tensor maps and parameters travel as
 // kernel parameters (grid constants).  Queue launches read theirs from
 // global memory instead, each CTA fencing a map through the tensor-map proxy
@@ -685,8 +703,11 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 item_of(L, t, g, ti, tj, slot, part);
                 const DigitGemmParams& Pg = params_of<Q>(L, g);
                 const int tix = tj * (tj + 1) / 2 + ti;
-                const int cnt = Pg.kc_cnt ? Pg.kc_cnt[tix] : -1;  // -1: every k-chunk
-                const unsigned long long* km = cnt >= 0 ? Pg.kc_mask + (size_t)tix * Pg.kc_words : nullptr;
+                // -1: every k-chunk
+                const int cnt = POOL ? pool_chunk_count(Pg, ti, tj) : (Pg.kc_cnt ? Pg.kc_cnt[tix] : -1);
+                const unsigned long long* km =
+                    (!POOL && cnt >= 0) ? Pg.kc_mask + (size_t)tix * Pg.kc_words : nullptr;
+                const bool masked = POOL || km != nullptr;
                 int kb, nk;
                 dense_k_range(L, Pg.n_pad / KC, slot, part, kb, nk);
                 if (cnt >= 0) nk = cnt;
@@ -707,11 +728,14 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     }
                 }
                 int w = 0;
-                unsigned long long bits = km ? km[0] : 0ull;
+                unsigned long long bits = POOL ? pool_chunk_word(Pg, ti, tj, 0) : (km ? km[0] : 0ull);
                 for (int c = 0; c < nk; ++c, ++it) {
                     int kc = kb + c;
-                    if (km) {
-                        while (bits == 0ull && w + 1 < Pg.kc_words) bits = km[++w];
+                    if (masked) {
+                        while (bits == 0ull && w + 1 < Pg.kc_words) {
+                            ++w;
+                            bits = POOL ? pool_chunk_word(Pg, ti, tj, w) : km[w];
+                        }
                         if (bits == 0ull) {  // count and mask disagree
                             atomicOr(L.err, ERR_PLAN);
                             *abort_flag = 1;
@@ -773,7 +797,8 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 int g, ti, tj, slot, part;
                 item_of(L, t, g, ti, tj, slot, part);
                 const DigitGemmParams& Pg = params_of<Q>(L, g);
-                const int nl = Pg.kc_cnt ? Pg.kc_cnt[tj * (tj + 1) / 2 + ti] : -1;
+                const int nl = POOL ? pool_chunk_count(Pg, ti, tj)
+                                    : (Pg.kc_cnt ? Pg.kc_cnt[tj * (tj + 1) / 2 + ti] : -1);
                 const int s_it = QRT ? Pg.s_in : S;
                 int kb, nk;
                 dense_k_range(L, Pg.n_pad / KC, slot, part, kb, nk);
@@ -844,7 +869,8 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
             tc_fence_after();
             // phase 1: accumulators -> double-float P in scratch; release TMEM
             // (a tile with no k-chunk of either operand has P = 0)
-            const bool empty = P.kc_cnt && P.kc_cnt[tj * (tj + 1) / 2 + ti] == 0;
+            const bool empty = POOL ? !pool_chunks_any(P, ti, tj, lane)
+                                    : (P.kc_cnt && P.kc_cnt[tj * (tj + 1) / 2 + ti] == 0);
             const int nacc = empty ? 0 : (s < NUM_ACC ? s : NUM_ACC);
             if (slot >= 0) {
                 // a part of a split tile: publish this region's accumulators
@@ -1113,7 +1139,23 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     for (int c = 0; c < EW / 2; ++c) pv_next[c] = src[(c >> 2) * 128 + (c & 3)];
                 }
                 // float64 output (n x n): row segment and its mirror column
-                if (out64 && i < n) {
+                if (POOL && out64 && i < n) {
+                    // pooled: 32 x 32 float64 blocks (i / 32, jb / 32) and its
+                    // mirror in the slots the output table gives (0: not stored)
+                    const int kr = P.out_idx[(size_t)(i >> 5) * P.nb + (jb >> 5)];
+                    const int kcl = P.out_idx[(size_t)(jb >> 5) * P.nb + (i >> 5)];
+                    double* const o_row = out64 + (size_t)kr * 1024 + (i & 31) * 32 + (jb & 31);
+                    double* const o_col = out64 + (size_t)kcl * 1024 + (jb & 31) * 32 + (i & 31);
+#pragma unroll
+                    for (int c = 0; c < EW; ++c) {
+                        const int j = jb + c;
+                        if (j < n && (!diag_tile || i <= j)) {
+                            const double v = (double)Ov[c].h + (double)Ov[c].l;
+                            if (kr) o_row[c] = v;
+                            if (i != j && kcl) o_col[c * 32] = v;
+                        }
+                    }
+                } else if (out64 && i < n) {
                     double* const o_row = out64 + (size_t)i * n;
                     double* const o_col = out64 + (size_t)jb * n + i;
 #pragma unroll

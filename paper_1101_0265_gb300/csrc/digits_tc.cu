@@ -67,16 +67,69 @@ __device__ __forceinline__ df split_entry(double x) {
     return (E >= -74 && E <= 127) ? split_double_bits(hi, lo) : split_double_slow(x);
 }
 
+// F's entries (i, j0 .. j0 + 3) of a strip row, from dense storage.
+struct DenseRows {
+    const double* F;
+    int64_t ldf;
+    int n;
+    bool vec;
+    __device__ __forceinline__ void operator()(int i, int j0, int, double (&x)[4]) const {
+        x[0] = x[1] = x[2] = x[3] = 0.0;
+        if (i >= n) return;
+        const double* row = F + (int64_t)i * ldf + j0;
+        if (vec && j0 + 3 < n) {
+            const double2 u0 = __ldg((const double2*)row), u1 = __ldg((const double2*)row + 1);
+            x[0] = u0.x;
+            x[1] = u0.y;
+            x[2] = u1.x;
+            x[3] = u1.y;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (j0 + c < n) x[c] = __ldg(row + c);
+        }
+    }
+};
+
+// The same entries from CSR storage (warp-collective: the warp gathers row
+// i's entries in the strip's 128 columns into its shared-memory row buffer,
+// then each lane reads its four).  Absent entries are zero.
+struct CsrRows {
+    const int64_t* ptr;
+    const int* col;
+    const double* val;
+    int n;
+    double* buf;  // 128 doubles per warp
+    __device__ __forceinline__ void operator()(int i, int j0, int lane, double (&x)[4]) const {
+        const int c0 = j0 - 4 * lane;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) buf[4 * lane + c] = 0.0;
+        __syncwarp();
+        if (i < n) {
+            const int64_t p1 = ptr[i + 1];
+            for (int64_t k = ptr[i] + lane; k < p1; k += 32) {
+                const int j = col[k];
+                if (j >= c0 && j < c0 + 128) buf[j - c0] = val[k];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = buf[4 * lane + c];
+        __syncwarp();
+    }
+};
+
 // One 32 x 128 strip of the split (see split_kernel); tr accumulates the
 // diagonal's trace (float), the strip's block norms go to bnorm2 when set.
 // POOLED: the planes go to the pool slots that pidx (nb x nb) gives the
 // blocks (slot 0: not written); a null pidx writes nothing (norms only).
-template <bool POOLED>
-__device__ __forceinline__ void split_strip(const double* __restrict__ F, int64_t ldf, int n, int n_pad, df a, df b,
-                                            float digit_scale, float rscale, float rinv, int s,
-                                            __nv_bfloat16* __restrict__ out, float* __restrict__ bnorm2, bool vec,
-                                            int strip, int lane, float& tr, const int* __restrict__ pidx = nullptr) {
-    const int nb = n_pad / 32, ns = n_pad / 128;  // nb^2 <= 2^24: 32-bit block indices
+// `rows` reads F's entries (DenseRows or CsrRows).
+template <bool POOLED, class Rows>
+__device__ __forceinline__ void split_strip(const Rows& rows, int n, int n_pad, df a, df b, float digit_scale,
+                                            float rscale, float rinv, int s, __nv_bfloat16* __restrict__ out,
+                                            float* __restrict__ bnorm2, int strip, int lane, float& tr,
+                                            const int* __restrict__ pidx = nullptr) {
+    const int nb = n_pad / 32, ns = n_pad / 128;  // nb^2 < 2^27: 32-bit block indices
     const int64_t total = (int64_t)n_pad * n_pad;
     const int I = strip / ns, Jq = strip - I * ns;
     const int j0 = Jq * 128 + lane * 4;
@@ -86,21 +139,8 @@ __device__ __forceinline__ void split_strip(const double* __restrict__ F, int64_
 #pragma unroll 2
     for (int r = 0; r < 32; ++r) {  // two rows' loads in flight per warp
         const int i = I * 32 + r;
-        double x[4] = {0.0, 0.0, 0.0, 0.0};
-        if (i < n) {
-            const double* row = F + (int64_t)i * ldf + j0;
-            if (vec && j0 + 3 < n) {
-                const double2 u0 = __ldg((const double2*)row), u1 = __ldg((const double2*)row + 1);
-                x[0] = u0.x;
-                x[1] = u0.y;
-                x[2] = u1.x;
-                x[3] = u1.y;
-            } else {
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (j0 + c < n) x[c] = __ldg(row + c);
-            }
-        }
+        double x[4];
+        rows(i, j0, lane, x);
         df z[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -116,7 +156,7 @@ __device__ __forceinline__ void split_strip(const double* __restrict__ F, int64_
             bsum += z[c].h * z[c].h;
             z[c] = df_scale(z[c], digit_scale);
         }
-        if (POOLED && slot == 0) continue;
+        if (POOLED && slot == 0) continue;  // (after rows(): every lane takes part in each row's read)
         // plane p at out + plane_index(p, i, j0, n_pad): pairs 2 total apart
         __nv_bfloat16* dst = out + (size_t)i * 2 * n_pad + ((j0 >> 5) << 6) + (j0 & 31);
         float plane_scale = 1.f;
@@ -159,7 +199,8 @@ __global__ void __launch_bounds__(256) split_kernel(const double* __restrict__ F
     const float rinv = 1.f / rscale;
     float tr = 0.f;
     for (int strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); strip < nb * ns; strip += warps)
-        split_strip<false>(F, ldf, n, n_pad, a, b, digit_scale, rscale, rinv, s, out, bnorm2, vec, strip, lane, tr);
+        split_strip<false>(DenseRows{F, ldf, n, vec}, n, n_pad, a, b, digit_scale, rscale, rinv, s, out, bnorm2, strip,
+                           lane, tr);
     if (red) {
         tr = warp_sum_f(tr);
         if (lane == 0) atomicAdd(red, (double)tr);
@@ -188,8 +229,8 @@ __global__ void __launch_bounds__(256) split_group_kernel(const SplitJob* __rest
         if (strip == 0 && J.zero4 && lane < 4) J.zero4[lane] = 0.0;
         const bool vec = (J.ldf & 1) == 0 && ((uintptr_t)J.F & 15) == 0;
         float tr = 0.f;
-        split_strip<false>(J.F, J.ldf, J.n, J.n_pad, df{J.a_h, J.a_l}, df{J.b_h, J.b_l}, J.digit_scale, J.rscale,
-                           1.f / J.rscale, J.s, J.out, nullptr, vec, strip, lane, tr);
+        split_strip<false>(DenseRows{J.F, J.ldf, J.n, vec}, J.n, J.n_pad, df{J.a_h, J.a_l}, df{J.b_h, J.b_l},
+                           J.digit_scale, J.rscale, 1.f / J.rscale, J.s, J.out, nullptr, strip, lane, tr);
     }
 }
 
@@ -206,7 +247,27 @@ __global__ void __launch_bounds__(256) split_pool_kernel(const double* __restric
     const float rinv = 1.f / rscale;
     float tr = 0.f;
     for (int strip = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); strip < nb * ns; strip += warps)
-        split_strip<true>(F, ldf, n, n_pad, a, b, digit_scale, rscale, rinv, s, pool, bnorm2, vec, strip, lane, tr,
+        split_strip<true>(DenseRows{F, ldf, n, vec}, n, n_pad, a, b, digit_scale, rscale, rinv, s, pool, bnorm2, strip,
+                          lane, tr, pidx);
+}
+
+// The pooled split from CSR storage, over a list of strips (I * (n_pad /
+// 128) + 128-column segment): the strips that hold a block of the pattern.
+__global__ void __launch_bounds__(256) split_csr_pool_kernel(const int64_t* __restrict__ ptr,
+                                                             const int* __restrict__ col,
+                                                             const double* __restrict__ val, int n, int n_pad, df a,
+                                                             df b, float digit_scale, float rscale, int s,
+                                                             __nv_bfloat16* __restrict__ pool,
+                                                             const int* __restrict__ pidx, float* __restrict__ bnorm2,
+                                                             const int* __restrict__ strips, int nstrips) {
+    __shared__ double rowbuf[8][128];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const float rinv = 1.f / rscale;
+    const CsrRows rows{ptr, col, val, n, rowbuf[warp]};
+    float tr = 0.f;
+    for (int q = blockIdx.x * (blockDim.x >> 5) + warp; q < nstrips; q += warps)
+        split_strip<true>(rows, n, n_pad, a, b, digit_scale, rscale, rinv, s, pool, bnorm2, strips[q], lane, tr,
                           pidx);
 }
 
@@ -347,7 +408,11 @@ int fill_digit_params(const DigitStep& st, DigitGemmParams* p, CUtensorMap* ma, 
     if (st.rbits < 4 || st.rbits > 8) return PURIFY_ERR_INVALID_ARG;
     const int kc = digit_step_kc(st);
     if (st.a_idx) {
-        if (!st.b_idx || (st.out && !st.out_idx) || st.a_slots < 1 || st.b_slots < 1) return PURIFY_ERR_INVALID_ARG;
+        // (kc_mask: one block-column bitset per 128-row panel, see
+        // pool_chunk_word; out64: a pool of 32 x 32 float64 blocks)
+        if (!st.b_idx || ((st.out || st.out64) && !st.out_idx) || st.a_slots < 1 || st.b_slots < 1 || !st.kc_mask ||
+            st.kc_cnt)
+            return PURIFY_ERR_INVALID_ARG;
         PURIFY_TRY(make_pool_map(ma, st.A, st.a_slots, plane_pairs(st.s_in)));
         PURIFY_TRY(make_pool_map(mb, st.B, st.b_slots, plane_pairs(st.s_in)));
     } else {
@@ -575,6 +640,23 @@ int launch_split_pool(const double* F, int64_t ldf, int n, int n_pad, double a, 
     if (blocks > 152 * 8) blocks = 152 * 8;
     split_pool_kernel<<<(unsigned)blocks, 256, 0, stream>>>(F, ldf, n, n_pad, to_df(a), to_df(b), ldexpf(1.f, 8 - e),
                                                              ldexpf(1.f, rbits), s, pool, pidx, bnorm2);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return PURIFY_OK;
+}
+
+int launch_split_csr_pool(const int64_t* ptr, const int* col, const double* val, int n, int n_pad, double a,
+                          double b, int e, int s, int rbits, __nv_bfloat16* pool, const int* pidx, float* bnorm2,
+                          const int* strips, int nstrips, cudaStream_t stream) {
+    if (s < 1 || s > kMaxDigitPlanes || n <= 0 || n_pad < n || n_pad % 128 || n_pad > (1 << 18) || rbits < 4 ||
+        rbits > 8 || (pidx && !pool) || (!pidx && !bnorm2) || !ptr || nstrips < 0 || (nstrips && !strips))
+        return PURIFY_ERR_INVALID_ARG;
+    if (nstrips == 0) return PURIFY_OK;
+    int64_t blocks = ((int64_t)nstrips + 7) / 8;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    split_csr_pool_kernel<<<(unsigned)blocks, 256, 0, stream>>>(ptr, col, val, n, n_pad, to_df(a), to_df(b),
+                                                                 ldexpf(1.f, 8 - e), ldexpf(1.f, rbits), s, pool,
+                                                                 pidx, bnorm2, strips, nstrips);
     PURIFY_CUDA_TRY(cudaGetLastError());
     count_launches(1);
     return PURIFY_OK;

@@ -78,8 +78,10 @@ struct DigitStep {
     // pooled planes (block-sparse runs): A, B and out are pools of 32 x 32
     // block slots (slot 0 the zero block) with nb x nb slot tables in device
     // memory; a_slots and b_slots are the pools' capacities in slots of
-    // pool_slot_bytes(s_in), the output pool's slots hold s_out planes.  Null: dense
-    // paired planes.
+    // pool_slot_bytes(s_in), the output pool's slots hold s_out planes, and
+    // out64 (when set) is a pool of 32 x 32 row-major float64 blocks under
+    // out_idx.  kc_mask then holds one block-column bitset per 128-row panel
+    // and kc_cnt is null.  Null: dense paired planes.
     const int* a_idx = nullptr;
     const int* b_idx = nullptr;
     const int* out_idx = nullptr;
@@ -148,6 +150,15 @@ inline size_t pool_slot_bytes(int s) { return (size_t)plane_pairs(s) * 32 * 64 *
 // I <= J.  pidx null: the norms only.
 int launch_split_pool(const double* F, int64_t ldf, int n, int n_pad, double a, double b, int e, int s, int rbits,
                       __nv_bfloat16* pool, const int* pidx, float* bnorm2, cudaStream_t stream);
+
+// The same from F in CSR storage (row pointers ptr[n + 1], column indices
+// sorted within each row), over `nstrips` strips (I * (n_pad / 128) + the
+// 128-column segment; device array) that hold every block to be written or
+// measured; bnorm2 entries of other blocks are left as they are.  The digits
+// and norms are those launch_split_pool computes from the dense F.
+int launch_split_csr_pool(const int64_t* ptr, const int* col, const double* val, int n, int n_pad, double a,
+                          double b, int e, int s, int rbits, __nv_bfloat16* pool, const int* pidx, float* bnorm2,
+                          const int* strips, int nstrips, cudaStream_t stream);
 
 // Many splits in one launch (see launch_split): a job per matrix, its strips
 // (32 x 128 pieces of the padded matrix, split_strips of them) numbered from

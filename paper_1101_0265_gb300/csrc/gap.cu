@@ -319,6 +319,7 @@ extern "C" int purify_estimate_gap(purify_t h, int lanczos_steps, double* homo_o
     PURIFY_TRY(ensure_red(h, 4 * (int64_t)(max_steps + 1)));
     PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 4 * (max_steps + 1), s));
     double* trF = h->red + 4 * (int64_t)max_steps;
+    PURIFY_TRY(ensure_dense_F(h));
     PURIFY_TRY(launch_trace_f64(h->F, n, trF, s));
     double tf = 0.0;
     PURIFY_CUDA_TRY(cudaMemcpyAsync(&tf, trF, sizeof(double), cudaMemcpyDeviceToHost, s));

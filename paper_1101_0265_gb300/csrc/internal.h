@@ -53,13 +53,24 @@ int launch_mirror_upper_f64(double* X, int64_t n, cudaStream_t s);
 int launch_trace_f64(const double* X, int64_t n, double* red, cudaStream_t s);
 
 // ---- bounds (kernels_bounds.cu) ------------------------------------------
+// F in CSR storage (device arrays): row pointers ptr[n + 1], column indices
+// sorted within each row, values.
+struct CsrF {
+    const int64_t* ptr = nullptr;
+    const int* col = nullptr;
+    const double* val = nullptr;
+};
 int launch_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi,
                           double* scratch, cudaStream_t s);
+// The same discs from CSR storage (scratch as above).
+int launch_gershgorin_csr_f64(const CsrF& F, int64_t n, double* lohi, double* scratch, cudaStream_t s);
 int64_t gershgorin_scratch_doubles(int64_t n);
 // k Lanczos steps; scratch holds lanczos_scratch_doubles(n, k) doubles.
 // Writes a[0..k), bsq[0..k) (squared off-diagonals) into scratch tail; the
-// host copies them out (see purify_k_lanczos_f64).
-int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaStream_t s);
+// host copies them out (see purify_k_lanczos_f64).  csr set: the matvecs
+// read F from CSR storage and F (dense) is not used.
+int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaStream_t s,
+                       const CsrF* csr = nullptr);
 int64_t lanczos_scratch_doubles(int64_t n, int k);
 // Offsets of the a / bsq arrays inside the Lanczos scratch.
 inline int64_t lanczos_a_offset(int64_t n) { return 3 * n + 1; }
@@ -128,6 +139,18 @@ struct purify_ctx {
     int64_t scratch_cap = 0;  // doubles
     int cur = -1;
     bool have_F = false;
+    // F loaded from COO for a block-sparse handle: CSR in device memory, and
+    // F (dense) allocated and filled only when a dense path asks for it
+    int64_t* csr_ptr = nullptr;
+    int* csr_col = nullptr;
+    double* csr_val = nullptr;
+    int64_t csr_rows_cap = 0, csr_nnz_cap = 0, csr_nnz = 0;
+    bool csr_valid = false;  // csr_* hold the current F
+    bool F_dense = false;    // F holds the current F
+    // with csr_valid: F's 32 x 32 block pattern and the diagonal, nb rows of
+    // f_pattern_words 64-bit words (nb = padded n / 32)
+    std::vector<uint64_t> f_pattern;
+    int f_pattern_words = 0;
     int64_t nocc = -1;
     double mu = NAN;
     purify_bounds b{NAN, NAN, NAN, NAN};
@@ -157,4 +180,17 @@ int ensure_red(purify_ctx* h, int64_t doubles);
 // Allocate the handle's second float64 iterate X[1] and product buffer S (at
 // its capacity) if they are not yet allocated.
 int ensure_work(purify_ctx* h);
+// The handle's float64 scratch holds at least `doubles` doubles.
+int ensure_scratch(purify_ctx* h, int64_t doubles);
+// Make the dense F (and the density buffer X[0]) valid: from the CSR copy
+// when the Hamiltonian was loaded in block-sparse form.
+int ensure_dense_F(purify_ctx* h);
+// The current F as CSR (csr_valid) for the bounds and the block-sparse split.
+inline CsrF csr_of(const purify_ctx* h) {
+    CsrF c;
+    c.ptr = h->csr_ptr;
+    c.col = h->csr_col;
+    c.val = h->csr_val;
+    return c;
+}
 }  // namespace purify

@@ -77,6 +77,45 @@ gershgorin_rows_kernel(const double* __restrict__ F, int64_t n, int64_t ld, doub
     }
 }
 
+// The same discs from CSR storage (one warp per row; the diagonal entry is
+// the disc's centre, the other entries' magnitudes its radius).
+__global__ void __launch_bounds__(256)
+gershgorin_csr_kernel(const int64_t* __restrict__ ptr, const int* __restrict__ col, const double* __restrict__ val,
+                      int n, double* __restrict__ part) {
+    __shared__ double slo[ROWS_PER_CTA], shi[ROWS_PER_CTA];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = (int)blockIdx.x * ROWS_PER_CTA + warp;
+    double lo = INFINITY, hi = -INFINITY;
+    if (i < n) {
+        double r = 0.0, d = 0.0;
+        const int64_t p1 = ptr[i + 1];
+        for (int64_t k = ptr[i] + lane; k < p1; k += 32) {
+            const double v = val[k];
+            if (col[k] == i)
+                d = v;
+            else
+                r += abs_bits(v);
+        }
+        r = warp_sum(r);
+        d = warp_sum(d);  // one lane holds the diagonal entry, the others 0
+        lo = d - r;
+        hi = d + r;
+    }
+    if (lane == 0) {
+        slo[warp] = lo;
+        shi[warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < ROWS_PER_CTA; ++w) {
+            lo = fmin(lo, slo[w]);
+            hi = fmax(hi, shi[w]);
+        }
+        part[2 * blockIdx.x] = lo;
+        part[2 * blockIdx.x + 1] = hi;
+    }
+}
+
 __global__ void minmax_reduce_kernel(const double* __restrict__ part, int64_t m, double* lohi) {
     __shared__ double slo[32], shi[32];
     double lo = INFINITY, hi = -INFINITY;
@@ -212,6 +251,35 @@ lanczos_matvec_kernel(const double* __restrict__ F, int64_t n, const double* __r
     }
 }
 
+// The matvec from CSR storage (one warp per row).
+__global__ void __launch_bounds__(256)
+lanczos_matvec_csr_kernel(const int64_t* __restrict__ ptr, const int* __restrict__ col,
+                          const double* __restrict__ val, int n, const double* __restrict__ v,
+                          const double* __restrict__ vprev, double* __restrict__ w, const double* bsq_prev,
+                          double* pa) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int i = (int)blockIdx.x * LZ_ROWS + warp;
+    __shared__ double sdot[LZ_ROWS];
+    double dot = 0.0;
+    if (i < n) {
+        double s0 = 0.0;
+        const int64_t p1 = ptr[i + 1];
+        for (int64_t k = ptr[i] + lane; k < p1; k += 32) s0 = fma(val[k], v[col[k]], s0);
+        const double s = warp_sum(s0);
+        const double bprev = bsq_prev ? sqrt(*bsq_prev) : 0.0;
+        const double wi = s - bprev * vprev[i];
+        if (lane == 0) w[i] = wi;
+        dot = wi * v[i];
+    }
+    if (lane == 0) sdot[warp] = dot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < LZ_ROWS; ++q) t += sdot[q];
+        pa[blockIdx.x] = t;
+    }
+}
+
 // a_j = sum of the matvec partials; w -= a_j v; pb[block] = share of w . w
 __global__ void __launch_bounds__(256)
 lanczos_orth_kernel(double* __restrict__ w, const double* __restrict__ v, int64_t n, const double* pa,
@@ -270,12 +338,23 @@ int launch_gershgorin_f64(const double* F, int64_t n, int64_t ld, double* lohi, 
     return PURIFY_OK;
 }
 
+int launch_gershgorin_csr_f64(const CsrF& F, int64_t n, double* lohi, double* scratch, cudaStream_t s) {
+    if (n <= 0 || !F.ptr) return PURIFY_ERR_INVALID_ARG;
+    const int64_t ctas = (n + ROWS_PER_CTA - 1) / ROWS_PER_CTA;
+    gershgorin_csr_kernel<<<(unsigned)ctas, 32 * ROWS_PER_CTA, 0, s>>>(F.ptr, F.col, F.val, (int)n, scratch);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    minmax_reduce_kernel<<<1, 1024, 0, s>>>(scratch, ctas, lohi);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(2);
+    return PURIFY_OK;
+}
+
 int64_t lanczos_scratch_doubles(int64_t n, int k) {
     return 3 * n + 1 + 2 * (int64_t)k + (n + LZ_ROWS - 1) / LZ_ROWS + kVecBlocksMax;
 }
 
-int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaStream_t s) {
-    if (n <= 0 || k <= 0) return PURIFY_ERR_INVALID_ARG;
+int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaStream_t s, const CsrF* csr) {
+    if (n <= 0 || k <= 0 || (!F && !csr)) return PURIFY_ERR_INVALID_ARG;
     double* vprev = scratch;
     double* v = scratch + n;
     double* w = scratch + 2 * n;
@@ -289,8 +368,12 @@ int launch_lanczos_f64(const double* F, int64_t n, int k, double* scratch, cudaS
     lanczos_start_kernel<<<vb, 256, 0, s>>>(v, vprev, n, pb);
     scale_by_norm_kernel<<<vb, 256, 0, s>>>(v, n, pb, (int)vb, qn);
     for (int j = 0; j < k; ++j) {
-        lanczos_matvec_kernel<<<(unsigned)rows, 32 * LZ_ROWS, 0, s>>>(F, n, v, vprev, w, j ? bsq + j - 1 : nullptr,
-                                                                        pa);
+        if (csr)
+            lanczos_matvec_csr_kernel<<<(unsigned)rows, 32 * LZ_ROWS, 0, s>>>(
+                csr->ptr, csr->col, csr->val, (int)n, v, vprev, w, j ? bsq + j - 1 : nullptr, pa);
+        else
+            lanczos_matvec_kernel<<<(unsigned)rows, 32 * LZ_ROWS, 0, s>>>(F, n, v, vprev, w,
+                                                                            j ? bsq + j - 1 : nullptr, pa);
         lanczos_orth_kernel<<<vb, 256, 0, s>>>(w, v, n, pa, rows, a + j, pb);
         lanczos_shift_kernel<<<vb, 256, 0, s>>>(vprev, v, w, n, pb, (int)vb, bsq + j);
     }

@@ -47,6 +47,10 @@ void mixed_free(MixedState* ms) {
         cudaFree(ms->pidx[k]);
     }
     cudaFree(ms->pwork);
+    cudaFree(ms->spat);
+    cudaFree(ms->rowbase);
+    cudaFree(ms->strips);
+    cudaFree(ms->dpool);
     if (ms->tgraph) cudaGraphExecDestroy(ms->tgraph);
     delete ms;
 }

@@ -78,6 +78,20 @@ struct MixedState {
     int4* pwork = nullptr;
     size_t pwork_cap = 0;
     double pool_bytes_peak = 0.0;  // most pool bytes in use at once in the last run
+    // slot tables made on the device from a pattern's bits and row bases
+    unsigned long long* spat = nullptr;
+    size_t spat_cap = 0;
+    int* rowbase = nullptr;
+    size_t rowbase_cap = 0;
+    int* strips = nullptr;  // the split's strip list (CSR input)
+    size_t strips_cap = 0;
+    // the density of a block-sparse run: 32 x 32 float64 blocks in dpool
+    // under the slot table pidx[1]; d_blocks lists its upper blocks (I <= J)
+    // in row-major order
+    double* dpool = nullptr;
+    size_t dpool_cap = 0;  // bytes
+    bool d_pooled = false;
+    std::vector<int2> d_blocks;
 };
 
 // Allocate (or grow) the handle's mixed-path buffers for a padded size
@@ -90,6 +104,15 @@ constexpr double kBitsGap = 26.0;
 int digits_for_gap(double g, const purify_options& o, int rbits);
 // F[key[k]] = v[k] for distinct keys row * n + col (device arrays).
 int launch_scatter_coo(const int64_t* key, const double* v, int64_t nnz, double* F, cudaStream_t s);
+// F (n x n, zeroed beforehand) from CSR storage.
+int launch_scatter_csr(const CsrF& F, int64_t n, double* out, cudaStream_t s);
+// The pooled density of the last block-sparse run (MixedState::d_pooled)
+// into D (host or device, leading dimension ld), and its kept upper blocks:
+// *count = their number, at most cap of them written as (I, J) pairs into ij
+// and 1024 row-major doubles each into values (either may be null; host or
+// device memory).
+int density_pooled(purify_ctx* h, double* D, int64_t ld);
+int density_blocks(purify_ctx* h, int32_t* ij, double* values, int64_t cap, int64_t* count);
 // Block-sparse Algorithm 2 run (sparse.cu).
 int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std::vector<double>& red);
 

@@ -375,6 +375,16 @@ static int ensure_capacity(purify_ctx* h, int64_t n) {
 // The second iterate and the product buffer (float64 runs, refinement, gap
 // estimation) at the handle's capacity, allocated on first use: block-sparse
 // and mixed runs hold only F and the density.
+int purify::ensure_dense_F(purify_ctx* h) {
+    if (h->F_dense) return PURIFY_OK;
+    if (!h->csr_valid) return PURIFY_ERR_STATE;
+    PURIFY_TRY(ensure_capacity(h, h->n));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(h->F, 0, sizeof(double) * (size_t)h->n * (size_t)h->n, h->stream));
+    PURIFY_TRY(launch_scatter_csr(csr_of(h), h->n, h->F, h->stream));
+    h->F_dense = true;
+    return PURIFY_OK;
+}
+
 int purify::ensure_work(purify_ctx* h) {
     if (h->X[1] && h->S) return PURIFY_OK;
     const size_t bytes = sizeof(double) * (size_t)h->cap * (size_t)h->cap;
@@ -383,7 +393,7 @@ int purify::ensure_work(purify_ctx* h) {
     return PURIFY_OK;
 }
 
-static int ensure_scratch(purify_ctx* h, int64_t doubles) {
+int purify::ensure_scratch(purify_ctx* h, int64_t doubles) {
     if (doubles <= h->scratch_cap) return PURIFY_OK;
     cudaFree(h->scratch);
     h->scratch = nullptr;
@@ -544,6 +554,9 @@ int purify_destroy(purify_t h) {
     free_buffers(h);
     cudaFree(h->red);
     cudaFree(h->scratch);
+    cudaFree(h->csr_ptr);
+    cudaFree(h->csr_col);
+    cudaFree(h->csr_val);
     mixed_free(h->mixed);
     for (cudaEvent_t e : h->pev) cudaEventDestroy(e);
     if (h->e0) cudaEventDestroy(h->e0);
@@ -562,7 +575,7 @@ int purify_set_options(purify_t h, const purify_options* opt) {
 }
 
 const double* purify_density_device_ptr(purify_t h) {
-    if (!h || h->cur < 0) return nullptr;
+    if (!h || h->cur < 0 || (h->mixed && h->mixed->d_pooled)) return nullptr;
     return h->X[h->cur];
 }
 
@@ -577,14 +590,19 @@ static int finish_set(purify_t h, int64_t n, int64_t nocc, double mu, const puri
         PURIFY_TRY(ensure_scratch(h, need));
         double* lohi = h->scratch;
         double* gs = h->scratch + 2;
-        PURIFY_TRY(launch_gershgorin_f64(h->F, n, n, lohi, gs, h->stream));
+        const bool csr = h->csr_valid && !h->F_dense;
+        const CsrF cf = csr_of(h);
+        if (csr)
+            PURIFY_TRY(launch_gershgorin_csr_f64(cf, n, lohi, gs, h->stream));
+        else
+            PURIFY_TRY(launch_gershgorin_f64(h->F, n, n, lohi, gs, h->stream));
         double g[2];
         double lo, hi;
         if (k > 0) {
             // the Lanczos steps are queued before any result is read back, so
             // the device runs the whole estimate without a host round trip
             double* ls = h->scratch + 2;  // Gershgorin partials are consumed already
-            PURIFY_TRY(launch_lanczos_f64(h->F, n, k, ls, h->stream));
+            PURIFY_TRY(launch_lanczos_f64(h->F, n, k, ls, h->stream, csr ? &cf : nullptr));
             PURIFY_CUDA_TRY(cudaMemcpyAsync(g, lohi, sizeof(g), cudaMemcpyDeviceToHost, h->stream));
             std::vector<double> a(k), bsq(k);
             PURIFY_CUDA_TRY(cudaMemcpyAsync(a.data(), ls + lanczos_a_offset(n), sizeof(double) * k,
@@ -639,8 +657,11 @@ int purify_set_hamiltonian(purify_t h, const double* F, int64_t n, int64_t ld, i
     PURIFY_TRY(join_in(h));
     PURIFY_TRY(ensure_capacity(h, n));
     h->n = n;
+    h->csr_valid = false;
+    h->F_dense = false;
     PURIFY_TRY(copy_in_matrix(h->F, F, n, ld, h->stream));
     PURIFY_TRY(launch_mirror_upper_f64(h->F, n, h->stream));
+    h->F_dense = true;
     return finish_set(h, n, nocc, mu, b, set_launches0);
 }
 
@@ -648,7 +669,10 @@ int purify_set_hamiltonian_coo(purify_t h, int64_t n, int64_t nnz, const int64_t
                                const int64_t* cols, const double* vals, int64_t nocc, double mu,
                                const purify_bounds* b) {
     if (!h || !b || n <= 0 || nnz < 0 || (nnz > 0 && (!rows || !cols || !vals))) return PURIFY_ERR_INVALID_ARG;
-    if (nocc > n || n > (int64_t)1 << 17) return PURIFY_ERR_INVALID_ARG;
+    // a block-sparse mixed handle keeps F in CSR form (no n x n array), so
+    // it takes larger n
+    const bool csr_mode = h->opt.block_sparse && h->opt.precision == PURIFY_MIXED;
+    if (nocc > n || n > (int64_t)1 << (csr_mode ? 18 : 17)) return PURIFY_ERR_INVALID_ARG;
     for (int64_t k = 0; k < nnz; ++k)
         if (rows[k] < 0 || rows[k] >= n || cols[k] < 0 || cols[k] >= n) return PURIFY_ERR_INVALID_ARG;
     // merge duplicates (summed in input order, so the result does not depend
@@ -682,7 +706,58 @@ int purify_set_hamiltonian_coo(purify_t h, int64_t n, int64_t nnz, const int64_t
     const long long set_launches0 = launches_so_far();
     h->have_F = false;
     h->cur = -1;
+    h->csr_valid = false;
+    h->F_dense = false;
     PURIFY_TRY(join_in(h));
+    if (csr_mode) {
+        // rows and columns in key order: CSR with sorted columns; F's block
+        // pattern (with the diagonal) for the block-sparse split
+        std::vector<int64_t> ptr(n + 1, 0);
+        std::vector<int> col(nnz);
+        const int nb = pad128(n) / 32, words = (nb + 63) / 64;
+        h->f_pattern.assign((size_t)nb * words, 0);
+        h->f_pattern_words = words;
+        for (int64_t u = 0; u < nnz; ++u) {
+            const int64_t i = ukey[u] / n, j = ukey[u] % n;
+            ++ptr[i + 1];
+            col[u] = (int)j;
+            h->f_pattern[(size_t)(i >> 5) * words + (j >> 11)] |= 1ull << ((j >> 5) & 63);
+        }
+        for (int I = 0; I < nb; ++I) h->f_pattern[(size_t)I * words + (I >> 6)] |= 1ull << (I & 63);
+        for (int64_t i = 0; i < n; ++i) ptr[i + 1] += ptr[i];
+        free_buffers(h);  // an earlier dense F and density
+        if (h->csr_rows_cap < n + 1) {
+            cudaFree(h->csr_ptr);
+            h->csr_ptr = nullptr;
+            h->csr_rows_cap = 0;
+            PURIFY_CUDA_TRY(cudaMalloc(&h->csr_ptr, sizeof(int64_t) * (size_t)(n + 1)));
+            h->csr_rows_cap = n + 1;
+        }
+        if (h->csr_nnz_cap < std::max<int64_t>(nnz, 1)) {
+            cudaFree(h->csr_col);
+            cudaFree(h->csr_val);
+            h->csr_col = nullptr;
+            h->csr_val = nullptr;
+            h->csr_nnz_cap = 0;
+            const int64_t c = std::max<int64_t>(nnz, 1);
+            PURIFY_CUDA_TRY(cudaMalloc(&h->csr_col, sizeof(int) * (size_t)c));
+            PURIFY_CUDA_TRY(cudaMalloc(&h->csr_val, sizeof(double) * (size_t)c));
+            h->csr_nnz_cap = c;
+        }
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(h->csr_ptr, ptr.data(), sizeof(int64_t) * ptr.size(), cudaMemcpyHostToDevice,
+                                        h->stream));
+        if (nnz > 0) {
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(h->csr_col, col.data(), sizeof(int) * (size_t)nnz, cudaMemcpyHostToDevice,
+                                            h->stream));
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(h->csr_val, uval.data(), sizeof(double) * (size_t)nnz,
+                                            cudaMemcpyHostToDevice, h->stream));
+        }
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));  // the host arrays go out of scope
+        h->n = n;
+        h->csr_nnz = nnz;
+        h->csr_valid = true;
+        return finish_set(h, n, nocc, mu, b, set_launches0);
+    }
     PURIFY_TRY(ensure_capacity(h, n));
     h->n = n;
     PURIFY_CUDA_TRY(cudaMemsetAsync(h->F, 0, sizeof(double) * (size_t)n * n, h->stream));
@@ -695,6 +770,7 @@ int purify_set_hamiltonian_coo(purify_t h, int64_t n, int64_t nnz, const int64_t
         PURIFY_TRY(launch_scatter_coo(dk, dv, nnz, h->F, h->stream));
         PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));  // the scratch is reused below
     }
+    h->F_dense = true;
     return finish_set(h, n, nocc, mu, b, set_launches0);
 }
 
@@ -737,6 +813,7 @@ static void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) 
 // Sets the trace of the last result and ||X - X^2||_F of its input.
 static int refine_f64(purify_ctx* h, int R) {
     if (R <= 0 || h->cur < 0) return PURIFY_OK;
+    if (h->mixed && h->mixed->d_pooled) return PURIFY_ERR_UNSUPPORTED;  // a block-sparse density
     PURIFY_TRY(ensure_work(h));
     PURIFY_TRY(ensure_red(h, 4 * (int64_t)(2 * R)));
     PURIFY_CUDA_TRY(cudaMemsetAsync(h->red, 0, sizeof(double) * 8 * R, h->stream));
@@ -987,6 +1064,10 @@ int purify_run(purify_t h, int scheme, double tol, int max_iter) {
     int r;
     bool graph_run = false;  // products replayed from a graph are not timed one by one
     if (h->opt.block_sparse && h->opt.precision != PURIFY_MIXED) return PURIFY_ERR_UNSUPPORTED;
+    if (h->mixed) h->mixed->d_pooled = false;
+    const bool pooled_run = h->opt.precision == PURIFY_MIXED && h->opt.block_sparse && !trace_rule &&
+                            pmm_order(scheme) != 3 && !is_asymmetric(scheme);
+    if (!pooled_run) PURIFY_TRY(ensure_dense_F(h));
     if (h->opt.precision == PURIFY_MIXED) {
         if (trace_rule && h->opt.block_sparse) return PURIFY_ERR_UNSUPPORTED;
         if (trace_rule) {
@@ -1081,9 +1162,22 @@ int purify_get_density(purify_t h, double* D, int64_t ld) {
     if (h->cur < 0) return PURIFY_ERR_STATE;
     PURIFY_TRY(set_device(h));
     PURIFY_TRY(join_in(h));
+    if (h->mixed && h->mixed->d_pooled) {
+        PURIFY_TRY(density_pooled(h, D, ld));
+        return join_out(h);
+    }
     PURIFY_CUDA_TRY(cudaMemcpy2DAsync(D, sizeof(double) * ld, h->X[h->cur], sizeof(double) * h->n,
                                       sizeof(double) * h->n, h->n, cudaMemcpyDefault, h->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return join_out(h);
+}
+
+int purify_get_density_blocks(purify_t h, int32_t* block_ij, double* values, int64_t cap, int64_t* count) {
+    if (!h || !count || cap < 0 || (cap > 0 && !block_ij && !values)) return PURIFY_ERR_INVALID_ARG;
+    if (h->cur < 0 || !h->mixed || !h->mixed->d_pooled) return PURIFY_ERR_STATE;
+    PURIFY_TRY(set_device(h));
+    PURIFY_TRY(join_in(h));
+    PURIFY_TRY(density_blocks(h, block_ij, values, cap, count));
     return join_out(h);
 }
 

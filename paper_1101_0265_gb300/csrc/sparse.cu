@@ -22,6 +22,7 @@
 #include <cstddef>
 #include <cmath>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "digits_tc.h"
@@ -208,49 +209,36 @@ struct Pattern {
 };
 
 // Pattern of X^2, of X and of the diagonal together (the blocks that Eq. 4
-// and Eq. 5 can make nonzero).
+// and Eq. 5 can make nonzero).  Rows are independent: large patterns are
+// split over host threads.
 void output_pattern(const Pattern& X, Pattern& out) {
     out.init(X.nb);
-    for (int I = 0; I < X.nb; ++I) {
-        uint64_t* o = out.row(I);
-        const uint64_t* xi = X.row(I);
-        for (int w = 0; w < X.words; ++w) {
-            o[w] |= xi[w];
-            uint64_t m = xi[w];
-            while (m) {
-                const int K = w * 64 + __builtin_ctzll(m);
-                m &= m - 1;
-                const uint64_t* xk = X.row(K);
-                for (int v = 0; v < X.words; ++v) o[v] |= xk[v];
+    auto rows = [&](int I0, int I1) {
+        for (int I = I0; I < I1; ++I) {
+            uint64_t* o = out.row(I);
+            const uint64_t* xi = X.row(I);
+            for (int w = 0; w < X.words; ++w) {
+                o[w] |= xi[w];
+                uint64_t m = xi[w];
+                while (m) {
+                    const int K = w * 64 + __builtin_ctzll(m);
+                    m &= m - 1;
+                    const uint64_t* xk = X.row(K);
+                    for (int v = 0; v < X.words; ++v) o[v] |= xk[v];
+                }
             }
+            out.set(I, I);
         }
-        out.set(I, I);
+    };
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nt = X.nb >= 512 ? std::max(1, std::min(hw, 16)) : 1;
+    if (nt == 1) {
+        rows(0, X.nb);
+        return;
     }
-}
-
-// Per upper 128 x 128 tile t = tj (tj + 1) / 2 + ti: the 32-wide k-chunks
-// where both row panels hold a nonzero block, as a bitmask (X.words words per
-// tile) and a count (-1 when that is every chunk).
-void chunk_masks(const Pattern& X, int T, std::vector<int>& cnt, std::vector<uint64_t>& mask) {
-    const int words = X.words, nb = X.nb;
-    std::vector<uint64_t> panel((size_t)T * words, 0);
-    for (int t = 0; t < T; ++t)
-        for (int r = 4 * t; r < 4 * t + 4 && r < nb; ++r)
-            for (int w = 0; w < words; ++w) panel[(size_t)t * words + w] |= X.row(r)[w];
-    const size_t tiles = (size_t)T * (T + 1) / 2;
-    cnt.assign(tiles, 0);
-    mask.assign(tiles * words, 0);
-    for (int tj = 0; tj < T; ++tj)
-        for (int ti = 0; ti <= tj; ++ti) {
-            const size_t t = (size_t)tj * (tj + 1) / 2 + ti;
-            int c = 0;
-            for (int w = 0; w < words; ++w) {
-                const uint64_t m = panel[(size_t)ti * words + w] & panel[(size_t)tj * words + w];
-                mask[t * words + w] = m;
-                c += __builtin_popcountll(m);
-            }
-            cnt[t] = (c == nb) ? -1 : c;
-        }
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(rows, (int)((int64_t)X.nb * t / nt), (int)((int64_t)X.nb * (t + 1) / nt));
+    for (std::thread& th : pool) th.join();
 }
 
 // Error-controlled truncation of the upper blocks of `pat` by their squared
@@ -433,16 +421,16 @@ namespace {
 // Pool k holds at least `bytes` bytes (capacity grows by a quarter beyond the
 // request, up to `max_bytes`).  The pool being resized is the one about to be
 // filled: nothing in it is kept.
-int ensure_pool(purify_ctx* h, int k, size_t bytes, size_t max_bytes) {
-    MixedState* ms = h->mixed;
-    if (bytes <= ms->pool_cap[k]) return PURIFY_OK;
+template <typename T>
+int ensure_bytes(purify_ctx* h, T** buf, size_t* cap, size_t bytes, size_t max_bytes) {
+    if (bytes <= *cap) return PURIFY_OK;
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
-    cudaFree(ms->pool[k]);
-    ms->pool[k] = nullptr;
-    ms->pool_cap[k] = 0;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
     const size_t c = std::max(bytes, std::min(bytes + bytes / 4 + (64 << 10), max_bytes));
-    PURIFY_CUDA_TRY(cudaMalloc(&ms->pool[k], c));
-    ms->pool_cap[k] = c;
+    PURIFY_CUDA_TRY(cudaMalloc(buf, c));
+    *cap = c;
     return PURIFY_OK;
 }
 
@@ -452,7 +440,7 @@ int ensure_pool(purify_ctx* h, int k, size_t bytes, size_t max_bytes) {
 __global__ void compact_slots_kernel(const __nv_bfloat16* __restrict__ src, const int* __restrict__ sidx,
                                      __nv_bfloat16* __restrict__ dst, const int* __restrict__ didx, int nb, int np) {
     const int lane = threadIdx.x & 31;
-    const int total = nb * nb;  // nb <= 4096
+    const int total = nb * nb;  // nb <= 8192
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < total; e += warps) {
         const int d = didx[e];
@@ -463,42 +451,256 @@ __global__ void compact_slots_kernel(const __nv_bfloat16* __restrict__ src, cons
     }
 }
 
-// Slot table of a pattern (every block of it, both triangles): slots 1, 2,
-// .. in row-major block order.  Returns the slots used, slot 0 included.
-size_t assign_slots(const Pattern& P, std::vector<int>& idx) {
-    idx.assign((size_t)P.nb * P.nb, 0);
-    int k = 1;
-    for (int I = 0; I < P.nb; ++I)
-        for (int J = 0; J < P.nb; ++J)
-            if (P.get(I, J)) idx[(size_t)I * P.nb + J] = k++;
-    return (size_t)k;
-}
+constexpr int kMaxPatternWords = 128;  // nb <= 8192
 
-// The upper 128 x 128 tiles holding a block of `out`, in banded order: the
-// product's work items {0, ti, tj, 0}.
-void pattern_tiles(const Pattern& out, int T, std::vector<int4>& work) {
-    std::vector<int2> band;
-    banded_tiles(T, band);
-    work.clear();
-    for (const int2& t : band) {
-        bool any = false;
-        for (int r = 4 * t.x; r < 4 * t.x + 4 && !any; ++r)
-            any = ((out.row(r)[(4 * t.y) >> 6] >> ((4 * t.y) & 63)) & 0xFull) != 0;
-        if (any) work.push_back(make_int4(0, t.x, t.y, 0));
+// Slot table of a block pattern (nb rows of `words` 64-bit words): block
+// (I, J) set gets row_base[I] + (the set blocks before it in row I), unset
+// blocks 0.  One warp per block row; the per-word prefix counts go through
+// shared memory.
+__global__ void __launch_bounds__(256) slot_table_kernel(const unsigned long long* __restrict__ pat, int nb,
+                                                         int words, const int* __restrict__ row_base,
+                                                         int* __restrict__ idx) {
+    __shared__ int pre[8][kMaxPatternWords];
+    __shared__ unsigned long long wv[8][kMaxPatternWords];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int I = blockIdx.x * 8 + warp; I < nb; I += gridDim.x * 8) {
+        const unsigned long long* row = pat + (size_t)I * words;
+        int carry = 0;
+        for (int w0 = 0; w0 < words; w0 += 32) {
+            const int w = w0 + lane;
+            const unsigned long long v = w < words ? row[w] : 0ull;
+            const int own = __popcll(v);
+            int c = own;  // inclusive prefix over the 32 words
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, c, o);
+                if (lane >= o) c += t;
+            }
+            if (w < words) {
+                pre[warp][w] = carry + c - own;
+                wv[warp][w] = v;
+            }
+            carry += __shfl_sync(0xffffffffu, c, 31);
+        }
+        __syncwarp();
+        const int base = row_base[I];
+        int* out = idx + (size_t)I * nb;
+        for (int J0 = 0; J0 < nb; J0 += 32) {
+            const int J = J0 + lane;
+            if (J < nb) {
+                const int w = J >> 6, b = J & 63;
+                const unsigned long long v = wv[warp][w];
+                const bool set = (v >> b) & 1ull;
+                out[J] = set ? base + pre[warp][w] + __popcll(v & ((1ull << b) - 1ull)) : 0;
+            }
+        }
+        __syncwarp();
     }
 }
 
-// Table k and a zero slot 0 for a pool whose slots hold s planes (slot 0
-// is cleared each time: slots of another size may have overlapped it).
-int upload_slots(purify_ctx* h, int k, const std::vector<int>& idx, int s) {
+// F[i n + col] = val over CSR rows (F zeroed beforehand); one warp per row.
+__global__ void scatter_csr_kernel(const int64_t* __restrict__ ptr, const int* __restrict__ col,
+                                   const double* __restrict__ val, int n, double* F) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < n; i += warps) {
+        const int64_t p1 = ptr[i + 1];
+        for (int64_t k = ptr[i] + lane; k < p1; k += 32) F[(size_t)i * n + col[k]] = val[k];
+    }
+}
+
+// Rows [I0 * 32, I1 * 32) of the pooled density into dst (leading dimension
+// ld, rows from I0 * 32; zeroed beforehand): one warp per table entry of
+// those block rows, rows and columns >= n left out.
+__global__ void scatter_dpool_kernel(const double* __restrict__ dpool, const int* __restrict__ tbl, int nb, int n,
+                                     int I0, int I1, double* __restrict__ dst, int64_t ld) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const int entries = (I1 - I0) * nb;
+    for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < entries; e += warps) {
+        const int I = I0 + e / nb, J = e % nb;
+        const int k = tbl[(size_t)I * nb + J];
+        if (k == 0) continue;
+        const double* blk = dpool + (size_t)k * 1024;
+        const int j = J * 32 + lane;
+        if (j >= n) continue;
+        for (int r = 0; r < 32 && I * 32 + r < n; ++r)
+            dst[(size_t)((I - I0) * 32 + r) * ld + j] = blk[r * 32 + lane];
+    }
+}
+
+// Blocks list[b0 .. b0 + count) of the pooled density, 1024 doubles each, into dst.
+__global__ void gather_dpool_kernel(const double* __restrict__ dpool, const int* __restrict__ tbl, int nb,
+                                    const int2* __restrict__ list, int64_t count, double* __restrict__ dst) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < count; b += warps) {
+        const int2 ij = list[b];
+        const int k = tbl[(size_t)ij.x * nb + ij.y];
+        const double* blk = dpool + (size_t)k * 1024;
+        for (int q = lane; q < 1024; q += 32) dst[b * 1024 + q] = blk[q];
+    }
+}
+
+// Row bases of a pattern's slot table (slot 0 reserved) and the slots used
+// (slot 0 included).
+size_t row_bases(const Pattern& P, std::vector<int>& base) {
+    base.resize(P.nb);
+    size_t k = 1;
+    for (int I = 0; I < P.nb; ++I) {
+        base[I] = (int)k;
+        const uint64_t* r = P.row(I);
+        for (int w = 0; w < P.words; ++w) k += (size_t)__builtin_popcountll(r[w]);
+    }
+    return k;
+}
+
+// Slot table k from pattern P on the device; returns the slots used.
+int upload_table(purify_ctx* h, const Pattern& P, int* table, size_t* used) {
     MixedState* ms = h->mixed;
-    PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->pidx[k], idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice,
+    if (P.words > kMaxPatternWords) return PURIFY_ERR_INVALID_ARG;
+    std::vector<int> base;
+    *used = row_bases(P, base);
+    PURIFY_TRY(grow(&ms->spat, &ms->spat_cap, P.bits.size()));
+    PURIFY_TRY(grow(&ms->rowbase, &ms->rowbase_cap, base.size()));
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->spat, P.bits.data(), sizeof(uint64_t) * P.bits.size(),
+                                    cudaMemcpyHostToDevice, h->stream));
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->rowbase, base.data(), sizeof(int) * base.size(), cudaMemcpyHostToDevice,
                                     h->stream));
-    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->pool[k], 0, pool_slot_bytes(s), h->stream));
+    const unsigned grid = (unsigned)std::min(152 * 8, (P.nb + 7) / 8);
+    slot_table_kernel<<<grid, 256, 0, h->stream>>>(ms->spat, P.nb, P.words, ms->rowbase, table);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
     return PURIFY_OK;
 }
 
+// Per 128-row panel t of X: the block columns where one of its four block
+// rows has a block (X.words words per panel).
+void panel_bits(const Pattern& X, int T, std::vector<uint64_t>& pan) {
+    pan.assign((size_t)T * X.words, 0);
+    for (int t = 0; t < T; ++t)
+        for (int r = 4 * t; r < 4 * t + 4 && r < X.nb; ++r)
+            for (int w = 0; w < X.words; ++w) pan[(size_t)t * X.words + w] |= X.row(r)[w];
+}
+
+// The upper 128 x 128 tiles holding a block of `out`, in banded order: the
+// product's work items {0, ti, tj, 0}; chunks receives the k-chunk products
+// they run (the popcount of the two panels' bits of X).
+void pattern_tiles(const Pattern& out, const std::vector<uint64_t>& xpan, int words, int T,
+                   std::vector<int4>& work, double* chunks) {
+    std::vector<uint64_t> opan;
+    panel_bits(out, T, opan);
+    std::vector<int2> band;
+    banded_tiles(T, band);
+    work.clear();
+    double c = 0.0;
+    for (const int2& t : band) {
+        const int J0 = 4 * t.y;
+        if (!((opan[(size_t)t.x * words + (J0 >> 6)] >> (J0 & 63)) & 0xFull)) continue;
+        work.push_back(make_int4(0, t.x, t.y, 0));
+        const uint64_t* a = &xpan[(size_t)t.x * words];
+        const uint64_t* b = &xpan[(size_t)t.y * words];
+        for (int w = 0; w < words; ++w) c += (double)__builtin_popcountll(a[w] & b[w]);
+    }
+    *chunks = c;
+}
+
+// X_0's strips (block row I, 128-column segment) that hold a block of P.
+void pattern_strips(const Pattern& P, int ns, std::vector<int>& strips) {
+    strips.clear();
+    for (int I = 0; I < P.nb; ++I)
+        for (int q = 0; q < ns; ++q) {
+            const int J0 = 4 * q;
+            if ((P.row(I)[J0 >> 6] >> (J0 & 63)) & 0xFull) strips.push_back(I * ns + q);
+        }
+}
+
 }  // namespace
+
+int launch_scatter_csr(const CsrF& F, int64_t n, double* out, cudaStream_t s) {
+    const unsigned grid = (unsigned)std::min<int64_t>(152 * 8, (n + 7) / 8);
+    scatter_csr_kernel<<<grid, 256, 0, s>>>(F.ptr, F.col, F.val, (int)n, out);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
+    return PURIFY_OK;
+}
+
+int density_pooled(purify_ctx* h, double* D, int64_t ld) {
+    MixedState* ms = h->mixed;
+    const int n = (int)h->n, nb = pad128(n) / 32;
+    cudaPointerAttributes attr;
+    PURIFY_CUDA_TRY(cudaPointerGetAttributes(&attr, D));
+    const bool dev = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    // block rows per pass: all of them into device memory, else through a
+    // staging panel of at most 256 MB
+    int rows = nb;
+    double* stage = D;
+    int64_t sld = ld;
+    if (!dev) {
+        rows = (int)std::max<int64_t>(1, std::min<int64_t>(nb, (256ll << 20) / (32ll * 8 * n)));
+        PURIFY_TRY(ensure_scratch(h, (int64_t)rows * 32 * n));
+        stage = h->scratch;
+        sld = n;
+    }
+    for (int I0 = 0; I0 < nb; I0 += rows) {
+        const int I1 = std::min(nb, I0 + rows);
+        const int r0 = I0 * 32, r1 = std::min(n, I1 * 32);
+        if (r1 <= r0) break;
+        double* dst = dev ? D + (size_t)r0 * ld : stage;
+        PURIFY_CUDA_TRY(cudaMemset2DAsync(dst, sizeof(double) * sld, 0, sizeof(double) * n, r1 - r0, h->stream));
+        const int64_t entries = (int64_t)(I1 - I0) * nb;
+        const unsigned grid = (unsigned)std::min<int64_t>(152 * 8, (entries + 7) / 8);
+        scatter_dpool_kernel<<<grid, 256, 0, h->stream>>>(ms->dpool, ms->pidx[1], nb, n, I0, I1, dst, sld);
+        PURIFY_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+        if (!dev)
+            PURIFY_CUDA_TRY(cudaMemcpy2DAsync(D + (size_t)r0 * ld, sizeof(double) * ld, stage, sizeof(double) * n,
+                                              sizeof(double) * n, r1 - r0, cudaMemcpyDeviceToHost, h->stream));
+    }
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return PURIFY_OK;
+}
+
+int density_blocks(purify_ctx* h, int32_t* ij, double* values, int64_t cap, int64_t* count) {
+    MixedState* ms = h->mixed;
+    const int nb = pad128(h->n) / 32;
+    const int64_t total = (int64_t)ms->d_blocks.size();
+    *count = total;
+    const int64_t m = std::min(cap, total);
+    if (m <= 0) return PURIFY_OK;
+    if (ij) {
+        std::vector<int32_t> flat(2 * (size_t)m);
+        for (int64_t b = 0; b < m; ++b) {
+            flat[2 * b] = ms->d_blocks[b].x;
+            flat[2 * b + 1] = ms->d_blocks[b].y;
+        }
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(ij, flat.data(), sizeof(int32_t) * flat.size(), cudaMemcpyDefault, h->stream));
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    if (!values) return PURIFY_OK;
+    cudaPointerAttributes attr;
+    PURIFY_CUDA_TRY(cudaPointerGetAttributes(&attr, values));
+    const bool dev = attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    // the block list on the device (in the drop-list buffer, free after a run)
+    PURIFY_TRY(grow(&ms->drops, &ms->drops_cap, (size_t)m));
+    PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->drops, ms->d_blocks.data(), sizeof(int2) * m, cudaMemcpyHostToDevice,
+                                    h->stream));
+    const int64_t per = dev ? m : std::max<int64_t>(1, (256ll << 20) / (1024 * 8));
+    if (!dev) PURIFY_TRY(ensure_scratch(h, std::min(per, m) * 1024));
+    for (int64_t b0 = 0; b0 < m; b0 += per) {
+        const int64_t c = std::min(per, m - b0);
+        double* dst = dev ? values + b0 * 1024 : h->scratch;
+        const unsigned grid = (unsigned)std::min<int64_t>(152 * 8, (c + 7) / 8);
+        gather_dpool_kernel<<<grid, 256, 0, h->stream>>>(ms->dpool, ms->pidx[1], nb, ms->drops + b0, c, dst);
+        PURIFY_CUDA_TRY(cudaGetLastError());
+        count_launches(1);
+        if (!dev)
+            PURIFY_CUDA_TRY(cudaMemcpyAsync(values + b0 * 1024, h->scratch, sizeof(double) * 1024 * c,
+                                            cudaMemcpyDeviceToHost, h->stream));
+        PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    return PURIFY_OK;
+}
 
 int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std::vector<double>& red) {
     if (scheme != PURIFY_TC_SF && scheme != PURIFY_TC_MONO) return PURIFY_ERR_UNSUPPORTED;
@@ -510,7 +712,10 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     const int n_pad = pad128(n);
     PURIFY_TRY(ensure_mixed(h, n_pad, false));
     MixedState* ms = h->mixed;
-    const int nb = n_pad / 32, T = n_pad / 128;
+    ms->d_pooled = false;
+    ms->d_blocks.clear();
+    const int nb = n_pad / 32, T = n_pad / 128, ns = n_pad / 128;
+    if ((nb + 63) / 64 > kMaxPatternWords) return PURIFY_ERR_INVALID_ARG;
     const int rb = remainder_bits(n_pad);
     const int m = (int)S.alpha.size();
     std::vector<int> sd(m + 1);
@@ -523,6 +728,8 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     int dmax = 0;
     for (int i = 0; i < m; ++i) dmax = std::max(dmax, sd[i]);
     h->st.digit_max = dmax;
+    const bool csr = h->csr_valid;
+    if (!csr && !h->F_dense) return PURIFY_ERR_STATE;
     PURIFY_TRY(grow(&ms->bnorm2, &ms->bnorm2_cap, (size_t)nb * nb));
     if (ms->pidx_cap < (size_t)nb * nb) {
         for (int k = 0; k < 2; ++k) {
@@ -546,9 +753,26 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     ms->pool_bytes_peak = 0.0;
     // X_0 = c0 I + c1 F: its block norms first (the split without planes),
     // then its pattern, truncated like every iterate, and its planes in the
-    // pool slots of the kept blocks
+    // pool slots of the kept blocks.  From CSR the split visits only the
+    // strips that hold a block of F's pattern (blocks outside it are zero).
     const int s0 = std::max(sd[0], 1);
-    PURIFY_TRY(launch_split_pool(h->F, n, n, n_pad, c1, c0, 0, s0, rb, nullptr, nullptr, ms->bnorm2, h->stream));
+    std::vector<int> strips;
+    if (csr) {
+        Pattern P0;
+        P0.nb = nb;
+        P0.words = h->f_pattern_words;
+        P0.bits = h->f_pattern;
+        pattern_strips(P0, ns, strips);
+        PURIFY_TRY(grow(&ms->strips, &ms->strips_cap, strips.size()));
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->strips, strips.data(), sizeof(int) * strips.size(),
+                                        cudaMemcpyHostToDevice, h->stream));
+        PURIFY_CUDA_TRY(cudaMemsetAsync(ms->bnorm2, 0, sizeof(float) * (size_t)nb * nb, h->stream));
+        PURIFY_TRY(launch_split_csr_pool(h->csr_ptr, h->csr_col, h->csr_val, n, n_pad, c1, c0, 0, s0, rb, nullptr,
+                                         nullptr, ms->bnorm2, ms->strips, (int)strips.size(), h->stream));
+    } else {
+        PURIFY_TRY(launch_split_pool(h->F, n, n, n_pad, c1, c0, 0, s0, rb, nullptr, nullptr, ms->bnorm2,
+                                     h->stream));
+    }
     PURIFY_CUDA_TRY(cudaMemcpyAsync(bn2.data(), ms->bnorm2, sizeof(float) * (size_t)nb * nb,
                                     cudaMemcpyDeviceToHost, h->stream));
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -569,51 +793,59 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
     // the product's output pattern before truncation; after each truncation
     // the kept blocks move from pool 1 into pool 0
     const size_t max_bytes = ((size_t)nb * nb + 1) * pool_slot_bytes(kMaxDigitPlanes);
-    std::vector<int> idx;
-    size_t used0 = assign_slots(X, idx);
-    PURIFY_TRY(ensure_pool(h, 0, used0 * pool_slot_bytes(s0), max_bytes));
-    PURIFY_TRY(upload_slots(h, 0, idx, s0));
-    PURIFY_TRY(launch_split_pool(h->F, n, n, n_pad, c1, c0, 0, s0, rb, ms->pool[0], ms->pidx[0], nullptr,
-                                 h->stream));
+    size_t used0 = 0;
+    PURIFY_TRY(upload_table(h, X, ms->pidx[0], &used0));
+    PURIFY_TRY(ensure_bytes(h, &ms->pool[0], &ms->pool_cap[0], used0 * pool_slot_bytes(s0), max_bytes));
+    PURIFY_CUDA_TRY(cudaMemsetAsync(ms->pool[0], 0, pool_slot_bytes(s0), h->stream));
+    if (csr)
+        PURIFY_TRY(launch_split_csr_pool(h->csr_ptr, h->csr_col, h->csr_val, n, n_pad, c1, c0, 0, s0, rb,
+                                         ms->pool[0], ms->pidx[0], nullptr, ms->strips, (int)strips.size(),
+                                         h->stream));
+    else
+        PURIFY_TRY(launch_split_pool(h->F, n, n, n_pad, c1, c0, 0, s0, rb, ms->pool[0], ms->pidx[0], nullptr,
+                                     h->stream));
     ms->pool_bytes_peak = (double)(used0 * pool_slot_bytes(s0));
 
-    double* D = h->X[0];
     *cur = 0;
-    std::vector<int> cnt;
-    std::vector<uint64_t> mask;
+    std::vector<uint64_t> xpan;
     std::vector<int4> work;
-    const size_t tiles = (size_t)T * (T + 1) / 2;
-    const size_t cnt_words = (tiles + 1) / 2;  // the counts, two ints per word
     const double pairs_tile = 2.0 * 128.0 * 128.0 * 32.0;  // one pair, one 32-wide k-chunk
     for (int i = 0; i < m; ++i) {
         const int s = sd[i], so = sd[i + 1];
         const bool last = (i + 1 == m);
         Pattern out;
         output_pattern(X, out);
-        chunk_masks(X, T, cnt, mask);
-        pattern_tiles(out, T, work);
-        PURIFY_TRY(grow(&ms->kc_buf, &ms->kc_buf_cap, cnt_words + mask.size()));
+        panel_bits(X, T, xpan);
+        double chunks = 0.0;
+        pattern_tiles(out, xpan, X.words, T, work, &chunks);
+        PURIFY_TRY(grow(&ms->kc_buf, &ms->kc_buf_cap, xpan.size()));
         PURIFY_TRY(grow(&ms->pwork, &ms->pwork_cap, work.size()));
-        int* kc_cnt = (int*)ms->kc_buf;
-        unsigned long long* kc_mask = ms->kc_buf + cnt_words;
-        PURIFY_CUDA_TRY(cudaMemcpyAsync(kc_cnt, cnt.data(), sizeof(int) * tiles, cudaMemcpyHostToDevice, h->stream));
-        PURIFY_CUDA_TRY(cudaMemcpyAsync(kc_mask, mask.data(), sizeof(uint64_t) * mask.size(), cudaMemcpyHostToDevice,
-                                        h->stream));
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->kc_buf, xpan.data(), sizeof(uint64_t) * xpan.size(),
+                                        cudaMemcpyHostToDevice, h->stream));
         PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->pwork, work.data(), sizeof(int4) * work.size(), cudaMemcpyHostToDevice,
                                         h->stream));
-        double chunks = 0.0;
-        for (const int4& w : work) {
-            const int c = cnt[(size_t)w.z * (w.z + 1) / 2 + w.y];
-            chunks += c < 0 ? (double)nb : (double)c;
-        }
         size_t used1 = 0;
+        PURIFY_TRY(upload_table(h, out, ms->pidx[1], &used1));
         if (!last) {
-            used1 = assign_slots(out, idx);
-            PURIFY_TRY(ensure_pool(h, 1, used1 * pool_slot_bytes(so), max_bytes));
-            PURIFY_TRY(upload_slots(h, 1, idx, so));
-        } else if (work.size() < tiles) {
-            // tiles outside the work list are not written
-            PURIFY_CUDA_TRY(cudaMemsetAsync(D, 0, sizeof(double) * (size_t)n * n, h->stream));
+            PURIFY_TRY(ensure_bytes(h, &ms->pool[1], &ms->pool_cap[1], used1 * pool_slot_bytes(so), max_bytes));
+            PURIFY_CUDA_TRY(cudaMemsetAsync(ms->pool[1], 0, pool_slot_bytes(so), h->stream));
+        } else {
+            // the density: 32 x 32 float64 blocks, zeroed (rows and columns
+            // >= n are not written).  When the device lacks room for it, the
+            // planes pool this step does not write is given back first.
+            const size_t need = used1 * 8192;
+            if (need > ms->dpool_cap && ms->pool[1]) {
+                size_t fr = 0, tot = 0;
+                PURIFY_CUDA_TRY(cudaMemGetInfo(&fr, &tot));
+                if (fr + ms->dpool_cap < need + need / 4 + ((size_t)1 << 30)) {
+                    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+                    cudaFree(ms->pool[1]);
+                    ms->pool[1] = nullptr;
+                    ms->pool_cap[1] = 0;
+                }
+            }
+            PURIFY_TRY(ensure_bytes(h, &ms->dpool, &ms->dpool_cap, need, ((size_t)nb * nb + 1) * 8192));
+            PURIFY_CUDA_TRY(cudaMemsetAsync(ms->dpool, 0, used1 * 8192, h->stream));
         }
         ms->pool_bytes_peak = std::max(ms->pool_bytes_peak,
                                        (double)(used0 * pool_slot_bytes(s) + used1 * pool_slot_bytes(so)));
@@ -632,15 +864,14 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
         st.err = ms->err;
         st.scratch = ms->scratch;
         st.max_ctas = ms->ctas;
-        st.kc_cnt = kc_cnt;
-        st.kc_mask = kc_mask;
+        st.kc_mask = ms->kc_buf;
         st.bnorm2 = ms->bnorm2;
         st.wait_cycles = 1000ll * h->opt.wait_kcycles;
+        st.out_idx = ms->pidx[1];
         if (last) {
-            st.out64 = D;
+            st.out64 = ms->dpool;
         } else {
             st.out = ms->pool[1];
-            st.out_idx = ms->pidx[1];
             st.s_out = so;
             st.e_out = 0;
         }
@@ -650,26 +881,40 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
         ++h->st.product_launches;
         h->st.tensor_flops += 0.5 * s * (s + 1) * pairs_tile * chunks;
         PURIFY_TRY(product_end(h));
-        PURIFY_TRY(truncate_step(h, out, tau, last ? nullptr : ms->pidx[1], last ? D : nullptr, n));
+        PURIFY_TRY(truncate_step(h, out, tau, ms->pidx[1], nullptr, n));
         X = out;
         ms->nnzb_history.push_back(X.count_upper());
         if (!last) {
             // the kept blocks into pool 0 (the step that read it is complete:
             // truncate_step waited for the stream)
-            used0 = assign_slots(X, idx);
-            PURIFY_TRY(ensure_pool(h, 0, used0 * pool_slot_bytes(so), max_bytes));
-            PURIFY_TRY(upload_slots(h, 0, idx, so));
-            const int total_warps = nb * nb;
-            const unsigned grid = (unsigned)std::min(152 * 8, (total_warps + 7) / 8);
+            PURIFY_TRY(upload_table(h, X, ms->pidx[0], &used0));
+            PURIFY_TRY(ensure_bytes(h, &ms->pool[0], &ms->pool_cap[0], used0 * pool_slot_bytes(so), max_bytes));
+            PURIFY_CUDA_TRY(cudaMemsetAsync(ms->pool[0], 0, pool_slot_bytes(so), h->stream));
+            const unsigned grid = (unsigned)std::min<int64_t>(152 * 8, ((int64_t)nb * nb + 7) / 8);
             compact_slots_kernel<<<grid, 256, 0, h->stream>>>(ms->pool[1], ms->pidx[1], ms->pool[0], ms->pidx[0], nb,
                                                                plane_pairs(so));
             PURIFY_CUDA_TRY(cudaGetLastError());
             count_launches(1);
             ms->pool_bytes_peak = std::max(ms->pool_bytes_peak,
                                            (double)((used0 + used1) * pool_slot_bytes(so)));
+        } else {
+            ms->pool_bytes_peak = std::max(ms->pool_bytes_peak, (double)(used0 * pool_slot_bytes(s) + used1 * 8192));
+            for (int I = 0; I < nb; ++I) {
+                const uint64_t* r = X.row(I);
+                for (int w = I >> 6; w < X.words; ++w) {
+                    uint64_t bits = r[w];
+                    if (w == (I >> 6)) bits &= ~0ull << (I & 63);  // J >= I
+                    for (; bits; bits &= bits - 1)
+                        ms->d_blocks.push_back(make_int2(I, w * 64 + __builtin_ctzll(bits)));
+                }
+            }
+            ms->d_pooled = true;
         }
     }
-    if (m == 0) PURIFY_TRY(launch_affine_f64(h->F, n, D, n, c1, c0, h->stream));
+    if (m == 0) {
+        PURIFY_TRY(ensure_dense_F(h));
+        PURIFY_TRY(launch_affine_f64(h->F, n, h->X[0], n, c1, c0, h->stream));
+    }
     PURIFY_CUDA_TRY(cudaEventRecord(h->e1, h->stream));
     red.assign(4 * (size_t)slots, 0.0);
     int err = 0;

@@ -223,3 +223,75 @@ def test_truncation_budget_vs_oracle(P, L, scheme):
         assert diff <= 1e-8, diff
     else:
         assert diff <= 3e-7 + 2 * r.tau * (hi - lo) / (2 * g), diff
+
+
+def test_density_blocks_expand_to_the_density(P):
+    # the kept blocks of a block-sparse run, read as a block list, are the
+    # nonzero blocks of the dense density (host and device outputs agree)
+    lat, F, lo, hi = _lattice(12)
+    g = lat.gap_bound
+    pur = P.Purifier(precision="mixed", block_sparse=True, trunc_tau=1e-6)
+    pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0, homo=-g, lumo=g)
+    pur.run("TC_SF", 1e-9, 200)
+    st = pur.stats()
+    D = pur.density()
+    Dd = torch.empty((lat.n, lat.n), dtype=torch.float64, device="cuda")
+    pur.density(Dd)
+    ij, vals = pur.density_blocks()
+    assert pur.density_device_ptr() == 0
+    pur.close()
+    assert np.array_equal(Dd.cpu().numpy(), D)
+    assert len(ij) == st["nnz_blocks"] and np.all(ij[:, 0] <= ij[:, 1])
+    assert np.array_equal(ij, ij[np.lexsort((ij[:, 1], ij[:, 0]))])  # row-major order
+    n, nb = lat.n, (lat.n + 127) // 128 * 4
+    Dp = np.zeros((nb * 32, nb * 32))
+    for (I_, J_), v in zip(ij, vals):
+        Dp[32 * I_:32 * I_ + 32, 32 * J_:32 * J_ + 32] = v
+        Dp[32 * J_:32 * J_ + 32, 32 * I_:32 * I_ + 32] = v.T
+    assert np.array_equal(Dp[:n, :n], D)
+    assert not Dp[n:, :].any() and not Dp[:, n:].any()
+    assert abs(np.trace(D) - lat.nocc) < 1e-6
+
+
+def test_csr_form_bounds_and_dense_paths(P):
+    # a block-sparse handle keeps F as CSR: its estimated bounds agree with
+    # the dense estimate to rounding, and a dense path asked for afterwards
+    # (options changed to the dense mixed path) gets F from the CSR copy and
+    # the same result as a handle loaded densely
+    lat, F, lo, hi = _lattice(8, instance=2)
+    g = lat.gap_bound
+    a = P.Purifier(precision="mixed", block_sparse=True)
+    a.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0, homo=-g, lumo=g)
+    b = P.Purifier(precision="mixed")
+    b.set_hamiltonian(F, nocc=lat.nocc, mu=0.0, homo=-g, lumo=g)
+    sa, sb = a.stats(), b.stats()
+    for k in ("lmin", "lmax"):
+        assert abs(sa[k] - sb[k]) <= 1e-12 * (abs(sb[k]) + 1.0), (k, sa[k], sb[k])
+    # the same bounds on both handles, then the dense mixed path on each
+    for h in (a, b):
+        h.set_options(block_sparse=False)
+    a.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0, lmin=lo, lmax=hi,
+                          homo=-g, lumo=g)
+    b.set_hamiltonian(F, nocc=lat.nocc, mu=0.0, lmin=lo, lmax=hi, homo=-g, lumo=g)
+    for h in (a, b):
+        h.run("TC_SF", 1e-9, 200)
+    assert np.array_equal(a.density(), b.density())
+    # CSR form kept, dense path requested later: the same again
+    c = P.Purifier(precision="mixed", block_sparse=True)
+    c.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0, lmin=lo, lmax=hi,
+                          homo=-g, lumo=g)
+    c.set_options(block_sparse=False)
+    c.run("TC_SF", 1e-9, 200)
+    assert np.array_equal(c.density(), b.density())
+    for h in (a, b, c):
+        h.close()
+
+
+def test_block_sparse_density_refuses_fp64_refinement(P):
+    lat, F, lo, hi = _lattice(8)
+    g = lat.gap_bound
+    pur = P.Purifier(precision="mixed", block_sparse=True, refine_fp64=1)
+    pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0, homo=-g, lumo=g)
+    with pytest.raises(P.PurifyError):
+        pur.run("TC_SF", 1e-9, 200)
+    pur.close()
