@@ -22,9 +22,11 @@
 #include <cstddef>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <thread>
 #include <vector>
 
+#include "digits_kernel.cuh"
 #include "digits_tc.h"
 #include "mixed.h"
 #include "queue_plan.h"
@@ -33,13 +35,19 @@ namespace purify {
 
 namespace {
 
-// Blocks (I, J) and (J, I) leave a pool's slot table: from then on they
-// read as slot 0, the zero block.
-__global__ void drop_slots_kernel(int* idx, int nb, const int2* blocks, int count) {
+// Blocks (I, J) and (J, I) leave the pattern's bits (words per row) and,
+// when idx is set, a pool's slot table: from then on they read as slot 0,
+// the zero block.
+__global__ void drop_blocks_kernel(unsigned long long* pat, int words, int* idx, int nb, const int2* blocks,
+                                   int count) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
         const int2 b = blocks[k];
-        idx[(size_t)b.x * nb + b.y] = 0;
-        idx[(size_t)b.y * nb + b.x] = 0;
+        atomicAnd(&pat[(size_t)b.x * words + (b.y >> 6)], ~(1ull << (b.y & 63)));
+        atomicAnd(&pat[(size_t)b.y * words + (b.x >> 6)], ~(1ull << (b.x & 63)));
+        if (idx) {
+            idx[(size_t)b.x * nb + b.y] = 0;
+            idx[(size_t)b.y * nb + b.x] = 0;
+        }
     }
 }
 
@@ -200,10 +208,13 @@ struct Pattern {
     void clear(int I, int J) { bits[(size_t)I * words + (J >> 6)] &= ~((uint64_t)1 << (J & 63)); }
     const uint64_t* row(int I) const { return &bits[(size_t)I * words]; }
     uint64_t* row(int I) { return &bits[(size_t)I * words]; }
-    int count_upper() const {
+    int count_upper() const {  // blocks with J >= I
         int c = 0;
-        for (int I = 0; I < nb; ++I)
-            for (int J = I; J < nb; ++J) c += get(I, J);
+        for (int I = 0; I < nb; ++I) {
+            const uint64_t* r = row(I);
+            c += __builtin_popcountll(r[I >> 6] & (~0ull << (I & 63)));
+            for (int w = (I >> 6) + 1; w < words; ++w) c += __builtin_popcountll(r[w]);
+        }
         return c;
     }
 };
@@ -290,14 +301,15 @@ int grow(T** p, size_t* cap, size_t n) {
     return PURIFY_OK;
 }
 
-// Remove the chosen blocks from a pool's slot table and / or zero them in
-// the float64 result.
-int apply_drops(purify_ctx* h, size_t count, int* idx, int nb, double* out64, int n) {
+// Remove the chosen blocks (ms->drops[0 .. count)) from the device pattern
+// (words per row) and a pool's slot table, and / or zero them in the float64
+// result.
+int apply_drops(purify_ctx* h, size_t count, int words, int* idx, int nb, double* out64, int n) {
     MixedState* ms = h->mixed;
     if (count == 0) return PURIFY_OK;
-    if (idx) {
+    {
         const unsigned grid = (unsigned)std::min<size_t>((count + 255) / 256, 152 * 4);
-        drop_slots_kernel<<<grid, 256, 0, h->stream>>>(idx, nb, ms->drops, (int)count);
+        drop_blocks_kernel<<<grid, 256, 0, h->stream>>>(ms->pat_dev, words, idx, nb, ms->drops, (int)count);
         PURIFY_CUDA_TRY(cudaGetLastError());
         count_launches(1);
     }
@@ -310,8 +322,8 @@ int apply_drops(purify_ctx* h, size_t count, int* idx, int nb, double* out64, in
 }
 
 // Choose the drops of one step on the device (see trunc_hist_kernel) and
-// zero them; the host receives the dropped blocks for its pattern and walks
-// the blocks tied at the selected norm in (row, column) order.
+// remove them; the host walks the blocks tied at the selected norm in (row,
+// column) order and receives the pattern that remains.
 int truncate_step(purify_ctx* h, Pattern& pat, double tau, int* idx, double* out64, int n) {
     MixedState* ms = h->mixed;
     const int nb = pat.nb, words = pat.words;
@@ -347,9 +359,6 @@ int truncate_step(purify_ctx* h, Pattern& pat, double tau, int* idx, double* out
     PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
     if (head.ntie > kTieCap) return PURIFY_ERR_INTERNAL;
     size_t nd = (size_t)head.ndrop;
-    std::vector<int2> drop(nd);
-    if (nd)
-        PURIFY_CUDA_TRY(cudaMemcpyAsync(drop.data(), ms->drops, sizeof(int2) * nd, cudaMemcpyDeviceToHost, h->stream));
     std::vector<int2> tie((size_t)head.ntie);
     if (head.ntie)
         PURIFY_CUDA_TRY(cudaMemcpyAsync(tie.data(), tie_dev, sizeof(int2) * tie.size(), cudaMemcpyDeviceToHost,
@@ -373,15 +382,15 @@ int truncate_step(purify_ctx* h, Pattern& pat, double tau, int* idx, double* out
         if (k) {
             PURIFY_CUDA_TRY(cudaMemcpyAsync(ms->drops + nd, tie.data(), sizeof(int2) * k, cudaMemcpyHostToDevice,
                                             h->stream));
-            drop.insert(drop.end(), tie.begin(), tie.begin() + (ptrdiff_t)k);
             nd += k;
         }
     }
-    for (const int2& b : drop) {
-        pat.clear(b.x, b.y);
-        pat.clear(b.y, b.x);
-    }
-    return apply_drops(h, nd, idx, nb, out64, n);
+    PURIFY_TRY(apply_drops(h, nd, words, idx, nb, out64, n));
+    if (nd)
+        PURIFY_CUDA_TRY(cudaMemcpyAsync(pat.bits.data(), ms->pat_dev, sizeof(uint64_t) * pat.bits.size(),
+                                        cudaMemcpyDeviceToHost, h->stream));
+    PURIFY_CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return PURIFY_OK;
 }
 
 void tc_coeffs(int branch, double a, double* cP, double* cE, double* cI) {
@@ -583,24 +592,49 @@ void panel_bits(const Pattern& X, int T, std::vector<uint64_t>& pan) {
             for (int w = 0; w < X.words; ++w) pan[(size_t)t * X.words + w] |= X.row(r)[w];
 }
 
-// The upper 128 x 128 tiles holding a block of `out`, in banded order: the
-// product's work items {0, ti, tj, 0}; chunks receives the k-chunk products
-// they run (the popcount of the two panels' bits of X).
+// The upper 128 x 128 tiles holding a block of `out`, in banded order (see
+// banded_tiles): the product's work items {0, ti, tj, 0}; chunks receives
+// the k-chunk products they run (the popcount of the two panels' bits of X).
+// Bands are independent: large patterns are split over host threads.
 void pattern_tiles(const Pattern& out, const std::vector<uint64_t>& xpan, int words, int T,
                    std::vector<int4>& work, double* chunks) {
     std::vector<uint64_t> opan;
     panel_bits(out, T, opan);
-    std::vector<int2> band;
-    banded_tiles(T, band);
+    const int bands = (T + dk::BAND - 1) / dk::BAND;
+    auto run = [&](int b_lo, int b_hi, std::vector<int4>& w_out, double& c_out) {
+        double c = 0.0;
+        for (int band = b_lo; band < b_hi; ++band) {
+            const int b0 = band * dk::BAND, b1 = std::min(T, b0 + dk::BAND);
+            for (int r = 0; r < b1; ++r)
+                for (int t = std::max(b0, r); t < b1; ++t) {
+                    const int J0 = 4 * t;
+                    if (!((opan[(size_t)r * words + (J0 >> 6)] >> (J0 & 63)) & 0xFull)) continue;
+                    w_out.push_back(make_int4(0, r, t, 0));
+                    const uint64_t* a = &xpan[(size_t)r * words];
+                    const uint64_t* b = &xpan[(size_t)t * words];
+                    for (int w = 0; w < words; ++w) c += (double)__builtin_popcountll(a[w] & b[w]);
+                }
+        }
+        c_out = c;
+    };
+    const int hw = (int)std::thread::hardware_concurrency();
+    const int nt = T >= 256 ? std::max(1, std::min({hw, 16, bands})) : 1;
+    std::vector<std::vector<int4>> parts(nt);
+    std::vector<double> csum(nt, 0.0);
+    if (nt == 1) {
+        run(0, bands, parts[0], csum[0]);
+    } else {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < nt; ++t)
+            pool.emplace_back(run, (int)((int64_t)bands * t / nt), (int)((int64_t)bands * (t + 1) / nt),
+                              std::ref(parts[t]), std::ref(csum[t]));
+        for (std::thread& th : pool) th.join();
+    }
     work.clear();
     double c = 0.0;
-    for (const int2& t : band) {
-        const int J0 = 4 * t.y;
-        if (!((opan[(size_t)t.x * words + (J0 >> 6)] >> (J0 & 63)) & 0xFull)) continue;
-        work.push_back(make_int4(0, t.x, t.y, 0));
-        const uint64_t* a = &xpan[(size_t)t.x * words];
-        const uint64_t* b = &xpan[(size_t)t.y * words];
-        for (int w = 0; w < words; ++w) c += (double)__builtin_popcountll(a[w] & b[w]);
+    for (int t = 0; t < nt; ++t) {
+        work.insert(work.end(), parts[t].begin(), parts[t].end());
+        c += csum[t];
     }
     *chunks = c;
 }
