@@ -729,9 +729,52 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 }
                 int w = 0;
                 unsigned long long bits = POOL ? pool_chunk_word(Pg, ti, tj, 0) : (km ? km[0] : 0ull);
+                // pooled: the next k-chunk and its eight slot-table entries are
+                // read one chunk ahead, so that their latency overlaps the
+                // current chunk's wait and copies
+                int ka[4] = {0, 0, 0, 0}, kb2[4] = {0, 0, 0, 0};
+                int na[4] = {0, 0, 0, 0}, nb2[4] = {0, 0, 0, 0};
+                int kc_next = -1;
+                auto pool_next = [&]() -> int {
+                    while (bits == 0ull && w + 1 < Pg.kc_words) {
+                        ++w;
+                        bits = pool_chunk_word(Pg, ti, tj, w);
+                    }
+                    if (bits == 0ull) return -1;
+                    const int k = w * 64 + __ffsll((long long)bits) - 1;
+                    bits &= bits - 1;
+                    return k;
+                };
+                auto pool_fetch = [&](int k) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        na[r] = Pg.a_idx[(size_t)(4 * ti + r) * Pg.nb + k];
+                        nb2[r] = Pg.b_idx[(size_t)(4 * tj + r) * Pg.nb + k];
+                    }
+                };
+                if constexpr (POOL) {
+                    if (nk > 0) {
+                        kc_next = pool_next();
+                        if (kc_next >= 0) pool_fetch(kc_next);
+                    }
+                }
                 for (int c = 0; c < nk; ++c, ++it) {
                     int kc = kb + c;
-                    if (masked) {
+                    if constexpr (POOL) {
+                        kc = kc_next;
+                        if (kc < 0) {  // count and mask disagree
+                            atomicOr(L.err, ERR_PLAN);
+                            *abort_flag = 1;
+                            break;
+                        }
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            ka[r] = na[r];
+                            kb2[r] = nb2[r];
+                        }
+                        kc_next = c + 1 < nk ? pool_next() : -1;
+                        if (kc_next >= 0) pool_fetch(kc_next);
+                    } else if (masked) {
                         while (bits == 0ull && w + 1 < Pg.kc_words) {
                             ++w;
                             bits = POOL ? pool_chunk_word(Pg, ti, tj, w) : km[w];
@@ -758,12 +801,6 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     if constexpr (POOL) {
                         // the panels' four 32-row blocks of k-block kc, one box per
                         // block and plane pair (absent blocks: the zero slot)
-                        int ka[4], kb2[4];
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            ka[r] = Pg.a_idx[(size_t)(4 * ti + r) * Pg.nb + kc];
-                            kb2[r] = Pg.b_idx[(size_t)(4 * tj + r) * Pg.nb + kc];
-                        }
 #pragma unroll
                         for (int r = 0; r < 4; ++r)
 #pragma unroll
