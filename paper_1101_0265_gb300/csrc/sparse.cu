@@ -120,38 +120,59 @@ __global__ void trunc_hist_kernel(const float* __restrict__ bn2, const unsigned 
     }
 }
 
+__device__ __forceinline__ unsigned long long sat_add(unsigned long long a, unsigned long long b) {
+    const unsigned long long c = a + b;
+    return c < a ? ~0ull : c;
+}
+
 // One CTA of 1024 threads: the first bin whose cumulative mass (added to
-// `base`) exceeds the budget; clears the histogram for the next pass.
+// `base`) exceeds the budget; clears the histogram for the next pass.  Warp
+// w owns bins [2048 w, 2048 w + 2048) and reads them 32 at a time
+// (coalesced): first its total, then, after an exclusive prefix of the 32
+// warp totals, its bins in order with a warp scan per 32 until the crossing.
+// Sums saturate (only sums up to the crossing matter, and those stay within
+// the budget plus one bin).
 __global__ void __launch_bounds__(1024) trunc_scan_kernel(TruncSel* sel, int pass) {
-    __shared__ unsigned long long part[1024];
+    constexpr int kWarps = 32, kPerWarp = kHistBins / kWarps;
+    __shared__ unsigned long long wsum[kWarps];
     __shared__ int first;
-    const int t = threadIdx.x;
-    constexpr int per = kHistBins / 1024;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned long long base = pass ? sel->cum_before : 0ull;
-    unsigned long long sum = 0;
-    for (int b = t * per; b < (t + 1) * per; ++b) sum += sel->hist_fx[b];
-    part[t] = sum;
-    if (t == 0) first = kHistBins;
-    __syncthreads();
-    // exclusive prefix of the 1024 partial sums (fixed order)
-    for (int o = 1; o < 1024; o <<= 1) {
-        const unsigned long long v = t >= o ? part[t - o] : 0ull;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    unsigned long long cum = base + (t ? part[t - 1] : 0ull);
     const unsigned long long budget = (unsigned long long)kBudgetUnits;
+    const unsigned long long* fx = sel->hist_fx + warp * kPerWarp;
+    const unsigned int* cnt = sel->hist_cnt + warp * kPerWarp;
+    unsigned long long s = 0;
+#pragma unroll 8
+    for (int c = lane; c < kPerWarp; c += 32) s = sat_add(s, fx[c]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = sat_add(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if (lane == 0) wsum[warp] = s;
+    if (threadIdx.x == 0) first = kHistBins;
+    __syncthreads();
+    unsigned long long cum = base;  // base + the bins of the warps before this one
+    for (int q = 0; q < warp; ++q) cum = sat_add(cum, wsum[q]);
     int mine = kHistBins;
     unsigned long long before = 0;
-    for (int b = t * per; b < (t + 1) * per; ++b) {
-        const unsigned long long v = sel->hist_fx[b];
-        if (sel->hist_cnt[b] && cum + v > budget) {
-            mine = b;
-            before = cum;
+    for (int c0 = 0; c0 < kPerWarp; c0 += 32) {
+        const unsigned long long v = fx[c0 + lane];
+        const bool has = cnt[c0 + lane] != 0;
+        unsigned long long incl = v;  // this chunk's bins up to this lane
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl = sat_add(incl, u);
+        }
+        unsigned long long excl = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) excl = 0ull;
+        const unsigned m = __ballot_sync(0xffffffffu, has && sat_add(cum, incl) > budget);
+        if (m) {
+            if (lane == __ffs(m) - 1) {
+                mine = warp * kPerWarp + c0 + lane;
+                before = cum + excl;
+            }
             break;
         }
-        cum += v;
+        cum = sat_add(cum, __shfl_sync(0xffffffffu, incl, 31));
     }
     if (mine < kHistBins) atomicMin(&first, mine);
     __syncthreads();
@@ -165,8 +186,8 @@ __global__ void __launch_bounds__(1024) trunc_scan_kernel(TruncSel* sel, int pas
             sel->key = ((unsigned)sel->hi << 16) | (unsigned)mine;
     }
     __syncthreads();
-    if (t == 0 && first == kHistBins) sel->found = 0;
-    for (int b = t; b < kHistBins; b += 1024) {
+    if (threadIdx.x == 0 && first == kHistBins) sel->found = 0;
+    for (int b = threadIdx.x; b < kHistBins; b += 1024) {
         sel->hist_fx[b] = 0;
         sel->hist_cnt[b] = 0;
     }
