@@ -231,6 +231,7 @@ class Purifier:
                "purify_create")
         self._h = h
         self.n = 0
+        self.device = int(device)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -317,16 +318,23 @@ class Purifier:
         _check(self._lib.purify_get_density(self._h, _ptr(out), ld), "purify_get_density")
         return out
 
-    def density_blocks(self, values: bool = True):
+    def density_blocks(self, values: bool = True, device: bool = False):
         """The kept 32 x 32 blocks of a block-sparse run's density: an
         (m, 2) int32 array of (I, J), I <= J, and an (m, 32, 32) float64
-        array of the blocks (None when values is False)."""
+        array of the blocks (None when values is False); numpy arrays, or
+        torch tensors on the handle's device when `device`."""
         cnt = C.c_int64(0)
         _check(self._lib.purify_get_density_blocks(self._h, None, None, 0, C.byref(cnt)),
                "purify_get_density_blocks")
         m = cnt.value
-        ij = np.empty((max(m, 1), 2), dtype=np.int32)
-        vals = np.empty((max(m, 1), 32, 32), dtype=np.float64) if values else None
+        if device:
+            import torch
+            dev = torch.device("cuda", self.device)
+            ij = torch.empty((max(m, 1), 2), dtype=torch.int32, device=dev)
+            vals = torch.empty((max(m, 1), 32, 32), dtype=torch.float64, device=dev) if values else None
+        else:
+            ij = np.empty((max(m, 1), 2), dtype=np.int32)
+            vals = np.empty((max(m, 1), 32, 32), dtype=np.float64) if values else None
         _check(self._lib.purify_get_density_blocks(self._h, _ptr(ij), _ptr(vals) if values else None, m,
                                                     C.byref(cnt)), "purify_get_density_blocks")
         return ij[:m], (vals[:m] if values else None)

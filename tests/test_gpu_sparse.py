@@ -339,3 +339,33 @@ def test_csr_form_at_a_ragged_size_equals_the_dense_path(P, kind):
     assert out[True][1]["iterations"] == out[False][1]["iterations"]
     if kind == "chain":
         assert out[True][1]["tensor_flops"] < out[False][1]["tensor_flops"]
+
+
+def test_pooled_density_host_and_device_outputs_agree(P):
+    # 24^3 at onsite +-6.0 (n = 13824): a host density goes through several
+    # staging panels, and more kept blocks than one host staging pass holds;
+    # host and device outputs of both readers are the same bits
+    lat = I.lattice_hamiltonian(24, onsite=6.0)
+    g = lat.gap_bound
+    pur = P.Purifier(precision="mixed", block_sparse=True, trunc_tau=1e-6)
+    pur.set_hamiltonian_coo(lat.n, lat.rows, lat.cols, lat.vals, nocc=lat.nocc, mu=0.0, homo=-g, lumo=g)
+    pur.run("TC_SF", 1e-9, 300)
+    st = pur.stats()
+    n = lat.n
+    assert n * n * 8 > 2 * (256 << 20)                  # at least three staging panels
+    Dh = pur.density()
+    Dd = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    pur.density(Dd)
+    assert np.array_equal(Dh, Dd.cpu().numpy())
+    del Dd
+    ij_h, v_h = pur.density_blocks()
+    ij_d, v_d = pur.density_blocks(device=True)
+    pur.close()
+    assert len(ij_h) == st["nnz_blocks"] > (256 << 20) // 8192  # more than one staging pass
+    assert np.array_equal(ij_h, ij_d.cpu().numpy())
+    assert np.array_equal(v_h, v_d.cpu().numpy())
+    # the blocks are D's: spot-check a few against the dense output
+    for k in np.random.default_rng(3).integers(0, len(ij_h), 16):
+        I_, J_ = ij_h[k]
+        assert np.array_equal(v_h[k], Dh[32 * I_:32 * I_ + 32, 32 * J_:32 * J_ + 32])
+    torch.cuda.empty_cache()
