@@ -37,13 +37,13 @@ FP64_FLOP_PER_CLK_SM = 4         # two float64 FMAs per SM and clock (nominal)
 # The tensor pipe's active share of one queue launch of the digit-plane
 # product (ncu sm__pipe_tensor_cycles_active of digit_gemm_kernel<32, 5, 2>:
 # one TC_SF run at n = 4096, 14 products in one launch).
-TENSOR_PIPE_PCT_NCU = 75.5
+TENSOR_PIPE_PCT_NCU = 75.3
 TENSOR_PIPE_SOURCE = "profiles/digit_gemm_queue_s5_n4096.md (ncu, one queue launch, n=4096, S=5, 14 products)"
 # DRAM bytes (read + write) of that launch, from the same ncu capture.
-TRAFFIC_DIGIT_GEMM = 17.769e9
+TRAFFIC_DIGIT_GEMM = 17.603e9
 TRAFFIC_PRODUCTS = 14
 TRAFFIC_SOURCE = ("ncu dram__bytes_read+write of digit_gemm_kernel<32,5,2>, n=4096, one queue launch of 14 "
-                  "products (14.445 GB read + 3.324 GB written; 1.269 GB per product)")
+                  "products (14.272 GB read + 3.331 GB written; 1.257 GB per product)")
 
 
 def parse():
