@@ -66,7 +66,7 @@ def test_headline_mixed_vs_closed_form(P, handle, cases, scheme, nocc, gap):
     st = handle.stats()
     D = handle.density()
     err = float(np.max(np.abs(D - Dc)))
-    # the benchmark spec's bound for the mixed path
+    # the accuracy bound of the n = 4096 workload's metric (1e-6)
     assert err <= 1e-6, err
     # trace and idempotency of the result, from D itself: a symmetric error E
     # with |E_ij| <= err moves the trace by at most n err and leaves
