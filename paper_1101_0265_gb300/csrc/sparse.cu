@@ -51,18 +51,6 @@ __global__ void drop_blocks_kernel(unsigned long long* pat, int words, int* idx,
     }
 }
 
-// Zero blocks (I, J) and (J, I) of an n x n float64 matrix.
-__global__ void mask_f64_kernel(double* D, int n, const int2* blocks) {
-    const int2 b = blocks[blockIdx.x];
-    for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
-        const int r = e >> 5, c = e & 31;
-        const int i0 = b.x * 32 + r, j0 = b.y * 32 + c;
-        if (i0 < n && j0 < n) D[(size_t)i0 * n + j0] = 0.0;
-        const int i1 = b.y * 32 + r, j1 = b.x * 32 + c;
-        if (i1 < n && j1 < n) D[(size_t)i1 * n + j1] = 0.0;
-    }
-}
-
 // ---- truncation selection on the device -------------------------------------
 // The greedy reading of the truncation (blocks in ascending norm, ties by
 // row then column, dropped while the dropped mass stays within tau^2) picks a
@@ -323,29 +311,21 @@ int grow(T** p, size_t* cap, size_t n) {
 }
 
 // Remove the chosen blocks (ms->drops[0 .. count)) from the device pattern
-// (words per row) and a pool's slot table, and / or zero them in the float64
-// result.
-int apply_drops(purify_ctx* h, size_t count, int words, int* idx, int nb, double* out64, int n) {
+// (words per row) and from the output pool's slot table.
+int apply_drops(purify_ctx* h, size_t count, int words, int* idx, int nb) {
     MixedState* ms = h->mixed;
     if (count == 0) return PURIFY_OK;
-    {
-        const unsigned grid = (unsigned)std::min<size_t>((count + 255) / 256, 152 * 4);
-        drop_blocks_kernel<<<grid, 256, 0, h->stream>>>(ms->pat_dev, words, idx, nb, ms->drops, (int)count);
-        PURIFY_CUDA_TRY(cudaGetLastError());
-        count_launches(1);
-    }
-    if (out64) {
-        mask_f64_kernel<<<(unsigned)count, 256, 0, h->stream>>>(out64, n, ms->drops);
-        PURIFY_CUDA_TRY(cudaGetLastError());
-        count_launches(1);
-    }
+    const unsigned grid = (unsigned)std::min<size_t>((count + 255) / 256, 152 * 4);
+    drop_blocks_kernel<<<grid, 256, 0, h->stream>>>(ms->pat_dev, words, idx, nb, ms->drops, (int)count);
+    PURIFY_CUDA_TRY(cudaGetLastError());
+    count_launches(1);
     return PURIFY_OK;
 }
 
 // Choose the drops of one step on the device (see trunc_hist_kernel) and
 // remove them; the host walks the blocks tied at the selected norm in (row,
 // column) order and receives the pattern that remains.
-int truncate_step(purify_ctx* h, Pattern& pat, double tau, int* idx, double* out64, int n) {
+int truncate_step(purify_ctx* h, Pattern& pat, double tau, int* idx) {
     MixedState* ms = h->mixed;
     const int nb = pat.nb, words = pat.words;
     const double budget = tau * tau;
@@ -406,7 +386,7 @@ int truncate_step(purify_ctx* h, Pattern& pat, double tau, int* idx, double* out
             nd += k;
         }
     }
-    PURIFY_TRY(apply_drops(h, nd, words, idx, nb, out64, n));
+    PURIFY_TRY(apply_drops(h, nd, words, idx, nb));
     if (nd)
         PURIFY_CUDA_TRY(cudaMemcpyAsync(pat.bits.data(), ms->pat_dev, sizeof(uint64_t) * pat.bits.size(),
                                         cudaMemcpyDeviceToHost, h->stream));
@@ -936,7 +916,7 @@ int run_block_sparse(purify_ctx* h, int scheme, const Schedule& S, int* cur, std
         ++h->st.product_launches;
         h->st.tensor_flops += 0.5 * s * (s + 1) * pairs_tile * chunks;
         PURIFY_TRY(product_end(h));
-        PURIFY_TRY(truncate_step(h, out, tau, ms->pidx[1], nullptr, n));
+        PURIFY_TRY(truncate_step(h, out, tau, ms->pidx[1]));
         X = out;
         ms->nnzb_history.push_back(X.count_upper());
         if (!last) {
