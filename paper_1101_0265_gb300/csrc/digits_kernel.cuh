@@ -1093,19 +1093,30 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                 }
                 cp_async_commit();
             };
-            if (use_E) fetch_E(col0);
+            // the warp's columns [c_lo, c_hi).  Pooled: leading and trailing
+            // 32 x 32 blocks outside the output pattern are skipped; there X
+            // and the product are exactly zero (every k-chunk product has a
+            // zero operand block), so Y, its norms and its reductions are
+            // zero too
+            int c_lo = col0, c_hi = col0 + EPI_COLS;
+            if constexpr (POOL) {
+                const int* orow = P.out_idx + (size_t)(i >> 5) * P.nb + ((tj * TILE) >> 5);
+                while (c_lo < c_hi && orow[c_lo >> 5] == 0) c_lo += 32;
+                while (c_hi > c_lo && orow[(c_hi - 32) >> 5] == 0) c_hi -= 32;
+            }
+            if (use_E && c_lo < c_hi) fetch_E(c_lo);
             // the double-float P of the next pass is loaded while this pass
             // re-splits and stores
             float4 pv_next[EW / 2];
-            {
-                const float4* src = (const float4*)scr;
+            if (c_lo < c_hi) {
+                const float4* src = (const float4*)(scr + ((c_lo - col0) >> 3) * 256);
 #pragma unroll
                 for (int c = 0; c < EW / 2; ++c) pv_next[c] = src[(c >> 2) * 128 + (c & 3)];
             }
             // EW columns per pass: a short loop body keeps the epilogue's
             // instructions resident while the other warps run
 #pragma unroll 1
-            for (int c0 = col0; c0 < col0 + EPI_COLS; c0 += EW) {
+            for (int c0 = c_lo; c0 < c_hi; c0 += EW) {
                 const int jb = tj * TILE + c0;
                 df Ov[EW];
                 {
@@ -1133,7 +1144,7 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                             }
                         }
                         // this pass's pieces are in registers: fetch the next pass's
-                        if (c0 + EW < col0 + EPI_COLS) fetch_E(c0 + EW);
+                        if (c0 + EW < c_hi) fetch_E(c0 + EW);
                     }
                     float bsum = 0.f;
 #pragma unroll
@@ -1170,7 +1181,7 @@ __global__ void __maxnreg__(MAX_REGS) digit_gemm_kernel(const __grid_constant__ 
                     else
                         bn2_1 += bsum;
                 }
-                if (c0 + EW < col0 + EPI_COLS) {
+                if (c0 + EW < c_hi) {
                     const float4* src = (const float4*)(scr + ((c0 + EW - col0) >> 3) * 256);
 #pragma unroll
                     for (int c = 0; c < EW / 2; ++c) pv_next[c] = src[(c >> 2) * 128 + (c & 3)];
